@@ -1,0 +1,348 @@
+"""Pins for the FP64 oracle against facts that do not come from the oracle.
+
+Each check uses an independent route: direct numerical integration of the
+kernel's definition, closed values, exact invariants (mass conservation,
+translation symmetry, scale invariance), or brute-force ray casting over the
+cell.  A dropped term, a wrong sign or a transposed operand anywhere in the
+oracle's decomposition fails at least one of them.
+"""
+import math
+import os
+
+import numpy as np
+import pytest
+from scipy import integrate
+
+import oracle
+import synth
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+
+
+# ----------------------------------------------------------------- test-side kernel definition
+# The M4 cubic spline, support 2h, sigma = 1/pi (Section III-C names the kernel;
+# the formula is the standard one).  Written here independently of the oracle.
+def w_def(q):
+    q = np.asarray(q, dtype=float)
+    return np.where(q < 1, 1 - 1.5 * q**2 + 0.75 * q**3, np.where(q < 2, 0.25 * (2 - q) ** 3, 0.0))
+
+
+def W_def(r, h=1.0):
+    return w_def(np.asarray(r) / h) / (math.pi * h**3)
+
+
+# exact radial mass per steradian, int_0^u W(r,1) r^2 dr, via numpy polynomial antiderivatives
+_P_in = np.polynomial.Polynomial([1, 0, -1.5, 0.75]) * np.polynomial.Polynomial([0, 0, 1]) / math.pi
+_P_out = np.polynomial.Polynomial([2, -1]) ** 3 * 0.25 * np.polynomial.Polynomial([0, 0, 1]) / math.pi
+_A_in = _P_in.integ()
+_A_out = _P_out.integ()
+
+
+def Fr_def(u):
+    u = np.asarray(u, dtype=float)
+    m1 = _A_in(1.0) - _A_in(0.0)
+    m2 = m1 + _A_out(2.0) - _A_out(1.0)
+    return np.where(u < 1, _A_in(np.minimum(u, 1)) - _A_in(0.0),
+                    np.where(u < 2, m1 + _A_out(np.clip(u, 1, 2)) - _A_out(1.0), m2))
+
+
+def load_golden():
+    vals = {}
+    with open(os.path.join(HERE, "golden", "kernel_constants.txt")) as fh:
+        for line in fh:
+            line = line.split("#")[0].strip()
+            if line:
+                k, v = line.split()
+                vals[k] = float(v)
+    return vals
+
+
+# ----------------------------------------------------------------- helpers: hand-built cells
+
+class OneCellGrid:
+    """A single convex cell given as faces (planes + CCW vertex loops)."""
+
+    def __init__(self, verts, loops, site):
+        verts = np.asarray(verts, float)
+        self.vx, self.vy, self.vz = verts[:, 0].copy(), verts[:, 1].copy(), verts[:, 2].copy()
+        self.cell_face_off = np.array([0, len(loops)], np.int64)
+        fvo = [0]
+        fv = []
+        planes = []
+        for lp in loops:
+            fv += list(lp)
+            fvo.append(len(fv))
+            p = verts[list(lp)]
+            a = np.zeros(3)
+            for k in range(len(p)):
+                a += np.cross(p[k], p[(k + 1) % len(p)])
+            n = a / np.linalg.norm(a)
+            planes.append([n[0], n[1], n[2], float(n @ p[0])])
+        self.face_vert_off = np.array(fvo, np.int64)
+        self.face_vert = np.array(fv, np.int32)
+        self.face_plane = np.array(planes, float)
+        self.site = np.asarray(site, float).reshape(1, 3)
+
+    @property
+    def ncell(self):
+        return 1
+
+
+def box_cell(lo, hi):
+    lo = np.asarray(lo, float)
+    hi = np.asarray(hi, float)
+    v = [[(hi if i & 1 else lo)[0], (hi if i & 2 else lo)[1], (hi if i & 4 else lo)[2]] for i in range(8)]
+    loops = [[1, 3, 7, 5], [0, 4, 6, 2], [2, 6, 7, 3], [0, 1, 5, 4], [4, 5, 7, 6], [0, 2, 3, 1]]
+    return OneCellGrid(v, loops, 0.5 * (lo + hi))
+
+
+def frac_one(grid, pos, h):
+    r = oracle.map_cells(grid, [pos[0]], [pos[1]], [pos[2]], [1.0], [h], cells=[0],
+                         off=np.array([0, 1], np.int64), idx=np.array([0], np.int32), nthreads=1)
+    return float(r["frac"][0])
+
+
+# ----------------------------------------------------------------- kernel pins
+
+def test_kernel_normalisation_and_golden_masses():
+    g = load_golden()
+    tot = integrate.quad(lambda r: 4 * math.pi * r * r * W_def(r), 0, 2, points=[1])[0]
+    assert abs(tot - 1.0) < 1e-13
+    assert abs(4 * math.pi * oracle.F(1.0) - g["mass_within_h"]) < 1e-15
+    assert abs(4 * math.pi * oracle.F(2.0) - g["mass_within_2h"]) < 1e-15
+    for u in (0.0, 0.1, 0.37, 0.99, 1.0, 1.5, 1.99, 2.0, 3.0):
+        ref = integrate.quad(lambda r: r * r * W_def(r), 0, min(u, 2.0), points=[1] if u > 1 else None)[0]
+        assert abs(oracle.F(u) - ref) < 1e-15, u
+
+
+def test_H_continuity_and_derivative():
+    for b in (1.0, 2.0):
+        assert abs(oracle.H(b - 1e-13) - oracle.H(b + 1e-13)) < 1e-12
+    for u in (0.2, 0.7, 1.3, 1.8, 2.5, 4.0):
+        d = 1e-6
+        fd = (oracle.H(u + d) - oracle.H(u - d)) / (2 * d)
+        assert abs(fd - oracle.F(u) / u**2) < 1e-9, u
+
+
+# ----------------------------------------------------------------- vertex pyramid pins
+
+@pytest.mark.parametrize("r0,R0,phi", [(0.3, 0.4, 0.9), (1.2, 0.5, 1.2), (0.05, 1.5, 0.3),
+                                       (0.8, 0.1, 1.45), (1.7, 0.2, 0.7), (0.5, 2.5, 0.2)])
+def test_wedge_matches_3d_integral(r0, R0, phi):
+    """I(r0,R0,phi) against a direct volume integral over the pyramid: points
+    lam*(rho cos t, rho sin t, r0), lam in [0,1], rho in [0, R0 sec t], t in [0, phi];
+    dV = lam^2 rho r0 dlam drho dt."""
+    def inner(t):
+        rmax = R0 / math.cos(t)
+
+        def f2(rho):
+            L = math.sqrt(rho * rho + r0 * r0)
+            # int_0^1 W(lam L) lam^2 dlam = (1/L^3) int_0^L W(r) r^2 dr
+            return rho * r0 * float(Fr_def(L)) / L**3
+        return integrate.quad(f2, 0, rmax, epsabs=1e-14, epsrel=1e-12, limit=200)[0]
+    ref = integrate.quad(inner, 0, phi, epsabs=1e-14, epsrel=1e-12, limit=200)[0]
+    assert abs(oracle.wedge(r0, R0, phi) - ref) < 1e-11
+
+
+@pytest.mark.parametrize("r0,R0,phi", [(2.0, 0.5, 1.0), (2.7, 1.3, 0.4), (5.0, 0.01, 1.5)])
+def test_wedge_beyond_support_is_solid_angle(r0, R0, phi):
+    omega = phi - math.asin(r0 * math.sin(phi) / math.hypot(r0, R0))
+    assert abs(oracle.wedge(r0, R0, phi) - omega / (4 * math.pi)) < 1e-15
+
+
+def test_cube_containing_support_gives_one():
+    g = box_cell([-2.5, -2.5, -2.5], [2.5, 2.5, 2.5])
+    assert abs(frac_one(g, [0.0, 0.0, 0.0], 1.0) - 1.0) < 1e-13
+    # off-centre but the whole support still inside
+    assert abs(frac_one(g, [0.3, -0.2, 0.4], 1.0) - 1.0) < 1e-13
+
+
+@pytest.mark.parametrize("d", [0.0, 0.05, 0.4, 0.999, 1.0, 1.3, 1.95])
+def test_halfspace_mass(d):
+    """Box with one face at distance d, all others beyond the support:
+    f = 1 - P(d), P(d) = int_d^2 2 pi r (r - d) W(r) dr (cap areas)."""
+    P = integrate.quad(lambda r: 2 * math.pi * r * (r - d) * W_def(r), d, 2, points=[1] if d < 1 else None,
+                       epsabs=1e-15)[0]
+    g = box_cell([-5, -5, -5], [5, 5, d])
+    f = frac_one(g, [0.0, 0.0, 0.0], 1.0)
+    if d == 0.0:
+        assert abs(P - load_golden()["halfspace_mass_d0"]) < 1e-14
+    assert abs(f - (1.0 - P)) < 1e-12, (d, f, 1 - P)
+    # particle outside the box, mirrored: mass inside is P(d)
+    g2 = box_cell([-5, -5, d], [5, 5, 5])
+    assert abs(frac_one(g2, [0.0, 0.0, 0.0], 1.0) - P) < 1e-12
+
+
+def test_scale_invariance():
+    g = box_cell([0.1, -0.3, -0.2], [0.9, 0.4, 0.6])
+    f1 = frac_one(g, [0.35, 0.05, 0.9], 0.4)
+    lam = 3.7
+    g2 = box_cell(np.array([0.1, -0.3, -0.2]) * lam, np.array([0.9, 0.4, 0.6]) * lam)
+    f2 = frac_one(g2, np.array([0.35, 0.05, 0.9]) * lam, 0.4 * lam)
+    assert f1 > 1e-3
+    assert abs(f1 - f2) < 1e-13
+
+
+# ----------------------------------------------------------------- brute force: ray casting
+
+def raycast_fraction(planes, pos, h, nmu=700, nphi=1400):
+    """f = int dOmega [Fr(t_out/h) - Fr(t_in/h)] over rays from the particle
+    through the convex cell {x : n.x <= d} (h = 1 units after scaling)."""
+    mu, wmu = np.polynomial.legendre.leggauss(nmu)
+    ph = (np.arange(nphi) + 0.5) * 2 * math.pi / nphi
+    st = np.sqrt(1 - mu**2)
+    om = np.stack([st[:, None] * np.cos(ph)[None, :], st[:, None] * np.sin(ph)[None, :],
+                   np.broadcast_to(mu[:, None], (nmu, nphi))], -1).reshape(-1, 3)
+    wts = (wmu[:, None] * np.full(nphi, 2 * math.pi / nphi)[None, :]).ravel()
+    tin = np.zeros(len(om))
+    tout = np.full(len(om), np.inf)
+    for nx, ny, nz, d in planes:
+        n = np.array([nx, ny, nz])
+        num = d - n @ pos
+        den = om @ n
+        with np.errstate(divide="ignore", invalid="ignore"):
+            t = num / den
+        pos_den = den > 0
+        neg_den = den < 0
+        tout = np.where(pos_den, np.minimum(tout, t), tout)
+        tin = np.where(neg_den, np.maximum(tin, t), tin)
+        if num < 0:
+            tout = np.where(den == 0, -1.0, tout)
+    tout = np.minimum(tout, 1e3)
+    ok = tout > tin
+    val = np.where(ok, Fr_def(tout / h) - Fr_def(tin / h), 0.0)
+    return float(np.sum(val * wts))
+
+
+def test_raycast_brute_force_small_voronoi():
+    rng = np.random.default_rng(11)
+    pts = rng.random((10, 3))
+    grid = synth.voronoi(pts, nthreads=1)
+    parts = rng.random((6, 3))
+    hs = rng.uniform(0.1, 0.35, 6)
+    worst = 0.0
+    for c in range(grid.ncell):
+        f0, f1 = grid.cell_face_off[c], grid.cell_face_off[c + 1]
+        planes = grid.face_plane[f0:f1]
+        for a in range(len(parts)):
+            ref = raycast_fraction(planes, parts[a], hs[a])
+            r = oracle.map_cells(grid, parts[:, 0], parts[:, 1], parts[:, 2], np.ones(6), hs, cells=[c],
+                                 off=np.array([0, 1], np.int64), idx=np.array([a], np.int32), nthreads=1)
+            worst = max(worst, abs(r["frac"][0] - ref))
+    assert worst < 2e-4, worst
+
+
+# ----------------------------------------------------------------- invariants on Voronoi grids
+
+def test_cell_volumes_tile_the_cube():
+    p = synth.uniform_particles(300, 5)
+    g = synth.voronoi(p.pos(), nthreads=1)
+    vol, rad = oracle.cell_geometry(g)
+    assert abs(vol.sum() - 1.0) < 1e-13
+    assert np.all(vol > 0) and np.all(rad > 0)
+
+
+def test_mass_conservation_interior_particles():
+    """sum_i f_ai = 1 for every particle whose support lies inside the cube."""
+    p = synth.uniform_particles(512, 7)
+    g = synth.voronoi(p.pos(), nthreads=1)
+    h = np.full(p.n, 0.15)
+    res = oracle.map_cells(g, p.x, p.y, p.z, p.m, h)
+    tot = np.zeros(p.n)
+    np.add.at(tot, res["idx"], res["frac"])
+    pos = p.pos()
+    interior = np.all((pos >= 2 * h[:, None]) & (pos <= 1 - 2 * h[:, None]), axis=1)
+    assert interior.sum() >= 10
+    assert np.max(np.abs(tot[interior] - 1.0)) < 1e-11
+    # particles near the walls lose mass outside the cube, never gain
+    assert np.all(tot <= 1.0 + 1e-11)
+
+
+def test_lattice_uniform_density():
+    """Cubic lattice, equal masses and h: every cell farther than 4h from the
+    walls holds exactly one particle's mass (translation symmetry), so rho = m/V."""
+    n = 12
+    p = synth.lattice_particles(n)
+    g = synth.voronoi(p.pos(), nthreads=1)
+    h = np.full(p.n, 1.2 / n)
+    site = g.site
+    far = np.all((site > 4 * h[0]) & (site < 1 - 4 * h[0]), axis=1)
+    cells = np.nonzero(far)[0]
+    assert len(cells) >= 8
+    res = oracle.map_cells(g, p.x, p.y, p.z, p.m, h, cells=cells)
+    assert np.max(np.abs(res["mass"] / p.m[0] - 1.0)) < 1e-11
+    assert np.max(np.abs(res["rho"] * res["vol"] / p.m[0] - 1.0)) < 1e-11
+    assert np.max(np.abs(res["vol"] * n**3 - 1.0)) < 1e-11
+
+
+def test_pair_rule_is_conservative():
+    """Every particle with nonzero f_ai is listed: compare the pair list against
+    brute-force f over ALL particles for a few cells."""
+    p = synth.uniform_particles(200, 3)
+    g = synth.voronoi(p.pos(), nthreads=1)
+    h = np.full(p.n, 0.12)
+    cells = np.array([0, 17, 99], np.int64)
+    off, idx = oracle.pair_lists(g, p.x, p.y, p.z, h, cells)
+    for k, c in enumerate(cells):
+        listed = set(idx[off[k]:off[k + 1]].tolist())
+        allidx = np.arange(p.n, dtype=np.int32)
+        r = oracle.map_cells(g, p.x, p.y, p.z, p.m, h, cells=[c], off=np.array([0, p.n], np.int64), idx=allidx)
+        nz = set(np.nonzero(np.abs(r["frac"]) > 1e-15)[0].tolist())
+        assert nz <= listed
+
+
+# ----------------------------------------------------------------- smoothing lengths
+
+def test_h_solve_residual_and_lattice_value():
+    n = 10
+    p = synth.lattice_particles(n, jitter=0.2, seed=1)
+    pos = p.pos()
+    tree = oracle.Tree(p.x, p.y, p.z, p.m)
+    h0 = oracle.particle_h_guess(tree)
+    targets = np.arange(p.n)
+    h, route = oracle.solve_h(p.x, p.y, p.z, h0, targets)
+    assert np.all(route == 0)
+    # independent residual: brute-force number density with the test's kernel
+    for a in (0, 123, 555, 999):
+        r = np.linalg.norm(pos - pos[a], axis=1)
+        nn = np.sum(W_def(r, h[a]))
+        assert abs(h[a] - 1.2 * nn ** (-1.0 / 3.0)) < 1e-9 * h[a]
+    # an interior particle of an unjittered lattice: h close to 1.2 x spacing
+    q = synth.lattice_particles(n)
+    hq, _ = oracle.solve_h(q.x, q.y, q.z, np.full(q.n, 0.1), [555])
+    assert abs(hq[0] * n / 1.2 - 1.0) < 0.05
+
+
+# ----------------------------------------------------------------- octree and walk
+
+def test_octree_invariants_and_walk_partition():
+    p = synth.lognormal_particles(4000, 9, ngrid=32)
+    t = oracle.Tree(p.x, p.y, p.z, p.m, 16)
+    assert abs(t.mass[0] - 1.0) < 1e-15
+    leaves = np.nonzero(t.leaf)[0]
+    assert t.count[leaves].sum() == p.n
+    assert np.all(t.count[leaves] <= 16)
+    # children labels: parent = label >> 3
+    for nid in np.nonzero(t.leaf == 0)[0][:200]:
+        fc, nc = t.first_child[nid], t.nchild[nid]
+        assert np.all(t.label[fc:fc + nc] >> 3 == t.label[nid])
+        assert abs(t.mass[fc:fc + nc].sum() - t.mass[nid]) < 1e-13
+    # size = distance from the centre of mass to the furthest particle
+    for nid in (0, leaves[0], leaves[-1]):
+        idx = t.particles_of(nid)
+        d = np.sqrt(((p.pos()[idx] - t.com[nid]) ** 2).sum(1)).max()
+        assert abs(d - t.size[nid]) < 1e-14
+    src = p.pos()[17]
+    for theta in (0.3, 0.5, 0.9):
+        acc, opened = t.walk(src, theta)
+        covered = np.concatenate([t.particles_of(i) for i in np.concatenate([acc, opened])])
+        assert len(covered) == p.n and len(np.unique(covered)) == p.n
+        m = t.mass[acc].sum() + sum(p.m[t.particles_of(i)].sum() for i in opened)
+        assert abs(m - p.m.sum()) < 1e-12
+        for i in acc:
+            r = np.linalg.norm(t.com[i] - src)
+            assert t.size[i] <= theta * r
+    # theta -> 0 opens everything down to particles
+    acc, opened = t.walk(src, 0.0)
+    assert np.all(t.size[acc] == 0.0)
+    assert sum(int(t.count[i]) for i in opened) + sum(int(t.count[i]) for i in acc) == p.n
