@@ -1,0 +1,396 @@
+#!/usr/bin/env python
+"""Benchmark: particle-cell pair integrals per second on GB300.
+
+Workload (one step = the whole mapping path on one snapshot): the clumpy
+cloud -- 2^20 equal-mass particles sampled from a log-normal density field
+(Gaussian random field with P(k) ~ k^-4 on a 128^3 grid, sigma_ln_rho = 1.5)
+in the unit cube, its clipped Voronoi grid (host-generated input, resident on
+the device), and per step: smoothing-length solve, octree, pair-list build,
+pair integrals and cell sums in the mixed FP32/FP64 build.
+
+value = pair integrals per second (pairs of the snapshot / device time per
+step), inputs resident in HBM.  e2e = the same metric with the particles and
+the grid copied from pinned host memory and the cell masses read back inside
+the timed region.  The FP64 build is timed on the same snapshot and reported
+under "fp64".  cpu_baseline = the FP64 CPU oracle on a bounded sample of
+cells of the same snapshot, on the host's cores.
+
+--impl reference times that oracle alone (one sample of cells per step).
+Multi-GPU (torchrun): every rank maps its own snapshot (weak scaling; no
+collective on the data path); time = max over ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+N_PARTICLES = 1 << 20
+SIGMA = 1.5
+WORKLOAD = "clumpy cloud: 2^20 equal-mass particles, log-normal field (GRF P(k)~k^-4, 128^3, sigma_ln_rho=1.5), clipped Voronoi grid, mixed FP32/FP64"
+
+
+# ----------------------------------------------------------------------------- helpers
+
+def dist_env():
+    return int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)), int(os.environ.get("LOCAL_RANK", 0))
+
+
+def make_snapshot(rank: int, n: int):
+    import synth
+    p = synth.lognormal_particles(n, synth.BASE_SEED + 2 + 1000 * rank, sigma=SIGMA)
+    g = synth.voronoi(p.pos())
+    return p, g
+
+
+class ClockSampler:
+    """nvidia-smi clock/throttle sampling during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_rank{gpu_index}.csv")
+
+    def start(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"], stdout=self.fh,
+                                         stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.fh.close()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": float(max(smax)), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# Algorithmic operation model of the pair-integral kernel (per counted unit):
+# (FP32-pipe ops, MUFU ops).  See the design doc for the derivation.
+OPS = {
+    "face_tests": (6, 0),
+    "edge_records": (11, 0),
+    "edge_terms": (15, 3),
+    "inner_evals": (92, 6),
+    "mid_intervals_mixed": (161, 20),
+    "mid_intervals_fp64": (184, 12),  # two closed-form evaluations
+}
+
+
+def algorithmic_ops(work: dict, terms: int, mixed: bool):
+    f = m = 0
+    for key, cnt in (("face_tests", work["face_tests"]), ("edge_records", work["edge_records"]),
+                     ("edge_terms", terms), ("inner_evals", work["inner_evals"])):
+        f += OPS[key][0] * cnt
+        m += OPS[key][1] * cnt
+    k = "mid_intervals_mixed" if mixed else "mid_intervals_fp64"
+    f += OPS[k][0] * work["mid_intervals"]
+    m += OPS[k][1] * work["mid_intervals"]
+    return f, m
+
+
+def load_peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        return {}
+
+
+# ----------------------------------------------------------------------------- our arm
+
+def run_ours(args):
+    import torch
+    import paper_2404_17084_gb300 as L
+
+    rank, world, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+
+    p, g = make_snapshot(rank, args.n)
+    t = lambda a: torch.as_tensor(np.ascontiguousarray(a), dtype=torch.float64, device=dev)
+    x, y, z, m = t(p.x), t(p.y), t(p.z), t(p.m)
+    h = torch.empty_like(x)
+    mass = torch.empty(g.ncell, dtype=torch.float64, device=dev)
+    rho = torch.empty_like(mass)
+
+    def barrier():
+        torch.cuda.synchronize()
+        if world > 1:
+            torch.distributed.barrier()
+
+    def setup(precision):
+        ctx = L.map_init(L.map_config_default(precision=precision, device=local))
+        handle = L.map_grid_upload(ctx, L.grid_to_device(g, dev))
+        return ctx, handle
+
+    def step(ctx, handle):
+        L.solve_h(ctx, L.make_particles(x, y, z, None, h))
+        L.map_particles_to_cells(ctx, L.make_particles(x, y, z, m, h), handle, mass, rho)
+
+    def timed(ctx, handle, steps, warmup, sampler=None):
+        for _ in range(warmup):
+            step(ctx, handle)
+        barrier()
+        _, l0 = L.map_get_work(ctx)
+        integ_ms = []
+        if sampler:
+            sampler.start()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(steps):
+            step(ctx, handle)
+            integ_ms.append(L.map_get_timing(ctx)["integrals"])
+        e1.record()
+        torch.cuda.synchronize()
+        clocks = sampler.stop() if sampler else None
+        ms = e0.elapsed_time(e1) / steps
+        if world > 1:
+            tt = torch.tensor([ms], device=dev)
+            torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
+            ms = float(tt.item())
+        st = L.map_get_stats(ctx)
+        work, l1 = L.map_get_work(ctx)
+        phases = L.map_get_timing(ctx)
+        return ms, st, work, (l1 - l0) // steps * steps, float(np.mean(integ_ms)), phases, clocks
+
+    # ---- mixed build (headline)
+    ctx, handle = setup(L.MAP_MIXED)
+    sampler = ClockSampler(local)
+    ms, st, work, launches, integ_ms, phases, clocks = timed(ctx, handle, args.steps, args.warmup, sampler)
+    n_pairs = st.n_pairs
+    mass_mixed = mass.cpu().numpy()
+    h_mixed = h.cpu().numpy()
+    # ---- e2e through the public API with host buffers
+    e2e = None if args.skip_e2e else e2e_run(L, torch, ctx, p, g, dev, args, barrier, world)
+    L.map_destroy(ctx)
+
+    # ---- FP64 build (one timed step: GB300's FP64 rate makes it ~70x slower)
+    fp64 = None
+    mass_fp64 = None
+    if not args.skip_fp64:
+        ctx64, handle64 = setup(L.MAP_FP64)
+        ms64, st64, work64, _, integ64, phases64, _ = timed(ctx64, handle64, 1, 0)
+        mass_fp64 = mass.cpu().numpy()
+        L.map_destroy(ctx64)
+        fp64 = {"value": st64.n_pairs * world / (ms64 * 1e-3), "ms_per_step": ms64, "steps": 1, "warmup": 0,
+                "integrals_ms": integ64, "phases_ms": {k: round(v, 3) for k, v in phases64.items()}}
+
+    f32, mufu = algorithmic_ops(work, st.n_edge_terms, True)
+    peaks = load_peaks()
+    sm_count = torch.cuda.get_device_properties(dev).multi_processor_count
+    f_clk = (clocks or {}).get("sm_max_mhz") or peaks.get("sm_max_mhz", 2070.0)
+    peak_ops = sm_count * 128 * f_clk * 1e6          # FP32 lane-ops per second
+    work_ops = max(f32, 8.0 * mufu)                   # MUFU: 16/clk/SM = 1/8 of the FP32 lanes
+    achieved = work_ops / (integ_ms * 1e-3)
+    line = {
+        "metric": "particle-cell pair integrals/sec at 1 GB300 (mixed vs FP64 form) + p50/p99 latency",
+        "value": n_pairs * world / (ms * 1e-3),
+        "unit": "pair integrals/s",
+        "n_gpus": world,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": ms,
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f32+f64",
+        "data": "synthetic",
+        "config": {"workload": WORKLOAD, "n_particles": args.n, "n_cells": g.ncell, "n_pairs": int(n_pairs),
+                   "n_faces": g.nface, "l2": "inputs larger than L2 (grid and pair list several GB)",
+                   "step": "solve_h + octree + pair list + pair integrals + cell sums"},
+        "phases_ms": {k: round(v, 3) for k, v in phases.items()},
+        "fp64": fp64,
+        "roofline": {"bound": "alu", "kernel": "pair_integrals<float,mixed>", "achieved": achieved / 1e12,
+                     "peak": peak_ops / 1e12, "unit": "Tops/s (FP32 issue slots)", "frac": achieved / peak_ops,
+                     "traffic": None, "ops_fp32": int(f32), "ops_mufu": int(mufu), "launch_ms": integ_ms,
+                     "peak_source": f"{sm_count} SMs x 128 FP32 lanes x {f_clk:.0f} MHz"},
+        "e2e": e2e,
+        "gpu_launches": int(launches),
+        "clocks": clocks,
+        "stats": {"edge_terms": int(st.n_edge_terms), "total_mass": st.total_mass, **{k: int(v) for k, v in work.items()}},
+    }
+    if rank == 0 and not args.no_cpu_baseline:
+        base, acc = cpu_baseline(p, g, h_mixed, mass_mixed, mass_fp64, args)
+        line["cpu_baseline"] = base
+        line["accuracy_vs_oracle"] = acc
+    if world > 1:
+        torch.distributed.barrier()
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+def e2e_run(L, torch, ctx, p, g, dev, args, barrier, world):
+    """Same metric through the public API: pinned host inputs copied in, the
+    grid uploaded and prepared, solve_h + mapping, cell masses read back."""
+    pin = lambda a, dt: torch.as_tensor(np.ascontiguousarray(a), dtype=dt).pin_memory()
+    hp = [pin(a, torch.float64) for a in (p.x, p.y, p.z, p.m)]
+    hg = dict(cell_face_off=pin(g.cell_face_off, torch.int64), face_vert_off=pin(g.face_vert_off, torch.int64),
+              face_vert=pin(g.face_vert, torch.int32), face_plane=pin(g.face_plane, torch.float64),
+              vx=pin(g.vx, torch.float64), vy=pin(g.vy, torch.float64), vz=pin(g.vz, torch.float64),
+              site=pin(g.site, torch.float64))
+    out_host = torch.empty(g.ncell, dtype=torch.float64).pin_memory()
+    h2d = sum(t.numel() * t.element_size() for t in hp) + sum(t.numel() * t.element_size() for t in hg.values())
+    d2h = out_host.numel() * out_host.element_size()
+
+    def one():
+        dp = [t.to(dev, non_blocking=True) for t in hp]
+        dg = {k: v.to(dev, non_blocking=True) for k, v in hg.items()}
+        handle = L.map_grid_upload(ctx, dg)
+        hh = torch.empty_like(dp[0])
+        L.solve_h(ctx, L.make_particles(dp[0], dp[1], dp[2], None, hh))
+        mass = torch.empty(g.ncell, dtype=torch.float64, device=dev)
+        L.map_particles_to_cells(ctx, L.make_particles(dp[0], dp[1], dp[2], dp[3], hh), handle, mass)
+        out_host.copy_(mass, non_blocking=True)
+        torch.cuda.synchronize()
+        L.map_grid_release(ctx, handle)
+        return L.map_get_pairs(ctx)[3]
+
+    steps = max(1, args.steps // 2)
+    one()
+    barrier()
+    t0 = time.perf_counter()
+    npairs = 0
+    for _ in range(steps):
+        npairs = one()
+    barrier()
+    sec = (time.perf_counter() - t0) / steps
+    return {"value": npairs * world / sec, "unit": "pair integrals/s", "h2d_bytes_per_step": int(h2d),
+            "d2h_bytes_per_step": int(d2h), "ms_per_step": sec * 1e3, "steps": steps}
+
+
+def oracle_sample(p, g, h, target_s: float, seed: int = 7):
+    """Time the oracle on a random sample of cells sized for ~target_s seconds."""
+    import oracle
+    rng = np.random.default_rng(seed)
+    order = rng.permutation(g.ncell)
+    ncores = os.cpu_count() or 1
+    # calibration on a few cells
+    k = 8
+    t0 = time.perf_counter()
+    r = oracle.map_cells(g, p.x, p.y, p.z, p.m, h, cells=np.sort(order[:k]), nthreads=ncores)
+    dt = time.perf_counter() - t0
+    k2 = int(min(g.ncell, max(k, k * target_s / max(dt, 1e-3))))
+    cells = np.sort(order[:k2])
+    t0 = time.perf_counter()
+    r = oracle.map_cells(g, p.x, p.y, p.z, p.m, h, cells=cells, nthreads=ncores)
+    dt = time.perf_counter() - t0
+    return cells, r, dt, ncores
+
+
+def cpu_baseline(p, g, h, mass_mixed, mass_fp64, args):
+    cells, r, dt, ncores = oracle_sample(p, g, h, args.cpu_seconds)
+    npairs = len(r["idx"])
+    ref = r["mass"]
+    scale = np.maximum(np.abs(ref), 1e-12 * np.abs(ref).max())
+    err_mixed = np.abs(mass_mixed[cells] - ref) / scale
+    err_fp64 = np.abs(mass_fp64[cells] - ref) / scale if mass_fp64 is not None else np.zeros(1)
+    base = {"value": npairs / dt, "unit": "pair integrals/s", "cores": ncores, "kind": "oracle",
+            "sample": f"{len(cells)} random cells of the same snapshot ({npairs} pairs; pair list by brute force "
+                      f"over all {p.n} particles + adaptive-quadrature pair integrals), {dt:.1f} s"}
+    acc = {"cells": int(len(cells)), "mixed_max_rel": float(err_mixed.max()),
+           "mixed_p99_rel": float(np.percentile(err_mixed, 99)), "fp64_max_rel": float(err_fp64.max()),
+           "fp64_p99_rel": float(np.percentile(err_fp64, 99)),
+           "note": "h from the GPU solve in both; per-cell mass vs the FP64 oracle"}
+    return base, acc
+
+
+# ----------------------------------------------------------------------------- reference arm (oracle)
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    import oracle
+    p, g = make_snapshot(0, args.n)
+    tree = oracle.Tree(p.x, p.y, p.z, p.m)
+    h, _ = oracle.solve_h(p.x, p.y, p.z, oracle.particle_h_guess(tree))
+    rng = np.random.default_rng(11)
+    ncores = os.cpu_count() or 1
+    per_step = args.ref_cells
+    total_pairs = 0
+    for _ in range(args.warmup):
+        cells = np.sort(rng.choice(g.ncell, per_step, replace=False))
+        oracle.map_cells(g, p.x, p.y, p.z, p.m, h, cells=cells, nthreads=ncores)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        cells = np.sort(rng.choice(g.ncell, per_step, replace=False))
+        r = oracle.map_cells(g, p.x, p.y, p.z, p.m, h, cells=cells, nthreads=ncores)
+        total_pairs += len(r["idx"])
+    dt = time.perf_counter() - t0
+    v = total_pairs / dt
+    line = {"impl": "reference", "metric": "particle-cell pair integrals/sec at 1 GB300 (mixed vs FP64 form) + p50/p99 latency",
+            "value": v, "unit": "pair integrals/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": dt * 1e3 / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "n_particles": args.n, "n_cells": g.ncell,
+                       "sample_per_step": f"{per_step} random cells (pair list + pair integrals)"},
+            "cpu_baseline": {"value": v, "unit": "pair integrals/s", "cores": ncores, "kind": "oracle",
+                             "sample": f"{per_step} random cells per step"},
+            "e2e": {"value": v, "unit": "pair integrals/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--n", type=int, default=N_PARTICLES)
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--ref-cells", type=int, default=64)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--skip-fp64", action="store_true")
+    ap.add_argument("--skip-e2e", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

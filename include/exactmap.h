@@ -1,0 +1,224 @@
+/*
+ * exactmap.h -- C ABI of the GB300 (sm_103a) library for the Exact mapping of
+ * SPH particle densities onto a Voronoi grid, with the tree-based
+ * pseudo-particle front end (Lau, Petkova & Bonnell 2024).
+ *
+ * Conventions
+ *  - Every function returns MAP_OK (0) or a negative MAP_E* code; none aborts,
+ *    exits or traps.  map_strerror() names a code.
+ *  - Array arguments are DEVICE pointers owned by the caller, unless a
+ *    function says otherwise.  The library owns only its context workspace.
+ *  - Calls are asynchronous on the given CUDA stream (NULL = legacy default
+ *    stream) unless documented as synchronising; statistics are read back with
+ *    map_get_stats(), which synchronises that stream.
+ *  - A context is not thread-safe: use one context per host thread.
+ *  - Lengths are in the unit cube [0,1]^3; masses are arbitrary positive
+ *    numbers; the kernel is the M4 cubic spline with support 2h.
+ */
+#ifndef EXACTMAP_H
+#define EXACTMAP_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ------------------------------------------------------------ status codes */
+#define MAP_OK 0
+#define MAP_EINVAL (-1)      /* bad argument: NULL, bad CSR, NaN, h <= 0, point outside the cube */
+#define MAP_ENOMEM (-2)      /* over the context's HBM budget or cudaMalloc failed; nothing was changed */
+#define MAP_ECUDA (-3)       /* a CUDA runtime call failed */
+#define MAP_ETIMEOUT (-4)    /* a bounded device wait ran out (work queue) */
+#define MAP_EDEGENERATE (-5) /* reserved: geometry not classifiable even in FP64 (result flagged) */
+#define MAP_EHANDLE (-6)     /* unknown grid handle */
+#define MAP_ECAPACITY (-7)   /* a caller-provided output buffer is too small */
+
+/* ------------------------------------------------------------ configuration */
+#define MAP_FP64 0  /* every wedge integral in FP64 (closed form) */
+#define MAP_MIXED 1 /* wedge integrals in FP32, FP64 accumulation */
+
+typedef struct {
+  int precision;                     /* MAP_FP64 or MAP_MIXED */
+  int device;                        /* CUDA device ordinal */
+  size_t hbm_budget;                 /* max bytes of workspace + resident grids; 0 = no limit */
+  double theta;                      /* opening angle of Eq. (5); default 0.5 */
+  double hfact;                      /* h = hfact n^(-1/3), Eq. (7); default 1.2 */
+  int leaf_size;                     /* octree leaf capacity; default 16 */
+  int ngb_bruteforce_max;            /* Section III-D: k_mid neighbour search above this many nodes; default 10000 */
+  int autotune;                      /* reserved: 1 = choose launch shapes by measurement */
+  unsigned long long queue_timeout_ns; /* bound on any device-side wait; default 2e9 */
+} map_config;
+
+/* Fill *cfg with the defaults listed above. */
+void map_config_default(map_config* cfg);
+
+/* ------------------------------------------------------------ data */
+
+/* Particle set, structure of arrays, FP64 device pointers of length n.
+ * h is input (map_particles_to_cells) or output (solve_h). */
+typedef struct {
+  int64_t n;
+  const double* x;
+  const double* y;
+  const double* z;
+  const double* m;
+  double* h;
+} map_particles;
+
+/* Convex-cell grid in CSR form (device pointers).  Cell c owns faces
+ * [cell_face_off[c], cell_face_off[c+1]); face f owns loop entries
+ * [face_vert_off[f], face_vert_off[f+1]) of face_vert, whose values index
+ * the vertex arrays.  Loops run counter-clockwise seen from outside the cell.
+ * face_plane holds 4 doubles per face (nx, ny, nz, d) with a unit outward
+ * normal: points of the cell satisfy n.x <= d.  site holds 3 doubles per
+ * cell: a point strictly inside the cell (the generating site). */
+typedef struct {
+  int64_t ncell;
+  int64_t nface;
+  int64_t nloop;
+  int64_t nvert;
+  const int64_t* cell_face_off;
+  const int64_t* face_vert_off;
+  const int32_t* face_vert;
+  const double* face_plane;
+  const double* vx;
+  const double* vy;
+  const double* vz;
+  const double* site;
+} map_grid;
+
+/* Per-cell outputs (device pointers of length ncell, caller-owned).
+ * cell_mass is required; cell_rho and cell_vol may be NULL. */
+typedef struct {
+  double* cell_mass; /* M_i = sum_a m_a f_ai, Eq. (3) numerator */
+  double* cell_rho;  /* rho_i = M_i / V_i, Eq. (1)-(3) */
+  double* cell_vol;  /* V_i */
+} map_outputs;
+
+/* Statistics of the last mapping call on a context. */
+typedef struct {
+  int64_t n_pairs;      /* listed particle-cell pairs (one pair integral each) */
+  int64_t n_edge_terms; /* edge integrals evaluated (two vertex pyramids each) */
+  int64_t n_fp64_terms; /* edge integrals evaluated in FP64 in the mixed build */
+  double total_mass;    /* sum_i M_i */
+  int status;           /* device-side status word (MAP_OK or a MAP_E* code) */
+} map_stats;
+
+typedef struct map_ctx map_ctx;
+
+/* ------------------------------------------------------------ lifetime */
+
+/* Create a context on cfg->device (NULL cfg = defaults).  Allocates a small
+ * pinned host block and selects the device; no device workspace yet. */
+int map_init(map_ctx** ctx, const map_config* cfg);
+
+/* Free all device and host memory of the context (grids included). */
+void map_destroy(map_ctx* ctx);
+
+/* Static string naming a status code. */
+const char* map_strerror(int code);
+
+/* ------------------------------------------------------------ grids */
+
+/* Copy a grid (device pointers, read during the call only) into context
+ * memory and precompute its per-face and per-edge geometry, cell volumes and
+ * cell radii (largest vertex distance from the site).  The grid stays
+ * resident until map_grid_release / map_destroy.  Synchronises the stream.
+ * Errors: MAP_EINVAL (empty or inconsistent sizes), MAP_ENOMEM. */
+int map_grid_upload(map_ctx* ctx, const map_grid* grid, int* handle, void* stream);
+
+/* Release a resident grid.  MAP_EHANDLE if unknown. */
+int map_grid_release(map_ctx* ctx, int handle);
+
+/* Copy the volumes V_i of a resident grid into vol (device, ncell doubles). */
+int map_grid_volumes(map_ctx* ctx, int handle, double* vol, void* stream);
+
+/* ------------------------------------------------------------ the mapping (Section II-B, Eq. 1-3) */
+
+/* For every cell i of the resident grid: build the list of particles a whose
+ * support may reach the cell, compute every pair integral
+ * f_ai = int_{V_i} W(|r'-r_a|, h_a) dV' in closed form from the cell's face
+ * and edge wedges (vertex pyramids, Section II-B), and write
+ * M_i = sum_a m_a f_ai and rho_i = M_i / V_i (Eq. 1-3).
+ *
+ * Pair rule (makes pair lists reproducible; the paper is silent): (i,a) is
+ * listed iff |r_a - s_i| < 2 h_a + R_i and n_f.r_a - d_f < 2 h_a for every
+ * face f of cell i, both evaluated in FP64 in a fixed order without FMA.
+ * Lists are sorted by particle index within each cell.
+ *
+ * p->h must hold positive smoothing lengths.  Synchronises the stream once
+ * (to size the pair list).  The pair list and the per-pair integrals stay in
+ * the context until the next call (map_get_pairs).
+ * Errors: MAP_EINVAL, MAP_EHANDLE, MAP_ENOMEM, MAP_ECUDA. */
+int map_particles_to_cells(map_ctx* ctx, const map_particles* p, int grid, map_outputs* out, void* stream);
+
+/* Device pointers to the last call's pair list: pair_off (ncell+1 int64),
+ * pair_idx (n_pairs int32 particle indices), pair_frac (n_pairs doubles,
+ * f_ai).  Owned by the context; valid until the next mapping call. */
+int map_get_pairs(map_ctx* ctx, const int64_t** pair_off, const int32_t** pair_idx, const double** pair_frac,
+                  int64_t* n_pairs);
+
+/* Copy the last call's pair list into caller-owned device buffers:
+ * pair_off (ncell+1 int64), pair_idx (n_pairs int32), pair_frac (n_pairs
+ * doubles, may be NULL).  capacity = the length of pair_idx / pair_frac;
+ * MAP_ECAPACITY if it is smaller than n_pairs.  Asynchronous on stream. */
+int map_copy_pairs(map_ctx* ctx, int64_t* pair_off, int32_t* pair_idx, double* pair_frac, int64_t capacity,
+                   void* stream);
+
+/* Statistics of the last mapping call; synchronises its stream. */
+int map_get_stats(map_ctx* ctx, map_stats* stats);
+
+/* Work tally of the last mapping call, read by the last map_get_stats():
+ * counts[0] face tests, counts[1] edge records read, counts[2] inner-piece
+ * antiderivative evaluations, counts[3] middle-piece intervals (all per
+ * pair, summed).  *launches: kernels this context has launched so far (its
+ * own kernels; library sort/scan primitives not counted).  These feed the
+ * algorithmic operation count of the roofline. */
+int map_get_work(map_ctx* ctx, int64_t* counts, int64_t* launches);
+
+/* Device time (ms, CUDA events on the call's stream) of the most recent
+ * phases: ms[0] octree build and ms[1] pair-list build and ms[2] the
+ * pair-integral kernel (all of the last map_particles_to_cells), ms[3] the
+ * last solve_h.  -1 for a phase not yet run.  Waits for those events. */
+int map_get_timing(map_ctx* ctx, float* ms);
+
+/* ------------------------------------------------------------ smoothing lengths (Section III-C, Eq. 7-9) */
+
+/* Solve h_a = hfact * n_a(h_a)^(-1/3), n_a(h) = sum_b W(|r_a - r_b|, h)
+ * (self term included) for every particle: Newton-Raphson (at most 30
+ * iterations, converged at |dh|/h < 1e-10), else bisection on
+ * [h0/16, 16 h0] (|dh|/h < 1e-12), else the estimate h0.  The initial guess
+ * h0 is hfact * (side of the particle's octree leaf cube) / (leaf count)^(1/3).
+ * Writes p->h; route (optional, n int32) receives 0 Newton, 1 bisection,
+ * 2 estimate.  Errors: MAP_EINVAL, MAP_ENOMEM, MAP_ECUDA. */
+int solve_h(map_ctx* ctx, map_particles* p, int32_t* route, void* stream);
+
+/* ------------------------------------------------------------ pseudo-particles (Section III-A/B, Eq. 5) */
+
+/* Build the octree of the full particle set (leaf capacity cfg.leaf_size),
+ * walk it from the root and open a node when r_node = 0 or
+ * s_node^2 > theta^2 r_node^2 with r_node the distance from the node's centre
+ * of mass to the nearest of the nsrc sources (src: host array of 3*nsrc
+ * doubles).  Accepted nodes become pseudo-particles (centre of mass, node
+ * mass); an opened leaf yields its particles, which keep their h.  Then solve
+ * the pseudo-particles' h as in solve_h over the node set (accepted nodes
+ * plus opened leaves standing in for their particles, Section III-C), with
+ * initial guess hfact * 2 s_node (Eq. 9).
+ *
+ * out: caller-owned device arrays of capacity out->n (x, y, z, m, h); on
+ * return *n_pseudo holds the number written, ordered depth-first (children
+ * in octant order).  kind (optional, capacity out->n int32): 0 node, 1
+ * particle; ident (optional, int64): node label (leading-1 Morton prefix) or
+ * particle index.  Synchronises the stream.
+ * Errors: MAP_EINVAL, MAP_ECAPACITY (*n_pseudo = required count),
+ * MAP_ENOMEM, MAP_ECUDA. */
+int build_pseudo_particles(map_ctx* ctx, const map_particles* full, const double* src, int nsrc,
+                           map_particles* out, int32_t* kind, int64_t* ident, int64_t* n_pseudo, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* EXACTMAP_H */

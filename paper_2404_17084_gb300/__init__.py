@@ -1,0 +1,278 @@
+"""Python binding of libexactmap (GB300 / sm_103a), the Exact SPH -> Voronoi
+density mapping with the tree-based pseudo-particle front end.
+
+The binding only marshals arguments into the C ABI declared in
+``include/exactmap.h``; every step of the computation runs in the library's
+CUDA kernels.  Functions keep the C names.  Arrays are torch CUDA tensors
+(float64 / int64 / int32); torch provides device memory and streams only.
+
+Importing this module loads the compiled library and raises ImportError if
+it is missing; there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import torch
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libexactmap.so")
+
+MAP_OK = 0
+MAP_EINVAL = -1
+MAP_ENOMEM = -2
+MAP_ECUDA = -3
+MAP_ETIMEOUT = -4
+MAP_EDEGENERATE = -5
+MAP_EHANDLE = -6
+MAP_ECAPACITY = -7
+MAP_FP64 = 0
+MAP_MIXED = 1
+
+if not os.path.exists(LIB_PATH):
+    raise ImportError(f"libexactmap.so not built ({LIB_PATH}); run paper_2404_17084_gb300/build.py")
+
+_lib = ctypes.CDLL(LIB_PATH)
+
+_P = ctypes.c_void_p
+_I64 = ctypes.c_int64
+
+
+class map_config(ctypes.Structure):
+    _fields_ = [("precision", ctypes.c_int), ("device", ctypes.c_int), ("hbm_budget", ctypes.c_size_t),
+                ("theta", ctypes.c_double), ("hfact", ctypes.c_double), ("leaf_size", ctypes.c_int),
+                ("ngb_bruteforce_max", ctypes.c_int), ("autotune", ctypes.c_int),
+                ("queue_timeout_ns", ctypes.c_ulonglong)]
+
+
+class map_particles(ctypes.Structure):
+    _fields_ = [("n", _I64), ("x", _P), ("y", _P), ("z", _P), ("m", _P), ("h", _P)]
+
+
+class map_grid(ctypes.Structure):
+    _fields_ = [("ncell", _I64), ("nface", _I64), ("nloop", _I64), ("nvert", _I64), ("cell_face_off", _P),
+                ("face_vert_off", _P), ("face_vert", _P), ("face_plane", _P), ("vx", _P), ("vy", _P), ("vz", _P),
+                ("site", _P)]
+
+
+class map_outputs(ctypes.Structure):
+    _fields_ = [("cell_mass", _P), ("cell_rho", _P), ("cell_vol", _P)]
+
+
+class map_stats(ctypes.Structure):
+    _fields_ = [("n_pairs", _I64), ("n_edge_terms", _I64), ("n_fp64_terms", _I64), ("total_mass", ctypes.c_double),
+                ("status", ctypes.c_int)]
+
+
+_lib.map_config_default.argtypes = [ctypes.POINTER(map_config)]
+_lib.map_config_default.restype = None
+_lib.map_init.argtypes = [ctypes.POINTER(_P), ctypes.POINTER(map_config)]
+_lib.map_destroy.argtypes = [_P]
+_lib.map_destroy.restype = None
+_lib.map_strerror.argtypes = [ctypes.c_int]
+_lib.map_strerror.restype = ctypes.c_char_p
+_lib.map_grid_upload.argtypes = [_P, ctypes.POINTER(map_grid), ctypes.POINTER(ctypes.c_int), _P]
+_lib.map_grid_release.argtypes = [_P, ctypes.c_int]
+_lib.map_grid_volumes.argtypes = [_P, ctypes.c_int, _P, _P]
+_lib.map_particles_to_cells.argtypes = [_P, ctypes.POINTER(map_particles), ctypes.c_int, ctypes.POINTER(map_outputs), _P]
+_lib.map_get_pairs.argtypes = [_P, ctypes.POINTER(_P), ctypes.POINTER(_P), ctypes.POINTER(_P), ctypes.POINTER(_I64)]
+_lib.map_copy_pairs.argtypes = [_P, _P, _P, _P, _I64, _P]
+_lib.map_get_stats.argtypes = [_P, ctypes.POINTER(map_stats)]
+_lib.map_get_work.argtypes = [_P, ctypes.POINTER(_I64), ctypes.POINTER(_I64)]
+_lib.map_get_timing.argtypes = [_P, ctypes.POINTER(ctypes.c_float)]
+_lib.solve_h.argtypes = [_P, ctypes.POINTER(map_particles), _P, _P]
+_lib.build_pseudo_particles.argtypes = [_P, ctypes.POINTER(map_particles), ctypes.POINTER(ctypes.c_double),
+                                        ctypes.c_int, ctypes.POINTER(map_particles), _P, _P,
+                                        ctypes.POINTER(_I64), _P]
+for _name in ("map_init", "map_grid_upload", "map_grid_release", "map_grid_volumes", "map_particles_to_cells",
+              "map_get_pairs", "map_copy_pairs", "map_get_stats", "map_get_work", "map_get_timing", "solve_h", "build_pseudo_particles"):
+    getattr(_lib, _name).restype = ctypes.c_int
+
+
+class MapError(RuntimeError):
+    def __init__(self, code: int, where: str):
+        super().__init__(f"{where}: {map_strerror(code)} ({code})")
+        self.code = code
+
+
+def _check(code: int, where: str) -> None:
+    if code != MAP_OK:
+        raise MapError(code, where)
+
+
+def _ptr(t):
+    if t is None:
+        return None
+    if not t.is_cuda or not t.is_contiguous():
+        raise ValueError("expected a contiguous CUDA tensor")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _stream(stream):
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+# ---------------------------------------------------------------- C names
+
+def map_strerror(code: int) -> str:
+    return _lib.map_strerror(code).decode()
+
+
+def map_config_default(**overrides) -> map_config:
+    cfg = map_config()
+    _lib.map_config_default(ctypes.byref(cfg))
+    for k, v in overrides.items():
+        setattr(cfg, k, v)
+    return cfg
+
+
+def map_init(cfg: map_config | None = None) -> ctypes.c_void_p:
+    ctx = ctypes.c_void_p()
+    _check(_lib.map_init(ctypes.byref(ctx), ctypes.byref(cfg) if cfg is not None else None), "map_init")
+    return ctx
+
+
+def map_destroy(ctx) -> None:
+    _lib.map_destroy(ctx)
+
+
+def make_particles(x, y, z, m=None, h=None) -> map_particles:
+    return map_particles(int(x.numel()), _ptr(x), _ptr(y), _ptr(z), _ptr(m), _ptr(h))
+
+
+def map_grid_upload(ctx, g: dict, stream=None) -> int:
+    """g: dict of CUDA tensors cell_face_off, face_vert_off (int64), face_vert
+    (int32), face_plane ([nface,4] float64), vx, vy, vz, site ([ncell,3])."""
+    mg = map_grid(int(g["cell_face_off"].numel() - 1), int(g["face_vert_off"].numel() - 1),
+                  int(g["face_vert"].numel()), int(g["vx"].numel()), _ptr(g["cell_face_off"]),
+                  _ptr(g["face_vert_off"]), _ptr(g["face_vert"]), _ptr(g["face_plane"]), _ptr(g["vx"]),
+                  _ptr(g["vy"]), _ptr(g["vz"]), _ptr(g["site"]))
+    h = ctypes.c_int(-1)
+    _check(_lib.map_grid_upload(ctx, ctypes.byref(mg), ctypes.byref(h), _stream(stream)), "map_grid_upload")
+    return h.value
+
+
+def map_grid_release(ctx, handle: int) -> None:
+    _check(_lib.map_grid_release(ctx, handle), "map_grid_release")
+
+
+def map_grid_volumes(ctx, handle: int, vol, stream=None) -> None:
+    _check(_lib.map_grid_volumes(ctx, handle, _ptr(vol), _stream(stream)), "map_grid_volumes")
+
+
+def map_particles_to_cells(ctx, p: map_particles, handle: int, cell_mass, cell_rho=None, cell_vol=None,
+                           stream=None) -> None:
+    out = map_outputs(_ptr(cell_mass), _ptr(cell_rho), _ptr(cell_vol))
+    _check(_lib.map_particles_to_cells(ctx, ctypes.byref(p), handle, ctypes.byref(out), _stream(stream)),
+           "map_particles_to_cells")
+
+
+def map_get_pairs(ctx):
+    """(pair_off_ptr, pair_idx_ptr, pair_frac_ptr, n_pairs) of the last call (context-owned)."""
+    a, b, c = ctypes.c_void_p(), ctypes.c_void_p(), ctypes.c_void_p()
+    n = ctypes.c_int64()
+    _check(_lib.map_get_pairs(ctx, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c), ctypes.byref(n)),
+           "map_get_pairs")
+    return a.value, b.value, c.value, n.value
+
+
+def map_copy_pairs(ctx, ncell: int, device=None, stream=None):
+    """The last call's pair list as new tensors (off int64, idx int32, frac float64)."""
+    n = map_get_pairs(ctx)[3]
+    dev = device or torch.device("cuda", torch.cuda.current_device())
+    off = torch.empty(ncell + 1, dtype=torch.int64, device=dev)
+    idx = torch.empty(max(n, 1), dtype=torch.int32, device=dev)
+    frac = torch.empty(max(n, 1), dtype=torch.float64, device=dev)
+    _check(_lib.map_copy_pairs(ctx, _ptr(off), _ptr(idx), _ptr(frac), max(n, 1), _stream(stream)), "map_copy_pairs")
+    return off, idx[:n], frac[:n]
+
+
+def map_get_stats(ctx) -> map_stats:
+    st = map_stats()
+    _check(_lib.map_get_stats(ctx, ctypes.byref(st)), "map_get_stats")
+    return st
+
+
+def map_get_work(ctx):
+    """(dict of per-class work counts of the last mapping call, kernel launches so far)."""
+    arr = (_I64 * 4)()
+    nl = _I64()
+    _check(_lib.map_get_work(ctx, arr, ctypes.byref(nl)), "map_get_work")
+    return dict(face_tests=arr[0], edge_records=arr[1], inner_evals=arr[2], mid_intervals=arr[3]), nl.value
+
+
+def map_get_timing(ctx):
+    """Device ms of the latest phases: dict(tree, pairs, integrals, solve_h)."""
+    arr = (ctypes.c_float * 4)()
+    _check(_lib.map_get_timing(ctx, arr), "map_get_timing")
+    return dict(tree=arr[0], pairs=arr[1], integrals=arr[2], solve_h=arr[3])
+
+
+def solve_h(ctx, p: map_particles, route=None, stream=None) -> None:
+    _check(_lib.solve_h(ctx, ctypes.byref(p), _ptr(route), _stream(stream)), "solve_h")
+
+
+def build_pseudo_particles(ctx, full: map_particles, src, out: map_particles, kind=None, ident=None, stream=None):
+    """Returns the number of pseudo-particles written (raises MapError with
+    code MAP_ECAPACITY, attribute .required, if out is too small)."""
+    srcs = [float(v) for v in src]
+    arr = (ctypes.c_double * len(srcs))(*srcs)
+    n = ctypes.c_int64(0)
+    code = _lib.build_pseudo_particles(ctx, ctypes.byref(full), arr, len(srcs) // 3, ctypes.byref(out), _ptr(kind),
+                                       _ptr(ident), ctypes.byref(n), _stream(stream))
+    if code != MAP_OK:
+        err = MapError(code, "build_pseudo_particles")
+        err.required = n.value
+        raise err
+    return n.value
+
+
+# ---------------------------------------------------------------- convenience
+
+def grid_to_device(grid, device="cuda") -> dict:
+    """Copy a host grid (any object with the CSR numpy arrays) to CUDA tensors."""
+    t = lambda a, dt: torch.as_tensor(a).to(device=device, dtype=dt).contiguous()
+    return dict(cell_face_off=t(grid.cell_face_off, torch.int64), face_vert_off=t(grid.face_vert_off, torch.int64),
+                face_vert=t(grid.face_vert, torch.int32), face_plane=t(grid.face_plane, torch.float64),
+                vx=t(grid.vx, torch.float64), vy=t(grid.vy, torch.float64), vz=t(grid.vz, torch.float64),
+                site=t(grid.site, torch.float64))
+
+
+class ExactMapper:
+    """A context plus the resident grids it owns (one GPU, one host thread)."""
+
+    def __init__(self, precision: int = MAP_MIXED, device: int = 0, **cfg):
+        self.device = torch.device("cuda", device)
+        self.cfg = map_config_default(precision=precision, device=device, **cfg)
+        self.ctx = map_init(self.cfg)
+
+    def close(self):
+        if self.ctx:
+            map_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def upload(self, grid) -> int:
+        g = grid if isinstance(grid, dict) else grid_to_device(grid, self.device)
+        return map_grid_upload(self.ctx, g)
+
+    def map(self, handle: int, ncell: int, x, y, z, m, h, stream=None):
+        mass = torch.empty(ncell, dtype=torch.float64, device=self.device)
+        rho = torch.empty(ncell, dtype=torch.float64, device=self.device)
+        p = make_particles(x, y, z, m, h)
+        map_particles_to_cells(self.ctx, p, handle, mass, rho, None, stream)
+        return mass, rho
+
+    def solve_h(self, x, y, z, stream=None):
+        h = torch.empty_like(x)
+        route = torch.empty(x.numel(), dtype=torch.int32, device=x.device)
+        solve_h(self.ctx, make_particles(x, y, z, None, h), route, stream)
+        return h, route

@@ -1,0 +1,168 @@
+// Grid upload: copy the CSR grid into context memory and precompute, per cell,
+// the site-relative face planes and the per-edge records the pair-integral
+// kernels read (Section II-B's r0, R0 and phi are affine in the particle
+// position once these are known), plus the cell volume (divergence theorem)
+// and the cell radius R_i used by the pair rule.
+#include <cstring>
+
+#include "internal.cuh"
+
+namespace {
+
+__global__ void prep_cells(int64_t ncell, const int64_t* __restrict__ cfo, const int64_t* __restrict__ fvo,
+                           const int32_t* __restrict__ fv, const double4_32a* __restrict__ plane,
+                           const double* __restrict__ vx, const double* __restrict__ vy,
+                           const double* __restrict__ vz, const double* __restrict__ site, double4_32a* face64,
+                           float4* face32, double* edge64, float* edge32, double* vol, double* rad,
+                           int* maxf, int* maxl, unsigned long long* status) {
+  int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (c >= ncell) return;
+  const double sx = site[3 * c], sy = site[3 * c + 1], sz = site[3 * c + 2];
+  const int64_t f0 = cfo[c], f1 = cfo[c + 1];
+  double V = 0.0, R = 0.0;
+  for (int64_t f = f0; f < f1; ++f) {
+    const double4_32a P = plane[f];
+    const double dr = P.w - (P.x * sx + P.y * sy + P.z * sz);
+    if (!(dr > 0.0)) atomicExch(status, (unsigned long long)(-MAP_EINVAL));  // site must be strictly inside
+    face64[f] = make_double4_32a(P.x, P.y, P.z, dr);
+    face32[f] = make_float4((float)P.x, (float)P.y, (float)P.z, (float)dr);
+    const int64_t b = fvo[f], e = fvo[f + 1];
+    const int64_t L = e - b;
+    double ax = 0, ay = 0, az = 0;
+    for (int64_t k = 0; k < L; ++k) {
+      const int32_t ia = fv[b + k], ib = fv[b + (k + 1 == L ? 0 : k + 1)];
+      const double Ax = vx[ia] - sx, Ay = vy[ia] - sy, Az = vz[ia] - sz;
+      const double Bx = vx[ib] - sx, By = vy[ib] - sy, Bz = vz[ib] - sz;
+      // cell radius: fixed evaluation order, no FMA contraction
+      double r = __dsqrt_rn(__dadd_rn(__dadd_rn(__dmul_rn(Ax, Ax), __dmul_rn(Ay, Ay)), __dmul_rn(Az, Az)));
+      R = r > R ? r : R;
+      // area vector (site-relative loop)
+      ax += Ay * Bz - Az * By;
+      ay += Az * Bx - Ax * Bz;
+      az += Ax * By - Ay * Bx;
+      double ex = Bx - Ax, ey = By - Ay, ez = Bz - Az;
+      const double len = sqrt(ex * ex + ey * ey + ez * ez);
+      double* E = edge64 + (b + k) * EDGE_STRIDE;
+      float* Ef = edge32 + (b + k) * EDGE_STRIDE;
+      if (len > 1e-13 * (dr > 0 ? dr : 1.0)) {
+        ex /= len; ey /= len; ez /= len;
+        // in-plane inward normal (loops are CCW seen from outside): m = n x e
+        const double mx = P.y * ez - P.z * ey, my = P.z * ex - P.x * ez, mz = P.x * ey - P.y * ex;
+        const double delta = mx * Ax + my * Ay + mz * Az;
+        const double ea = ex * Ax + ey * Ay + ez * Az;
+        const double eb = ex * Bx + ey * By + ez * Bz;
+        const double rec[9] = {mx, my, mz, delta, ex, ey, ez, ea, eb};
+        for (int j = 0; j < 9; ++j) { E[j] = rec[j]; Ef[j] = (float)rec[j]; }
+      } else {
+        // zero-length edge: no wedge; R0s = m.y - delta*hinv is +huge, so the edge
+        // never makes p 'outside' and its r0^2 + R0^2 is beyond the support
+        const double rec[9] = {0, 0, 0, -1e30, 0, 0, 0, 0, 0};
+        for (int j = 0; j < 9; ++j) { E[j] = rec[j]; Ef[j] = (float)rec[j]; }
+      }
+      for (int j = 9; j < EDGE_STRIDE; ++j) { E[j] = 0; Ef[j] = 0; }
+    }
+    const double area = 0.5 * (ax * P.x + ay * P.y + az * P.z);
+    V += dr * area / 3.0;
+  }
+  vol[c] = V;
+  rad[c] = R;
+  atomicMax(maxf, (int)(f1 - f0));
+  atomicMax(maxl, (int)(fvo[f1] - fvo[f0]));
+}
+
+// CSR sanity: offsets start at 0, end at the totals, never decrease; every
+// face has at least 3 loop entries, every cell at least 4 faces; vertex
+// indices in range.  Any violation sets *bad; nothing is indexed with an
+// unchecked value.
+__global__ void check_csr(int64_t ncell, int64_t nface, int64_t nloop, int64_t nvert, const int64_t* __restrict__ cfo,
+                          const int64_t* __restrict__ fvo, const int32_t* __restrict__ fv, unsigned long long* bad) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t c = i; c < ncell; c += stride) {
+    const int64_t a = cfo[c], b = cfo[c + 1];
+    if (a < 0 || b > nface || b - a < 4) atomicOr(bad, 1ULL);
+  }
+  for (int64_t f = i; f < nface; f += stride) {
+    const int64_t a = fvo[f], b = fvo[f + 1];
+    if (a < 0 || b > nloop || b - a < 3) atomicOr(bad, 2ULL);
+  }
+  for (int64_t k = i; k < nloop; k += stride) {
+    const int32_t v = fv[k];
+    if (v < 0 || v >= nvert) atomicOr(bad, 4ULL);
+  }
+  if (i == 0 && (cfo[0] != 0 || cfo[ncell] != nface || fvo[0] != 0 || fvo[nface] != nloop)) atomicOr(bad, 8ULL);
+}
+
+}  // namespace
+
+int ctx_alloc_grid(map_ctx* ctx, PreparedGrid* g, void** p, size_t bytes) {
+  if (bytes == 0) bytes = 16;
+  if (ctx->cfg.hbm_budget && ctx->bytes_in_use + bytes > ctx->cfg.hbm_budget) return MAP_ENOMEM;
+  if (cudaMalloc(p, bytes) != cudaSuccess) {
+    cudaGetLastError();
+    return MAP_ENOMEM;
+  }
+  ctx->bytes_in_use += bytes;
+  g->bytes += bytes;
+  g->allocs.push_back(*p);
+  return MAP_OK;
+}
+
+int grid_prepare(map_ctx* ctx, const map_grid* in, PreparedGrid* g, cudaStream_t s) {
+  g->ncell = in->ncell;
+  g->nface = in->nface;
+  g->nloop = in->nloop;
+  g->nvert = in->nvert;
+  const int64_t nc = in->ncell, nf = in->nface, nl = in->nloop, nv = in->nvert;
+  MAP_TRY(ctx_alloc_grid(ctx, g, (void**)&g->cell_face_off, (nc + 1) * sizeof(int64_t)));
+  MAP_TRY(ctx_alloc_grid(ctx, g, (void**)&g->face_vert_off, (nf + 1) * sizeof(int64_t)));
+  MAP_TRY(ctx_alloc_grid(ctx, g, (void**)&g->face_vert, nl * sizeof(int32_t)));
+  MAP_TRY(ctx_alloc_grid(ctx, g, (void**)&g->face_plane, nf * sizeof(double4_32a)));
+  MAP_TRY(ctx_alloc_grid(ctx, g, (void**)&g->face64, nf * sizeof(double4_32a)));
+  MAP_TRY(ctx_alloc_grid(ctx, g, (void**)&g->face32, nf * sizeof(float4)));
+  MAP_TRY(ctx_alloc_grid(ctx, g, (void**)&g->edge64, nl * EDGE_STRIDE * sizeof(double)));
+  MAP_TRY(ctx_alloc_grid(ctx, g, (void**)&g->edge32, nl * EDGE_STRIDE * sizeof(float)));
+  MAP_TRY(ctx_alloc_grid(ctx, g, (void**)&g->site, nc * 3 * sizeof(double)));
+  MAP_TRY(ctx_alloc_grid(ctx, g, (void**)&g->vol, nc * sizeof(double)));
+  MAP_TRY(ctx_alloc_grid(ctx, g, (void**)&g->rad, nc * sizeof(double)));
+  MAP_TRY(ctx_alloc_grid(ctx, g, (void**)&g->vx, nv * sizeof(double)));
+  MAP_TRY(ctx_alloc_grid(ctx, g, (void**)&g->vy, nv * sizeof(double)));
+  MAP_TRY(ctx_alloc_grid(ctx, g, (void**)&g->vz, nv * sizeof(double)));
+  CUDA_TRY(cudaMemcpyAsync(g->cell_face_off, in->cell_face_off, (nc + 1) * sizeof(int64_t), cudaMemcpyDefault, s));
+  CUDA_TRY(cudaMemcpyAsync(g->face_vert_off, in->face_vert_off, (nf + 1) * sizeof(int64_t), cudaMemcpyDefault, s));
+  CUDA_TRY(cudaMemcpyAsync(g->face_vert, in->face_vert, nl * sizeof(int32_t), cudaMemcpyDefault, s));
+  CUDA_TRY(cudaMemcpyAsync(g->face_plane, in->face_plane, nf * sizeof(double4_32a), cudaMemcpyDefault, s));
+  CUDA_TRY(cudaMemcpyAsync(g->site, in->site, nc * 3 * sizeof(double), cudaMemcpyDefault, s));
+  CUDA_TRY(cudaMemcpyAsync(g->vx, in->vx, nv * sizeof(double), cudaMemcpyDefault, s));
+  CUDA_TRY(cudaMemcpyAsync(g->vy, in->vy, nv * sizeof(double), cudaMemcpyDefault, s));
+  CUDA_TRY(cudaMemcpyAsync(g->vz, in->vz, nv * sizeof(double), cudaMemcpyDefault, s));
+  // small device scratch: [0] max faces, [1] max loops, bytes 16..23 status, 24..31 CSR check
+  int* d_small = nullptr;
+  MAP_TRY(ctx_alloc_grid(ctx, g, (void**)&d_small, 64));
+  CUDA_TRY(cudaMemsetAsync(d_small, 0, 64, s));
+  unsigned long long* d_status = reinterpret_cast<unsigned long long*>(d_small + 4);
+  unsigned long long* d_bad = reinterpret_cast<unsigned long long*>(d_small + 6);
+  check_csr<<<1024, 256, 0, s>>>(nc, nf, nl, nv, g->cell_face_off, g->face_vert_off, g->face_vert, d_bad); ++ctx->launches;
+  CUDA_TRY(cudaGetLastError());
+  unsigned long long bad = 0;
+  CUDA_TRY(cudaMemcpyAsync(&bad, d_bad, sizeof(bad), cudaMemcpyDeviceToHost, s));
+  CUDA_TRY(cudaStreamSynchronize(s));
+  if (bad) return MAP_EINVAL;
+  const int tpb = 128;
+  const int64_t blocks = (nc + tpb - 1) / tpb;
+  prep_cells<<<(unsigned)blocks, tpb, 0, s>>>(nc, g->cell_face_off, g->face_vert_off, g->face_vert, g->face_plane,
+                                              g->vx, g->vy, g->vz, g->site, g->face64, g->face32, g->edge64,
+                                              g->edge32, g->vol, g->rad, d_small, d_small + 1, d_status); ++ctx->launches;
+  CUDA_TRY(cudaGetLastError());
+  int64_t hs[4] = {0, 0, 0, 0};
+  CUDA_TRY(cudaMemcpyAsync(hs, d_small, 32, cudaMemcpyDeviceToHost, s));
+  CUDA_TRY(cudaStreamSynchronize(s));
+  int hi[8];
+  std::memcpy(hi, hs, sizeof(hi));
+  g->max_faces = hi[0];
+  g->max_loops = hi[1];
+  unsigned long long st;
+  std::memcpy(&st, &hi[4], sizeof(st));
+  if (st != 0) return MAP_EINVAL;
+  return MAP_OK;
+}

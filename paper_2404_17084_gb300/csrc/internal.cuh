@@ -1,0 +1,152 @@
+// Internal definitions shared by the library's translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <vector>
+
+#include "../../include/exactmap.h"
+
+#define MAP_PI 3.14159265358979323846
+
+#define CUDA_TRY(expr)                        \
+  do {                                        \
+    cudaError_t _e = (expr);                  \
+    if (_e != cudaSuccess) return MAP_ECUDA;  \
+  } while (0)
+
+#define MAP_TRY(expr)            \
+  do {                           \
+    int _r = (expr);             \
+    if (_r != MAP_OK) return _r; \
+  } while (0)
+
+// A device buffer that only grows.
+struct DevBuf {
+  void* p = nullptr;
+  size_t cap = 0;
+};
+
+// A grid prepared for the kernels (all device memory owned by the context).
+struct PreparedGrid {
+  int64_t ncell = 0, nface = 0, nloop = 0, nvert = 0;
+  int64_t* cell_face_off = nullptr;  // [ncell+1]
+  int64_t* face_vert_off = nullptr;  // [nface+1]
+  double4_32a* face_plane = nullptr;     // absolute (nx,ny,nz,d) [nface]
+  double4_32a* face64 = nullptr;         // site-relative (nx,ny,nz,d - n.s) [nface]
+  float4* face32 = nullptr;          // same, FP32
+  double* edge64 = nullptr;          // EDGE_STRIDE doubles per loop entry (site-relative)
+  float* edge32 = nullptr;           // EDGE_STRIDE floats per loop entry
+  double* site = nullptr;            // [3*ncell]
+  double* vol = nullptr;             // [ncell]
+  double* rad = nullptr;             // [ncell] largest vertex distance from the site
+  double* vx = nullptr;              // vertices (for the pair rule bounding tests)
+  double* vy = nullptr;
+  double* vz = nullptr;
+  int32_t* face_vert = nullptr;
+  int max_faces = 0;                 // largest face count of a cell
+  int max_loops = 0;                 // largest loop-entry count of a cell
+  std::vector<void*> allocs;
+  size_t bytes = 0;
+};
+
+// Per-edge record: in-plane inward normal m (3), delta = m.(v_a - s) (so that
+// m.(p - v_a) = m.(r - s) - delta > 0 when p is on the inner side),
+// unit direction e (3), eps_a = e.(v_a - s), eps_b = e.(v_b - s), pad (3).
+#define EDGE_STRIDE 12
+
+// Octree over a particle set (Morton order, level-synchronous build).
+struct DevTree {
+  int64_t n = 0;          // particles
+  int64_t nnodes = 0;
+  int nlevels = 0;
+  std::vector<int64_t> level_begin;  // host: first node of each level (+ end)
+  // particle arrays in Morton order
+  uint64_t* keys = nullptr;
+  int32_t* idx = nullptr;             // sorted position -> particle index
+  double* xs = nullptr;               // positions/mass/h in sorted order
+  double* ys = nullptr;
+  double* zs = nullptr;
+  double* ms = nullptr;
+  double* hs = nullptr;
+  int32_t* owner = nullptr;           // sorted position -> leaf node
+  // node arrays
+  int64_t* label = nullptr;
+  int32_t* level = nullptr;
+  int64_t* begin = nullptr;           // range in sorted order
+  int64_t* end = nullptr;
+  int64_t* first_child = nullptr;
+  int32_t* nchild = nullptr;
+  int32_t* parent = nullptr;
+  double* mass = nullptr;
+  double* com = nullptr;              // 3 per node
+  unsigned long long* size_bits = nullptr;  // FP64 bits of the node size (max distance to COM)
+  unsigned long long* hmax_bits = nullptr;  // FP64 bits of max h in the subtree
+  unsigned long long* bbox_bits = nullptr;  // 6 per node: FP64 bits of (minx,miny,minz) and (maxx,maxy,maxz)
+};
+
+struct map_ctx {
+  map_config cfg;
+  int device = 0;
+  int sm_count = 0;
+  size_t bytes_in_use = 0;
+  std::vector<PreparedGrid*> grids;
+  // workspace
+  DevBuf ws_tree[24];
+  DevBuf ws_pairs[8];
+  DevBuf ws_misc[8];
+  DevBuf cub_tmp;
+  DevTree tree;
+  // results of the last mapping call
+  int64_t last_ncell = 0;
+  int64_t n_pairs = 0;
+  int64_t* pair_off = nullptr;
+  int32_t* pair_idx = nullptr;
+  double* pair_frac = nullptr;
+  // device counters: [0] status, [1] edge terms, [2] fp64 terms, [3] work queue,
+  // [4..5] scratch, [8] face tests, [9] edge records read, [10] inner-piece
+  // antiderivative evaluations, [11] middle-piece Gauss-Legendre intervals
+  unsigned long long* d_counters = nullptr;
+  double* d_total = nullptr;
+  map_stats* h_stats = nullptr;  // pinned
+  cudaStream_t last_stream = nullptr;
+  int64_t* h_scratch = nullptr;  // pinned scratch for small readbacks
+  int64_t launches = 0;          // kernels this context has launched (own kernels only)
+  int64_t last_work[4] = {0, 0, 0, 0};  // work tally of the last mapping call (see map_get_work)
+  // phase events (start/stop pairs): 0 tree build, 1 pair list, 2 pair integrals, 3 h solve
+  cudaEvent_t ev[8] = {};
+  bool ev_used[4] = {false, false, false, false};
+};
+
+inline void phase_begin(map_ctx* ctx, int k, cudaStream_t s) { if (ctx->ev[2 * k]) cudaEventRecord(ctx->ev[2 * k], s); }
+inline void phase_end(map_ctx* ctx, int k, cudaStream_t s) {
+  if (ctx->ev[2 * k + 1]) { cudaEventRecord(ctx->ev[2 * k + 1], s); ctx->ev_used[k] = true; }
+}
+
+// ---------------------------------------------------------------- allocation
+int ctx_ensure(map_ctx* ctx, DevBuf& b, size_t bytes);
+int ctx_alloc_grid(map_ctx* ctx, PreparedGrid* g, void** p, size_t bytes);
+
+template <typename T>
+inline int ensure_t(map_ctx* ctx, DevBuf& b, size_t count, T** out) {
+  int r = ctx_ensure(ctx, b, count * sizeof(T) + 256);
+  if (r != MAP_OK) return r;
+  *out = reinterpret_cast<T*>(b.p);
+  return MAP_OK;
+}
+
+// ---------------------------------------------------------------- subsystems
+int grid_prepare(map_ctx* ctx, const map_grid* in, PreparedGrid* g, cudaStream_t s);
+int tree_build(map_ctx* ctx, const double* x, const double* y, const double* z, const double* m,
+               const double* h, int64_t n, cudaStream_t s);
+int pairs_build(map_ctx* ctx, const PreparedGrid* g, cudaStream_t s);
+int integrals_run(map_ctx* ctx, const PreparedGrid* g, const map_particles* p, map_outputs* out, cudaStream_t s);
+int h_solve_run(map_ctx* ctx, const double* x, const double* y, const double* z, int64_t n, double* h,
+                int32_t* route, const double* h0_override, cudaStream_t s);
+int pseudo_run(map_ctx* ctx, const map_particles* full, const double* src, int nsrc, map_particles* out,
+               int32_t* kind, int64_t* ident, int64_t* n_pseudo, cudaStream_t s);
+
+// FP64 bit helpers for atomic max/min on non-negative doubles
+__device__ __forceinline__ unsigned long long dbits(double v) { return (unsigned long long)__double_as_longlong(v); }
+__device__ __forceinline__ double bitsd(unsigned long long b) { return __longlong_as_double((long long)b); }

@@ -1,0 +1,180 @@
+// Pair-list build: for every cell i, the particles a whose support may reach
+// the cell.  The rule (the paper is silent; fixed so that lists are
+// reproducible bit for bit) is
+//     |r_a - s_i| < 2 h_a + R_i   and   n_f.r_a - d_f < 2 h_a for every face f,
+// in FP64 with a fixed operation order and no FMA contraction
+// (__dmul_rn/__dadd_rn/__dsqrt_rn).  Candidates come from a traversal of the
+// particle octree pruned by node bounding box and largest h; lists are sorted
+// by particle index within each cell.
+#include <cub/cub.cuh>
+
+#include "internal.cuh"
+
+namespace {
+
+struct PairTree {
+  const double *xs, *ys, *zs, *hs;
+  const int32_t* idx;
+  const int64_t *nb, *ne, *fc;
+  const int32_t* nch;
+  const unsigned long long* bbox;
+  const unsigned long long* hmax;
+};
+
+struct PairGrid {
+  const int64_t* cfo;
+  const double4_32a* plane;  // absolute planes (the exact FP64 rule)
+  const float4* face32;      // site-relative planes (n, d - n.s) in FP32 (screening)
+  const double* site;
+  const double* rad;
+};
+
+// The exact rule, FP64, fixed order, no FMA contraction.
+__device__ __forceinline__ bool exact_dist(double sx, double sy, double sz, double R, double x, double y, double z,
+                                           double h) {
+  const double dx = __dsub_rn(x, sx), dy = __dsub_rn(y, sy), dz = __dsub_rn(z, sz);
+  const double dist = __dsqrt_rn(__dadd_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)), __dmul_rn(dz, dz)));
+  return dist < __dadd_rn(__dmul_rn(2.0, h), R);
+}
+__device__ __forceinline__ bool exact_face(const double4_32a P, double x, double y, double z, double h) {
+  const double s = __dsub_rn(__dadd_rn(__dadd_rn(__dmul_rn(P.x, x), __dmul_rn(P.y, y)), __dmul_rn(P.z, z)), P.w);
+  return s < __dmul_rn(2.0, h);
+}
+
+// The pair rule, decided in FP32 wherever the FP32 value is farther from the
+// threshold than a rigorous bound on its rounding error (all FP32 roundings
+// together stay below 1e-6 of the magnitudes involved; the margin is 1e-5),
+// and by the exact FP64 rule otherwise -- so the outcome is always the FP64
+// rule's.
+__device__ __forceinline__ bool pair_rule(const PairGrid& G, int64_t c, double sx, double sy, double sz, double R,
+                                          double x, double y, double z, double h) {
+  const float fx = (float)(x - sx), fy = (float)(y - sy), fz = (float)(z - sz);
+  const double reach = 2.0 * h + R;
+  const float reach2 = (float)(reach * reach);
+  const float d2 = fx * fx + fy * fy + fz * fz;
+  if (d2 > reach2 * 1.00001f) return false;
+  if (!(d2 < reach2 * 0.99999f) && !exact_dist(sx, sy, sz, R, x, y, z, h)) return false;
+  const float thr = (float)(2.0 * h);
+  const float l1 = fabsf(fx) + fabsf(fy) + fabsf(fz);
+  for (int64_t f = G.cfo[c]; f < G.cfo[c + 1]; ++f) {
+    const float4 F = G.face32[f];
+    const float sv = (F.x * fx + F.y * fy + F.z * fz) - F.w;
+    const float marg = 1e-5f * (l1 + fabsf(F.w) + thr) + 1e-30f;
+    if (sv > thr + marg) return false;
+    if (sv >= thr - marg && !exact_face(G.plane[f], x, y, z, h)) return false;
+  }
+  return true;
+}
+
+__device__ __forceinline__ double box_d2(const unsigned long long* bb, double x, double y, double z) {
+  double lo0 = bitsd(bb[0]), lo1 = bitsd(bb[1]), lo2 = bitsd(bb[2]);
+  double hi0 = bitsd(bb[3]), hi1 = bitsd(bb[4]), hi2 = bitsd(bb[5]);
+  double dx = x < lo0 ? lo0 - x : (x > hi0 ? x - hi0 : 0.0);
+  double dy = y < lo1 ? lo1 - y : (y > hi1 ? y - hi1 : 0.0);
+  double dz = z < lo2 ? lo2 - z : (z > hi2 ? z - hi2 : 0.0);
+  return dx * dx + dy * dy + dz * dz;
+}
+
+// FILL = false: count pairs per cell; FILL = true: write them at off[c].
+template <bool FILL>
+__global__ void pair_traverse(int64_t ncell, const int32_t* __restrict__ order, PairTree T, PairGrid G,
+                              int64_t* count, const int64_t* __restrict__ off, int32_t* out) {
+  int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (t >= ncell) return;
+  const int64_t c = order ? order[t] : t;
+  const double sx = G.site[3 * c], sy = G.site[3 * c + 1], sz = G.site[3 * c + 2];
+  const double R = G.rad[c];
+  int64_t w = FILL ? off[c] : 0;
+  int64_t cnt = 0;
+  int32_t stack[192];
+  int sp = 0;
+  stack[sp++] = 0;
+  while (sp > 0) {
+    const int32_t nd = stack[--sp];
+    // conservative prune: no particle of the node can pass the distance test
+    const double reach = 2.0 * bitsd(T.hmax[nd]) + R;
+    if (box_d2(T.bbox + 6 * nd, sx, sy, sz) > reach * reach * (1.0 + 1e-12)) continue;
+    if (T.nch[nd] == 0) {
+      for (int64_t k = T.nb[nd]; k < T.ne[nd]; ++k) {
+        if (pair_rule(G, c, sx, sy, sz, R, T.xs[k], T.ys[k], T.zs[k], T.hs[k])) {
+          if (FILL) out[w++] = T.idx[k];
+          ++cnt;
+        }
+      }
+    } else {
+      const int64_t c0 = T.fc[nd];
+      for (int k = T.nch[nd] - 1; k >= 0; --k) stack[sp++] = (int32_t)(c0 + k);
+    }
+  }
+  if (!FILL) count[c] = cnt;
+}
+
+__global__ void site_keys(int64_t n, const double* __restrict__ site, uint64_t* keys, int32_t* idx) {
+  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  auto q = [](double v) -> uint64_t {
+    double s = floor(v * 1024.0);
+    s = s < 0 ? 0 : (s > 1023 ? 1023 : s);
+    return (uint64_t)s;
+  };
+  uint64_t k = 0;
+  uint64_t xi = q(site[3 * i]), yi = q(site[3 * i + 1]), zi = q(site[3 * i + 2]);
+  for (int b = 9; b >= 0; --b) k = (k << 3) | (((xi >> b) & 1) << 2) | (((yi >> b) & 1) << 1) | ((zi >> b) & 1);
+  keys[i] = k;
+  idx[i] = (int32_t)i;
+}
+
+inline unsigned nblk(int64_t n, int t) { return (unsigned)((n + t - 1) / t); }
+
+}  // namespace
+
+int pairs_build(map_ctx* ctx, const PreparedGrid* g, cudaStream_t s) {
+  DevTree& T = ctx->tree;
+  const int64_t nc = g->ncell;
+  const int tpb = 128;
+  // cells visited in Morton order of their sites for coherent traversals
+  uint64_t *k_in, *k_out;
+  int32_t *o_in, *order;
+  MAP_TRY(ensure_t(ctx, ctx->ws_pairs[4], nc, &k_in));
+  MAP_TRY(ensure_t(ctx, ctx->ws_pairs[5], nc, &k_out));
+  MAP_TRY(ensure_t(ctx, ctx->ws_pairs[6], nc, &o_in));
+  MAP_TRY(ensure_t(ctx, ctx->ws_pairs[7], nc, &order));
+  site_keys<<<nblk(nc, 256), 256, 0, s>>>(nc, g->site, k_in, o_in); ++ctx->launches;
+  CUDA_TRY(cudaGetLastError());
+  size_t tb = 0;
+  CUDA_TRY(cub::DeviceRadixSort::SortPairs(nullptr, tb, k_in, k_out, o_in, order, nc, 0, 30, s));
+  MAP_TRY(ctx_ensure(ctx, ctx->cub_tmp, tb));
+  CUDA_TRY(cub::DeviceRadixSort::SortPairs(ctx->cub_tmp.p, tb, k_in, k_out, o_in, order, nc, 0, 30, s));
+
+  PairTree PT{T.xs, T.ys, T.zs, T.hs, T.idx, T.begin, T.end, T.first_child, T.nchild, T.bbox_bits, T.hmax_bits};
+  PairGrid PG{g->cell_face_off, g->face_plane, g->face32, g->site, g->rad};
+  int64_t *count, *off;
+  MAP_TRY(ensure_t(ctx, ctx->ws_pairs[0], nc + 1, &count));
+  MAP_TRY(ensure_t(ctx, ctx->ws_pairs[1], nc + 1, &off));
+  CUDA_TRY(cudaMemsetAsync(count + nc, 0, sizeof(int64_t), s));
+  pair_traverse<false><<<nblk(nc, tpb), tpb, 0, s>>>(nc, order, PT, PG, count, nullptr, nullptr); ++ctx->launches;
+  CUDA_TRY(cudaGetLastError());
+  tb = 0;
+  CUDA_TRY(cub::DeviceScan::ExclusiveSum(nullptr, tb, count, off, nc + 1, s));
+  MAP_TRY(ctx_ensure(ctx, ctx->cub_tmp, tb));
+  CUDA_TRY(cub::DeviceScan::ExclusiveSum(ctx->cub_tmp.p, tb, count, off, nc + 1, s));
+  CUDA_TRY(cudaMemcpyAsync(ctx->h_scratch, off + nc, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+  CUDA_TRY(cudaStreamSynchronize(s));
+  const int64_t np = ctx->h_scratch[0];
+  int32_t *raw, *sorted;
+  MAP_TRY(ensure_t(ctx, ctx->ws_pairs[2], np + 1, &raw));
+  MAP_TRY(ensure_t(ctx, ctx->ws_pairs[3], np + 1, &sorted));
+  pair_traverse<true><<<nblk(nc, tpb), tpb, 0, s>>>(nc, order, PT, PG, nullptr, off, raw); ++ctx->launches;
+  CUDA_TRY(cudaGetLastError());
+  if (np > 0) {
+    tb = 0;
+    CUDA_TRY(cub::DeviceSegmentedSort::SortKeys(nullptr, tb, raw, sorted, np, nc, off, off + 1, s));
+    MAP_TRY(ctx_ensure(ctx, ctx->cub_tmp, tb));
+    CUDA_TRY(cub::DeviceSegmentedSort::SortKeys(ctx->cub_tmp.p, tb, raw, sorted, np, nc, off, off + 1, s));
+  }
+  ctx->n_pairs = np;
+  ctx->pair_off = off;
+  ctx->pair_idx = sorted;
+  ctx->last_ncell = nc;
+  return MAP_OK;
+}

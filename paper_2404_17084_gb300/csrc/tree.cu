@@ -1,0 +1,525 @@
+// Device octree over a particle set and the smoothing-length solve.
+//
+// Octree (Section III-A, built as an octree with a leaf capacity instead of
+// the paper's RCB tree): 63-bit Morton keys (21 bits per axis) are radix
+// sorted; nodes are built level by level from the sorted keys, a node at
+// level L being the cube of side 2^-L holding a contiguous key range, split
+// while it holds more than leaf_size particles (up to level 21).  Labels carry
+// a leading 1 bit, so parent = label >> 3 (the paper's heap-style label
+// arithmetic with eight children).  Node mass and centre of mass are summed
+// bottom-up; node size (distance from the centre of mass to the furthest
+// particle, Section III-A), largest h and bounding box are reduced over each
+// node's particles.
+//
+// h solve (Section III-C, Eq. 7-9): Newton-Raphson on g(h) = h - hfact n(h)^(-1/3)
+// with n(h) = sum_b W(r_ab, h) summed by an octree range query, then bisection,
+// then the estimate.
+#include <cub/cub.cuh>
+
+#include "internal.cuh"
+
+namespace {
+
+constexpr int MORTON_BITS = 21;
+constexpr int64_t BIG_NODE = 4096;
+
+struct MaxOp {
+  __device__ __forceinline__ double operator()(double a, double b) const { return a > b ? a : b; }
+};
+struct MinOp {
+  __device__ __forceinline__ double operator()(double a, double b) const { return a < b ? a : b; }
+};
+
+__device__ __forceinline__ uint64_t spread3(uint64_t v) {
+  v &= 0x1fffff;
+  v = (v | v << 32) & 0x1f00000000ffffULL;
+  v = (v | v << 16) & 0x1f0000ff0000ffULL;
+  v = (v | v << 8) & 0x100f00f00f00f00fULL;
+  v = (v | v << 4) & 0x10c30c30c30c30c3ULL;
+  v = (v | v << 2) & 0x1249249249249249ULL;
+  return v;
+}
+
+__device__ __forceinline__ uint64_t coord21(double v) {
+  double s = floor(v * 2097152.0);
+  if (!(s >= 0.0)) s = 0.0;
+  if (s > 2097151.0) s = 2097151.0;
+  return (uint64_t)s;
+}
+
+__global__ void morton_keys(int64_t n, const double* __restrict__ x, const double* __restrict__ y,
+                            const double* __restrict__ z, uint64_t* keys, int32_t* idx) {
+  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  keys[i] = (spread3(coord21(x[i])) << 2) | (spread3(coord21(y[i])) << 1) | spread3(coord21(z[i]));
+  idx[i] = (int32_t)i;
+}
+
+__global__ void gather_sorted(int64_t n, const int32_t* __restrict__ idx, const double* __restrict__ x,
+                              const double* __restrict__ y, const double* __restrict__ z,
+                              const double* __restrict__ m, const double* __restrict__ h, double* xs, double* ys,
+                              double* zs, double* ms, double* hs) {
+  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  int32_t a = idx[i];
+  xs[i] = x[a] + 0.0;  // + 0.0 turns -0.0 into +0.0 (bit-ordered min/max below)
+  ys[i] = y[a] + 0.0;
+  zs[i] = z[a] + 0.0;
+  ms[i] = m ? m[a] : 1.0;
+  hs[i] = h ? h[a] : 0.0;
+}
+
+__device__ __forceinline__ int64_t lower_octant(const uint64_t* keys, int64_t b, int64_t e, int shift, int o) {
+  // first position in [b,e) whose octant at this shift is >= o
+  int64_t lo = b, hi = e;
+  while (lo < hi) {
+    int64_t mid = (lo + hi) >> 1;
+    if ((int)((keys[mid] >> shift) & 7) < o) lo = mid + 1; else hi = mid;
+  }
+  return lo;
+}
+
+__global__ void split_count(int64_t lb, int64_t le, const uint64_t* __restrict__ keys, const int64_t* __restrict__ nb,
+                            const int64_t* __restrict__ ne, const int32_t* __restrict__ lev, int leaf_size,
+                            int32_t* nchild) {
+  int64_t i = lb + blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= le) return;
+  int64_t b = nb[i], e = ne[i];
+  int L = lev[i];
+  int cnt = 0;
+  if (e - b > leaf_size && L < MORTON_BITS) {
+    int shift = 3 * (MORTON_BITS - L - 1);
+    int64_t prev = b;
+    for (int o = 1; o <= 8; ++o) {
+      int64_t nx = (o == 8) ? e : lower_octant(keys, b, e, shift, o);
+      if (nx > prev) ++cnt;
+      prev = nx;
+    }
+  }
+  nchild[i - lb] = cnt;
+}
+
+__global__ void split_write(int64_t lb, int64_t le, int64_t next_begin, const uint64_t* __restrict__ keys,
+                            int64_t* nb, int64_t* ne, int32_t* lev, int64_t* label, int64_t* first_child,
+                            int32_t* nchild_out, int32_t* parent, const int32_t* __restrict__ nchild,
+                            const int64_t* __restrict__ choff) {
+  int64_t i = lb + blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= le) return;
+  int cnt = nchild[i - lb];
+  nchild_out[i] = cnt;
+  if (cnt == 0) { first_child[i] = -1; return; }
+  int64_t b = nb[i], e = ne[i];
+  int L = lev[i];
+  int shift = 3 * (MORTON_BITS - L - 1);
+  int64_t w = next_begin + choff[i - lb];
+  first_child[i] = w;
+  int64_t prev = b;
+  for (int o = 1; o <= 8; ++o) {
+    int64_t nx = (o == 8) ? e : lower_octant(keys, b, e, shift, o);
+    if (nx > prev) {
+      nb[w] = prev;
+      ne[w] = nx;
+      lev[w] = L + 1;
+      label[w] = label[i] * 8 + (o - 1);
+      parent[w] = (int32_t)i;
+      ++w;
+    }
+    prev = nx;
+  }
+}
+
+// Bottom-up sums for one level: leaves sum their particles in sorted order,
+// internal nodes sum their children in octant order.
+__global__ void node_sums(int64_t lb, int64_t le, const int64_t* __restrict__ nb, const int64_t* __restrict__ ne,
+                          const int64_t* __restrict__ fc, const int32_t* __restrict__ nch,
+                          const double* __restrict__ xs, const double* __restrict__ ys,
+                          const double* __restrict__ zs, const double* __restrict__ ms, double* mass,
+                          double* msum /* 3 per node: sum m x */, int32_t* owner) {
+  int64_t i = lb + blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= le) return;
+  double M = 0, Sx = 0, Sy = 0, Sz = 0;
+  if (nch[i] == 0) {
+    for (int64_t k = nb[i]; k < ne[i]; ++k) {
+      double mk = ms[k];
+      M += mk;
+      Sx += mk * xs[k];
+      Sy += mk * ys[k];
+      Sz += mk * zs[k];
+      owner[k] = (int32_t)i;
+    }
+  } else {
+    for (int64_t c = fc[i]; c < fc[i] + nch[i]; ++c) {
+      M += mass[c];
+      Sx += msum[3 * c];
+      Sy += msum[3 * c + 1];
+      Sz += msum[3 * c + 2];
+    }
+  }
+  mass[i] = M;
+  msum[3 * i] = Sx;
+  msum[3 * i + 1] = Sy;
+  msum[3 * i + 2] = Sz;
+}
+
+__global__ void node_com(int64_t nn, const double* __restrict__ mass, const double* __restrict__ msum, double* com,
+                         unsigned long long* size_bits, unsigned long long* hmax_bits, unsigned long long* bbox) {
+  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= nn) return;
+  double M = mass[i];
+  com[3 * i] = msum[3 * i] / M;
+  com[3 * i + 1] = msum[3 * i + 1] / M;
+  com[3 * i + 2] = msum[3 * i + 2] / M;
+  size_bits[i] = 0ULL;
+  hmax_bits[i] = 0ULL;
+  for (int k = 0; k < 3; ++k) {
+    bbox[6 * i + k] = 0x7ff0000000000000ULL;  // +inf
+    bbox[6 * i + 3 + k] = 0ULL;
+  }
+}
+
+// Small nodes: every particle walks up from its leaf while the node holds at
+// most BIG_NODE particles and reduces into it with atomics.
+__global__ void node_extent_small(int64_t n, const int32_t* __restrict__ owner, const int32_t* __restrict__ parent,
+                                  const int64_t* __restrict__ nb, const int64_t* __restrict__ ne,
+                                  const double* __restrict__ xs, const double* __restrict__ ys,
+                                  const double* __restrict__ zs, const double* __restrict__ hs,
+                                  const double* __restrict__ com, unsigned long long* size_bits,
+                                  unsigned long long* hmax_bits, unsigned long long* bbox) {
+  int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (k >= n) return;
+  double x = xs[k], y = ys[k], z = zs[k], h = hs[k];
+  int32_t node = owner[k];
+  while (node >= 0 && ne[node] - nb[node] <= BIG_NODE) {
+    double dx = x - com[3 * node], dy = y - com[3 * node + 1], dz = z - com[3 * node + 2];
+    double d = sqrt(dx * dx + dy * dy + dz * dz);
+    atomicMax(&size_bits[node], dbits(d));
+    atomicMax(&hmax_bits[node], dbits(h));
+    atomicMin(&bbox[6 * node + 0], dbits(x));
+    atomicMin(&bbox[6 * node + 1], dbits(y));
+    atomicMin(&bbox[6 * node + 2], dbits(z));
+    atomicMax(&bbox[6 * node + 3], dbits(x));
+    atomicMax(&bbox[6 * node + 4], dbits(y));
+    atomicMax(&bbox[6 * node + 5], dbits(z));
+    node = parent[node];
+  }
+}
+
+// Big nodes: one block per node reduces over its whole particle range.
+__global__ void node_extent_big(const int32_t* __restrict__ big, const int64_t* __restrict__ nb,
+                                const int64_t* __restrict__ ne, const double* __restrict__ xs,
+                                const double* __restrict__ ys, const double* __restrict__ zs,
+                                const double* __restrict__ hs, const double* __restrict__ com,
+                                unsigned long long* size_bits, unsigned long long* hmax_bits,
+                                unsigned long long* bbox) {
+  const int32_t node = big[blockIdx.x];
+  const double cx = com[3 * node], cy = com[3 * node + 1], cz = com[3 * node + 2];
+  double smax = 0, hmax = 0, lo[3] = {1e300, 1e300, 1e300}, hi[3] = {0, 0, 0};
+  for (int64_t k = nb[node] + threadIdx.x; k < ne[node]; k += blockDim.x) {
+    double x = xs[k], y = ys[k], z = zs[k];
+    double dx = x - cx, dy = y - cy, dz = z - cz;
+    smax = fmax(smax, sqrt(dx * dx + dy * dy + dz * dz));
+    hmax = fmax(hmax, hs[k]);
+    lo[0] = fmin(lo[0], x); lo[1] = fmin(lo[1], y); lo[2] = fmin(lo[2], z);
+    hi[0] = fmax(hi[0], x); hi[1] = fmax(hi[1], y); hi[2] = fmax(hi[2], z);
+  }
+  typedef cub::BlockReduce<double, 256> BR;
+  __shared__ typename BR::TempStorage tmp;
+  double v;
+  v = BR(tmp).Reduce(smax, MaxOp()); if (threadIdx.x == 0) size_bits[node] = dbits(v); __syncthreads();
+  v = BR(tmp).Reduce(hmax, MaxOp()); if (threadIdx.x == 0) hmax_bits[node] = dbits(v); __syncthreads();
+  for (int k = 0; k < 3; ++k) {
+    v = BR(tmp).Reduce(lo[k], MinOp()); if (threadIdx.x == 0) bbox[6 * node + k] = dbits(v); __syncthreads();
+    v = BR(tmp).Reduce(hi[k], MaxOp()); if (threadIdx.x == 0) bbox[6 * node + 3 + k] = dbits(v); __syncthreads();
+  }
+}
+
+__global__ void collect_big(int64_t nn, const int64_t* __restrict__ nb, const int64_t* __restrict__ ne, int32_t* big,
+                            unsigned long long* nbig) {
+  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= nn) return;
+  if (ne[i] - nb[i] > BIG_NODE) big[atomicAdd(nbig, 1ULL)] = (int32_t)i;
+}
+
+inline unsigned nblk(int64_t n, int t) { return (unsigned)((n + t - 1) / t); }
+
+}  // namespace
+
+// ---------------------------------------------------------------- tree build
+
+static int grow_nodes(map_ctx* ctx, int64_t need) {
+  DevTree& T = ctx->tree;
+  // node arrays live in ws_tree[8..19]; growing keeps the old contents
+  struct Arr { int slot; size_t esz; void** p; };
+  Arr arrs[] = {{8, sizeof(int64_t), (void**)&T.label},      {9, sizeof(int32_t), (void**)&T.level},
+                {10, sizeof(int64_t), (void**)&T.begin},     {11, sizeof(int64_t), (void**)&T.end},
+                {12, sizeof(int64_t), (void**)&T.first_child}, {13, sizeof(int32_t), (void**)&T.nchild},
+                {14, sizeof(int32_t), (void**)&T.parent},    {15, sizeof(double), (void**)&T.mass},
+                {16, 3 * sizeof(double), (void**)&T.com},    {17, sizeof(unsigned long long), (void**)&T.size_bits},
+                {18, sizeof(unsigned long long), (void**)&T.hmax_bits},
+                {19, 6 * sizeof(unsigned long long), (void**)&T.bbox_bits}};
+  for (auto& a : arrs) {
+    DevBuf& b = ctx->ws_tree[a.slot];
+    size_t bytes = (size_t)need * a.esz;
+    if (b.cap >= bytes) { *a.p = b.p; continue; }
+    size_t nb = bytes + bytes / 2 + 4096;
+    if (ctx->cfg.hbm_budget && ctx->bytes_in_use + nb > ctx->cfg.hbm_budget) return MAP_ENOMEM;
+    void* np = nullptr;
+    if (cudaMalloc(&np, nb) != cudaSuccess) { cudaGetLastError(); return MAP_ENOMEM; }
+    ctx->bytes_in_use += nb;
+    if (b.p) {
+      CUDA_TRY(cudaMemcpy(np, b.p, b.cap, cudaMemcpyDeviceToDevice));
+      cudaFree(b.p);
+      ctx->bytes_in_use -= b.cap;
+    }
+    b.p = np;
+    b.cap = nb;
+    *a.p = np;
+  }
+  return MAP_OK;
+}
+
+int tree_build(map_ctx* ctx, const double* x, const double* y, const double* z, const double* m, const double* h,
+               int64_t n, cudaStream_t s) {
+  DevTree& T = ctx->tree;
+  T.n = n;
+  const int tpb = 256;
+  uint64_t* keys_in;
+  int32_t* idx_in;
+  MAP_TRY(ensure_t(ctx, ctx->ws_tree[0], n, &keys_in));
+  MAP_TRY(ensure_t(ctx, ctx->ws_tree[1], n, &idx_in));
+  MAP_TRY(ensure_t(ctx, ctx->ws_tree[2], n, &T.keys));
+  MAP_TRY(ensure_t(ctx, ctx->ws_tree[3], n, &T.idx));
+  MAP_TRY(ensure_t(ctx, ctx->ws_tree[4], 5 * n, &T.xs));
+  T.ys = T.xs + n; T.zs = T.xs + 2 * n; T.ms = T.xs + 3 * n; T.hs = T.xs + 4 * n;
+  MAP_TRY(ensure_t(ctx, ctx->ws_tree[5], n, &T.owner));
+  morton_keys<<<nblk(n, tpb), tpb, 0, s>>>(n, x, y, z, keys_in, idx_in); ++ctx->launches;
+  CUDA_TRY(cudaGetLastError());
+  size_t tmp_bytes = 0;
+  CUDA_TRY(cub::DeviceRadixSort::SortPairs(nullptr, tmp_bytes, keys_in, T.keys, idx_in, T.idx, n, 0, 63, s));
+  MAP_TRY(ctx_ensure(ctx, ctx->cub_tmp, tmp_bytes));
+  CUDA_TRY(cub::DeviceRadixSort::SortPairs(ctx->cub_tmp.p, tmp_bytes, keys_in, T.keys, idx_in, T.idx, n, 0, 63, s));
+  gather_sorted<<<nblk(n, tpb), tpb, 0, s>>>(n, T.idx, x, y, z, m, h, T.xs, T.ys, T.zs, T.ms, T.hs); ++ctx->launches;
+  CUDA_TRY(cudaGetLastError());
+
+  // level-synchronous build
+  int64_t cap = n / 4 + 64;
+  MAP_TRY(grow_nodes(ctx, cap));
+  int64_t root_label = 1, zero = 0;
+  int32_t root_level = 0, root_parent = -1;
+  CUDA_TRY(cudaMemcpyAsync(T.label, &root_label, sizeof(int64_t), cudaMemcpyHostToDevice, s));
+  CUDA_TRY(cudaMemcpyAsync(T.level, &root_level, sizeof(int32_t), cudaMemcpyHostToDevice, s));
+  CUDA_TRY(cudaMemcpyAsync(T.begin, &zero, sizeof(int64_t), cudaMemcpyHostToDevice, s));
+  CUDA_TRY(cudaMemcpyAsync(T.end, &n, sizeof(int64_t), cudaMemcpyHostToDevice, s));
+  CUDA_TRY(cudaMemcpyAsync(T.parent, &root_parent, sizeof(int32_t), cudaMemcpyHostToDevice, s));
+  T.level_begin.assign(1, 0);
+  int64_t lb = 0, le = 1;
+  while (le > lb) {
+    T.level_begin.push_back(le);
+    int64_t nf = le - lb;
+    int32_t* nchild;
+    int64_t* choff;
+    MAP_TRY(ensure_t(ctx, ctx->ws_tree[6], nf + 1, &nchild));
+    MAP_TRY(ensure_t(ctx, ctx->ws_tree[7], nf + 1, &choff));
+    split_count<<<nblk(nf, tpb), tpb, 0, s>>>(lb, le, T.keys, T.begin, T.end, T.level, ctx->cfg.leaf_size, nchild); ++ctx->launches;
+    CUDA_TRY(cudaGetLastError());
+    size_t sb = 0;
+    CUDA_TRY(cub::DeviceScan::ExclusiveSum(nullptr, sb, nchild, choff, nf + 1, s));
+    MAP_TRY(ctx_ensure(ctx, ctx->cub_tmp, sb));
+    // the (nf+1)-th entry of nchild is set to 0 so that choff[nf] is the total
+    CUDA_TRY(cudaMemsetAsync(nchild + nf, 0, sizeof(int32_t), s));
+    CUDA_TRY(cub::DeviceScan::ExclusiveSum(ctx->cub_tmp.p, sb, nchild, choff, nf + 1, s));
+    CUDA_TRY(cudaMemcpyAsync(ctx->h_scratch, choff + nf, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+    CUDA_TRY(cudaStreamSynchronize(s));
+    int64_t nnew = ctx->h_scratch[0];
+    if (le + nnew > cap) {
+      cap = (le + nnew) * 2;
+      MAP_TRY(grow_nodes(ctx, cap));
+    }
+    split_write<<<nblk(nf, tpb), tpb, 0, s>>>(lb, le, le, T.keys, T.begin, T.end, T.level, T.label, T.first_child,
+                                             T.nchild, T.parent, nchild, choff); ++ctx->launches;
+    CUDA_TRY(cudaGetLastError());
+    lb = le;
+    le = le + nnew;
+  }
+  T.nnodes = le;
+  T.nlevels = (int)T.level_begin.size() - 1;
+  // bottom-up sums, deepest level first
+  double* msum;
+  MAP_TRY(ensure_t(ctx, ctx->ws_tree[20], 3 * T.nnodes, &msum));
+  for (int L = T.nlevels - 1; L >= 0; --L) {
+    int64_t a = T.level_begin[L], b = T.level_begin[L + 1];
+    node_sums<<<nblk(b - a, tpb), tpb, 0, s>>>(a, b, T.begin, T.end, T.first_child, T.nchild, T.xs, T.ys, T.zs,
+                                               T.ms, T.mass, msum, T.owner); ++ctx->launches;
+    CUDA_TRY(cudaGetLastError());
+  }
+  node_com<<<nblk(T.nnodes, tpb), tpb, 0, s>>>(T.nnodes, T.mass, msum, T.com, T.size_bits, T.hmax_bits,
+                                               T.bbox_bits); ++ctx->launches;
+  CUDA_TRY(cudaGetLastError());
+  node_extent_small<<<nblk(n, tpb), tpb, 0, s>>>(n, T.owner, T.parent, T.begin, T.end, T.xs, T.ys, T.zs, T.hs,
+                                                 T.com, T.size_bits, T.hmax_bits, T.bbox_bits); ++ctx->launches;
+  CUDA_TRY(cudaGetLastError());
+  int32_t* big;
+  MAP_TRY(ensure_t(ctx, ctx->ws_tree[21], T.nnodes, &big));
+  unsigned long long* d_nbig = ctx->d_counters + 4;
+  CUDA_TRY(cudaMemsetAsync(d_nbig, 0, sizeof(unsigned long long), s));
+  collect_big<<<nblk(T.nnodes, tpb), tpb, 0, s>>>(T.nnodes, T.begin, T.end, big, d_nbig); ++ctx->launches;
+  CUDA_TRY(cudaGetLastError());
+  CUDA_TRY(cudaMemcpyAsync(ctx->h_scratch, d_nbig, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+  CUDA_TRY(cudaStreamSynchronize(s));
+  int64_t nbig = ctx->h_scratch[0];
+  if (nbig > 0) {
+    node_extent_big<<<(unsigned)nbig, 256, 0, s>>>(big, T.begin, T.end, T.xs, T.ys, T.zs, T.hs, T.com, T.size_bits,
+                                                   T.hmax_bits, T.bbox_bits); ++ctx->launches;
+    CUDA_TRY(cudaGetLastError());
+  }
+  return MAP_OK;
+}
+
+// ---------------------------------------------------------------- h solve
+
+namespace {
+
+__device__ __forceinline__ double w_m4(double q) {
+  if (q < 1.0) return 1.0 - 1.5 * q * q + 0.75 * q * q * q;
+  if (q < 2.0) { double t = 2.0 - q; return 0.25 * t * t * t; }
+  return 0.0;
+}
+__device__ __forceinline__ double dw_m4(double q) {
+  if (q < 1.0) return -3.0 * q + 2.25 * q * q;
+  if (q < 2.0) { double t = 2.0 - q; return -0.75 * t * t; }
+  return 0.0;
+}
+
+__device__ __forceinline__ double box_dist2(const unsigned long long* bb, double x, double y, double z) {
+  double lo0 = bitsd(bb[0]), lo1 = bitsd(bb[1]), lo2 = bitsd(bb[2]);
+  double hi0 = bitsd(bb[3]), hi1 = bitsd(bb[4]), hi2 = bitsd(bb[5]);
+  double dx = x < lo0 ? lo0 - x : (x > hi0 ? x - hi0 : 0.0);
+  double dy = y < lo1 ? lo1 - y : (y > hi1 ? y - hi1 : 0.0);
+  double dz = z < lo2 ? lo2 - z : (z > hi2 ? z - hi2 : 0.0);
+  return dx * dx + dy * dy + dz * dz;
+}
+
+struct TreeView {
+  const double *xs, *ys, *zs;
+  const int64_t *nb, *ne, *fc;
+  const int32_t* nch;
+  const unsigned long long* bbox;
+};
+
+// n(h) = sum_b W(r_ab, h) and dn/dh over all tree particles within 2h.
+__device__ void density_sum(const TreeView& T, double x, double y, double z, double h, double& n, double& dn) {
+  const double R = 2.0 * h, R2 = R * R;
+  const double inv_h = 1.0 / h;
+  const double norm = 1.0 / (MAP_PI * h * h * h);
+  double s = 0.0, ds = 0.0;
+  int32_t stack[192];
+  int sp = 0;
+  stack[sp++] = 0;
+  while (sp > 0) {
+    int32_t nd = stack[--sp];
+    if (box_dist2(T.bbox + 6 * nd, x, y, z) >= R2) continue;
+    if (T.nch[nd] == 0) {
+      for (int64_t k = T.nb[nd]; k < T.ne[nd]; ++k) {
+        double dx = T.xs[k] - x, dy = T.ys[k] - y, dz = T.zs[k] - z;
+        double r2 = dx * dx + dy * dy + dz * dz;
+        if (r2 >= R2) continue;
+        double q = sqrt(r2) * inv_h;
+        double w = w_m4(q);
+        s += w;
+        ds += 3.0 * w + q * dw_m4(q);
+      }
+    } else {
+      int64_t c0 = T.fc[nd];
+      for (int c = T.nch[nd] - 1; c >= 0; --c) stack[sp++] = (int32_t)(c0 + c);
+    }
+  }
+  n = s * norm;
+  dn = -ds * norm * inv_h;
+}
+
+__device__ __forceinline__ double g_of(const TreeView& T, double x, double y, double z, double h, double hfact) {
+  double n, dn;
+  density_sum(T, x, y, z, h, n, dn);
+  return h - hfact * pow(n, -1.0 / 3.0);
+}
+
+// One thread per particle (sorted order).  h0 per sorted position.
+__global__ void h_newton(int64_t n, TreeView T, const int32_t* __restrict__ idx, const double* __restrict__ h0s,
+                         double hfact, double* hout, int32_t* route) {
+  int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (k >= n) return;
+  const double x = T.xs[k], y = T.ys[k], z = T.zs[k];
+  const double g0 = h0s[k];
+  const double lo = g0 / 16.0, hi = g0 * 16.0;
+  double h = g0;
+  bool ok = false;
+  for (int it = 0; it < 30; ++it) {
+    double nn, dn;
+    density_sum(T, x, y, z, h, nn, dn);
+    double f = h - hfact * pow(nn, -1.0 / 3.0);
+    double fp = 1.0 + hfact / 3.0 * pow(nn, -4.0 / 3.0) * dn;
+    double hn = h - f / fp;
+    if (!(hn >= lo && hn <= hi)) break;
+    if (fabs(hn - h) < 1e-10 * hn) { h = hn; ok = true; break; }
+    h = hn;
+  }
+  int r = 0;
+  if (!ok) {
+    double flo = g_of(T, x, y, z, lo, hfact), fhi = g_of(T, x, y, z, hi, hfact);
+    if (!(flo < 0.0 && fhi > 0.0)) {
+      h = g0;
+      r = 2;
+    } else {
+      double a0 = lo, b0 = hi;
+      for (int it = 0; it < 200; ++it) {
+        double mid = 0.5 * (a0 + b0);
+        double fm = g_of(T, x, y, z, mid, hfact);
+        if (fm < 0.0) a0 = mid; else b0 = mid;
+        if (b0 - a0 < 1e-12 * mid) break;
+      }
+      h = 0.5 * (a0 + b0);
+      r = 1;
+    }
+  }
+  const int32_t a = idx[k];
+  hout[a] = h;
+  if (route) route[a] = r;
+}
+
+// Initial guess: hfact * side(leaf cube) / count^(1/3), per sorted position.
+__global__ void h_guess_leaf(int64_t n, const int32_t* __restrict__ owner, const int32_t* __restrict__ lev,
+                             const int64_t* __restrict__ nb, const int64_t* __restrict__ ne, double hfact,
+                             double* h0s) {
+  int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (k >= n) return;
+  int32_t leaf = owner[k];
+  double side = ldexp(1.0, -lev[leaf]);
+  h0s[k] = hfact * side / cbrt((double)(ne[leaf] - nb[leaf]));
+}
+
+__global__ void gather_h0(int64_t n, const int32_t* __restrict__ idx, const double* __restrict__ h0, double* h0s) {
+  int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (k >= n) return;
+  h0s[k] = h0[idx[k]];
+}
+
+}  // namespace
+
+int h_solve_run(map_ctx* ctx, const double* x, const double* y, const double* z, int64_t n, double* h, int32_t* route,
+                const double* h0_override, cudaStream_t s) {
+  MAP_TRY(tree_build(ctx, x, y, z, nullptr, nullptr, n, s));
+  DevTree& T = ctx->tree;
+  double* h0s;
+  MAP_TRY(ensure_t(ctx, ctx->ws_tree[22], n, &h0s));
+  const int tpb = 128;
+  if (h0_override)
+    gather_h0<<<nblk(n, tpb), tpb, 0, s>>>(n, T.idx, h0_override, h0s);
+  else
+    h_guess_leaf<<<nblk(n, tpb), tpb, 0, s>>>(n, T.owner, T.level, T.begin, T.end, ctx->cfg.hfact, h0s);
+  ++ctx->launches;
+  CUDA_TRY(cudaGetLastError());
+  TreeView V{T.xs, T.ys, T.zs, T.begin, T.end, T.first_child, T.nchild, T.bbox_bits};
+  h_newton<<<nblk(n, tpb), tpb, 0, s>>>(n, V, T.idx, h0s, ctx->cfg.hfact, h, route); ++ctx->launches;
+  CUDA_TRY(cudaGetLastError());
+  return MAP_OK;
+}

@@ -1,0 +1,145 @@
+"""GPU parity: the CUDA path (through the C ABI) against the FP64 oracle.
+
+Gates (per cell, relative to the oracle, absolute floor at 1e-12 of the
+largest cell mass): FP64 build 1e-9, mixed build 1e-5; total mass 1e-12 and
+1e-7; pair lists bit-equal; smoothing lengths 1e-9 relative.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+from gpu_helpers import gpu_map, oracle_h, rel_err, sample_cells, lib, dev_particles
+
+pytestmark = pytest.mark.gpu
+
+TOL = {0: (1e-9, 1e-12), 1: (1e-5, 1e-7)}
+
+
+@pytest.fixture(scope="module")
+def uniform4096():
+    """Plain Exact mapping workload: 4096 equal-mass particles uniform in the cube."""
+    p = synth.uniform_particles(4096, synth.BASE_SEED + 1)
+    g = synth.voronoi(p.pos())
+    h, route = oracle_h(p)
+    ref = oracle.map_cells(g, p.x, p.y, p.z, p.m, h)
+    return p, g, h, route, ref
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_uniform4096_all_cells(uniform4096, precision):
+    p, g, h, _, ref = uniform4096
+    out = gpu_map(g, p, h, precision)
+    assert out["status"] == 0
+    # pair lists: bit-equal
+    assert np.array_equal(out["off"], ref["off"])
+    assert np.array_equal(out["idx"], ref["idx"])
+    cell_tol, tot_tol = TOL[precision]
+    e = rel_err(out["mass"], ref["mass"])
+    assert e.max() < cell_tol, (precision, e.max(), np.percentile(e, 99))
+    assert abs(out["total"] - ref["mass"].sum()) < tot_tol * ref["mass"].sum()
+    assert np.max(np.abs(out["vol"] - ref["vol"]) / ref["vol"]) < 1e-12
+    assert np.max(np.abs(out["rho"] / ref["rho"] - 1)) < cell_tol * 1.01 + 1e-12
+    # per-pair integrals: FP64 closed form ~1e-14 per edge term; the mixed build's
+    # FP32 edge terms carry <= 4e-8 each (inner closed form 2.4e-8, middle
+    # Gauss-Legendre 3.5e-8, geometry 1e-7 h), and a pair sums ~50 of them
+    fe = np.abs(out["frac"] - ref["frac"])
+    assert fe.max() < (1e-11 if precision == 0 else 5e-6), fe.max()
+
+
+def test_uniform4096_mass_conservation(uniform4096):
+    """Interior particles: sum_i f_ai = 1 on the GPU too (mixed build)."""
+    p, g, h, _, _ = uniform4096
+    out = gpu_map(g, p, h, 1)
+    tot = np.zeros(p.n)
+    np.add.at(tot, out["idx"], out["frac"])
+    pos = p.pos()
+    interior = np.all((pos >= 2 * h[:, None]) & (pos <= 1 - 2 * h[:, None]), axis=1)
+    assert interior.sum() > 100
+    assert np.max(np.abs(tot[interior] - 1)) < 1e-6
+
+
+def test_solve_h_uniform4096(uniform4096):
+    p, g, h_ref, route_ref, _ = uniform4096
+    L = lib()
+    ctx = L.map_init(L.map_config_default(precision=0))
+    try:
+        x, y, z, m, hh = dev_particles(p)
+        route = __import__("torch").empty(p.n, dtype=__import__("torch").int32, device="cuda")
+        L.solve_h(ctx, L.make_particles(x, y, z, None, hh), route)
+        h = hh.cpu().numpy()
+        r = route.cpu().numpy()
+    finally:
+        L.map_destroy(ctx)
+    assert np.array_equal(r, route_ref)
+    assert np.max(np.abs(h / h_ref - 1)) < 1e-9
+
+
+@pytest.fixture(scope="module")
+def clumpy():
+    """Clumpy-cloud workload at reduced size: 2^16 particles from the log-normal field."""
+    p = synth.lognormal_particles(1 << 16, synth.BASE_SEED + 2)
+    g = synth.voronoi(p.pos())
+    h, route = oracle_h(p)
+    cells = sample_cells(g.ncell, 400, 5)
+    ref = oracle.map_cells(g, p.x, p.y, p.z, p.m, h, cells=cells)
+    return p, g, h, cells, ref
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_clumpy_sampled_cells(clumpy, precision):
+    p, g, h, cells, ref = clumpy
+    out = gpu_map(g, p, h, precision)
+    for k, c in enumerate(cells):
+        a = out["idx"][out["off"][c]:out["off"][c + 1]]
+        b = ref["idx"][ref["off"][k]:ref["off"][k + 1]]
+        assert np.array_equal(a, b), c
+    cell_tol, _ = TOL[precision]
+    e = rel_err(out["mass"][cells], ref["mass"], floor_frac=1e-12)
+    assert e.max() < cell_tol, (e.max(), np.percentile(e, 99))
+
+
+def test_edge_cases_tiny_and_huge_support():
+    """One particle (one cell = the cube); a few particles whose supports cover
+    the whole cube; particles with tiny supports inside their own cells."""
+    rng = np.random.default_rng(3)
+    # one particle: the whole support inside the cube -> M = m
+    p1 = synth.Particles(np.array([0.5]), np.array([0.5]), np.array([0.5]), np.array([2.0]))
+    g1 = synth.voronoi(p1.pos())
+    for prec in (0, 1):
+        out = gpu_map(g1, p1, np.array([0.2]), prec)
+        assert out["n_pairs"] == 1
+        assert abs(out["mass"][0] - 2.0) < 1e-12
+    # ragged: 37 particles, supports larger than the cube
+    p2 = synth.uniform_particles(37, 99)
+    g2 = synth.voronoi(p2.pos())
+    h2 = rng.uniform(0.6, 1.5, 37)
+    ref = oracle.map_cells(g2, p2.x, p2.y, p2.z, p2.m, h2)
+    for prec in (0, 1):
+        out = gpu_map(g2, p2, h2, prec)
+        assert np.array_equal(out["idx"], ref["idx"])
+        assert rel_err(out["mass"], ref["mass"]).max() < TOL[prec][0]
+    # tiny supports: every particle lies entirely inside its own cell
+    p3 = synth.uniform_particles(200, 5)
+    g3 = synth.voronoi(p3.pos())
+    h3 = np.full(200, 1e-5)
+    out = gpu_map(g3, p3, h3, 1)
+    assert np.max(np.abs(out["mass"] - p3.m)) < 1e-12 * p3.m[0] + 1e-16
+
+
+def test_particles_on_face_planes():
+    """Lattice sites with extra particles placed exactly on shared faces: the
+    mapping stays continuous (each such particle splits between its cells)."""
+    n = 6
+    lat = synth.lattice_particles(n)
+    g = synth.voronoi(lat.pos())
+    extra = np.array([[3.0 / n, 2.5 / n, 2.5 / n], [3.0 / n, 3.0 / n, 2.5 / n]])
+    pos = np.concatenate([lat.pos(), extra])
+    m = np.full(len(pos), 1.0 / len(pos))
+    p = synth.Particles(pos[:, 0].copy(), pos[:, 1].copy(), pos[:, 2].copy(), m)
+    h = np.full(len(pos), 1.3 / n)
+    ref = oracle.map_cells(g, p.x, p.y, p.z, p.m, h)
+    for prec in (0, 1):
+        out = gpu_map(g, p, h, prec)
+        assert np.array_equal(out["idx"], ref["idx"])
+        assert rel_err(out["mass"], ref["mass"]).max() < TOL[prec][0]
