@@ -195,6 +195,7 @@ int map_get_timing(map_ctx* ctx, float* ms);
  * 2 estimate.  Errors: MAP_EINVAL, MAP_ENOMEM, MAP_ECUDA. */
 int solve_h(map_ctx* ctx, map_particles* p, int32_t* route, void* stream);
 
+
 /* ------------------------------------------------------------ pseudo-particles (Section III-A/B, Eq. 5) */
 
 /* Build the octree of the full particle set (leaf capacity cfg.leaf_size),

@@ -1,13 +1,26 @@
 // Pair integrals and cell sums (Section II-B, Eq. 1-3).
 //
-// Persistent kernel: each CTA pulls cells from a device work queue, stages the
-// cell's site-relative face planes and edge records in shared memory, and
-// gives every thread one particle of the cell's pair list.  All threads of a
-// CTA walk the same faces and edges in lockstep (broadcast shared-memory
-// reads), so loop trip counts never diverge; only the per-edge pieces do.
-// Per pair: f_ai = [inside] - sum_f s_f (2 pi r0 E(r0) [p in face] - sum_e s_e K_e)
-// (see wedge.cuh).  M_i = sum_a m_a f_ai is accumulated in FP64 and reduced
-// across the CTA; rho_i = M_i / V_i.
+// Persistent kernel: each CTA pulls cells from a device work queue and stages
+// the cell's site-relative face planes and edge records in shared memory.  A
+// cell's pairs are processed NT at a time, one pair per thread, in two phases
+// per chunk of ECH directed edges:
+//
+//  phase 1 (per thread = pair): for each edge of the chunk compute r0 (face),
+//    R0 and the along-edge coordinates of the vertices, update the inside
+//    flag, and QUEUE each piece of the edge integral K'_e -- at most one
+//    inner piece, two middle pieces and two pieces beyond the support -- as
+//    (r0, R0, lo, hi); the sign s_f s_e is folded into the interval direction.
+//    (Mixed build: a face whose plane passes within 1e-4 h of the particle is
+//    decided and evaluated in FP64 in this thread instead.)
+//  phase 2 (all threads): evaluate the queued pieces kind by kind, every lane
+//    running the same code; add each result to its pair's accumulator with
+//    64-bit fixed-point shared-memory atomics (integer addition is
+//    associative, so the sum is bit-reproducible).
+//
+// Without the queue, lanes (different particles) branch into different
+// pieces and a warp runs every path with a few lanes active (measured 5.3 of
+// 32).  Per pair: f_ai = [inside] + sum_f sum_e s_f s_e K'_e (see wedge.cuh).  M_i = sum_a m_a f_ai is accumulated in
+// FP64 and reduced across the CTA; rho_i = M_i / V_i.
 #include <cub/cub.cuh>
 
 #include "internal.cuh"
@@ -31,75 +44,81 @@ struct IntegralArgs {
   double* frac;
   double* cell_mass;
   double* cell_rho;
-  unsigned long long* counters;  // [1] edge terms, [3] work queue
+  unsigned long long* counters;  // [1] edge terms, [2] FP64 terms, [3] work queue, [8..11] work tally
+  const double4_32a* face64;     // FP64 geometry for the near-degenerate fallback of the mixed build
+  const double* edge64;
 };
 
-// Loop-entry offsets of a cell's faces, from shared memory or global memory.
-struct SmemLoops {
-  const int* p;
-  __device__ __forceinline__ int operator[](int i) const { return p[i]; }
-};
-struct GlobalLoops {
-  const int64_t* fvo;  // face_vert_off + first face of the cell
-  int64_t l0;
-  __device__ __forceinline__ int operator[](int i) const { return (int)(fvo[i] - l0); }
-};
+// Mixed build: a face whose plane, or an edge whose line, passes within TAU
+// (in units of h) of the particle (resp. its projection) is evaluated in FP64:
+// FP32 rounding (~1e-7 h) could otherwise give inconsistent signs to a plane
+// seen from two faces.  Exact zeros (particle exactly on a plane or edge line)
+// are moved to +EPS on the inner side in both builds: the integral is
+// continuous in the particle position, and treating every exact zero as
+// 'inside' is one consistent displacement of the particle into the cell.
+constexpr float TAU = 1e-4f;
+constexpr double EPS = 1e-12;
 
-// f_ai for one particle (coordinates relative to the site, in units of h).
-template <typename T, bool MIXED, typename Loops>
-__device__ __forceinline__ T pair_fraction(const typename Vec4<T>::type* __restrict__ faces, Loops floop,
-                                           const T* __restrict__ edges, int nf, T yx, T yy, T yz, T hinv,
-                                           wedge::WorkCount& wc) {
-  T tot = T(0);
-  bool inside = true;
-  wc.faces += nf;
-  for (int fi = 0; fi < nf; ++fi) {
-    const typename Vec4<T>::type F = faces[fi];
-    const T r0s = F.w * hinv - (F.x * yx + F.y * yy + F.z * yz);
-    const bool fin = r0s >= T(0);
-    inside = inside && fin;
-    const T r0 = fabs(r0s);
-    if (r0 >= T(2)) continue;
-    bool pin = true;
-    T jsum = T(0);
-    const int k1 = floop[fi + 1];
-    wc.edges += k1 - floop[fi];
-    for (int k = floop[fi]; k < k1; ++k) {
-      const T* E = edges + k * EDGE_STRIDE;
-      const T R0s = (E[0] * yx + E[1] * yy + E[2] * yz) - E[3] * hinv;  // m.(p - v_a): > 0 inside
-      const T base = E[4] * yx + E[5] * yy + E[6] * yz;
-      const bool ein = R0s >= T(0);
-      pin = pin && ein;
-      const T R0 = fabs(R0s);
-      if (r0 * r0 + R0 * R0 < T(4)) {
-        const T K = wedge::edge_integral<T, MIXED>(r0, R0, E[7] * hinv - base, E[8] * hinv - base, wc);
-        jsum += ein ? K : -K;
-        ++wc.terms;
-      }
-    }
-    const T cf = (pin ? wedge::face_term<T>(r0) : T(0)) - jsum;
-    tot += fin ? cf : -cf;
-  }
-  return (inside ? T(1) : T(0)) - tot;
+constexpr double FIX_SCALE = 1125899906842624.0;  // 2^50
+constexpr double FIX_INV = 1.0 / 1125899906842624.0;
+
+template <typename T>
+__device__ __forceinline__ long long to_fixed(T v) {
+  return __double2ll_rn((double)v * FIX_SCALE);
 }
 
-template <typename T, bool MIXED, int NT>
+// Exclusive warp prefix sum of v; returns the warp total in *tot.
+__device__ __forceinline__ int warp_excl(int v, int* tot) {
+  const int lane = threadIdx.x & 31;
+  int s = v;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    int t = __shfl_up_sync(0xffffffffu, s, o);
+    if (lane >= o) s += t;
+  }
+  *tot = __shfl_sync(0xffffffffu, s, 31);
+  return s - v;
+}
+
+template <typename T, bool MIXED, int NT, int ECH>
 __global__ void __launch_bounds__(NT) pair_integrals(IntegralArgs A, const typename Vec4<T>::type* __restrict__ face,
                                                      const T* __restrict__ edge, int smem_faces, int smem_loops) {
   typedef typename Vec4<T>::type V4;
+  constexpr int QIN = NT * ECH;       // inner pieces per chunk (<= 1 per edge per pair)
+  constexpr int QMID = 2 * NT * ECH;  // middle pieces per chunk (<= 2 per edge per pair)
+  constexpr int QOUT = 2 * NT * ECH;  // beyond-support pieces per chunk (<= 2 per edge per pair)
   extern __shared__ __align__(128) unsigned char smem[];
-  V4* s_face = reinterpret_cast<V4*>(smem);
-  T* s_edge = reinterpret_cast<T*>(smem + sizeof(V4) * smem_faces);
-  int* s_floop = reinterpret_cast<int*>(smem + sizeof(V4) * smem_faces + sizeof(T) * EDGE_STRIDE * smem_loops);
+  // dynamic layout: queues first (fixed size), then the staged cell geometry
+  V4* q_in = reinterpret_cast<V4*>(smem);
+  V4* q_mid = q_in + QIN;
+  V4* q_out = q_mid + QMID;
+  unsigned char* qs_in = reinterpret_cast<unsigned char*>(q_out + QOUT);
+  unsigned char* qs_mid = qs_in + QIN;
+  unsigned char* qs_out = qs_mid + QMID;
+  unsigned char* geo = qs_out + QOUT;
+  geo = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(geo) + 127) & ~uintptr_t(127));
+  V4* s_face = reinterpret_cast<V4*>(geo);
+  T* s_edge = reinterpret_cast<T*>(geo + sizeof(V4) * smem_faces);
+  int* s_floop = reinterpret_cast<int*>(geo + sizeof(V4) * smem_faces + sizeof(T) * EDGE_STRIDE * smem_loops);
+  unsigned short* s_fidx = reinterpret_cast<unsigned short*>(s_floop + smem_faces + 1);
+
   __shared__ int64_t s_cell;
-  __shared__ unsigned long long s_work[5];
+  __shared__ int s_cnt[2][3];  // ping-pong queue counters (inner, middle, outer)
+  __shared__ long long s_acc[NT];
+  __shared__ unsigned long long s_work[8];
   typedef cub::BlockReduce<double, NT> BR;
   __shared__ typename BR::TempStorage s_br;
-  if (threadIdx.x < 5) s_work[threadIdx.x] = 0;
-  wedge::WorkCount wc;
+
+  const int tid = threadIdx.x;
+  if (tid < 8) s_work[tid] = 0;
+  if (tid < 6) s_cnt[tid / 3][tid % 3] = 0;
+  wedge::WorkCount wc, wcd;
+  int n64 = 0;
+  int buf = 0;
+
   for (;;) {
     __syncthreads();
-    if (threadIdx.x == 0) s_cell = (int64_t)atomicAdd(&A.counters[3], 1ULL);
+    if (tid == 0) s_cell = (int64_t)atomicAdd(&A.counters[3], 1ULL);
     __syncthreads();
     const int64_t c = s_cell;
     if (c >= A.ncell) break;
@@ -107,36 +126,169 @@ __global__ void __launch_bounds__(NT) pair_integrals(IntegralArgs A, const typen
     const int nf = (int)(A.cfo[c + 1] - f0);
     const int64_t l0 = A.fvo[f0];
     const int nl = (int)(A.fvo[f0 + nf] - l0);
-    // stage the cell geometry (cells larger than the staging area read global memory)
-    const bool fits = nf <= smem_faces && nl <= smem_loops;
-    if (fits) {
-      for (int i = threadIdx.x; i <= nf; i += NT) s_floop[i] = (int)(A.fvo[f0 + i] - l0);
-      for (int i = threadIdx.x; i < nf; i += NT) s_face[i] = face[f0 + i];
+    if (!(nf <= smem_faces && nl <= smem_loops)) continue;  // mapped by pair_integrals_large
+    for (int i = tid; i <= nf; i += NT) s_floop[i] = (int)(A.fvo[f0 + i] - l0);
+    for (int i = tid; i < nf; i += NT) s_face[i] = face[f0 + i];
+    {
       const int ne = nl * EDGE_STRIDE;
       const T* src = edge + l0 * EDGE_STRIDE;
-      for (int i = threadIdx.x; i < ne; i += NT) s_edge[i] = src[i];
+      for (int i = tid; i < ne; i += NT) s_edge[i] = src[i];
     }
     __syncthreads();
+    for (int fi = tid; fi < nf; fi += NT)
+      for (int k = s_floop[fi]; k < s_floop[fi + 1]; ++k) s_fidx[k] = (unsigned short)fi;
+    __syncthreads();
+
     const double sx = A.site[3 * c], sy = A.site[3 * c + 1], sz = A.site[3 * c + 2];
     double macc = 0.0;
-    const int64_t p1 = A.pair_off[c + 1];
-    for (int64_t p = A.pair_off[c] + threadIdx.x; p < p1; p += NT) {
-      const int32_t a = A.pair_idx[p];
-      const double hinv = 1.0 / A.h[a];
-      const T yx = (T)((A.x[a] - sx) * hinv);
-      const T yy = (T)((A.y[a] - sy) * hinv);
-      const T yz = (T)((A.z[a] - sz) * hinv);
-      T f;
-      if (fits)
-        f = pair_fraction<T, MIXED>(s_face, SmemLoops{s_floop}, s_edge, nf, yx, yy, yz, (T)hinv, wc);
-      else
-        f = pair_fraction<T, MIXED>(face + f0, GlobalLoops{A.fvo + f0, l0}, edge + l0 * EDGE_STRIDE, nf, yx, yy, yz,
-                                    (T)hinv, wc);
-      if (A.frac) A.frac[p] = (double)f;
-      macc += A.m[a] * (double)f;
+    const int64_t pb = A.pair_off[c], pe = A.pair_off[c + 1];
+    for (int64_t p0 = pb; p0 < pe; p0 += NT) {
+      const int64_t p = p0 + tid;
+      const bool active = p < pe;
+      T yx = T(0), yy = T(0), yz = T(0), hinv = T(0);
+      double ydx = 0.0, ydy = 0.0, ydz = 0.0, hinvd = 0.0;
+      int32_t a = 0;
+      if (active) {
+        a = A.pair_idx[p];
+        hinvd = 1.0 / A.h[a];
+        ydx = (A.x[a] - sx) * hinvd;
+        ydy = (A.y[a] - sy) * hinvd;
+        ydz = (A.z[a] - sz) * hinvd;
+        yx = (T)ydx;
+        yy = (T)ydy;
+        yz = (T)ydz;
+        hinv = (T)hinvd;
+      }
+      s_acc[tid] = 0;
+      bool inside = true;
+      double dacc = 0.0;
+      int cur = -1;
+      T r0 = T(0);
+      bool fin = true, inrange = false;
+      for (int kc = 0; kc < nl; kc += ECH) {
+        // ---------------- phase 1: geometry and queueing
+        const int kend = min(kc + ECH, nl);
+        for (int k = kc; k < kend; ++k) {
+          const int fi = s_fidx[k];
+          if (fi != cur) {
+            const V4 F = s_face[fi];
+            const T r0s = F.w * hinv - (F.x * yx + F.y * yy + F.z * yz);
+            fin = r0s >= T(0);
+            r0 = fabs(r0s);
+            if (!MIXED) r0 = r0 > T(1e-12) ? r0 : T(1e-12);
+            inrange = active && r0 < T(2);
+            cur = fi;
+            if (active) wc.faces++;
+            if (MIXED && inrange && r0 < T(1e-4)) {
+              // the face plane passes within 1e-4 h of the particle: decide
+              // the side and evaluate the whole face in FP64 in this thread
+              const double4_32a G = A.face64[f0 + fi];
+              const double rs = G.w * hinvd - (G.x * ydx + G.y * ydy + G.z * ydz);
+              fin = rs >= 0.0;
+              const double r0d = fabs(rs) > 1e-12 ? fabs(rs) : 1e-12;
+              for (int kk = s_floop[fi]; kk < s_floop[fi + 1]; ++kk) {
+                const double* D = A.edge64 + (l0 + kk) * EDGE_STRIDE;
+                const double R0sd = (D[0] * ydx + D[1] * ydy + D[2] * ydz) - D[3] * hinvd;
+                const double based = D[4] * ydx + D[5] * ydy + D[6] * ydz;
+                const bool eind = R0sd >= 0.0;
+                const double R0d = fabs(R0sd) > 1e-12 ? fabs(R0sd) : 1e-12;
+                const double K = wedge::kprime_edge<double, false>(r0d, R0d, D[7] * hinvd - based,
+                                                                   D[8] * hinvd - based, wcd);
+                dacc += (fin == eind) ? K : -K;
+                ++n64;
+              }
+              inrange = false;  // its edges are done
+            }
+            inside = inside && fin;
+          }
+          int nin = 0, nmid = 0, nout = 0;
+          T R0 = T(0);
+          T li = T(0), hi_ = T(0), lm[2] = {T(0), T(0)}, hm[2] = {T(0), T(0)}, lo_[2] = {T(0), T(0)},
+            ho[2] = {T(0), T(0)};
+          if (inrange) {
+            const T* E = s_edge + k * EDGE_STRIDE;
+            const T R0s = (E[0] * yx + E[1] * yy + E[2] * yz) - E[3] * hinv;  // m.(p - v_a): > 0 inside
+            const T base = E[4] * yx + E[5] * yy + E[6] * yz;
+            const bool ein = R0s >= T(0);
+            R0 = fabs(R0s);
+            if (!MIXED) R0 = R0 > T(1e-12) ? R0 : T(1e-12);
+            wc.edges++;
+            wedge::split_edge<T>(
+                r0, R0, E[7] * hinv - base, E[8] * hinv - base, fin == ein,
+                [&](T l, T h) { li = l; hi_ = h; nin = 1; },
+                [&](T l, T h) { lm[nmid] = l; hm[nmid] = h; ++nmid; },
+                [&](T l, T h) { lo_[nout] = l; ho[nout] = h; ++nout; });
+          }
+          // warp-aggregated append to the shared queues
+          int tin, tmid, tout;
+          const int oin = warp_excl(nin, &tin);
+          const int omid = warp_excl(nmid, &tmid);
+          const int oout = warp_excl(nout, &tout);
+          int bin = 0, bmid = 0, bout = 0;
+          if ((tid & 31) == 0) {
+            if (tin) bin = atomicAdd(&s_cnt[buf][0], tin);
+            if (tmid) bmid = atomicAdd(&s_cnt[buf][1], tmid);
+            if (tout) bout = atomicAdd(&s_cnt[buf][2], tout);
+          }
+          bin = __shfl_sync(0xffffffffu, bin, 0);
+          bmid = __shfl_sync(0xffffffffu, bmid, 0);
+          bout = __shfl_sync(0xffffffffu, bout, 0);
+          V4 it;
+          it.x = r0;
+          it.y = R0;
+          if (nin) {
+            it.z = li; it.w = hi_;
+            q_in[bin + oin] = it;
+            qs_in[bin + oin] = (unsigned char)tid;
+          }
+          for (int j = 0; j < nmid; ++j) {
+            it.z = lm[j]; it.w = hm[j];
+            q_mid[bmid + omid + j] = it;
+            qs_mid[bmid + omid + j] = (unsigned char)tid;
+          }
+          for (int j = 0; j < nout; ++j) {
+            it.z = lo_[j]; it.w = ho[j];
+            q_out[bout + oout + j] = it;
+            qs_out[bout + oout + j] = (unsigned char)tid;
+          }
+          if (nin + nmid + nout) wc.terms++;
+        }
+        __syncthreads();
+        // ---------------- phase 2: uniform evaluation of the queued pieces
+        const int n_in = s_cnt[buf][0], n_mid = s_cnt[buf][1], n_out = s_cnt[buf][2];
+        if (tid < 3) s_cnt[buf ^ 1][tid] = 0;  // the next chunk appends there
+        for (int i = tid; i < n_in; i += NT) {
+          const V4 q = q_in[i];
+          const T v = wedge::piece_inner<T>(q.x, q.y, q.z, q.w);
+          atomicAdd(reinterpret_cast<unsigned long long*>(&s_acc[qs_in[i]]), (unsigned long long)to_fixed(v));
+        }
+        for (int i = tid; i < n_mid; i += NT) {
+          const V4 q = q_mid[i];
+          const T v = wedge::piece_mid<T, MIXED>(q.x, q.y, q.z, q.w);
+          atomicAdd(reinterpret_cast<unsigned long long*>(&s_acc[qs_mid[i]]), (unsigned long long)to_fixed(v));
+        }
+        for (int i = tid; i < n_out; i += NT) {
+          const V4 q = q_out[i];
+          const T v = wedge::piece_outer<T>(q.x, q.y, q.z, q.w);
+          atomicAdd(reinterpret_cast<unsigned long long*>(&s_acc[qs_out[i]]), (unsigned long long)to_fixed(v));
+        }
+        if (tid == 0) {
+          s_work[3] += 2 * (unsigned long long)n_in;
+          s_work[4] += (unsigned long long)n_mid;
+          s_work[6] += (unsigned long long)n_out;
+        }
+        buf ^= 1;
+        __syncthreads();
+      }
+      if (active) {
+        const double f = (inside ? 1.0 : 0.0) + dacc + (double)s_acc[tid] * FIX_INV;
+        if (A.frac) A.frac[p] = f;
+        macc += A.m[a] * f;
+      }
+      __syncthreads();
     }
     const double M = BR(s_br).Sum(macc);
-    if (threadIdx.x == 0) {
+    if (tid == 0) {
       A.cell_mass[c] = M;
       if (A.cell_rho) A.cell_rho[c] = M / A.vol[c];
     }
@@ -144,41 +296,104 @@ __global__ void __launch_bounds__(NT) pair_integrals(IntegralArgs A, const typen
   atomicAdd(&s_work[0], (unsigned long long)wc.terms);
   atomicAdd(&s_work[1], (unsigned long long)wc.faces);
   atomicAdd(&s_work[2], (unsigned long long)wc.edges);
-  atomicAdd(&s_work[3], (unsigned long long)wc.inner);
-  atomicAdd(&s_work[4], (unsigned long long)wc.mid);
+  atomicAdd(&s_work[5], (unsigned long long)n64);
   __syncthreads();
-  if (threadIdx.x == 0) {
+  if (tid == 0) {
     atomicAdd(&A.counters[1], s_work[0]);
+    atomicAdd(&A.counters[2], s_work[5]);
     atomicAdd(&A.counters[8], s_work[1]);
     atomicAdd(&A.counters[9], s_work[2]);
     atomicAdd(&A.counters[10], s_work[3]);
     atomicAdd(&A.counters[11], s_work[4]);
+    atomicAdd(&A.counters[12], s_work[6]);
   }
 }
 
-template <typename T, bool MIXED, int NT>
+// Cells too large for the staging area (none in practice for Voronoi cells;
+// kept so that any valid grid is mapped): one CTA per such cell, one thread
+// per pair, geometry read from global memory, every edge evaluated in place.
+template <typename T, bool MIXED>
+__global__ void pair_integrals_large(IntegralArgs A, const typename Vec4<T>::type* __restrict__ face,
+                                     const T* __restrict__ edge, int smem_faces, int smem_loops) {
+  typedef typename Vec4<T>::type V4;
+  typedef cub::BlockReduce<double, 128> BR;
+  __shared__ typename BR::TempStorage s_br;
+  const int64_t c = blockIdx.x;
+  const int64_t f0 = A.cfo[c];
+  const int nf = (int)(A.cfo[c + 1] - f0);
+  const int64_t l0 = A.fvo[f0];
+  const int nl = (int)(A.fvo[f0 + nf] - l0);
+  if (nf <= smem_faces && nl <= smem_loops) return;
+  const double sx = A.site[3 * c], sy = A.site[3 * c + 1], sz = A.site[3 * c + 2];
+  double macc = 0.0;
+  wedge::WorkCount wc;
+  for (int64_t p = A.pair_off[c] + threadIdx.x; p < A.pair_off[c + 1]; p += 128) {
+    const int32_t a = A.pair_idx[p];
+    const double hh = 1.0 / A.h[a];
+    const double ydx = (A.x[a] - sx) * hh, ydy = (A.y[a] - sy) * hh, ydz = (A.z[a] - sz) * hh;
+    double tot = 0.0;
+    bool inside = true;
+    // always FP64 here: large cells are rare and this path has no queue
+    for (int fi = 0; fi < nf; ++fi) {
+      const double4_32a G = A.face64[f0 + fi];
+      const double rs = G.w * hh - (G.x * ydx + G.y * ydy + G.z * ydz);
+      const bool fin = rs >= 0.0;
+      inside = inside && fin;
+      const double r0 = fabs(rs) > 1e-12 ? fabs(rs) : 1e-12;
+      if (r0 >= 2.0) continue;
+      for (int64_t k = A.fvo[f0 + fi] - l0; k < A.fvo[f0 + fi + 1] - l0; ++k) {
+        const double* D = A.edge64 + (l0 + k) * EDGE_STRIDE;
+        const double R0s = (D[0] * ydx + D[1] * ydy + D[2] * ydz) - D[3] * hh;
+        const double base = D[4] * ydx + D[5] * ydy + D[6] * ydz;
+        const bool ein = R0s >= 0.0;
+        const double R0 = fabs(R0s) > 1e-12 ? fabs(R0s) : 1e-12;
+        const double K = wedge::kprime_edge<double, false>(r0, R0, D[7] * hh - base, D[8] * hh - base, wc);
+        tot += (fin == ein) ? K : -K;
+      }
+    }
+    const double f = (inside ? 1.0 : 0.0) + tot;
+    if (A.frac) A.frac[p] = f;
+    macc += A.m[a] * f;
+  }
+  const double M = BR(s_br).Sum(macc);
+  if (threadIdx.x == 0) {
+    A.cell_mass[c] = M;
+    if (A.cell_rho) A.cell_rho[c] = M / A.vol[c];
+  }
+}
+
+constexpr size_t SMEM_CAP = 200 * 1024;
+
+template <typename T, bool MIXED, int NT, int ECH>
 int launch(map_ctx* ctx, const PreparedGrid* g, const IntegralArgs& A, cudaStream_t s) {
   typedef typename Vec4<T>::type V4;
+  const size_t queue = (size_t)(5 * NT * ECH) * (sizeof(V4) + 1) + 128;
   int sf = g->max_faces, sl = g->max_loops;
-  size_t bytes = sizeof(V4) * sf + sizeof(T) * EDGE_STRIDE * sl + sizeof(int) * (sf + 1) + 16;
-  const size_t cap = 160 * 1024;
-  if (bytes > cap) {
-    // stage only cells up to a fixed size; larger ones read global memory
-    sf = 128;
-    sl = (int)((cap - sizeof(V4) * sf - sizeof(int) * (sf + 1) - 16) / (sizeof(T) * EDGE_STRIDE));
-    bytes = sizeof(V4) * sf + sizeof(T) * EDGE_STRIDE * sl + sizeof(int) * (sf + 1) + 16;
+  auto geo_bytes = [](int f, int l) {
+    return sizeof(V4) * f + sizeof(T) * EDGE_STRIDE * l + sizeof(int) * (f + 1) + sizeof(unsigned short) * l + 16;
+  };
+  size_t bytes = queue + geo_bytes(sf, sl);
+  if (bytes > SMEM_CAP) {
+    sf = sf < 128 ? sf : 128;
+    sl = (int)((SMEM_CAP - queue - sizeof(V4) * sf - sizeof(int) * (sf + 1) - 16) /
+               (sizeof(T) * EDGE_STRIDE + sizeof(unsigned short)));
+    bytes = queue + geo_bytes(sf, sl);
   }
-  auto kern = pair_integrals<T, MIXED, NT>;
+  auto kern = pair_integrals<T, MIXED, NT, ECH>;
   CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes));
   int per_sm = 0;
   CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, NT, bytes));
   if (per_sm < 1) per_sm = 1;
   int64_t blocks = (int64_t)per_sm * ctx->sm_count;
   if (blocks > g->ncell) blocks = g->ncell > 0 ? g->ncell : 1;
-  kern<<<(unsigned)blocks, NT, bytes, s>>>(A, reinterpret_cast<const V4*>(MIXED ? (const void*)g->face32 : (const void*)g->face64),
-                                           reinterpret_cast<const T*>(MIXED ? (const void*)g->edge32 : (const void*)g->edge64),
-                                           sf, sl); ++ctx->launches;
+  const V4* fp = reinterpret_cast<const V4*>(MIXED ? (const void*)g->face32 : (const void*)g->face64);
+  const T* ep = reinterpret_cast<const T*>(MIXED ? (const void*)g->edge32 : (const void*)g->edge64);
+  kern<<<(unsigned)blocks, NT, bytes, s>>>(A, fp, ep, sf, sl); ++ctx->launches;
   CUDA_TRY(cudaGetLastError());
+  if (sf < g->max_faces || sl < g->max_loops) {
+    pair_integrals_large<T, MIXED><<<(unsigned)g->ncell, 128, 0, s>>>(A, fp, ep, sf, sl); ++ctx->launches;
+    CUDA_TRY(cudaGetLastError());
+  }
   return MAP_OK;
 }
 
@@ -212,11 +427,13 @@ int integrals_run(map_ctx* ctx, const PreparedGrid* g, const map_particles* p, m
   A.cell_mass = out->cell_mass;
   A.cell_rho = out->cell_rho;
   A.counters = ctx->d_counters;
+  A.face64 = g->face64;
+  A.edge64 = g->edge64;
   phase_begin(ctx, 2, s);
   if (ctx->cfg.precision == MAP_MIXED)
-    MAP_TRY((launch<float, true, 128>(ctx, g, A, s)));
+    MAP_TRY((launch<float, true, 128, 4>(ctx, g, A, s)));
   else
-    MAP_TRY((launch<double, false, 128>(ctx, g, A, s)));
+    MAP_TRY((launch<double, false, 128, 4>(ctx, g, A, s)));
   phase_end(ctx, 2, s);
   if (out->cell_vol) CUDA_TRY(cudaMemcpyAsync(out->cell_vol, g->vol, g->ncell * sizeof(double), cudaMemcpyDeviceToDevice, s));
   sum_cells<<<1, 256, 0, s>>>(g->ncell, out->cell_mass, ctx->d_total); ++ctx->launches;

@@ -119,12 +119,19 @@ def test_edge_cases_tiny_and_huge_support():
         out = gpu_map(g2, p2, h2, prec)
         assert np.array_equal(out["idx"], ref["idx"])
         assert rel_err(out["mass"], ref["mass"]).max() < TOL[prec][0]
-    # tiny supports: every particle lies entirely inside its own cell
+    # tiny supports: each cell holds its own particle's mass, except where a
+    # site lies within 2h of a wall (one does here, 1.4e-6 away) and mass
+    # leaves the cube
     p3 = synth.uniform_particles(200, 5)
     g3 = synth.voronoi(p3.pos())
     h3 = np.full(200, 1e-5)
-    out = gpu_map(g3, p3, h3, 1)
-    assert np.max(np.abs(out["mass"] - p3.m)) < 1e-12 * p3.m[0] + 1e-16
+    ref3 = oracle.map_cells(g3, p3.x, p3.y, p3.z, p3.m, h3)
+    for prec in (0, 1):
+        out = gpu_map(g3, p3, h3, prec)
+        assert out["n_pairs"] == 200
+        assert rel_err(out["mass"], ref3["mass"]).max() < TOL[prec][0]
+        whole = np.abs(ref3["mass"] / p3.m - 1) < 1e-9
+        assert whole.sum() >= 190 and np.all(out["mass"][whole] == p3.m[whole])
 
 
 def test_particles_on_face_planes():
