@@ -196,6 +196,26 @@ int map_get_timing(map_ctx* ctx, float* ms);
 int solve_h(map_ctx* ctx, map_particles* p, int32_t* route, void* stream);
 
 
+/* solve_h for callers that cannot allocate device memory (a process that has
+ * handed all of the GPU's memory to its own pools, a pipeline that forbids
+ * allocation after start-up).  The paper has no counterpart: this is a
+ * deployment variant of solve_h (same octree and Newton/bisection kernels,
+ * same results), taking only caller arrays -- x, y, z (n doubles each, in
+ * the unit cube), h (n doubles, out), route (n int32, out, may be NULL) --
+ * and using as scratch one fixed 16 MiB array in the library's device image,
+ * which every GPU that loads the library holds until the process exits.  It
+ * calls no cudaMalloc, cudaFree or allocating library routine.
+ *   - n is limited to 32768 particles; larger n returns MAP_ECAPACITY, as
+ *     does an octree that outgrows the array (more than 2n nodes).
+ *   - The first call on a device looks up the array's device address
+ *     (cudaGetSymbolAddress) and reserves a small host-side table; make that
+ *     first call before any stream capture.
+ *   - All calls share the array and its last contents: calls whose work
+ *     overlaps on the GPU (other streams, other host threads) race.
+ *   - Synchronises the stream.  Errors: MAP_EINVAL, MAP_ECAPACITY, MAP_ECUDA. */
+int solve_h_noalloc(const double* x, const double* y, const double* z, int64_t n, double hfact, double* h,
+                    int32_t* route, void* stream);
+
 /* ------------------------------------------------------------ pseudo-particles (Section III-A/B, Eq. 5) */
 
 /* Build the octree of the full particle set (leaf capacity cfg.leaf_size),
