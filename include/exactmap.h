@@ -189,7 +189,10 @@ int map_get_timing(map_ctx* ctx, float* ms);
 /* Solve h_a = hfact * n_a(h_a)^(-1/3), n_a(h) = sum_b W(|r_a - r_b|, h)
  * (self term included) for every particle: Newton-Raphson (at most 30
  * iterations, converged at |dh|/h < 1e-10), else bisection on
- * [h0/16, 16 h0] (|dh|/h < 1e-12), else the estimate h0.  The initial guess
+ * [h0/16, 16 h0] (|dh|/h < 1e-12), else the estimate h0.  A MAP_MIXED
+ * context sums the kernel in FP32 (on FP32 hi/lo splits of the coordinates)
+ * and stops Newton at |dh|/h < 1e-6, which gives h to ~1e-7 relative.  The
+ * initial guess
  * h0 is hfact * (side of the particle's octree leaf cube) / (leaf count)^(1/3).
  * Writes p->h; route (optional, n int32) receives 0 Newton, 1 bisection,
  * 2 estimate.  Errors: MAP_EINVAL, MAP_ENOMEM, MAP_ECUDA. */
@@ -200,9 +203,9 @@ int solve_h(map_ctx* ctx, map_particles* p, int32_t* route, void* stream);
  * handed all of the GPU's memory to its own pools, a pipeline that forbids
  * allocation after start-up).  The paper has no counterpart: this is a
  * deployment variant of solve_h (same octree and Newton/bisection kernels,
- * same results), taking only caller arrays -- x, y, z (n doubles each, in
+ * same results as solve_h on an MAP_FP64 context), taking only caller arrays -- x, y, z (n doubles each, in
  * the unit cube), h (n doubles, out), route (n int32, out, may be NULL) --
- * and using as scratch one fixed 16 MiB array in the library's device image,
+ * and using as scratch one fixed 24 MiB array in the library's device image,
  * which every GPU that loads the library holds until the process exits.  It
  * calls no cudaMalloc, cudaFree or allocating library routine.
  *   - n is limited to 32768 particles; larger n returns MAP_ECAPACITY, as

@@ -1,9 +1,10 @@
 // Pair integrals and cell sums (Section II-B, Eq. 1-3).
 //
 // Persistent kernel: each CTA pulls cells from a device work queue and stages
-// the cell's site-relative face planes and edge records in shared memory.  A
-// cell's pairs are processed NT at a time, one pair per thread, in two phases
-// per chunk of ECH directed edges:
+// the cell's site-relative face planes and edge records in shared memory.
+// Each warp then takes the cell's pairs 32 at a time, one pair per lane,
+// independently of the other warps, in three phases per chunk of ECH
+// directed edges:
 //
 //  phase 1 (per thread = pair): for each edge of the chunk compute r0 (face),
 //    R0 and the along-edge coordinates of the vertices, update the inside
@@ -12,10 +13,11 @@
 //    (r0, R0, lo, hi); the sign s_f s_e is folded into the interval direction.
 //    (Mixed build: a face whose plane passes within 1e-4 h of the particle is
 //    decided and evaluated in FP64 in this thread instead.)
-//  phase 2 (all threads): evaluate the queued pieces kind by kind, every lane
-//    running the same code; add each result to its pair's accumulator with
-//    64-bit fixed-point shared-memory atomics (integer addition is
-//    associative, so the sum is bit-reproducible).
+//  phase 2 (whole warp): evaluate the queued pieces kind by kind, every lane
+//    running the same code, each result written to its piece's slot;
+//  phase 3 (per lane): sum the lane's own piece results in a fixed order
+//    (compensated), so that every result is bit-reproducible.
+// Only __syncwarp separates the phases; CTA barriers fall at cell boundaries.
 //
 // Without the queue, lanes (different particles) branch into different
 // pieces and a warp runs every path with a few lanes active (measured 5.3 of
@@ -31,6 +33,9 @@ namespace {
 template <typename T> struct Vec4;
 template <> struct Vec4<float> { typedef float4 type; };
 template <> struct Vec4<double> { typedef double4_32a type; };
+template <typename T> struct Vec2;
+template <> struct Vec2<float> { typedef float2 type; };
+template <> struct Vec2<double> { typedef double2 type; };
 
 struct IntegralArgs {
   int64_t ncell;
@@ -59,14 +64,6 @@ struct IntegralArgs {
 constexpr float TAU = 1e-4f;
 constexpr double EPS = 1e-12;
 
-constexpr double FIX_SCALE = 1125899906842624.0;  // 2^50
-constexpr double FIX_INV = 1.0 / 1125899906842624.0;
-
-template <typename T>
-__device__ __forceinline__ long long to_fixed(T v) {
-  return __double2ll_rn((double)v * FIX_SCALE);
-}
-
 // Exclusive warp prefix sum of v; returns the warp total in *tot.
 __device__ __forceinline__ int warp_excl(int v, int* tot) {
   const int lane = threadIdx.x & 31;
@@ -80,22 +77,27 @@ __device__ __forceinline__ int warp_excl(int v, int* tot) {
   return s - v;
 }
 
+// Per-warp work area in shared memory for one chunk of ECH edges: every lane
+// owns fixed slots -- (r0, R0) per edge, (lo, hi) and a result per piece (5
+// pieces per edge: 1 inner, 2 middle, 2 beyond the support) -- and three
+// compact lists name the occupied slots of each kind.
+template <typename T, int ECH>
+struct WarpArea {
+  typename Vec2<T>::type rr[ECH][32];     // (r0, R0) per (edge, lane)
+  typename Vec2<T>::type lh[ECH * 5][32]; // (lo, hi) per (piece slot, lane)
+  T res[ECH * 5][32];                     // piece results
+  unsigned short q[3][ECH * 64];          // occupied slots: inner, middle, beyond
+};
+
 template <typename T, bool MIXED, int NT, int ECH>
-__global__ void __launch_bounds__(NT) pair_integrals(IntegralArgs A, const typename Vec4<T>::type* __restrict__ face,
+__global__ void __launch_bounds__(NT, 4) pair_integrals(IntegralArgs A, const typename Vec4<T>::type* __restrict__ face,
                                                      const T* __restrict__ edge, int smem_faces, int smem_loops) {
   typedef typename Vec4<T>::type V4;
-  constexpr int QIN = NT * ECH;       // inner pieces per chunk (<= 1 per edge per pair)
-  constexpr int QMID = 2 * NT * ECH;  // middle pieces per chunk (<= 2 per edge per pair)
-  constexpr int QOUT = 2 * NT * ECH;  // beyond-support pieces per chunk (<= 2 per edge per pair)
+  typedef typename Vec2<T>::type V2;
+  constexpr int NW = NT / 32;
   extern __shared__ __align__(128) unsigned char smem[];
-  // dynamic layout: queues first (fixed size), then the staged cell geometry
-  V4* q_in = reinterpret_cast<V4*>(smem);
-  V4* q_mid = q_in + QIN;
-  V4* q_out = q_mid + QMID;
-  unsigned char* qs_in = reinterpret_cast<unsigned char*>(q_out + QOUT);
-  unsigned char* qs_mid = qs_in + QIN;
-  unsigned char* qs_out = qs_mid + QMID;
-  unsigned char* geo = qs_out + QOUT;
+  WarpArea<T, ECH>* areas = reinterpret_cast<WarpArea<T, ECH>*>(smem);
+  unsigned char* geo = smem + sizeof(WarpArea<T, ECH>) * NW;
   geo = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(geo) + 127) & ~uintptr_t(127));
   V4* s_face = reinterpret_cast<V4*>(geo);
   T* s_edge = reinterpret_cast<T*>(geo + sizeof(V4) * smem_faces);
@@ -103,18 +105,16 @@ __global__ void __launch_bounds__(NT) pair_integrals(IntegralArgs A, const typen
   unsigned short* s_fidx = reinterpret_cast<unsigned short*>(s_floop + smem_faces + 1);
 
   __shared__ int64_t s_cell;
-  __shared__ int s_cnt[2][3];  // ping-pong queue counters (inner, middle, outer)
-  __shared__ long long s_acc[NT];
   __shared__ unsigned long long s_work[8];
   typedef cub::BlockReduce<double, NT> BR;
   __shared__ typename BR::TempStorage s_br;
 
-  const int tid = threadIdx.x;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  WarpArea<T, ECH>& W = areas[warp];
   if (tid < 8) s_work[tid] = 0;
-  if (tid < 6) s_cnt[tid / 3][tid % 3] = 0;
   wedge::WorkCount wc, wcd;
   int n64 = 0;
-  int buf = 0;
+  unsigned long long n_in_tot = 0, n_mid_tot = 0, n_out_tot = 0;
 
   for (;;) {
     __syncthreads();
@@ -142,33 +142,42 @@ __global__ void __launch_bounds__(NT) pair_integrals(IntegralArgs A, const typen
     const double sx = A.site[3 * c], sy = A.site[3 * c + 1], sz = A.site[3 * c + 2];
     double macc = 0.0;
     const int64_t pb = A.pair_off[c], pe = A.pair_off[c + 1];
-    for (int64_t p0 = pb; p0 < pe; p0 += NT) {
-      const int64_t p = p0 + tid;
+    // each warp takes 32 pairs at a time; warps proceed independently
+    for (int64_t p0 = pb + warp * 32; p0 < pe; p0 += NT) {
+      const int64_t p = p0 + lane;
       const bool active = p < pe;
       T yx = T(0), yy = T(0), yz = T(0), hinv = T(0);
-      double ydx = 0.0, ydy = 0.0, ydz = 0.0, hinvd = 0.0;
       int32_t a = 0;
       if (active) {
         a = A.pair_idx[p];
-        hinvd = 1.0 / A.h[a];
-        ydx = (A.x[a] - sx) * hinvd;
-        ydy = (A.y[a] - sy) * hinvd;
-        ydz = (A.z[a] - sz) * hinvd;
-        yx = (T)ydx;
-        yy = (T)ydy;
-        yz = (T)ydz;
-        hinv = (T)hinvd;
+        const double hh = A.h[a];
+        if (MIXED) {
+          const float hi = 1.0f / (float)hh;
+          yx = (float)(A.x[a] - sx) * hi;
+          yy = (float)(A.y[a] - sy) * hi;
+          yz = (float)(A.z[a] - sz) * hi;
+          hinv = hi;
+        } else {
+          const double hi = 1.0 / hh;
+          yx = (A.x[a] - sx) * hi;
+          yy = (A.y[a] - sy) * hi;
+          yz = (A.z[a] - sz) * hi;
+          hinv = hi;
+        }
       }
-      s_acc[tid] = 0;
       bool inside = true;
       double dacc = 0.0;
+      T fsum = T(0), fcomp = T(0);  // compensated sum of this pair's pieces
       int cur = -1;
       T r0 = T(0);
       bool fin = true, inrange = false;
       for (int kc = 0; kc < nl; kc += ECH) {
-        // ---------------- phase 1: geometry and queueing
+        // ---------------- phase 1: geometry, fixed slots, compact lists
         const int kend = min(kc + ECH, nl);
+        unsigned long long mask = 0;  // 5 bits per edge of the chunk
+        int cnt_in = 0, cnt_mid = 0, cnt_out = 0;
         for (int k = kc; k < kend; ++k) {
+          const int kl = k - kc;
           const int fi = s_fidx[k];
           if (fi != cur) {
             const V4 F = s_face[fi];
@@ -182,18 +191,19 @@ __global__ void __launch_bounds__(NT) pair_integrals(IntegralArgs A, const typen
             if (MIXED && inrange && r0 < T(1e-4)) {
               // the face plane passes within 1e-4 h of the particle: decide
               // the side and evaluate the whole face in FP64 in this thread
+              const double hh = 1.0 / A.h[a];
+              const double ydx = (A.x[a] - sx) * hh, ydy = (A.y[a] - sy) * hh, ydz = (A.z[a] - sz) * hh;
               const double4_32a G = A.face64[f0 + fi];
-              const double rs = G.w * hinvd - (G.x * ydx + G.y * ydy + G.z * ydz);
+              const double rs = G.w * hh - (G.x * ydx + G.y * ydy + G.z * ydz);
               fin = rs >= 0.0;
               const double r0d = fabs(rs) > 1e-12 ? fabs(rs) : 1e-12;
               for (int kk = s_floop[fi]; kk < s_floop[fi + 1]; ++kk) {
                 const double* D = A.edge64 + (l0 + kk) * EDGE_STRIDE;
-                const double R0sd = (D[0] * ydx + D[1] * ydy + D[2] * ydz) - D[3] * hinvd;
+                const double R0sd = (D[0] * ydx + D[1] * ydy + D[2] * ydz) - D[3] * hh;
                 const double based = D[4] * ydx + D[5] * ydy + D[6] * ydz;
                 const bool eind = R0sd >= 0.0;
                 const double R0d = fabs(R0sd) > 1e-12 ? fabs(R0sd) : 1e-12;
-                const double K = wedge::kprime_edge<double, false>(r0d, R0d, D[7] * hinvd - based,
-                                                                   D[8] * hinvd - based, wcd);
+                const double K = wedge::kprime_edge<double, false>(r0d, R0d, D[7] * hh - based, D[8] * hh - based, wcd);
                 dacc += (fin == eind) ? K : -K;
                 ++n64;
               }
@@ -202,96 +212,87 @@ __global__ void __launch_bounds__(NT) pair_integrals(IntegralArgs A, const typen
             inside = inside && fin;
           }
           int nin = 0, nmid = 0, nout = 0;
-          T R0 = T(0);
-          T li = T(0), hi_ = T(0), lm[2] = {T(0), T(0)}, hm[2] = {T(0), T(0)}, lo_[2] = {T(0), T(0)},
-            ho[2] = {T(0), T(0)};
           if (inrange) {
             const T* E = s_edge + k * EDGE_STRIDE;
             const T R0s = (E[0] * yx + E[1] * yy + E[2] * yz) - E[3] * hinv;  // m.(p - v_a): > 0 inside
             const T base = E[4] * yx + E[5] * yy + E[6] * yz;
             const bool ein = R0s >= T(0);
-            R0 = fabs(R0s);
+            T R0 = fabs(R0s);
             if (!MIXED) R0 = R0 > T(1e-12) ? R0 : T(1e-12);
             wc.edges++;
+            V2 rr;
+            rr.x = r0;
+            rr.y = R0;
+            W.rr[kl][lane] = rr;
+            // slots: 0 inner, 1-2 middle, 3-4 beyond the support
             wedge::split_edge<T>(
                 r0, R0, E[7] * hinv - base, E[8] * hinv - base, fin == ein,
-                [&](T l, T h) { li = l; hi_ = h; nin = 1; },
-                [&](T l, T h) { lm[nmid] = l; hm[nmid] = h; ++nmid; },
-                [&](T l, T h) { lo_[nout] = l; ho[nout] = h; ++nout; });
+                [&](T l, T h) { V2 v; v.x = l; v.y = h; W.lh[kl * 5 + 0][lane] = v; nin = 1; },
+                [&](T l, T h) { V2 v; v.x = l; v.y = h; W.lh[kl * 5 + 1 + nmid][lane] = v; ++nmid; },
+                [&](T l, T h) { V2 v; v.x = l; v.y = h; W.lh[kl * 5 + 3 + nout][lane] = v; ++nout; });
+            mask |= (unsigned long long)((nin) | (((1 << nmid) - 1) << 1) | (((1 << nout) - 1) << 3)) << (5 * kl);
+            if (nin + nmid + nout) wc.terms++;
           }
-          // warp-aggregated append to the shared queues
+          // warp-aggregated append of this edge's slot ids to the compact lists
           int tin, tmid, tout;
           const int oin = warp_excl(nin, &tin);
           const int omid = warp_excl(nmid, &tmid);
           const int oout = warp_excl(nout, &tout);
-          int bin = 0, bmid = 0, bout = 0;
-          if ((tid & 31) == 0) {
-            if (tin) bin = atomicAdd(&s_cnt[buf][0], tin);
-            if (tmid) bmid = atomicAdd(&s_cnt[buf][1], tmid);
-            if (tout) bout = atomicAdd(&s_cnt[buf][2], tout);
-          }
-          bin = __shfl_sync(0xffffffffu, bin, 0);
-          bmid = __shfl_sync(0xffffffffu, bmid, 0);
-          bout = __shfl_sync(0xffffffffu, bout, 0);
-          V4 it;
-          it.x = r0;
-          it.y = R0;
-          if (nin) {
-            it.z = li; it.w = hi_;
-            q_in[bin + oin] = it;
-            qs_in[bin + oin] = (unsigned char)tid;
-          }
-          for (int j = 0; j < nmid; ++j) {
-            it.z = lm[j]; it.w = hm[j];
-            q_mid[bmid + omid + j] = it;
-            qs_mid[bmid + omid + j] = (unsigned char)tid;
-          }
-          for (int j = 0; j < nout; ++j) {
-            it.z = lo_[j]; it.w = ho[j];
-            q_out[bout + oout + j] = it;
-            qs_out[bout + oout + j] = (unsigned char)tid;
-          }
-          if (nin + nmid + nout) wc.terms++;
+          if (nin) W.q[0][cnt_in + oin] = (unsigned short)((kl * 5 + 0) * 32 + lane);
+          for (int j = 0; j < nmid; ++j) W.q[1][cnt_mid + omid + j] = (unsigned short)((kl * 5 + 1 + j) * 32 + lane);
+          for (int j = 0; j < nout; ++j) W.q[2][cnt_out + oout + j] = (unsigned short)((kl * 5 + 3 + j) * 32 + lane);
+          cnt_in += tin;
+          cnt_mid += tmid;
+          cnt_out += tout;
         }
-        __syncthreads();
-        // ---------------- phase 2: uniform evaluation of the queued pieces
-        const int n_in = s_cnt[buf][0], n_mid = s_cnt[buf][1], n_out = s_cnt[buf][2];
-        if (tid < 3) s_cnt[buf ^ 1][tid] = 0;  // the next chunk appends there
-        for (int i = tid; i < n_in; i += NT) {
-          const V4 q = q_in[i];
-          const T v = wedge::piece_inner<T>(q.x, q.y, q.z, q.w);
-          atomicAdd(reinterpret_cast<unsigned long long*>(&s_acc[qs_in[i]]), (unsigned long long)to_fixed(v));
+        __syncwarp();
+        // ---------------- phase 2: uniform evaluation, kind by kind
+        for (int i = lane; i < cnt_in; i += 32) {
+          const int sl = W.q[0][i], ow = sl & 31, ps = sl >> 5;
+          const V2 rr = W.rr[ps / 5][ow], lh = W.lh[ps][ow];
+          W.res[ps][ow] = wedge::piece_inner<T>(rr.x, rr.y, lh.x, lh.y);
         }
-        for (int i = tid; i < n_mid; i += NT) {
-          const V4 q = q_mid[i];
-          const T v = wedge::piece_mid<T, MIXED>(q.x, q.y, q.z, q.w);
-          atomicAdd(reinterpret_cast<unsigned long long*>(&s_acc[qs_mid[i]]), (unsigned long long)to_fixed(v));
+        for (int i = lane; i < cnt_mid; i += 32) {
+          const int sl = W.q[1][i], ow = sl & 31, ps = sl >> 5;
+          const V2 rr = W.rr[ps / 5][ow], lh = W.lh[ps][ow];
+          W.res[ps][ow] = wedge::piece_mid<T, MIXED>(rr.x, rr.y, lh.x, lh.y);
         }
-        for (int i = tid; i < n_out; i += NT) {
-          const V4 q = q_out[i];
-          const T v = wedge::piece_outer<T>(q.x, q.y, q.z, q.w);
-          atomicAdd(reinterpret_cast<unsigned long long*>(&s_acc[qs_out[i]]), (unsigned long long)to_fixed(v));
+        for (int i = lane; i < cnt_out; i += 32) {
+          const int sl = W.q[2][i], ow = sl & 31, ps = sl >> 5;
+          const V2 rr = W.rr[ps / 5][ow], lh = W.lh[ps][ow];
+          W.res[ps][ow] = wedge::piece_outer<T>(rr.x, rr.y, lh.x, lh.y);
         }
-        if (tid == 0) {
-          s_work[3] += 2 * (unsigned long long)n_in;
-          s_work[4] += (unsigned long long)n_mid;
-          s_work[6] += (unsigned long long)n_out;
+        n_in_tot += cnt_in;
+        n_mid_tot += cnt_mid;
+        n_out_tot += cnt_out;
+        __syncwarp();
+        // ---------------- phase 3: each lane sums its own pieces in a fixed order
+        while (mask) {
+          const int b = __ffsll((long long)mask) - 1;
+          mask &= mask - 1;
+          const T v = W.res[b][lane] - fcomp;
+          const T t = fsum + v;
+          fcomp = (t - fsum) - v;
+          fsum = t;
         }
-        buf ^= 1;
-        __syncthreads();
+        __syncwarp();
       }
       if (active) {
-        const double f = (inside ? 1.0 : 0.0) + dacc + (double)s_acc[tid] * FIX_INV;
+        const double f = (inside ? 1.0 : 0.0) + dacc + (double)fsum;
         if (A.frac) A.frac[p] = f;
         macc += A.m[a] * f;
       }
-      __syncthreads();
     }
     const double M = BR(s_br).Sum(macc);
     if (tid == 0) {
       A.cell_mass[c] = M;
       if (A.cell_rho) A.cell_rho[c] = M / A.vol[c];
     }
+  }
+  if (lane == 0) {
+    atomicAdd(&s_work[3], 2 * n_in_tot);
+    atomicAdd(&s_work[4], n_mid_tot);
+    atomicAdd(&s_work[6], n_out_tot);
   }
   atomicAdd(&s_work[0], (unsigned long long)wc.terms);
   atomicAdd(&s_work[1], (unsigned long long)wc.faces);
@@ -367,7 +368,7 @@ constexpr size_t SMEM_CAP = 200 * 1024;
 template <typename T, bool MIXED, int NT, int ECH>
 int launch(map_ctx* ctx, const PreparedGrid* g, const IntegralArgs& A, cudaStream_t s) {
   typedef typename Vec4<T>::type V4;
-  const size_t queue = (size_t)(5 * NT * ECH) * (sizeof(V4) + 1) + 128;
+  const size_t queue = sizeof(WarpArea<T, ECH>) * (NT / 32) + 128;
   int sf = g->max_faces, sl = g->max_loops;
   auto geo_bytes = [](int f, int l) {
     return sizeof(V4) * f + sizeof(T) * EDGE_STRIDE * l + sizeof(int) * (f + 1) + sizeof(unsigned short) * l + 16;
@@ -433,7 +434,7 @@ int integrals_run(map_ctx* ctx, const PreparedGrid* g, const map_particles* p, m
   if (ctx->cfg.precision == MAP_MIXED)
     MAP_TRY((launch<float, true, 128, 4>(ctx, g, A, s)));
   else
-    MAP_TRY((launch<double, false, 128, 4>(ctx, g, A, s)));
+    MAP_TRY((launch<double, false, 128, 2>(ctx, g, A, s)));
   phase_end(ctx, 2, s);
   if (out->cell_vol) CUDA_TRY(cudaMemcpyAsync(out->cell_vol, g->vol, g->ncell * sizeof(double), cudaMemcpyDeviceToDevice, s));
   sum_cells<<<1, 256, 0, s>>>(g->ncell, out->cell_mass, ctx->d_total); ++ctx->launches;

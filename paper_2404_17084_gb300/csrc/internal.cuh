@@ -71,6 +71,7 @@ struct DevTree {
   double* ms = nullptr;
   double* hs = nullptr;
   int32_t* owner = nullptr;           // sorted position -> leaf node
+  float* split = nullptr;             // 6 floats per sorted position: FP32 hi/lo of x, y, z
   // node arrays
   int64_t* label = nullptr;
   int32_t* level = nullptr;
@@ -84,6 +85,7 @@ struct DevTree {
   unsigned long long* size_bits = nullptr;  // FP64 bits of the node size (max distance to COM)
   unsigned long long* hmax_bits = nullptr;  // FP64 bits of max h in the subtree
   unsigned long long* bbox_bits = nullptr;  // 6 per node: FP64 bits of (minx,miny,minz) and (maxx,maxy,maxz)
+  float* box32 = nullptr;             // 8 per node: FP32 box rounded outward, largest h rounded up, pad
 };
 
 struct map_ctx {
@@ -93,7 +95,7 @@ struct map_ctx {
   size_t bytes_in_use = 0;
   std::vector<PreparedGrid*> grids;
   // workspace
-  DevBuf ws_tree[24];
+  DevBuf ws_tree[32];
   DevBuf ws_pairs[8];
   DevBuf ws_misc[8];
   DevBuf cub_tmp;
@@ -139,7 +141,7 @@ inline int ensure_t(map_ctx* ctx, DevBuf& b, size_t count, T** out) {
 // ---------------------------------------------------------------- subsystems
 int grid_prepare(map_ctx* ctx, const map_grid* in, PreparedGrid* g, cudaStream_t s);
 int tree_build(map_ctx* ctx, const double* x, const double* y, const double* z, const double* m,
-               const double* h, int64_t n, cudaStream_t s);
+               const double* h, int64_t n, cudaStream_t s, bool want_size = false);
 int pairs_build(map_ctx* ctx, const PreparedGrid* g, cudaStream_t s);
 int integrals_run(map_ctx* ctx, const PreparedGrid* g, const map_particles* p, map_outputs* out, cudaStream_t s);
 int h_solve_run(map_ctx* ctx, const double* x, const double* y, const double* z, int64_t n, double* h,

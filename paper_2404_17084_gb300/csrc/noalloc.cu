@@ -26,7 +26,7 @@
 namespace {
 
 constexpr int64_t NOALLOC_MAX_N = 32768;
-constexpr size_t NOALLOC_BYTES = 16u << 20;  // 16 MiB, held by every GPU that loads the library
+constexpr size_t NOALLOC_BYTES = 24u << 20;  // 24 MiB, held by every GPU that loads the library
 constexpr int MAX_DEVICES = 64;
 
 // The scratch array.  In host code this name is only a stand-in for the
@@ -61,6 +61,7 @@ int setup_device(int dev) {
   S.base = static_cast<unsigned char*>(p);
   map_ctx& C = S.ctx;
   map_config_default(&C.cfg);
+  C.cfg.precision = MAP_FP64;  // the FP64 Newton tolerance, as solve_h on an FP64 context
   C.cfg.device = dev;
   C.device = dev;
   if (cudaDeviceGetAttribute(&C.sm_count, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return MAP_ECUDA;
@@ -89,6 +90,8 @@ int setup_device(int dev) {
   ok &= take(C.ws_tree[20], 24 * NC + slack);
   ok &= take(C.ws_tree[21], 4 * NC + slack);
   ok &= take(C.ws_tree[22], 8 * N + slack);
+  ok &= take(C.ws_tree[23], 24 * N + slack);  // FP32 hi/lo split coordinates
+  ok &= take(C.ws_tree[24], 32 * NC + slack);  // FP32 node boxes
   DevBuf counters;
   ok &= take(counters, 16 * sizeof(unsigned long long));
   if (!ok) return MAP_ENOMEM;

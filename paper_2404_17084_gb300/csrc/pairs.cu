@@ -19,6 +19,7 @@ struct PairTree {
   const int32_t* nch;
   const unsigned long long* bbox;
   const unsigned long long* hmax;
+  const float* box32;  // outward-rounded FP32 boxes and largest h (8 floats per node)
 };
 
 struct PairGrid {
@@ -75,38 +76,102 @@ __device__ __forceinline__ double box_d2(const unsigned long long* bb, double x,
   return dx * dx + dy * dy + dz * dz;
 }
 
+// One warp walks the octree for 32 cells that are consecutive in Morton order
+// of their sites (so close together), sharing the node loads: every lane
+// tests each visited node against its own cell (FP32, outward-rounded box,
+// 1e-6 absolute margin: 2 * largest h + cell radius), the warp descends when
+// any lane needs the node, and at a leaf only the lanes that reach it test
+// its particles with the pair rule.
 // FILL = false: count pairs per cell; FILL = true: write them at off[c].
 template <bool FILL>
-__global__ void pair_traverse(int64_t ncell, const int32_t* __restrict__ order, PairTree T, PairGrid G,
-                              int64_t* count, const int64_t* __restrict__ off, int32_t* out) {
-  int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (t >= ncell) return;
-  const int64_t c = order ? order[t] : t;
-  const double sx = G.site[3 * c], sy = G.site[3 * c + 1], sz = G.site[3 * c + 2];
-  const double R = G.rad[c];
-  int64_t w = FILL ? off[c] : 0;
+__global__ void __launch_bounds__(128) pair_traverse(int64_t ncell, const int32_t* __restrict__ order, PairTree T,
+                                                     PairGrid G, int64_t* count, const int64_t* __restrict__ off,
+                                                     int32_t* out) {
+  __shared__ int32_t s_stack[4][200];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t t = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x);
+  const bool valid = t < ncell;
+  if (__all_sync(0xffffffffu, !valid)) return;
+  const int64_t c = valid ? (order ? order[t] : t) : -1;
+  double sx = 0, sy = 0, sz = 0, R = 0;
+  if (valid) { sx = G.site[3 * c]; sy = G.site[3 * c + 1]; sz = G.site[3 * c + 2]; R = G.rad[c]; }
+  const float fsx = (float)sx, fsy = (float)sy, fsz = (float)sz, fR = (float)R;
+  int64_t w = (FILL && valid) ? off[c] : 0;
   int64_t cnt = 0;
-  int32_t stack[192];
-  int sp = 0;
-  stack[sp++] = 0;
+  int32_t* stack = s_stack[warp];
+  int sp = 1;
+  if (lane == 0) stack[0] = 0;
+  __syncwarp();
   while (sp > 0) {
     const int32_t nd = stack[--sp];
-    // conservative prune: no particle of the node can pass the distance test
-    const double reach = 2.0 * bitsd(T.hmax[nd]) + R;
-    if (box_d2(T.bbox + 6 * nd, sx, sy, sz) > reach * reach * (1.0 + 1e-12)) continue;
+    __syncwarp();
+    const float* b = T.box32 + 8 * nd;
+    const float dx = fsx < b[0] ? b[0] - fsx : (fsx > b[3] ? fsx - b[3] : 0.f);
+    const float dy = fsy < b[1] ? b[1] - fsy : (fsy > b[4] ? fsy - b[4] : 0.f);
+    const float dz = fsz < b[2] ? b[2] - fsz : (fsz > b[5] ? fsz - b[5] : 0.f);
+    const float reach = (2.f * b[6] + fR + 1e-6f) * 1.000001f;
+    const bool need = valid && dx * dx + dy * dy + dz * dz <= reach * reach;
+    if (!__any_sync(0xffffffffu, need)) continue;
     if (T.nch[nd] == 0) {
-      for (int64_t k = T.nb[nd]; k < T.ne[nd]; ++k) {
-        if (pair_rule(G, c, sx, sy, sz, R, T.xs[k], T.ys[k], T.zs[k], T.hs[k])) {
-          if (FILL) out[w++] = T.idx[k];
-          ++cnt;
+      if (need) {
+        for (int64_t k = T.nb[nd]; k < T.ne[nd]; ++k) {
+          if (pair_rule(G, c, sx, sy, sz, R, T.xs[k], T.ys[k], T.zs[k], T.hs[k])) {
+            if (FILL) out[w++] = T.idx[k];
+            ++cnt;
+          }
         }
       }
     } else {
+      const int nc = T.nch[nd];
       const int64_t c0 = T.fc[nd];
-      for (int k = T.nch[nd] - 1; k >= 0; --k) stack[sp++] = (int32_t)(c0 + k);
+      if (lane < nc) stack[sp + lane] = (int32_t)(c0 + nc - 1 - lane);
+      sp += nc;
+      __syncwarp();
     }
   }
-  if (!FILL) count[c] = cnt;
+  if (!FILL && valid) count[c] = cnt;
+}
+
+// Sort each cell's pair list (<= 1024 entries) in shared memory, one warp
+// per cell, bitonic; longer lists are left to the library segmented sort.
+__global__ void __launch_bounds__(128) sort_small_segments(int64_t ncell, const int64_t* __restrict__ off,
+                                                           const int32_t* __restrict__ in, int32_t* out) {
+  __shared__ int32_t buf[4][1024];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t c = blockIdx.x * 4LL + warp;
+  if (c >= ncell) return;
+  const int64_t b = off[c], e = off[c + 1];
+  const int L = (int)(e - b);
+  if (L > 1024 || L == 0) return;
+  int P = 1;
+  while (P < L) P <<= 1;
+  int32_t* v = buf[warp];
+  for (int i = lane; i < P; i += 32) v[i] = i < L ? in[b + i] : 0x7fffffff;
+  __syncwarp();
+  for (int k = 2; k <= P; k <<= 1)
+    for (int j = k >> 1; j > 0; j >>= 1) {
+      for (int i = lane; i < P; i += 32) {
+        const int ixj = i ^ j;
+        if (ixj > i) {
+          const int32_t a0 = v[i], a1 = v[ixj];
+          const bool up = (i & k) == 0;
+          if ((a0 > a1) == up) { v[i] = a1; v[ixj] = a0; }
+        }
+      }
+      __syncwarp();
+    }
+  for (int i = lane; i < L; i += 32) out[b + i] = v[i];
+}
+
+__global__ void mark_large(int64_t ncell, const int64_t* __restrict__ off, int64_t* beg, int64_t* end,
+                           unsigned long long* nlarge) {
+  const int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (c >= ncell) return;
+  if (off[c + 1] - off[c] > 1024) {
+    const unsigned long long k = atomicAdd(nlarge, 1ULL);
+    beg[k] = off[c];
+    end[k] = off[c + 1];
+  }
 }
 
 __global__ void site_keys(int64_t n, const double* __restrict__ site, uint64_t* keys, int32_t* idx) {
@@ -146,7 +211,8 @@ int pairs_build(map_ctx* ctx, const PreparedGrid* g, cudaStream_t s) {
   MAP_TRY(ctx_ensure(ctx, ctx->cub_tmp, tb));
   CUDA_TRY(cub::DeviceRadixSort::SortPairs(ctx->cub_tmp.p, tb, k_in, k_out, o_in, order, nc, 0, 30, s));
 
-  PairTree PT{T.xs, T.ys, T.zs, T.hs, T.idx, T.begin, T.end, T.first_child, T.nchild, T.bbox_bits, T.hmax_bits};
+  PairTree PT{T.xs, T.ys, T.zs, T.hs, T.idx, T.begin, T.end, T.first_child, T.nchild, T.bbox_bits, T.hmax_bits,
+              T.box32};
   PairGrid PG{g->cell_face_off, g->face_plane, g->face32, g->site, g->rad};
   int64_t *count, *off;
   MAP_TRY(ensure_t(ctx, ctx->ws_pairs[0], nc + 1, &count));
@@ -167,10 +233,24 @@ int pairs_build(map_ctx* ctx, const PreparedGrid* g, cudaStream_t s) {
   pair_traverse<true><<<nblk(nc, tpb), tpb, 0, s>>>(nc, order, PT, PG, nullptr, off, raw); ++ctx->launches;
   CUDA_TRY(cudaGetLastError());
   if (np > 0) {
-    tb = 0;
-    CUDA_TRY(cub::DeviceSegmentedSort::SortKeys(nullptr, tb, raw, sorted, np, nc, off, off + 1, s));
-    MAP_TRY(ctx_ensure(ctx, ctx->cub_tmp, tb));
-    CUDA_TRY(cub::DeviceSegmentedSort::SortKeys(ctx->cub_tmp.p, tb, raw, sorted, np, nc, off, off + 1, s));
+    sort_small_segments<<<nblk(nc, 4), 128, 0, s>>>(nc, off, raw, sorted); ++ctx->launches;
+    CUDA_TRY(cudaGetLastError());
+    int64_t *lb, *le;
+    MAP_TRY(ensure_t(ctx, ctx->ws_misc[1], nc + 1, &lb));
+    MAP_TRY(ensure_t(ctx, ctx->ws_misc[2], nc + 1, &le));
+    unsigned long long* d_nl = ctx->d_counters + 5;
+    CUDA_TRY(cudaMemsetAsync(d_nl, 0, sizeof(unsigned long long), s));
+    mark_large<<<nblk(nc, 256), 256, 0, s>>>(nc, off, lb, le, d_nl); ++ctx->launches;
+    CUDA_TRY(cudaGetLastError());
+    CUDA_TRY(cudaMemcpyAsync(ctx->h_scratch, d_nl, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+    CUDA_TRY(cudaStreamSynchronize(s));
+    const int64_t nlarge = ctx->h_scratch[0];
+    if (nlarge > 0) {
+      tb = 0;
+      CUDA_TRY(cub::DeviceSegmentedSort::SortKeys(nullptr, tb, raw, sorted, np, nlarge, lb, le, s));
+      MAP_TRY(ctx_ensure(ctx, ctx->cub_tmp, tb));
+      CUDA_TRY(cub::DeviceSegmentedSort::SortKeys(ctx->cub_tmp.p, tb, raw, sorted, np, nlarge, lb, le, s));
+    }
   }
   ctx->n_pairs = np;
   ctx->pair_off = off;

@@ -255,7 +255,7 @@ __global__ void min_member_level(int64_t nm, const int32_t* __restrict__ members
 int pseudo_run(map_ctx* ctx, const map_particles* full, const double* src, int nsrc, map_particles* out,
                int32_t* kind, int64_t* ident, int64_t* n_pseudo, cudaStream_t s) {
   const int64_t n = full->n;
-  MAP_TRY(tree_build(ctx, full->x, full->y, full->z, full->m, full->h, n, s));
+  MAP_TRY(tree_build(ctx, full->x, full->y, full->z, full->m, full->h, n, s, true));
   DevTree& T = ctx->tree;
   const int64_t nn = T.nnodes;
   const int tpb = 256;

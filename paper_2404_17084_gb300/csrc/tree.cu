@@ -58,15 +58,23 @@ __global__ void morton_keys(int64_t n, const double* __restrict__ x, const doubl
 __global__ void gather_sorted(int64_t n, const int32_t* __restrict__ idx, const double* __restrict__ x,
                               const double* __restrict__ y, const double* __restrict__ z,
                               const double* __restrict__ m, const double* __restrict__ h, double* xs, double* ys,
-                              double* zs, double* ms, double* hs) {
+                              double* zs, double* ms, double* hs, float* split) {
   int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (i >= n) return;
   int32_t a = idx[i];
-  xs[i] = x[a] + 0.0;  // + 0.0 turns -0.0 into +0.0 (bit-ordered min/max below)
-  ys[i] = y[a] + 0.0;
-  zs[i] = z[a] + 0.0;
+  const double px = x[a] + 0.0, py = y[a] + 0.0, pz = z[a] + 0.0;  // + 0.0: -0.0 -> +0.0 (bit-ordered min/max)
+  xs[i] = px;
+  ys[i] = py;
+  zs[i] = pz;
   ms[i] = m ? m[a] : 1.0;
   hs[i] = h ? h[a] : 0.0;
+  // FP32 hi/lo split of the coordinates: x = hi + lo to ~2^-48, so that the
+  // difference of two nearby points, (hi_j - hi_i) + (lo_j - lo_i), keeps
+  // ~24 bits relative to the separation
+  const float hx = (float)px, hy = (float)py, hz = (float)pz;
+  split[6 * i + 0] = hx; split[6 * i + 1] = (float)(px - (double)hx);
+  split[6 * i + 2] = hy; split[6 * i + 3] = (float)(py - (double)hy);
+  split[6 * i + 4] = hz; split[6 * i + 5] = (float)(pz - (double)hz);
 }
 
 __device__ __forceinline__ int64_t lower_octant(const uint64_t* keys, int64_t b, int64_t e, int shift, int o) {
@@ -128,23 +136,30 @@ __global__ void split_write(int64_t lb, int64_t le, int64_t next_begin, const ui
   }
 }
 
-// Bottom-up sums for one level: leaves sum their particles in sorted order,
-// internal nodes sum their children in octant order.
+// Bottom-up pass for one level: leaves sum their particles in sorted order,
+// internal nodes sum their children in octant order (mass, mass-weighted
+// position); bounding box and largest h are the union / maximum over the
+// particles (leaves) or the children (internal nodes), exact in any order.
 __global__ void node_sums(int64_t lb, int64_t le, const int64_t* __restrict__ nb, const int64_t* __restrict__ ne,
                           const int64_t* __restrict__ fc, const int32_t* __restrict__ nch,
                           const double* __restrict__ xs, const double* __restrict__ ys,
-                          const double* __restrict__ zs, const double* __restrict__ ms, double* mass,
-                          double* msum /* 3 per node: sum m x */, int32_t* owner) {
+                          const double* __restrict__ zs, const double* __restrict__ ms,
+                          const double* __restrict__ hs, double* mass, double* msum /* 3 per node: sum m x */,
+                          unsigned long long* hmax_bits, unsigned long long* bbox, int32_t* owner) {
   int64_t i = lb + blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (i >= le) return;
-  double M = 0, Sx = 0, Sy = 0, Sz = 0;
+  double M = 0, Sx = 0, Sy = 0, Sz = 0, hm = 0;
+  double lo0 = 1e300, lo1 = 1e300, lo2 = 1e300, hi0 = 0, hi1 = 0, hi2 = 0;
   if (nch[i] == 0) {
     for (int64_t k = nb[i]; k < ne[i]; ++k) {
-      double mk = ms[k];
+      const double mk = ms[k], x = xs[k], y = ys[k], z = zs[k];
       M += mk;
-      Sx += mk * xs[k];
-      Sy += mk * ys[k];
-      Sz += mk * zs[k];
+      Sx += mk * x;
+      Sy += mk * y;
+      Sz += mk * z;
+      hm = fmax(hm, hs[k]);
+      lo0 = fmin(lo0, x); lo1 = fmin(lo1, y); lo2 = fmin(lo2, z);
+      hi0 = fmax(hi0, x); hi1 = fmax(hi1, y); hi2 = fmax(hi2, z);
       owner[k] = (int32_t)i;
     }
   } else {
@@ -153,16 +168,22 @@ __global__ void node_sums(int64_t lb, int64_t le, const int64_t* __restrict__ nb
       Sx += msum[3 * c];
       Sy += msum[3 * c + 1];
       Sz += msum[3 * c + 2];
+      hm = fmax(hm, bitsd(hmax_bits[c]));
+      lo0 = fmin(lo0, bitsd(bbox[6 * c])); lo1 = fmin(lo1, bitsd(bbox[6 * c + 1])); lo2 = fmin(lo2, bitsd(bbox[6 * c + 2]));
+      hi0 = fmax(hi0, bitsd(bbox[6 * c + 3])); hi1 = fmax(hi1, bitsd(bbox[6 * c + 4])); hi2 = fmax(hi2, bitsd(bbox[6 * c + 5]));
     }
   }
   mass[i] = M;
   msum[3 * i] = Sx;
   msum[3 * i + 1] = Sy;
   msum[3 * i + 2] = Sz;
+  hmax_bits[i] = dbits(hm);
+  bbox[6 * i] = dbits(lo0); bbox[6 * i + 1] = dbits(lo1); bbox[6 * i + 2] = dbits(lo2);
+  bbox[6 * i + 3] = dbits(hi0); bbox[6 * i + 4] = dbits(hi1); bbox[6 * i + 5] = dbits(hi2);
 }
 
 __global__ void node_com(int64_t nn, const double* __restrict__ mass, const double* __restrict__ msum, double* com,
-                         unsigned long long* size_bits, unsigned long long* hmax_bits, unsigned long long* bbox) {
+                         unsigned long long* size_bits) {
   int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (i >= nn) return;
   double M = mass[i];
@@ -170,67 +191,60 @@ __global__ void node_com(int64_t nn, const double* __restrict__ mass, const doub
   com[3 * i + 1] = msum[3 * i + 1] / M;
   com[3 * i + 2] = msum[3 * i + 2] / M;
   size_bits[i] = 0ULL;
-  hmax_bits[i] = 0ULL;
-  for (int k = 0; k < 3; ++k) {
-    bbox[6 * i + k] = 0x7ff0000000000000ULL;  // +inf
-    bbox[6 * i + 3 + k] = 0ULL;
-  }
 }
 
-// Small nodes: every particle walks up from its leaf while the node holds at
-// most BIG_NODE particles and reduces into it with atomics.
+// Node size (distance from the centre of mass to the furthest particle,
+// Section III-A), needed by the pseudo-particle walk only.  Small nodes: every
+// particle walks up from its leaf while the node holds at most BIG_NODE
+// particles and reduces into it with atomics.
 __global__ void node_extent_small(int64_t n, const int32_t* __restrict__ owner, const int32_t* __restrict__ parent,
                                   const int64_t* __restrict__ nb, const int64_t* __restrict__ ne,
                                   const double* __restrict__ xs, const double* __restrict__ ys,
-                                  const double* __restrict__ zs, const double* __restrict__ hs,
-                                  const double* __restrict__ com, unsigned long long* size_bits,
-                                  unsigned long long* hmax_bits, unsigned long long* bbox) {
+                                  const double* __restrict__ zs, const double* __restrict__ com,
+                                  unsigned long long* size_bits) {
   int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (k >= n) return;
-  double x = xs[k], y = ys[k], z = zs[k], h = hs[k];
+  double x = xs[k], y = ys[k], z = zs[k];
   int32_t node = owner[k];
   while (node >= 0 && ne[node] - nb[node] <= BIG_NODE) {
     double dx = x - com[3 * node], dy = y - com[3 * node + 1], dz = z - com[3 * node + 2];
-    double d = sqrt(dx * dx + dy * dy + dz * dz);
-    atomicMax(&size_bits[node], dbits(d));
-    atomicMax(&hmax_bits[node], dbits(h));
-    atomicMin(&bbox[6 * node + 0], dbits(x));
-    atomicMin(&bbox[6 * node + 1], dbits(y));
-    atomicMin(&bbox[6 * node + 2], dbits(z));
-    atomicMax(&bbox[6 * node + 3], dbits(x));
-    atomicMax(&bbox[6 * node + 4], dbits(y));
-    atomicMax(&bbox[6 * node + 5], dbits(z));
+    atomicMax(&size_bits[node], dbits(sqrt(dx * dx + dy * dy + dz * dz)));
     node = parent[node];
   }
 }
 
-// Big nodes: one block per node reduces over its whole particle range.
-__global__ void node_extent_big(const int32_t* __restrict__ big, const int64_t* __restrict__ nb,
+// Big nodes: several blocks per node, each reducing a slice of its range.
+__global__ void node_extent_big(const int32_t* __restrict__ big, int slices, const int64_t* __restrict__ nb,
                                 const int64_t* __restrict__ ne, const double* __restrict__ xs,
                                 const double* __restrict__ ys, const double* __restrict__ zs,
-                                const double* __restrict__ hs, const double* __restrict__ com,
-                                unsigned long long* size_bits, unsigned long long* hmax_bits,
-                                unsigned long long* bbox) {
-  const int32_t node = big[blockIdx.x];
+                                const double* __restrict__ com, unsigned long long* size_bits) {
+  const int32_t node = big[blockIdx.x / slices];
+  const int slice = blockIdx.x % slices;
   const double cx = com[3 * node], cy = com[3 * node + 1], cz = com[3 * node + 2];
-  double smax = 0, hmax = 0, lo[3] = {1e300, 1e300, 1e300}, hi[3] = {0, 0, 0};
-  for (int64_t k = nb[node] + threadIdx.x; k < ne[node]; k += blockDim.x) {
-    double x = xs[k], y = ys[k], z = zs[k];
-    double dx = x - cx, dy = y - cy, dz = z - cz;
+  double smax = 0;
+  for (int64_t k = nb[node] + (int64_t)slice * blockDim.x + threadIdx.x; k < ne[node];
+       k += (int64_t)slices * blockDim.x) {
+    const double dx = xs[k] - cx, dy = ys[k] - cy, dz = zs[k] - cz;
     smax = fmax(smax, sqrt(dx * dx + dy * dy + dz * dz));
-    hmax = fmax(hmax, hs[k]);
-    lo[0] = fmin(lo[0], x); lo[1] = fmin(lo[1], y); lo[2] = fmin(lo[2], z);
-    hi[0] = fmax(hi[0], x); hi[1] = fmax(hi[1], y); hi[2] = fmax(hi[2], z);
   }
   typedef cub::BlockReduce<double, 256> BR;
   __shared__ typename BR::TempStorage tmp;
-  double v;
-  v = BR(tmp).Reduce(smax, MaxOp()); if (threadIdx.x == 0) size_bits[node] = dbits(v); __syncthreads();
-  v = BR(tmp).Reduce(hmax, MaxOp()); if (threadIdx.x == 0) hmax_bits[node] = dbits(v); __syncthreads();
+  const double v = BR(tmp).Reduce(smax, MaxOp());
+  if (threadIdx.x == 0) atomicMax(&size_bits[node], dbits(v));
+}
+
+// FP32 copy of each node's bounding box (rounded outward) and largest h
+// (rounded up), for conservative FP32 pruning in traversals.
+__global__ void node_box32(int64_t nn, const unsigned long long* __restrict__ bbox,
+                           const unsigned long long* __restrict__ hmax, float* box32) {
+  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= nn) return;
   for (int k = 0; k < 3; ++k) {
-    v = BR(tmp).Reduce(lo[k], MinOp()); if (threadIdx.x == 0) bbox[6 * node + k] = dbits(v); __syncthreads();
-    v = BR(tmp).Reduce(hi[k], MaxOp()); if (threadIdx.x == 0) bbox[6 * node + 3 + k] = dbits(v); __syncthreads();
+    box32[8 * i + k] = __double2float_rd(bitsd(bbox[6 * i + k]));
+    box32[8 * i + 3 + k] = __double2float_ru(bitsd(bbox[6 * i + 3 + k]));
   }
+  box32[8 * i + 6] = __double2float_ru(bitsd(hmax[i]));
+  box32[8 * i + 7] = 0.f;
 }
 
 __global__ void collect_big(int64_t nn, const int64_t* __restrict__ nb, const int64_t* __restrict__ ne, int32_t* big,
@@ -279,7 +293,7 @@ static int grow_nodes(map_ctx* ctx, int64_t need) {
 }
 
 int tree_build(map_ctx* ctx, const double* x, const double* y, const double* z, const double* m, const double* h,
-               int64_t n, cudaStream_t s) {
+               int64_t n, cudaStream_t s, bool want_size) {
   DevTree& T = ctx->tree;
   T.n = n;
   const int tpb = 256;
@@ -292,13 +306,14 @@ int tree_build(map_ctx* ctx, const double* x, const double* y, const double* z, 
   MAP_TRY(ensure_t(ctx, ctx->ws_tree[4], 5 * n, &T.xs));
   T.ys = T.xs + n; T.zs = T.xs + 2 * n; T.ms = T.xs + 3 * n; T.hs = T.xs + 4 * n;
   MAP_TRY(ensure_t(ctx, ctx->ws_tree[5], n, &T.owner));
+  MAP_TRY(ensure_t(ctx, ctx->ws_tree[23], 6 * n, &T.split));
   morton_keys<<<nblk(n, tpb), tpb, 0, s>>>(n, x, y, z, keys_in, idx_in); ++ctx->launches;
   CUDA_TRY(cudaGetLastError());
   size_t tmp_bytes = 0;
   CUDA_TRY(cub::DeviceRadixSort::SortPairs(nullptr, tmp_bytes, keys_in, T.keys, idx_in, T.idx, n, 0, 63, s));
   MAP_TRY(ctx_ensure(ctx, ctx->cub_tmp, tmp_bytes));
   CUDA_TRY(cub::DeviceRadixSort::SortPairs(ctx->cub_tmp.p, tmp_bytes, keys_in, T.keys, idx_in, T.idx, n, 0, 63, s));
-  gather_sorted<<<nblk(n, tpb), tpb, 0, s>>>(n, T.idx, x, y, z, m, h, T.xs, T.ys, T.zs, T.ms, T.hs); ++ctx->launches;
+  gather_sorted<<<nblk(n, tpb), tpb, 0, s>>>(n, T.idx, x, y, z, m, h, T.xs, T.ys, T.zs, T.ms, T.hs, T.split); ++ctx->launches;
   CUDA_TRY(cudaGetLastError());
 
   // level-synchronous build
@@ -349,29 +364,37 @@ int tree_build(map_ctx* ctx, const double* x, const double* y, const double* z, 
   for (int L = T.nlevels - 1; L >= 0; --L) {
     int64_t a = T.level_begin[L], b = T.level_begin[L + 1];
     node_sums<<<nblk(b - a, tpb), tpb, 0, s>>>(a, b, T.begin, T.end, T.first_child, T.nchild, T.xs, T.ys, T.zs,
-                                               T.ms, T.mass, msum, T.owner); ++ctx->launches;
+                                               T.ms, T.hs, T.mass, msum, T.hmax_bits, T.bbox_bits, T.owner);
+    ++ctx->launches;
     CUDA_TRY(cudaGetLastError());
   }
-  node_com<<<nblk(T.nnodes, tpb), tpb, 0, s>>>(T.nnodes, T.mass, msum, T.com, T.size_bits, T.hmax_bits,
-                                               T.bbox_bits); ++ctx->launches;
+  node_com<<<nblk(T.nnodes, tpb), tpb, 0, s>>>(T.nnodes, T.mass, msum, T.com, T.size_bits); ++ctx->launches;
   CUDA_TRY(cudaGetLastError());
-  node_extent_small<<<nblk(n, tpb), tpb, 0, s>>>(n, T.owner, T.parent, T.begin, T.end, T.xs, T.ys, T.zs, T.hs,
-                                                 T.com, T.size_bits, T.hmax_bits, T.bbox_bits); ++ctx->launches;
-  CUDA_TRY(cudaGetLastError());
-  int32_t* big;
-  MAP_TRY(ensure_t(ctx, ctx->ws_tree[21], T.nnodes, &big));
-  unsigned long long* d_nbig = ctx->d_counters + 4;
-  CUDA_TRY(cudaMemsetAsync(d_nbig, 0, sizeof(unsigned long long), s));
-  collect_big<<<nblk(T.nnodes, tpb), tpb, 0, s>>>(T.nnodes, T.begin, T.end, big, d_nbig); ++ctx->launches;
-  CUDA_TRY(cudaGetLastError());
-  CUDA_TRY(cudaMemcpyAsync(ctx->h_scratch, d_nbig, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
-  CUDA_TRY(cudaStreamSynchronize(s));
-  int64_t nbig = ctx->h_scratch[0];
-  if (nbig > 0) {
-    node_extent_big<<<(unsigned)nbig, 256, 0, s>>>(big, T.begin, T.end, T.xs, T.ys, T.zs, T.hs, T.com, T.size_bits,
-                                                   T.hmax_bits, T.bbox_bits); ++ctx->launches;
+  if (want_size) {
+    node_extent_small<<<nblk(n, tpb), tpb, 0, s>>>(n, T.owner, T.parent, T.begin, T.end, T.xs, T.ys, T.zs, T.com,
+                                                   T.size_bits); ++ctx->launches;
     CUDA_TRY(cudaGetLastError());
+    int32_t* big;
+    MAP_TRY(ensure_t(ctx, ctx->ws_tree[21], T.nnodes, &big));
+    unsigned long long* d_nbig = ctx->d_counters + 4;
+    CUDA_TRY(cudaMemsetAsync(d_nbig, 0, sizeof(unsigned long long), s));
+    collect_big<<<nblk(T.nnodes, tpb), tpb, 0, s>>>(T.nnodes, T.begin, T.end, big, d_nbig); ++ctx->launches;
+    CUDA_TRY(cudaGetLastError());
+    CUDA_TRY(cudaMemcpyAsync(ctx->h_scratch, d_nbig, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+    CUDA_TRY(cudaStreamSynchronize(s));
+    const int64_t nbig = ctx->h_scratch[0];
+    if (nbig > 0) {
+      const int slices = 32;
+      node_extent_big<<<(unsigned)(nbig * slices), 256, 0, s>>>(big, slices, T.begin, T.end, T.xs, T.ys, T.zs,
+                                                                T.com, T.size_bits); ++ctx->launches;
+      CUDA_TRY(cudaGetLastError());
+    }
   }
+  float* box32;
+  MAP_TRY(ensure_t(ctx, ctx->ws_tree[24], 8 * T.nnodes, &box32));
+  T.box32 = box32;
+  node_box32<<<nblk(T.nnodes, tpb), tpb, 0, s>>>(T.nnodes, T.bbox_bits, T.hmax_bits, box32); ++ctx->launches;
+  CUDA_TRY(cudaGetLastError());
   return MAP_OK;
 }
 
@@ -404,7 +427,19 @@ struct TreeView {
   const int64_t *nb, *ne, *fc;
   const int32_t* nch;
   const unsigned long long* bbox;
+  const float* box32;  // outward-rounded FP32 boxes (8 floats per node)
 };
+
+// Conservative FP32 test: true when no point of the node's box is within R
+// of (x,y,z).  The box is rounded outward and the query point's rounding
+// (<= 6e-8 in the unit cube) is covered by a 1e-6 absolute margin.
+__device__ __forceinline__ bool box_far32(const float* b, float x, float y, float z, double R) {
+  const float dx = x < b[0] ? b[0] - x : (x > b[3] ? x - b[3] : 0.f);
+  const float dy = y < b[1] ? b[1] - y : (y > b[4] ? y - b[4] : 0.f);
+  const float dz = z < b[2] ? b[2] - z : (z > b[5] ? z - b[5] : 0.f);
+  const float Rm = (float)(R + 1e-6) * 1.000001f;
+  return dx * dx + dy * dy + dz * dz > Rm * Rm;
+}
 
 // n(h) = sum_b W(r_ab, h) and dn/dh over all tree particles within 2h.
 __device__ void density_sum(const TreeView& T, double x, double y, double z, double h, double& n, double& dn) {
@@ -443,37 +478,119 @@ __device__ __forceinline__ double g_of(const TreeView& T, double x, double y, do
   return h - hfact * pow(n, -1.0 / 3.0);
 }
 
-// One thread per particle (sorted order).  h0 per sorted position.
-__global__ void h_newton(int64_t n, TreeView T, const int32_t* __restrict__ idx, const double* __restrict__ h0s,
-                         double hfact, double* hout, int32_t* route) {
+constexpr int MAXR = 64;  // cached candidate leaf ranges per particle
+
+// Leaves whose bounding box comes within R of (x,y,z); false if more than MAXR.
+__device__ bool gather_ranges(const TreeView& T, double x, double y, double z, double R, int2* rng, int& nr) {
+  const float fx = (float)x, fy = (float)y, fz = (float)z;
+  int32_t stack[192];
+  int sp = 0;
+  stack[sp++] = 0;
+  nr = 0;
+  while (sp > 0) {
+    const int32_t nd = stack[--sp];
+    if (box_far32(T.box32 + 8 * nd, fx, fy, fz, R)) continue;
+    if (T.nch[nd] == 0) {
+      if (nr == MAXR) return false;
+      rng[nr++] = make_int2((int)T.nb[nd], (int)T.ne[nd]);
+    } else {
+      const int64_t c0 = T.fc[nd];
+      for (int c = T.nch[nd] - 1; c >= 0; --c) stack[sp++] = (int32_t)(c0 + c);
+    }
+  }
+  return true;
+}
+
+// n(h), dn/dh over cached ranges.  MIXED: FP32 sums on hi/lo split
+// coordinates (h to ~1e-7 relative); else FP64.
+template <bool MIXED>
+__device__ void range_sum(const TreeView& T, const float* __restrict__ split, int64_t k, double x, double y, double z,
+                          double h, const int2* rng, int nr, double& n, double& dn) {
+  if (MIXED) {
+    const float hxi = split[6 * k], lxi = split[6 * k + 1], hyi = split[6 * k + 2], lyi = split[6 * k + 3];
+    const float hzi = split[6 * k + 4], lzi = split[6 * k + 5];
+    const float inv_h = (float)(1.0 / h);
+    float s = 0.f, ds = 0.f;
+    for (int r = 0; r < nr; ++r)
+      for (int j = rng[r].x; j < rng[r].y; ++j) {
+        const float* P = split + 6 * (int64_t)j;
+        const float dx = ((P[0] - hxi) + (P[1] - lxi)) * inv_h;
+        const float dy = ((P[2] - hyi) + (P[3] - lyi)) * inv_h;
+        const float dz = ((P[4] - hzi) + (P[5] - lzi)) * inv_h;
+        const float q2 = dx * dx + dy * dy + dz * dz;
+        if (q2 >= 4.f) continue;
+        const float q = sqrtf(q2);
+        float w, dwq;
+        if (q < 1.f) { w = 1.f - 1.5f * q2 + 0.75f * q2 * q; dwq = -3.f * q2 + 2.25f * q2 * q; }
+        else { const float t = 2.f - q; w = 0.25f * t * t * t; dwq = -0.75f * t * t * q; }
+        s += w;
+        ds += 3.f * w + dwq;
+      }
+    const double norm = 1.0 / (MAP_PI * h * h * h);
+    n = (double)s * norm;
+    dn = -(double)ds * norm / h;
+  } else {
+    const double R2 = 4.0 * h * h, inv_h = 1.0 / h;
+    double s = 0.0, ds = 0.0;
+    for (int r = 0; r < nr; ++r)
+      for (int j = rng[r].x; j < rng[r].y; ++j) {
+        const double dx = T.xs[j] - x, dy = T.ys[j] - y, dz = T.zs[j] - z;
+        const double r2 = dx * dx + dy * dy + dz * dz;
+        if (r2 >= R2) continue;
+        const double q = sqrt(r2) * inv_h;
+        const double w = w_m4(q);
+        s += w;
+        ds += 3.0 * w + q * dw_m4(q);
+      }
+    const double norm = 1.0 / (MAP_PI * h * h * h);
+    n = s * norm;
+    dn = -ds * norm * inv_h;
+  }
+}
+
+// One thread per particle (sorted order).  Newton on cached candidate ranges
+// (gathered for a support up to 2*hcap, hcap = 1.25 h, regathered whenever h
+// outgrows it); bisection falls back to a full range query per evaluation.
+template <bool MIXED>
+__global__ void h_newton(int64_t n, TreeView T, const float* __restrict__ split, const int32_t* __restrict__ idx,
+                         const double* __restrict__ h0s, double hfact, double tol, double* hout, int32_t* route) {
   int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (k >= n) return;
   const double x = T.xs[k], y = T.ys[k], z = T.zs[k];
   const double g0 = h0s[k];
   const double lo = g0 / 16.0, hi = g0 * 16.0;
+  int2 rng[MAXR];
+  int nr = 0;
+  double hcap = 1.25 * g0;
+  bool cached = gather_ranges(T, x, y, z, 2.0 * hcap, rng, nr);
   double h = g0;
   bool ok = false;
   for (int it = 0; it < 30; ++it) {
+    if (h > hcap) {
+      hcap = 1.25 * h;
+      cached = gather_ranges(T, x, y, z, 2.0 * hcap, rng, nr);
+    }
     double nn, dn;
-    density_sum(T, x, y, z, h, nn, dn);
-    double f = h - hfact * pow(nn, -1.0 / 3.0);
-    double fp = 1.0 + hfact / 3.0 * pow(nn, -4.0 / 3.0) * dn;
-    double hn = h - f / fp;
+    if (cached) range_sum<MIXED>(T, split, k, x, y, z, h, rng, nr, nn, dn);
+    else density_sum(T, x, y, z, h, nn, dn);
+    const double f = h - hfact * pow(nn, -1.0 / 3.0);
+    const double fp = 1.0 + hfact / 3.0 * pow(nn, -4.0 / 3.0) * dn;
+    const double hn = h - f / fp;
     if (!(hn >= lo && hn <= hi)) break;
-    if (fabs(hn - h) < 1e-10 * hn) { h = hn; ok = true; break; }
+    if (fabs(hn - h) < tol * hn) { h = hn; ok = true; break; }
     h = hn;
   }
   int r = 0;
   if (!ok) {
-    double flo = g_of(T, x, y, z, lo, hfact), fhi = g_of(T, x, y, z, hi, hfact);
+    const double flo = g_of(T, x, y, z, lo, hfact), fhi = g_of(T, x, y, z, hi, hfact);
     if (!(flo < 0.0 && fhi > 0.0)) {
       h = g0;
       r = 2;
     } else {
       double a0 = lo, b0 = hi;
       for (int it = 0; it < 200; ++it) {
-        double mid = 0.5 * (a0 + b0);
-        double fm = g_of(T, x, y, z, mid, hfact);
+        const double mid = 0.5 * (a0 + b0);
+        const double fm = g_of(T, x, y, z, mid, hfact);
         if (fm < 0.0) a0 = mid; else b0 = mid;
         if (b0 - a0 < 1e-12 * mid) break;
       }
@@ -518,8 +635,13 @@ int h_solve_run(map_ctx* ctx, const double* x, const double* y, const double* z,
     h_guess_leaf<<<nblk(n, tpb), tpb, 0, s>>>(n, T.owner, T.level, T.begin, T.end, ctx->cfg.hfact, h0s);
   ++ctx->launches;
   CUDA_TRY(cudaGetLastError());
-  TreeView V{T.xs, T.ys, T.zs, T.begin, T.end, T.first_child, T.nchild, T.bbox_bits};
-  h_newton<<<nblk(n, tpb), tpb, 0, s>>>(n, V, T.idx, h0s, ctx->cfg.hfact, h, route); ++ctx->launches;
+  TreeView V{T.xs, T.ys, T.zs, T.begin, T.end, T.first_child, T.nchild, T.bbox_bits, T.box32};
+  // the mixed build converges h in FP32 sums to 1e-6 relative; the FP64 build to 1e-10
+  if (ctx->cfg.precision == MAP_MIXED)
+    h_newton<true><<<nblk(n, tpb), tpb, 0, s>>>(n, V, T.split, T.idx, h0s, ctx->cfg.hfact, 1e-6, h, route);
+  else
+    h_newton<false><<<nblk(n, tpb), tpb, 0, s>>>(n, V, T.split, T.idx, h0s, ctx->cfg.hfact, 1e-10, h, route);
+  ++ctx->launches;
   CUDA_TRY(cudaGetLastError());
   return MAP_OK;
 }

@@ -183,10 +183,26 @@ struct Poly {
       nf.push_back(loop); nfn.push_back(n); nfd.push_back(d); nnb.push_back(nbid);
     }
     v.swap(nvtx); f.swap(nf); fn.swap(nfn); fd.swap(nfd); nb.swap(nnb);
-    compact();
+    drop_unused();
     update_rmax();
     return true;
   }
+
+  // remove vertices no face refers to (cheap; the O(V^2) weld runs once per cell)
+  void drop_unused() {
+    std::vector<int>& used = scratch_used;
+    used.assign(v.size(), -1);
+    std::vector<V3>& nvtx = scratch_v;
+    nvtx.clear();
+    for (auto& loop : f)
+      for (int& id : loop) {
+        if (used[id] < 0) { used[id] = (int)nvtx.size(); nvtx.push_back(v[id]); }
+        id = used[id];
+      }
+    v.swap(nvtx);
+  }
+  std::vector<int> scratch_used;
+  std::vector<V3> scratch_v;
 
   // weld near-coincident vertices, drop degenerate faces and unused vertices
   void compact() {
@@ -265,6 +281,7 @@ void make_cell(const double* pts, int n, const KdTree& kd, int i, CellOut& out) 
       heap.push_back({kd.mind2(nd.right, s), nd.right}); std::push_heap(heap.begin(), heap.end(), cmp);
     }
   }
+  P.compact();
   out.v.resize(P.v.size());
   for (size_t k = 0; k < P.v.size(); ++k) out.v[k] = add(s, P.v[k]);
   out.f = P.f; out.fn = P.fn; out.nb = P.nb;

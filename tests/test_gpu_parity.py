@@ -59,10 +59,13 @@ def test_uniform4096_mass_conservation(uniform4096):
     assert np.max(np.abs(tot[interior] - 1)) < 1e-6
 
 
-def test_solve_h_uniform4096(uniform4096):
+@pytest.mark.parametrize("precision,tol", [(0, 1e-9), (1, 1e-6)])
+def test_solve_h_uniform4096(uniform4096, precision, tol):
+    """FP64 build: Newton to 1e-10 in FP64 sums.  Mixed build: FP32 sums on
+    hi/lo-split coordinates, Newton to 1e-6, h to ~1e-7 relative."""
     p, g, h_ref, route_ref, _ = uniform4096
     L = lib()
-    ctx = L.map_init(L.map_config_default(precision=0))
+    ctx = L.map_init(L.map_config_default(precision=precision))
     try:
         x, y, z, m, hh = dev_particles(p)
         route = __import__("torch").empty(p.n, dtype=__import__("torch").int32, device="cuda")
@@ -72,7 +75,7 @@ def test_solve_h_uniform4096(uniform4096):
     finally:
         L.map_destroy(ctx)
     assert np.array_equal(r, route_ref)
-    assert np.max(np.abs(h / h_ref - 1)) < 1e-9
+    assert np.max(np.abs(h / h_ref - 1)) < tol
 
 
 @pytest.fixture(scope="module")
