@@ -104,26 +104,32 @@ class ClockSampler:
 
 
 # Algorithmic operation model of the pair-integral kernel (per counted unit):
-# (FP32-pipe ops, MUFU ops).  See the design doc for the derivation.
+# (FP32-pipe ops, MUFU ops), counted from the formulas as written, with an
+# IEEE divide = 1 MUFU + 8, sqrt = 1 MUFU + 3, atan/atan2 = 1 MUFU + 18-22,
+# asinh = 2 MUFU + 20.  See the design doc for the derivation.
 OPS = {
-    "face_tests": (6, 0),
-    "edge_records": (11, 0),
-    "edge_terms": (15, 3),
-    "inner_evals": (92, 6),
-    "mid_intervals_mixed": (161, 20),
-    "mid_intervals_fp64": (184, 12),  # two closed-form evaluations
+    "face_tests": (6, 0),            # r0 = d'/h - n.y, side, |.|
+    "edge_records": (11, 0),         # R0, along-edge a_a, a_b, side
+    "edge_terms": (15, 2),           # c^2, s2, s1, clamps (split_edge)
+    "inner_evals": (96, 6),          # one antiderivative: U, Omega, L, P2..P5
+    "mid_intervals_mixed": (200, 14),  # 6-node Gauss-Legendre panel + setup + kappa dPhi
+    "mid_split_mixed": (200, 14),    # the second piece of an interval split at the foot
+    "mid_intervals_fp64": (240, 14),  # two closed-form evaluations + kappa dPhi
+    "outer_intervals": (45, 2),      # -c0 dPhi (both branches of c0 evaluated)
 }
 
 
 def algorithmic_ops(work: dict, terms: int, mixed: bool):
     f = m = 0
-    for key, cnt in (("face_tests", work["face_tests"]), ("edge_records", work["edge_records"]),
-                     ("edge_terms", terms), ("inner_evals", work["inner_evals"])):
+    units = [("face_tests", work["face_tests"]), ("edge_records", work["edge_records"]),
+             ("edge_terms", terms), ("inner_evals", work["inner_evals"]),
+             ("outer_intervals", work["outer_intervals"]),
+             ("mid_intervals_mixed" if mixed else "mid_intervals_fp64", work["mid_intervals"])]
+    if mixed:
+        units.append(("mid_split_mixed", work["mid_split"]))
+    for key, cnt in units:
         f += OPS[key][0] * cnt
         m += OPS[key][1] * cnt
-    k = "mid_intervals_mixed" if mixed else "mid_intervals_fp64"
-    f += OPS[k][0] * work["mid_intervals"]
-    m += OPS[k][1] * work["mid_intervals"]
     return f, m
 
 

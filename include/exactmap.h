@@ -47,7 +47,8 @@ typedef struct {
   double hfact;                      /* h = hfact n^(-1/3), Eq. (7); default 1.2 */
   int leaf_size;                     /* octree leaf capacity; default 16 */
   int ngb_bruteforce_max;            /* Section III-D: k_mid neighbour search above this many nodes; default 10000 */
-  int autotune;                      /* reserved: 1 = choose launch shapes by measurement */
+  int autotune;                      /* 1: map_batch times the pair-integral kernel's launch shapes on the
+                                        context's first mixed batch and keeps the fastest; default 0 */
   unsigned long long queue_timeout_ns; /* bound on any device-side wait; default 2e9 */
 } map_config;
 
@@ -170,12 +171,14 @@ int map_copy_pairs(map_ctx* ctx, int64_t* pair_off, int32_t* pair_idx, double* p
 /* Statistics of the last mapping call; synchronises its stream. */
 int map_get_stats(map_ctx* ctx, map_stats* stats);
 
-/* Work tally of the last mapping call, read by the last map_get_stats():
- * counts[0] face tests, counts[1] edge records read, counts[2] inner-piece
- * antiderivative evaluations, counts[3] middle-piece intervals (all per
- * pair, summed).  *launches: kernels this context has launched so far (its
- * own kernels; library sort/scan primitives not counted).  These feed the
- * algorithmic operation count of the roofline. */
+/* Work tally of the last mapping call, read by the last map_get_stats().
+ * counts must hold 6 entries: [0] face tests, [1] edge records read,
+ * [2] inner-piece antiderivative evaluations, [3] middle-piece intervals,
+ * [4] beyond-the-support intervals, [5] middle intervals of the mixed build
+ * split at the foot (a second Gauss-Legendre panel); all per pair, summed.
+ * *launches: kernels this context has launched so far (its own kernels;
+ * library sort/scan primitives not counted).  These feed the algorithmic
+ * operation count of the roofline. */
 int map_get_work(map_ctx* ctx, int64_t* counts, int64_t* launches);
 
 /* Device time (ms, CUDA events on the call's stream) of the most recent
@@ -183,6 +186,31 @@ int map_get_work(map_ctx* ctx, int64_t* counts, int64_t* launches);
  * pair-integral kernel (all of the last map_particles_to_cells), ms[3] the
  * last solve_h.  -1 for a phase not yet run.  Waits for those events. */
 int map_get_timing(map_ctx* ctx, float* ms);
+
+/* ------------------------------------------------------------ batches */
+
+/* Map nsnap independent snapshots (configuration: many uneven instances in
+ * one persistent launch).  Snapshot j is the particle set parts[j] (m, h
+ * given) on the resident grid grids[j], with outputs outs[j], exactly as in
+ * map_particles_to_cells; every snapshot's result equals what that call
+ * gives.  Octree and pair list are built snapshot by snapshot (synchronising
+ * the stream); the pair integrals of all snapshots then run in ONE launch of
+ * the persistent kernel, whose device work queue hands out the cells of every
+ * snapshot, largest pair count first.  That launch, with its descriptor
+ * upload and the per-snapshot sums, is captured in a CUDA graph and replayed
+ * while the batch's pointers and sizes are unchanged.  totals (optional,
+ * device, nsnap doubles) receives sum_i M_i per snapshot.  Per-pair fractions
+ * are not kept (map_get_pairs / map_copy_pairs then report no list);
+ * map_get_stats covers the whole batch.  The batch runs on a stream of the
+ * context, ordered after and before the given stream by events.
+ * Errors: MAP_EINVAL, MAP_EHANDLE, MAP_ENOMEM, MAP_ECUDA. */
+int map_batch(map_ctx* ctx, int nsnap, const map_particles* parts, const int* grids, const map_outputs* outs,
+              double* totals, void* stream);
+
+/* The autotuner's state: *chosen = launch shape in use for the mixed build,
+ * ms[0..*nvariants) = its timing of each shape on the tuning batch (0 when
+ * not run).  ms must hold at least 8 floats. */
+int map_get_autotune(map_ctx* ctx, int* chosen, float* ms, int* nvariants);
 
 /* ------------------------------------------------------------ smoothing lengths (Section III-C, Eq. 7-9) */
 

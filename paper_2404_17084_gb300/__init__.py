@@ -85,8 +85,13 @@ _lib.solve_h.argtypes = [_P, ctypes.POINTER(map_particles), _P, _P]
 _lib.build_pseudo_particles.argtypes = [_P, ctypes.POINTER(map_particles), ctypes.POINTER(ctypes.c_double),
                                         ctypes.c_int, ctypes.POINTER(map_particles), _P, _P,
                                         ctypes.POINTER(_I64), _P]
+_lib.map_batch.argtypes = [_P, ctypes.c_int, ctypes.POINTER(map_particles), ctypes.POINTER(ctypes.c_int),
+                           ctypes.POINTER(map_outputs), _P, _P]
+_lib.map_get_autotune.argtypes = [_P, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_float),
+                                  ctypes.POINTER(ctypes.c_int)]
 for _name in ("map_init", "map_grid_upload", "map_grid_release", "map_grid_volumes", "map_particles_to_cells",
-              "map_get_pairs", "map_copy_pairs", "map_get_stats", "map_get_work", "map_get_timing", "solve_h", "build_pseudo_particles"):
+              "map_get_pairs", "map_copy_pairs", "map_get_stats", "map_get_work", "map_get_timing", "solve_h",
+              "build_pseudo_particles", "map_batch", "map_get_autotune"):
     getattr(_lib, _name).restype = ctypes.c_int
 
 
@@ -170,6 +175,28 @@ def map_particles_to_cells(ctx, p: map_particles, handle: int, cell_mass, cell_r
            "map_particles_to_cells")
 
 
+def map_batch(ctx, parts, handles, cell_mass, cell_rho=None, cell_vol=None, totals=None, stream=None) -> None:
+    """Map len(parts) snapshots in one batched launch: parts[j] (map_particles)
+    on resident grid handles[j], writing cell_mass[j] (and cell_rho[j],
+    cell_vol[j] when given); totals: optional CUDA float64 tensor of
+    len(parts) receiving sum_i M_i per snapshot."""
+    n = len(parts)
+    P = (map_particles * n)(*parts)
+    H = (ctypes.c_int * n)(*handles)
+    O = (map_outputs * n)(*[map_outputs(_ptr(cell_mass[j]), _ptr(cell_rho[j]) if cell_rho else None,
+                                        _ptr(cell_vol[j]) if cell_vol else None) for j in range(n)])
+    _check(_lib.map_batch(ctx, n, P, H, O, _ptr(totals), _stream(stream)), "map_batch")
+
+
+def map_get_autotune(ctx):
+    """(chosen launch shape, [ms per shape]) of the context's autotuner."""
+    c = ctypes.c_int()
+    nv = ctypes.c_int()
+    ms = (ctypes.c_float * 8)()
+    _check(_lib.map_get_autotune(ctx, ctypes.byref(c), ms, ctypes.byref(nv)), "map_get_autotune")
+    return c.value, [ms[i] for i in range(nv.value)]
+
+
 def map_get_pairs(ctx):
     """(pair_off_ptr, pair_idx_ptr, pair_frac_ptr, n_pairs) of the last call (context-owned)."""
     a, b, c = ctypes.c_void_p(), ctypes.c_void_p(), ctypes.c_void_p()
@@ -198,10 +225,11 @@ def map_get_stats(ctx) -> map_stats:
 
 def map_get_work(ctx):
     """(dict of per-class work counts of the last mapping call, kernel launches so far)."""
-    arr = (_I64 * 4)()
+    arr = (_I64 * 6)()
     nl = _I64()
     _check(_lib.map_get_work(ctx, arr, ctypes.byref(nl)), "map_get_work")
-    return dict(face_tests=arr[0], edge_records=arr[1], inner_evals=arr[2], mid_intervals=arr[3]), nl.value
+    return dict(face_tests=arr[0], edge_records=arr[1], inner_evals=arr[2], mid_intervals=arr[3],
+                outer_intervals=arr[4], mid_split=arr[5]), nl.value
 
 
 def map_get_timing(ctx):

@@ -20,6 +20,8 @@ __global__ void validate_particles(int64_t n, const double* __restrict__ x, cons
 
 inline cudaStream_t S(void* s) { return reinterpret_cast<cudaStream_t>(s); }
 
+}  // namespace
+
 int check_particles(map_ctx* ctx, const map_particles* p, bool need_m, bool need_h, cudaStream_t s) {
   if (!p || p->n <= 0 || !p->x || !p->y || !p->z) return MAP_EINVAL;
   if (need_m && !p->m) return MAP_EINVAL;
@@ -34,8 +36,6 @@ int check_particles(map_ctx* ctx, const map_particles* p, bool need_m, bool need
   CUDA_TRY(cudaStreamSynchronize(s));
   return ctx->h_scratch[0] ? MAP_EINVAL : MAP_OK;
 }
-
-}  // namespace
 
 int ctx_ensure(map_ctx* ctx, DevBuf& b, size_t bytes) {
   if (b.cap >= bytes) return MAP_OK;
@@ -140,6 +140,11 @@ void map_destroy(map_ctx* ctx) {
   if (ctx->h_stats) cudaFreeHost(ctx->h_stats);
   if (ctx->h_scratch) cudaFreeHost(ctx->h_scratch);
   for (auto& e : ctx->ev) if (e) cudaEventDestroy(e);
+  for (auto& b : ctx->batch_off) if (b.p) cudaFree(b.p);
+  for (auto& b : ctx->batch_idx) if (b.p) cudaFree(b.p);
+  if (ctx->bexec) cudaGraphExecDestroy(ctx->bexec);
+  for (auto& e : ctx->bev) if (e) cudaEventDestroy(e);
+  if (ctx->bstream) cudaStreamDestroy(ctx->bstream);
   delete ctx;
 }
 
@@ -246,7 +251,7 @@ int map_get_stats(map_ctx* ctx, map_stats* st) {
   st->n_fp64_terms = (int64_t)c[2];
   st->total_mass = tot;
   st->status = c[0] ? MAP_EINVAL : MAP_OK;
-  for (int k = 0; k < 4; ++k) ctx->last_work[k] = (int64_t)c[8 + k];
+  for (int k = 0; k < 6; ++k) ctx->last_work[k] = (int64_t)c[8 + k];
   return MAP_OK;
 }
 
@@ -265,7 +270,7 @@ int map_get_timing(map_ctx* ctx, float* ms) {
 int map_get_work(map_ctx* ctx, int64_t* counts, int64_t* launches) {
   if (!ctx) return MAP_EINVAL;
   if (counts)
-    for (int k = 0; k < 4; ++k) counts[k] = ctx->last_work[k];
+    for (int k = 0; k < 6; ++k) counts[k] = ctx->last_work[k];
   if (launches) *launches = ctx->launches;
   return MAP_OK;
 }

@@ -1,0 +1,211 @@
+// Batched mapping: many independent snapshots (particle set + resident grid)
+// in one persistent pair-integral launch.
+//
+// Each snapshot's octree and pair list are built in turn (these steps size
+// their buffers from device counts, so they synchronise the stream).  The
+// pair lists are written to per-snapshot buffers of the context, reused by
+// later batches of the same shape.  The pair
+// integrals of every snapshot then run in ONE launch of the persistent
+// kernel: its device work queue hands out the cells of all snapshots, the
+// snapshots laid out largest pair count first (longest-processing-time
+// order), so that the last cells handed out are those of the smallest
+// snapshots and the tail of the launch is short.  The descriptor upload, the
+// launch and the per-snapshot mass sums are captured once in a CUDA graph and
+// replayed while the batch's descriptors are byte-identical.
+//
+// Autotuner: with map_config.autotune set, the first batch of a context in
+// the mixed build runs the integral launch in each of its launch shapes (the
+// register cap per thread, i.e. resident warps per SM, at 4 warps and 4 cells
+// in flight per CTA), times each with CUDA events, and keeps the fastest for
+// every later call of the context.  All shapes compute bit-identical results.
+#include <algorithm>
+#include <cstring>
+#include <numeric>
+
+#include "internal.cuh"
+
+namespace {
+
+__global__ void sum_totals(int n, const double* __restrict__ v, double* out) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) {
+    double t = 0.0;
+    for (int i = 0; i < n; ++i) t += v[i];
+    *out = t;
+  }
+}
+
+int ensure_stream(map_ctx* ctx) {
+  if (!ctx->bstream) CUDA_TRY(cudaStreamCreateWithFlags(&ctx->bstream, cudaStreamNonBlocking));
+  for (auto& e : ctx->bev)
+    if (!e) CUDA_TRY(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+  return MAP_OK;
+}
+
+// Times each launch shape of the integral kernel on this batch (descriptors
+// already on the device) and records the fastest.
+int autotune(map_ctx* ctx, const BatchArgs& B, cudaStream_t s) {
+  cudaEvent_t e0, e1;
+  CUDA_TRY(cudaEventCreate(&e0));
+  CUDA_TRY(cudaEventCreate(&e1));
+  int best = 0;
+  float best_ms = 0.f;
+  int rc = MAP_OK;
+  for (int v = 0; v < N_VARIANTS && rc == MAP_OK; ++v) {
+    cudaEventRecord(e0, s);
+    rc = integrals_enqueue(ctx, B, v, s);
+    cudaEventRecord(e1, s);
+    if (rc != MAP_OK) break;
+    if (cudaEventSynchronize(e1) != cudaSuccess) { rc = MAP_ECUDA; break; }
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    ctx->tune_ms[v] = ms;
+    if (v == 0 || ms < best_ms) { best = v; best_ms = ms; }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (rc != MAP_OK) return rc;
+  ctx->tuned[MAP_MIXED] = best;
+  ctx->tune_done[MAP_MIXED] = true;
+  return MAP_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int map_batch(map_ctx* ctx, int nsnap, const map_particles* parts, const int* grids, const map_outputs* outs,
+              double* totals, void* stream) {
+  if (!ctx || nsnap < 1 || !parts || !grids || !outs) return MAP_EINVAL;
+  for (int j = 0; j < nsnap; ++j) {
+    if (grids[j] < 0 || grids[j] >= (int)ctx->grids.size() || !ctx->grids[grids[j]]) return MAP_EHANDLE;
+    if (!outs[j].cell_mass) return MAP_EINVAL;
+  }
+  CUDA_TRY(cudaSetDevice(ctx->device));
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  MAP_TRY(ensure_stream(ctx));
+  if ((int)ctx->batch_off.size() < nsnap) {
+    ctx->batch_off.resize(nsnap);
+    ctx->batch_idx.resize(nsnap);
+  }
+  // 1. octree and pair list per snapshot, kept in the batch slots
+  std::vector<SnapDesc> hd(nsnap);
+  std::vector<int64_t> np(nsnap);
+  int64_t n_pairs = 0, total = 0;
+  phase_begin(ctx, 1, s);
+  for (int j = 0; j < nsnap; ++j) {
+    const map_particles* p = &parts[j];
+    MAP_TRY(check_particles(ctx, p, true, true, s));
+    const PreparedGrid* g = ctx->grids[grids[j]];
+    MAP_TRY(tree_build(ctx, p->x, p->y, p->z, p->m, p->h, p->n, s));
+    // the list goes straight to the snapshot's slot (reused by later batches)
+    MAP_TRY(pairs_build(ctx, g, s, &ctx->batch_off[j], &ctx->batch_idx[j]));
+    hd[j] = make_desc(ctx, g, p, &outs[j], ctx->pair_off, ctx->pair_idx, nullptr, j);
+    np[j] = ctx->n_pairs;
+    n_pairs += np[j];
+    total += g->ncell;
+  }
+  phase_end(ctx, 1, s);
+  ctx->pair_off = nullptr;  // no single pair list describes a batch
+  ctx->pair_idx = nullptr;
+  ctx->pair_frac = nullptr;
+  ctx->n_pairs = n_pairs;
+  ctx->last_ncell = total;
+
+  // 2. longest-processing-time order of the queue
+  std::vector<int> order(nsnap);
+  std::iota(order.begin(), order.end(), 0);
+  std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return np[a] > np[b]; });
+  std::vector<SnapDesc> qd(nsnap);
+  std::vector<int64_t> base(nsnap + 1);
+  base[0] = 0;
+  for (int i = 0; i < nsnap; ++i) {
+    qd[i] = hd[order[i]];
+    base[i + 1] = base[i] + qd[i].ncell;
+  }
+  SnapDesc* d_desc;
+  int64_t* d_base;
+  double* d_tot;
+  MAP_TRY(ensure_t(ctx, ctx->ws_misc[5], nsnap, &d_desc));
+  MAP_TRY(ensure_t(ctx, ctx->ws_misc[6], nsnap + 1, &d_base));
+  MAP_TRY(ensure_t(ctx, ctx->ws_misc[7], nsnap, &d_tot));
+  const BatchArgs B{d_desc, d_base, nsnap, total, ctx->d_counters};
+
+  // 3. the integral launch of the whole batch: ordered after the caller's
+  // stream, on the context's own stream (graphs cannot be captured on the
+  // legacy default stream)
+  CUDA_TRY(cudaEventRecord(ctx->bev[0], s));
+  CUDA_TRY(cudaStreamWaitEvent(ctx->bstream, ctx->bev[0], 0));
+  const int prec = ctx->cfg.precision == MAP_MIXED ? MAP_MIXED : MAP_FP64;
+  if (ctx->cfg.autotune && prec == MAP_MIXED && !ctx->tune_done[MAP_MIXED]) {
+    MAP_TRY(integrals_upload(ctx, qd.data(), base.data(), nsnap, d_desc, d_base, ctx->bstream));
+    MAP_TRY(autotune(ctx, B, ctx->bstream));
+  }
+  const int variant = ctx->tuned[prec];
+  // graph signature: descriptor bytes, queue layout, launch shape, targets
+  std::vector<unsigned char> sig(sizeof(SnapDesc) * nsnap + sizeof(int64_t) * (nsnap + 1) + 4 * sizeof(void*));
+  {
+    unsigned char* q = sig.data();
+    std::memcpy(q, qd.data(), sizeof(SnapDesc) * nsnap);
+    q += sizeof(SnapDesc) * nsnap;
+    std::memcpy(q, base.data(), sizeof(int64_t) * (nsnap + 1));
+    q += sizeof(int64_t) * (nsnap + 1);
+    const void* extra[4] = {d_desc, d_base, d_tot, reinterpret_cast<const void*>((intptr_t)(variant * 2 + prec))};
+    std::memcpy(q, extra, sizeof(extra));
+  }
+  if (!ctx->bexec || sig != ctx->bsig) {
+    if (ctx->bexec) {
+      CUDA_TRY(cudaGraphExecDestroy(ctx->bexec));
+      ctx->bexec = nullptr;
+    }
+    const int64_t l0 = ctx->launches;
+    CUDA_TRY(cudaStreamBeginCapture(ctx->bstream, cudaStreamCaptureModeThreadLocal));
+    int rc = integrals_upload(ctx, qd.data(), base.data(), nsnap, d_desc, d_base, ctx->bstream);
+    if (rc == MAP_OK) rc = integrals_enqueue(ctx, B, variant, ctx->bstream);
+    if (rc == MAP_OK) rc = integrals_sum(ctx, d_desc, nsnap, d_tot, ctx->bstream);
+    cudaGraph_t graph = nullptr;
+    const cudaError_t ce = cudaStreamEndCapture(ctx->bstream, &graph);
+    if (rc != MAP_OK || ce != cudaSuccess) {
+      if (graph) cudaGraphDestroy(graph);
+      cudaGetLastError();
+      return rc != MAP_OK ? rc : MAP_ECUDA;
+    }
+    const cudaError_t ie = cudaGraphInstantiate(&ctx->bexec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (ie != cudaSuccess) {
+      ctx->bexec = nullptr;
+      cudaGetLastError();
+      return MAP_ECUDA;
+    }
+    ctx->bexec_launches = ctx->launches - l0;
+    ctx->launches = l0;
+    ctx->bsig.swap(sig);
+  }
+  phase_begin(ctx, 2, ctx->bstream);
+  CUDA_TRY(cudaGraphLaunch(ctx->bexec, ctx->bstream));
+  phase_end(ctx, 2, ctx->bstream);
+  ctx->launches += ctx->bexec_launches;
+  sum_totals<<<1, 32, 0, ctx->bstream>>>(nsnap, d_tot, ctx->d_total); ++ctx->launches;
+  CUDA_TRY(cudaGetLastError());
+  if (totals) CUDA_TRY(cudaMemcpyAsync(totals, d_tot, nsnap * sizeof(double), cudaMemcpyDeviceToDevice, ctx->bstream));
+  for (int j = 0; j < nsnap; ++j)
+    if (outs[j].cell_vol) {
+      const PreparedGrid* g = ctx->grids[grids[j]];
+      CUDA_TRY(cudaMemcpyAsync(outs[j].cell_vol, g->vol, g->ncell * sizeof(double), cudaMemcpyDeviceToDevice,
+                               ctx->bstream));
+    }
+  CUDA_TRY(cudaEventRecord(ctx->bev[1], ctx->bstream));
+  CUDA_TRY(cudaStreamWaitEvent(s, ctx->bev[1], 0));
+  ctx->last_stream = s;
+  return MAP_OK;
+}
+
+int map_get_autotune(map_ctx* ctx, int* chosen, float* ms, int* nvariants) {
+  if (!ctx) return MAP_EINVAL;
+  if (chosen) *chosen = ctx->tuned[MAP_MIXED];
+  if (ms)
+    for (int v = 0; v < N_VARIANTS; ++v) ms[v] = ctx->tune_ms[v];
+  if (nvariants) *nvariants = N_VARIANTS;
+  return MAP_OK;
+}
+
+}  // extern "C"

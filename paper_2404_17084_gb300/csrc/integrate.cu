@@ -1,28 +1,29 @@
 // Pair integrals and cell sums (Section II-B, Eq. 1-3).
 //
-// Persistent kernel: each CTA pulls cells from a device work queue and stages
-// the cell's site-relative face planes and edge records in shared memory.
-// Each warp then takes the cell's pairs 32 at a time, one pair per lane,
-// independently of the other warps, in three phases per chunk of ECH
-// directed edges:
+// Persistent kernel, one warp per cell at a time: a warp pulls a cell from a
+// device work queue and takes the cell's pairs 32 at a time, one pair per
+// lane.  Warps share nothing and never wait for one another.  The cell's
+// site-relative face planes and edge records are read straight from global
+// memory: every lane reads the same record, so each read is one broadcast
+// transaction, served from L1 after the first block of pairs.
 //
-//  phase 1 (per thread = pair): for each edge of the chunk compute r0 (face),
-//    R0 and the along-edge coordinates of the vertices, update the inside
-//    flag, and QUEUE each piece of the edge integral K'_e -- at most one
-//    inner piece, two middle pieces and two pieces beyond the support -- as
-//    (r0, R0, lo, hi); the sign s_f s_e is folded into the interval direction.
-//    (Mixed build: a face whose plane passes within 1e-4 h of the particle is
-//    decided and evaluated in FP64 in this thread instead.)
-//  phase 2 (whole warp): evaluate the queued pieces kind by kind, every lane
-//    running the same code, each result written to its piece's slot;
-//  phase 3 (per lane): sum the lane's own piece results in a fixed order
-//    (compensated), so that every result is bit-reproducible.
-// Only __syncwarp separates the phases; CTA barriers fall at cell boundaries.
+// For each face (r0 from the plane; the inside flag) and each directed edge
+// of it (R0 and the along-edge coordinates of the vertices), every lane splits
+// its edge integral K'_e into pieces -- at most one inner piece, two middle
+// pieces and two pieces beyond the support -- as (r0, R0, lo, hi), the sign
+// s_f s_e folded into the interval direction, and pushes them onto three
+// per-warp stacks, one per kind.  Whenever a stack holds 32 pieces the whole
+// warp evaluates them together (every lane the same code), so the costly
+// evaluations run with all lanes busy; the stacks carry over from edge to
+// edge and are flushed after the last face.  Each result is added to its
+// owner lane's FP64 accumulator, lanes with the same owner in turn, so the
+// order of additions is fixed and every result is bit-reproducible.
+// (Mixed build: a face whose plane passes within 1e-4 h of the particle is
+// decided and evaluated in FP64 by the owner lane instead.)
 //
-// Without the queue, lanes (different particles) branch into different
-// pieces and a warp runs every path with a few lanes active (measured 5.3 of
-// 32).  Per pair: f_ai = [inside] + sum_f sum_e s_f s_e K'_e (see wedge.cuh).  M_i = sum_a m_a f_ai is accumulated in
-// FP64 and reduced across the CTA; rho_i = M_i / V_i.
+// Per pair: f_ai = [inside] + sum_f sum_e s_f s_e K'_e (see wedge.cuh).
+// M_i = sum_a m_a f_ai is accumulated in FP64 and reduced across the warp;
+// rho_i = M_i / V_i.
 #include <cub/cub.cuh>
 
 #include "internal.cuh"
@@ -33,36 +34,18 @@ namespace {
 template <typename T> struct Vec4;
 template <> struct Vec4<float> { typedef float4 type; };
 template <> struct Vec4<double> { typedef double4_32a type; };
-template <typename T> struct Vec2;
-template <> struct Vec2<float> { typedef float2 type; };
-template <> struct Vec2<double> { typedef double2 type; };
 
-struct IntegralArgs {
-  int64_t ncell;
-  const int64_t* cfo;
-  const int64_t* fvo;
-  const double* site;
-  const double* vol;
-  const int64_t* pair_off;
-  const int32_t* pair_idx;
-  const double *x, *y, *z, *m, *h;
-  double* frac;
-  double* cell_mass;
-  double* cell_rho;
-  unsigned long long* counters;  // [1] edge terms, [2] FP64 terms, [3] work queue, [8..11] work tally
-  const double4_32a* face64;     // FP64 geometry for the near-degenerate fallback of the mixed build
-  const double* edge64;
-};
-
-// Mixed build: a face whose plane, or an edge whose line, passes within TAU
-// (in units of h) of the particle (resp. its projection) is evaluated in FP64:
-// FP32 rounding (~1e-7 h) could otherwise give inconsistent signs to a plane
-// seen from two faces.  Exact zeros (particle exactly on a plane or edge line)
-// are moved to +EPS on the inner side in both builds: the integral is
-// continuous in the particle position, and treating every exact zero as
-// 'inside' is one consistent displacement of the particle into the cell.
+// Mixed build: a face whose plane passes within TAU (in units of h) of the
+// particle is evaluated in FP64: FP32 rounding (~1e-7 h) could otherwise give
+// inconsistent signs to a plane seen from two faces.  Exact zeros (particle
+// exactly on a plane or edge line) are moved to +EPS on the inner side in the
+// FP64 build: the integral is continuous in the particle position, and
+// treating every exact zero as 'inside' is one consistent displacement of the
+// particle into the cell.
 constexpr float TAU = 1e-4f;
 constexpr double EPS = 1e-12;
+constexpr unsigned FULL = 0xffffffffu;
+constexpr int LCAP = 96;  // stack depth: < 32 left after a drain + up to 2 pieces per lane
 
 // Exclusive warp prefix sum of v; returns the warp total in *tot.
 __device__ __forceinline__ int warp_excl(int v, int* tot) {
@@ -70,80 +53,127 @@ __device__ __forceinline__ int warp_excl(int v, int* tot) {
   int s = v;
 #pragma unroll
   for (int o = 1; o < 32; o <<= 1) {
-    int t = __shfl_up_sync(0xffffffffu, s, o);
+    const int t = __shfl_up_sync(FULL, s, o);
     if (lane >= o) s += t;
   }
-  *tot = __shfl_sync(0xffffffffu, s, 31);
+  *tot = __shfl_sync(FULL, s, 31);
   return s - v;
 }
 
-// Per-warp work area in shared memory for one chunk of ECH edges: every lane
-// owns fixed slots -- (r0, R0) per edge, (lo, hi) and a result per piece (5
-// pieces per edge: 1 inner, 2 middle, 2 beyond the support) -- and three
-// compact lists name the occupied slots of each kind.
-template <typename T, int ECH>
-struct WarpArea {
-  typename Vec2<T>::type rr[ECH][32];     // (r0, R0) per (edge, lane)
-  typename Vec2<T>::type lh[ECH * 5][32]; // (lo, hi) per (piece slot, lane)
-  T res[ECH * 5][32];                     // piece results
-  unsigned short q[3][ECH * 64];          // occupied slots: inner, middle, beyond
+// Per-warp piece stacks (inner, middle, beyond the support) and the lanes'
+// FP64 accumulators.
+template <typename T>
+struct WarpStacks {
+  typename Vec4<T>::type e[3][LCAP];  // (r0, R0, lo, hi)
+  unsigned char own[3][LCAP];         // owner lane
+  double acc[32];
+  SnapDesc d;                         // the snapshot of the warp's current cell
 };
 
-template <typename T, bool MIXED, int NT, int ECH>
-__global__ void __launch_bounds__(NT, 4) pair_integrals(IntegralArgs A, const typename Vec4<T>::type* __restrict__ face,
-                                                     const T* __restrict__ edge, int smem_faces, int smem_loops) {
+// Evaluates the queued pieces: every stack holding 32 or more (all that is
+// left when flush), 32 at a time from the top, and adds each result to its
+// owner lane's accumulator.  Not inlined: the three evaluators then appear
+// once in the kernel's code.
+template <typename T, bool MIXED>
+__device__ __noinline__ void drain(WarpStacks<T>& S, int& cnt0, int& cnt1, int& cnt2, bool flush,
+                                   unsigned long long& t0, unsigned long long& t1, unsigned long long& t2) {
+  const int lane = threadIdx.x & 31;
+  for (;;) {
+    int K, n;
+    if (cnt1 >= 32 || (flush && cnt1 > 0)) { K = 1; n = cnt1 < 32 ? cnt1 : 32; cnt1 -= n; t1 += n; }
+    else if (cnt0 >= 32 || (flush && cnt0 > 0)) { K = 0; n = cnt0 < 32 ? cnt0 : 32; cnt0 -= n; t0 += n; }
+    else if (cnt2 >= 32 || (flush && cnt2 > 0)) { K = 2; n = cnt2 < 32 ? cnt2 : 32; cnt2 -= n; t2 += n; }
+    else break;
+    const int base = K == 0 ? cnt0 : (K == 1 ? cnt1 : cnt2);
+    const bool on = lane < n;
+    T v = T(0);
+    int o = 32 + lane;  // a key no owner has, for idle lanes
+    if (on) {
+      const typename Vec4<T>::type P = S.e[K][base + lane];
+      o = S.own[K][base + lane];
+      if (K == 1) v = wedge::piece_mid<T, MIXED>(P.x, P.y, P.z, P.w);
+      else if (K == 0) v = wedge::piece_inner<T>(P.x, P.y, P.z, P.w);
+      else v = wedge::piece_outer<T>(P.x, P.y, P.z, P.w);
+    }
+    // lanes holding pieces of the same owner add in turn, in lane order
+    const unsigned grp = __match_any_sync(FULL, o);
+    const int rank = __popc(grp & ((1u << lane) - 1u));
+    for (int r = 0;; ++r) {
+      const bool mine = on && rank == r;
+      if (!__any_sync(FULL, mine)) break;
+      if (mine) S.acc[o] += (double)v;
+      __syncwarp();
+    }
+  }
+}
+
+// Mixed build, a face whose plane passes within TAU of the particle: decide
+// the side and evaluate every edge of the face in FP64 in this lane.
+__device__ __noinline__ double face_fp64(const SnapDesc& A, int64_t f, int64_t kb, int64_t ke, int64_t l0,
+                                         int32_t a, double sx, double sy, double sz, bool& fin, int& n64) {
+  const double hh = 1.0 / A.h[a];
+  const double ydx = (A.x[a] - sx) * hh, ydy = (A.y[a] - sy) * hh, ydz = (A.z[a] - sz) * hh;
+  const double4_32a G = A.face64[f];
+  const double rs = G.w * hh - (G.x * ydx + G.y * ydy + G.z * ydz);
+  fin = rs >= 0.0;
+  const double r0d = fabs(rs) > EPS ? fabs(rs) : EPS;
+  double acc = 0.0;
+  for (int64_t kk = kb; kk < ke; ++kk) {
+    const double* D = A.edge64 + (l0 + kk) * EDGE_STRIDE;
+    const double R0sd = (D[0] * ydx + D[1] * ydy + D[2] * ydz) - D[3] * hh;
+    const double based = D[4] * ydx + D[5] * ydy + D[6] * ydz;
+    const bool eind = R0sd >= 0.0;
+    const double R0d = fabs(R0sd) > EPS ? fabs(R0sd) : EPS;
+    wedge::WorkCount wcd;
+    const double K = wedge::kprime_edge<double, false>(r0d, R0d, D[7] * hh - based, D[8] * hh - based, wcd);
+    acc += (fin == eind) ? K : -K;
+    ++n64;
+  }
+  return acc;
+}
+
+template <typename T, bool MIXED, int NW, int MINB>
+__global__ void __launch_bounds__(NW * 32, MINB) pair_integrals(BatchArgs B) {
   typedef typename Vec4<T>::type V4;
-  typedef typename Vec2<T>::type V2;
-  constexpr int NW = NT / 32;
-  extern __shared__ __align__(128) unsigned char smem[];
-  WarpArea<T, ECH>* areas = reinterpret_cast<WarpArea<T, ECH>*>(smem);
-  unsigned char* geo = smem + sizeof(WarpArea<T, ECH>) * NW;
-  geo = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(geo) + 127) & ~uintptr_t(127));
-  V4* s_face = reinterpret_cast<V4*>(geo);
-  T* s_edge = reinterpret_cast<T*>(geo + sizeof(V4) * smem_faces);
-  int* s_floop = reinterpret_cast<int*>(geo + sizeof(V4) * smem_faces + sizeof(T) * EDGE_STRIDE * smem_loops);
-  unsigned short* s_fidx = reinterpret_cast<unsigned short*>(s_floop + smem_faces + 1);
-
-  __shared__ int64_t s_cell;
-  __shared__ unsigned long long s_work[8];
-  typedef cub::BlockReduce<double, NT> BR;
-  __shared__ typename BR::TempStorage s_br;
-
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  WarpArea<T, ECH>& W = areas[warp];
-  if (tid < 8) s_work[tid] = 0;
-  wedge::WorkCount wc, wcd;
+  __shared__ WarpStacks<T> stacks[NW];
+  const int lane = threadIdx.x & 31;
+  WarpStacks<T>& S = stacks[threadIdx.x >> 5];
+  const SnapDesc& A = S.d;
+  wedge::WorkCount wc;
+  unsigned long long n_in = 0, n_mid = 0, n_out = 0;
   int n64 = 0;
-  unsigned long long n_in_tot = 0, n_mid_tot = 0, n_out_tot = 0;
+  unsigned n_split = 0;  // middle intervals split at the foot (counted once, evaluated as two pieces)
+  int cur = -1;          // snapshot held in S.d
 
   for (;;) {
-    __syncthreads();
-    if (tid == 0) s_cell = (int64_t)atomicAdd(&A.counters[3], 1ULL);
-    __syncthreads();
-    const int64_t c = s_cell;
-    if (c >= A.ncell) break;
+    int64_t g = 0;
+    if (lane == 0) g = (int64_t)atomicAdd(&B.counters[3], 1ULL);
+    g = __shfl_sync(FULL, g, 0);
+    if (g >= B.total) break;
+    // the snapshot owning queue position g: last j with cell_base[j] <= g
+    int jl = 0, jh = B.nsnap - 1;
+    while (jl < jh) {
+      const int jm = (jl + jh + 1) >> 1;
+      if (B.cell_base[jm] <= g) jl = jm; else jh = jm - 1;
+    }
+    if (jl != cur) {
+      __syncwarp();
+      const unsigned long long* src = reinterpret_cast<const unsigned long long*>(B.snaps + jl);
+      unsigned long long* dst = reinterpret_cast<unsigned long long*>(&S.d);
+      for (int i = lane; i < (int)(sizeof(SnapDesc) / 8); i += 32) dst[i] = src[i];
+      __syncwarp();
+      cur = jl;
+    }
+    const int64_t c = g - B.cell_base[jl];
+    const V4* __restrict__ face = reinterpret_cast<const V4*>(A.face);
+    const T* __restrict__ edge = reinterpret_cast<const T*>(A.edge);
     const int64_t f0 = A.cfo[c];
     const int nf = (int)(A.cfo[c + 1] - f0);
     const int64_t l0 = A.fvo[f0];
-    const int nl = (int)(A.fvo[f0 + nf] - l0);
-    if (!(nf <= smem_faces && nl <= smem_loops)) continue;  // mapped by pair_integrals_large
-    for (int i = tid; i <= nf; i += NT) s_floop[i] = (int)(A.fvo[f0 + i] - l0);
-    for (int i = tid; i < nf; i += NT) s_face[i] = face[f0 + i];
-    {
-      const int ne = nl * EDGE_STRIDE;
-      const T* src = edge + l0 * EDGE_STRIDE;
-      for (int i = tid; i < ne; i += NT) s_edge[i] = src[i];
-    }
-    __syncthreads();
-    for (int fi = tid; fi < nf; fi += NT)
-      for (int k = s_floop[fi]; k < s_floop[fi + 1]; ++k) s_fidx[k] = (unsigned short)fi;
-    __syncthreads();
-
     const double sx = A.site[3 * c], sy = A.site[3 * c + 1], sz = A.site[3 * c + 2];
     double macc = 0.0;
     const int64_t pb = A.pair_off[c], pe = A.pair_off[c + 1];
-    // each warp takes 32 pairs at a time; warps proceed independently
-    for (int64_t p0 = pb + warp * 32; p0 < pe; p0 += NT) {
+    for (int64_t p0 = pb; p0 < pe; p0 += 32) {
       const int64_t p = p0 + lane;
       const bool active = p < pe;
       T yx = T(0), yy = T(0), yz = T(0), hinv = T(0);
@@ -165,279 +195,237 @@ __global__ void __launch_bounds__(NT, 4) pair_integrals(IntegralArgs A, const ty
           hinv = hi;
         }
       }
+      S.acc[lane] = 0.0;
       bool inside = true;
       double dacc = 0.0;
-      T fsum = T(0), fcomp = T(0);  // compensated sum of this pair's pieces
-      int cur = -1;
-      T r0 = T(0);
-      bool fin = true, inrange = false;
-      for (int kc = 0; kc < nl; kc += ECH) {
-        // ---------------- phase 1: geometry, fixed slots, compact lists
-        const int kend = min(kc + ECH, nl);
-        unsigned long long mask = 0;  // 5 bits per edge of the chunk
-        int cnt_in = 0, cnt_mid = 0, cnt_out = 0;
-        for (int k = kc; k < kend; ++k) {
-          const int kl = k - kc;
-          const int fi = s_fidx[k];
-          if (fi != cur) {
-            const V4 F = s_face[fi];
-            const T r0s = F.w * hinv - (F.x * yx + F.y * yy + F.z * yz);
-            fin = r0s >= T(0);
-            r0 = fabs(r0s);
-            if (!MIXED) r0 = r0 > T(1e-12) ? r0 : T(1e-12);
-            inrange = active && r0 < T(2);
-            cur = fi;
-            if (active) wc.faces++;
-            if (MIXED && inrange && r0 < T(1e-4)) {
-              // the face plane passes within 1e-4 h of the particle: decide
-              // the side and evaluate the whole face in FP64 in this thread
-              const double hh = 1.0 / A.h[a];
-              const double ydx = (A.x[a] - sx) * hh, ydy = (A.y[a] - sy) * hh, ydz = (A.z[a] - sz) * hh;
-              const double4_32a G = A.face64[f0 + fi];
-              const double rs = G.w * hh - (G.x * ydx + G.y * ydy + G.z * ydz);
-              fin = rs >= 0.0;
-              const double r0d = fabs(rs) > 1e-12 ? fabs(rs) : 1e-12;
-              for (int kk = s_floop[fi]; kk < s_floop[fi + 1]; ++kk) {
-                const double* D = A.edge64 + (l0 + kk) * EDGE_STRIDE;
-                const double R0sd = (D[0] * ydx + D[1] * ydy + D[2] * ydz) - D[3] * hh;
-                const double based = D[4] * ydx + D[5] * ydy + D[6] * ydz;
-                const bool eind = R0sd >= 0.0;
-                const double R0d = fabs(R0sd) > 1e-12 ? fabs(R0sd) : 1e-12;
-                const double K = wedge::kprime_edge<double, false>(r0d, R0d, D[7] * hh - based, D[8] * hh - based, wcd);
-                dacc += (fin == eind) ? K : -K;
-                ++n64;
-              }
-              inrange = false;  // its edges are done
+      int cnt0 = 0, cnt1 = 0, cnt2 = 0;  // stack heights (warp-uniform)
+      int64_t kb = A.fvo[f0] - l0;
+      for (int fi = 0; fi < nf; ++fi) {
+        const V4 F = face[f0 + fi];
+        const int64_t ke = A.fvo[f0 + fi + 1] - l0;
+        const T r0s = F.w * hinv - (F.x * yx + F.y * yy + F.z * yz);
+        bool fin = r0s >= T(0);
+        T r0 = fabs(r0s);
+        if (!MIXED) r0 = r0 > T(EPS) ? r0 : T(EPS);
+        bool inrange = active && r0 < T(2);
+        if (active) wc.faces++;
+        if (MIXED && inrange && r0 < T(TAU)) {
+          int c64 = 0;
+          dacc += face_fp64(A, f0 + fi, kb, ke, l0, a, sx, sy, sz, fin, c64);
+          n64 += c64;
+          inrange = false;  // its edges are done
+        }
+        inside = inside && fin;
+        if (__any_sync(FULL, inrange)) {
+          for (int64_t k = kb; k < ke; ++k) {
+            const T* E = edge + (l0 + k) * EDGE_STRIDE;
+            const T e0 = E[0], e1 = E[1], e2 = E[2], e3 = E[3], e4 = E[4], e5 = E[5], e6 = E[6], e7 = E[7], e8 = E[8];
+            int nin = 0, nmid = 0, nout = 0;
+            T R0 = T(0), il = T(0), ih = T(0), ml0 = T(0), mh0 = T(0), ml1 = T(0), mh1 = T(0);
+            T ol0 = T(0), oh0 = T(0), ol1 = T(0), oh1 = T(0);
+            if (inrange) {
+              const T R0s = (e0 * yx + e1 * yy + e2 * yz) - e3 * hinv;  // m.(p - v_a): > 0 inside
+              const T base = e4 * yx + e5 * yy + e6 * yz;
+              const bool ein = R0s >= T(0);
+              R0 = fabs(R0s);
+              if (!MIXED) R0 = R0 > T(EPS) ? R0 : T(EPS);
+              wc.edges++;
+              wedge::split_edge<T>(
+                  r0, R0, e7 * hinv - base, e8 * hinv - base, fin == ein,
+                  [&](T l, T h) { il = l; ih = h; nin = 1; },
+                  [&](T l, T h) {
+                    if (MIXED && wedge::straddles(l, h)) {
+                      // two pieces, [l, 0] and [0, h]: this is the only middle piece of the edge
+                      ml0 = l; mh0 = T(0); ml1 = T(0); mh1 = h; nmid = 2; ++n_split;
+                    } else {
+                      if (nmid == 0) { ml0 = l; mh0 = h; } else { ml1 = l; mh1 = h; }
+                      ++nmid;
+                    }
+                  },
+                  [&](T l, T h) { if (nout == 0) { ol0 = l; oh0 = h; } else { ol1 = l; oh1 = h; } ++nout; });
+              if (nin + nmid + nout) wc.terms++;
             }
-            inside = inside && fin;
+            // push this edge's pieces (warp-aggregated)
+            int t0, t1, t2;
+            const int o0 = cnt0 + warp_excl(nin, &t0);
+            const int o1 = cnt1 + warp_excl(nmid, &t1);
+            const int o2 = cnt2 + warp_excl(nout, &t2);
+            if (nin) { S.e[0][o0] = V4{r0, R0, il, ih}; S.own[0][o0] = (unsigned char)lane; }
+            if (nmid > 0) { S.e[1][o1] = V4{r0, R0, ml0, mh0}; S.own[1][o1] = (unsigned char)lane; }
+            if (nmid > 1) { S.e[1][o1 + 1] = V4{r0, R0, ml1, mh1}; S.own[1][o1 + 1] = (unsigned char)lane; }
+            if (nout > 0) { S.e[2][o2] = V4{r0, R0, ol0, oh0}; S.own[2][o2] = (unsigned char)lane; }
+            if (nout > 1) { S.e[2][o2 + 1] = V4{r0, R0, ol1, oh1}; S.own[2][o2 + 1] = (unsigned char)lane; }
+            cnt0 += t0;
+            cnt1 += t1;
+            cnt2 += t2;
+            __syncwarp();
+            // evaluate full stacks, 32 pieces at a time from the top
+            if (cnt0 >= 32 || cnt1 >= 32 || cnt2 >= 32) drain<T, MIXED>(S, cnt0, cnt1, cnt2, false, n_in, n_mid, n_out);
           }
-          int nin = 0, nmid = 0, nout = 0;
-          if (inrange) {
-            const T* E = s_edge + k * EDGE_STRIDE;
-            const T R0s = (E[0] * yx + E[1] * yy + E[2] * yz) - E[3] * hinv;  // m.(p - v_a): > 0 inside
-            const T base = E[4] * yx + E[5] * yy + E[6] * yz;
-            const bool ein = R0s >= T(0);
-            T R0 = fabs(R0s);
-            if (!MIXED) R0 = R0 > T(1e-12) ? R0 : T(1e-12);
-            wc.edges++;
-            V2 rr;
-            rr.x = r0;
-            rr.y = R0;
-            W.rr[kl][lane] = rr;
-            // slots: 0 inner, 1-2 middle, 3-4 beyond the support
-            wedge::split_edge<T>(
-                r0, R0, E[7] * hinv - base, E[8] * hinv - base, fin == ein,
-                [&](T l, T h) { V2 v; v.x = l; v.y = h; W.lh[kl * 5 + 0][lane] = v; nin = 1; },
-                [&](T l, T h) { V2 v; v.x = l; v.y = h; W.lh[kl * 5 + 1 + nmid][lane] = v; ++nmid; },
-                [&](T l, T h) { V2 v; v.x = l; v.y = h; W.lh[kl * 5 + 3 + nout][lane] = v; ++nout; });
-            mask |= (unsigned long long)((nin) | (((1 << nmid) - 1) << 1) | (((1 << nout) - 1) << 3)) << (5 * kl);
-            if (nin + nmid + nout) wc.terms++;
-          }
-          // warp-aggregated append of this edge's slot ids to the compact lists
-          int tin, tmid, tout;
-          const int oin = warp_excl(nin, &tin);
-          const int omid = warp_excl(nmid, &tmid);
-          const int oout = warp_excl(nout, &tout);
-          if (nin) W.q[0][cnt_in + oin] = (unsigned short)((kl * 5 + 0) * 32 + lane);
-          for (int j = 0; j < nmid; ++j) W.q[1][cnt_mid + omid + j] = (unsigned short)((kl * 5 + 1 + j) * 32 + lane);
-          for (int j = 0; j < nout; ++j) W.q[2][cnt_out + oout + j] = (unsigned short)((kl * 5 + 3 + j) * 32 + lane);
-          cnt_in += tin;
-          cnt_mid += tmid;
-          cnt_out += tout;
         }
-        __syncwarp();
-        // ---------------- phase 2: uniform evaluation, kind by kind
-        for (int i = lane; i < cnt_in; i += 32) {
-          const int sl = W.q[0][i], ow = sl & 31, ps = sl >> 5;
-          const V2 rr = W.rr[ps / 5][ow], lh = W.lh[ps][ow];
-          W.res[ps][ow] = wedge::piece_inner<T>(rr.x, rr.y, lh.x, lh.y);
-        }
-        for (int i = lane; i < cnt_mid; i += 32) {
-          const int sl = W.q[1][i], ow = sl & 31, ps = sl >> 5;
-          const V2 rr = W.rr[ps / 5][ow], lh = W.lh[ps][ow];
-          W.res[ps][ow] = wedge::piece_mid<T, MIXED>(rr.x, rr.y, lh.x, lh.y);
-        }
-        for (int i = lane; i < cnt_out; i += 32) {
-          const int sl = W.q[2][i], ow = sl & 31, ps = sl >> 5;
-          const V2 rr = W.rr[ps / 5][ow], lh = W.lh[ps][ow];
-          W.res[ps][ow] = wedge::piece_outer<T>(rr.x, rr.y, lh.x, lh.y);
-        }
-        n_in_tot += cnt_in;
-        n_mid_tot += cnt_mid;
-        n_out_tot += cnt_out;
-        __syncwarp();
-        // ---------------- phase 3: each lane sums its own pieces in a fixed order
-        while (mask) {
-          const int b = __ffsll((long long)mask) - 1;
-          mask &= mask - 1;
-          const T v = W.res[b][lane] - fcomp;
-          const T t = fsum + v;
-          fcomp = (t - fsum) - v;
-          fsum = t;
-        }
-        __syncwarp();
+        kb = ke;
       }
+      // flush what is left (fewer than 32 of each kind)
+      if (cnt0 || cnt1 || cnt2) drain<T, MIXED>(S, cnt0, cnt1, cnt2, true, n_in, n_mid, n_out);
+      __syncwarp();
       if (active) {
-        const double f = (inside ? 1.0 : 0.0) + dacc + (double)fsum;
+        const double f = (inside ? 1.0 : 0.0) + dacc + S.acc[lane];
         if (A.frac) A.frac[p] = f;
         macc += A.m[a] * f;
       }
+      __syncwarp();
     }
-    const double M = BR(s_br).Sum(macc);
-    if (tid == 0) {
-      A.cell_mass[c] = M;
-      if (A.cell_rho) A.cell_rho[c] = M / A.vol[c];
+    for (int o = 16; o > 0; o >>= 1) macc += __shfl_down_sync(FULL, macc, o);
+    if (lane == 0) {
+      A.cell_mass[c] = macc;
+      if (A.cell_rho) A.cell_rho[c] = macc / A.vol[c];
     }
+    __syncwarp();
   }
-  if (lane == 0) {
-    atomicAdd(&s_work[3], 2 * n_in_tot);
-    atomicAdd(&s_work[4], n_mid_tot);
-    atomicAdd(&s_work[6], n_out_tot);
-  }
-  atomicAdd(&s_work[0], (unsigned long long)wc.terms);
-  atomicAdd(&s_work[1], (unsigned long long)wc.faces);
-  atomicAdd(&s_work[2], (unsigned long long)wc.edges);
-  atomicAdd(&s_work[5], (unsigned long long)n64);
-  __syncthreads();
-  if (tid == 0) {
-    atomicAdd(&A.counters[1], s_work[0]);
-    atomicAdd(&A.counters[2], s_work[5]);
-    atomicAdd(&A.counters[8], s_work[1]);
-    atomicAdd(&A.counters[9], s_work[2]);
-    atomicAdd(&A.counters[10], s_work[3]);
-    atomicAdd(&A.counters[11], s_work[4]);
-    atomicAdd(&A.counters[12], s_work[6]);
-  }
-}
-
-// Cells too large for the staging area (none in practice for Voronoi cells;
-// kept so that any valid grid is mapped): one CTA per such cell, one thread
-// per pair, geometry read from global memory, every edge evaluated in place.
-template <typename T, bool MIXED>
-__global__ void pair_integrals_large(IntegralArgs A, const typename Vec4<T>::type* __restrict__ face,
-                                     const T* __restrict__ edge, int smem_faces, int smem_loops) {
-  typedef typename Vec4<T>::type V4;
-  typedef cub::BlockReduce<double, 128> BR;
-  __shared__ typename BR::TempStorage s_br;
-  const int64_t c = blockIdx.x;
-  const int64_t f0 = A.cfo[c];
-  const int nf = (int)(A.cfo[c + 1] - f0);
-  const int64_t l0 = A.fvo[f0];
-  const int nl = (int)(A.fvo[f0 + nf] - l0);
-  if (nf <= smem_faces && nl <= smem_loops) return;
-  const double sx = A.site[3 * c], sy = A.site[3 * c + 1], sz = A.site[3 * c + 2];
-  double macc = 0.0;
-  wedge::WorkCount wc;
-  for (int64_t p = A.pair_off[c] + threadIdx.x; p < A.pair_off[c + 1]; p += 128) {
-    const int32_t a = A.pair_idx[p];
-    const double hh = 1.0 / A.h[a];
-    const double ydx = (A.x[a] - sx) * hh, ydy = (A.y[a] - sy) * hh, ydz = (A.z[a] - sz) * hh;
-    double tot = 0.0;
-    bool inside = true;
-    // always FP64 here: large cells are rare and this path has no queue
-    for (int fi = 0; fi < nf; ++fi) {
-      const double4_32a G = A.face64[f0 + fi];
-      const double rs = G.w * hh - (G.x * ydx + G.y * ydy + G.z * ydz);
-      const bool fin = rs >= 0.0;
-      inside = inside && fin;
-      const double r0 = fabs(rs) > 1e-12 ? fabs(rs) : 1e-12;
-      if (r0 >= 2.0) continue;
-      for (int64_t k = A.fvo[f0 + fi] - l0; k < A.fvo[f0 + fi + 1] - l0; ++k) {
-        const double* D = A.edge64 + (l0 + k) * EDGE_STRIDE;
-        const double R0s = (D[0] * ydx + D[1] * ydy + D[2] * ydz) - D[3] * hh;
-        const double base = D[4] * ydx + D[5] * ydy + D[6] * ydz;
-        const bool ein = R0s >= 0.0;
-        const double R0 = fabs(R0s) > 1e-12 ? fabs(R0s) : 1e-12;
-        const double K = wedge::kprime_edge<double, false>(r0, R0, D[7] * hh - base, D[8] * hh - base, wc);
-        tot += (fin == ein) ? K : -K;
-      }
-    }
-    const double f = (inside ? 1.0 : 0.0) + tot;
-    if (A.frac) A.frac[p] = f;
-    macc += A.m[a] * f;
-  }
-  const double M = BR(s_br).Sum(macc);
-  if (threadIdx.x == 0) {
-    A.cell_mass[c] = M;
-    if (A.cell_rho) A.cell_rho[c] = M / A.vol[c];
-  }
-}
-
-constexpr size_t SMEM_CAP = 200 * 1024;
-
-template <typename T, bool MIXED, int NT, int ECH>
-int launch(map_ctx* ctx, const PreparedGrid* g, const IntegralArgs& A, cudaStream_t s) {
-  typedef typename Vec4<T>::type V4;
-  const size_t queue = sizeof(WarpArea<T, ECH>) * (NT / 32) + 128;
-  int sf = g->max_faces, sl = g->max_loops;
-  auto geo_bytes = [](int f, int l) {
-    return sizeof(V4) * f + sizeof(T) * EDGE_STRIDE * l + sizeof(int) * (f + 1) + sizeof(unsigned short) * l + 16;
+  // work tally: warp sums, one atomic per warp and counter
+  auto wsum = [](unsigned long long v) {
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(FULL, v, o);
+    return v;
   };
-  size_t bytes = queue + geo_bytes(sf, sl);
-  if (bytes > SMEM_CAP) {
-    sf = sf < 128 ? sf : 128;
-    sl = (int)((SMEM_CAP - queue - sizeof(V4) * sf - sizeof(int) * (sf + 1) - 16) /
-               (sizeof(T) * EDGE_STRIDE + sizeof(unsigned short)));
-    bytes = queue + geo_bytes(sf, sl);
+  const unsigned long long terms = wsum((unsigned long long)wc.terms), faces = wsum((unsigned long long)wc.faces);
+  const unsigned long long edges = wsum((unsigned long long)wc.edges), fp64 = wsum((unsigned long long)n64);
+  const unsigned long long split = wsum((unsigned long long)n_split);
+  if (lane == 0) {
+    atomicAdd(&B.counters[1], terms);
+    atomicAdd(&B.counters[2], fp64);
+    atomicAdd(&B.counters[8], faces);
+    atomicAdd(&B.counters[9], edges);
+    atomicAdd(&B.counters[10], 2 * n_in);
+    atomicAdd(&B.counters[11], n_mid - split);  // intervals: a split one is one interval, two pieces
+    atomicAdd(&B.counters[12], n_out);
+    atomicAdd(&B.counters[13], split);
   }
-  auto kern = pair_integrals<T, MIXED, NT, ECH>;
-  CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes));
+}
+
+template <typename T, bool MIXED, int NW, int MINB>
+int launch(map_ctx* ctx, const BatchArgs& B, cudaStream_t s) {
+  auto kern = pair_integrals<T, MIXED, NW, MINB>;
   int per_sm = 0;
-  CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, NT, bytes));
+  CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, NW * 32, 0));
   if (per_sm < 1) per_sm = 1;
   int64_t blocks = (int64_t)per_sm * ctx->sm_count;
-  if (blocks > g->ncell) blocks = g->ncell > 0 ? g->ncell : 1;
-  const V4* fp = reinterpret_cast<const V4*>(MIXED ? (const void*)g->face32 : (const void*)g->face64);
-  const T* ep = reinterpret_cast<const T*>(MIXED ? (const void*)g->edge32 : (const void*)g->edge64);
-  kern<<<(unsigned)blocks, NT, bytes, s>>>(A, fp, ep, sf, sl); ++ctx->launches;
+  const int64_t need = (B.total + NW - 1) / NW;
+  if (blocks > need) blocks = need > 0 ? need : 1;
+  kern<<<(unsigned)blocks, NW * 32, 0, s>>>(B); ++ctx->launches;
   CUDA_TRY(cudaGetLastError());
-  if (sf < g->max_faces || sl < g->max_loops) {
-    pair_integrals_large<T, MIXED><<<(unsigned)g->ncell, 128, 0, s>>>(A, fp, ep, sf, sl); ++ctx->launches;
+  return MAP_OK;
+}
+
+// Descriptor upload through kernel parameters: the values are captured at
+// launch, so the host copy may be reused at once and the launch can sit in a
+// CUDA graph.
+constexpr int DESC_CHUNK = 24;  // 24 x 160 bytes of parameters per launch
+struct DescChunk {
+  SnapDesc d[DESC_CHUNK];
+  int n;
+};
+__global__ void put_descs(DescChunk c, SnapDesc* dst) {
+  if ((int)threadIdx.x < c.n) dst[threadIdx.x] = c.d[threadIdx.x];
+}
+constexpr int I64_CHUNK = 480;
+struct I64Chunk {
+  int64_t v[I64_CHUNK];
+  int n;
+};
+__global__ void put_i64(I64Chunk c, int64_t* dst) {
+  for (int i = threadIdx.x; i < c.n; i += blockDim.x) dst[i] = c.v[i];
+}
+
+// sum_i M_i of each snapshot (one block per snapshot, fixed order)
+__global__ void sum_snapshots(const SnapDesc* __restrict__ d, double* totals) {
+  typedef cub::BlockReduce<double, 256> BR;
+  __shared__ typename BR::TempStorage tmp;
+  const SnapDesc& D = d[blockIdx.x];
+  double acc = 0.0;
+  for (int64_t i = threadIdx.x; i < D.ncell; i += 256) acc += D.cell_mass[i];
+  const double t = BR(tmp).Sum(acc);
+  if (threadIdx.x == 0) totals[D.orig] = t;
+}
+
+}  // namespace
+
+int integrals_upload(map_ctx* ctx, const SnapDesc* h_desc, const int64_t* h_base, int nsnap, SnapDesc* d_desc,
+                      int64_t* d_base, cudaStream_t s) {
+  for (int j0 = 0; j0 < nsnap; j0 += DESC_CHUNK) {
+    DescChunk c;
+    c.n = nsnap - j0 < DESC_CHUNK ? nsnap - j0 : DESC_CHUNK;
+    for (int i = 0; i < c.n; ++i) c.d[i] = h_desc[j0 + i];
+    put_descs<<<1, DESC_CHUNK, 0, s>>>(c, d_desc + j0); ++ctx->launches;
+    CUDA_TRY(cudaGetLastError());
+  }
+  for (int j0 = 0; j0 <= nsnap; j0 += I64_CHUNK) {
+    I64Chunk c;
+    c.n = nsnap + 1 - j0 < I64_CHUNK ? nsnap + 1 - j0 : I64_CHUNK;
+    for (int i = 0; i < c.n; ++i) c.v[i] = h_base[j0 + i];
+    put_i64<<<1, 128, 0, s>>>(c, d_base + j0); ++ctx->launches;
     CUDA_TRY(cudaGetLastError());
   }
   return MAP_OK;
 }
 
-__global__ void sum_cells(int64_t n, const double* __restrict__ v, double* out) {
-  typedef cub::BlockReduce<double, 256> BR;
-  __shared__ typename BR::TempStorage tmp;
-  double acc = 0.0;
-  for (int64_t i = threadIdx.x; i < n; i += 256) acc += v[i];
-  double t = BR(tmp).Sum(acc);
-  if (threadIdx.x == 0) *out = t;
+int integrals_enqueue(map_ctx* ctx, const BatchArgs& B, int variant, cudaStream_t s) {
+  CUDA_TRY(cudaMemsetAsync(ctx->d_counters, 0, 4 * sizeof(unsigned long long), s));
+  CUDA_TRY(cudaMemsetAsync(ctx->d_counters + 8, 0, 8 * sizeof(unsigned long long), s));
+  if (ctx->cfg.precision == MAP_MIXED) {
+    switch (variant) {
+      case 1: return launch<float, true, 4, 4>(ctx, B, s);
+      case 2: return launch<float, true, 4, 6>(ctx, B, s);
+      default: return launch<float, true, 4, 5>(ctx, B, s);
+    }
+  }
+  return launch<double, false, 4, 4>(ctx, B, s);
 }
 
-}  // namespace
+int integrals_sum(map_ctx* ctx, const SnapDesc* d_desc, int nsnap, double* totals, cudaStream_t s) {
+  sum_snapshots<<<nsnap, 256, 0, s>>>(d_desc, totals); ++ctx->launches;
+  CUDA_TRY(cudaGetLastError());
+  return MAP_OK;
+}
+
+SnapDesc make_desc(map_ctx* ctx, const PreparedGrid* g, const map_particles* p, const map_outputs* out,
+                   const int64_t* pair_off, const int32_t* pair_idx, double* frac, int orig) {
+  SnapDesc d;
+  d.ncell = g->ncell;
+  d.cfo = g->cell_face_off;
+  d.fvo = g->face_vert_off;
+  d.site = g->site;
+  d.vol = g->vol;
+  d.pair_off = pair_off;
+  d.pair_idx = pair_idx;
+  d.x = p->x; d.y = p->y; d.z = p->z; d.m = p->m; d.h = p->h;
+  d.frac = frac;
+  d.cell_mass = out->cell_mass;
+  d.cell_rho = out->cell_rho;
+  const bool mixed = ctx->cfg.precision == MAP_MIXED;
+  d.face = mixed ? (const void*)g->face32 : (const void*)g->face64;
+  d.edge = mixed ? (const void*)g->edge32 : (const void*)g->edge64;
+  d.face64 = g->face64;
+  d.edge64 = g->edge64;
+  d.orig = orig;
+  return d;
+}
 
 int integrals_run(map_ctx* ctx, const PreparedGrid* g, const map_particles* p, map_outputs* out, cudaStream_t s) {
   double* frac;
   MAP_TRY(ensure_t(ctx, ctx->ws_misc[0], ctx->n_pairs + 1, &frac));
   ctx->pair_frac = frac;
-  CUDA_TRY(cudaMemsetAsync(ctx->d_counters, 0, 4 * sizeof(unsigned long long), s));
-  CUDA_TRY(cudaMemsetAsync(ctx->d_counters + 8, 0, 8 * sizeof(unsigned long long), s));
-  IntegralArgs A;
-  A.ncell = g->ncell;
-  A.cfo = g->cell_face_off;
-  A.fvo = g->face_vert_off;
-  A.site = g->site;
-  A.vol = g->vol;
-  A.pair_off = ctx->pair_off;
-  A.pair_idx = ctx->pair_idx;
-  A.x = p->x; A.y = p->y; A.z = p->z; A.m = p->m; A.h = p->h;
-  A.frac = frac;
-  A.cell_mass = out->cell_mass;
-  A.cell_rho = out->cell_rho;
-  A.counters = ctx->d_counters;
-  A.face64 = g->face64;
-  A.edge64 = g->edge64;
+  SnapDesc* d_desc;
+  int64_t* d_base;
+  MAP_TRY(ensure_t(ctx, ctx->ws_misc[3], 1, &d_desc));
+  MAP_TRY(ensure_t(ctx, ctx->ws_misc[4], 2, &d_base));
+  const SnapDesc h = make_desc(ctx, g, p, out, ctx->pair_off, ctx->pair_idx, frac, 0);
+  const int64_t base[2] = {0, g->ncell};
+  MAP_TRY(integrals_upload(ctx, &h, base, 1, d_desc, d_base, s));
+  BatchArgs B{d_desc, d_base, 1, g->ncell, ctx->d_counters};
   phase_begin(ctx, 2, s);
-  if (ctx->cfg.precision == MAP_MIXED)
-    MAP_TRY((launch<float, true, 128, 4>(ctx, g, A, s)));
-  else
-    MAP_TRY((launch<double, false, 128, 2>(ctx, g, A, s)));
+  MAP_TRY(integrals_enqueue(ctx, B, ctx->tuned[ctx->cfg.precision], s));
   phase_end(ctx, 2, s);
   if (out->cell_vol) CUDA_TRY(cudaMemcpyAsync(out->cell_vol, g->vol, g->ncell * sizeof(double), cudaMemcpyDeviceToDevice, s));
-  sum_cells<<<1, 256, 0, s>>>(g->ncell, out->cell_mass, ctx->d_total); ++ctx->launches;
-  CUDA_TRY(cudaGetLastError());
+  MAP_TRY(integrals_sum(ctx, d_desc, 1, ctx->d_total, s));
   return MAP_OK;
 }

@@ -115,10 +115,22 @@ struct map_ctx {
   cudaStream_t last_stream = nullptr;
   int64_t* h_scratch = nullptr;  // pinned scratch for small readbacks
   int64_t launches = 0;          // kernels this context has launched (own kernels only)
-  int64_t last_work[4] = {0, 0, 0, 0};  // work tally of the last mapping call (see map_get_work)
+  int64_t last_work[6] = {0, 0, 0, 0, 0, 0};  // work tally of the last mapping call (see map_get_work)
   // phase events (start/stop pairs): 0 tree build, 1 pair list, 2 pair integrals, 3 h solve
   cudaEvent_t ev[8] = {};
   bool ev_used[4] = {false, false, false, false};
+  // launch shape of the pair-integral kernel, per precision (the autotuner's choice)
+  int tuned[2] = {0, 0};
+  bool tune_done[2] = {false, false};
+  float tune_ms[3] = {0.f, 0.f, 0.f};
+  // batches: per-snapshot pair lists of the last batch, and the CUDA graph of
+  // its integral launch with the descriptor bytes it was captured for
+  std::vector<DevBuf> batch_off, batch_idx;
+  cudaStream_t bstream = nullptr;
+  cudaEvent_t bev[2] = {};
+  cudaGraphExec_t bexec = nullptr;
+  std::vector<unsigned char> bsig;
+  int64_t bexec_launches = 0;  // kernels per replay of bexec
 };
 
 inline void phase_begin(map_ctx* ctx, int k, cudaStream_t s) { if (ctx->ev[2 * k]) cudaEventRecord(ctx->ev[2 * k], s); }
@@ -138,16 +150,62 @@ inline int ensure_t(map_ctx* ctx, DevBuf& b, size_t count, T** out) {
   return MAP_OK;
 }
 
+// One mapping problem of the pair-integral kernel: a resident grid, a
+// particle set, its pair list and its outputs (device pointers).
+struct SnapDesc {
+  int64_t ncell;
+  const int64_t* cfo;
+  const int64_t* fvo;
+  const double* site;
+  const double* vol;
+  const int64_t* pair_off;
+  const int32_t* pair_idx;
+  const double *x, *y, *z, *m, *h;
+  double* frac;        // per-pair f_ai, or NULL
+  double* cell_mass;
+  double* cell_rho;    // or NULL
+  const void* face;    // site-relative planes: float4 (mixed) or double4 (FP64)
+  const void* edge;    // EDGE_STRIDE floats or doubles per loop entry
+  const double4_32a* face64;
+  const double* edge64;
+  int64_t orig;        // the caller's index of this snapshot
+};
+
+// The queue of the pair-integral kernel: cells of nsnap snapshots, snapshot j
+// owning queue positions [cell_base[j], cell_base[j+1]).
+struct BatchArgs {
+  const SnapDesc* snaps;
+  const int64_t* cell_base;
+  int nsnap;
+  int64_t total;
+  unsigned long long* counters;  // [1] edge terms, [2] FP64 terms, [3] queue, [8..13] work tally
+};
+
+constexpr int N_VARIANTS = 3;  // launch shapes of the mixed pair-integral kernel (register caps 102, 128, 85)
+
 // ---------------------------------------------------------------- subsystems
 int grid_prepare(map_ctx* ctx, const map_grid* in, PreparedGrid* g, cudaStream_t s);
 int tree_build(map_ctx* ctx, const double* x, const double* y, const double* z, const double* m,
                const double* h, int64_t n, cudaStream_t s, bool want_size = false);
-int pairs_build(map_ctx* ctx, const PreparedGrid* g, cudaStream_t s);
+// Pair list of the grid against the current octree; the offsets and indices
+// go to off_buf / idx_buf (default: the context's workspace).
+int pairs_build(map_ctx* ctx, const PreparedGrid* g, cudaStream_t s, DevBuf* off_buf = nullptr,
+                DevBuf* idx_buf = nullptr);
+int check_particles(map_ctx* ctx, const map_particles* p, bool need_m, bool need_h, cudaStream_t s);
 int integrals_run(map_ctx* ctx, const PreparedGrid* g, const map_particles* p, map_outputs* out, cudaStream_t s);
+SnapDesc make_desc(map_ctx* ctx, const PreparedGrid* g, const map_particles* p, const map_outputs* out,
+                   const int64_t* pair_off, const int32_t* pair_idx, double* frac, int orig);
+int integrals_upload(map_ctx* ctx, const SnapDesc* h_desc, const int64_t* h_base, int nsnap, SnapDesc* d_desc,
+                      int64_t* d_base, cudaStream_t s);
+int integrals_enqueue(map_ctx* ctx, const BatchArgs& B, int variant, cudaStream_t s);
+int integrals_sum(map_ctx* ctx, const SnapDesc* d_desc, int nsnap, double* totals, cudaStream_t s);
 int h_solve_run(map_ctx* ctx, const double* x, const double* y, const double* z, int64_t n, double* h,
                 int32_t* route, const double* h0_override, cudaStream_t s);
 int pseudo_run(map_ctx* ctx, const map_particles* full, const double* src, int nsrc, map_particles* out,
                int32_t* kind, int64_t* ident, int64_t* n_pseudo, cudaStream_t s);
+
+// blocks of t threads covering n items
+inline unsigned nblk(int64_t n, int t) { return (unsigned)((n + t - 1) / t); }
 
 // FP64 bit helpers for atomic max/min on non-negative doubles
 __device__ __forceinline__ unsigned long long dbits(double v) { return (unsigned long long)__double_as_longlong(v); }

@@ -189,11 +189,10 @@ __global__ void site_keys(int64_t n, const double* __restrict__ site, uint64_t* 
   idx[i] = (int32_t)i;
 }
 
-inline unsigned nblk(int64_t n, int t) { return (unsigned)((n + t - 1) / t); }
 
 }  // namespace
 
-int pairs_build(map_ctx* ctx, const PreparedGrid* g, cudaStream_t s) {
+int pairs_build(map_ctx* ctx, const PreparedGrid* g, cudaStream_t s, DevBuf* off_buf, DevBuf* idx_buf) {
   DevTree& T = ctx->tree;
   const int64_t nc = g->ncell;
   const int tpb = 128;
@@ -216,7 +215,7 @@ int pairs_build(map_ctx* ctx, const PreparedGrid* g, cudaStream_t s) {
   PairGrid PG{g->cell_face_off, g->face_plane, g->face32, g->site, g->rad};
   int64_t *count, *off;
   MAP_TRY(ensure_t(ctx, ctx->ws_pairs[0], nc + 1, &count));
-  MAP_TRY(ensure_t(ctx, ctx->ws_pairs[1], nc + 1, &off));
+  MAP_TRY(ensure_t(ctx, off_buf ? *off_buf : ctx->ws_pairs[1], nc + 1, &off));
   CUDA_TRY(cudaMemsetAsync(count + nc, 0, sizeof(int64_t), s));
   pair_traverse<false><<<nblk(nc, tpb), tpb, 0, s>>>(nc, order, PT, PG, count, nullptr, nullptr); ++ctx->launches;
   CUDA_TRY(cudaGetLastError());
@@ -229,7 +228,7 @@ int pairs_build(map_ctx* ctx, const PreparedGrid* g, cudaStream_t s) {
   const int64_t np = ctx->h_scratch[0];
   int32_t *raw, *sorted;
   MAP_TRY(ensure_t(ctx, ctx->ws_pairs[2], np + 1, &raw));
-  MAP_TRY(ensure_t(ctx, ctx->ws_pairs[3], np + 1, &sorted));
+  MAP_TRY(ensure_t(ctx, idx_buf ? *idx_buf : ctx->ws_pairs[3], np + 1, &sorted));
   pair_traverse<true><<<nblk(nc, tpb), tpb, 0, s>>>(nc, order, PT, PG, nullptr, off, raw); ++ctx->launches;
   CUDA_TRY(cudaGetLastError());
   if (np > 0) {

@@ -23,7 +23,6 @@
 
 namespace {
 
-inline unsigned nblk(int64_t n, int t) { return (unsigned)((n + t - 1) / t); }
 
 constexpr int64_t KIND_PARTICLE = (int64_t)1 << 62;
 

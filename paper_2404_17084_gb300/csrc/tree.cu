@@ -1,4 +1,4 @@
-// Device octree over a particle set and the smoothing-length solve.
+// Device octree over a particle set.
 //
 // Octree (Section III-A, built as an octree with a leaf capacity instead of
 // the paper's RCB tree): 63-bit Morton keys (21 bits per axis) are radix
@@ -10,10 +10,6 @@
 // bottom-up; node size (distance from the centre of mass to the furthest
 // particle, Section III-A), largest h and bounding box are reduced over each
 // node's particles.
-//
-// h solve (Section III-C, Eq. 7-9): Newton-Raphson on g(h) = h - hfact n(h)^(-1/3)
-// with n(h) = sum_b W(r_ab, h) summed by an octree range query, then bisection,
-// then the estimate.
 #include <cub/cub.cuh>
 
 #include "internal.cuh"
@@ -254,7 +250,6 @@ __global__ void collect_big(int64_t nn, const int64_t* __restrict__ nb, const in
   if (ne[i] - nb[i] > BIG_NODE) big[atomicAdd(nbig, 1ULL)] = (int32_t)i;
 }
 
-inline unsigned nblk(int64_t n, int t) { return (unsigned)((n + t - 1) / t); }
 
 }  // namespace
 
@@ -394,254 +389,6 @@ int tree_build(map_ctx* ctx, const double* x, const double* y, const double* z, 
   MAP_TRY(ensure_t(ctx, ctx->ws_tree[24], 8 * T.nnodes, &box32));
   T.box32 = box32;
   node_box32<<<nblk(T.nnodes, tpb), tpb, 0, s>>>(T.nnodes, T.bbox_bits, T.hmax_bits, box32); ++ctx->launches;
-  CUDA_TRY(cudaGetLastError());
-  return MAP_OK;
-}
-
-// ---------------------------------------------------------------- h solve
-
-namespace {
-
-__device__ __forceinline__ double w_m4(double q) {
-  if (q < 1.0) return 1.0 - 1.5 * q * q + 0.75 * q * q * q;
-  if (q < 2.0) { double t = 2.0 - q; return 0.25 * t * t * t; }
-  return 0.0;
-}
-__device__ __forceinline__ double dw_m4(double q) {
-  if (q < 1.0) return -3.0 * q + 2.25 * q * q;
-  if (q < 2.0) { double t = 2.0 - q; return -0.75 * t * t; }
-  return 0.0;
-}
-
-__device__ __forceinline__ double box_dist2(const unsigned long long* bb, double x, double y, double z) {
-  double lo0 = bitsd(bb[0]), lo1 = bitsd(bb[1]), lo2 = bitsd(bb[2]);
-  double hi0 = bitsd(bb[3]), hi1 = bitsd(bb[4]), hi2 = bitsd(bb[5]);
-  double dx = x < lo0 ? lo0 - x : (x > hi0 ? x - hi0 : 0.0);
-  double dy = y < lo1 ? lo1 - y : (y > hi1 ? y - hi1 : 0.0);
-  double dz = z < lo2 ? lo2 - z : (z > hi2 ? z - hi2 : 0.0);
-  return dx * dx + dy * dy + dz * dz;
-}
-
-struct TreeView {
-  const double *xs, *ys, *zs;
-  const int64_t *nb, *ne, *fc;
-  const int32_t* nch;
-  const unsigned long long* bbox;
-  const float* box32;  // outward-rounded FP32 boxes (8 floats per node)
-};
-
-// Conservative FP32 test: true when no point of the node's box is within R
-// of (x,y,z).  The box is rounded outward and the query point's rounding
-// (<= 6e-8 in the unit cube) is covered by a 1e-6 absolute margin.
-__device__ __forceinline__ bool box_far32(const float* b, float x, float y, float z, double R) {
-  const float dx = x < b[0] ? b[0] - x : (x > b[3] ? x - b[3] : 0.f);
-  const float dy = y < b[1] ? b[1] - y : (y > b[4] ? y - b[4] : 0.f);
-  const float dz = z < b[2] ? b[2] - z : (z > b[5] ? z - b[5] : 0.f);
-  const float Rm = (float)(R + 1e-6) * 1.000001f;
-  return dx * dx + dy * dy + dz * dz > Rm * Rm;
-}
-
-// n(h) = sum_b W(r_ab, h) and dn/dh over all tree particles within 2h.
-__device__ void density_sum(const TreeView& T, double x, double y, double z, double h, double& n, double& dn) {
-  const double R = 2.0 * h, R2 = R * R;
-  const double inv_h = 1.0 / h;
-  const double norm = 1.0 / (MAP_PI * h * h * h);
-  double s = 0.0, ds = 0.0;
-  int32_t stack[192];
-  int sp = 0;
-  stack[sp++] = 0;
-  while (sp > 0) {
-    int32_t nd = stack[--sp];
-    if (box_dist2(T.bbox + 6 * nd, x, y, z) >= R2) continue;
-    if (T.nch[nd] == 0) {
-      for (int64_t k = T.nb[nd]; k < T.ne[nd]; ++k) {
-        double dx = T.xs[k] - x, dy = T.ys[k] - y, dz = T.zs[k] - z;
-        double r2 = dx * dx + dy * dy + dz * dz;
-        if (r2 >= R2) continue;
-        double q = sqrt(r2) * inv_h;
-        double w = w_m4(q);
-        s += w;
-        ds += 3.0 * w + q * dw_m4(q);
-      }
-    } else {
-      int64_t c0 = T.fc[nd];
-      for (int c = T.nch[nd] - 1; c >= 0; --c) stack[sp++] = (int32_t)(c0 + c);
-    }
-  }
-  n = s * norm;
-  dn = -ds * norm * inv_h;
-}
-
-__device__ __forceinline__ double g_of(const TreeView& T, double x, double y, double z, double h, double hfact) {
-  double n, dn;
-  density_sum(T, x, y, z, h, n, dn);
-  return h - hfact * pow(n, -1.0 / 3.0);
-}
-
-constexpr int MAXR = 64;  // cached candidate leaf ranges per particle
-
-// Leaves whose bounding box comes within R of (x,y,z); false if more than MAXR.
-__device__ bool gather_ranges(const TreeView& T, double x, double y, double z, double R, int2* rng, int& nr) {
-  const float fx = (float)x, fy = (float)y, fz = (float)z;
-  int32_t stack[192];
-  int sp = 0;
-  stack[sp++] = 0;
-  nr = 0;
-  while (sp > 0) {
-    const int32_t nd = stack[--sp];
-    if (box_far32(T.box32 + 8 * nd, fx, fy, fz, R)) continue;
-    if (T.nch[nd] == 0) {
-      if (nr == MAXR) return false;
-      rng[nr++] = make_int2((int)T.nb[nd], (int)T.ne[nd]);
-    } else {
-      const int64_t c0 = T.fc[nd];
-      for (int c = T.nch[nd] - 1; c >= 0; --c) stack[sp++] = (int32_t)(c0 + c);
-    }
-  }
-  return true;
-}
-
-// n(h), dn/dh over cached ranges.  MIXED: FP32 sums on hi/lo split
-// coordinates (h to ~1e-7 relative); else FP64.
-template <bool MIXED>
-__device__ void range_sum(const TreeView& T, const float* __restrict__ split, int64_t k, double x, double y, double z,
-                          double h, const int2* rng, int nr, double& n, double& dn) {
-  if (MIXED) {
-    const float hxi = split[6 * k], lxi = split[6 * k + 1], hyi = split[6 * k + 2], lyi = split[6 * k + 3];
-    const float hzi = split[6 * k + 4], lzi = split[6 * k + 5];
-    const float inv_h = (float)(1.0 / h);
-    float s = 0.f, ds = 0.f;
-    for (int r = 0; r < nr; ++r)
-      for (int j = rng[r].x; j < rng[r].y; ++j) {
-        const float* P = split + 6 * (int64_t)j;
-        const float dx = ((P[0] - hxi) + (P[1] - lxi)) * inv_h;
-        const float dy = ((P[2] - hyi) + (P[3] - lyi)) * inv_h;
-        const float dz = ((P[4] - hzi) + (P[5] - lzi)) * inv_h;
-        const float q2 = dx * dx + dy * dy + dz * dz;
-        if (q2 >= 4.f) continue;
-        const float q = sqrtf(q2);
-        float w, dwq;
-        if (q < 1.f) { w = 1.f - 1.5f * q2 + 0.75f * q2 * q; dwq = -3.f * q2 + 2.25f * q2 * q; }
-        else { const float t = 2.f - q; w = 0.25f * t * t * t; dwq = -0.75f * t * t * q; }
-        s += w;
-        ds += 3.f * w + dwq;
-      }
-    const double norm = 1.0 / (MAP_PI * h * h * h);
-    n = (double)s * norm;
-    dn = -(double)ds * norm / h;
-  } else {
-    const double R2 = 4.0 * h * h, inv_h = 1.0 / h;
-    double s = 0.0, ds = 0.0;
-    for (int r = 0; r < nr; ++r)
-      for (int j = rng[r].x; j < rng[r].y; ++j) {
-        const double dx = T.xs[j] - x, dy = T.ys[j] - y, dz = T.zs[j] - z;
-        const double r2 = dx * dx + dy * dy + dz * dz;
-        if (r2 >= R2) continue;
-        const double q = sqrt(r2) * inv_h;
-        const double w = w_m4(q);
-        s += w;
-        ds += 3.0 * w + q * dw_m4(q);
-      }
-    const double norm = 1.0 / (MAP_PI * h * h * h);
-    n = s * norm;
-    dn = -ds * norm * inv_h;
-  }
-}
-
-// One thread per particle (sorted order).  Newton on cached candidate ranges
-// (gathered for a support up to 2*hcap, hcap = 1.25 h, regathered whenever h
-// outgrows it); bisection falls back to a full range query per evaluation.
-template <bool MIXED>
-__global__ void h_newton(int64_t n, TreeView T, const float* __restrict__ split, const int32_t* __restrict__ idx,
-                         const double* __restrict__ h0s, double hfact, double tol, double* hout, int32_t* route) {
-  int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (k >= n) return;
-  const double x = T.xs[k], y = T.ys[k], z = T.zs[k];
-  const double g0 = h0s[k];
-  const double lo = g0 / 16.0, hi = g0 * 16.0;
-  int2 rng[MAXR];
-  int nr = 0;
-  double hcap = 1.25 * g0;
-  bool cached = gather_ranges(T, x, y, z, 2.0 * hcap, rng, nr);
-  double h = g0;
-  bool ok = false;
-  for (int it = 0; it < 30; ++it) {
-    if (h > hcap) {
-      hcap = 1.25 * h;
-      cached = gather_ranges(T, x, y, z, 2.0 * hcap, rng, nr);
-    }
-    double nn, dn;
-    if (cached) range_sum<MIXED>(T, split, k, x, y, z, h, rng, nr, nn, dn);
-    else density_sum(T, x, y, z, h, nn, dn);
-    const double f = h - hfact * pow(nn, -1.0 / 3.0);
-    const double fp = 1.0 + hfact / 3.0 * pow(nn, -4.0 / 3.0) * dn;
-    const double hn = h - f / fp;
-    if (!(hn >= lo && hn <= hi)) break;
-    if (fabs(hn - h) < tol * hn) { h = hn; ok = true; break; }
-    h = hn;
-  }
-  int r = 0;
-  if (!ok) {
-    const double flo = g_of(T, x, y, z, lo, hfact), fhi = g_of(T, x, y, z, hi, hfact);
-    if (!(flo < 0.0 && fhi > 0.0)) {
-      h = g0;
-      r = 2;
-    } else {
-      double a0 = lo, b0 = hi;
-      for (int it = 0; it < 200; ++it) {
-        const double mid = 0.5 * (a0 + b0);
-        const double fm = g_of(T, x, y, z, mid, hfact);
-        if (fm < 0.0) a0 = mid; else b0 = mid;
-        if (b0 - a0 < 1e-12 * mid) break;
-      }
-      h = 0.5 * (a0 + b0);
-      r = 1;
-    }
-  }
-  const int32_t a = idx[k];
-  hout[a] = h;
-  if (route) route[a] = r;
-}
-
-// Initial guess: hfact * side(leaf cube) / count^(1/3), per sorted position.
-__global__ void h_guess_leaf(int64_t n, const int32_t* __restrict__ owner, const int32_t* __restrict__ lev,
-                             const int64_t* __restrict__ nb, const int64_t* __restrict__ ne, double hfact,
-                             double* h0s) {
-  int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (k >= n) return;
-  int32_t leaf = owner[k];
-  double side = ldexp(1.0, -lev[leaf]);
-  h0s[k] = hfact * side / cbrt((double)(ne[leaf] - nb[leaf]));
-}
-
-__global__ void gather_h0(int64_t n, const int32_t* __restrict__ idx, const double* __restrict__ h0, double* h0s) {
-  int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (k >= n) return;
-  h0s[k] = h0[idx[k]];
-}
-
-}  // namespace
-
-int h_solve_run(map_ctx* ctx, const double* x, const double* y, const double* z, int64_t n, double* h, int32_t* route,
-                const double* h0_override, cudaStream_t s) {
-  MAP_TRY(tree_build(ctx, x, y, z, nullptr, nullptr, n, s));
-  DevTree& T = ctx->tree;
-  double* h0s;
-  MAP_TRY(ensure_t(ctx, ctx->ws_tree[22], n, &h0s));
-  const int tpb = 128;
-  if (h0_override)
-    gather_h0<<<nblk(n, tpb), tpb, 0, s>>>(n, T.idx, h0_override, h0s);
-  else
-    h_guess_leaf<<<nblk(n, tpb), tpb, 0, s>>>(n, T.owner, T.level, T.begin, T.end, ctx->cfg.hfact, h0s);
-  ++ctx->launches;
-  CUDA_TRY(cudaGetLastError());
-  TreeView V{T.xs, T.ys, T.zs, T.begin, T.end, T.first_child, T.nchild, T.bbox_bits, T.box32};
-  // the mixed build converges h in FP32 sums to 1e-6 relative; the FP64 build to 1e-10
-  if (ctx->cfg.precision == MAP_MIXED)
-    h_newton<true><<<nblk(n, tpb), tpb, 0, s>>>(n, V, T.split, T.idx, h0s, ctx->cfg.hfact, 1e-6, h, route);
-  else
-    h_newton<false><<<nblk(n, tpb), tpb, 0, s>>>(n, V, T.split, T.idx, h0s, ctx->cfg.hfact, 1e-10, h, route);
-  ++ctx->launches;
   CUDA_TRY(cudaGetLastError());
   return MAP_OK;
 }

@@ -50,9 +50,13 @@
 // FP32.  There the mixed build integrates
 //     r0 [E(U) - E(r0)] = N(s)/(120 pi) + kappa,  N = r0 p(U)/U - p(r0),
 //     p(u) = (2-u)^5 (1+u),
-// taking N R0/(R0^2+s^2) by 6-point Gauss-Legendre: N vanishes at the poles
-// s = +-i R0, and the remainder's only singularities are the branch points
-// s = +-i c, at distance >= 1 from the interval, so six nodes reach ~1e-8.
+// taking N R0/(R0^2+s^2) by 6-point Gauss-Legendre.  N vanishes at the poles
+// s = +-i R0 and tends to zero with (2-U)^5 at the support, so the integrand
+// keeps its relative accuracy where the kernel is small; its only
+// singularities are the branch points s = +-i c.  An interval that straddles
+// the foot s = 0 is split there, so that each part starts or ends level with
+// the branch points: unsplit, an interval of length 2 sqrt 3 at c = 1 loses
+// 1e-4 relative; split, the rule's truncation stays below ~5e-8 absolute.
 #pragma once
 
 #include <cuda_runtime.h>
@@ -83,17 +87,14 @@ constexpr double INV_4PI = 1.0 / (4.0 * 3.14159265358979323846);
 constexpr double INV_120PI = 1.0 / (120.0 * 3.14159265358979323846);
 
 // c0 = r0 E(r0)
+// (both branches evaluated and selected: no divergence between lanes)
 template <typename T>
 __device__ __forceinline__ T c0_of(T r0) {
-  if (r0 < T(1)) {
-    const T r2 = r0 * r0, r3 = r2 * r0;
-    return (T(1) - T(1.4) * r0 + (T(2) / T(3)) * r3 - T(0.3) * r3 * r2 + T(0.1) * r3 * r3) * T(INV_4PI);
-  }
-  if (r0 < T(2)) {
-    const T t = T(2) - r0, t2 = t * t;
-    return t2 * t2 * t * (T(1) + r0) * T(INV_120PI);
-  }
-  return T(0);
+  const T r2 = r0 * r0, r3 = r2 * r0;
+  const T a = (T(1) - T(1.4) * r0 + (T(2) / T(3)) * r3 - T(0.3) * r3 * r2 + T(0.1) * r3 * r3) * T(INV_4PI);
+  const T t = T(2) - r0, t2 = t * t;
+  const T b = t2 * t2 * t * (T(1) + r0) * T(INV_120PI);
+  return r0 < T(1) ? a : (r0 < T(2) ? b : T(0));
 }
 
 template <typename T>
@@ -174,19 +175,19 @@ __device__ __forceinline__ T piece_inner(T r0, T R0, T lo, T hi) {
   return (g1 - g0) * T(INV_4PI);
 }
 
+// Mixed build: the caller splits an interval that straddles the foot s = 0
+// into two pieces before calling (see split_edge_mixed), so that every call
+// is one Gauss-Legendre panel; kappa dPhi is evaluated unconditionally
+// (kappa = 0 for r0 >= 1), keeping the lanes of a warp on one path.
 template <typename T, bool MIXED>
 __device__ __forceinline__ T piece_mid(T r0, T R0, T lo, T hi) {
   const T c2 = r0 * r0 + R0 * R0;
-  T v;
-  if (MIXED) {
-    v = mid_gl<T>(r0, R0, c2, lo, hi) * T(INV_120PI);
-  } else {
-    const T c = xsqrt(c2);
-    T g1, g0, d;
-    antider<T, false, true>(r0, R0, c2, c, hi, d, g1);
-    antider<T, false, true>(r0, R0, c2, c, lo, d, g0);
-    v = (g1 - g0) * T(INV_120PI);
-  }
+  if (MIXED) return mid_gl<T>(r0, R0, c2, lo, hi) * T(INV_120PI) + kappa_of(r0) * dphi(lo, hi, R0);
+  const T c = xsqrt(c2);
+  T g1, g0, d;
+  antider<T, false, true>(r0, R0, c2, c, hi, d, g1);
+  antider<T, false, true>(r0, R0, c2, c, lo, d, g0);
+  const T v = (g1 - g0) * T(INV_120PI);
   const T k = kappa_of(r0);
   return k != T(0) ? v + k * dphi(lo, hi, R0) : v;
 }
@@ -221,13 +222,27 @@ __device__ __forceinline__ void split_edge(T r0, T R0, T aa, T ab, bool pos, FIn
   }
 }
 
+// True when the interval straddles the foot s = 0 (the mixed build evaluates
+// it as two pieces, [lo, 0] and [0, hi]: each starts or ends level with the
+// branch points s = +-i c of the middle-piece integrand).
+template <typename T>
+__device__ __forceinline__ bool straddles(T lo, T hi) {
+  return (lo < T(0)) != (hi < T(0)) && lo != T(0) && hi != T(0);
+}
+
 // K' of one edge evaluated in this thread.
 template <typename T, bool MIXED>
 __device__ __forceinline__ T kprime_edge(T r0, T R0, T aa, T ab, WorkCount& wc) {
   T acc = T(0);
   split_edge<T>(r0, R0, aa, ab, true,
                 [&](T lo, T hi) { acc += piece_inner<T>(r0, R0, lo, hi); wc.inner += 2; },
-                [&](T lo, T hi) { acc += piece_mid<T, MIXED>(r0, R0, lo, hi); wc.mid++; },
+                [&](T lo, T hi) {
+                  if (MIXED && straddles(lo, hi))
+                    acc += piece_mid<T, MIXED>(r0, R0, lo, T(0)) + piece_mid<T, MIXED>(r0, R0, T(0), hi);
+                  else
+                    acc += piece_mid<T, MIXED>(r0, R0, lo, hi);
+                  wc.mid++;
+                },
                 [&](T lo, T hi) { acc += piece_outer<T>(r0, R0, lo, hi); wc.outer++; });
   return acc;
 }

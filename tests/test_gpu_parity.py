@@ -86,12 +86,12 @@ def clumpy():
     h, route = oracle_h(p)
     cells = sample_cells(g.ncell, 400, 5)
     ref = oracle.map_cells(g, p.x, p.y, p.z, p.m, h, cells=cells)
-    return p, g, h, cells, ref
+    return p, g, h, cells, ref, route
 
 
 @pytest.mark.parametrize("precision", [0, 1])
 def test_clumpy_sampled_cells(clumpy, precision):
-    p, g, h, cells, ref = clumpy
+    p, g, h, cells, ref, _ = clumpy
     out = gpu_map(g, p, h, precision)
     for k, c in enumerate(cells):
         a = out["idx"][out["off"][c]:out["off"][c + 1]]
@@ -100,6 +100,26 @@ def test_clumpy_sampled_cells(clumpy, precision):
     cell_tol, _ = TOL[precision]
     e = rel_err(out["mass"][cells], ref["mass"], floor_frac=1e-12)
     assert e.max() < cell_tol, (e.max(), np.percentile(e, 99))
+
+
+@pytest.mark.parametrize("precision,tol", [(0, 1e-9), (1, 1e-6)])
+def test_solve_h_clumpy(clumpy, precision, tol):
+    """Clumpy set: a wide spread of h, some particles whose Newton iterates
+    leave [h0/16, 16 h0] and finish by bisection (route 1)."""
+    p, _, h_ref, _, _, route_ref = clumpy
+    assert np.count_nonzero(route_ref == 1) > 0
+    L = lib()
+    ctx = L.map_init(L.map_config_default(precision=precision))
+    try:
+        x, y, z, m, hh = dev_particles(p)
+        route = __import__("torch").empty(p.n, dtype=__import__("torch").int32, device="cuda")
+        L.solve_h(ctx, L.make_particles(x, y, z, None, hh), route)
+        h = hh.cpu().numpy()
+        r = route.cpu().numpy()
+    finally:
+        L.map_destroy(ctx)
+    assert np.array_equal(r, route_ref), np.nonzero(r != route_ref)
+    assert np.max(np.abs(h / h_ref - 1)) < tol
 
 
 def test_edge_cases_tiny_and_huge_support():
