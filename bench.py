@@ -36,6 +36,7 @@ if ROOT not in sys.path:
 
 N_PARTICLES = 1 << 20
 SIGMA = 1.5
+OUTDIR = [os.path.join(ROOT, "bench_out")]  # clock samples and --dump output
 WORKLOAD = "clumpy cloud: 2^20 equal-mass particles, log-normal field (GRF P(k)~k^-4, 128^3, sigma_ln_rho=1.5), clipped Voronoi grid, mixed FP32/FP64"
 
 
@@ -62,7 +63,7 @@ class ClockSampler:
     def __init__(self, gpu_index: int):
         self.gpu = gpu_index
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_rank{gpu_index}.csv")
+        self.path = os.path.join(OUTDIR[0], f"clocks_rank{gpu_index}.csv")
 
     def start(self):
         try:
@@ -106,7 +107,7 @@ class ClockSampler:
 # Algorithmic operation model of the pair-integral kernel (per counted unit):
 # (FP32-pipe ops, MUFU ops), counted from the formulas as written, with an
 # IEEE divide = 1 MUFU + 8, sqrt = 1 MUFU + 3, atan/atan2 = 1 MUFU + 18-22,
-# asinh = 2 MUFU + 20.  See the design doc for the derivation.
+# asinh = 2 MUFU + 20.
 OPS = {
     "face_tests": (6, 0),            # r0 = d'/h - n.y, side, |.|
     "edge_records": (11, 0),         # R0, along-edge a_a, a_b, side
@@ -229,8 +230,8 @@ def run_ours(args):
         mass_mixed_h64 = mass.cpu().numpy()
         L.map_destroy(ctxm)
         if args.dump:
-            os.makedirs(os.path.join(ROOT, "gpurun_out"), exist_ok=True)
-            np.savez(os.path.join(ROOT, "gpurun_out", "cells.npz"), mass_mixed=mass_mixed, mass_fp64=mass_fp64,
+            os.makedirs(OUTDIR[0], exist_ok=True)
+            np.savez(os.path.join(OUTDIR[0], "cells.npz"), mass_mixed=mass_mixed, mass_fp64=mass_fp64,
                      mass_mixed_h64=mass_mixed_h64, h_mixed=h_mixed, h_fp64=h_fp64)
         fp64 = {"value": st64.n_pairs * world / (ms64 * 1e-3), "ms_per_step": ms64, "steps": 1, "warmup": 0,
                 "integrals_ms": integ64, "phases_ms": {k: round(v, 3) for k, v in phases64.items()}}
@@ -288,6 +289,254 @@ def run_ours(args):
         print(json.dumps(line), flush=True)
     if world > 1:
         torch.distributed.destroy_process_group()
+
+
+BATCH_WORKLOAD = ("batched uneven instances: {n} snapshots, particle counts log-uniform in [2^10, 2^18], half uniform, "
+                  "half log-normal clumpy (sigma_ln_rho 1.0-2.0, 64^3 GRF), clipped Voronoi grids, one persistent "
+                  "launch, mixed FP32/FP64")
+
+
+def run_batch(args):
+    """Batched workload: every step solves h for each snapshot and maps all of
+    them with one map_batch call (one persistent integral launch through a
+    CUDA graph; launch shape chosen by the autotuner in the first warm-up)."""
+    import torch
+    import paper_2404_17084_gb300 as L
+    import synth
+
+    rank, world, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    specs = synth.batch_specs(args.nsnap, synth.BASE_SEED + 4 + 1000 * rank)
+    t0 = time.perf_counter()
+    snaps = []
+    for spec in specs:
+        p = synth.batch_particles(spec)
+        snaps.append((p, synth.voronoi(p.pos())))
+    gen_s = time.perf_counter() - t0
+    ctx = L.map_init(L.map_config_default(precision=L.MAP_MIXED, device=local, autotune=1))
+    t = lambda a: torch.as_tensor(np.ascontiguousarray(a), dtype=torch.float64, device=dev)
+    handles, parts, hparts, keep, mass = [], [], [], [], []
+    for p, g in snaps:
+        handles.append(L.map_grid_upload(ctx, L.grid_to_device(g, dev)))
+        x, y, z, m = t(p.x), t(p.y), t(p.z), t(p.m)
+        h = torch.empty_like(x)
+        keep.append((x, y, z, m, h))
+        parts.append(L.make_particles(x, y, z, m, h))
+        hparts.append(L.make_particles(x, y, z, None, h))
+        mass.append(torch.empty(g.ncell, dtype=torch.float64, device=dev))
+    totals = torch.empty(len(snaps), dtype=torch.float64, device=dev)
+
+    def step():
+        for hp in hparts:
+            L.solve_h(ctx, hp)
+        L.map_batch(ctx, parts, handles, mass, totals=totals)
+
+    def barrier():
+        torch.cuda.synchronize()
+        if world > 1:
+            torch.distributed.barrier()
+
+    for _ in range(args.warmup):
+        step()
+    barrier()
+    _, l0 = L.map_get_work(ctx)
+    sampler = ClockSampler(local)
+    sampler.start()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    integ = []
+    e0.record()
+    for _ in range(args.steps):
+        step()
+        integ.append(L.map_get_timing(ctx)["integrals"])
+    e1.record()
+    torch.cuda.synchronize()
+    clocks = sampler.stop()
+    ms = e0.elapsed_time(e1) / args.steps
+    if world > 1:
+        tt = torch.tensor([ms], device=dev)
+        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
+        ms = float(tt.item())
+    st = L.map_get_stats(ctx)
+    work, l1 = L.map_get_work(ctx)
+    chosen, tune_ms = L.map_get_autotune(ctx)
+    integ_ms = float(np.mean(integ))
+    batch_mass = [mm.cpu().numpy() for mm in mass]
+    # the same snapshots one call at a time (mapping only, h as solved above)
+    torch.cuda.synchronize()
+    s0 = time.perf_counter()
+    single_mass = []
+    for j, (p, g) in enumerate(snaps):
+        out = torch.empty(g.ncell, dtype=torch.float64, device=dev)
+        L.map_particles_to_cells(ctx, parts[j], handles[j], out)
+        single_mass.append(out)
+    torch.cuda.synchronize()
+    single_s = time.perf_counter() - s0
+    same = all(np.array_equal(a, b.cpu().numpy()) for a, b in zip(batch_mass, single_mass))
+    f32, mufu = algorithmic_ops(work, st.n_edge_terms, True)
+    sm_count = torch.cuda.get_device_properties(dev).multi_processor_count
+    f_clk = (clocks or {}).get("sm_max_mhz") or 2070.0
+    peak_ops = sm_count * 128 * f_clk * 1e6
+    achieved = max(f32, 8.0 * mufu) / (integ_ms * 1e-3)
+    n_part = int(sum(p.n for p, _ in snaps))
+    line = {
+        "metric": "particle-cell pair integrals/sec at 1 GB300 (mixed vs FP64 form) + p50/p99 latency",
+        "value": st.n_pairs * world / (ms * 1e-3),
+        "unit": "pair integrals/s",
+        "n_gpus": world,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": ms,
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f32+f64",
+        "data": "synthetic",
+        "config": {"workload": BATCH_WORKLOAD.format(n=len(snaps)), "n_snapshots": len(snaps),
+                   "n_particles": n_part, "n_pairs": int(st.n_pairs),
+                   "l2": "inputs larger than L2 (grids and pair lists several GB)",
+                   "step": "per snapshot solve_h, then one map_batch (octree + pair list per snapshot, one "
+                           "persistent integral launch over all snapshots)"},
+        "batch": {"integrals_ms": integ_ms, "integral_launch_pairs_per_s": st.n_pairs / (integ_ms * 1e-3),
+                  "autotune": {"chosen": chosen, "ms_per_shape": tune_ms,
+                               "shapes": ["4 warps/CTA, 5 CTAs/SM", "4 warps/CTA, 4 CTAs/SM",
+                                          "4 warps/CTA, 6 CTAs/SM"]},
+                  "one_call_per_snapshot_mapping_s": single_s, "batched_equals_single": bool(same),
+                  "host_input_generation_s": gen_s},
+        "roofline": {"bound": "alu", "kernel": "pair_integrals<float,mixed> (batched launch)",
+                     "achieved": achieved / 1e12, "peak": peak_ops / 1e12, "unit": "Tops/s (FP32 issue slots)",
+                     "frac": achieved / peak_ops, "traffic": None, "launch_ms": integ_ms},
+        "e2e": None,
+        "gpu_launches": int((l1 - l0) // max(args.steps, 1) * args.steps),
+        "clocks": clocks,
+        "stats": {"edge_terms": int(st.n_edge_terms), "total_mass": st.total_mass,
+                  **{k: int(v) for k, v in work.items()}},
+    }
+    L.map_destroy(ctx)
+    if world > 1:
+        torch.distributed.barrier()
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+SERVE_WORKLOAD = ("serving loop: Poisson stream of {n} mapping requests ({pool} distinct), particle counts "
+                  "log-normal in log2 (median 2^15, sigma 1.5) clipped to [2^12, 2^21], random uniform / log-normal "
+                  "clumpy fields, host inputs and outputs, {slots} slots admitted by HBM, mixed FP32/FP64")
+
+
+def serve_specs(k: int, seed: int):
+    rng = np.random.default_rng(seed)
+    l2 = np.clip(rng.normal(15.0, 1.5, k), 12.0, 21.0)
+    kinds = rng.choice(["uniform", "clumpy"], size=k)
+    sig = rng.uniform(1.0, 2.0, k)
+    seeds = rng.integers(1, 2**31, k)
+    return [(int(2.0 ** l2[j]), str(kinds[j]), float(sig[j]), int(seeds[j])) for j in range(k)]
+
+
+def run_serve(args):
+    """Serving workload: requests (host arrays) arrive as a Poisson stream and
+    go through the library's serving loop (continuous batching over slots,
+    admission by HBM); throughput and p50/p99 latency are measured on the
+    host clock from submission to results in host memory."""
+    import threading
+    import torch
+    import paper_2404_17084_gb300 as L
+    import synth
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    t0 = time.perf_counter()
+    pool = []
+    for spec in serve_specs(args.pool, synth.BASE_SEED + 5 + 1000 * rank):
+        p = synth.batch_particles(spec)
+        pool.append((p, synth.voronoi(p.pos())))
+    gen_s = time.perf_counter() - t0
+    srv = L.map_server_create(L.map_server_config_default(device=local, precision=L.MAP_MIXED, slots=args.slots))
+    outs = [np.empty(g.ncell) for _, g in pool]
+
+    def burst(idx):
+        ts = [L.map_server_submit(srv, pool[j][0].x, pool[j][0].y, pool[j][0].z, pool[j][0].m, pool[j][1],
+                                  outs[j]) for j in idx]
+        return [L.map_server_wait(srv, t) for t in ts]
+
+    # warm-up and capacity: the whole pool back to back (all queued at once)
+    for _ in range(max(1, args.warmup // 3)):
+        burst(range(len(pool)))
+    c0 = time.perf_counter()
+    res = burst(range(len(pool)))
+    cap_s = time.perf_counter() - c0
+    capacity = len(pool) / cap_s
+    rate = args.rate if args.rate > 0 else 0.8 * capacity
+    rng = np.random.default_rng(synth.BASE_SEED + 6)
+    order = rng.integers(0, len(pool), args.requests)
+    gaps = rng.exponential(1.0 / rate, args.requests)
+    tickets = [None] * args.requests
+    out_bufs = [np.empty(pool[j][1].ncell) for j in order]
+
+    def submitter():
+        t_next = time.perf_counter()
+        for i, j in enumerate(order):
+            t_next += gaps[i]
+            d = t_next - time.perf_counter()
+            if d > 0:
+                time.sleep(d)
+            p, g = pool[j]
+            tickets[i] = L.map_server_submit(srv, p.x, p.y, p.z, p.m, g, out_bufs[i])
+
+    sampler = ClockSampler(local)
+    sampler.start()
+    w0 = time.perf_counter()
+    th = threading.Thread(target=submitter)
+    th.start()
+    results = []
+    for i in range(args.requests):
+        while tickets[i] is None:
+            time.sleep(0.0005)
+        results.append(L.map_server_wait(srv, tickets[i]))
+    wall = time.perf_counter() - w0
+    th.join()
+    clocks = sampler.stop()
+    L.map_server_destroy(srv)
+    ok = all(r.status == 0 for r in results)
+    same = all(np.array_equal(out_bufs[i], outs[order[i]]) for i in range(args.requests))
+    lat = np.array([r.latency_ms for r in results])
+    que = np.array([r.queue_ms for r in results])
+    pairs = int(sum(r.n_pairs for r in results))
+    line = {
+        "metric": "particle-cell pair integrals/sec at 1 GB300 (mixed vs FP64 form) + p50/p99 latency",
+        "value": pairs / wall,
+        "unit": "pair integrals/s",
+        "n_gpus": 1,
+        "steps": args.requests,
+        "warmup": args.warmup,
+        "ms_per_step": wall * 1e3 / args.requests,
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f32+f64",
+        "data": "synthetic",
+        "config": {"workload": SERVE_WORKLOAD.format(n=args.requests, pool=len(pool), slots=args.slots),
+                   "arrival_rate_per_s": rate, "capacity_per_s": capacity,
+                   "step": "one request: copy-in, grid upload, solve_h, pair list, pair integrals, copy-out"},
+        "serving": {"requests_per_s": args.requests / wall, "latency_ms": {"p50": float(np.percentile(lat, 50)),
+                    "p99": float(np.percentile(lat, 99)), "max": float(lat.max())},
+                    "queue_ms": {"p50": float(np.percentile(que, 50)), "p99": float(np.percentile(que, 99))},
+                    "all_ok": bool(ok), "results_equal_to_first_pass": bool(same),
+                    "n_particles_p50": int(np.median([pool[j][0].n for j in order])),
+                    "host_input_generation_s": gen_s},
+        "e2e": {"value": pairs / wall, "unit": "pair integrals/s",
+                "h2d_bytes_per_step": int(np.mean([pool[j][0].n * 32 + pool[j][1].nbytes() for j in order])),
+                "d2h_bytes_per_step": int(np.mean([pool[j][1].ncell * 8 for j in order]))},
+        "gpu_launches": None,
+        "clocks": clocks,
+    }
+    if rank == 0:
+        print(json.dumps(line), flush=True)
 
 
 def e2e_run(L, torch, ctx, p, g, dev, args, barrier, world):
@@ -421,10 +670,25 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--skip-fp64", action="store_true")
     ap.add_argument("--skip-e2e", action="store_true")
-    ap.add_argument("--dump", action="store_true", help="save per-cell results to gpurun_out/cells.npz")
+    ap.add_argument("--dump", action="store_true", help="save per-cell results to <outdir>/cells.npz")
+    ap.add_argument("--outdir", default=os.path.join(ROOT, "bench_out"),
+                    help="folder for the clock samples and --dump output")
+    ap.add_argument("--workload", default="clumpy", choices=["clumpy", "batch", "serve"],
+                    help="clumpy: one 2^20 snapshot (default); batch: uneven snapshots in one launch; "
+                         "serve: Poisson stream of requests through the serving loop")
+    ap.add_argument("--pool", type=int, default=32, help="distinct requests of the serve workload")
+    ap.add_argument("--requests", type=int, default=160, help="requests submitted in the serve workload")
+    ap.add_argument("--rate", type=float, default=0.0, help="serve arrival rate (req/s); 0 = 80%% of capacity")
+    ap.add_argument("--slots", type=int, default=4, help="serving slots")
+    ap.add_argument("--nsnap", type=int, default=256, help="snapshots of the batch workload")
     args = ap.parse_args()
+    OUTDIR[0] = args.outdir
     if args.impl == "reference":
         run_reference(args)
+    elif args.workload == "batch":
+        run_batch(args)
+    elif args.workload == "serve":
+        run_serve(args)
     else:
         run_ours(args)
 

@@ -212,6 +212,77 @@ int map_batch(map_ctx* ctx, int nsnap, const map_particles* parts, const int* gr
  * not run).  ms must hold at least 8 floats. */
 int map_get_autotune(map_ctx* ctx, int* chosen, float* ms, int* nvariants);
 
+/* ------------------------------------------------------------ serving */
+
+/* A request loop with continuous batching (the paper has no counterpart: it
+ * maps one snapshot at a time).  Requests carry host arrays; the server runs
+ * up to `slots` of them at once, each on its own context and CUDA stream, so
+ * their work overlaps on the device.  Queued requests are admitted in arrival
+ * order as soon as a slot is idle and the request's device-memory estimate
+ * fits hbm_budget next to what running requests and idle slots' cached
+ * workspace hold (idle caches are released to make room).  A request runs:
+ * copy-in, grid upload, solve_h, map_particles_to_cells, copy-out.  Its
+ * result depends on its own inputs only, so it is bit-identical alone and in
+ * any mix.  Threads: submit, wait and stats may be called from any thread. */
+typedef struct map_server map_server;
+
+typedef struct {
+  int device;        /* CUDA device ordinal */
+  int precision;     /* MAP_FP64 or MAP_MIXED (default) */
+  int slots;         /* requests on the device at once; default 4, 1..64 */
+  size_t hbm_budget; /* bytes the server may hold; 0 = 90% of the free memory at creation */
+  double hfact;      /* Eq. (7); default 1.2 */
+} map_server_config;
+
+/* One mapping request.  All pointers are HOST memory owned by the caller and
+ * must stay valid until map_server_wait returns for the request.  The grid
+ * arrays follow map_grid; cell_mass (ncell) is required, cell_rho (ncell) and
+ * h (n, the solved smoothing lengths) are optional outputs. */
+typedef struct {
+  int64_t n;
+  const double *x, *y, *z, *m;
+  int64_t ncell, nface, nloop, nvert;
+  const int64_t* cell_face_off;
+  const int64_t* face_vert_off;
+  const int32_t* face_vert;
+  const double *face_plane, *vx, *vy, *vz, *site;
+  double* cell_mass;
+  double* cell_rho;
+  double* h;
+} map_request;
+
+typedef struct {
+  int status;            /* MAP_OK, or MAP_ENOMEM when the request alone exceeds the budget, or the
+                            first error of its steps */
+  int64_t n_pairs;       /* pair integrals of the request */
+  double total_mass;     /* sum_i M_i */
+  double queue_ms;       /* submit to admission */
+  double latency_ms;     /* submit to results in host memory */
+  size_t bytes_reserved; /* the admission estimate */
+} map_request_result;
+
+void map_server_config_default(map_server_config* cfg);
+
+/* Start a server (its contexts, streams and worker threads).
+ * Errors: MAP_EINVAL, MAP_ENOMEM, MAP_ECUDA. */
+int map_server_create(const map_server_config* cfg, map_server** srv);
+
+/* Queue a request; *ticket identifies it.  Returns at once.
+ * Errors: MAP_EINVAL (missing arrays, inconsistent sizes, server stopping). */
+int map_server_submit(map_server* srv, const map_request* req, int64_t* ticket);
+
+/* Block until the request is done and fill *res (may be NULL).  A ticket can
+ * be waited for once.  Errors: MAP_EINVAL (unknown ticket). */
+int map_server_wait(map_server* srv, int64_t ticket, map_request_result* res);
+
+/* Requests completed so far, running now, queued, and the bytes the server
+ * holds or has reserved. */
+int map_server_stats(map_server* srv, int64_t* completed, int* running, int64_t* queued, size_t* held_bytes);
+
+/* Fail the queued requests, wait for the running ones, stop the workers and
+ * free everything. */
+void map_server_destroy(map_server* srv);
+
 /* ------------------------------------------------------------ smoothing lengths (Section III-C, Eq. 7-9) */
 
 /* Solve h_a = hfact * n_a(h_a)^(-1/3), n_a(h) = sum_b W(|r_a - r_b|, h)

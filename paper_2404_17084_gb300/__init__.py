@@ -14,6 +14,7 @@ from __future__ import annotations
 import ctypes
 import os
 
+import numpy as np
 import torch
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
@@ -85,6 +86,34 @@ _lib.solve_h.argtypes = [_P, ctypes.POINTER(map_particles), _P, _P]
 _lib.build_pseudo_particles.argtypes = [_P, ctypes.POINTER(map_particles), ctypes.POINTER(ctypes.c_double),
                                         ctypes.c_int, ctypes.POINTER(map_particles), _P, _P,
                                         ctypes.POINTER(_I64), _P]
+class map_server_config(ctypes.Structure):
+    _fields_ = [("device", ctypes.c_int), ("precision", ctypes.c_int), ("slots", ctypes.c_int),
+                ("hbm_budget", ctypes.c_size_t), ("hfact", ctypes.c_double)]
+
+
+class map_request(ctypes.Structure):
+    _fields_ = [("n", _I64), ("x", _P), ("y", _P), ("z", _P), ("m", _P), ("ncell", _I64), ("nface", _I64),
+                ("nloop", _I64), ("nvert", _I64), ("cell_face_off", _P), ("face_vert_off", _P),
+                ("face_vert", _P), ("face_plane", _P), ("vx", _P), ("vy", _P), ("vz", _P), ("site", _P),
+                ("cell_mass", _P), ("cell_rho", _P), ("h", _P)]
+
+
+class map_request_result(ctypes.Structure):
+    _fields_ = [("status", ctypes.c_int), ("n_pairs", _I64), ("total_mass", ctypes.c_double),
+                ("queue_ms", ctypes.c_double), ("latency_ms", ctypes.c_double), ("bytes_reserved", ctypes.c_size_t)]
+
+
+_lib.map_server_config_default.argtypes = [ctypes.POINTER(map_server_config)]
+_lib.map_server_config_default.restype = None
+_lib.map_server_create.argtypes = [ctypes.POINTER(map_server_config), ctypes.POINTER(_P)]
+_lib.map_server_submit.argtypes = [_P, ctypes.POINTER(map_request), ctypes.POINTER(_I64)]
+_lib.map_server_wait.argtypes = [_P, _I64, ctypes.POINTER(map_request_result)]
+_lib.map_server_stats.argtypes = [_P, ctypes.POINTER(_I64), ctypes.POINTER(ctypes.c_int), ctypes.POINTER(_I64),
+                                  ctypes.POINTER(ctypes.c_size_t)]
+_lib.map_server_destroy.argtypes = [_P]
+_lib.map_server_destroy.restype = None
+for _name in ("map_server_create", "map_server_submit", "map_server_wait", "map_server_stats"):
+    getattr(_lib, _name).restype = ctypes.c_int
 _lib.map_batch.argtypes = [_P, ctypes.c_int, ctypes.POINTER(map_particles), ctypes.POINTER(ctypes.c_int),
                            ctypes.POINTER(map_outputs), _P, _P]
 _lib.map_get_autotune.argtypes = [_P, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_float),
@@ -195,6 +224,84 @@ def map_get_autotune(ctx):
     ms = (ctypes.c_float * 8)()
     _check(_lib.map_get_autotune(ctx, ctypes.byref(c), ms, ctypes.byref(nv)), "map_get_autotune")
     return c.value, [ms[i] for i in range(nv.value)]
+
+
+# ---------------------------------------------------------------- serving
+
+def map_server_config_default(**overrides) -> map_server_config:
+    cfg = map_server_config()
+    _lib.map_server_config_default(ctypes.byref(cfg))
+    for k, v in overrides.items():
+        setattr(cfg, k, v)
+    return cfg
+
+
+_server_keep = {}  # (server, ticket) -> host arrays kept alive until the wait
+
+
+def map_server_create(cfg: map_server_config | None = None) -> ctypes.c_void_p:
+    srv = ctypes.c_void_p()
+    _check(_lib.map_server_create(ctypes.byref(cfg) if cfg is not None else None, ctypes.byref(srv)),
+           "map_server_create")
+    return srv
+
+
+def _host(a, dtype):
+    a = np.ascontiguousarray(a, dtype=dtype)
+    return a, ctypes.c_void_p(a.ctypes.data)
+
+
+def map_server_submit(srv, x, y, z, m, grid, cell_mass, cell_rho=None, h=None) -> int:
+    """Queue one request of host (numpy) arrays: particles x, y, z, m and a
+    grid (synth.Grid or dict of its CSR arrays); cell_mass (ncell float64,
+    written on completion) and optional cell_rho, h.  Returns the ticket."""
+    G = grid if isinstance(grid, dict) else {k: getattr(grid, k) for k in (
+        "cell_face_off", "face_vert_off", "face_vert", "face_plane", "vx", "vy", "vz", "site")}
+    keep = []
+    def ptr(a, dt):
+        arr, p = _host(a, dt)
+        keep.append(arr)
+        return p
+    for out in (cell_mass, cell_rho, h):
+        if out is not None and not (isinstance(out, np.ndarray) and out.dtype == np.float64
+                                    and out.flags["C_CONTIGUOUS"]):
+            raise ValueError("outputs must be contiguous float64 numpy arrays")
+    req = map_request(len(x), ptr(x, np.float64), ptr(y, np.float64), ptr(z, np.float64), ptr(m, np.float64),
+                      len(G["cell_face_off"]) - 1, len(G["face_vert_off"]) - 1, len(G["face_vert"]), len(G["vx"]),
+                      ptr(G["cell_face_off"], np.int64), ptr(G["face_vert_off"], np.int64),
+                      ptr(G["face_vert"], np.int32), ptr(G["face_plane"], np.float64), ptr(G["vx"], np.float64),
+                      ptr(G["vy"], np.float64), ptr(G["vz"], np.float64), ptr(G["site"], np.float64),
+                      ctypes.c_void_p(cell_mass.ctypes.data),
+                      ctypes.c_void_p(cell_rho.ctypes.data) if cell_rho is not None else None,
+                      ctypes.c_void_p(h.ctypes.data) if h is not None else None)
+    keep += [cell_mass, cell_rho, h]
+    t = _I64()
+    _check(_lib.map_server_submit(srv, ctypes.byref(req), ctypes.byref(t)), "map_server_submit")
+    _server_keep[(srv.value, t.value)] = keep
+    return t.value
+
+
+def map_server_wait(srv, ticket: int) -> map_request_result:
+    res = map_request_result()
+    _check(_lib.map_server_wait(srv, ticket, ctypes.byref(res)), "map_server_wait")
+    _server_keep.pop((srv.value, ticket), None)
+    return res
+
+
+def map_server_stats(srv):
+    """(completed, running, queued, held_bytes)."""
+    c, q = _I64(), _I64()
+    r = ctypes.c_int()
+    b = ctypes.c_size_t()
+    _check(_lib.map_server_stats(srv, ctypes.byref(c), ctypes.byref(r), ctypes.byref(q), ctypes.byref(b)),
+           "map_server_stats")
+    return c.value, r.value, q.value, b.value
+
+
+def map_server_destroy(srv) -> None:
+    _lib.map_server_destroy(srv)
+    for k in [k for k in _server_keep if k[0] == srv.value]:
+        _server_keep.pop(k, None)
 
 
 def map_get_pairs(ctx):

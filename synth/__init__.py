@@ -98,6 +98,11 @@ class Grid:
     def nface(self) -> int:
         return int(self.face_vert_off.shape[0] - 1)
 
+    def nbytes(self) -> int:
+        """Bytes of the CSR arrays a mapping call reads (face_nb excluded)."""
+        return int(sum(a.nbytes for a in (self.cell_face_off, self.face_vert_off, self.face_vert, self.face_plane,
+                                          self.vx, self.vy, self.vz, self.site)))
+
 
 def rng_for(config: int, salt: int = 0) -> np.random.Generator:
     return np.random.default_rng(BASE_SEED + config + 1000 * salt)
@@ -142,6 +147,27 @@ def lognormal_particles(n: int, seed: int, sigma: float = 1.5, ngrid: int = 128,
     z = (iz + u[:, 2]) / ngrid
     m = np.full(n, 1.0 / n)
     return Particles(x, y, z, m)
+
+
+def batch_specs(nsnap: int, seed: int, log2_lo: float = 10.0, log2_hi: float = 18.0):
+    """Uneven batch of independent snapshots: particle counts log-uniform in
+    [2^log2_lo, 2^log2_hi]; half uniform, half log-normal clumpy with
+    sigma_ln_rho uniform in [1, 2].  Returns (n, kind, sigma, seed) tuples."""
+    rng = np.random.default_rng(seed)
+    n = np.exp(rng.uniform(log2_lo * np.log(2.0), log2_hi * np.log(2.0), nsnap)).astype(np.int64)
+    kind = np.array(["uniform", "clumpy"] * ((nsnap + 1) // 2))[:nsnap]
+    rng.shuffle(kind)
+    sigma = rng.uniform(1.0, 2.0, nsnap)
+    seeds = rng.integers(1, 2**31, nsnap)
+    return [(int(n[j]), str(kind[j]), float(sigma[j]), int(seeds[j])) for j in range(nsnap)]
+
+
+def batch_particles(spec) -> Particles:
+    """The particles of one batch_specs entry (clumpy fields on a 64^3 grid)."""
+    n, kind, sigma, seed = spec
+    if kind == "uniform":
+        return uniform_particles(n, seed)
+    return lognormal_particles(n, seed, sigma=sigma, ngrid=64)
 
 
 def lattice_particles(nside: int, jitter: float = 0.0, seed: int = 0) -> Particles:
