@@ -46,9 +46,40 @@ def dist_env():
     return int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)), int(os.environ.get("LOCAL_RANK", 0))
 
 
+def dist_init(world: int):
+    """One process per GPU: NCCL with GPUs, gloo without (host-logic tests)."""
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+
+
+def rank_seed(base: int, rank: int) -> int:
+    """Each rank maps its own snapshot (weak scaling, no data-path collective)."""
+    return base + 1000 * rank
+
+
+def max_over_ranks(ms: float, world: int, device=None) -> float:
+    """The slowest rank's time: the job's time."""
+    if world <= 1:
+        return ms
+    import torch
+    t = torch.tensor([ms], dtype=torch.float64, device=device)
+    torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    return float(t.item())
+
+
+def emit(line: dict, rank: int) -> bool:
+    """Rank 0 prints the JSON line; the others print nothing."""
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+        return True
+    return False
+
+
 def make_snapshot(rank: int, n: int):
     import synth
-    p = synth.lognormal_particles(n, synth.BASE_SEED + 2 + 1000 * rank, sigma=SIGMA)
+    p = synth.lognormal_particles(n, rank_seed(synth.BASE_SEED + 2, rank), sigma=SIGMA)
     g = synth.voronoi(p.pos())
     return p, g
 
@@ -148,9 +179,7 @@ def run_ours(args):
     import paper_2404_17084_gb300 as L
 
     rank, world, local = dist_env()
-    if world > 1:
-        import torch.distributed as dist
-        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    dist_init(world)
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
 
@@ -167,7 +196,8 @@ def run_ours(args):
             torch.distributed.barrier()
 
     def setup(precision):
-        ctx = L.map_init(L.map_config_default(precision=precision, device=local))
+        # the first warm-up step of the mixed build runs the launch-shape autotuner
+        ctx = L.map_init(L.map_config_default(precision=precision, device=local, autotune=1))
         handle = L.map_grid_upload(ctx, L.grid_to_device(g, dev))
         return ctx, handle
 
@@ -191,11 +221,7 @@ def run_ours(args):
         e1.record()
         torch.cuda.synchronize()
         clocks = sampler.stop() if sampler else None
-        ms = e0.elapsed_time(e1) / steps
-        if world > 1:
-            tt = torch.tensor([ms], device=dev)
-            torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
-            ms = float(tt.item())
+        ms = max_over_ranks(e0.elapsed_time(e1) / steps, world, dev)
         st = L.map_get_stats(ctx)
         work, l1 = L.map_get_work(ctx)
         phases = L.map_get_timing(ctx)
@@ -205,6 +231,7 @@ def run_ours(args):
     ctx, handle = setup(L.MAP_MIXED)
     sampler = ClockSampler(local)
     ms, st, work, launches, integ_ms, phases, clocks = timed(ctx, handle, args.steps, args.warmup, sampler)
+    tune_chosen, tune_ms = L.map_get_autotune(ctx)
     n_pairs = st.n_pairs
     mass_mixed = mass.cpu().numpy()
     h_mixed = h.cpu().numpy()
@@ -268,6 +295,8 @@ def run_ours(args):
         "e2e": e2e,
         "gpu_launches": int(launches),
         "clocks": clocks,
+        "autotune": {"chosen": tune_chosen, "ms_per_shape": tune_ms,
+                     "shapes": ["4 warps/CTA, 5 CTAs/SM", "4 warps/CTA, 4 CTAs/SM", "4 warps/CTA, 6 CTAs/SM"]},
         "stats": {"edge_terms": int(st.n_edge_terms), "total_mass": st.total_mass, **{k: int(v) for k, v in work.items()}},
     }
     if mass_fp64 is not None:
@@ -285,8 +314,7 @@ def run_ours(args):
         line["accuracy_vs_oracle"] = acc
     if world > 1:
         torch.distributed.barrier()
-    if rank == 0:
-        print(json.dumps(line), flush=True)
+    emit(line, rank)
     if world > 1:
         torch.distributed.destroy_process_group()
 
@@ -305,12 +333,10 @@ def run_batch(args):
     import synth
 
     rank, world, local = dist_env()
-    if world > 1:
-        import torch.distributed as dist
-        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    dist_init(world)
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
-    specs = synth.batch_specs(args.nsnap, synth.BASE_SEED + 4 + 1000 * rank)
+    specs = synth.batch_specs(args.nsnap, rank_seed(synth.BASE_SEED + 4, rank))
     t0 = time.perf_counter()
     snaps = []
     for spec in specs:
@@ -355,11 +381,7 @@ def run_batch(args):
     e1.record()
     torch.cuda.synchronize()
     clocks = sampler.stop()
-    ms = e0.elapsed_time(e1) / args.steps
-    if world > 1:
-        tt = torch.tensor([ms], device=dev)
-        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
-        ms = float(tt.item())
+    ms = max_over_ranks(e0.elapsed_time(e1) / args.steps, world, dev)
     st = L.map_get_stats(ctx)
     work, l1 = L.map_get_work(ctx)
     chosen, tune_ms = L.map_get_autotune(ctx)
@@ -418,8 +440,7 @@ def run_batch(args):
     L.map_destroy(ctx)
     if world > 1:
         torch.distributed.barrier()
-    if rank == 0:
-        print(json.dumps(line), flush=True)
+    emit(line, rank)
     if world > 1:
         torch.distributed.destroy_process_group()
 
@@ -452,7 +473,7 @@ def run_serve(args):
     torch.cuda.set_device(local)
     t0 = time.perf_counter()
     pool = []
-    for spec in serve_specs(args.pool, synth.BASE_SEED + 5 + 1000 * rank):
+    for spec in serve_specs(args.pool, rank_seed(synth.BASE_SEED + 5, rank)):
         p = synth.batch_particles(spec)
         pool.append((p, synth.voronoi(p.pos())))
     gen_s = time.perf_counter() - t0
@@ -535,8 +556,7 @@ def run_serve(args):
         "gpu_launches": None,
         "clocks": clocks,
     }
-    if rank == 0:
-        print(json.dumps(line), flush=True)
+    emit(line, rank)
 
 
 def e2e_run(L, torch, ctx, p, g, dev, args, barrier, world):

@@ -47,8 +47,9 @@ typedef struct {
   double hfact;                      /* h = hfact n^(-1/3), Eq. (7); default 1.2 */
   int leaf_size;                     /* octree leaf capacity; default 16 */
   int ngb_bruteforce_max;            /* Section III-D: k_mid neighbour search above this many nodes; default 10000 */
-  int autotune;                      /* 1: map_batch times the pair-integral kernel's launch shapes on the
-                                        context's first mixed batch and keeps the fastest; default 0 */
+  int autotune;                      /* 1: the context's first mixed mapping call (map_batch or
+                                        map_particles_to_cells) times the pair-integral kernel's launch
+                                        shapes and keeps the fastest; default 0 */
   unsigned long long queue_timeout_ns; /* bound on any device-side wait; default 2e9 */
 } map_config;
 

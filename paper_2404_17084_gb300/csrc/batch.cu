@@ -13,11 +13,12 @@
 // launch and the per-snapshot mass sums are captured once in a CUDA graph and
 // replayed while the batch's descriptors are byte-identical.
 //
-// Autotuner: with map_config.autotune set, the first batch of a context in
-// the mixed build runs the integral launch in each of its launch shapes (the
-// register cap per thread, i.e. resident warps per SM, at 4 warps and 4 cells
-// in flight per CTA), times each with CUDA events, and keeps the fastest for
-// every later call of the context.  All shapes compute bit-identical results.
+// Autotuner: with map_config.autotune set, the first mapping call of a
+// context in the mixed build (a batch, or a single snapshot) runs the
+// integral launch in each of its launch shapes (the register cap per thread,
+// i.e. resident warps per SM, at 4 warps and 4 cells in flight per CTA),
+// times each with CUDA events, and keeps the fastest for every later call of
+// the context.  All shapes compute bit-identical results.
 #include <algorithm>
 #include <cstring>
 #include <numeric>
@@ -41,9 +42,11 @@ int ensure_stream(map_ctx* ctx) {
   return MAP_OK;
 }
 
+}  // namespace
+
 // Times each launch shape of the integral kernel on this batch (descriptors
 // already on the device) and records the fastest.
-int autotune(map_ctx* ctx, const BatchArgs& B, cudaStream_t s) {
+int integrals_autotune(map_ctx* ctx, const BatchArgs& B, cudaStream_t s) {
   cudaEvent_t e0, e1;
   CUDA_TRY(cudaEventCreate(&e0));
   CUDA_TRY(cudaEventCreate(&e1));
@@ -68,8 +71,6 @@ int autotune(map_ctx* ctx, const BatchArgs& B, cudaStream_t s) {
   ctx->tune_done[MAP_MIXED] = true;
   return MAP_OK;
 }
-
-}  // namespace
 
 extern "C" {
 
@@ -138,7 +139,7 @@ int map_batch(map_ctx* ctx, int nsnap, const map_particles* parts, const int* gr
   const int prec = ctx->cfg.precision == MAP_MIXED ? MAP_MIXED : MAP_FP64;
   if (ctx->cfg.autotune && prec == MAP_MIXED && !ctx->tune_done[MAP_MIXED]) {
     MAP_TRY(integrals_upload(ctx, qd.data(), base.data(), nsnap, d_desc, d_base, ctx->bstream));
-    MAP_TRY(autotune(ctx, B, ctx->bstream));
+    MAP_TRY(integrals_autotune(ctx, B, ctx->bstream));
   }
   const int variant = ctx->tuned[prec];
   // graph signature: descriptor bytes, queue layout, launch shape, targets

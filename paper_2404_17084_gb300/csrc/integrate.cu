@@ -16,8 +16,9 @@
 // warp evaluates them together (every lane the same code), so the costly
 // evaluations run with all lanes busy; the stacks carry over from edge to
 // edge and are flushed after the last face.  Each result is added to its
-// owner lane's FP64 accumulator, lanes with the same owner in turn, so the
-// order of additions is fixed and every result is bit-reproducible.
+// owner lane's compensated (Kahan) accumulator, lanes with the same owner in
+// turn, so the order of additions is fixed and every result is
+// bit-reproducible.
 // (Mixed build: a face whose plane passes within 1e-4 h of the particle is
 // decided and evaluated in FP64 by the owner lane instead.)
 //
@@ -47,26 +48,23 @@ constexpr double EPS = 1e-12;
 constexpr unsigned FULL = 0xffffffffu;
 constexpr int LCAP = 96;  // stack depth: < 32 left after a drain + up to 2 pieces per lane
 
-// Exclusive warp prefix sum of v; returns the warp total in *tot.
-__device__ __forceinline__ int warp_excl(int v, int* tot) {
-  const int lane = threadIdx.x & 31;
-  int s = v;
-#pragma unroll
-  for (int o = 1; o < 32; o <<= 1) {
-    const int t = __shfl_up_sync(FULL, s, o);
-    if (lane >= o) s += t;
-  }
-  *tot = __shfl_sync(FULL, s, 31);
-  return s - v;
+// Exclusive warp prefix sum of v in {0, 1, 2} (two ballots); returns the
+// warp total in *tot.
+__device__ __forceinline__ int warp_excl2(int v, int* tot) {
+  const unsigned lt = (1u << (threadIdx.x & 31)) - 1u;
+  const unsigned b0 = __ballot_sync(FULL, v & 1), b1 = __ballot_sync(FULL, v & 2);
+  *tot = __popc(b0) + 2 * __popc(b1);
+  return __popc(b0 & lt) + 2 * __popc(b1 & lt);
 }
 
 // Per-warp piece stacks (inner, middle, beyond the support) and the lanes'
-// FP64 accumulators.
+// compensated accumulators.
 template <typename T>
 struct WarpStacks {
   typename Vec4<T>::type e[3][LCAP];  // (r0, R0, lo, hi)
   unsigned char own[3][LCAP];         // owner lane
-  double acc[32];
+  T acc[32];                          // per-owner sum of its pieces ...
+  T cmp[32];                          // ... and its compensation (Kahan)
   SnapDesc d;                         // the snapshot of the warp's current cell
 };
 
@@ -75,8 +73,8 @@ struct WarpStacks {
 // owner lane's accumulator.  Not inlined: the three evaluators then appear
 // once in the kernel's code.
 template <typename T, bool MIXED>
-__device__ __noinline__ void drain(WarpStacks<T>& S, int& cnt0, int& cnt1, int& cnt2, bool flush,
-                                   unsigned long long& t0, unsigned long long& t1, unsigned long long& t2) {
+__device__ __noinline__ void drain(WarpStacks<T>& S, int& cnt0, int& cnt1, int& cnt2, bool flush, unsigned& t0,
+                                   unsigned& t1, unsigned& t2) {
   const int lane = threadIdx.x & 31;
   for (;;) {
     int K, n;
@@ -93,7 +91,7 @@ __device__ __noinline__ void drain(WarpStacks<T>& S, int& cnt0, int& cnt1, int& 
       o = S.own[K][base + lane];
       if (K == 1) v = wedge::piece_mid<T, MIXED>(P.x, P.y, P.z, P.w);
       else if (K == 0) v = wedge::piece_inner<T>(P.x, P.y, P.z, P.w);
-      else v = wedge::piece_outer<T>(P.x, P.y, P.z, P.w);
+      else v = -P.x * wedge::dphi(P.z, P.w, P.y);  // P.x = c0 (see the push)
     }
     // lanes holding pieces of the same owner add in turn, in lane order
     const unsigned grp = __match_any_sync(FULL, o);
@@ -101,7 +99,14 @@ __device__ __noinline__ void drain(WarpStacks<T>& S, int& cnt0, int& cnt1, int& 
     for (int r = 0;; ++r) {
       const bool mine = on && rank == r;
       if (!__any_sync(FULL, mine)) break;
-      if (mine) S.acc[o] += (double)v;
+      if (mine) {
+        // compensated (Kahan) addition: the error stays at a few ulp of the
+        // pair's total however many pieces of either sign it sums
+        const T y = v - S.cmp[o];
+        const T t = S.acc[o] + y;
+        S.cmp[o] = (t - S.acc[o]) - y;
+        S.acc[o] = t;
+      }
       __syncwarp();
     }
   }
@@ -140,7 +145,7 @@ __global__ void __launch_bounds__(NW * 32, MINB) pair_integrals(BatchArgs B) {
   WarpStacks<T>& S = stacks[threadIdx.x >> 5];
   const SnapDesc& A = S.d;
   wedge::WorkCount wc;
-  unsigned long long n_in = 0, n_mid = 0, n_out = 0;
+  unsigned n_in = 0, n_mid = 0, n_out = 0;  // pieces evaluated by this warp
   int n64 = 0;
   unsigned n_split = 0;  // middle intervals split at the foot (counted once, evaluated as two pieces)
   int cur = -1;          // snapshot held in S.d
@@ -170,7 +175,7 @@ __global__ void __launch_bounds__(NW * 32, MINB) pair_integrals(BatchArgs B) {
     const int64_t f0 = A.cfo[c];
     const int nf = (int)(A.cfo[c + 1] - f0);
     const int64_t l0 = A.fvo[f0];
-    const double sx = A.site[3 * c], sy = A.site[3 * c + 1], sz = A.site[3 * c + 2];
+    const T* __restrict__ ecell = edge + l0 * EDGE_STRIDE;
     double macc = 0.0;
     const int64_t pb = A.pair_off[c], pe = A.pair_off[c + 1];
     for (int64_t p0 = pb; p0 < pe; p0 += 32) {
@@ -181,6 +186,7 @@ __global__ void __launch_bounds__(NW * 32, MINB) pair_integrals(BatchArgs B) {
       if (active) {
         a = A.pair_idx[p];
         const double hh = A.h[a];
+        const double sx = A.site[3 * c], sy = A.site[3 * c + 1], sz = A.site[3 * c + 2];
         if (MIXED) {
           const float hi = 1.0f / (float)hh;
           yx = (float)(A.x[a] - sx) * hi;
@@ -195,66 +201,67 @@ __global__ void __launch_bounds__(NW * 32, MINB) pair_integrals(BatchArgs B) {
           hinv = hi;
         }
       }
-      S.acc[lane] = 0.0;
+      S.acc[lane] = T(0);
+      S.cmp[lane] = T(0);
       bool inside = true;
       double dacc = 0.0;
       int cnt0 = 0, cnt1 = 0, cnt2 = 0;  // stack heights (warp-uniform)
-      int64_t kb = A.fvo[f0] - l0;
+      int kb = 0;
       for (int fi = 0; fi < nf; ++fi) {
         const V4 F = face[f0 + fi];
-        const int64_t ke = A.fvo[f0 + fi + 1] - l0;
+        const int ke = (int)(A.fvo[f0 + fi + 1] - l0);
         const T r0s = F.w * hinv - (F.x * yx + F.y * yy + F.z * yz);
         bool fin = r0s >= T(0);
         T r0 = fabs(r0s);
         if (!MIXED) r0 = r0 > T(EPS) ? r0 : T(EPS);
         bool inrange = active && r0 < T(2);
+        const T c0f = wedge::c0_of(r0);
         if (active) wc.faces++;
         if (MIXED && inrange && r0 < T(TAU)) {
           int c64 = 0;
-          dacc += face_fp64(A, f0 + fi, kb, ke, l0, a, sx, sy, sz, fin, c64);
+          dacc += face_fp64(A, f0 + fi, kb, ke, l0, a, A.site[3 * c], A.site[3 * c + 1], A.site[3 * c + 2], fin, c64);
           n64 += c64;
           inrange = false;  // its edges are done
         }
         inside = inside && fin;
         if (__any_sync(FULL, inrange)) {
-          for (int64_t k = kb; k < ke; ++k) {
-            const T* E = edge + (l0 + k) * EDGE_STRIDE;
+          for (int k = kb; k < ke; ++k) {
+            const T* E = ecell + k * EDGE_STRIDE;
             const T e0 = E[0], e1 = E[1], e2 = E[2], e3 = E[3], e4 = E[4], e5 = E[5], e6 = E[6], e7 = E[7], e8 = E[8];
-            int nin = 0, nmid = 0, nout = 0;
-            T R0 = T(0), il = T(0), ih = T(0), ml0 = T(0), mh0 = T(0), ml1 = T(0), mh1 = T(0);
-            T ol0 = T(0), oh0 = T(0), ol1 = T(0), oh1 = T(0);
+            // R0 = m.(p - v_a) (> 0 inside), along-edge vertex positions
+            const T R0s = (e0 * yx + e1 * yy + e2 * yz) - e3 * hinv;
+            const T base = e4 * yx + e5 * yy + e6 * yz;
+            const bool ein = R0s >= T(0);
+            T R0 = fabs(R0s);
+            if (!MIXED) R0 = R0 > T(EPS) ? R0 : T(EPS);
+            const wedge::EdgeSplit<T> P =
+                wedge::split_edge_flat<T>(r0, R0, e7 * hinv - base, e8 * hinv - base, fin == ein, inrange);
+            const int nin = P.v & 1u, nmid = ((P.v >> 1) & 1u) + ((P.v >> 2) & 1u);
+            const int nout = ((P.v >> 3) & 1u) + ((P.v >> 4) & 1u);
             if (inrange) {
-              const T R0s = (e0 * yx + e1 * yy + e2 * yz) - e3 * hinv;  // m.(p - v_a): > 0 inside
-              const T base = e4 * yx + e5 * yy + e6 * yz;
-              const bool ein = R0s >= T(0);
-              R0 = fabs(R0s);
-              if (!MIXED) R0 = R0 > T(EPS) ? R0 : T(EPS);
               wc.edges++;
-              wedge::split_edge<T>(
-                  r0, R0, e7 * hinv - base, e8 * hinv - base, fin == ein,
-                  [&](T l, T h) { il = l; ih = h; nin = 1; },
-                  [&](T l, T h) {
-                    if (MIXED && wedge::straddles(l, h)) {
-                      // two pieces, [l, 0] and [0, h]: this is the only middle piece of the edge
-                      ml0 = l; mh0 = T(0); ml1 = T(0); mh1 = h; nmid = 2; ++n_split;
-                    } else {
-                      if (nmid == 0) { ml0 = l; mh0 = h; } else { ml1 = l; mh1 = h; }
-                      ++nmid;
-                    }
-                  },
-                  [&](T l, T h) { if (nout == 0) { ol0 = l; oh0 = h; } else { ol1 = l; oh1 = h; } ++nout; });
-              if (nin + nmid + nout) wc.terms++;
+              if (P.v) wc.terms++;
+              n_split += P.split;
             }
             // push this edge's pieces (warp-aggregated)
             int t0, t1, t2;
-            const int o0 = cnt0 + warp_excl(nin, &t0);
-            const int o1 = cnt1 + warp_excl(nmid, &t1);
-            const int o2 = cnt2 + warp_excl(nout, &t2);
-            if (nin) { S.e[0][o0] = V4{r0, R0, il, ih}; S.own[0][o0] = (unsigned char)lane; }
-            if (nmid > 0) { S.e[1][o1] = V4{r0, R0, ml0, mh0}; S.own[1][o1] = (unsigned char)lane; }
-            if (nmid > 1) { S.e[1][o1 + 1] = V4{r0, R0, ml1, mh1}; S.own[1][o1 + 1] = (unsigned char)lane; }
-            if (nout > 0) { S.e[2][o2] = V4{r0, R0, ol0, oh0}; S.own[2][o2] = (unsigned char)lane; }
-            if (nout > 1) { S.e[2][o2 + 1] = V4{r0, R0, ol1, oh1}; S.own[2][o2 + 1] = (unsigned char)lane; }
+            const int o0 = cnt0 + warp_excl2(nin, &t0);
+            const int o1 = cnt1 + warp_excl2(nmid, &t1);
+            const int o2 = cnt2 + warp_excl2(nout, &t2);
+            const unsigned char ln = (unsigned char)lane;
+            T lo, hi;
+            if (P.v & 1u) { P.get(0, lo, hi); S.e[0][o0] = V4{r0, R0, lo, hi}; S.own[0][o0] = ln; }
+            if (P.v & 2u) { P.get(1, lo, hi); S.e[1][o1] = V4{r0, R0, lo, hi}; S.own[1][o1] = ln; }
+            if (P.v & 4u) {
+              const int q = o1 + ((P.v >> 1) & 1u);
+              P.get(2, lo, hi); S.e[1][q] = V4{r0, R0, lo, hi}; S.own[1][q] = ln;
+            }
+            // beyond the support only c0 = r0 E(r0) is needed, once per face
+            if (P.v & 8u) { P.get(3, lo, hi); S.e[2][o2] = V4{c0f, R0, lo, hi}; S.own[2][o2] = ln; }
+            if (P.v & 16u) {
+              const int q = o2 + ((P.v >> 3) & 1u);
+              P.get(4, lo, hi); S.e[2][q] = V4{c0f, R0, lo, hi}; S.own[2][q] = ln;
+            }
             cnt0 += t0;
             cnt1 += t1;
             cnt2 += t2;
@@ -269,7 +276,7 @@ __global__ void __launch_bounds__(NW * 32, MINB) pair_integrals(BatchArgs B) {
       if (cnt0 || cnt1 || cnt2) drain<T, MIXED>(S, cnt0, cnt1, cnt2, true, n_in, n_mid, n_out);
       __syncwarp();
       if (active) {
-        const double f = (inside ? 1.0 : 0.0) + dacc + S.acc[lane];
+        const double f = (inside ? 1.0 : 0.0) + dacc + ((double)S.acc[lane] - (double)S.cmp[lane]);
         if (A.frac) A.frac[p] = f;
         macc += A.m[a] * f;
       }
@@ -295,9 +302,9 @@ __global__ void __launch_bounds__(NW * 32, MINB) pair_integrals(BatchArgs B) {
     atomicAdd(&B.counters[2], fp64);
     atomicAdd(&B.counters[8], faces);
     atomicAdd(&B.counters[9], edges);
-    atomicAdd(&B.counters[10], 2 * n_in);
-    atomicAdd(&B.counters[11], n_mid - split);  // intervals: a split one is one interval, two pieces
-    atomicAdd(&B.counters[12], n_out);
+    atomicAdd(&B.counters[10], 2ull * n_in);
+    atomicAdd(&B.counters[11], (unsigned long long)n_mid - split);  // a split interval: one interval, two pieces
+    atomicAdd(&B.counters[12], (unsigned long long)n_out);
     atomicAdd(&B.counters[13], split);
   }
 }
@@ -422,6 +429,8 @@ int integrals_run(map_ctx* ctx, const PreparedGrid* g, const map_particles* p, m
   const int64_t base[2] = {0, g->ncell};
   MAP_TRY(integrals_upload(ctx, &h, base, 1, d_desc, d_base, s));
   BatchArgs B{d_desc, d_base, 1, g->ncell, ctx->d_counters};
+  if (ctx->cfg.autotune && ctx->cfg.precision == MAP_MIXED && !ctx->tune_done[MAP_MIXED])
+    MAP_TRY(integrals_autotune(ctx, B, s));
   phase_begin(ctx, 2, s);
   MAP_TRY(integrals_enqueue(ctx, B, ctx->tuned[ctx->cfg.precision], s));
   phase_end(ctx, 2, s);

@@ -199,6 +199,7 @@ int integrals_upload(map_ctx* ctx, const SnapDesc* h_desc, const int64_t* h_base
                       int64_t* d_base, cudaStream_t s);
 int integrals_enqueue(map_ctx* ctx, const BatchArgs& B, int variant, cudaStream_t s);
 int integrals_sum(map_ctx* ctx, const SnapDesc* d_desc, int nsnap, double* totals, cudaStream_t s);
+int integrals_autotune(map_ctx* ctx, const BatchArgs& B, cudaStream_t s);
 int h_solve_run(map_ctx* ctx, const double* x, const double* y, const double* z, int64_t n, double* h,
                 int32_t* route, const double* h0_override, cudaStream_t s);
 int pseudo_run(map_ctx* ctx, const map_particles* full, const double* src, int nsrc, map_particles* out,

@@ -140,6 +140,19 @@ __device__ __forceinline__ void antider(T r0, T R0, T c2, T c, T s, T& gin, T& g
     gmid = -(T(32) - T(30) * r02 * r02 - r06) * Om + r0 * (T(40) * P2 - T(30) * P3 + T(9) * P4 - P5);
 }
 
+// Node arithmetic of the Gauss-Legendre rule and the breakpoints.  FP32:
+// sqrt(x), x > 0, from the hardware reciprocal square root and one Newton step
+// (y <- y + r (x - y^2) / 2, ~1 ulp), and the quotient as a product with the
+// hardware reciprocal (2 ulp); FP64: the correctly rounded operations.
+__device__ __forceinline__ float gl_sqrt(float x) {
+  const float r = rsqrtf(x);
+  const float y = x * r;
+  return fmaf(0.5f * r, fmaf(-y, y, x), y);
+}
+__device__ __forceinline__ double gl_sqrt(double x) { return sqrt(x); }
+__device__ __forceinline__ float gl_div(float a, float b) { return __fdividef(a, b); }
+__device__ __forceinline__ double gl_div(double a, double b) { return a / b; }
+
 // 120 pi int_lo^hi r0 [E_mid(U) - E_mid(r0)] R0/(R0^2+s^2) ds by 6-point Gauss-Legendre.
 template <typename T>
 __device__ __forceinline__ T mid_gl(T r0, T R0, T c2, T lo, T hi) {
@@ -154,9 +167,9 @@ __device__ __forceinline__ T mid_gl(T r0, T R0, T c2, T lo, T hi) {
 #pragma unroll
     for (int sgn = -1; sgn <= 1; sgn += 2) {
       const T s = ctr + T(sgn) * half * gx[k];
-      const T U = xsqrt(c2 + s * s);
+      const T U = gl_sqrt(c2 + s * s);  // >= 1 on a middle piece
       const T den = U * (R02 + s * s);
-      acc += gw[k] * (den > T(0) ? (r0 * pmid(U) - pr0 * U) / den : T(0));
+      acc += gw[k] * (den > T(0) ? gl_div(r0 * pmid(U) - pr0 * U, den) : T(0));
     }
   }
   return R0 * half * acc;
@@ -175,10 +188,10 @@ __device__ __forceinline__ T piece_inner(T r0, T R0, T lo, T hi) {
   return (g1 - g0) * T(INV_4PI);
 }
 
-// Mixed build: the caller splits an interval that straddles the foot s = 0
-// into two pieces before calling (see split_edge_mixed), so that every call
-// is one Gauss-Legendre panel; kappa dPhi is evaluated unconditionally
-// (kappa = 0 for r0 >= 1), keeping the lanes of a warp on one path.
+// Mixed build: a middle interval never straddles the foot s = 0 (the split
+// puts a breakpoint there), so every call is one Gauss-Legendre panel; kappa
+// dPhi is evaluated unconditionally (kappa = 0 for r0 >= 1), keeping the
+// lanes of a warp on one path.
 template <typename T, bool MIXED>
 __device__ __forceinline__ T piece_mid(T r0, T R0, T lo, T hi) {
   const T c2 = r0 * r0 + R0 * R0;
@@ -197,37 +210,75 @@ __device__ __forceinline__ T piece_outer(T r0, T R0, T lo, T hi) {
   return -c0_of(r0) * dphi(lo, hi, R0);
 }
 
-// Split one edge into pieces.  Emits up to 1 inner, 2 middle and 2 outer
-// pieces through the callbacks as (lo, hi) with the sign pos folded into the
-// direction.  r0 > 0 and r0 < 2 are assumed.
-template <typename T, typename FIn, typename FMid, typename FOut>
-__device__ __forceinline__ void split_edge(T r0, T R0, T aa, T ab, bool pos, FIn fin, FMid fmid, FOut fout) {
-  const T c2 = r0 * r0 + R0 * R0;
-  auto emit = [&](auto& f, T lo, T hi) { if (pos) f(lo, hi); else f(hi, lo); };
-  if (c2 >= T(4)) { emit(fout, aa, ab); return; }
-  const T s2 = xsqrt(T(4) - c2);
-  if (ab > s2) emit(fout, aa > s2 ? aa : s2, ab);
-  if (aa < -s2) emit(fout, aa, ab < -s2 ? ab : -s2);
-  const T x0 = aa > -s2 ? aa : -s2;
-  const T x1 = ab < s2 ? ab : s2;
-  if (!(x1 > x0)) return;
-  if (c2 < T(1)) {
-    const T s1 = xsqrt(T(1) - c2);
-    const T lo = x0 > -s1 ? x0 : -s1, hi = x1 < s1 ? x1 : s1;
-    if (hi > lo) emit(fin, lo, hi);
-    if (x0 < -s1) emit(fmid, x0, x1 < -s1 ? x1 : -s1);
-    if (x1 > s1) emit(fmid, x0 > s1 ? x0 : s1, x1);
-  } else {
-    emit(fmid, x0, x1);
+// Split one edge into pieces, branch-free: with c^2 = r0^2 + R0^2 and the
+// breakpoints s2 = sqrt(4 - c^2) (U = 2) and s1 = sqrt(1 - c^2) (U = 1), taken
+// as 0 where they do not exist, the edge [aa, ab] gives
+//   beyond the support: [aa, min(ab, -s2)] and [max(aa, s2), ab]
+//                       (the whole edge as one piece when c^2 >= 4),
+//   middle:             [x0, min(x1, -s1)] and [max(x0, s1), x1],
+//   inner:              [max(x0, -s1), min(x1, s1)],
+// with x0 = max(aa, -s2), x1 = min(ab, s2), each kept when non-empty.  For
+// c^2 >= 1 (s1 = 0) the middle pieces are the middle interval split at the
+// foot s = 0, so that each starts or ends level with the branch points of the
+// middle-piece integrand.  Every lane runs the same instructions.  The
+// breakpoints use the fast square root in FP32: E is smooth across u = 1 and
+// u = 2, so moving a breakpoint by an ulp changes K' only at third order.
+// Pieces are returned as (lo, hi) with the sign pos folded into the direction
+// (lo > hi for pos == false).  r0 > 0 and r0 < 2 are assumed.
+template <typename T>
+struct EdgeSplit {
+  T aa, ab, s1, s2, x0, x1;
+  bool far, pos, split;
+  unsigned v;  // bit i: piece i non-empty (0 inner, 1-2 middle, 3-4 beyond the support)
+
+  // bounds of piece i (0..4), direction folded in
+  __device__ __forceinline__ void get(int i, T& lo, T& hi) const {
+    T l, h;
+    switch (i) {
+      case 0: l = x0 > -s1 ? x0 : -s1; h = x1 < s1 ? x1 : s1; break;
+      case 1: l = x0; h = x1 < -s1 ? x1 : -s1; break;
+      case 2: l = x0 > s1 ? x0 : s1; h = x1; break;
+      case 3: l = aa; h = far ? ab : (ab < -s2 ? ab : -s2); break;
+      default: l = aa > s2 ? aa : s2; h = ab; break;
+    }
+    lo = pos ? l : h;
+    hi = pos ? h : l;
   }
+};
+
+template <typename T>
+__device__ __forceinline__ EdgeSplit<T> split_edge_flat(T r0, T R0, T aa, T ab, bool pos, bool on) {
+  const T c2 = r0 * r0 + R0 * R0;
+  EdgeSplit<T> P;
+  P.far = c2 >= T(4);
+  P.s2 = P.far ? T(0) : gl_sqrt(T(4) - c2);
+  P.s1 = c2 < T(1) ? gl_sqrt(T(1) - c2) : T(0);
+  P.aa = aa;
+  P.ab = ab;
+  P.pos = pos;
+  P.x0 = aa > -P.s2 ? aa : -P.s2;
+  P.x1 = ab < P.s2 ? ab : P.s2;
+  const T s1 = P.s1, s2 = P.s2, x0 = P.x0, x1 = P.x1;
+  const bool v0 = (x1 < s1 ? x1 : s1) > (x0 > -s1 ? x0 : -s1);
+  const bool v1 = (x1 < -s1 ? x1 : -s1) > x0;
+  const bool v2 = x1 > (x0 > s1 ? x0 : s1);
+  const bool v3 = (P.far ? ab : (ab < -s2 ? ab : -s2)) > aa;
+  const bool v4 = !P.far && ab > (aa > s2 ? aa : s2);
+  P.v = on ? (unsigned)v0 | ((unsigned)v1 << 1) | ((unsigned)v2 << 2) | ((unsigned)v3 << 3) | ((unsigned)v4 << 4) : 0u;
+  P.split = on && v1 && v2 && !(c2 < T(1));
+  return P;
 }
 
-// True when the interval straddles the foot s = 0 (the mixed build evaluates
-// it as two pieces, [lo, 0] and [0, hi]: each starts or ends level with the
-// branch points s = +-i c of the middle-piece integrand).
-template <typename T>
-__device__ __forceinline__ bool straddles(T lo, T hi) {
-  return (lo < T(0)) != (hi < T(0)) && lo != T(0) && hi != T(0);
+// The same split through callbacks (in-thread evaluation).
+template <typename T, typename FIn, typename FMid, typename FOut>
+__device__ __forceinline__ void split_edge(T r0, T R0, T aa, T ab, bool pos, FIn fin, FMid fmid, FOut fout) {
+  const EdgeSplit<T> P = split_edge_flat<T>(r0, R0, aa, ab, pos, true);
+  T lo, hi;
+  if (P.v & 1u) { P.get(0, lo, hi); fin(lo, hi); }
+  if (P.v & 2u) { P.get(1, lo, hi); fmid(lo, hi); }
+  if (P.v & 4u) { P.get(2, lo, hi); fmid(lo, hi); }
+  if (P.v & 8u) { P.get(3, lo, hi); fout(lo, hi); }
+  if (P.v & 16u) { P.get(4, lo, hi); fout(lo, hi); }
 }
 
 // K' of one edge evaluated in this thread.
@@ -236,13 +287,7 @@ __device__ __forceinline__ T kprime_edge(T r0, T R0, T aa, T ab, WorkCount& wc) 
   T acc = T(0);
   split_edge<T>(r0, R0, aa, ab, true,
                 [&](T lo, T hi) { acc += piece_inner<T>(r0, R0, lo, hi); wc.inner += 2; },
-                [&](T lo, T hi) {
-                  if (MIXED && straddles(lo, hi))
-                    acc += piece_mid<T, MIXED>(r0, R0, lo, T(0)) + piece_mid<T, MIXED>(r0, R0, T(0), hi);
-                  else
-                    acc += piece_mid<T, MIXED>(r0, R0, lo, hi);
-                  wc.mid++;
-                },
+                [&](T lo, T hi) { acc += piece_mid<T, MIXED>(r0, R0, lo, hi); wc.mid++; },
                 [&](T lo, T hi) { acc += piece_outer<T>(r0, R0, lo, hi); wc.outer++; });
   return acc;
 }
