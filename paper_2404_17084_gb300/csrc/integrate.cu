@@ -57,6 +57,21 @@ __device__ __forceinline__ int warp_excl2(int v, int* tot) {
   return __popc(b0 & lt) + 2 * __popc(b1 & lt);
 }
 
+// One edge record (EDGE_STRIDE words, 16-byte aligned) in vector loads.
+__device__ __forceinline__ void load_edge(const float* E, float& e0, float& e1, float& e2, float& e3, float& e4,
+                                          float& e5, float& e6, float& e7, float& e8) {
+  const float4 a = reinterpret_cast<const float4*>(E)[0], b = reinterpret_cast<const float4*>(E)[1];
+  const float4 c = reinterpret_cast<const float4*>(E)[2];
+  e0 = a.x; e1 = a.y; e2 = a.z; e3 = a.w; e4 = b.x; e5 = b.y; e6 = b.z; e7 = b.w; e8 = c.x;
+}
+__device__ __forceinline__ void load_edge(const double* E, double& e0, double& e1, double& e2, double& e3,
+                                          double& e4, double& e5, double& e6, double& e7, double& e8) {
+  const double2 a = reinterpret_cast<const double2*>(E)[0], b = reinterpret_cast<const double2*>(E)[1];
+  const double2 c = reinterpret_cast<const double2*>(E)[2], d = reinterpret_cast<const double2*>(E)[3];
+  const double2 f = reinterpret_cast<const double2*>(E)[4];
+  e0 = a.x; e1 = a.y; e2 = b.x; e3 = b.y; e4 = c.x; e5 = c.y; e6 = d.x; e7 = d.y; e8 = f.x;
+}
+
 // Per-warp piece stacks (inner, middle, beyond the support) and the lanes'
 // compensated accumulators.
 template <typename T>
@@ -100,12 +115,16 @@ __device__ __noinline__ void drain(WarpStacks<T>& S, int& cnt0, int& cnt1, int& 
       const bool mine = on && rank == r;
       if (!__any_sync(FULL, mine)) break;
       if (mine) {
-        // compensated (Kahan) addition: the error stays at a few ulp of the
-        // pair's total however many pieces of either sign it sums
-        const T y = v - S.cmp[o];
-        const T t = S.acc[o] + y;
-        S.cmp[o] = (t - S.acc[o]) - y;
-        S.acc[o] = t;
+        if (sizeof(T) == 4) {
+          // compensated (Kahan) addition: the error stays at a few ulp of the
+          // pair's total however many pieces of either sign it sums
+          const T y = v - S.cmp[o];
+          const T t = S.acc[o] + y;
+          S.cmp[o] = (t - S.acc[o]) - y;
+          S.acc[o] = t;
+        } else {
+          S.acc[o] += v;  // FP64: plain sums are ample
+        }
       }
       __syncwarp();
     }
@@ -226,8 +245,8 @@ __global__ void __launch_bounds__(NW * 32, MINB) pair_integrals(BatchArgs B) {
         inside = inside && fin;
         if (__any_sync(FULL, inrange)) {
           for (int k = kb; k < ke; ++k) {
-            const T* E = ecell + k * EDGE_STRIDE;
-            const T e0 = E[0], e1 = E[1], e2 = E[2], e3 = E[3], e4 = E[4], e5 = E[5], e6 = E[6], e7 = E[7], e8 = E[8];
+            T e0, e1, e2, e3, e4, e5, e6, e7, e8;
+            load_edge(ecell + k * EDGE_STRIDE, e0, e1, e2, e3, e4, e5, e6, e7, e8);
             // R0 = m.(p - v_a) (> 0 inside), along-edge vertex positions
             const T R0s = (e0 * yx + e1 * yy + e2 * yz) - e3 * hinv;
             const T base = e4 * yx + e5 * yy + e6 * yz;

@@ -14,6 +14,7 @@ namespace {
 
 struct PairTree {
   const double *xs, *ys, *zs, *hs;
+  const float* split;  // 6 per sorted position: FP32 hi/lo of x, y, z
   const int32_t* idx;
   const int64_t *nb, *ne, *fc;
   const int32_t* nch;
@@ -43,37 +44,41 @@ __device__ __forceinline__ bool exact_face(const double4_32a P, double x, double
 }
 
 // The pair rule, decided in FP32 wherever the FP32 value is farther from the
-// threshold than a rigorous bound on its rounding error (all FP32 roundings
-// together stay below 1e-6 of the magnitudes involved; the margin is 1e-5),
-// and by the exact FP64 rule otherwise -- so the outcome is always the FP64
-// rule's.
-__device__ __forceinline__ bool pair_rule(const PairGrid& G, int64_t c, double sx, double sy, double sz, double R,
-                                          double x, double y, double z, double h) {
-  const float fx = (float)(x - sx), fy = (float)(y - sy), fz = (float)(z - sz);
-  const double reach = 2.0 * h + R;
-  const float reach2 = (float)(reach * reach);
+// threshold than a rigorous bound on its rounding error, and by the exact
+// FP64 rule otherwise -- so the outcome is always the FP64 rule's.  The FP32
+// separation comes from the hi/lo split of both points,
+// (hi_a - hi_s) + (lo_a - lo_s), within a few ulp of the separation itself;
+// with the rounding of h, R and the squares, all FP32 roundings together stay
+// below 1e-6 of the magnitudes involved, and the margin is 1e-5.  No FP64
+// operation runs unless a value falls inside the margin.
+struct SiteSplit {
+  float hx, lx, hy, ly, hz, lz, R;
+};
+
+__device__ __forceinline__ bool pair_rule(const PairGrid& G, const PairTree& T, int64_t c, const SiteSplit& S,
+                                          int64_t k) {
+  const float* P = T.split + 6 * k;
+  const float fx = (P[0] - S.hx) + (P[1] - S.lx);
+  const float fy = (P[2] - S.hy) + (P[3] - S.ly);
+  const float fz = (P[4] - S.hz) + (P[5] - S.lz);
+  const float hf = (float)T.hs[k];
+  const float reach = fmaf(2.f, hf, S.R);
+  const float reach2 = reach * reach;
   const float d2 = fx * fx + fy * fy + fz * fz;
   if (d2 > reach2 * 1.00001f) return false;
-  if (!(d2 < reach2 * 0.99999f) && !exact_dist(sx, sy, sz, R, x, y, z, h)) return false;
-  const float thr = (float)(2.0 * h);
+  if (!(d2 < reach2 * 0.99999f) &&
+      !exact_dist(G.site[3 * c], G.site[3 * c + 1], G.site[3 * c + 2], G.rad[c], T.xs[k], T.ys[k], T.zs[k], T.hs[k]))
+    return false;
+  const float thr = 2.f * hf;
   const float l1 = fabsf(fx) + fabsf(fy) + fabsf(fz);
   for (int64_t f = G.cfo[c]; f < G.cfo[c + 1]; ++f) {
     const float4 F = G.face32[f];
     const float sv = (F.x * fx + F.y * fy + F.z * fz) - F.w;
     const float marg = 1e-5f * (l1 + fabsf(F.w) + thr) + 1e-30f;
     if (sv > thr + marg) return false;
-    if (sv >= thr - marg && !exact_face(G.plane[f], x, y, z, h)) return false;
+    if (sv >= thr - marg && !exact_face(G.plane[f], T.xs[k], T.ys[k], T.zs[k], T.hs[k])) return false;
   }
   return true;
-}
-
-__device__ __forceinline__ double box_d2(const unsigned long long* bb, double x, double y, double z) {
-  double lo0 = bitsd(bb[0]), lo1 = bitsd(bb[1]), lo2 = bitsd(bb[2]);
-  double hi0 = bitsd(bb[3]), hi1 = bitsd(bb[4]), hi2 = bitsd(bb[5]);
-  double dx = x < lo0 ? lo0 - x : (x > hi0 ? x - hi0 : 0.0);
-  double dy = y < lo1 ? lo1 - y : (y > hi1 ? y - hi1 : 0.0);
-  double dz = z < lo2 ? lo2 - z : (z > hi2 ? z - hi2 : 0.0);
-  return dx * dx + dy * dy + dz * dz;
 }
 
 // One warp walks the octree for 32 cells that are consecutive in Morton order
@@ -96,6 +101,11 @@ __global__ void __launch_bounds__(128) pair_traverse(int64_t ncell, const int32_
   double sx = 0, sy = 0, sz = 0, R = 0;
   if (valid) { sx = G.site[3 * c]; sy = G.site[3 * c + 1]; sz = G.site[3 * c + 2]; R = G.rad[c]; }
   const float fsx = (float)sx, fsy = (float)sy, fsz = (float)sz, fR = (float)R;
+  SiteSplit SS;
+  SS.hx = fsx; SS.lx = (float)(sx - (double)fsx);
+  SS.hy = fsy; SS.ly = (float)(sy - (double)fsy);
+  SS.hz = fsz; SS.lz = (float)(sz - (double)fsz);
+  SS.R = fR;
   int64_t w = (FILL && valid) ? off[c] : 0;
   int64_t cnt = 0;
   int32_t* stack = s_stack[warp];
@@ -115,7 +125,7 @@ __global__ void __launch_bounds__(128) pair_traverse(int64_t ncell, const int32_
     if (T.nch[nd] == 0) {
       if (need) {
         for (int64_t k = T.nb[nd]; k < T.ne[nd]; ++k) {
-          if (pair_rule(G, c, sx, sy, sz, R, T.xs[k], T.ys[k], T.zs[k], T.hs[k])) {
+          if (pair_rule(G, T, c, SS, k)) {
             if (FILL) out[w++] = T.idx[k];
             ++cnt;
           }
@@ -210,8 +220,8 @@ int pairs_build(map_ctx* ctx, const PreparedGrid* g, cudaStream_t s, DevBuf* off
   MAP_TRY(ctx_ensure(ctx, ctx->cub_tmp, tb));
   CUDA_TRY(cub::DeviceRadixSort::SortPairs(ctx->cub_tmp.p, tb, k_in, k_out, o_in, order, nc, 0, 30, s));
 
-  PairTree PT{T.xs, T.ys, T.zs, T.hs, T.idx, T.begin, T.end, T.first_child, T.nchild, T.bbox_bits, T.hmax_bits,
-              T.box32};
+  PairTree PT{T.xs, T.ys, T.zs, T.hs, T.split, T.idx, T.begin, T.end, T.first_child, T.nchild, T.bbox_bits,
+              T.hmax_bits, T.box32};
   PairGrid PG{g->cell_face_off, g->face_plane, g->face32, g->site, g->rad};
   int64_t *count, *off;
   MAP_TRY(ensure_t(ctx, ctx->ws_pairs[0], nc + 1, &count));

@@ -220,7 +220,8 @@ __device__ __forceinline__ T piece_outer(T r0, T R0, T lo, T hi) {
 // with x0 = max(aa, -s2), x1 = min(ab, s2), each kept when non-empty.  For
 // c^2 >= 1 (s1 = 0) the middle pieces are the middle interval split at the
 // foot s = 0, so that each starts or ends level with the branch points of the
-// middle-piece integrand.  Every lane runs the same instructions.  The
+// middle-piece integrand (FP32 only: in FP64 the interval stays whole).
+// Every lane runs the same instructions.  The
 // breakpoints use the fast square root in FP32: E is smooth across u = 1 and
 // u = 2, so moving a breakpoint by an ulp changes K' only at third order.
 // Pieces are returned as (lo, hi) with the sign pos folded into the direction
@@ -229,6 +230,7 @@ template <typename T>
 struct EdgeSplit {
   T aa, ab, s1, s2, x0, x1;
   bool far, pos, split;
+  bool whole;  // FP64: a middle interval with c^2 >= 1 stays one piece (piece 1)
   unsigned v;  // bit i: piece i non-empty (0 inner, 1-2 middle, 3-4 beyond the support)
 
   // bounds of piece i (0..4), direction folded in
@@ -236,7 +238,7 @@ struct EdgeSplit {
     T l, h;
     switch (i) {
       case 0: l = x0 > -s1 ? x0 : -s1; h = x1 < s1 ? x1 : s1; break;
-      case 1: l = x0; h = x1 < -s1 ? x1 : -s1; break;
+      case 1: l = x0; h = (whole || x1 < -s1) ? x1 : -s1; break;
       case 2: l = x0 > s1 ? x0 : s1; h = x1; break;
       case 3: l = aa; h = far ? ab : (ab < -s2 ? ab : -s2); break;
       default: l = aa > s2 ? aa : s2; h = ab; break;
@@ -258,10 +260,13 @@ __device__ __forceinline__ EdgeSplit<T> split_edge_flat(T r0, T R0, T aa, T ab, 
   P.pos = pos;
   P.x0 = aa > -P.s2 ? aa : -P.s2;
   P.x1 = ab < P.s2 ? ab : P.s2;
+  // the foot split serves the FP32 quadrature only; the FP64 closed form
+  // takes the middle interval whole
+  P.whole = sizeof(T) == 8 && !(c2 < T(1));
   const T s1 = P.s1, s2 = P.s2, x0 = P.x0, x1 = P.x1;
   const bool v0 = (x1 < s1 ? x1 : s1) > (x0 > -s1 ? x0 : -s1);
-  const bool v1 = (x1 < -s1 ? x1 : -s1) > x0;
-  const bool v2 = x1 > (x0 > s1 ? x0 : s1);
+  const bool v1 = ((P.whole || x1 < -s1) ? x1 : -s1) > x0;
+  const bool v2 = !P.whole && x1 > (x0 > s1 ? x0 : s1);
   const bool v3 = (P.far ? ab : (ab < -s2 ? ab : -s2)) > aa;
   const bool v4 = !P.far && ab > (aa > s2 ? aa : s2);
   P.v = on ? (unsigned)v0 | ((unsigned)v1 << 1) | ((unsigned)v2 << 2) | ((unsigned)v3 << 3) | ((unsigned)v4 << 4) : 0u;
