@@ -96,7 +96,7 @@ struct map_ctx {
   std::vector<PreparedGrid*> grids;
   // workspace
   DevBuf ws_tree[32];
-  DevBuf ws_pairs[8];
+  DevBuf ws_pairs[10];
   DevBuf ws_misc[8];
   DevBuf cub_tmp;
   DevTree tree;

@@ -87,15 +87,20 @@ __device__ __forceinline__ bool pair_rule(const PairGrid& G, const PairTree& T, 
 // 1e-6 absolute margin: 2 * largest h + cell radius), the warp descends when
 // any lane needs the node, and at a leaf only the lanes that reach it test
 // its particles with the pair rule.
-// FILL = false: count pairs per cell; FILL = true: write them at off[c].
+// FILL = false: count pairs per cell, keeping the first PAIR_ROW of them in
+// the cell's row of `out` (ncell x PAIR_ROW); FILL = true: write the pairs at
+// off[c] (the cells of `order` whose count exceeded the row; their number is
+// read from *n_dev).
+constexpr int PAIR_ROW = 256;
+
 template <bool FILL>
 __global__ void __launch_bounds__(128) pair_traverse(int64_t ncell, const int32_t* __restrict__ order, PairTree T,
                                                      PairGrid G, int64_t* count, const int64_t* __restrict__ off,
-                                                     int32_t* out) {
+                                                     int32_t* out, const unsigned long long* n_dev) {
   __shared__ int32_t s_stack[4][200];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int64_t t = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x);
-  const bool valid = t < ncell;
+  const bool valid = t < (n_dev ? (int64_t)*n_dev : ncell);
   if (__all_sync(0xffffffffu, !valid)) return;
   const int64_t c = valid ? (order ? order[t] : t) : -1;
   double sx = 0, sy = 0, sz = 0, R = 0;
@@ -106,7 +111,7 @@ __global__ void __launch_bounds__(128) pair_traverse(int64_t ncell, const int32_
   SS.hy = fsy; SS.ly = (float)(sy - (double)fsy);
   SS.hz = fsz; SS.lz = (float)(sz - (double)fsz);
   SS.R = fR;
-  int64_t w = (FILL && valid) ? off[c] : 0;
+  int64_t w = valid ? (FILL ? off[c] : c * PAIR_ROW) : 0;
   int64_t cnt = 0;
   int32_t* stack = s_stack[warp];
   int sp = 1;
@@ -126,7 +131,7 @@ __global__ void __launch_bounds__(128) pair_traverse(int64_t ncell, const int32_
       if (need) {
         for (int64_t k = T.nb[nd]; k < T.ne[nd]; ++k) {
           if (pair_rule(G, T, c, SS, k)) {
-            if (FILL) out[w++] = T.idx[k];
+            if (FILL || cnt < PAIR_ROW) out[w++] = T.idx[k];
             ++cnt;
           }
         }
@@ -140,6 +145,25 @@ __global__ void __launch_bounds__(128) pair_traverse(int64_t ncell, const int32_
     }
   }
   if (!FILL && valid) count[c] = cnt;
+}
+
+// Move the rows kept by the counting pass to their place in the list (one
+// warp per cell); cells whose count exceeded the row go to the overflow list
+// for the filling pass.
+__global__ void __launch_bounds__(128) place_rows(int64_t ncell, const int64_t* __restrict__ count,
+                                                  const int64_t* __restrict__ off, const int32_t* __restrict__ rows,
+                                                  int32_t* out, int32_t* ovf, unsigned long long* n_ovf) {
+  const int64_t c = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (c >= ncell) return;
+  const int64_t n = count[c];
+  if (n > PAIR_ROW) {
+    if (lane == 0) ovf[atomicAdd(n_ovf, 1ULL)] = (int32_t)c;
+    return;
+  }
+  const int32_t* src = rows + c * PAIR_ROW;
+  int32_t* dst = out + off[c];
+  for (int64_t i = lane; i < n; i += 32) dst[i] = src[i];
 }
 
 // Sort each cell's pair list (<= 1024 entries) in shared memory, one warp
@@ -226,8 +250,11 @@ int pairs_build(map_ctx* ctx, const PreparedGrid* g, cudaStream_t s, DevBuf* off
   int64_t *count, *off;
   MAP_TRY(ensure_t(ctx, ctx->ws_pairs[0], nc + 1, &count));
   MAP_TRY(ensure_t(ctx, off_buf ? *off_buf : ctx->ws_pairs[1], nc + 1, &off));
+  int32_t* rows;
+  MAP_TRY(ensure_t(ctx, ctx->ws_pairs[8], (size_t)nc * PAIR_ROW, &rows));
   CUDA_TRY(cudaMemsetAsync(count + nc, 0, sizeof(int64_t), s));
-  pair_traverse<false><<<nblk(nc, tpb), tpb, 0, s>>>(nc, order, PT, PG, count, nullptr, nullptr); ++ctx->launches;
+  pair_traverse<false><<<nblk(nc, tpb), tpb, 0, s>>>(nc, order, PT, PG, count, nullptr, rows, nullptr);
+  ++ctx->launches;
   CUDA_TRY(cudaGetLastError());
   tb = 0;
   CUDA_TRY(cub::DeviceScan::ExclusiveSum(nullptr, tb, count, off, nc + 1, s));
@@ -239,7 +266,14 @@ int pairs_build(map_ctx* ctx, const PreparedGrid* g, cudaStream_t s, DevBuf* off
   int32_t *raw, *sorted;
   MAP_TRY(ensure_t(ctx, ctx->ws_pairs[2], np + 1, &raw));
   MAP_TRY(ensure_t(ctx, idx_buf ? *idx_buf : ctx->ws_pairs[3], np + 1, &sorted));
-  pair_traverse<true><<<nblk(nc, tpb), tpb, 0, s>>>(nc, order, PT, PG, nullptr, off, raw); ++ctx->launches;
+  // rows that fit go straight to the list; the other cells are walked again
+  int32_t* ovf;
+  MAP_TRY(ensure_t(ctx, ctx->ws_pairs[9], nc, &ovf));
+  unsigned long long* d_novf = ctx->d_counters + 6;
+  CUDA_TRY(cudaMemsetAsync(d_novf, 0, sizeof(unsigned long long), s));
+  place_rows<<<nblk(nc * 32, tpb), tpb, 0, s>>>(nc, count, off, rows, raw, ovf, d_novf); ++ctx->launches;
+  CUDA_TRY(cudaGetLastError());
+  pair_traverse<true><<<nblk(nc, tpb), tpb, 0, s>>>(nc, ovf, PT, PG, nullptr, off, raw, d_novf); ++ctx->launches;
   CUDA_TRY(cudaGetLastError());
   if (np > 0) {
     sort_small_segments<<<nblk(nc, 4), 128, 0, s>>>(nc, off, raw, sorted); ++ctx->launches;
