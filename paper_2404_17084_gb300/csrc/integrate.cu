@@ -11,14 +11,15 @@
 // of it (R0 and the along-edge coordinates of the vertices), every lane splits
 // its edge integral K'_e into pieces -- at most one inner piece, two middle
 // pieces and two pieces beyond the support -- as (r0, R0, lo, hi), the sign
-// s_f s_e folded into the interval direction, and pushes them onto three
-// per-warp stacks, one per kind.  Whenever a stack holds 32 pieces the whole
-// warp evaluates them together (every lane the same code), so the costly
-// evaluations run with all lanes busy; the stacks carry over from edge to
-// edge and are flushed after the last face.  Each result is added to its
-// owner lane's compensated (Kahan) accumulator, lanes with the same owner in
-// turn, so the order of additions is fixed and every result is
-// bit-reproducible.
+// s_f s_e folded into the interval direction.  The pieces beyond the support
+// (-r0 E(r0) dPhi, one atan2 for both) are added by the lane itself.  Inner
+// and middle pieces are pushed onto two per-warp stacks, one per kind;
+// whenever a stack holds 32 pieces the whole warp evaluates them together
+// (every lane the same code), so the costly evaluations run with all lanes
+// busy; the stacks carry over from edge to edge and are flushed after the
+// last face.  Each result is added to its owner lane's compensated (Kahan)
+// accumulator, lanes with the same owner in turn, so the order of additions
+// is fixed and every result is bit-reproducible.
 // (Mixed build: a face whose plane passes within 1e-4 h of the particle is
 // decided and evaluated in FP64 by the owner lane instead.)
 //
@@ -72,12 +73,16 @@ __device__ __forceinline__ void load_edge(const double* E, double& e0, double& e
   e0 = a.x; e1 = a.y; e2 = b.x; e3 = b.y; e4 = c.x; e5 = c.y; e6 = d.x; e7 = d.y; e8 = f.x;
 }
 
-// Per-warp piece stacks (inner, middle, beyond the support) and the lanes'
-// compensated accumulators.
+// Per-warp piece stacks (inner, middle) and the lanes' compensated
+// accumulators.
 template <typename T>
 struct WarpStacks {
-  typename Vec4<T>::type e[3][LCAP];  // (r0, R0, lo, hi)
-  unsigned char own[3][LCAP];         // owner lane
+  // FP32 adds the pieces beyond the support in the lane itself (one atan2
+  // per edge); FP64, where an atan2 costs far more than the stacking, stacks
+  // them as a third kind
+  static constexpr int NK = sizeof(T) == 4 ? 2 : 3;
+  typename Vec4<T>::type e[NK][LCAP];  // (r0, R0, lo, hi): inner, middle[, beyond]
+  unsigned char own[NK][LCAP];         // owner lane
   T acc[32];                          // per-owner sum of its pieces ...
   T cmp[32];                          // ... and its compensation (Kahan)
   SnapDesc d;                         // the snapshot of the warp's current cell
@@ -85,18 +90,21 @@ struct WarpStacks {
 
 // Evaluates the queued pieces: every stack holding 32 or more (all that is
 // left when flush), 32 at a time from the top, and adds each result to its
-// owner lane's accumulator.  Not inlined: the three evaluators then appear
-// once in the kernel's code.
+// owner lane's accumulator.  Not inlined: the evaluators then appear once in
+// the kernel's code.
 template <typename T, bool MIXED>
-__device__ __noinline__ void drain(WarpStacks<T>& S, int& cnt0, int& cnt1, int& cnt2, bool flush, unsigned& t0,
-                                   unsigned& t1, unsigned& t2) {
+__device__ __noinline__ void drain(WarpStacks<T>& S, int& cnt0, int& cnt1, int& cnt2, bool flush,
+                                   unsigned& t0, unsigned& t1, unsigned& t2) {
   const int lane = threadIdx.x & 31;
   for (;;) {
     int K, n;
     if (cnt1 >= 32 || (flush && cnt1 > 0)) { K = 1; n = cnt1 < 32 ? cnt1 : 32; cnt1 -= n; t1 += n; }
     else if (cnt0 >= 32 || (flush && cnt0 > 0)) { K = 0; n = cnt0 < 32 ? cnt0 : 32; cnt0 -= n; t0 += n; }
-    else if (cnt2 >= 32 || (flush && cnt2 > 0)) { K = 2; n = cnt2 < 32 ? cnt2 : 32; cnt2 -= n; t2 += n; }
-    else break;
+    else if (WarpStacks<T>::NK == 3 && (cnt2 >= 32 || (flush && cnt2 > 0))) {
+      K = 2; n = cnt2 < 32 ? cnt2 : 32; cnt2 -= n; t2 += n;
+    } else {
+      break;
+    }
     const int base = K == 0 ? cnt0 : (K == 1 ? cnt1 : cnt2);
     const bool on = lane < n;
     T v = T(0);
@@ -106,7 +114,7 @@ __device__ __noinline__ void drain(WarpStacks<T>& S, int& cnt0, int& cnt1, int& 
       o = S.own[K][base + lane];
       if (K == 1) v = wedge::piece_mid<T, MIXED>(P.x, P.y, P.z, P.w);
       else if (K == 0) v = wedge::piece_inner<T>(P.x, P.y, P.z, P.w);
-      else v = -P.x * wedge::dphi(P.z, P.w, P.y);  // P.x = c0 (see the push)
+      else if constexpr (WarpStacks<T>::NK == 3) v = -P.x * wedge::dphi(P.z, P.w, P.y);  // P.x = c0 (the push)
     }
     // lanes holding pieces of the same owner add in turn, in lane order
     const unsigned grp = __match_any_sync(FULL, o);
@@ -164,7 +172,9 @@ __global__ void __launch_bounds__(NW * 32, MINB) pair_integrals(BatchArgs B) {
   WarpStacks<T>& S = stacks[threadIdx.x >> 5];
   const SnapDesc& A = S.d;
   wedge::WorkCount wc;
-  unsigned n_in = 0, n_mid = 0, n_out = 0;  // pieces evaluated by this warp
+  unsigned n_in = 0, n_mid = 0;  // stacked pieces evaluated by this warp
+  unsigned n_out = 0;            // this lane's beyond-support intervals (FP32)
+  unsigned n_out_st = 0;         // stacked beyond-support pieces evaluated by this warp (FP64)
   int n64 = 0;
   unsigned n_split = 0;  // middle intervals split at the foot (counted once, evaluated as two pieces)
   int cur = -1;          // snapshot held in S.d
@@ -225,6 +235,7 @@ __global__ void __launch_bounds__(NW * 32, MINB) pair_integrals(BatchArgs B) {
       bool inside = true;
       double dacc = 0.0;
       int cnt0 = 0, cnt1 = 0, cnt2 = 0;  // stack heights (warp-uniform)
+      T osum = T(0), ocmp = T(0);  // this lane's beyond-support terms (compensated)
       int kb = 0;
       for (int fi = 0; fi < nf; ++fi) {
         const V4 F = face[f0 + fi];
@@ -263,10 +274,9 @@ __global__ void __launch_bounds__(NW * 32, MINB) pair_integrals(BatchArgs B) {
               n_split += P.split;
             }
             // push this edge's pieces (warp-aggregated)
-            int t0, t1, t2;
+            int t0, t1, t2 = 0;
             const int o0 = cnt0 + warp_excl2(nin, &t0);
             const int o1 = cnt1 + warp_excl2(nmid, &t1);
-            const int o2 = cnt2 + warp_excl2(nout, &t2);
             const unsigned char ln = (unsigned char)lane;
             T lo, hi;
             if (P.v & 1u) { P.get(0, lo, hi); S.e[0][o0] = V4{r0, R0, lo, hi}; S.own[0][o0] = ln; }
@@ -275,27 +285,50 @@ __global__ void __launch_bounds__(NW * 32, MINB) pair_integrals(BatchArgs B) {
               const int q = o1 + ((P.v >> 1) & 1u);
               P.get(2, lo, hi); S.e[1][q] = V4{r0, R0, lo, hi}; S.own[1][q] = ln;
             }
-            // beyond the support only c0 = r0 E(r0) is needed, once per face
-            if (P.v & 8u) { P.get(3, lo, hi); S.e[2][o2] = V4{c0f, R0, lo, hi}; S.own[2][o2] = ln; }
-            if (P.v & 16u) {
-              const int q = o2 + ((P.v >> 3) & 1u);
-              P.get(4, lo, hi); S.e[2][q] = V4{c0f, R0, lo, hi}; S.own[2][q] = ln;
+            // beyond the support, in this lane: -c0 (dPhi_left + dPhi_right)
+            // as the argument of the product of the two intervals' numbers
+            // (R0^2 + lo hi) + i (hi - lo) R0 -- each angle lies in
+            // (-pi/2, pi/2) and together they span less than pi -- one atan2
+            // per edge, branch-free (an empty interval contributes 1)
+            if constexpr (WarpStacks<T>::NK == 3) {
+              const int o2 = cnt2 + warp_excl2(nout, &t2);
+              if (P.v & 8u) { P.get(3, lo, hi); S.e[2][o2] = V4{c0f, R0, lo, hi}; S.own[2][o2] = ln; }
+              if (P.v & 16u) {
+                const int q = o2 + ((P.v >> 3) & 1u);
+                P.get(4, lo, hi); S.e[2][q] = V4{c0f, R0, lo, hi}; S.own[2][q] = ln;
+              }
+            } else {
+              T l3, h3, l4, h4;
+              P.get(3, l3, h3);
+              P.get(4, l4, h4);
+              const bool v3 = P.v & 8u, v4 = P.v & 16u;
+              const T R02 = R0 * R0;
+              const T ar = v3 ? R02 + l3 * h3 : T(1), ai = v3 ? (h3 - l3) * R0 : T(0);
+              const T br = v4 ? R02 + l4 * h4 : T(1), bi = v4 ? (h4 - l4) * R0 : T(0);
+              const T re = ar * br - ai * bi, im = ar * bi + ai * br;
+              const T y = -c0f * wedge::xatan2(im, re) - ocmp;
+              const T t = osum + y;
+              ocmp = (t - osum) - y;
+              osum = t;
+              n_out += nout;
             }
             cnt0 += t0;
             cnt1 += t1;
             cnt2 += t2;
             __syncwarp();
             // evaluate full stacks, 32 pieces at a time from the top
-            if (cnt0 >= 32 || cnt1 >= 32 || cnt2 >= 32) drain<T, MIXED>(S, cnt0, cnt1, cnt2, false, n_in, n_mid, n_out);
+            if (cnt0 >= 32 || cnt1 >= 32 || cnt2 >= 32)
+              drain<T, MIXED>(S, cnt0, cnt1, cnt2, false, n_in, n_mid, n_out_st);
           }
         }
         kb = ke;
       }
       // flush what is left (fewer than 32 of each kind)
-      if (cnt0 || cnt1 || cnt2) drain<T, MIXED>(S, cnt0, cnt1, cnt2, true, n_in, n_mid, n_out);
+      if (cnt0 || cnt1 || cnt2) drain<T, MIXED>(S, cnt0, cnt1, cnt2, true, n_in, n_mid, n_out_st);
       __syncwarp();
       if (active) {
-        const double f = (inside ? 1.0 : 0.0) + dacc + ((double)S.acc[lane] - (double)S.cmp[lane]);
+        const double f = (inside ? 1.0 : 0.0) + dacc + ((double)S.acc[lane] - (double)S.cmp[lane]) +
+                         ((double)osum - (double)ocmp);
         if (A.frac) A.frac[p] = f;
         macc += A.m[a] * f;
       }
@@ -316,6 +349,7 @@ __global__ void __launch_bounds__(NW * 32, MINB) pair_integrals(BatchArgs B) {
   const unsigned long long terms = wsum((unsigned long long)wc.terms), faces = wsum((unsigned long long)wc.faces);
   const unsigned long long edges = wsum((unsigned long long)wc.edges), fp64 = wsum((unsigned long long)n64);
   const unsigned long long split = wsum((unsigned long long)n_split);
+  const unsigned long long outs = wsum((unsigned long long)n_out);
   if (lane == 0) {
     atomicAdd(&B.counters[1], terms);
     atomicAdd(&B.counters[2], fp64);
@@ -323,7 +357,7 @@ __global__ void __launch_bounds__(NW * 32, MINB) pair_integrals(BatchArgs B) {
     atomicAdd(&B.counters[9], edges);
     atomicAdd(&B.counters[10], 2ull * n_in);
     atomicAdd(&B.counters[11], (unsigned long long)n_mid - split);  // a split interval: one interval, two pieces
-    atomicAdd(&B.counters[12], (unsigned long long)n_out);
+    atomicAdd(&B.counters[12], outs + n_out_st);
     atomicAdd(&B.counters[13], split);
   }
 }
