@@ -151,6 +151,14 @@ OPS = {
 }
 
 
+# DRAM traffic of the mixed pair-integral kernel per pair:
+# dram__bytes_read.sum + dram__bytes_write.sum of one ncu capture of the 2^16
+# clumpy case (391 MB for 7,813,809 pairs), scaled to a launch by its pair
+# count (the kernel streams the same per-pair data at any size).  It belongs
+# to the kernel as captured: set it to None when the kernel changes.
+INTEGRAL_DRAM_BYTES_PER_PAIR = 50.0
+
+
 def algorithmic_ops(work: dict, terms: int, mixed: bool):
     f = m = 0
     units = [("face_tests", work["face_tests"]), ("edge_records", work["edge_records"]),
@@ -290,7 +298,9 @@ def run_ours(args):
         "fp64": fp64,
         "roofline": {"bound": "alu", "kernel": "pair_integrals<float,mixed>", "achieved": achieved / 1e12,
                      "peak": peak_ops / 1e12, "unit": "Tops/s (FP32 issue slots)", "frac": achieved / peak_ops,
-                     "traffic": None, "ops_fp32": int(f32), "ops_mufu": int(mufu), "launch_ms": integ_ms,
+                     "traffic": (None if INTEGRAL_DRAM_BYTES_PER_PAIR is None
+                                 else INTEGRAL_DRAM_BYTES_PER_PAIR * n_pairs),
+                     "ops_fp32": int(f32), "ops_mufu": int(mufu), "launch_ms": integ_ms,
                      "peak_source": f"{sm_count} SMs x 128 FP32 lanes x {f_clk:.0f} MHz"},
         "e2e": e2e,
         "gpu_launches": int(launches),
@@ -430,7 +440,10 @@ def run_batch(args):
                   "host_input_generation_s": gen_s},
         "roofline": {"bound": "alu", "kernel": "pair_integrals<float,mixed> (batched launch)",
                      "achieved": achieved / 1e12, "peak": peak_ops / 1e12, "unit": "Tops/s (FP32 issue slots)",
-                     "frac": achieved / peak_ops, "traffic": None, "launch_ms": integ_ms},
+                     "frac": achieved / peak_ops,
+                     "traffic": (None if INTEGRAL_DRAM_BYTES_PER_PAIR is None
+                                 else INTEGRAL_DRAM_BYTES_PER_PAIR * int(st.n_pairs)),
+                     "launch_ms": integ_ms},
         "e2e": None,
         "gpu_launches": int((l1 - l0) // max(args.steps, 1) * args.steps),
         "clocks": clocks,
@@ -556,6 +569,170 @@ def run_serve(args):
         "gpu_launches": None,
         "clocks": clocks,
     }
+    emit(line, rank)
+
+
+def _step_timer(torch, step, steps, warmup):
+    for _ in range(warmup):
+        step()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(steps):
+        step()
+    e1.record()
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / steps
+
+
+def run_uniform(args):
+    """Plain Exact mapping, FP64: 4096 equal-mass particles uniform in the
+    cube; every cell against the oracle, and mass conservation on interior
+    particles (support inside the cube)."""
+    import torch
+    import paper_2404_17084_gb300 as L
+    import oracle
+    import synth
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    p = synth.uniform_particles(4096, rank_seed(synth.BASE_SEED + 1, rank))
+    g = synth.voronoi(p.pos())
+    t = lambda a: torch.as_tensor(np.ascontiguousarray(a), dtype=torch.float64, device=dev)
+    x, y, z, m = t(p.x), t(p.y), t(p.z), t(p.m)
+    res = {}
+    for prec, name in ((L.MAP_FP64, "fp64"), (L.MAP_MIXED, "mixed")):
+        ctx = L.map_init(L.map_config_default(precision=prec, device=local))
+        hd = L.map_grid_upload(ctx, L.grid_to_device(g, dev))
+        h = torch.empty_like(x)
+        mass = torch.empty(g.ncell, dtype=torch.float64, device=dev)
+
+        def step():
+            L.solve_h(ctx, L.make_particles(x, y, z, None, h))
+            L.map_particles_to_cells(ctx, L.make_particles(x, y, z, m, h), hd, mass)
+
+        ms = _step_timer(torch, step, args.steps, max(args.warmup, 3))
+        st = L.map_get_stats(ctx)
+        off, idx, frac = L.map_copy_pairs(ctx, g.ncell)
+        res[name] = dict(ms=ms, n_pairs=int(st.n_pairs), mass=mass.cpu().numpy(), h=h.cpu().numpy(),
+                         idx=idx.cpu().numpy(), frac=frac.cpu().numpy(), phases=L.map_get_timing(ctx))
+        L.map_destroy(ctx)
+    h64 = res["fp64"]["h"]
+    t0 = time.perf_counter()
+    ref = oracle.map_cells(g, p.x, p.y, p.z, p.m, h64)
+    cpu_s = time.perf_counter() - t0
+    scale = np.maximum(np.abs(ref["mass"]), 1e-12 * np.abs(ref["mass"]).max())
+    e64 = np.abs(res["fp64"]["mass"] - ref["mass"]) / scale
+    tot = np.zeros(p.n)
+    np.add.at(tot, res["fp64"]["idx"], res["fp64"]["frac"])
+    pos = p.pos()
+    interior = np.all((pos >= 2 * h64[:, None]) & (pos <= 1 - 2 * h64[:, None]), axis=1)
+    ref_m = oracle.map_cells(g, p.x, p.y, p.z, p.m, res["mixed"]["h"])
+    em = np.abs(res["mixed"]["mass"] - ref_m["mass"]) / np.maximum(np.abs(ref_m["mass"]),
+                                                                   1e-12 * np.abs(ref_m["mass"]).max())
+    line = {
+        "metric": "particle-cell pair integrals/sec at 1 GB300 (mixed vs FP64 form) + p50/p99 latency",
+        "value": res["fp64"]["n_pairs"] / (res["fp64"]["ms"] * 1e-3), "unit": "pair integrals/s", "n_gpus": 1,
+        "steps": args.steps, "warmup": max(args.warmup, 3), "ms_per_step": res["fp64"]["ms"],
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": "plain Exact mapping: 4096 equal-mass particles (m = 1/4096) uniform in the unit "
+                               "cube, clipped Voronoi grid, h = 1.2 (m/rho)^(1/3), FP64", "n_cells": g.ncell,
+                   "n_pairs": res["fp64"]["n_pairs"], "l2": "inputs smaller than L2 (a 4096-particle case)",
+                   "step": "solve_h + octree + pair list + pair integrals + cell sums"},
+        "mixed": {"value": res["mixed"]["n_pairs"] / (res["mixed"]["ms"] * 1e-3), "ms_per_step": res["mixed"]["ms"],
+                  "all_cells_vs_oracle": {"max_rel": float(em.max()), "p99_rel": float(np.percentile(em, 99))}},
+        "accuracy_vs_oracle": {"cells": g.ncell, "fp64_max_rel": float(e64.max()),
+                               "fp64_p99_rel": float(np.percentile(e64, 99)),
+                               "total_mass_rel": float(abs(res["fp64"]["mass"].sum() - ref["mass"].sum())
+                                                       / ref["mass"].sum()),
+                               "interior_particles": int(interior.sum()),
+                               "interior_sum_f_max_dev": float(np.max(np.abs(tot[interior] - 1)))},
+        "cpu_baseline": {"value": len(ref["idx"]) / cpu_s, "unit": "pair integrals/s", "cores": os.cpu_count(),
+                         "kind": "oracle", "sample": f"every cell ({g.ncell}), {cpu_s:.1f} s"},
+        "phases_ms": {k: round(v, 3) for k, v in res["fp64"]["phases"].items()},
+        "e2e": None, "gpu_launches": None,
+    }
+    emit(line, rank)
+
+
+def run_pseudo(args):
+    """Pseudo-particle path: 2^22 particles from the log-normal field, h from
+    the GPU solve, the source at the densest particle; the octree walk turns
+    nodes into pseudo-particles (theta = 0.5, leaf 16) with their own h; the
+    pseudo set is mapped onto its own Voronoi grid, and the full set onto the
+    same grid for the full-resolution comparison."""
+    import torch
+    import paper_2404_17084_gb300 as L
+    import synth
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    n = args.n if args.n != N_PARTICLES else 1 << 22
+    p = synth.lognormal_particles(n, rank_seed(synth.BASE_SEED + 3, rank), sigma=SIGMA)
+    t = lambda a: torch.as_tensor(np.ascontiguousarray(a), dtype=torch.float64, device=dev)
+    x, y, z, m = t(p.x), t(p.y), t(p.z), t(p.m)
+    h = torch.empty_like(x)
+    ctx = L.map_init(L.map_config_default(precision=L.MAP_MIXED, device=local, autotune=1))
+    L.solve_h(ctx, L.make_particles(x, y, z, None, h))
+    torch.cuda.synchronize()
+    hn = h.cpu().numpy()
+    src = p.pos()[int(np.argmin(hn))]
+    cap = n
+    ox, oy, oz, om, oh = (torch.empty(cap, dtype=torch.float64, device=dev) for _ in range(5))
+    full = L.make_particles(x, y, z, m, h)
+    outp = L.make_particles(ox, oy, oz, om, oh)
+    npseudo = [0]
+
+    def build():
+        npseudo[0] = L.build_pseudo_particles(ctx, full, src, outp)
+
+    build_ms = _step_timer(torch, build, args.steps, max(args.warmup, 3))
+    k = npseudo[0]
+    pos = np.stack([ox[:k].cpu().numpy(), oy[:k].cpu().numpy(), oz[:k].cpu().numpy()], 1)
+    keep = synth.dedupe_sites(pos)
+    g = synth.voronoi(pos[keep])
+    hd = L.map_grid_upload(ctx, L.grid_to_device(g, dev))
+    mass_p = torch.empty(g.ncell, dtype=torch.float64, device=dev)
+    mass_f = torch.empty_like(mass_p)
+    pseudo = L.make_particles(ox[:k], oy[:k], oz[:k], om[:k], oh[:k])
+
+    def map_pseudo():
+        L.map_particles_to_cells(ctx, pseudo, hd, mass_p)
+
+    map_ms = _step_timer(torch, map_pseudo, args.steps, max(args.warmup, 3))
+    st_p = L.map_get_stats(ctx)
+
+    def map_full():
+        L.map_particles_to_cells(ctx, full, hd, mass_f)
+
+    full_ms = _step_timer(torch, map_full, 1, 1)
+    st_f = L.map_get_stats(ctx)
+    mp, mf = mass_p.cpu().numpy(), mass_f.cpu().numpy()
+    rel = np.abs(mp - mf) / np.maximum(mf, 1e-12 * mf.max())
+    step_ms = build_ms + map_ms
+    line = {
+        "metric": "particle-cell pair integrals/sec at 1 GB300 (mixed vs FP64 form) + p50/p99 latency",
+        "value": st_p.n_pairs / (step_ms * 1e-3), "unit": "pair integrals/s", "n_gpus": 1,
+        "steps": args.steps, "warmup": max(args.warmup, 3), "ms_per_step": step_ms, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
+        "config": {"workload": f"pseudo-particle path: 2^{int(np.log2(n))} particles, log-normal field "
+                               "(sigma_ln_rho = 1.5), octree leaf 16, source at the densest particle, theta = 0.5, "
+                               "pseudo h on ~58 neighbours, pseudo set mapped onto its own Voronoi grid, mixed",
+                   "n_particles": n, "n_pseudo": k, "n_cells": g.ncell, "n_pairs_pseudo": int(st_p.n_pairs),
+                   "step": "build_pseudo_particles (walk + pseudo h) + mapping of the pseudo set"},
+        "pseudo": {"build_ms": build_ms, "map_ms": map_ms,
+                   "reduction": {"particles": n / k, "pairs_full_on_same_grid": int(st_f.n_pairs),
+                                 "pairs_ratio": st_f.n_pairs / max(st_p.n_pairs, 1)},
+                   "full_resolution_map_ms": full_ms,
+                   "vs_full_resolution_per_cell_rel": {"p50": float(np.percentile(rel, 50)),
+                                                        "p90": float(np.percentile(rel, 90)),
+                                                        "p99": float(np.percentile(rel, 99))},
+                   "mass_pseudo_vs_full": float(abs(om[:k].sum().item() - m.sum().item()) / m.sum().item())},
+        "e2e": None, "gpu_launches": None,
+    }
+    L.map_destroy(ctx)
     emit(line, rank)
 
 
@@ -693,9 +870,10 @@ def main():
     ap.add_argument("--dump", action="store_true", help="save per-cell results to <outdir>/cells.npz")
     ap.add_argument("--outdir", default=os.path.join(ROOT, "bench_out"),
                     help="folder for the clock samples and --dump output")
-    ap.add_argument("--workload", default="clumpy", choices=["clumpy", "batch", "serve"],
+    ap.add_argument("--workload", default="clumpy", choices=["clumpy", "batch", "serve", "uniform", "pseudo"],
                     help="clumpy: one 2^20 snapshot (default); batch: uneven snapshots in one launch; "
-                         "serve: Poisson stream of requests through the serving loop")
+                         "serve: Poisson stream of requests through the serving loop; uniform: 4096 uniform "
+                         "particles, FP64; pseudo: 2^22 particles reduced to pseudo-particles")
     ap.add_argument("--pool", type=int, default=32, help="distinct requests of the serve workload")
     ap.add_argument("--requests", type=int, default=160, help="requests submitted in the serve workload")
     ap.add_argument("--rate", type=float, default=0.0, help="serve arrival rate (req/s); 0 = 80%% of capacity")
@@ -709,6 +887,10 @@ def main():
         run_batch(args)
     elif args.workload == "serve":
         run_serve(args)
+    elif args.workload == "uniform":
+        run_uniform(args)
+    elif args.workload == "pseudo":
+        run_pseudo(args)
     else:
         run_ours(args)
 
