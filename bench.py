@@ -709,6 +709,7 @@ def run_pseudo(args):
 
     full_ms = _step_timer(torch, map_full, 1, 1)
     st_f = L.map_get_stats(ctx)
+    full_phases = L.map_get_timing(ctx)
     mp, mf = mass_p.cpu().numpy(), mass_f.cpu().numpy()
     rel = np.abs(mp - mf) / np.maximum(mf, 1e-12 * mf.max())
     step_ms = build_ms + map_ms
@@ -726,6 +727,7 @@ def run_pseudo(args):
                    "reduction": {"particles": n / k, "pairs_full_on_same_grid": int(st_f.n_pairs),
                                  "pairs_ratio": st_f.n_pairs / max(st_p.n_pairs, 1)},
                    "full_resolution_map_ms": full_ms,
+                   "full_resolution_phases_ms": {k: round(v, 3) for k, v in full_phases.items()},
                    "vs_full_resolution_per_cell_rel": {"p50": float(np.percentile(rel, 50)),
                                                         "p90": float(np.percentile(rel, 90)),
                                                         "p99": float(np.percentile(rel, 99))},

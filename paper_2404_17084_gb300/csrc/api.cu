@@ -140,8 +140,9 @@ void map_destroy(map_ctx* ctx) {
   if (ctx->h_stats) cudaFreeHost(ctx->h_stats);
   if (ctx->h_scratch) cudaFreeHost(ctx->h_scratch);
   for (auto& e : ctx->ev) if (e) cudaEventDestroy(e);
-  for (auto& b : ctx->batch_off) if (b.p) cudaFree(b.p);
-  for (auto& b : ctx->batch_idx) if (b.p) cudaFree(b.p);
+  for (auto* v : {&ctx->batch_off, &ctx->batch_idx, &ctx->batch_itm, &ctx->batch_ioff, &ctx->batch_part})
+    for (auto& b : *v)
+      if (b.p) cudaFree(b.p);
   if (ctx->bexec) cudaGraphExecDestroy(ctx->bexec);
   for (auto& e : ctx->bev) if (e) cudaEventDestroy(e);
   if (ctx->bstream) cudaStreamDestroy(ctx->bstream);

@@ -18,7 +18,8 @@
 // integral launch in each of its launch shapes (the register cap per thread,
 // i.e. resident warps per SM, at 4 warps and 4 cells in flight per CTA),
 // times each with CUDA events, and keeps the fastest for every later call of
-// the context.  All shapes compute bit-identical results.
+// the context.  Each shape is deterministic; two shapes are separate
+// compilations of the same source and may round FP32 differently.
 #include <algorithm>
 #include <cstring>
 #include <numeric>
@@ -87,6 +88,9 @@ int map_batch(map_ctx* ctx, int nsnap, const map_particles* parts, const int* gr
   if ((int)ctx->batch_off.size() < nsnap) {
     ctx->batch_off.resize(nsnap);
     ctx->batch_idx.resize(nsnap);
+    ctx->batch_itm.resize(nsnap);
+    ctx->batch_ioff.resize(nsnap);
+    ctx->batch_part.resize(nsnap);
   }
   // 1. octree and pair list per snapshot, kept in the batch slots
   std::vector<SnapDesc> hd(nsnap);
@@ -99,7 +103,13 @@ int map_batch(map_ctx* ctx, int nsnap, const map_particles* parts, const int* gr
     const PreparedGrid* g = ctx->grids[grids[j]];
     MAP_TRY(tree_build(ctx, p->x, p->y, p->z, p->m, p->h, p->n, s));
     // the list goes straight to the snapshot's slot (reused by later batches)
-    MAP_TRY(pairs_build(ctx, g, s, &ctx->batch_off[j], &ctx->batch_idx[j]));
+    PairBufs pb;
+    pb.off = &ctx->batch_off[j];
+    pb.idx = &ctx->batch_idx[j];
+    pb.items = &ctx->batch_itm[j];
+    pb.ioff = &ctx->batch_ioff[j];
+    pb.part = &ctx->batch_part[j];
+    MAP_TRY(pairs_build(ctx, g, s, pb));
     hd[j] = make_desc(ctx, g, p, &outs[j], ctx->pair_off, ctx->pair_idx, nullptr, j);
     np[j] = ctx->n_pairs;
     n_pairs += np[j];
@@ -109,6 +119,9 @@ int map_batch(map_ctx* ctx, int nsnap, const map_particles* parts, const int* gr
   ctx->pair_off = nullptr;  // no single pair list describes a batch
   ctx->pair_idx = nullptr;
   ctx->pair_frac = nullptr;
+  ctx->items = nullptr;
+  ctx->item_off = nullptr;
+  ctx->partial = nullptr;
   ctx->n_pairs = n_pairs;
   ctx->last_ncell = total;
 
@@ -117,19 +130,22 @@ int map_batch(map_ctx* ctx, int nsnap, const map_particles* parts, const int* gr
   std::iota(order.begin(), order.end(), 0);
   std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return np[a] > np[b]; });
   std::vector<SnapDesc> qd(nsnap);
-  std::vector<int64_t> base(nsnap + 1);
-  base[0] = 0;
+  std::vector<int64_t> ibase(nsnap + 1), base(nsnap + 1);
+  ibase[0] = base[0] = 0;
   for (int i = 0; i < nsnap; ++i) {
     qd[i] = hd[order[i]];
+    ibase[i + 1] = ibase[i] + qd[i].nitems;
     base[i + 1] = base[i] + qd[i].ncell;
   }
   SnapDesc* d_desc;
   int64_t* d_base;
   double* d_tot;
   MAP_TRY(ensure_t(ctx, ctx->ws_misc[5], nsnap, &d_desc));
-  MAP_TRY(ensure_t(ctx, ctx->ws_misc[6], nsnap + 1, &d_base));
+  MAP_TRY(ensure_t(ctx, ctx->ws_misc[6], 2 * (nsnap + 1), &d_base));
   MAP_TRY(ensure_t(ctx, ctx->ws_misc[7], nsnap, &d_tot));
-  const BatchArgs B{d_desc, d_base, nsnap, total, ctx->d_counters};
+  int64_t* d_ibase = d_base;
+  int64_t* d_cbase = d_base + nsnap + 1;
+  const BatchArgs B{d_desc, d_ibase, d_cbase, nsnap, ibase[nsnap], total, ctx->d_counters};
 
   // 3. the integral launch of the whole batch: ordered after the caller's
   // stream, on the context's own stream (graphs cannot be captured on the
@@ -138,16 +154,19 @@ int map_batch(map_ctx* ctx, int nsnap, const map_particles* parts, const int* gr
   CUDA_TRY(cudaStreamWaitEvent(ctx->bstream, ctx->bev[0], 0));
   const int prec = ctx->cfg.precision == MAP_MIXED ? MAP_MIXED : MAP_FP64;
   if (ctx->cfg.autotune && prec == MAP_MIXED && !ctx->tune_done[MAP_MIXED]) {
-    MAP_TRY(integrals_upload(ctx, qd.data(), base.data(), nsnap, d_desc, d_base, ctx->bstream));
+    MAP_TRY(integrals_upload(ctx, qd.data(), ibase.data(), base.data(), nsnap, d_desc, d_ibase, d_cbase,
+                             ctx->bstream));
     MAP_TRY(integrals_autotune(ctx, B, ctx->bstream));
   }
   const int variant = ctx->tuned[prec];
   // graph signature: descriptor bytes, queue layout, launch shape, targets
-  std::vector<unsigned char> sig(sizeof(SnapDesc) * nsnap + sizeof(int64_t) * (nsnap + 1) + 4 * sizeof(void*));
+  std::vector<unsigned char> sig(sizeof(SnapDesc) * nsnap + 2 * sizeof(int64_t) * (nsnap + 1) + 4 * sizeof(void*));
   {
     unsigned char* q = sig.data();
     std::memcpy(q, qd.data(), sizeof(SnapDesc) * nsnap);
     q += sizeof(SnapDesc) * nsnap;
+    std::memcpy(q, ibase.data(), sizeof(int64_t) * (nsnap + 1));
+    q += sizeof(int64_t) * (nsnap + 1);
     std::memcpy(q, base.data(), sizeof(int64_t) * (nsnap + 1));
     q += sizeof(int64_t) * (nsnap + 1);
     const void* extra[4] = {d_desc, d_base, d_tot, reinterpret_cast<const void*>((intptr_t)(variant * 2 + prec))};
@@ -160,7 +179,8 @@ int map_batch(map_ctx* ctx, int nsnap, const map_particles* parts, const int* gr
     }
     const int64_t l0 = ctx->launches;
     CUDA_TRY(cudaStreamBeginCapture(ctx->bstream, cudaStreamCaptureModeThreadLocal));
-    int rc = integrals_upload(ctx, qd.data(), base.data(), nsnap, d_desc, d_base, ctx->bstream);
+    int rc = integrals_upload(ctx, qd.data(), ibase.data(), base.data(), nsnap, d_desc, d_ibase, d_cbase,
+                              ctx->bstream);
     if (rc == MAP_OK) rc = integrals_enqueue(ctx, B, variant, ctx->bstream);
     if (rc == MAP_OK) rc = integrals_sum(ctx, d_desc, nsnap, d_tot, ctx->bstream);
     cudaGraph_t graph = nullptr;

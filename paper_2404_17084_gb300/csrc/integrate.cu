@@ -184,11 +184,11 @@ __global__ void __launch_bounds__(NW * 32, MINB) pair_integrals(BatchArgs B) {
     if (lane == 0) g = (int64_t)atomicAdd(&B.counters[3], 1ULL);
     g = __shfl_sync(FULL, g, 0);
     if (g >= B.total) break;
-    // the snapshot owning queue position g: last j with cell_base[j] <= g
+    // the snapshot owning queue position g: last j with item_base[j] <= g
     int jl = 0, jh = B.nsnap - 1;
     while (jl < jh) {
       const int jm = (jl + jh + 1) >> 1;
-      if (B.cell_base[jm] <= g) jl = jm; else jh = jm - 1;
+      if (B.item_base[jm] <= g) jl = jm; else jh = jm - 1;
     }
     if (jl != cur) {
       __syncwarp();
@@ -198,7 +198,9 @@ __global__ void __launch_bounds__(NW * 32, MINB) pair_integrals(BatchArgs B) {
       __syncwarp();
       cur = jl;
     }
-    const int64_t c = g - B.cell_base[jl];
+    const int64_t it = g - B.item_base[jl];
+    const PairItem item = A.items[it];
+    const int64_t c = item.cell;
     const V4* __restrict__ face = reinterpret_cast<const V4*>(A.face);
     const T* __restrict__ edge = reinterpret_cast<const T*>(A.edge);
     const int64_t f0 = A.cfo[c];
@@ -206,7 +208,7 @@ __global__ void __launch_bounds__(NW * 32, MINB) pair_integrals(BatchArgs B) {
     const int64_t l0 = A.fvo[f0];
     const T* __restrict__ ecell = edge + l0 * EDGE_STRIDE;
     double macc = 0.0;
-    const int64_t pb = A.pair_off[c], pe = A.pair_off[c + 1];
+    const int64_t pb = item.lo, pe = item.lo + item.cnt;
     for (int64_t p0 = pb; p0 < pe; p0 += 32) {
       const int64_t p = p0 + lane;
       const bool active = p < pe;
@@ -335,10 +337,7 @@ __global__ void __launch_bounds__(NW * 32, MINB) pair_integrals(BatchArgs B) {
       __syncwarp();
     }
     for (int o = 16; o > 0; o >>= 1) macc += __shfl_down_sync(FULL, macc, o);
-    if (lane == 0) {
-      A.cell_mass[c] = macc;
-      if (A.cell_rho) A.cell_rho[c] = macc / A.vol[c];
-    }
+    if (lane == 0) A.partial[it] = macc;  // summed per cell by cell_sums
     __syncwarp();
   }
   // work tally: warp sums, one atomic per warp and counter
@@ -379,7 +378,7 @@ int launch(map_ctx* ctx, const BatchArgs& B, cudaStream_t s) {
 // Descriptor upload through kernel parameters: the values are captured at
 // launch, so the host copy may be reused at once and the launch can sit in a
 // CUDA graph.
-constexpr int DESC_CHUNK = 24;  // 24 x 160 bytes of parameters per launch
+constexpr int DESC_CHUNK = 16;  // 16 x 192 bytes of parameters per launch
 struct DescChunk {
   SnapDesc d[DESC_CHUNK];
   int n;
@@ -396,6 +395,25 @@ __global__ void put_i64(I64Chunk c, int64_t* dst) {
   for (int i = threadIdx.x; i < c.n; i += blockDim.x) dst[i] = c.v[i];
 }
 
+// M_i = sum of cell i's item partials, in item order; rho_i = M_i / V_i.
+// One thread per cell over the cells of all snapshots.
+__global__ void cell_sums(const SnapDesc* __restrict__ d, const int64_t* __restrict__ cell_base, int nsnap,
+                          int64_t total_cells) {
+  const int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (g >= total_cells) return;
+  int jl = 0, jh = nsnap - 1;
+  while (jl < jh) {
+    const int jm = (jl + jh + 1) >> 1;
+    if (cell_base[jm] <= g) jl = jm; else jh = jm - 1;
+  }
+  const SnapDesc& D = d[jl];
+  const int64_t c = g - cell_base[jl];
+  double M = 0.0;
+  for (int64_t i = D.item_off[c]; i < D.item_off[c + 1]; ++i) M += D.partial[i];
+  D.cell_mass[c] = M;
+  if (D.cell_rho) D.cell_rho[c] = M / D.vol[c];
+}
+
 // sum_i M_i of each snapshot (one block per snapshot, fixed order)
 __global__ void sum_snapshots(const SnapDesc* __restrict__ d, double* totals) {
   typedef cub::BlockReduce<double, 256> BR;
@@ -409,8 +427,8 @@ __global__ void sum_snapshots(const SnapDesc* __restrict__ d, double* totals) {
 
 }  // namespace
 
-int integrals_upload(map_ctx* ctx, const SnapDesc* h_desc, const int64_t* h_base, int nsnap, SnapDesc* d_desc,
-                      int64_t* d_base, cudaStream_t s) {
+int integrals_upload(map_ctx* ctx, const SnapDesc* h_desc, const int64_t* h_ibase, const int64_t* h_cbase,
+                     int nsnap, SnapDesc* d_desc, int64_t* d_ibase, int64_t* d_cbase, cudaStream_t s) {
   for (int j0 = 0; j0 < nsnap; j0 += DESC_CHUNK) {
     DescChunk c;
     c.n = nsnap - j0 < DESC_CHUNK ? nsnap - j0 : DESC_CHUNK;
@@ -418,12 +436,16 @@ int integrals_upload(map_ctx* ctx, const SnapDesc* h_desc, const int64_t* h_base
     put_descs<<<1, DESC_CHUNK, 0, s>>>(c, d_desc + j0); ++ctx->launches;
     CUDA_TRY(cudaGetLastError());
   }
-  for (int j0 = 0; j0 <= nsnap; j0 += I64_CHUNK) {
-    I64Chunk c;
-    c.n = nsnap + 1 - j0 < I64_CHUNK ? nsnap + 1 - j0 : I64_CHUNK;
-    for (int i = 0; i < c.n; ++i) c.v[i] = h_base[j0 + i];
-    put_i64<<<1, 128, 0, s>>>(c, d_base + j0); ++ctx->launches;
-    CUDA_TRY(cudaGetLastError());
+  for (int k = 0; k < 2; ++k) {
+    const int64_t* h = k == 0 ? h_ibase : h_cbase;
+    int64_t* dd = k == 0 ? d_ibase : d_cbase;
+    for (int j0 = 0; j0 <= nsnap; j0 += I64_CHUNK) {
+      I64Chunk c;
+      c.n = nsnap + 1 - j0 < I64_CHUNK ? nsnap + 1 - j0 : I64_CHUNK;
+      for (int i = 0; i < c.n; ++i) c.v[i] = h[j0 + i];
+      put_i64<<<1, 128, 0, s>>>(c, dd + j0); ++ctx->launches;
+      CUDA_TRY(cudaGetLastError());
+    }
   }
   return MAP_OK;
 }
@@ -433,12 +455,19 @@ int integrals_enqueue(map_ctx* ctx, const BatchArgs& B, int variant, cudaStream_
   CUDA_TRY(cudaMemsetAsync(ctx->d_counters + 8, 0, 8 * sizeof(unsigned long long), s));
   if (ctx->cfg.precision == MAP_MIXED) {
     switch (variant) {
-      case 1: return launch<float, true, 4, 4>(ctx, B, s);
-      case 2: return launch<float, true, 4, 6>(ctx, B, s);
-      default: return launch<float, true, 4, 5>(ctx, B, s);
+      case 1: MAP_TRY((launch<float, true, 4, 4>(ctx, B, s))); break;
+      case 2: MAP_TRY((launch<float, true, 4, 6>(ctx, B, s))); break;
+      default: MAP_TRY((launch<float, true, 4, 5>(ctx, B, s))); break;
     }
+  } else {
+    MAP_TRY((launch<double, false, 4, 4>(ctx, B, s)));
   }
-  return launch<double, false, 4, 4>(ctx, B, s);
+  if (B.total_cells > 0) {
+    cell_sums<<<nblk(B.total_cells, 256), 256, 0, s>>>(B.snaps, B.cell_base, B.nsnap, B.total_cells);
+    ++ctx->launches;
+    CUDA_TRY(cudaGetLastError());
+  }
+  return MAP_OK;
 }
 
 int integrals_sum(map_ctx* ctx, const SnapDesc* d_desc, int nsnap, double* totals, cudaStream_t s) {
@@ -466,6 +495,10 @@ SnapDesc make_desc(map_ctx* ctx, const PreparedGrid* g, const map_particles* p, 
   d.edge = mixed ? (const void*)g->edge32 : (const void*)g->edge64;
   d.face64 = g->face64;
   d.edge64 = g->edge64;
+  d.items = ctx->items;
+  d.item_off = ctx->item_off;
+  d.partial = ctx->partial;
+  d.nitems = ctx->n_items;
   d.orig = orig;
   return d;
 }
@@ -477,11 +510,11 @@ int integrals_run(map_ctx* ctx, const PreparedGrid* g, const map_particles* p, m
   SnapDesc* d_desc;
   int64_t* d_base;
   MAP_TRY(ensure_t(ctx, ctx->ws_misc[3], 1, &d_desc));
-  MAP_TRY(ensure_t(ctx, ctx->ws_misc[4], 2, &d_base));
+  MAP_TRY(ensure_t(ctx, ctx->ws_misc[4], 4, &d_base));
   const SnapDesc h = make_desc(ctx, g, p, out, ctx->pair_off, ctx->pair_idx, frac, 0);
-  const int64_t base[2] = {0, g->ncell};
-  MAP_TRY(integrals_upload(ctx, &h, base, 1, d_desc, d_base, s));
-  BatchArgs B{d_desc, d_base, 1, g->ncell, ctx->d_counters};
+  const int64_t ibase[2] = {0, ctx->n_items}, cbase[2] = {0, g->ncell};
+  MAP_TRY(integrals_upload(ctx, &h, ibase, cbase, 1, d_desc, d_base, d_base + 2, s));
+  BatchArgs B{d_desc, d_base, d_base + 2, 1, ctx->n_items, g->ncell, ctx->d_counters};
   if (ctx->cfg.autotune && ctx->cfg.precision == MAP_MIXED && !ctx->tune_done[MAP_MIXED])
     MAP_TRY(integrals_autotune(ctx, B, s));
   phase_begin(ctx, 2, s);

@@ -88,6 +88,15 @@ struct DevTree {
   float* box32 = nullptr;             // 8 per node: FP32 box rounded outward, largest h rounded up, pad
 };
 
+// A work item of the pair-integral kernel: cnt pairs of one cell, starting
+// at position lo of the pair list.  Cells with many pairs are split into
+// several items so that grids of few, large cells still fill the GPU.
+struct PairItem {
+  int64_t lo;
+  int32_t cell;
+  int32_t cnt;
+};
+
 struct map_ctx {
   map_config cfg;
   int device = 0;
@@ -96,7 +105,7 @@ struct map_ctx {
   std::vector<PreparedGrid*> grids;
   // workspace
   DevBuf ws_tree[32];
-  DevBuf ws_pairs[10];
+  DevBuf ws_pairs[13];
   DevBuf ws_misc[8];
   DevBuf cub_tmp;
   DevTree tree;
@@ -106,6 +115,10 @@ struct map_ctx {
   int64_t* pair_off = nullptr;
   int32_t* pair_idx = nullptr;
   double* pair_frac = nullptr;
+  struct PairItem* items = nullptr;  // work items of the pair-integral kernel
+  int64_t* item_off = nullptr;       // [ncell+1]: items of cell c
+  double* partial = nullptr;         // per item: its pairs' mass
+  int64_t n_items = 0;
   // device counters: [0] status, [1] edge terms, [2] fp64 terms, [3] work queue,
   // [4..5] scratch, [8] face tests, [9] edge records read, [10] inner-piece
   // antiderivative evaluations, [11] middle-piece Gauss-Legendre intervals
@@ -125,7 +138,7 @@ struct map_ctx {
   float tune_ms[3] = {0.f, 0.f, 0.f};
   // batches: per-snapshot pair lists of the last batch, and the CUDA graph of
   // its integral launch with the descriptor bytes it was captured for
-  std::vector<DevBuf> batch_off, batch_idx;
+  std::vector<DevBuf> batch_off, batch_idx, batch_itm, batch_ioff, batch_part;
   cudaStream_t bstream = nullptr;
   cudaEvent_t bev[2] = {};
   cudaGraphExec_t bexec = nullptr;
@@ -164,6 +177,10 @@ struct SnapDesc {
   double* frac;        // per-pair f_ai, or NULL
   double* cell_mass;
   double* cell_rho;    // or NULL
+  const PairItem* items;     // work items
+  const int64_t* item_off;   // [ncell+1]
+  double* partial;           // per item
+  int64_t nitems;
   const void* face;    // site-relative planes: float4 (mixed) or double4 (FP64)
   const void* edge;    // EDGE_STRIDE floats or doubles per loop entry
   const double4_32a* face64;
@@ -171,13 +188,16 @@ struct SnapDesc {
   int64_t orig;        // the caller's index of this snapshot
 };
 
-// The queue of the pair-integral kernel: cells of nsnap snapshots, snapshot j
-// owning queue positions [cell_base[j], cell_base[j+1]).
+// The queue of the pair-integral kernel: work items of nsnap snapshots,
+// snapshot j owning queue positions [item_base[j], item_base[j+1]) and cells
+// [cell_base[j], cell_base[j+1]) of the per-cell sums.
 struct BatchArgs {
   const SnapDesc* snaps;
+  const int64_t* item_base;
   const int64_t* cell_base;
   int nsnap;
-  int64_t total;
+  int64_t total;        // items
+  int64_t total_cells;
   unsigned long long* counters;  // [1] edge terms, [2] FP64 terms, [3] queue, [8..13] work tally
 };
 
@@ -187,16 +207,24 @@ constexpr int N_VARIANTS = 3;  // launch shapes of the mixed pair-integral kerne
 int grid_prepare(map_ctx* ctx, const map_grid* in, PreparedGrid* g, cudaStream_t s);
 int tree_build(map_ctx* ctx, const double* x, const double* y, const double* z, const double* m,
                const double* h, int64_t n, cudaStream_t s, bool want_size = false);
-// Pair list of the grid against the current octree; the offsets and indices
-// go to off_buf / idx_buf (default: the context's workspace).
-int pairs_build(map_ctx* ctx, const PreparedGrid* g, cudaStream_t s, DevBuf* off_buf = nullptr,
-                DevBuf* idx_buf = nullptr);
+// Output buffers of a pair-list build; nullptr members mean the context's
+// workspace.
+struct PairBufs {
+  DevBuf* off = nullptr;    // pair offsets per cell
+  DevBuf* idx = nullptr;    // pair list
+  DevBuf* items = nullptr;  // work items
+  DevBuf* ioff = nullptr;   // items per cell (offsets)
+  DevBuf* part = nullptr;   // per-item partial masses
+};
+
+// Pair list of the grid against the current octree, and its work items.
+int pairs_build(map_ctx* ctx, const PreparedGrid* g, cudaStream_t s, const PairBufs& out = PairBufs());
 int check_particles(map_ctx* ctx, const map_particles* p, bool need_m, bool need_h, cudaStream_t s);
 int integrals_run(map_ctx* ctx, const PreparedGrid* g, const map_particles* p, map_outputs* out, cudaStream_t s);
 SnapDesc make_desc(map_ctx* ctx, const PreparedGrid* g, const map_particles* p, const map_outputs* out,
                    const int64_t* pair_off, const int32_t* pair_idx, double* frac, int orig);
-int integrals_upload(map_ctx* ctx, const SnapDesc* h_desc, const int64_t* h_base, int nsnap, SnapDesc* d_desc,
-                      int64_t* d_base, cudaStream_t s);
+int integrals_upload(map_ctx* ctx, const SnapDesc* h_desc, const int64_t* h_ibase, const int64_t* h_cbase,
+                     int nsnap, SnapDesc* d_desc, int64_t* d_ibase, int64_t* d_cbase, cudaStream_t s);
 int integrals_enqueue(map_ctx* ctx, const BatchArgs& B, int variant, cudaStream_t s);
 int integrals_sum(map_ctx* ctx, const SnapDesc* d_desc, int nsnap, double* totals, cudaStream_t s);
 int integrals_autotune(map_ctx* ctx, const BatchArgs& B, cudaStream_t s);

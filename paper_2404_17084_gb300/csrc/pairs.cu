@@ -147,6 +147,108 @@ __global__ void __launch_bounds__(128) pair_traverse(int64_t ncell, const int32_
   if (!FILL && valid) count[c] = cnt;
 }
 
+// The same walk with one warp per cell, for grids with many particles per
+// cell (few, large cells): lanes test a node's children in parallel, the
+// particles of the leaves the cell reaches are gathered in a buffer, and all
+// 32 lanes apply the pair rule to 32 candidates at a time.  Output as
+// pair_traverse (any order: each cell's list is sorted afterwards).
+constexpr int WALK_STK = 160;   // a popped node pushes at most 8 of its children; 22 levels at most
+constexpr int WALK_CAND = 512;  // candidate positions gathered before they are tested
+
+template <bool FILL>
+__global__ void __launch_bounds__(128) pair_walk_warp(int64_t ncell, const int32_t* __restrict__ cells, PairTree T,
+                                                      PairGrid G, int64_t* count, const int64_t* __restrict__ off,
+                                                      int32_t* out, const unsigned long long* n_dev) {
+  __shared__ int32_t s_stk[4][WALK_STK];
+  __shared__ int32_t s_cand[4][WALK_CAND];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t t = blockIdx.x * 4 + warp;
+  if (t >= (n_dev ? (int64_t)*n_dev : ncell)) return;  // whole warp
+  const int64_t c = cells ? cells[t] : t;
+  const double sx = G.site[3 * c], sy = G.site[3 * c + 1], sz = G.site[3 * c + 2], R = G.rad[c];
+  const float fsx = (float)sx, fsy = (float)sy, fsz = (float)sz, fR = (float)R;
+  SiteSplit SS;
+  SS.hx = fsx; SS.lx = (float)(sx - (double)fsx);
+  SS.hy = fsy; SS.ly = (float)(sy - (double)fsy);
+  SS.hz = fsz; SS.lz = (float)(sz - (double)fsz);
+  SS.R = fR;
+  int32_t* stk = s_stk[warp];
+  int32_t* cand = s_cand[warp];
+  int64_t w = FILL ? off[c] : c * PAIR_ROW;
+  int64_t cnt = 0;
+  int sp = 1, nc_ = 0;  // stack depth, candidates held
+  if (lane == 0) stk[0] = 0;
+  __syncwarp();
+  // test the candidates held, 32 at a time
+  auto flush = [&]() {
+    __syncwarp();  // the candidates written by every lane are visible
+    for (int b = 0; b < nc_; b += 32) {
+      const int j = b + lane;
+      const bool hit = j < nc_ && pair_rule(G, T, c, SS, cand[j]);
+      const unsigned m = __ballot_sync(0xffffffffu, hit);
+      if (hit) {
+        const int64_t q = cnt + __popc(m & ((1u << lane) - 1u));
+        if (FILL || q < PAIR_ROW) out[w + q] = T.idx[cand[j]];
+      }
+      cnt += __popc(m);
+    }
+    __syncwarp();
+    nc_ = 0;
+  };
+  while (sp > 0) {
+    const int nd = stk[sp - 1];
+    --sp;
+    const int nch = T.nch[nd];
+    if (nch == 0) {  // the root is a leaf
+      const int64_t a0 = T.nb[nd], a1 = T.ne[nd];
+      for (int64_t a = a0; a < a1; a += WALK_CAND) {
+        const int k = (int)((a1 - a) < WALK_CAND ? (a1 - a) : WALK_CAND);
+        __syncwarp();
+        for (int i = lane; i < k; i += 32) cand[i] = (int32_t)(a + i);
+        __syncwarp();
+        nc_ = k;
+        flush();
+      }
+      continue;
+    }
+    const int64_t c0 = T.fc[nd];
+    bool need = false, leaf = false;
+    if (lane < nch) {
+      const float* b = T.box32 + 8 * (c0 + lane);
+      const float dx = fsx < b[0] ? b[0] - fsx : (fsx > b[3] ? fsx - b[3] : 0.f);
+      const float dy = fsy < b[1] ? b[1] - fsy : (fsy > b[4] ? fsy - b[4] : 0.f);
+      const float dz = fsz < b[2] ? b[2] - fsz : (fsz > b[5] ? fsz - b[5] : 0.f);
+      const float reach = (2.f * b[6] + fR + 1e-6f) * 1.000001f;
+      need = dx * dx + dy * dy + dz * dz <= reach * reach;
+      leaf = need && T.nch[c0 + lane] == 0;
+    }
+    const unsigned ml = __ballot_sync(0xffffffffu, leaf), mi = __ballot_sync(0xffffffffu, need && !leaf);
+    const int ni = __popc(mi);
+    __syncwarp();  // every lane has read the popped entry
+    if (sp + ni > WALK_STK) break;  // unreachable for trees of at most 22 levels
+    if (need && !leaf) stk[sp + ni - 1 - __popc(mi & ((1u << lane) - 1u))] = (int)(c0 + lane);
+    sp += ni;
+    // leaf children: gather their particles, testing whenever the buffer fills
+    unsigned m = ml;
+    while (m) {
+      const int bl = __ffs(m) - 1;
+      m &= m - 1;
+      const int64_t a0 = T.nb[c0 + bl], a1 = T.ne[c0 + bl];
+      for (int64_t a = a0; a < a1;) {
+        if (nc_ == WALK_CAND) flush();
+        const int room = WALK_CAND - nc_;
+        const int k = (int)((a1 - a) < room ? (a1 - a) : room);
+        for (int i = lane; i < k; i += 32) cand[nc_ + i] = (int32_t)(a + i);
+        nc_ += k;
+        a += k;
+      }
+    }
+    __syncwarp();
+  }
+  flush();
+  if (!FILL && lane == 0) count[c] = cnt;
+}
+
 // Move the rows kept by the counting pass to their place in the list (one
 // warp per cell); cells whose count exceeded the row go to the overflow list
 // for the filling pass.
@@ -164,6 +266,27 @@ __global__ void __launch_bounds__(128) place_rows(int64_t ncell, const int64_t* 
   const int32_t* src = rows + c * PAIR_ROW;
   int32_t* dst = out + off[c];
   for (int64_t i = lane; i < n; i += 32) dst[i] = src[i];
+}
+
+// Work items: cell c's n pairs in max(1, ceil(ceil(n/32)/K)) items of at
+// most K blocks of 32 pairs.
+__global__ void item_count(int64_t ncell, const int64_t* __restrict__ off, int64_t K, int64_t* cnt) {
+  const int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (c >= ncell) return;
+  const int64_t blocks = (off[c + 1] - off[c] + 31) / 32;
+  cnt[c] = blocks > K ? (blocks + K - 1) / K : 1;
+}
+__global__ void item_fill(int64_t ncell, const int64_t* __restrict__ off, const int64_t* __restrict__ ioff,
+                          int64_t K, PairItem* items) {
+  const int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (c >= ncell) return;
+  const int64_t b = off[c], n = off[c + 1] - b, span = 32 * K;
+  int64_t lo = 0;
+  for (int64_t i = ioff[c]; i < ioff[c + 1]; ++i) {
+    const int64_t k = n - lo < span ? n - lo : span;
+    items[i] = PairItem{b + lo, (int32_t)c, (int32_t)k};
+    lo += k;
+  }
 }
 
 // Sort each cell's pair list (<= 1024 entries) in shared memory, one warp
@@ -226,7 +349,7 @@ __global__ void site_keys(int64_t n, const double* __restrict__ site, uint64_t* 
 
 }  // namespace
 
-int pairs_build(map_ctx* ctx, const PreparedGrid* g, cudaStream_t s, DevBuf* off_buf, DevBuf* idx_buf) {
+int pairs_build(map_ctx* ctx, const PreparedGrid* g, cudaStream_t s, const PairBufs& out) {
   DevTree& T = ctx->tree;
   const int64_t nc = g->ncell;
   const int tpb = 128;
@@ -249,11 +372,16 @@ int pairs_build(map_ctx* ctx, const PreparedGrid* g, cudaStream_t s, DevBuf* off
   PairGrid PG{g->cell_face_off, g->face_plane, g->face32, g->site, g->rad};
   int64_t *count, *off;
   MAP_TRY(ensure_t(ctx, ctx->ws_pairs[0], nc + 1, &count));
-  MAP_TRY(ensure_t(ctx, off_buf ? *off_buf : ctx->ws_pairs[1], nc + 1, &off));
+  MAP_TRY(ensure_t(ctx, out.off ? *out.off : ctx->ws_pairs[1], nc + 1, &off));
   int32_t* rows;
   MAP_TRY(ensure_t(ctx, ctx->ws_pairs[8], (size_t)nc * PAIR_ROW, &rows));
   CUDA_TRY(cudaMemsetAsync(count + nc, 0, sizeof(int64_t), s));
-  pair_traverse<false><<<nblk(nc, tpb), tpb, 0, s>>>(nc, order, PT, PG, count, nullptr, rows, nullptr);
+  // many particles per cell (few, large cells): one warp per cell
+  const bool per_warp = T.n > 16 * nc;
+  if (per_warp)
+    pair_walk_warp<false><<<(unsigned)((nc + 3) / 4), tpb, 0, s>>>(nc, nullptr, PT, PG, count, nullptr, rows, nullptr);
+  else
+    pair_traverse<false><<<nblk(nc, tpb), tpb, 0, s>>>(nc, order, PT, PG, count, nullptr, rows, nullptr);
   ++ctx->launches;
   CUDA_TRY(cudaGetLastError());
   tb = 0;
@@ -265,7 +393,7 @@ int pairs_build(map_ctx* ctx, const PreparedGrid* g, cudaStream_t s, DevBuf* off
   const int64_t np = ctx->h_scratch[0];
   int32_t *raw, *sorted;
   MAP_TRY(ensure_t(ctx, ctx->ws_pairs[2], np + 1, &raw));
-  MAP_TRY(ensure_t(ctx, idx_buf ? *idx_buf : ctx->ws_pairs[3], np + 1, &sorted));
+  MAP_TRY(ensure_t(ctx, out.idx ? *out.idx : ctx->ws_pairs[3], np + 1, &sorted));
   // rows that fit go straight to the list; the other cells are walked again
   int32_t* ovf;
   MAP_TRY(ensure_t(ctx, ctx->ws_pairs[9], nc, &ovf));
@@ -273,7 +401,11 @@ int pairs_build(map_ctx* ctx, const PreparedGrid* g, cudaStream_t s, DevBuf* off
   CUDA_TRY(cudaMemsetAsync(d_novf, 0, sizeof(unsigned long long), s));
   place_rows<<<nblk(nc * 32, tpb), tpb, 0, s>>>(nc, count, off, rows, raw, ovf, d_novf); ++ctx->launches;
   CUDA_TRY(cudaGetLastError());
-  pair_traverse<true><<<nblk(nc, tpb), tpb, 0, s>>>(nc, ovf, PT, PG, nullptr, off, raw, d_novf); ++ctx->launches;
+  if (per_warp)
+    pair_walk_warp<true><<<(unsigned)((nc + 3) / 4), tpb, 0, s>>>(nc, ovf, PT, PG, nullptr, off, raw, d_novf);
+  else
+    pair_traverse<true><<<nblk(nc, tpb), tpb, 0, s>>>(nc, ovf, PT, PG, nullptr, off, raw, d_novf);
+  ++ctx->launches;
   CUDA_TRY(cudaGetLastError());
   if (np > 0) {
     sort_small_segments<<<nblk(nc, 4), 128, 0, s>>>(nc, off, raw, sorted); ++ctx->launches;
@@ -295,9 +427,37 @@ int pairs_build(map_ctx* ctx, const PreparedGrid* g, cudaStream_t s, DevBuf* off
       CUDA_TRY(cub::DeviceSegmentedSort::SortKeys(ctx->cub_tmp.p, tb, raw, sorted, np, nlarge, lb, le, s));
     }
   }
+  // work items: K blocks of 32 pairs at most, K chosen so that the launch has
+  // at least 16 items per resident warp (4 warps x 6 CTAs per SM)
+  const int64_t blocks = np / 32 + nc;
+  const int64_t target = 16LL * ctx->sm_count * 24;
+  const int64_t K = blocks / target > 1 ? blocks / target : 1;
+  int64_t *icnt, *ioff;
+  MAP_TRY(ensure_t(ctx, ctx->ws_pairs[0], nc + 1, &icnt));  // the counts are no longer needed
+  MAP_TRY(ensure_t(ctx, out.ioff ? *out.ioff : ctx->ws_pairs[11], nc + 1, &ioff));
+  item_count<<<nblk(nc, 256), 256, 0, s>>>(nc, off, K, icnt); ++ctx->launches;
+  CUDA_TRY(cudaGetLastError());
+  CUDA_TRY(cudaMemsetAsync(icnt + nc, 0, sizeof(int64_t), s));
+  tb = 0;
+  CUDA_TRY(cub::DeviceScan::ExclusiveSum(nullptr, tb, icnt, ioff, nc + 1, s));
+  MAP_TRY(ctx_ensure(ctx, ctx->cub_tmp, tb));
+  CUDA_TRY(cub::DeviceScan::ExclusiveSum(ctx->cub_tmp.p, tb, icnt, ioff, nc + 1, s));
+  CUDA_TRY(cudaMemcpyAsync(ctx->h_scratch, ioff + nc, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+  CUDA_TRY(cudaStreamSynchronize(s));
+  const int64_t nitems = ctx->h_scratch[0];
+  PairItem* items;
+  double* part;
+  MAP_TRY(ensure_t(ctx, out.items ? *out.items : ctx->ws_pairs[10], nitems, &items));
+  MAP_TRY(ensure_t(ctx, out.part ? *out.part : ctx->ws_pairs[12], nitems, &part));
+  item_fill<<<nblk(nc, 256), 256, 0, s>>>(nc, off, ioff, K, items); ++ctx->launches;
+  CUDA_TRY(cudaGetLastError());
   ctx->n_pairs = np;
   ctx->pair_off = off;
   ctx->pair_idx = sorted;
+  ctx->items = items;
+  ctx->item_off = ioff;
+  ctx->partial = part;
+  ctx->n_items = nitems;
   ctx->last_ncell = nc;
   return MAP_OK;
 }

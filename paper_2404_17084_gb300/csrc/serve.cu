@@ -79,12 +79,15 @@ void trim(map_ctx* ctx) {
   for (auto& b : ctx->ws_tree) drop(b);
   for (auto& b : ctx->ws_pairs) drop(b);
   for (auto& b : ctx->ws_misc) drop(b);
-  for (auto& b : ctx->batch_off) drop(b);
-  for (auto& b : ctx->batch_idx) drop(b);
+  for (auto* v : {&ctx->batch_off, &ctx->batch_idx, &ctx->batch_itm, &ctx->batch_ioff, &ctx->batch_part})
+    for (auto& b : *v) drop(b);
   drop(ctx->cub_tmp);
   ctx->pair_off = nullptr;
   ctx->pair_idx = nullptr;
   ctx->pair_frac = nullptr;
+  ctx->items = nullptr;
+  ctx->item_off = nullptr;
+  ctx->partial = nullptr;
   ctx->bsig.clear();
 }
 

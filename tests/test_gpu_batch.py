@@ -64,15 +64,18 @@ def test_batch_equals_single(snapshots, precision):
 
 
 def test_batch_autotune_and_replay(snapshots):
-    """The autotuner times every launch shape and keeps one; all shapes and
-    the replayed graph give the same bits."""
+    """The autotuner times every launch shape and keeps one.  Replays of the
+    captured graph give the same bits; another launch shape (a separate
+    compilation of the same source) agrees to FP32 rounding."""
     ref, _, _ = run_batch(snapshots, 1)
     runs, _, (chosen, ms) = run_batch(snapshots, 1, autotune=1, repeat=3)
     assert 0 <= chosen < len(ms) and all(t > 0 for t in ms)
-    for masses, totals in runs:
-        for a, b in zip(masses, ref[0][0]):
+    for masses, totals in runs[1:]:
+        for a, b in zip(masses, runs[0][0]):
             assert np.array_equal(a, b)
-        assert np.array_equal(totals, ref[0][1])
+        assert np.array_equal(totals, runs[0][1])
+    worst = max(rel_err(a, b).max() for a, b in zip(runs[0][0], ref[0][0]))
+    assert worst < 1e-6, worst
 
 
 def test_batch_fp64_vs_oracle(snapshots):

@@ -173,3 +173,21 @@ def test_particles_on_face_planes():
         out = gpu_map(g, p, h, prec)
         assert np.array_equal(out["idx"], ref["idx"])
         assert rel_err(out["mass"], ref["mass"]).max() < TOL[prec][0]
+
+
+def test_few_large_cells():
+    """Many particles per cell (64 here): the pair list comes from the
+    warp-per-cell walk and cells span several work items; lists bit-equal,
+    masses within the gates."""
+    lat = synth.lattice_particles(4, jitter=0.3, seed=7)
+    g = synth.voronoi(lat.pos())
+    p = synth.uniform_particles(4096, synth.BASE_SEED + 7)
+    h, _ = oracle_h(p)
+    ref = oracle.map_cells(g, p.x, p.y, p.z, p.m, h)
+    assert np.diff(ref["off"]).max() > 256  # some cells overflow the 256-pair row
+    for prec in (0, 1):
+        out = gpu_map(g, p, h, prec)
+        assert np.array_equal(out["off"], ref["off"])
+        assert np.array_equal(out["idx"], ref["idx"])
+        assert rel_err(out["mass"], ref["mass"]).max() < TOL[prec][0]
+        assert abs(out["total"] - ref["mass"].sum()) < TOL[prec][1] * ref["mass"].sum()
