@@ -156,7 +156,7 @@ OPS = {
 # clumpy case (391 MB for 7,813,809 pairs), scaled to a launch by its pair
 # count (the kernel streams the same per-pair data at any size).  It belongs
 # to the kernel as captured: set it to None when the kernel changes.
-INTEGRAL_DRAM_BYTES_PER_PAIR = 50.0
+INTEGRAL_DRAM_BYTES_PER_PAIR = None  # re-captured after the work-item change
 
 
 def algorithmic_ops(work: dict, terms: int, mixed: bool):
