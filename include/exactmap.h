@@ -51,6 +51,11 @@ typedef struct {
                                         map_particles_to_cells) times the pair-integral kernel's launch
                                         shapes and keeps the fastest; default 0 */
   unsigned long long queue_timeout_ns; /* bound on any device-side wait; default 2e9 */
+  int count_work;                    /* 1: the pair-integral kernel also tallies its work (map_get_work,
+                                        map_stats.n_edge_terms / n_fp64_terms), in a separate compilation
+                                        of one launch shape that keeps the tally in registers (slower, and
+                                        its FP32 rounding may differ within the mixed build's tolerance);
+                                        0: those counts read 0; default 0 */
 } map_config;
 
 /* Fill *cfg with the defaults listed above. */
@@ -102,8 +107,8 @@ typedef struct {
 /* Statistics of the last mapping call on a context. */
 typedef struct {
   int64_t n_pairs;      /* listed particle-cell pairs (one pair integral each) */
-  int64_t n_edge_terms; /* edge integrals evaluated (two vertex pyramids each) */
-  int64_t n_fp64_terms; /* edge integrals evaluated in FP64 in the mixed build */
+  int64_t n_edge_terms; /* edge integrals evaluated (two vertex pyramids each); count_work only */
+  int64_t n_fp64_terms; /* edge integrals evaluated in FP64 in the mixed build; count_work only */
   double total_mass;    /* sum_i M_i */
   int status;           /* device-side status word (MAP_OK or a MAP_E* code) */
 } map_stats;
@@ -177,7 +182,8 @@ int map_get_stats(map_ctx* ctx, map_stats* stats);
  * [2] inner-piece antiderivative evaluations, [3] middle-piece intervals,
  * [4] beyond-the-support intervals, [5] middle intervals of the mixed build
  * split at the foot (a second Gauss-Legendre panel); all per pair, summed.
- * *launches: kernels this context has launched so far (its own kernels;
+ * The counts are tallied only by a context created with count_work = 1
+ * (zeros otherwise).  *launches: kernels this context has launched so far (its own kernels;
  * library sort/scan primitives not counted).  These feed the algorithmic
  * operation count of the roofline. */
 int map_get_work(map_ctx* ctx, int64_t* counts, int64_t* launches);

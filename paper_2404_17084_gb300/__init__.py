@@ -44,7 +44,7 @@ class map_config(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int), ("device", ctypes.c_int), ("hbm_budget", ctypes.c_size_t),
                 ("theta", ctypes.c_double), ("hfact", ctypes.c_double), ("leaf_size", ctypes.c_int),
                 ("ngb_bruteforce_max", ctypes.c_int), ("autotune", ctypes.c_int),
-                ("queue_timeout_ns", ctypes.c_ulonglong)]
+                ("queue_timeout_ns", ctypes.c_ulonglong), ("count_work", ctypes.c_int)]
 
 
 class map_particles(ctypes.Structure):

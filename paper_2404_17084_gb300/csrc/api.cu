@@ -74,6 +74,7 @@ void map_config_default(map_config* cfg) {
   cfg->ngb_bruteforce_max = 10000;
   cfg->autotune = 0;
   cfg->queue_timeout_ns = 2000000000ULL;
+  cfg->count_work = 0;
 }
 
 const char* map_strerror(int code) {

@@ -73,27 +73,33 @@ __device__ __forceinline__ void load_edge(const double* E, double& e0, double& e
   e0 = a.x; e1 = a.y; e2 = b.x; e3 = b.y; e4 = c.x; e5 = c.y; e6 = d.x; e7 = d.y; e8 = f.x;
 }
 
-// Per-warp piece stacks (inner, middle) and the lanes' compensated
-// accumulators.
+// Per-warp piece stacks (inner, middle) and the results' accumulators.
+//
+// FP32: col[o][l] sums the pieces of owner lane o that lane l evaluated, so
+// that in a drain every lane adds into its own column (bank l, no conflicts
+// and no ordering between lanes); after the last drain of a block each owner
+// adds up its row (compensated) and clears it.  Every cell sees its own
+// lane's pieces in program order, so the result is bit-reproducible.
+// FP64: one accumulator per owner, lanes with the same owner adding in turn.
 template <typename T>
 struct WarpStacks {
   // FP32 adds the pieces beyond the support in the lane itself (one atan2
   // per edge); FP64, where an atan2 costs far more than the stacking, stacks
   // them as a third kind
   static constexpr int NK = sizeof(T) == 4 ? 2 : 3;
+  static constexpr bool COL = sizeof(T) == 4;
   typename Vec4<T>::type e[NK][LCAP];  // (r0, R0, lo, hi): inner, middle[, beyond]
   unsigned char own[NK][LCAP];         // owner lane
-  T acc[32];                          // per-owner sum of its pieces ...
-  T cmp[32];                          // ... and its compensation (Kahan)
-  SnapDesc d;                         // the snapshot of the warp's current cell
+  float col[COL ? 32 : 1][32];         // FP32: [owner][evaluating lane]
+  T acc[COL ? 1 : 32];                 // FP64: per-owner sum of its pieces
+  SnapDesc d;                          // the snapshot of the warp's current cell
 };
 
 // Evaluates the queued pieces: every stack holding 32 or more (all that is
 // left when flush), 32 at a time from the top, and adds each result to its
-// owner lane's accumulator.  Not inlined: the evaluators then appear once in
-// the kernel's code.
+// owner lane's accumulator.
 template <typename T, bool MIXED>
-__device__ __noinline__ void drain(WarpStacks<T>& S, int& cnt0, int& cnt1, int& cnt2, bool flush,
+__device__ __forceinline__ void drain(WarpStacks<T>& S, int& cnt0, int& cnt1, int& cnt2, bool flush,
                                    unsigned& t0, unsigned& t1, unsigned& t2) {
   const int lane = threadIdx.x & 31;
   for (;;) {
@@ -116,27 +122,39 @@ __device__ __noinline__ void drain(WarpStacks<T>& S, int& cnt0, int& cnt1, int& 
       else if (K == 0) v = wedge::piece_inner<T>(P.x, P.y, P.z, P.w);
       else if constexpr (WarpStacks<T>::NK == 3) v = -P.x * wedge::dphi(P.z, P.w, P.y);  // P.x = c0 (the push)
     }
-    // lanes holding pieces of the same owner add in turn, in lane order
-    const unsigned grp = __match_any_sync(FULL, o);
-    const int rank = __popc(grp & ((1u << lane) - 1u));
-    for (int r = 0;; ++r) {
-      const bool mine = on && rank == r;
-      if (!__any_sync(FULL, mine)) break;
-      if (mine) {
-        if (sizeof(T) == 4) {
-          // compensated (Kahan) addition: the error stays at a few ulp of the
-          // pair's total however many pieces of either sign it sums
-          const T y = v - S.cmp[o];
-          const T t = S.acc[o] + y;
-          S.cmp[o] = (t - S.acc[o]) - y;
-          S.acc[o] = t;
-        } else {
-          S.acc[o] += v;  // FP64: plain sums are ample
-        }
-      }
+    if constexpr (WarpStacks<T>::COL) {
+      if (on) S.col[o][lane] += v;  // this lane's column: no other lane touches it
       __syncwarp();
+    } else {
+      // lanes holding pieces of the same owner add in turn, in lane order
+      const unsigned grp = __match_any_sync(FULL, o);
+      const int rank = __popc(grp & ((1u << lane) - 1u));
+      for (int r = 0;; ++r) {
+        const bool mine = on && rank == r;
+        if (!__any_sync(FULL, mine)) break;
+        if (mine) S.acc[o] += v;  // FP64: plain sums are ample
+        __syncwarp();
+      }
     }
   }
+}
+
+// FP32: this lane's row of the column accumulators, summed with compensation
+// (Kahan) in a fixed order and cleared for the next block.  Lane o starts at
+// column o, so the 32 lanes read 32 different banks at every step.
+__device__ __forceinline__ float take_row(float (*col)[32], int o, float& comp) {
+  float s = 0.f, c = 0.f;
+#pragma unroll 8
+  for (int j = 0; j < 32; ++j) {
+    const int k = (j + o) & 31;
+    const float y = col[o][k] - c;
+    col[o][k] = 0.f;
+    const float t = s + y;
+    c = (t - s) - y;
+    s = t;
+  }
+  comp = c;
+  return s;
 }
 
 // Mixed build, a face whose plane passes within TAU of the particle: decide
@@ -164,7 +182,9 @@ __device__ __noinline__ double face_fp64(const SnapDesc& A, int64_t f, int64_t k
   return acc;
 }
 
-template <typename T, bool MIXED, int NW, int MINB>
+// COUNT: also tally the work (face tests, edge records, pieces) for the
+// operation count; a separate compilation, as the tally holds registers.
+template <typename T, bool MIXED, int NW, int MINB, bool COUNT>
 __global__ void __launch_bounds__(NW * 32, MINB) pair_integrals(BatchArgs B) {
   typedef typename Vec4<T>::type V4;
   __shared__ WarpStacks<T> stacks[NW];
@@ -178,6 +198,10 @@ __global__ void __launch_bounds__(NW * 32, MINB) pair_integrals(BatchArgs B) {
   int n64 = 0;
   unsigned n_split = 0;  // middle intervals split at the foot (counted once, evaluated as two pieces)
   int cur = -1;          // snapshot held in S.d
+  if constexpr (WarpStacks<T>::COL) {
+    for (int r = 0; r < 32; ++r) S.col[r][lane] = 0.f;
+    __syncwarp();
+  }
 
   for (;;) {
     int64_t g = 0;
@@ -232,8 +256,7 @@ __global__ void __launch_bounds__(NW * 32, MINB) pair_integrals(BatchArgs B) {
           hinv = hi;
         }
       }
-      S.acc[lane] = T(0);
-      S.cmp[lane] = T(0);
+      if constexpr (!WarpStacks<T>::COL) S.acc[lane] = T(0);
       bool inside = true;
       double dacc = 0.0;
       int cnt0 = 0, cnt1 = 0, cnt2 = 0;  // stack heights (warp-uniform)
@@ -248,11 +271,11 @@ __global__ void __launch_bounds__(NW * 32, MINB) pair_integrals(BatchArgs B) {
         if (!MIXED) r0 = r0 > T(EPS) ? r0 : T(EPS);
         bool inrange = active && r0 < T(2);
         const T c0f = wedge::c0_of(r0);
-        if (active) wc.faces++;
+        if (COUNT && active) wc.faces++;
         if (MIXED && inrange && r0 < T(TAU)) {
           int c64 = 0;
           dacc += face_fp64(A, f0 + fi, kb, ke, l0, a, A.site[3 * c], A.site[3 * c + 1], A.site[3 * c + 2], fin, c64);
-          n64 += c64;
+          if (COUNT) n64 += c64;
           inrange = false;  // its edges are done
         }
         inside = inside && fin;
@@ -270,7 +293,7 @@ __global__ void __launch_bounds__(NW * 32, MINB) pair_integrals(BatchArgs B) {
                 wedge::split_edge_flat<T>(r0, R0, e7 * hinv - base, e8 * hinv - base, fin == ein, inrange);
             const int nin = P.v & 1u, nmid = ((P.v >> 1) & 1u) + ((P.v >> 2) & 1u);
             const int nout = ((P.v >> 3) & 1u) + ((P.v >> 4) & 1u);
-            if (inrange) {
+            if (COUNT && inrange) {
               wc.edges++;
               if (P.v) wc.terms++;
               n_split += P.split;
@@ -312,7 +335,7 @@ __global__ void __launch_bounds__(NW * 32, MINB) pair_integrals(BatchArgs B) {
               const T t = osum + y;
               ocmp = (t - osum) - y;
               osum = t;
-              n_out += nout;
+              if (COUNT) n_out += nout;
             }
             cnt0 += t0;
             cnt1 += t1;
@@ -328,9 +351,16 @@ __global__ void __launch_bounds__(NW * 32, MINB) pair_integrals(BatchArgs B) {
       // flush what is left (fewer than 32 of each kind)
       if (cnt0 || cnt1 || cnt2) drain<T, MIXED>(S, cnt0, cnt1, cnt2, true, n_in, n_mid, n_out_st);
       __syncwarp();
+      double pieces;
+      if constexpr (WarpStacks<T>::COL) {
+        float comp;
+        const float s = take_row(S.col, lane, comp);
+        pieces = (double)s - (double)comp;
+      } else {
+        pieces = (double)S.acc[lane];
+      }
       if (active) {
-        const double f = (inside ? 1.0 : 0.0) + dacc + ((double)S.acc[lane] - (double)S.cmp[lane]) +
-                         ((double)osum - (double)ocmp);
+        const double f = (inside ? 1.0 : 0.0) + dacc + pieces + ((double)osum - (double)ocmp);
         if (A.frac) A.frac[p] = f;
         macc += A.m[a] * f;
       }
@@ -340,6 +370,7 @@ __global__ void __launch_bounds__(NW * 32, MINB) pair_integrals(BatchArgs B) {
     if (lane == 0) A.partial[it] = macc;  // summed per cell by cell_sums
     __syncwarp();
   }
+  if (!COUNT) return;
   // work tally: warp sums, one atomic per warp and counter
   auto wsum = [](unsigned long long v) {
     for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(FULL, v, o);
@@ -361,9 +392,9 @@ __global__ void __launch_bounds__(NW * 32, MINB) pair_integrals(BatchArgs B) {
   }
 }
 
-template <typename T, bool MIXED, int NW, int MINB>
+template <typename T, bool MIXED, int NW, int MINB, bool COUNT = false>
 int launch(map_ctx* ctx, const BatchArgs& B, cudaStream_t s) {
-  auto kern = pair_integrals<T, MIXED, NW, MINB>;
+  auto kern = pair_integrals<T, MIXED, NW, MINB, COUNT>;
   int per_sm = 0;
   CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, NW * 32, 0));
   if (per_sm < 1) per_sm = 1;
@@ -453,12 +484,17 @@ int integrals_upload(map_ctx* ctx, const SnapDesc* h_desc, const int64_t* h_ibas
 int integrals_enqueue(map_ctx* ctx, const BatchArgs& B, int variant, cudaStream_t s) {
   CUDA_TRY(cudaMemsetAsync(ctx->d_counters, 0, 4 * sizeof(unsigned long long), s));
   CUDA_TRY(cudaMemsetAsync(ctx->d_counters + 8, 0, 8 * sizeof(unsigned long long), s));
-  if (ctx->cfg.precision == MAP_MIXED) {
+  const bool count = ctx->cfg.count_work != 0;
+  if (ctx->cfg.precision == MAP_MIXED && count) {
+    MAP_TRY((launch<float, true, 4, 5, true>(ctx, B, s)));
+  } else if (ctx->cfg.precision == MAP_MIXED) {
     switch (variant) {
       case 1: MAP_TRY((launch<float, true, 4, 4>(ctx, B, s))); break;
       case 2: MAP_TRY((launch<float, true, 4, 6>(ctx, B, s))); break;
       default: MAP_TRY((launch<float, true, 4, 5>(ctx, B, s))); break;
     }
+  } else if (count) {
+    MAP_TRY((launch<double, false, 4, 4, true>(ctx, B, s)));
   } else {
     MAP_TRY((launch<double, false, 4, 4>(ctx, B, s)));
   }

@@ -59,6 +59,31 @@ def test_uniform4096_mass_conservation(uniform4096):
     assert np.max(np.abs(tot[interior] - 1)) < 1e-6
 
 
+@pytest.mark.parametrize("precision", [0, 1])
+def test_count_work(uniform4096, precision):
+    """count_work = 1 runs the counting compilation of the integral kernel:
+    its tally is positive (zeros without it) and both compilations meet the
+    build's gate against the oracle and agree with each other."""
+    p, g, h, _, ref = uniform4096
+    L = lib()
+    res = {}
+    for cw in (0, 1):
+        ctx = L.map_init(L.map_config_default(precision=precision, count_work=cw))
+        try:
+            out = gpu_map(g, p, h, precision, ctx=ctx)
+            work, _ = L.map_get_work(ctx)
+        finally:
+            L.map_destroy(ctx)
+        assert out["status"] == 0
+        assert rel_err(out["mass"], ref["mass"]).max() < TOL[precision][0]
+        res[cw] = (out, work)
+    assert res[0][0]["terms"] == 0 and all(v == 0 for v in res[0][1].values())
+    w, terms = res[1][1], res[1][0]["terms"]
+    assert w["face_tests"] > 0 and 0 < terms <= w["edge_records"]
+    assert w["mid_intervals"] > 0 and w["outer_intervals"] > 0
+    assert rel_err(res[1][0]["mass"], res[0][0]["mass"]).max() < (1e-12 if precision == 0 else 1e-6)
+
+
 @pytest.mark.parametrize("precision,tol", [(0, 1e-9), (1, 1e-6)])
 def test_solve_h_uniform4096(uniform4096, precision, tol):
     """FP64 build: Newton to 1e-10 in FP64 sums.  Mixed build: FP32 sums on
