@@ -231,6 +231,7 @@ __global__ void __launch_bounds__(NW * 32, MINB) pair_integrals(BatchArgs B) {
     const int nf = (int)(A.cfo[c + 1] - f0);
     const int64_t l0 = A.fvo[f0];
     const T* __restrict__ ecell = edge + l0 * EDGE_STRIDE;
+    const int nedge = (int)(A.fvo[f0 + nf] - l0);
     double macc = 0.0;
     const int64_t pb = item.lo, pe = item.lo + item.cnt;
     for (int64_t p0 = pb; p0 < pe; p0 += 32) {
@@ -262,6 +263,8 @@ __global__ void __launch_bounds__(NW * 32, MINB) pair_integrals(BatchArgs B) {
       int cnt0 = 0, cnt1 = 0, cnt2 = 0;  // stack heights (warp-uniform)
       T osum = T(0), ocmp = T(0);  // this lane's beyond-support terms (compensated)
       int kb = 0;
+      int pk = -1;  // index of the edge record held in n0..n8
+      T n0, n1, n2, n3, n4, n5, n6, n7, n8;
       for (int fi = 0; fi < nf; ++fi) {
         const V4 F = face[f0 + fi];
         const int ke = (int)(A.fvo[f0 + fi + 1] - l0);
@@ -280,9 +283,12 @@ __global__ void __launch_bounds__(NW * 32, MINB) pair_integrals(BatchArgs B) {
         }
         inside = inside && fin;
         if (__any_sync(FULL, inrange)) {
+          if (pk != kb) load_edge(ecell + kb * EDGE_STRIDE, n0, n1, n2, n3, n4, n5, n6, n7, n8);
           for (int k = kb; k < ke; ++k) {
-            T e0, e1, e2, e3, e4, e5, e6, e7, e8;
-            load_edge(ecell + k * EDGE_STRIDE, e0, e1, e2, e3, e4, e5, e6, e7, e8);
+            const T e0 = n0, e1 = n1, e2 = n2, e3 = n3, e4 = n4, e5 = n5, e6 = n6, e7 = n7, e8 = n8;
+            // the next record (of this face or the next) loads while this one is used
+            pk = k + 1;
+            if (pk < nedge) load_edge(ecell + pk * EDGE_STRIDE, n0, n1, n2, n3, n4, n5, n6, n7, n8);
             // R0 = m.(p - v_a) (> 0 inside), along-edge vertex positions
             const T R0s = (e0 * yx + e1 * yy + e2 * yz) - e3 * hinv;
             const T base = e4 * yx + e5 * yy + e6 * yz;
