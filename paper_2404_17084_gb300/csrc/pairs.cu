@@ -84,21 +84,31 @@ __device__ __forceinline__ bool pair_rule(const PairGrid& G, const PairTree& T, 
 // One warp walks the octree for 32 cells that are consecutive in Morton order
 // of their sites (so close together), sharing the node loads: every lane
 // tests each visited node against its own cell (FP32, outward-rounded box,
-// 1e-6 absolute margin: 2 * largest h + cell radius), the warp descends when
-// any lane needs the node, and at a leaf only the lanes that reach it test
-// its particles with the pair rule.
+// 1e-6 absolute margin: 2 * largest h + cell radius) and the warp descends
+// when any lane needs the node.  At a leaf, the (cell, particle) tests of the
+// lanes that reach it are spread over all 32 lanes -- each lane's cell data
+// sit in shared memory -- and every hit is appended to its cell's list
+// (lanes with the same cell take consecutive places, in lane order).
 // FILL = false: count pairs per cell, keeping the first PAIR_ROW of them in
 // the cell's row of `out` (ncell x PAIR_ROW); FILL = true: write the pairs at
 // off[c] (the cells of `order` whose count exceeded the row; their number is
 // read from *n_dev).
 constexpr int PAIR_ROW = 256;
 
+struct WalkCells {  // per warp: the 32 lanes' cells, one entry per lane
+  float hx[32], lx[32], hy[32], ly[32], hz[32], lz[32], R[32];
+  int64_t c[32], w[32], cnt[32];
+  int32_t need[32];  // the lanes that reach the current leaf, in lane order
+};
+
 template <bool FILL>
 __global__ void __launch_bounds__(128) pair_traverse(int64_t ncell, const int32_t* __restrict__ order, PairTree T,
                                                      PairGrid G, int64_t* count, const int64_t* __restrict__ off,
                                                      int32_t* out, const unsigned long long* n_dev) {
   __shared__ int32_t s_stack[4][200];
+  __shared__ WalkCells s_cells[4];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const unsigned lt = (1u << lane) - 1u;
   const int64_t t = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x);
   const bool valid = t < (n_dev ? (int64_t)*n_dev : ncell);
   if (__all_sync(0xffffffffu, !valid)) return;
@@ -106,13 +116,14 @@ __global__ void __launch_bounds__(128) pair_traverse(int64_t ncell, const int32_
   double sx = 0, sy = 0, sz = 0, R = 0;
   if (valid) { sx = G.site[3 * c]; sy = G.site[3 * c + 1]; sz = G.site[3 * c + 2]; R = G.rad[c]; }
   const float fsx = (float)sx, fsy = (float)sy, fsz = (float)sz, fR = (float)R;
-  SiteSplit SS;
-  SS.hx = fsx; SS.lx = (float)(sx - (double)fsx);
-  SS.hy = fsy; SS.ly = (float)(sy - (double)fsy);
-  SS.hz = fsz; SS.lz = (float)(sz - (double)fsz);
-  SS.R = fR;
-  int64_t w = valid ? (FILL ? off[c] : c * PAIR_ROW) : 0;
-  int64_t cnt = 0;
+  WalkCells& W = s_cells[warp];
+  W.hx[lane] = fsx; W.lx[lane] = (float)(sx - (double)fsx);
+  W.hy[lane] = fsy; W.ly[lane] = (float)(sy - (double)fsy);
+  W.hz[lane] = fsz; W.lz[lane] = (float)(sz - (double)fsz);
+  W.R[lane] = fR;
+  W.c[lane] = c;
+  W.w[lane] = valid ? (FILL ? off[c] : c * PAIR_ROW) : 0;
+  W.cnt[lane] = 0;
   int32_t* stack = s_stack[warp];
   int sp = 1;
   if (lane == 0) stack[0] = 0;
@@ -126,13 +137,43 @@ __global__ void __launch_bounds__(128) pair_traverse(int64_t ncell, const int32_
     const float dz = fsz < b[2] ? b[2] - fsz : (fsz > b[5] ? fsz - b[5] : 0.f);
     const float reach = (2.f * b[6] + fR + 1e-6f) * 1.000001f;
     const bool need = valid && dx * dx + dy * dy + dz * dz <= reach * reach;
-    if (!__any_sync(0xffffffffu, need)) continue;
+    const unsigned mneed = __ballot_sync(0xffffffffu, need);
+    if (!mneed) continue;
     if (T.nch[nd] == 0) {
-      if (need) {
-        for (int64_t k = T.nb[nd]; k < T.ne[nd]; ++k) {
-          if (pair_rule(G, T, c, SS, k)) {
-            if (FILL || cnt < PAIR_ROW) out[w++] = T.idx[k];
-            ++cnt;
+      const int64_t k0 = T.nb[nd];
+      const int nl = (int)(T.ne[nd] - k0);
+      const int nn = __popc(mneed);
+      if (need) W.need[__popc(mneed & lt)] = lane;
+      __syncwarp();
+      // tests (needing cell i, particle j): chunks of up to 32 particles, g
+      // cells per round, lane -> (i = r + lane / chunk, j = p + lane % chunk)
+      const int chunk = nl < 32 ? nl : 32;
+      const int g = chunk > 0 ? 32 / chunk : 1;
+      const int li = chunk > 0 ? lane / chunk : 0, lj = chunk > 0 ? lane - li * chunk : 0;
+      for (int p = 0; p < nl; p += chunk) {
+        for (int r = 0; r < nn; r += g) {
+          const int i = r + li, j = p + lj;
+          const bool on = li < g && i < nn && j < nl;
+          const int l = on ? W.need[i] : 0;
+          bool hit = false;
+          if (on) {
+            SiteSplit SS;
+            SS.hx = W.hx[l]; SS.lx = W.lx[l];
+            SS.hy = W.hy[l]; SS.ly = W.ly[l];
+            SS.hz = W.hz[l]; SS.lz = W.lz[l];
+            SS.R = W.R[l];
+            hit = pair_rule(G, T, W.c[l], SS, k0 + j);
+          }
+          if (__any_sync(0xffffffffu, hit)) {
+            const unsigned grp = __match_any_sync(0xffffffffu, hit ? l : 32 + lane);
+            int64_t q = 0;
+            if (hit) {
+              q = W.cnt[l] + __popc(grp & lt);
+              if (FILL || q < PAIR_ROW) out[W.w[l] + q] = T.idx[k0 + j];
+            }
+            __syncwarp();
+            if (hit && (grp & lt) == 0) W.cnt[l] += __popc(grp);
+            __syncwarp();
           }
         }
       }
@@ -144,7 +185,7 @@ __global__ void __launch_bounds__(128) pair_traverse(int64_t ncell, const int32_
       __syncwarp();
     }
   }
-  if (!FILL && valid) count[c] = cnt;
+  if (!FILL && valid) count[c] = W.cnt[lane];
 }
 
 // The same walk with one warp per cell, for grids with many particles per
