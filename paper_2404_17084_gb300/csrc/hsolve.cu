@@ -28,7 +28,7 @@ namespace {
 
 constexpr int HS_WARPS = 4;     // warps per block
 constexpr int HS_RNG = 384;     // particle ranges held per warp
-constexpr int HS_CAP = 2048;    // candidate positions held per warp
+constexpr int HS_CAP = 1024;    // candidate positions held per warp (a multiple of 32)
 // Depth-first stack: the tree has at most 22 levels and a popped node pushes at
 // most its 8 children, so at most 8 + 7 * 21 = 155 entries are live.
 constexpr int HS_STK = 160;
