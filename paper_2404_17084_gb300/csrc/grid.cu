@@ -1,8 +1,10 @@
 // Grid upload: copy the CSR grid into context memory and precompute, per cell,
 // the site-relative face planes and the per-edge records the pair-integral
 // kernels read (Section II-B's r0, R0 and phi are affine in the particle
-// position once these are known), plus the cell volume (divergence theorem)
-// and the cell radius R_i used by the pair rule.
+// position once these are known), a bounding sphere per face (centre
+// site-relative, radius rounded up: a face whose sphere lies beyond a
+// particle's support contributes nothing), plus the cell volume (divergence
+// theorem) and the cell radius R_i used by the pair rule.
 #include <cstring>
 
 #include "internal.cuh"
@@ -13,7 +15,7 @@ __global__ void prep_cells(int64_t ncell, const int64_t* __restrict__ cfo, const
                            const int32_t* __restrict__ fv, const double4_32a* __restrict__ plane,
                            const double* __restrict__ vx, const double* __restrict__ vy,
                            const double* __restrict__ vz, const double* __restrict__ site, double4_32a* face64,
-                           float4* face32, double* edge64, float* edge32, double* vol, double* rad,
+                           float4* face32, float4* fsph32, double* edge64, float* edge32, double* vol, double* rad,
                            int* maxf, int* maxl, unsigned long long* status) {
   int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (c >= ncell) return;
@@ -28,6 +30,24 @@ __global__ void prep_cells(int64_t ncell, const int64_t* __restrict__ cfo, const
     face32[f] = make_float4((float)P.x, (float)P.y, (float)P.z, (float)dr);
     const int64_t b = fvo[f], e = fvo[f + 1];
     const int64_t L = e - b;
+    {
+      // bounding sphere: centre at the vertex mean, radius the largest
+      // vertex distance, rounded up to FP32 with a relative margin
+      double cx = 0, cy = 0, cz = 0;
+      for (int64_t k = 0; k < L; ++k) {
+        const int32_t ia = fv[b + k];
+        cx += vx[ia] - sx; cy += vy[ia] - sy; cz += vz[ia] - sz;
+      }
+      cx /= (double)L; cy /= (double)L; cz /= (double)L;
+      double r2 = 0;
+      for (int64_t k = 0; k < L; ++k) {
+        const int32_t ia = fv[b + k];
+        const double dx = vx[ia] - sx - cx, dy = vy[ia] - sy - cy, dz = vz[ia] - sz - cz;
+        const double d2 = dx * dx + dy * dy + dz * dz;
+        r2 = d2 > r2 ? d2 : r2;
+      }
+      fsph32[f] = make_float4((float)cx, (float)cy, (float)cz, (float)(sqrt(r2) * (1.0 + 1e-5) + 1e-12));
+    }
     double ax = 0, ay = 0, az = 0;
     for (int64_t k = 0; k < L; ++k) {
       const int32_t ia = fv[b + k], ib = fv[b + (k + 1 == L ? 0 : k + 1)];
@@ -120,6 +140,7 @@ int grid_prepare(map_ctx* ctx, const map_grid* in, PreparedGrid* g, cudaStream_t
   MAP_TRY(ctx_alloc_grid(ctx, g, (void**)&g->face_plane, nf * sizeof(double4_32a)));
   MAP_TRY(ctx_alloc_grid(ctx, g, (void**)&g->face64, nf * sizeof(double4_32a)));
   MAP_TRY(ctx_alloc_grid(ctx, g, (void**)&g->face32, nf * sizeof(float4)));
+  MAP_TRY(ctx_alloc_grid(ctx, g, (void**)&g->fsph32, nf * sizeof(float4)));
   MAP_TRY(ctx_alloc_grid(ctx, g, (void**)&g->edge64, nl * EDGE_STRIDE * sizeof(double)));
   MAP_TRY(ctx_alloc_grid(ctx, g, (void**)&g->edge32, nl * EDGE_STRIDE * sizeof(float)));
   MAP_TRY(ctx_alloc_grid(ctx, g, (void**)&g->site, nc * 3 * sizeof(double)));
@@ -151,7 +172,7 @@ int grid_prepare(map_ctx* ctx, const map_grid* in, PreparedGrid* g, cudaStream_t
   const int tpb = 128;
   const int64_t blocks = (nc + tpb - 1) / tpb;
   prep_cells<<<(unsigned)blocks, tpb, 0, s>>>(nc, g->cell_face_off, g->face_vert_off, g->face_vert, g->face_plane,
-                                              g->vx, g->vy, g->vz, g->site, g->face64, g->face32, g->edge64,
+                                              g->vx, g->vy, g->vz, g->site, g->face64, g->face32, g->fsph32, g->edge64,
                                               g->edge32, g->vol, g->rad, d_small, d_small + 1, d_status); ++ctx->launches;
   CUDA_TRY(cudaGetLastError());
   int64_t hs[4] = {0, 0, 0, 0};
@@ -161,6 +182,8 @@ int grid_prepare(map_ctx* ctx, const map_grid* in, PreparedGrid* g, cudaStream_t
   std::memcpy(hi, hs, sizeof(hi));
   g->max_faces = hi[0];
   g->max_loops = hi[1];
+  // the mixed integral kernel packs a cell-relative loop index in 26 bits
+  if (g->max_loops >= (1 << 26)) return MAP_EINVAL;
   unsigned long long st;
   std::memcpy(&st, &hi[4], sizeof(st));
   if (st != 0) return MAP_EINVAL;

@@ -26,6 +26,11 @@
 // Per pair: f_ai = [inside] + sum_f sum_e s_f s_e K'_e (see wedge.cuh).
 // M_i = sum_a m_a f_ai is accumulated in FP64 and reduced across the warp;
 // rho_i = M_i / V_i.
+//
+// That is the FP64 build's kernel (pair_integrals).  The mixed build's kernel
+// (pair_integrals_mixed) adds a level of compaction between the face loop and
+// the edges: only a lane whose face can reach its support queues the face's
+// edges, as (pair, edge) records that the warp then splits 32 at a time.
 #include <cub/cub.cuh>
 
 #include "internal.cuh"
@@ -398,6 +403,247 @@ __global__ void __launch_bounds__(NW * 32, MINB) pair_integrals(BatchArgs B) {
   }
 }
 
+// ---------------------------------------------------------------- mixed build
+// The mixed build compacts the work twice.  The face loop runs with one pair
+// per lane; a lane whose face is within its support -- plane within 2h and
+// face bounding sphere not wholly beyond 2h (such a face contributes nothing:
+// every point of it lies beyond the support, so the particle's projection is
+// outside the polygon and the angles of its edges cancel) -- pushes one
+// (pair, edge) record per edge of the face on a per-warp stack.  Every 32
+// records the warp splits those 32 edges, one per lane, and pushes their
+// inner and middle pieces on the piece stacks as before; the beyond-support
+// part is evaluated in the lane.  All results go to the owner pair's row of
+// the column accumulators.
+constexpr int CCAP = 64;  // (pair, edge) records: < 32 left + up to 32 pushed per edge
+
+struct MixWarp {
+  WarpStacks<float> st;  // piece stacks, column accumulators, snapshot
+  uint4 cmb[CCAP];       // (r0 bits, c0 bits, edge << 6 | fin << 5 | owner, 0)
+  float4 py[32];         // per pair: y (site-relative, in units of h), 1/h
+};
+
+// Splits the n (<= 32) records on top of the record stack, one per lane.
+template <bool COUNT>
+__device__ __forceinline__ void edge_round(MixWarp& M, const float* __restrict__ ecell, int base, int n, int& cnt0,
+                                           int& cnt1, unsigned& n_in, unsigned& n_mid, wedge::WorkCount& wc,
+                                           unsigned& n_split, unsigned& n_out) {
+  WarpStacks<float>& S = M.st;
+  const int lane = threadIdx.x & 31;
+  __syncwarp();
+  const bool on = lane < n;
+  uint4 C = make_uint4(0u, 0u, 0u, 0u);
+  if (on) C = M.cmb[base + lane];
+  __syncwarp();  // the records are taken: new ones may overwrite them
+  const int o = (int)(C.z & 31u);
+  const bool fin = (C.z >> 5) & 1u;
+  const float r0 = __uint_as_float(C.x), c0f = __uint_as_float(C.y);
+  const float4 Y = M.py[o];
+  float e0 = 0.f, e1 = 0.f, e2 = 0.f, e3 = 0.f, e4 = 0.f, e5 = 0.f, e6 = 0.f, e7 = 0.f, e8 = 0.f;
+  if (on) load_edge(ecell + (size_t)(C.z >> 6) * EDGE_STRIDE, e0, e1, e2, e3, e4, e5, e6, e7, e8);
+  const float R0s = (e0 * Y.x + e1 * Y.y + e2 * Y.z) - e3 * Y.w;
+  const float bse = e4 * Y.x + e5 * Y.y + e6 * Y.z;
+  const bool ein = R0s >= 0.f;
+  const float R0 = fabsf(R0s);
+  const wedge::EdgeSplit<float> P =
+      wedge::split_edge_flat<float>(r0, R0, e7 * Y.w - bse, e8 * Y.w - bse, fin == ein, on);
+  const int nin = P.v & 1u, nmid = ((P.v >> 1) & 1u) + ((P.v >> 2) & 1u);
+  if (COUNT && on) {
+    wc.edges++;
+    if (P.v) wc.terms++;
+    n_split += P.split;
+    n_out += ((P.v >> 3) & 1u) + ((P.v >> 4) & 1u);
+  }
+  int t0, t1;
+  const int o0 = cnt0 + warp_excl2(nin, &t0);
+  const int o1 = cnt1 + warp_excl2(nmid, &t1);
+  const unsigned char ow = (unsigned char)o;
+  float lo, hi;
+  if (P.v & 1u) { P.get(0, lo, hi); S.e[0][o0] = float4{r0, R0, lo, hi}; S.own[0][o0] = ow; }
+  if (P.v & 2u) { P.get(1, lo, hi); S.e[1][o1] = float4{r0, R0, lo, hi}; S.own[1][o1] = ow; }
+  if (P.v & 4u) {
+    const int q = o1 + ((P.v >> 1) & 1u);
+    P.get(2, lo, hi); S.e[1][q] = float4{r0, R0, lo, hi}; S.own[1][q] = ow;
+  }
+  // beyond the support: -c0 (dPhi_left + dPhi_right) as the argument of the
+  // product of the two intervals' numbers (R0^2 + lo hi) + i (hi - lo) R0
+  {
+    float l3, h3, l4, h4;
+    P.get(3, l3, h3);
+    P.get(4, l4, h4);
+    const bool v3 = P.v & 8u, v4 = P.v & 16u;
+    const float R02 = R0 * R0;
+    const float ar = v3 ? R02 + l3 * h3 : 1.f, ai = v3 ? (h3 - l3) * R0 : 0.f;
+    const float br = v4 ? R02 + l4 * h4 : 1.f, bi = v4 ? (h4 - l4) * R0 : 0.f;
+    const float re = ar * br - ai * bi, im = ar * bi + ai * br;
+    if (on) S.col[o][lane] += -c0f * wedge::xatan2(im, re);
+  }
+  cnt0 += t0;
+  cnt1 += t1;
+  __syncwarp();
+  if (cnt0 >= 32 || cnt1 >= 32) {
+    int cnt2 = 0;
+    unsigned n_st = 0;
+    drain<float, true>(S, cnt0, cnt1, cnt2, false, n_in, n_mid, n_st);
+  }
+}
+
+template <int NW, int MINB, bool COUNT>
+__global__ void __launch_bounds__(NW * 32, MINB) pair_integrals_mixed(BatchArgs B) {
+  __shared__ MixWarp mw[NW];
+  const int lane = threadIdx.x & 31;
+  const unsigned lt = (1u << lane) - 1u;
+  MixWarp& M = mw[threadIdx.x >> 5];
+  WarpStacks<float>& S = M.st;
+  const SnapDesc& A = S.d;
+  wedge::WorkCount wc;
+  unsigned n_in = 0, n_mid = 0, n_split = 0, n_out = 0;
+  int n64 = 0;
+  int cur = -1;
+  for (int r = 0; r < 32; ++r) S.col[r][lane] = 0.f;
+  __syncwarp();
+
+  for (;;) {
+    int64_t g = 0;
+    if (lane == 0) g = (int64_t)atomicAdd(&B.counters[3], 1ULL);
+    g = __shfl_sync(FULL, g, 0);
+    if (g >= B.total) break;
+    int jl = 0, jh = B.nsnap - 1;
+    while (jl < jh) {
+      const int jm = (jl + jh + 1) >> 1;
+      if (B.item_base[jm] <= g) jl = jm; else jh = jm - 1;
+    }
+    if (jl != cur) {
+      __syncwarp();
+      const unsigned long long* src = reinterpret_cast<const unsigned long long*>(B.snaps + jl);
+      unsigned long long* dst = reinterpret_cast<unsigned long long*>(&S.d);
+      for (int i = lane; i < (int)(sizeof(SnapDesc) / 8); i += 32) dst[i] = src[i];
+      __syncwarp();
+      cur = jl;
+    }
+    const int64_t it = g - B.item_base[jl];
+    const PairItem item = A.items[it];
+    const int64_t c = item.cell;
+    const float4* __restrict__ face = reinterpret_cast<const float4*>(A.face);
+    const float4* __restrict__ fsph = A.fsph;
+    const int64_t f0 = A.cfo[c];
+    const int nf = (int)(A.cfo[c + 1] - f0);
+    const int64_t l0 = A.fvo[f0];
+    const float* __restrict__ ecell = reinterpret_cast<const float*>(A.edge) + l0 * EDGE_STRIDE;
+    const double sx = A.site[3 * c], sy = A.site[3 * c + 1], sz = A.site[3 * c + 2];
+    double macc = 0.0;
+    const int64_t pb = item.lo, pe = item.lo + item.cnt;
+    for (int64_t p0 = pb; p0 < pe; p0 += 32) {
+      const int64_t p = p0 + lane;
+      const bool active = p < pe;
+      float yx = 0.f, yy = 0.f, yz = 0.f, hinv = 0.f;
+      int32_t a = 0;
+      if (active) {
+        a = A.pair_idx[p];
+        hinv = 1.0f / (float)A.h[a];
+        yx = (float)(A.x[a] - sx) * hinv;
+        yy = (float)(A.y[a] - sy) * hinv;
+        yz = (float)(A.z[a] - sz) * hinv;
+      }
+      M.py[lane] = make_float4(yx, yy, yz, hinv);
+      bool inside = true;
+      double dacc = 0.0;
+      int cntc = 0, cnt0 = 0, cnt1 = 0;  // stack heights (warp-uniform)
+      __syncwarp();
+      int kb = 0;
+      for (int fi = 0; fi < nf; ++fi) {
+        const float4 F = face[f0 + fi];
+        const int ke = (int)(A.fvo[f0 + fi + 1] - l0);
+        const float r0s = F.w * hinv - (F.x * yx + F.y * yy + F.z * yz);
+        bool fin = r0s >= 0.f;
+        const float r0 = fabsf(r0s);
+        bool inrange = active && r0 < 2.f;
+        if (COUNT && active) wc.faces++;
+        if (inrange && r0 < TAU) {
+          int c64 = 0;
+          dacc += face_fp64(A, f0 + fi, kb, ke, l0, a, sx, sy, sz, fin, c64);
+          if (COUNT) n64 += c64;
+          inrange = false;  // its edges are done
+        }
+        inside = inside && fin;
+        if (inrange) {
+          // the face's bounding sphere wholly beyond the support: nothing to add
+          const float4 Q = fsph[f0 + fi];
+          const float dx = yx - Q.x * hinv, dy = yy - Q.y * hinv, dz = yz - Q.z * hinv;
+          const float rr = 2.f + Q.w * hinv;
+          if (dx * dx + dy * dy + dz * dz >= rr * rr * 1.00001f) inrange = false;
+        }
+        const unsigned mn = __ballot_sync(FULL, inrange);
+        if (mn) {
+          const int nn = __popc(mn), rank = __popc(mn & lt);
+          const float c0f = wedge::c0_of(r0);
+          const unsigned tag = (unsigned)lane | (fin ? 32u : 0u);
+          for (int k = kb; k < ke; ++k) {
+            if (inrange) M.cmb[cntc + rank] = make_uint4(__float_as_uint(r0), __float_as_uint(c0f), tag | ((unsigned)k << 6), 0u);
+            cntc += nn;
+            if (cntc >= 32) {
+              cntc -= 32;
+              edge_round<COUNT>(M, ecell, cntc, 32, cnt0, cnt1, n_in, n_mid, wc, n_split, n_out);
+            }
+          }
+        }
+        kb = ke;
+      }
+      // what is left: fewer than 32 records, then fewer than 32 pieces of each kind
+      if (cntc) edge_round<COUNT>(M, ecell, 0, cntc, cnt0, cnt1, n_in, n_mid, wc, n_split, n_out);
+      if (cnt0 || cnt1) {
+        int cnt2 = 0;
+        unsigned n_st = 0;
+        drain<float, true>(S, cnt0, cnt1, cnt2, true, n_in, n_mid, n_st);
+      }
+      __syncwarp();
+      float comp;
+      const float rs = take_row(S.col, lane, comp);
+      if (active) {
+        const double f = (inside ? 1.0 : 0.0) + dacc + ((double)rs - (double)comp);
+        if (A.frac) A.frac[p] = f;
+        macc += A.m[a] * f;
+      }
+      __syncwarp();
+    }
+    for (int o = 16; o > 0; o >>= 1) macc += __shfl_down_sync(FULL, macc, o);
+    if (lane == 0) A.partial[it] = macc;
+    __syncwarp();
+  }
+  if (!COUNT) return;
+  auto wsum = [](unsigned long long v) {
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(FULL, v, o);
+    return v;
+  };
+  const unsigned long long terms = wsum((unsigned long long)wc.terms), faces = wsum((unsigned long long)wc.faces);
+  const unsigned long long edges = wsum((unsigned long long)wc.edges), fp64 = wsum((unsigned long long)n64);
+  const unsigned long long split = wsum((unsigned long long)n_split);
+  const unsigned long long outs = wsum((unsigned long long)n_out);
+  if (lane == 0) {
+    atomicAdd(&B.counters[1], terms);
+    atomicAdd(&B.counters[2], fp64);
+    atomicAdd(&B.counters[8], faces);
+    atomicAdd(&B.counters[9], edges);
+    atomicAdd(&B.counters[10], 2ull * n_in);
+    atomicAdd(&B.counters[11], (unsigned long long)n_mid - split);
+    atomicAdd(&B.counters[12], outs);
+    atomicAdd(&B.counters[13], split);
+  }
+}
+
+template <int NW, int MINB, bool COUNT = false>
+int launch_mixed(map_ctx* ctx, const BatchArgs& B, cudaStream_t s) {
+  auto kern = pair_integrals_mixed<NW, MINB, COUNT>;
+  int per_sm = 0;
+  CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, NW * 32, 0));
+  if (per_sm < 1) per_sm = 1;
+  int64_t blocks = (int64_t)per_sm * ctx->sm_count;
+  const int64_t need = (B.total + NW - 1) / NW;
+  if (blocks > need) blocks = need > 0 ? need : 1;
+  kern<<<(unsigned)blocks, NW * 32, 0, s>>>(B); ++ctx->launches;
+  CUDA_TRY(cudaGetLastError());
+  return MAP_OK;
+}
+
 template <typename T, bool MIXED, int NW, int MINB, bool COUNT = false>
 int launch(map_ctx* ctx, const BatchArgs& B, cudaStream_t s) {
   auto kern = pair_integrals<T, MIXED, NW, MINB, COUNT>;
@@ -492,12 +738,12 @@ int integrals_enqueue(map_ctx* ctx, const BatchArgs& B, int variant, cudaStream_
   CUDA_TRY(cudaMemsetAsync(ctx->d_counters + 8, 0, 8 * sizeof(unsigned long long), s));
   const bool count = ctx->cfg.count_work != 0;
   if (ctx->cfg.precision == MAP_MIXED && count) {
-    MAP_TRY((launch<float, true, 4, 5, true>(ctx, B, s)));
+    MAP_TRY((launch_mixed<4, 5, true>(ctx, B, s)));
   } else if (ctx->cfg.precision == MAP_MIXED) {
     switch (variant) {
-      case 1: MAP_TRY((launch<float, true, 4, 4>(ctx, B, s))); break;
-      case 2: MAP_TRY((launch<float, true, 4, 6>(ctx, B, s))); break;
-      default: MAP_TRY((launch<float, true, 4, 5>(ctx, B, s))); break;
+      case 1: MAP_TRY((launch_mixed<4, 4>(ctx, B, s))); break;
+      case 2: MAP_TRY((launch_mixed<4, 6>(ctx, B, s))); break;
+      default: MAP_TRY((launch_mixed<4, 5>(ctx, B, s))); break;
     }
   } else if (count) {
     MAP_TRY((launch<double, false, 4, 4, true>(ctx, B, s)));
@@ -537,6 +783,7 @@ SnapDesc make_desc(map_ctx* ctx, const PreparedGrid* g, const map_particles* p, 
   d.edge = mixed ? (const void*)g->edge32 : (const void*)g->edge64;
   d.face64 = g->face64;
   d.edge64 = g->edge64;
+  d.fsph = g->fsph32;
   d.items = ctx->items;
   d.item_off = ctx->item_off;
   d.partial = ctx->partial;

@@ -36,6 +36,7 @@ struct PreparedGrid {
   double4_32a* face_plane = nullptr;     // absolute (nx,ny,nz,d) [nface]
   double4_32a* face64 = nullptr;         // site-relative (nx,ny,nz,d - n.s) [nface]
   float4* face32 = nullptr;          // same, FP32
+  float4* fsph32 = nullptr;          // per face: bounding-sphere centre (site-relative) and radius, FP32
   double* edge64 = nullptr;          // EDGE_STRIDE doubles per loop entry (site-relative)
   float* edge32 = nullptr;           // EDGE_STRIDE floats per loop entry
   double* site = nullptr;            // [3*ncell]
@@ -185,6 +186,7 @@ struct SnapDesc {
   const void* edge;    // EDGE_STRIDE floats or doubles per loop entry
   const double4_32a* face64;
   const double* edge64;
+  const float4* fsph;  // per face: bounding sphere (site-relative centre, radius), FP32
   int64_t orig;        // the caller's index of this snapshot
 };
 

@@ -61,7 +61,7 @@ double ms_between(std::chrono::steady_clock::time_point a, std::chrono::steady_c
 // two index arrays) and the per-cell outputs, with 25% headroom.
 size_t request_bytes(const map_request& r) {
   const double parts = 48.0 * r.n + 200.0 * r.n + 160.0 * 16.0 * r.n;
-  const double grid = 96.0 * r.ncell + 130.0 * r.nface + 160.0 * r.nloop + 48.0 * r.nvert;
+  const double grid = 96.0 * r.ncell + 146.0 * r.nface + 160.0 * r.nloop + 48.0 * r.nvert;
   const double outs = 24.0 * r.ncell;
   return (size_t)(1.25 * (parts + grid + outs)) + (64u << 20);
 }
