@@ -153,10 +153,11 @@ OPS = {
 
 # DRAM traffic of the mixed pair-integral kernel per pair:
 # dram__bytes_read.sum + dram__bytes_write.sum of one ncu capture of the 2^16
-# clumpy case (391 MB for 7,813,809 pairs), scaled to a launch by its pair
-# count (the kernel streams the same per-pair data at any size).  It belongs
-# to the kernel as captured: set it to None when the kernel changes.
-INTEGRAL_DRAM_BYTES_PER_PAIR = None  # re-captured after the work-item change
+# clumpy case (386 MB for 7,813,809 pairs, profiles/pair_integrals_mixed_clumpy_65536.md),
+# scaled to a launch by its pair count (the kernel streams the same per-pair
+# data at any size).  It belongs to the kernel as captured: set it to None
+# when the kernel changes.
+INTEGRAL_DRAM_BYTES_PER_PAIR = 49.4
 
 
 def counted_work(L, torch, precision, device, grids, dev, parts):
@@ -320,7 +321,7 @@ def run_ours(args):
                    "step": "solve_h + octree + pair list + pair integrals + cell sums"},
         "phases_ms": {k: round(v, 3) for k, v in phases.items()},
         "fp64": fp64,
-        "roofline": {"bound": "alu", "kernel": "pair_integrals<float,mixed>", "achieved": achieved / 1e12,
+        "roofline": {"bound": "alu", "kernel": "pair_integrals_mixed", "achieved": achieved / 1e12,
                      "peak": peak_ops / 1e12, "unit": "Tops/s (FP32 issue slots)", "frac": achieved / peak_ops,
                      "traffic": (None if INTEGRAL_DRAM_BYTES_PER_PAIR is None
                                  else INTEGRAL_DRAM_BYTES_PER_PAIR * n_pairs),
@@ -464,7 +465,7 @@ def run_batch(args):
                                           "4 warps/CTA, 6 CTAs/SM"]},
                   "one_call_per_snapshot_mapping_s": single_s, "batched_equals_single": bool(same),
                   "host_input_generation_s": gen_s},
-        "roofline": {"bound": "alu", "kernel": "pair_integrals<float,mixed> (batched launch)",
+        "roofline": {"bound": "alu", "kernel": "pair_integrals_mixed (batched launch)",
                      "achieved": achieved / 1e12, "peak": peak_ops / 1e12, "unit": "Tops/s (FP32 issue slots)",
                      "frac": achieved / peak_ops,
                      "traffic": (None if INTEGRAL_DRAM_BYTES_PER_PAIR is None
