@@ -434,6 +434,11 @@ def run_batch(args):
     torch.cuda.synchronize()
     single_s = time.perf_counter() - s0
     same = all(np.array_equal(a, b.cpu().numpy()) for a, b in zip(batch_mass, single_mass))
+    # the batch's grids take most of the GPU's memory (edge records of 1.1e7
+    # cells): release them before the counting context uploads its own copy
+    L.map_destroy(ctx)
+    del single_mass
+    torch.cuda.empty_cache()
     terms, work = counted_work(L, torch, L.MAP_MIXED, local, [g for _, g in snaps], dev, parts)
     f32, mufu = algorithmic_ops(work, terms, True)
     sm_count = torch.cuda.get_device_properties(dev).multi_processor_count
@@ -478,7 +483,6 @@ def run_batch(args):
                   **{k: int(v) for k, v in work.items()},
                   "counted_by": "one untimed map_batch of a count_work context on the same snapshots and h"},
     }
-    L.map_destroy(ctx)
     if world > 1:
         torch.distributed.barrier()
     emit(line, rank)
