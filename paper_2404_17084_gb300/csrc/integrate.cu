@@ -440,12 +440,16 @@ __device__ __forceinline__ void edge_round(MixWarp& M, const float* __restrict__
   const float4 Y = M.py[o];
   float e0 = 0.f, e1 = 0.f, e2 = 0.f, e3 = 0.f, e4 = 0.f, e5 = 0.f, e6 = 0.f, e7 = 0.f, e8 = 0.f;
   if (on) load_edge(ecell + (size_t)(C.z >> 6) * EDGE_STRIDE, e0, e1, e2, e3, e4, e5, e6, e7, e8);
-  const float R0s = (e0 * Y.x + e1 * Y.y + e2 * Y.z) - e3 * Y.w;
-  const float bse = e4 * Y.x + e5 * Y.y + e6 * Y.z;
+  // R0 = m.y - delta/h and the foot's along-edge position e.y, side by side
+  // in two-lane arithmetic, then the vertices' positions from the foot
+  using wedge::f2;
+  const f2 g = wedge::fma2(f2{e2, e6}, wedge::sp(Y.z),
+                           wedge::fma2(f2{e1, e5}, wedge::sp(Y.y), wedge::mul2(f2{e0, e4}, wedge::sp(Y.x))));
+  const float R0s = fmaf(-e3, Y.w, g.x);
   const bool ein = R0s >= 0.f;
   const float R0 = fabsf(R0s);
-  const wedge::EdgeSplit<float> P =
-      wedge::split_edge_flat<float>(r0, R0, e7 * Y.w - bse, e8 * Y.w - bse, fin == ein, on);
+  const f2 ab = wedge::fma2(f2{e7, e8}, wedge::sp(Y.w), wedge::sp(-g.y));
+  const wedge::EdgeSplit<float> P = wedge::split_edge_flat<float>(r0, R0, ab.x, ab.y, fin == ein, on);
   const int nin = P.v & 1u, nmid = ((P.v >> 1) & 1u) + ((P.v >> 2) & 1u);
   if (COUNT && on) {
     wc.edges++;
@@ -474,8 +478,8 @@ __device__ __forceinline__ void edge_round(MixWarp& M, const float* __restrict__
     const float R02 = R0 * R0;
     const float ar = v3 ? R02 + l3 * h3 : 1.f, ai = v3 ? (h3 - l3) * R0 : 0.f;
     const float br = v4 ? R02 + l4 * h4 : 1.f, bi = v4 ? (h4 - l4) * R0 : 0.f;
-    const float re = ar * br - ai * bi, im = ar * bi + ai * br;
-    if (on) S.col[o][lane] += -c0f * wedge::xatan2(im, re);
+    const f2 z = wedge::fma2(f2{-ai, ai}, f2{bi, br}, wedge::mul2(wedge::sp(ar), f2{br, bi}));
+    if (on) S.col[o][lane] += -c0f * wedge::xatan2(z.y, z.x);
   }
   cnt0 += t0;
   cnt1 += t1;

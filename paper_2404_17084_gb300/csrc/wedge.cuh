@@ -200,6 +200,66 @@ __device__ __forceinline__ T mid_gl(T r0, T R0, T c2, T lo, T hi) {
   return R0 * half * acc;
 }
 
+// FP32 pairs in one instruction (Blackwell's two-lane FP32 arithmetic,
+// round-to-nearest per lane, the same results as two scalar operations).
+struct f2 { float x, y; };
+__device__ __forceinline__ unsigned long long f2_bits(f2 a) {
+  return (unsigned long long)__float_as_uint(a.x) | ((unsigned long long)__float_as_uint(a.y) << 32);
+}
+__device__ __forceinline__ f2 f2_from(unsigned long long b) {
+  return f2{__uint_as_float((unsigned)b), __uint_as_float((unsigned)(b >> 32))};
+}
+__device__ __forceinline__ f2 fma2(f2 a, f2 b, f2 c) {
+  unsigned long long d;
+  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(f2_bits(a)), "l"(f2_bits(b)), "l"(f2_bits(c)));
+  return f2_from(d);
+}
+__device__ __forceinline__ f2 mul2(f2 a, f2 b) {
+  unsigned long long d;
+  asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(f2_bits(a)), "l"(f2_bits(b)));
+  return f2_from(d);
+}
+__device__ __forceinline__ f2 add2(f2 a, f2 b) {
+  unsigned long long d;
+  asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(f2_bits(a)), "l"(f2_bits(b)));
+  return f2_from(d);
+}
+__device__ __forceinline__ f2 sp(float v) { return f2{v, v}; }
+
+// The FP32 rule with the nodes +x_k and -x_k of each pair in one two-lane
+// operation: the same arithmetic per node as the scalar form above.
+template <>
+__device__ __forceinline__ float mid_gl<float>(float r0, float R0, float c2, float lo, float hi) {
+  const float gx[3] = {0.2386191860831969086305017f, 0.6612093864662645136613996f, 0.9324695142031520278123016f};
+  const float gw[3] = {0.4679139345726910473898703f, 0.3607615730481386075698335f, 0.1713244923791703450402961f};
+  const float pr0 = pmid(r0);
+  const float half = 0.5f * (hi - lo), ctr = 0.5f * (hi + lo);
+  const float R02 = R0 * R0;
+  f2 acc = sp(0.f);
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    const float hg = half * gx[k];
+    const f2 s = add2(sp(ctr), f2{hg, -hg});
+    const f2 s2 = mul2(s, s);
+    const f2 u2 = add2(sp(c2), s2);
+    // square root from the reciprocal square root and one Newton step
+    const f2 r = f2{rsqrtf(u2.x), rsqrtf(u2.y)};
+    const f2 y = mul2(u2, r);
+    const f2 e = fma2(f2{-y.x, -y.y}, y, u2);
+    const f2 U = fma2(mul2(sp(0.5f), r), e, y);
+    // p(U) = (2 - U)^5 (1 + U)
+    const f2 t = add2(sp(2.f), f2{-U.x, -U.y});
+    const f2 t2 = mul2(t, t);
+    const f2 t5 = mul2(mul2(t2, t2), t);
+    const f2 pm = mul2(t5, add2(sp(1.f), U));
+    const f2 num = fma2(sp(r0), pm, mul2(sp(-pr0), U));
+    const f2 den = mul2(U, add2(sp(R02), s2));
+    const f2 q = f2{den.x > 0.f ? __fdividef(num.x, den.x) : 0.f, den.y > 0.f ? __fdividef(num.y, den.y) : 0.f};
+    acc = fma2(sp(gw[k]), q, acc);
+  }
+  return R0 * half * (acc.x + acc.y);
+}
+
 // ------------------------------------------------------------------ piece evaluators
 // Each returns the contribution of one piece of K' over [lo, hi] (lo > hi
 // gives the negated value, which carries the sign s_f s_e).
@@ -278,8 +338,18 @@ __device__ __forceinline__ EdgeSplit<T> split_edge_flat(T r0, T R0, T aa, T ab, 
   const T c2 = r0 * r0 + R0 * R0;
   EdgeSplit<T> P;
   P.far = c2 >= T(4);
-  P.s2 = P.far ? T(0) : gl_sqrt(T(4) - c2);
-  P.s1 = c2 < T(1) ? gl_sqrt(T(1) - c2) : T(0);
+  if constexpr (sizeof(T) == 4) {
+    // both square roots in two-lane arithmetic (gl_sqrt's steps per lane)
+    const f2 xs = f2{4.f - c2, 1.f - c2};
+    const f2 r = f2{rsqrtf(xs.x), rsqrtf(xs.y)};
+    const f2 y = mul2(xs, r);
+    const f2 q = fma2(mul2(sp(0.5f), r), fma2(f2{-y.x, -y.y}, y, xs), y);
+    P.s2 = P.far ? T(0) : q.x;
+    P.s1 = c2 < T(1) ? q.y : T(0);
+  } else {
+    P.s2 = P.far ? T(0) : gl_sqrt(T(4) - c2);
+    P.s1 = c2 < T(1) ? gl_sqrt(T(1) - c2) : T(0);
+  }
   P.aa = aa;
   P.ab = ab;
   P.pos = pos;
