@@ -169,7 +169,9 @@ __device__ int walk_next(const HsTree& T, HsWarp& W, HsWalk& it, const float* q,
 }
 
 // Lane partial sums of w(q) and 3 w + q w'(q) over cand[0, cnt) for the
-// particle at sorted position k.
+// particle at sorted position k.  A lane takes positions lane, lane + 32, ...
+// in that order; two of them per pass, with the loads of both issued before
+// either term is added (the order of the additions is unchanged).
 template <bool F32>
 __device__ __forceinline__ void warp_accum(const HsTree& T, const HsWarp& W, int cnt, int64_t k, double h,
                                            float& s32, float& d32, double& s64, double& d64) {
@@ -178,39 +180,60 @@ __device__ __forceinline__ void warp_accum(const HsTree& T, const HsWarp& W, int
   const float hx = P0[0], lx = P0[1], hy = P0[2], ly = P0[3], hz = P0[4], lz = P0[5];
   const float inv_hf = 1.0f / (float)h;
   if (F32) {
-    for (int j = lane; j < cnt; j += 32) {
-      const float2* P = reinterpret_cast<const float2*>(T.split + 6 * (int64_t)W.cand[j]);
-      const float2 a = P[0], b = P[1], c = P[2];
+    auto term = [&](float2 a, float2 b, float2 c) {
       const float dx = ((a.x - hx) + (a.y - lx)) * inv_hf;
       const float dy = ((b.x - hy) + (b.y - ly)) * inv_hf;
       const float dz = ((c.x - hz) + (c.y - lz)) * inv_hf;
       const float q2 = dx * dx + dy * dy + dz * dz;
-      if (q2 >= 4.f) continue;
+      if (q2 >= 4.f) return;
       const float q = sqrtf(q2);
       float w, dwq;
       if (q < 1.f) { w = 1.f - 1.5f * q2 + 0.75f * q2 * q; dwq = -3.f * q2 + 2.25f * q2 * q; }
       else { const float t = 2.f - q; w = 0.25f * t * t * t; dwq = -0.75f * t * t * q; }
       s32 += w;
       d32 += 3.f * w + dwq;
+    };
+    int j = lane;
+    for (; j + 32 < cnt; j += 64) {
+      const float2* P = reinterpret_cast<const float2*>(T.split + 6 * (int64_t)W.cand[j]);
+      const float2* Q = reinterpret_cast<const float2*>(T.split + 6 * (int64_t)W.cand[j + 32]);
+      const float2 a = P[0], b = P[1], c = P[2], a1 = Q[0], b1 = Q[1], c1 = Q[2];
+      term(a, b, c);
+      term(a1, b1, c1);
+    }
+    if (j < cnt) {
+      const float2* P = reinterpret_cast<const float2*>(T.split + 6 * (int64_t)W.cand[j]);
+      term(P[0], P[1], P[2]);
     }
   } else {
     const double x = T.xs[k], y = T.ys[k], z = T.zs[k];
     const double R2 = 4.0 * h * h, inv_h = 1.0 / h;
-    for (int j = lane; j < cnt; j += 32) {
-      const int64_t c = W.cand[j];
-      const float2* P = reinterpret_cast<const float2*>(T.split + 6 * c);
-      const float2 a = P[0], b = P[1], cc = P[2];
+    auto term = [&](int64_t c, float2 a, float2 b, float2 cc) {
       const float dx = ((a.x - hx) + (a.y - lx)) * inv_hf;
       const float dy = ((b.x - hy) + (b.y - ly)) * inv_hf;
       const float dz = ((cc.x - hz) + (cc.y - lz)) * inv_hf;
-      if (dx * dx + dy * dy + dz * dz > 4.00004f) continue;  // FP32 screen, 1e-5 relative margin
+      if (dx * dx + dy * dy + dz * dz > 4.00004f) return;  // FP32 screen, 1e-5 relative margin
       const double ex = T.xs[c] - x, ey = T.ys[c] - y, ez = T.zs[c] - z;
       const double r2 = ex * ex + ey * ey + ez * ez;
-      if (r2 >= R2) continue;
+      if (r2 >= R2) return;
       const double q = sqrt(r2) * inv_h;
       const double w = w_m4(q);
       s64 += w;
       d64 += 3.0 * w + q * dw_m4(q);
+    };
+    int j = lane;
+    for (; j + 32 < cnt; j += 64) {
+      const int64_t c0 = W.cand[j], c1 = W.cand[j + 32];
+      const float2* P = reinterpret_cast<const float2*>(T.split + 6 * c0);
+      const float2* Q = reinterpret_cast<const float2*>(T.split + 6 * c1);
+      const float2 a = P[0], b = P[1], c = P[2], a1 = Q[0], b1 = Q[1], cc1 = Q[2];
+      term(c0, a, b, c);
+      term(c1, a1, b1, cc1);
+    }
+    if (j < cnt) {
+      const int64_t c0 = W.cand[j];
+      const float2* P = reinterpret_cast<const float2*>(T.split + 6 * c0);
+      term(c0, P[0], P[1], P[2]);
     }
   }
 }

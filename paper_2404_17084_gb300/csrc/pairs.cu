@@ -70,6 +70,10 @@ __device__ __forceinline__ bool pair_rule(const PairGrid& G, const PairTree& T, 
       !exact_dist(G.site[3 * c], G.site[3 * c + 1], G.site[3 * c + 2], G.rad[c], T.xs[k], T.ys[k], T.zs[k], T.hs[k]))
     return false;
   const float thr = 2.f * hf;
+  // every face test passes when the particle lies within 2h of the site: the
+  // site is inside each face plane, so n.r - d < |r - s| for every face (the
+  // 1e-4 relative margin covers the FP32 rounding many times over)
+  if (d2 < thr * thr * 0.9999f) return true;
   const float l1 = fabsf(fx) + fabsf(fy) + fabsf(fz);
   for (int64_t f = G.cfo[c]; f < G.cfo[c + 1]; ++f) {
     const float4 F = G.face32[f];
