@@ -142,13 +142,17 @@ __device__ int walk_next(const HsTree& T, HsWarp& W, HsWalk& it, const float* q,
     if (it.sp == 0) break;
     const int nd = W.stk[it.sp - 1];
     --it.sp;
-    const int nc = T.nch[nd];
-    const int64_t c0 = T.fc[nd];
+    // the node's link word: first child << 4 | child count (see the tree build)
+    const unsigned link = __float_as_uint(T.box32[8 * (int64_t)nd + 7]);
+    const int nc = link == NODE_LINK_FAR ? T.nch[nd] : (int)(link & 15u);
+    const int64_t c0 = link == NODE_LINK_FAR ? T.fc[nd] : (int64_t)(link >> 4);
     bool hit = false, take = false;
     if (lane < nc) {
-      const float* bx = T.box32 + 8 * (c0 + lane);
+      const float4 b0 = reinterpret_cast<const float4*>(T.box32)[2 * (c0 + lane)];
+      const float4 b1 = reinterpret_cast<const float4*>(T.box32)[2 * (c0 + lane) + 1];
+      const float bx[6] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y};
       hit = !box_far_box(bx, q, it.Rm);
-      take = hit && (T.nch[c0 + lane] == 0 || box_within_box(bx, q, it.Rin));
+      take = hit && (__float_as_uint(b1.w) == 0u || box_within_box(bx, q, it.Rin));
     }
     const unsigned mt = __ballot_sync(FULL, take), mi = __ballot_sync(FULL, hit && !take);
     const int ni = __popc(mi);

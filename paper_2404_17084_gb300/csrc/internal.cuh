@@ -52,6 +52,10 @@ struct PreparedGrid {
   size_t bytes = 0;
 };
 
+// Last word of a node's FP32 walk record (box32) when its first child does
+// not fit in 28 bits.
+#define NODE_LINK_FAR 0xffffffffu
+
 // Per-edge record: in-plane inward normal m (3), delta = m.(v_a - s) (so that
 // m.(p - v_a) = m.(r - s) - delta > 0 when p is on the inner side),
 // unit direction e (3), eps_a = e.(v_a - s), eps_b = e.(v_b - s), pad (3).

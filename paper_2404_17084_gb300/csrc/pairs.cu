@@ -135,15 +135,17 @@ __global__ void __launch_bounds__(128) pair_traverse(int64_t ncell, const int32_
   while (sp > 0) {
     const int32_t nd = stack[--sp];
     __syncwarp();
-    const float* b = T.box32 + 8 * nd;
-    const float dx = fsx < b[0] ? b[0] - fsx : (fsx > b[3] ? fsx - b[3] : 0.f);
-    const float dy = fsy < b[1] ? b[1] - fsy : (fsy > b[4] ? fsy - b[4] : 0.f);
-    const float dz = fsz < b[2] ? b[2] - fsz : (fsz > b[5] ? fsz - b[5] : 0.f);
-    const float reach = (2.f * b[6] + fR + 1e-6f) * 1.000001f;
+    const float4 b0 = reinterpret_cast<const float4*>(T.box32)[2 * (int64_t)nd];
+    const float4 b1 = reinterpret_cast<const float4*>(T.box32)[2 * (int64_t)nd + 1];
+    const float dx = fsx < b0.x ? b0.x - fsx : (fsx > b0.w ? fsx - b0.w : 0.f);
+    const float dy = fsy < b0.y ? b0.y - fsy : (fsy > b1.x ? fsy - b1.x : 0.f);
+    const float dz = fsz < b0.z ? b0.z - fsz : (fsz > b1.y ? fsz - b1.y : 0.f);
+    const float reach = (2.f * b1.z + fR + 1e-6f) * 1.000001f;
     const bool need = valid && dx * dx + dy * dy + dz * dz <= reach * reach;
     const unsigned mneed = __ballot_sync(0xffffffffu, need);
     if (!mneed) continue;
-    if (T.nch[nd] == 0) {
+    const unsigned link = __float_as_uint(b1.w);
+    if (link == 0u) {
       const int64_t k0 = T.nb[nd];
       const int nl = (int)(T.ne[nd] - k0);
       const int nn = __popc(mneed);
@@ -182,8 +184,8 @@ __global__ void __launch_bounds__(128) pair_traverse(int64_t ncell, const int32_
         }
       }
     } else {
-      const int nc = T.nch[nd];
-      const int64_t c0 = T.fc[nd];
+      const int nc = link == NODE_LINK_FAR ? T.nch[nd] : (int)(link & 15u);
+      const int64_t c0 = link == NODE_LINK_FAR ? T.fc[nd] : (int64_t)(link >> 4);
       if (lane < nc) stack[sp + lane] = (int32_t)(c0 + nc - 1 - lane);
       sp += nc;
       __syncwarp();

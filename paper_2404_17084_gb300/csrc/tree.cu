@@ -231,8 +231,13 @@ __global__ void node_extent_big(const int32_t* __restrict__ big, int slices, con
 
 // FP32 copy of each node's bounding box (rounded outward) and largest h
 // (rounded up), for conservative FP32 pruning in traversals.
+// The walks' node record, two 16-byte loads: the outward-rounded FP32 box,
+// the largest h, and (bits of the last float) first child << 4 | child count
+// for an internal node with a first child below 2^28, 0 for a leaf, and
+// NODE_LINK_FAR when the index does not fit (read the arrays then).
 __global__ void node_box32(int64_t nn, const unsigned long long* __restrict__ bbox,
-                           const unsigned long long* __restrict__ hmax, float* box32) {
+                           const unsigned long long* __restrict__ hmax, const int64_t* __restrict__ fc,
+                           const int32_t* __restrict__ nch, float* box32) {
   int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (i >= nn) return;
   for (int k = 0; k < 3; ++k) {
@@ -240,7 +245,10 @@ __global__ void node_box32(int64_t nn, const unsigned long long* __restrict__ bb
     box32[8 * i + 3 + k] = __double2float_ru(bitsd(bbox[6 * i + 3 + k]));
   }
   box32[8 * i + 6] = __double2float_ru(bitsd(hmax[i]));
-  box32[8 * i + 7] = 0.f;
+  const int nc = nch[i];
+  const int64_t f = fc[i];
+  const unsigned link = nc == 0 ? 0u : (f < (1LL << 28) ? ((unsigned)f << 4) | (unsigned)nc : NODE_LINK_FAR);
+  box32[8 * i + 7] = __uint_as_float(link);
 }
 
 __global__ void collect_big(int64_t nn, const int64_t* __restrict__ nb, const int64_t* __restrict__ ne, int32_t* big,
@@ -388,7 +396,8 @@ int tree_build(map_ctx* ctx, const double* x, const double* y, const double* z, 
   float* box32;
   MAP_TRY(ensure_t(ctx, ctx->ws_tree[24], 8 * T.nnodes, &box32));
   T.box32 = box32;
-  node_box32<<<nblk(T.nnodes, tpb), tpb, 0, s>>>(T.nnodes, T.bbox_bits, T.hmax_bits, box32); ++ctx->launches;
+  node_box32<<<nblk(T.nnodes, tpb), tpb, 0, s>>>(T.nnodes, T.bbox_bits, T.hmax_bits, T.first_child, T.nchild,
+                                                 box32); ++ctx->launches;
   CUDA_TRY(cudaGetLastError());
   return MAP_OK;
 }
