@@ -131,12 +131,17 @@ const char* map_strerror(int code);
 
 /* Copy a grid (device pointers, read during the call only) into context
  * memory and precompute its per-face and per-edge geometry, cell volumes and
- * cell radii (largest vertex distance from the site).  The grid stays
+ * cell radii (largest vertex distance from the site).  The geometry kept is
+ * what the context's precision reads: FP32 face planes, face bounding
+ * spheres and edge records for MAP_MIXED, FP64 edge records for MAP_FP64.  The grid stays
  * resident until map_grid_release / map_destroy.  Synchronises the stream.
  * Errors: MAP_EINVAL (empty or inconsistent sizes), MAP_ENOMEM. */
 int map_grid_upload(map_ctx* ctx, const map_grid* grid, int* handle, void* stream);
 
-/* Release a resident grid.  MAP_EHANDLE if unknown. */
+/* Release a resident grid.  Its device buffers stay with the context and
+ * serve later uploads of the same or a smaller grid (no cudaMalloc then);
+ * they are freed by map_destroy, or when an upload or the HBM budget needs
+ * the room.  Waits for the device.  MAP_EHANDLE if unknown. */
 int map_grid_release(map_ctx* ctx, int handle);
 
 /* Copy the volumes V_i of a resident grid into vol (device, ncell doubles). */

@@ -129,9 +129,10 @@ void map_destroy(map_ctx* ctx) {
   cudaDeviceSynchronize();
   for (PreparedGrid* g : ctx->grids)
     if (g) {
-      for (void* p : g->allocs) cudaFree(p);
+      for (const DevBuf& b : g->allocs) cudaFree(b.p);
       delete g;
     }
+  for (const DevBuf& b : ctx->grid_pool) cudaFree(b.p);
   for (auto& b : ctx->ws_tree) if (b.p) cudaFree(b.p);
   for (auto& b : ctx->ws_pairs) if (b.p) cudaFree(b.p);
   for (auto& b : ctx->ws_misc) if (b.p) cudaFree(b.p);
@@ -163,8 +164,7 @@ int map_grid_upload(map_ctx* ctx, const map_grid* grid, int* handle, void* strea
   int r = grid_prepare(ctx, grid, g, S(stream));
   if (r != MAP_OK) {
     cudaStreamSynchronize(S(stream));
-    for (void* p : g->allocs) cudaFree(p);
-    ctx->bytes_in_use -= g->bytes;
+    grid_recycle(ctx, g);
     delete g;
     return r;
   }
@@ -181,8 +181,7 @@ int map_grid_release(map_ctx* ctx, int handle) {
   cudaSetDevice(ctx->device);
   cudaDeviceSynchronize();
   PreparedGrid* g = ctx->grids[handle];
-  for (void* p : g->allocs) cudaFree(p);
-  ctx->bytes_in_use -= g->bytes;
+  grid_recycle(ctx, g);  // kept for the next upload; freed by map_destroy or when room runs out
   delete g;
   ctx->grids[handle] = nullptr;
   return MAP_OK;

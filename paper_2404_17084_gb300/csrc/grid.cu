@@ -30,7 +30,7 @@ __global__ void prep_cells(int64_t ncell, const int64_t* __restrict__ cfo, const
     face32[f] = make_float4((float)P.x, (float)P.y, (float)P.z, (float)dr);
     const int64_t b = fvo[f], e = fvo[f + 1];
     const int64_t L = e - b;
-    {
+    if (fsph32) {
       // bounding sphere: centre at the vertex mean, radius the largest
       // vertex distance, rounded up to FP32 with a relative margin
       double cx = 0, cy = 0, cz = 0;
@@ -60,26 +60,20 @@ __global__ void prep_cells(int64_t ncell, const int64_t* __restrict__ cfo, const
       ax += Ay * Bz - Az * By;
       ay += Az * Bx - Ax * Bz;
       az += Ax * By - Ay * Bx;
-      double ex = Bx - Ax, ey = By - Ay, ez = Bz - Az;
-      const double len = sqrt(ex * ex + ey * ey + ez * ez);
-      double* E = edge64 + (b + k) * EDGE_STRIDE;
-      float* Ef = edge32 + (b + k) * EDGE_STRIDE;
-      if (len > 1e-13 * (dr > 0 ? dr : 1.0)) {
-        ex /= len; ey /= len; ez /= len;
-        // in-plane inward normal (loops are CCW seen from outside): m = n x e
-        const double mx = P.y * ez - P.z * ey, my = P.z * ex - P.x * ez, mz = P.x * ey - P.y * ex;
-        const double delta = mx * Ax + my * Ay + mz * Az;
-        const double ea = ex * Ax + ey * Ay + ez * Az;
-        const double eb = ex * Bx + ey * By + ez * Bz;
-        const double rec[9] = {mx, my, mz, delta, ex, ey, ez, ea, eb};
-        for (int j = 0; j < 9; ++j) { E[j] = rec[j]; Ef[j] = (float)rec[j]; }
-      } else {
-        // zero-length edge: no wedge; R0s = m.y - delta*hinv is +huge, so the edge
-        // never makes p 'outside' and its r0^2 + R0^2 is beyond the support
-        const double rec[9] = {0, 0, 0, -1e30, 0, 0, 0, 0, 0};
-        for (int j = 0; j < 9; ++j) { E[j] = rec[j]; Ef[j] = (float)rec[j]; }
+      // a zero-length edge gets R0s = m.y - delta*hinv = +huge: it never
+      // makes p 'outside' and its r0^2 + R0^2 is beyond the support
+      double rec[9];
+      edge_record64(P.x, P.y, P.z, dr, Ax, Ay, Az, Bx, By, Bz, rec);
+      if (edge64) {
+        double* E = edge64 + (b + k) * EDGE_STRIDE;
+        for (int j = 0; j < 9; ++j) E[j] = rec[j];
+        for (int j = 9; j < EDGE_STRIDE; ++j) E[j] = 0;
       }
-      for (int j = 9; j < EDGE_STRIDE; ++j) { E[j] = 0; Ef[j] = 0; }
+      if (edge32) {
+        float* Ef = edge32 + (b + k) * EDGE_STRIDE;
+        for (int j = 0; j < 9; ++j) Ef[j] = (float)rec[j];
+        for (int j = 9; j < EDGE_STRIDE; ++j) Ef[j] = 0;
+      }
     }
     const double area = 0.5 * (ax * P.x + ay * P.y + az * P.z);
     V += dr * area / 3.0;
@@ -115,16 +109,52 @@ __global__ void check_csr(int64_t ncell, int64_t nface, int64_t nloop, int64_t n
 
 }  // namespace
 
+void grid_recycle(map_ctx* ctx, PreparedGrid* g) {
+  for (const DevBuf& b : g->allocs) ctx->grid_pool.push_back(b);
+  g->allocs.clear();
+  g->bytes = 0;
+}
+
+void grid_pool_drop(map_ctx* ctx) {
+  for (const DevBuf& b : ctx->grid_pool) {
+    cudaFree(b.p);
+    ctx->bytes_in_use -= b.cap;
+  }
+  ctx->grid_pool.clear();
+}
+
+// A grid buffer: the smallest pooled buffer of a released grid that holds
+// `bytes` (and wastes at most as much again), else a new allocation, after
+// freeing the pool if the budget or the device has no room.
 int ctx_alloc_grid(map_ctx* ctx, PreparedGrid* g, void** p, size_t bytes) {
   if (bytes == 0) bytes = 16;
+  int best = -1;
+  for (int i = 0; i < (int)ctx->grid_pool.size(); ++i) {
+    const size_t c = ctx->grid_pool[i].cap;
+    if (c >= bytes && c <= 2 * bytes + (1u << 20) && (best < 0 || c < ctx->grid_pool[best].cap)) best = i;
+  }
+  if (best >= 0) {
+    const DevBuf b = ctx->grid_pool[best];
+    ctx->grid_pool.erase(ctx->grid_pool.begin() + best);
+    *p = b.p;
+    g->bytes += b.cap;
+    g->allocs.push_back(b);
+    return MAP_OK;
+  }
+  if (ctx->cfg.hbm_budget && ctx->bytes_in_use + bytes > ctx->cfg.hbm_budget) grid_pool_drop(ctx);
   if (ctx->cfg.hbm_budget && ctx->bytes_in_use + bytes > ctx->cfg.hbm_budget) return MAP_ENOMEM;
   if (cudaMalloc(p, bytes) != cudaSuccess) {
     cudaGetLastError();
-    return MAP_ENOMEM;
+    if (ctx->grid_pool.empty()) return MAP_ENOMEM;
+    grid_pool_drop(ctx);
+    if (cudaMalloc(p, bytes) != cudaSuccess) {
+      cudaGetLastError();
+      return MAP_ENOMEM;
+    }
   }
   ctx->bytes_in_use += bytes;
   g->bytes += bytes;
-  g->allocs.push_back(*p);
+  g->allocs.push_back(DevBuf{*p, bytes});
   return MAP_OK;
 }
 
@@ -139,10 +169,17 @@ int grid_prepare(map_ctx* ctx, const map_grid* in, PreparedGrid* g, cudaStream_t
   MAP_TRY(ctx_alloc_grid(ctx, g, (void**)&g->face_vert, nl * sizeof(int32_t)));
   MAP_TRY(ctx_alloc_grid(ctx, g, (void**)&g->face_plane, nf * sizeof(double4_32a)));
   MAP_TRY(ctx_alloc_grid(ctx, g, (void**)&g->face64, nf * sizeof(double4_32a)));
+  // FP32 faces for the pair rule's screen; then the records a context's
+  // integral kernel reads: face spheres and FP32 edges for the mixed build
+  // (its rare FP64 faces rebuild their edge records from the vertices), FP64
+  // edges for the FP64 build
   MAP_TRY(ctx_alloc_grid(ctx, g, (void**)&g->face32, nf * sizeof(float4)));
-  MAP_TRY(ctx_alloc_grid(ctx, g, (void**)&g->fsph32, nf * sizeof(float4)));
-  MAP_TRY(ctx_alloc_grid(ctx, g, (void**)&g->edge64, nl * EDGE_STRIDE * sizeof(double)));
-  MAP_TRY(ctx_alloc_grid(ctx, g, (void**)&g->edge32, nl * EDGE_STRIDE * sizeof(float)));
+  if (ctx->cfg.precision == MAP_MIXED) {
+    MAP_TRY(ctx_alloc_grid(ctx, g, (void**)&g->fsph32, nf * sizeof(float4)));
+    MAP_TRY(ctx_alloc_grid(ctx, g, (void**)&g->edge32, nl * EDGE_STRIDE * sizeof(float)));
+  } else {
+    MAP_TRY(ctx_alloc_grid(ctx, g, (void**)&g->edge64, nl * EDGE_STRIDE * sizeof(double)));
+  }
   MAP_TRY(ctx_alloc_grid(ctx, g, (void**)&g->site, nc * 3 * sizeof(double)));
   MAP_TRY(ctx_alloc_grid(ctx, g, (void**)&g->vol, nc * sizeof(double)));
   MAP_TRY(ctx_alloc_grid(ctx, g, (void**)&g->rad, nc * sizeof(double)));

@@ -162,6 +162,14 @@ __device__ __forceinline__ float take_row(float (*col)[32], int o, float& comp) 
   return s;
 }
 
+// The FP64 record of the directed edge ia -> ib of face G (not inlined: the
+// rare FP64 faces then add no registers to the integral kernels).
+__device__ __noinline__ void edge_rec64_at(const SnapDesc& A, const double4_32a& G, int32_t ia, int32_t ib,
+                                           double sx, double sy, double sz, double* D) {
+  edge_record64(G.x, G.y, G.z, G.w, A.vx[ia] - sx, A.vy[ia] - sy, A.vz[ia] - sz, A.vx[ib] - sx, A.vy[ib] - sy,
+                A.vz[ib] - sz, D);
+}
+
 // Mixed build, a face whose plane passes within TAU of the particle: decide
 // the side and evaluate every edge of the face in FP64 in this lane.
 __device__ __noinline__ double face_fp64(const SnapDesc& A, int64_t f, int64_t kb, int64_t ke, int64_t l0,
@@ -173,8 +181,14 @@ __device__ __noinline__ double face_fp64(const SnapDesc& A, int64_t f, int64_t k
   fin = rs >= 0.0;
   const double r0d = fabs(rs) > EPS ? fabs(rs) : EPS;
   double acc = 0.0;
+  const int64_t b = l0 + kb;
+  const int64_t L = ke - kb;
   for (int64_t kk = kb; kk < ke; ++kk) {
-    const double* D = A.edge64 + (l0 + kk) * EDGE_STRIDE;
+    // the edge's FP64 record, from its vertices as the grid preparation makes it
+    const int64_t k = kk - kb;
+    const int32_t ia = A.face_vert[b + k], ib = A.face_vert[b + (k + 1 == L ? 0 : k + 1)];
+    double D[9];
+    edge_rec64_at(A, G, ia, ib, sx, sy, sz, D);
     const double R0sd = (D[0] * ydx + D[1] * ydy + D[2] * ydz) - D[3] * hh;
     const double based = D[4] * ydx + D[5] * ydy + D[6] * ydz;
     const bool eind = R0sd >= 0.0;
@@ -788,6 +802,10 @@ SnapDesc make_desc(map_ctx* ctx, const PreparedGrid* g, const map_particles* p, 
   d.face64 = g->face64;
   d.edge64 = g->edge64;
   d.fsph = g->fsph32;
+  d.face_vert = g->face_vert;
+  d.vx = g->vx;
+  d.vy = g->vy;
+  d.vz = g->vz;
   d.items = ctx->items;
   d.item_off = ctx->item_off;
   d.partial = ctx->partial;

@@ -37,8 +37,8 @@ struct PreparedGrid {
   double4_32a* face64 = nullptr;         // site-relative (nx,ny,nz,d - n.s) [nface]
   float4* face32 = nullptr;          // same, FP32
   float4* fsph32 = nullptr;          // per face: bounding-sphere centre (site-relative) and radius, FP32
-  double* edge64 = nullptr;          // EDGE_STRIDE doubles per loop entry (site-relative)
-  float* edge32 = nullptr;           // EDGE_STRIDE floats per loop entry
+  double* edge64 = nullptr;          // EDGE_STRIDE doubles per loop entry (site-relative); FP64 contexts
+  float* edge32 = nullptr;           // EDGE_STRIDE floats per loop entry; mixed contexts
   double* site = nullptr;            // [3*ncell]
   double* vol = nullptr;             // [ncell]
   double* rad = nullptr;             // [ncell] largest vertex distance from the site
@@ -48,7 +48,7 @@ struct PreparedGrid {
   int32_t* face_vert = nullptr;
   int max_faces = 0;                 // largest face count of a cell
   int max_loops = 0;                 // largest loop-entry count of a cell
-  std::vector<void*> allocs;
+  std::vector<DevBuf> allocs;
   size_t bytes = 0;
 };
 
@@ -60,6 +60,29 @@ struct PreparedGrid {
 // m.(p - v_a) = m.(r - s) - delta > 0 when p is on the inner side),
 // unit direction e (3), eps_a = e.(v_a - s), eps_b = e.(v_b - s), pad (3).
 #define EDGE_STRIDE 12
+
+// The record of the directed edge from vertex A to vertex B (site-relative
+// positions) of a face with unit outward normal (nx, ny, nz), in FP64, into
+// rec[0..8]; dr = d - n.s sets the length below which the edge counts as
+// zero-length (no wedge: R0 is then +huge, beyond any support).
+__device__ __forceinline__ void edge_record64(double nx, double ny, double nz, double dr, double Ax, double Ay,
+                                              double Az, double Bx, double By, double Bz, double* rec) {
+  double ex = Bx - Ax, ey = By - Ay, ez = Bz - Az;
+  const double len = sqrt(ex * ex + ey * ey + ez * ez);
+  if (len > 1e-13 * (dr > 0 ? dr : 1.0)) {
+    ex /= len; ey /= len; ez /= len;
+    // in-plane inward normal (loops are CCW seen from outside): m = n x e
+    const double mx = ny * ez - nz * ey, my = nz * ex - nx * ez, mz = nx * ey - ny * ex;
+    rec[0] = mx; rec[1] = my; rec[2] = mz;
+    rec[3] = mx * Ax + my * Ay + mz * Az;
+    rec[4] = ex; rec[5] = ey; rec[6] = ez;
+    rec[7] = ex * Ax + ey * Ay + ez * Az;
+    rec[8] = ex * Bx + ey * By + ez * Bz;
+  } else {
+    for (int j = 0; j < 9; ++j) rec[j] = 0.0;
+    rec[3] = -1e30;
+  }
+}
 
 // Octree over a particle set (Morton order, level-synchronous build).
 struct DevTree {
@@ -106,8 +129,9 @@ struct map_ctx {
   map_config cfg;
   int device = 0;
   int sm_count = 0;
-  size_t bytes_in_use = 0;
+  size_t bytes_in_use = 0;             // device bytes held (workspace, grids, grid pool)
   std::vector<PreparedGrid*> grids;
+  std::vector<DevBuf> grid_pool;       // buffers of released grids, reused by later uploads
   // workspace
   DevBuf ws_tree[32];
   DevBuf ws_pairs[13];
@@ -191,6 +215,8 @@ struct SnapDesc {
   const double4_32a* face64;
   const double* edge64;
   const float4* fsph;  // per face: bounding sphere (site-relative centre, radius), FP32
+  const int32_t* face_vert;          // loop entries -> vertices (the FP64 faces of the mixed build)
+  const double *vx, *vy, *vz;
   int64_t orig;        // the caller's index of this snapshot
 };
 
@@ -211,6 +237,10 @@ constexpr int N_VARIANTS = 3;  // launch shapes of the mixed pair-integral kerne
 
 // ---------------------------------------------------------------- subsystems
 int grid_prepare(map_ctx* ctx, const map_grid* in, PreparedGrid* g, cudaStream_t s);
+// Returns a grid's buffers to the context's pool (the caller has synchronised
+// the device), and frees the pool.
+void grid_recycle(map_ctx* ctx, PreparedGrid* g);
+void grid_pool_drop(map_ctx* ctx);
 int tree_build(map_ctx* ctx, const double* x, const double* y, const double* z, const double* m,
                const double* h, int64_t n, cudaStream_t s, bool want_size = false);
 // Output buffers of a pair-list build; nullptr members mean the context's

@@ -59,9 +59,12 @@ double ms_between(std::chrono::steady_clock::time_point a, std::chrono::steady_c
 // Device bytes a request may hold: its input copies, the prepared grid, the
 // octree, the pair list (160 pairs per particle assumed: FP64 fraction and
 // two index arrays) and the per-cell outputs, with 25% headroom.
-size_t request_bytes(const map_request& r) {
+size_t request_bytes(const map_request& r, int precision) {
   const double parts = 48.0 * r.n + 200.0 * r.n + 160.0 * 16.0 * r.n;
-  const double grid = 96.0 * r.ncell + 146.0 * r.nface + 160.0 * r.nloop + 48.0 * r.nvert;
+  // per loop entry: the staged index and the edge records the precision keeps
+  // (12 floats for the mixed build, 12 doubles for FP64)
+  const double loop = precision == MAP_MIXED ? 64.0 : 112.0;
+  const double grid = 96.0 * r.ncell + 146.0 * r.nface + loop * r.nloop + 48.0 * r.nvert;
   const double outs = 24.0 * r.ncell;
   return (size_t)(1.25 * (parts + grid + outs)) + (64u << 20);
 }
@@ -69,7 +72,8 @@ size_t request_bytes(const map_request& r) {
 // Context workspace kept by an idle slot.
 size_t cached_bytes(const map_server::Slot& s) { return s.ctx ? s.ctx->bytes_in_use : 0; }
 
-// Frees a context's workspace (not its grids); the next request reallocates.
+// Frees a context's workspace and its pool of released grid buffers (not
+// its grids); the next request reallocates.
 void trim(map_ctx* ctx) {
   cudaSetDevice(ctx->device);
   cudaDeviceSynchronize();
@@ -82,6 +86,7 @@ void trim(map_ctx* ctx) {
   for (auto* v : {&ctx->batch_off, &ctx->batch_idx, &ctx->batch_itm, &ctx->batch_ioff, &ctx->batch_part})
     for (auto& b : *v) drop(b);
   drop(ctx->cub_tmp);
+  grid_pool_drop(ctx);
   ctx->pair_off = nullptr;
   ctx->pair_idx = nullptr;
   ctx->pair_frac = nullptr;
@@ -100,7 +105,7 @@ void admit(map_server* S) {
     if (free_slot < 0) return;
     const int64_t t = S->queue.front();
     map_server::Rec& R = S->recs[t];
-    const size_t need = request_bytes(R.req);
+    const size_t need = request_bytes(R.req, S->cfg.precision);
     auto held = [&]() {
       size_t h = 0;
       for (auto& s : S->slots) h += s.busy ? (s.reserved > cached_bytes(s) ? s.reserved : cached_bytes(s)) : cached_bytes(s);
