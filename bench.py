@@ -771,8 +771,9 @@ def run_pseudo(args):
 
 
 def e2e_run(L, torch, ctx, p, g, dev, args, barrier, world):
-    """Same metric through the public API: pinned host inputs copied in, the
-    grid uploaded and prepared, solve_h + mapping, cell masses read back."""
+    """Same metric through the public API: pinned host inputs copied in (the
+    particles by torch, the grid by map_grid_upload itself), the grid
+    prepared, solve_h + mapping, cell masses read back."""
     pin = lambda a, dt: torch.as_tensor(np.ascontiguousarray(a), dtype=dt).pin_memory()
     hp = [pin(a, torch.float64) for a in (p.x, p.y, p.z, p.m)]
     hg = dict(cell_face_off=pin(g.cell_face_off, torch.int64), face_vert_off=pin(g.face_vert_off, torch.int64),
@@ -785,8 +786,7 @@ def e2e_run(L, torch, ctx, p, g, dev, args, barrier, world):
 
     def one():
         dp = [t.to(dev, non_blocking=True) for t in hp]
-        dg = {k: v.to(dev, non_blocking=True) for k, v in hg.items()}
-        handle = L.map_grid_upload(ctx, dg)
+        handle = L.map_grid_upload(ctx, hg)
         hh = torch.empty_like(dp[0])
         L.solve_h(ctx, L.make_particles(dp[0], dp[1], dp[2], None, hh))
         mass = torch.empty(g.ncell, dtype=torch.float64, device=dev)

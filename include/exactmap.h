@@ -129,8 +129,8 @@ const char* map_strerror(int code);
 
 /* ------------------------------------------------------------ grids */
 
-/* Copy a grid (device pointers, read during the call only) into context
- * memory and precompute its per-face and per-edge geometry, cell volumes and
+/* Copy a grid (device or page-locked host pointers, read during the call
+ * only; host arrays are copied in by the call itself) into context memory and precompute its per-face and per-edge geometry, cell volumes and
  * cell radii (largest vertex distance from the site).  The geometry kept is
  * what the context's precision reads: FP32 face planes, face bounding
  * spheres and edge records for MAP_MIXED, FP64 edge records for MAP_FP64.  The grid stays

@@ -143,6 +143,12 @@ def _ptr(t):
     return ctypes.c_void_p(t.data_ptr())
 
 
+def _ptr_dev_or_pinned(t):
+    if not t.is_contiguous() or not (t.is_cuda or t.is_pinned()):
+        raise ValueError("expected a contiguous CUDA or page-locked host tensor")
+    return ctypes.c_void_p(t.data_ptr())
+
+
 def _stream(stream):
     if stream is None:
         stream = torch.cuda.current_stream()
@@ -178,12 +184,14 @@ def make_particles(x, y, z, m=None, h=None) -> map_particles:
 
 
 def map_grid_upload(ctx, g: dict, stream=None) -> int:
-    """g: dict of CUDA tensors cell_face_off, face_vert_off (int64), face_vert
-    (int32), face_plane ([nface,4] float64), vx, vy, vz, site ([ncell,3])."""
+    """g: dict of CUDA or page-locked host tensors cell_face_off, face_vert_off
+    (int64), face_vert (int32), face_plane ([nface,4] float64), vx, vy, vz,
+    site ([ncell,3])."""
+    P = _ptr_dev_or_pinned
     mg = map_grid(int(g["cell_face_off"].numel() - 1), int(g["face_vert_off"].numel() - 1),
-                  int(g["face_vert"].numel()), int(g["vx"].numel()), _ptr(g["cell_face_off"]),
-                  _ptr(g["face_vert_off"]), _ptr(g["face_vert"]), _ptr(g["face_plane"]), _ptr(g["vx"]),
-                  _ptr(g["vy"]), _ptr(g["vz"]), _ptr(g["site"]))
+                  int(g["face_vert"].numel()), int(g["vx"].numel()), P(g["cell_face_off"]),
+                  P(g["face_vert_off"]), P(g["face_vert"]), P(g["face_plane"]), P(g["vx"]),
+                  P(g["vy"]), P(g["vz"]), P(g["site"]))
     h = ctypes.c_int(-1)
     _check(_lib.map_grid_upload(ctx, ctypes.byref(mg), ctypes.byref(h), _stream(stream)), "map_grid_upload")
     return h.value

@@ -21,7 +21,7 @@ __global__ void prep_cells(int64_t ncell, const int64_t* __restrict__ cfo, const
   if (c >= ncell) return;
   const double sx = site[3 * c], sy = site[3 * c + 1], sz = site[3 * c + 2];
   const int64_t f0 = cfo[c], f1 = cfo[c + 1];
-  double V = 0.0, R = 0.0;
+  double V = 0.0, R2 = 0.0;
   for (int64_t f = f0; f < f1; ++f) {
     const double4_32a P = plane[f];
     const double dr = P.w - (P.x * sx + P.y * sy + P.z * sz);
@@ -30,54 +30,83 @@ __global__ void prep_cells(int64_t ncell, const int64_t* __restrict__ cfo, const
     face32[f] = make_float4((float)P.x, (float)P.y, (float)P.z, (float)dr);
     const int64_t b = fvo[f], e = fvo[f + 1];
     const int64_t L = e - b;
+    // site-relative vertices: differences in FP64, FP32 copies for the mixed
+    // build's records (their rounding, ~1e-7 of the cell size, is that of
+    // rounding an FP64 record)
+    float mx = 0.f, my = 0.f, mz = 0.f;  // FP32 vertex mean (face sphere centre)
     if (fsph32) {
-      // bounding sphere: centre at the vertex mean, radius the largest
-      // vertex distance, rounded up to FP32 with a relative margin
-      double cx = 0, cy = 0, cz = 0;
       for (int64_t k = 0; k < L; ++k) {
         const int32_t ia = fv[b + k];
-        cx += vx[ia] - sx; cy += vy[ia] - sy; cz += vz[ia] - sz;
+        mx += (float)(vx[ia] - sx); my += (float)(vy[ia] - sy); mz += (float)(vz[ia] - sz);
       }
-      cx /= (double)L; cy /= (double)L; cz /= (double)L;
-      double r2 = 0;
-      for (int64_t k = 0; k < L; ++k) {
-        const int32_t ia = fv[b + k];
-        const double dx = vx[ia] - sx - cx, dy = vy[ia] - sy - cy, dz = vz[ia] - sz - cz;
-        const double d2 = dx * dx + dy * dy + dz * dz;
-        r2 = d2 > r2 ? d2 : r2;
-      }
-      fsph32[f] = make_float4((float)cx, (float)cy, (float)cz, (float)(sqrt(r2) * (1.0 + 1e-5) + 1e-12));
+      const float il = 1.0f / (float)L;
+      mx *= il; my *= il; mz *= il;
     }
+    float sr2 = 0.f;  // FP32 squared sphere radius
     double ax = 0, ay = 0, az = 0;
+    const int32_t i0 = fv[b];
+    const double X0 = vx[i0] - sx, Y0 = vy[i0] - sy, Z0 = vz[i0] - sz;
+    double Ax = X0, Ay = Y0, Az = Z0;
     for (int64_t k = 0; k < L; ++k) {
-      const int32_t ia = fv[b + k], ib = fv[b + (k + 1 == L ? 0 : k + 1)];
-      const double Ax = vx[ia] - sx, Ay = vy[ia] - sy, Az = vz[ia] - sz;
-      const double Bx = vx[ib] - sx, By = vy[ib] - sy, Bz = vz[ib] - sz;
-      // cell radius: fixed evaluation order, no FMA contraction
-      double r = __dsqrt_rn(__dadd_rn(__dadd_rn(__dmul_rn(Ax, Ax), __dmul_rn(Ay, Ay)), __dmul_rn(Az, Az)));
-      R = r > R ? r : R;
+      double Bx = X0, By = Y0, Bz = Z0;
+      if (k + 1 < L) {
+        const int32_t ib = fv[b + k + 1];
+        Bx = vx[ib] - sx; By = vy[ib] - sy; Bz = vz[ib] - sz;
+      }
+      // cell radius: fixed evaluation order, no FMA contraction; one
+      // correctly rounded square root of the largest square at the end
+      const double r2 = __dadd_rn(__dadd_rn(__dmul_rn(Ax, Ax), __dmul_rn(Ay, Ay)), __dmul_rn(Az, Az));
+      R2 = r2 > R2 ? r2 : R2;
       // area vector (site-relative loop)
       ax += Ay * Bz - Az * By;
       ay += Az * Bx - Ax * Bz;
       az += Ax * By - Ay * Bx;
       // a zero-length edge gets R0s = m.y - delta*hinv = +huge: it never
       // makes p 'outside' and its r0^2 + R0^2 is beyond the support
-      double rec[9];
-      edge_record64(P.x, P.y, P.z, dr, Ax, Ay, Az, Bx, By, Bz, rec);
       if (edge64) {
+        double rec[9];
+        edge_record64(P.x, P.y, P.z, dr, Ax, Ay, Az, Bx, By, Bz, rec);
         double* E = edge64 + (b + k) * EDGE_STRIDE;
         for (int j = 0; j < 9; ++j) E[j] = rec[j];
         for (int j = 9; j < EDGE_STRIDE; ++j) E[j] = 0;
       }
       if (edge32) {
+        const float ax32 = (float)Ax, ay32 = (float)Ay, az32 = (float)Az;
+        const float bx32 = (float)Bx, by32 = (float)By, bz32 = (float)Bz;
+        float rec[9];
+        float ex = bx32 - ax32, ey = by32 - ay32, ez = bz32 - az32;
+        const float len = sqrtf(ex * ex + ey * ey + ez * ez);
+        if (len > 0.f) {
+          const float il = 1.0f / len;
+          ex *= il; ey *= il; ez *= il;
+          const float nx = (float)P.x, ny = (float)P.y, nz = (float)P.z;
+          const float gx = ny * ez - nz * ey, gy = nz * ex - nx * ez, gz = nx * ey - ny * ex;
+          rec[0] = gx; rec[1] = gy; rec[2] = gz;
+          rec[3] = gx * ax32 + gy * ay32 + gz * az32;
+          rec[4] = ex; rec[5] = ey; rec[6] = ez;
+          rec[7] = ex * ax32 + ey * ay32 + ez * az32;
+          rec[8] = ex * bx32 + ey * by32 + ez * bz32;
+        } else {
+          for (int j = 0; j < 9; ++j) rec[j] = 0.f;
+          rec[3] = -1e30f;
+        }
         float* Ef = edge32 + (b + k) * EDGE_STRIDE;
-        for (int j = 0; j < 9; ++j) Ef[j] = (float)rec[j];
+        for (int j = 0; j < 9; ++j) Ef[j] = rec[j];
         for (int j = 9; j < EDGE_STRIDE; ++j) Ef[j] = 0;
+        if (fsph32) {
+          const float dx = ax32 - mx, dy = ay32 - my, dz = az32 - mz;
+          sr2 = fmaxf(sr2, dx * dx + dy * dy + dz * dz);
+        }
       }
+      Ax = Bx; Ay = By; Az = Bz;
     }
+    // bounding sphere: centre at the vertex mean, radius the largest vertex
+    // distance, rounded up (FP32 rounding is far inside the margin)
+    if (fsph32) fsph32[f] = make_float4(mx, my, mz, sqrtf(sr2) * (1.0f + 1e-5f) + 1e-12f);
     const double area = 0.5 * (ax * P.x + ay * P.y + az * P.z);
     V += dr * area / 3.0;
   }
+  const double R = __dsqrt_rn(R2);
   vol[c] = V;
   rad[c] = R;
   atomicMax(maxf, (int)(f1 - f0));

@@ -216,3 +216,32 @@ def test_few_large_cells():
         assert np.array_equal(out["idx"], ref["idx"])
         assert rel_err(out["mass"], ref["mass"]).max() < TOL[prec][0]
         assert abs(out["total"] - ref["mass"].sum()) < TOL[prec][1] * ref["mass"].sum()
+
+
+def test_grid_upload_from_pinned_host_and_reuse(uniform4096):
+    """map_grid_upload takes page-locked host arrays as well as device arrays
+    (the same prepared grid, so bit-equal volumes and masses), and a grid
+    uploaded after a release reuses the released buffers with the same result."""
+    import torch
+    p, g, h, _, _ = uniform4096
+    L = lib()
+    ctx = L.map_init(L.map_config_default(precision=1))
+    try:
+        x, y, z, m, hh = dev_particles(p, h)
+        res = []
+        for src in ("device", "pinned", "device"):
+            if src == "device":
+                gd = L.grid_to_device(g)
+            else:
+                gd = {k: v.cpu().pin_memory() for k, v in L.grid_to_device(g).items()}
+            handle = L.map_grid_upload(ctx, gd)
+            mass = torch.empty(g.ncell, dtype=torch.float64, device="cuda")
+            vol = torch.empty_like(mass)
+            L.map_particles_to_cells(ctx, L.make_particles(x, y, z, m, hh), handle, mass, None, vol)
+            torch.cuda.synchronize()
+            res.append((mass.cpu().numpy(), vol.cpu().numpy()))
+            L.map_grid_release(ctx, handle)
+    finally:
+        L.map_destroy(ctx)
+    for a, b in res[1:]:
+        assert np.array_equal(a, res[0][0]) and np.array_equal(b, res[0][1])
