@@ -136,6 +136,7 @@ void map_destroy(map_ctx* ctx) {
   for (auto& b : ctx->ws_tree) if (b.p) cudaFree(b.p);
   for (auto& b : ctx->ws_pairs) if (b.p) cudaFree(b.p);
   for (auto& b : ctx->ws_misc) if (b.p) cudaFree(b.p);
+  for (auto& b : ctx->ws_grid) if (b.p) cudaFree(b.p);
   if (ctx->cub_tmp.p) cudaFree(ctx->cub_tmp.p);
   if (ctx->d_counters) cudaFree(ctx->d_counters);
   if (ctx->d_total) cudaFree(ctx->d_total);

@@ -11,104 +11,129 @@
 
 namespace {
 
-__global__ void prep_cells(int64_t ncell, const int64_t* __restrict__ cfo, const int64_t* __restrict__ fvo,
+// Face -> cell map (one thread per cell).
+__global__ void face_cells(int64_t ncell, const int64_t* __restrict__ cfo, int32_t* fcell) {
+  const int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (c >= ncell) return;
+  for (int64_t f = cfo[c]; f < cfo[c + 1]; ++f) fcell[f] = (int32_t)c;
+}
+
+// One thread per face: site-relative planes, the face's bounding sphere and
+// edge records, its term dr * area / 3 of the cell volume (divergence
+// theorem) and the largest squared vertex distance from the site.
+__global__ void prep_faces(int64_t nface, const int32_t* __restrict__ fcell, const int64_t* __restrict__ fvo,
                            const int32_t* __restrict__ fv, const double4_32a* __restrict__ plane,
                            const double* __restrict__ vx, const double* __restrict__ vy,
                            const double* __restrict__ vz, const double* __restrict__ site, double4_32a* face64,
-                           float4* face32, float4* fsph32, double* edge64, float* edge32, double* vol, double* rad,
-                           int* maxf, int* maxl, unsigned long long* status) {
-  int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (c >= ncell) return;
+                           float4* face32, float4* fsph32, double* edge64, float* edge32, double* volf, double* r2f,
+                           unsigned long long* status) {
+  const int64_t f = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (f >= nface) return;
+  const int64_t c = fcell[f];
   const double sx = site[3 * c], sy = site[3 * c + 1], sz = site[3 * c + 2];
+  const double4_32a P = plane[f];
+  const double dr = P.w - (P.x * sx + P.y * sy + P.z * sz);
+  if (!(dr > 0.0)) atomicExch(status, (unsigned long long)(-MAP_EINVAL));  // site must be strictly inside
+  face64[f] = make_double4_32a(P.x, P.y, P.z, dr);
+  face32[f] = make_float4((float)P.x, (float)P.y, (float)P.z, (float)dr);
+  const int64_t b = fvo[f], e = fvo[f + 1];
+  const int64_t L = e - b;
+  // site-relative vertices: differences in FP64, FP32 copies for the mixed
+  // build's records (their rounding, ~1e-7 of the cell size, is that of
+  // rounding an FP64 record)
+  float mx = 0.f, my = 0.f, mz = 0.f;  // FP32 vertex mean (face sphere centre)
+  if (fsph32) {
+    for (int64_t k = 0; k < L; ++k) {
+      const int32_t ia = fv[b + k];
+      mx += (float)(vx[ia] - sx); my += (float)(vy[ia] - sy); mz += (float)(vz[ia] - sz);
+    }
+    const float il = 1.0f / (float)L;
+    mx *= il; my *= il; mz *= il;
+  }
+  float sr2 = 0.f;  // FP32 squared sphere radius
+  double R2 = 0.0;
+  double ax = 0, ay = 0, az = 0;
+  const int32_t i0 = fv[b];
+  const double X0 = vx[i0] - sx, Y0 = vy[i0] - sy, Z0 = vz[i0] - sz;
+  double Ax = X0, Ay = Y0, Az = Z0;
+  for (int64_t k = 0; k < L; ++k) {
+    double Bx = X0, By = Y0, Bz = Z0;
+    if (k + 1 < L) {
+      const int32_t ib = fv[b + k + 1];
+      Bx = vx[ib] - sx; By = vy[ib] - sy; Bz = vz[ib] - sz;
+    }
+    // cell radius: fixed evaluation order, no FMA contraction; one
+    // correctly rounded square root of the cell's largest square at the end
+    const double r2 = __dadd_rn(__dadd_rn(__dmul_rn(Ax, Ax), __dmul_rn(Ay, Ay)), __dmul_rn(Az, Az));
+    R2 = r2 > R2 ? r2 : R2;
+    // area vector (site-relative loop)
+    ax += Ay * Bz - Az * By;
+    ay += Az * Bx - Ax * Bz;
+    az += Ax * By - Ay * Bx;
+    // a zero-length edge gets R0s = m.y - delta*hinv = +huge: it never
+    // makes p 'outside' and its r0^2 + R0^2 is beyond the support
+    if (edge64) {
+      double rec[9];
+      edge_record64(P.x, P.y, P.z, dr, Ax, Ay, Az, Bx, By, Bz, rec);
+      double* E = edge64 + (b + k) * EDGE_STRIDE;
+      for (int j = 0; j < 9; ++j) E[j] = rec[j];
+      for (int j = 9; j < EDGE_STRIDE; ++j) E[j] = 0;
+    }
+    if (edge32) {
+      const float ax32 = (float)Ax, ay32 = (float)Ay, az32 = (float)Az;
+      const float bx32 = (float)Bx, by32 = (float)By, bz32 = (float)Bz;
+      float rec[12];
+      float ex = bx32 - ax32, ey = by32 - ay32, ez = bz32 - az32;
+      const float len = sqrtf(ex * ex + ey * ey + ez * ez);
+      if (len > 0.f) {
+        const float il = 1.0f / len;
+        ex *= il; ey *= il; ez *= il;
+        const float nx = (float)P.x, ny = (float)P.y, nz = (float)P.z;
+        const float gx = ny * ez - nz * ey, gy = nz * ex - nx * ez, gz = nx * ey - ny * ex;
+        rec[0] = gx; rec[1] = gy; rec[2] = gz;
+        rec[3] = gx * ax32 + gy * ay32 + gz * az32;
+        rec[4] = ex; rec[5] = ey; rec[6] = ez;
+        rec[7] = ex * ax32 + ey * ay32 + ez * az32;
+        rec[8] = ex * bx32 + ey * by32 + ez * bz32;
+      } else {
+        for (int j = 0; j < 9; ++j) rec[j] = 0.f;
+        rec[3] = -1e30f;
+      }
+      rec[9] = rec[10] = rec[11] = 0.f;
+      float4* Ef = reinterpret_cast<float4*>(edge32 + (b + k) * EDGE_STRIDE);
+      Ef[0] = make_float4(rec[0], rec[1], rec[2], rec[3]);
+      Ef[1] = make_float4(rec[4], rec[5], rec[6], rec[7]);
+      Ef[2] = make_float4(rec[8], rec[9], rec[10], rec[11]);
+      if (fsph32) {
+        const float dx = ax32 - mx, dy = ay32 - my, dz = az32 - mz;
+        sr2 = fmaxf(sr2, dx * dx + dy * dy + dz * dz);
+      }
+    }
+    Ax = Bx; Ay = By; Az = Bz;
+  }
+  // bounding sphere: centre at the vertex mean, radius the largest vertex
+  // distance, rounded up (FP32 rounding is far inside the margin)
+  if (fsph32) fsph32[f] = make_float4(mx, my, mz, sqrtf(sr2) * (1.0f + 1e-5f) + 1e-12f);
+  const double area = 0.5 * (ax * P.x + ay * P.y + az * P.z);
+  volf[f] = dr * area / 3.0;
+  r2f[f] = R2;
+}
+
+// One thread per cell: volume (the faces' terms in face order), radius R_i
+// and the largest face and loop counts.
+__global__ void prep_cells(int64_t ncell, const int64_t* __restrict__ cfo, const int64_t* __restrict__ fvo,
+                           const double* __restrict__ volf, const double* __restrict__ r2f, double* vol, double* rad,
+                           int* maxf, int* maxl) {
+  const int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (c >= ncell) return;
   const int64_t f0 = cfo[c], f1 = cfo[c + 1];
   double V = 0.0, R2 = 0.0;
   for (int64_t f = f0; f < f1; ++f) {
-    const double4_32a P = plane[f];
-    const double dr = P.w - (P.x * sx + P.y * sy + P.z * sz);
-    if (!(dr > 0.0)) atomicExch(status, (unsigned long long)(-MAP_EINVAL));  // site must be strictly inside
-    face64[f] = make_double4_32a(P.x, P.y, P.z, dr);
-    face32[f] = make_float4((float)P.x, (float)P.y, (float)P.z, (float)dr);
-    const int64_t b = fvo[f], e = fvo[f + 1];
-    const int64_t L = e - b;
-    // site-relative vertices: differences in FP64, FP32 copies for the mixed
-    // build's records (their rounding, ~1e-7 of the cell size, is that of
-    // rounding an FP64 record)
-    float mx = 0.f, my = 0.f, mz = 0.f;  // FP32 vertex mean (face sphere centre)
-    if (fsph32) {
-      for (int64_t k = 0; k < L; ++k) {
-        const int32_t ia = fv[b + k];
-        mx += (float)(vx[ia] - sx); my += (float)(vy[ia] - sy); mz += (float)(vz[ia] - sz);
-      }
-      const float il = 1.0f / (float)L;
-      mx *= il; my *= il; mz *= il;
-    }
-    float sr2 = 0.f;  // FP32 squared sphere radius
-    double ax = 0, ay = 0, az = 0;
-    const int32_t i0 = fv[b];
-    const double X0 = vx[i0] - sx, Y0 = vy[i0] - sy, Z0 = vz[i0] - sz;
-    double Ax = X0, Ay = Y0, Az = Z0;
-    for (int64_t k = 0; k < L; ++k) {
-      double Bx = X0, By = Y0, Bz = Z0;
-      if (k + 1 < L) {
-        const int32_t ib = fv[b + k + 1];
-        Bx = vx[ib] - sx; By = vy[ib] - sy; Bz = vz[ib] - sz;
-      }
-      // cell radius: fixed evaluation order, no FMA contraction; one
-      // correctly rounded square root of the largest square at the end
-      const double r2 = __dadd_rn(__dadd_rn(__dmul_rn(Ax, Ax), __dmul_rn(Ay, Ay)), __dmul_rn(Az, Az));
-      R2 = r2 > R2 ? r2 : R2;
-      // area vector (site-relative loop)
-      ax += Ay * Bz - Az * By;
-      ay += Az * Bx - Ax * Bz;
-      az += Ax * By - Ay * Bx;
-      // a zero-length edge gets R0s = m.y - delta*hinv = +huge: it never
-      // makes p 'outside' and its r0^2 + R0^2 is beyond the support
-      if (edge64) {
-        double rec[9];
-        edge_record64(P.x, P.y, P.z, dr, Ax, Ay, Az, Bx, By, Bz, rec);
-        double* E = edge64 + (b + k) * EDGE_STRIDE;
-        for (int j = 0; j < 9; ++j) E[j] = rec[j];
-        for (int j = 9; j < EDGE_STRIDE; ++j) E[j] = 0;
-      }
-      if (edge32) {
-        const float ax32 = (float)Ax, ay32 = (float)Ay, az32 = (float)Az;
-        const float bx32 = (float)Bx, by32 = (float)By, bz32 = (float)Bz;
-        float rec[9];
-        float ex = bx32 - ax32, ey = by32 - ay32, ez = bz32 - az32;
-        const float len = sqrtf(ex * ex + ey * ey + ez * ez);
-        if (len > 0.f) {
-          const float il = 1.0f / len;
-          ex *= il; ey *= il; ez *= il;
-          const float nx = (float)P.x, ny = (float)P.y, nz = (float)P.z;
-          const float gx = ny * ez - nz * ey, gy = nz * ex - nx * ez, gz = nx * ey - ny * ex;
-          rec[0] = gx; rec[1] = gy; rec[2] = gz;
-          rec[3] = gx * ax32 + gy * ay32 + gz * az32;
-          rec[4] = ex; rec[5] = ey; rec[6] = ez;
-          rec[7] = ex * ax32 + ey * ay32 + ez * az32;
-          rec[8] = ex * bx32 + ey * by32 + ez * bz32;
-        } else {
-          for (int j = 0; j < 9; ++j) rec[j] = 0.f;
-          rec[3] = -1e30f;
-        }
-        float* Ef = edge32 + (b + k) * EDGE_STRIDE;
-        for (int j = 0; j < 9; ++j) Ef[j] = rec[j];
-        for (int j = 9; j < EDGE_STRIDE; ++j) Ef[j] = 0;
-        if (fsph32) {
-          const float dx = ax32 - mx, dy = ay32 - my, dz = az32 - mz;
-          sr2 = fmaxf(sr2, dx * dx + dy * dy + dz * dz);
-        }
-      }
-      Ax = Bx; Ay = By; Az = Bz;
-    }
-    // bounding sphere: centre at the vertex mean, radius the largest vertex
-    // distance, rounded up (FP32 rounding is far inside the margin)
-    if (fsph32) fsph32[f] = make_float4(mx, my, mz, sqrtf(sr2) * (1.0f + 1e-5f) + 1e-12f);
-    const double area = 0.5 * (ax * P.x + ay * P.y + az * P.z);
-    V += dr * area / 3.0;
+    V += volf[f];
+    R2 = r2f[f] > R2 ? r2f[f] : R2;
   }
-  const double R = __dsqrt_rn(R2);
   vol[c] = V;
-  rad[c] = R;
+  rad[c] = __dsqrt_rn(R2);
   atomicMax(maxf, (int)(f1 - f0));
   atomicMax(maxl, (int)(fvo[f1] - fvo[f0]));
 }
@@ -237,9 +262,19 @@ int grid_prepare(map_ctx* ctx, const map_grid* in, PreparedGrid* g, cudaStream_t
   if (bad) return MAP_EINVAL;
   const int tpb = 128;
   const int64_t blocks = (nc + tpb - 1) / tpb;
-  prep_cells<<<(unsigned)blocks, tpb, 0, s>>>(nc, g->cell_face_off, g->face_vert_off, g->face_vert, g->face_plane,
-                                              g->vx, g->vy, g->vz, g->site, g->face64, g->face32, g->fsph32, g->edge64,
-                                              g->edge32, g->vol, g->rad, d_small, d_small + 1, d_status); ++ctx->launches;
+  int32_t* fcell;
+  double *volf, *r2f;
+  MAP_TRY(ensure_t(ctx, ctx->ws_grid[0], nf, &fcell));
+  MAP_TRY(ensure_t(ctx, ctx->ws_grid[1], nf, &volf));
+  MAP_TRY(ensure_t(ctx, ctx->ws_grid[2], nf, &r2f));
+  face_cells<<<(unsigned)blocks, tpb, 0, s>>>(nc, g->cell_face_off, fcell); ++ctx->launches;
+  CUDA_TRY(cudaGetLastError());
+  prep_faces<<<nblk(nf, tpb), tpb, 0, s>>>(nf, fcell, g->face_vert_off, g->face_vert, g->face_plane, g->vx, g->vy,
+                                           g->vz, g->site, g->face64, g->face32, g->fsph32, g->edge64, g->edge32,
+                                           volf, r2f, d_status); ++ctx->launches;
+  CUDA_TRY(cudaGetLastError());
+  prep_cells<<<(unsigned)blocks, tpb, 0, s>>>(nc, g->cell_face_off, g->face_vert_off, volf, r2f, g->vol, g->rad,
+                                              d_small, d_small + 1); ++ctx->launches;
   CUDA_TRY(cudaGetLastError());
   int64_t hs[4] = {0, 0, 0, 0};
   CUDA_TRY(cudaMemcpyAsync(hs, d_small, 32, cudaMemcpyDeviceToHost, s));

@@ -136,6 +136,7 @@ struct map_ctx {
   DevBuf ws_tree[32];
   DevBuf ws_pairs[13];
   DevBuf ws_misc[8];
+  DevBuf ws_grid[3];                   // grid preparation: face -> cell, per-face volume term and radius^2
   DevBuf cub_tmp;
   DevTree tree;
   // results of the last mapping call
