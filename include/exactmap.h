@@ -158,7 +158,8 @@ int map_grid_volumes(map_ctx* ctx, int handle, double* vol, void* stream);
  * Pair rule (makes pair lists reproducible; the paper is silent): (i,a) is
  * listed iff |r_a - s_i| < 2 h_a + R_i and n_f.r_a - d_f < 2 h_a for every
  * face f of cell i, both evaluated in FP64 in a fixed order without FMA.
- * Lists are sorted by particle index within each cell.
+ * The lists, as map_get_pairs / map_copy_pairs return them, are sorted by
+ * particle index within each cell.
  *
  * p->h must hold positive smoothing lengths.  Synchronises the stream once
  * (to size the pair list).  The pair list and the per-pair integrals stay in
@@ -167,15 +168,20 @@ int map_grid_volumes(map_ctx* ctx, int handle, double* vol, void* stream);
 int map_particles_to_cells(map_ctx* ctx, const map_particles* p, int grid, map_outputs* out, void* stream);
 
 /* Device pointers to the last call's pair list: pair_off (ncell+1 int64),
- * pair_idx (n_pairs int32 particle indices), pair_frac (n_pairs doubles,
- * f_ai).  Owned by the context; valid until the next mapping call. */
+ * pair_idx (n_pairs int32 particle indices, ascending within each cell),
+ * pair_frac (n_pairs doubles, f_ai).  Owned by the context; valid until the
+ * next mapping call.  The mapping itself keeps each cell's list in the order
+ * of its octree walk; the first request for the pointers after a mapping
+ * call sorts the lists in place on that call's stream and waits for it. */
 int map_get_pairs(map_ctx* ctx, const int64_t** pair_off, const int32_t** pair_idx, const double** pair_frac,
                   int64_t* n_pairs);
 
 /* Copy the last call's pair list into caller-owned device buffers:
- * pair_off (ncell+1 int64), pair_idx (n_pairs int32), pair_frac (n_pairs
- * doubles, may be NULL).  capacity = the length of pair_idx / pair_frac;
- * MAP_ECAPACITY if it is smaller than n_pairs.  Asynchronous on stream. */
+ * pair_off (ncell+1 int64), pair_idx (n_pairs int32, ascending within each
+ * cell), pair_frac (n_pairs doubles, may be NULL).  capacity = the length of
+ * pair_idx / pair_frac; MAP_ECAPACITY if it is smaller than n_pairs.  Sorts
+ * the lists first when map_get_pairs has not (waiting for the mapping call's
+ * stream), then copies asynchronously on stream. */
 int map_copy_pairs(map_ctx* ctx, int64_t* pair_off, int32_t* pair_idx, double* pair_frac, int64_t capacity,
                    void* stream);
 

@@ -217,6 +217,10 @@ int map_particles_to_cells(map_ctx* ctx, const map_particles* p, int handle, map
 int map_get_pairs(map_ctx* ctx, const int64_t** pair_off, const int32_t** pair_idx, const double** pair_frac,
                   int64_t* n_pairs) {
   if (!ctx) return MAP_EINVAL;
+  if (pair_off || pair_idx || pair_frac) {
+    CUDA_TRY(cudaSetDevice(ctx->device));
+    MAP_TRY(pairs_sort_lists(ctx, ctx->last_stream));
+  }
   if (pair_off) *pair_off = ctx->pair_off;
   if (pair_idx) *pair_idx = ctx->pair_idx;
   if (pair_frac) *pair_frac = ctx->pair_frac;
@@ -231,6 +235,10 @@ int map_copy_pairs(map_ctx* ctx, int64_t* pair_off, int32_t* pair_idx, double* p
   if (capacity < ctx->n_pairs) return MAP_ECAPACITY;
   CUDA_TRY(cudaSetDevice(ctx->device));
   cudaStream_t s = S(stream);
+  if (!ctx->pairs_sorted) {
+    // sort on the mapping call's stream, then order this copy after it
+    MAP_TRY(pairs_sort_lists(ctx, ctx->last_stream));
+  }
   CUDA_TRY(cudaMemcpyAsync(pair_off, ctx->pair_off, (ctx->last_ncell + 1) * sizeof(int64_t), cudaMemcpyDeviceToDevice, s));
   if (ctx->n_pairs > 0) {
     CUDA_TRY(cudaMemcpyAsync(pair_idx, ctx->pair_idx, ctx->n_pairs * sizeof(int32_t), cudaMemcpyDeviceToDevice, s));

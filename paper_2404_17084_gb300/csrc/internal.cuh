@@ -134,7 +134,7 @@ struct map_ctx {
   std::vector<DevBuf> grid_pool;       // buffers of released grids, reused by later uploads
   // workspace
   DevBuf ws_tree[32];
-  DevBuf ws_pairs[13];
+  DevBuf ws_pairs[14];
   DevBuf ws_misc[8];
   DevBuf ws_grid[3];                   // grid preparation: face -> cell, per-face volume term and radius^2
   DevBuf cub_tmp;
@@ -143,8 +143,9 @@ struct map_ctx {
   int64_t last_ncell = 0;
   int64_t n_pairs = 0;
   int64_t* pair_off = nullptr;
-  int32_t* pair_idx = nullptr;
+  int32_t* pair_idx = nullptr;        // in the walk's order until pairs_sort_lists
   double* pair_frac = nullptr;
+  bool pairs_sorted = false;          // lists sorted by particle index within each cell
   struct PairItem* items = nullptr;  // work items of the pair-integral kernel
   int64_t* item_off = nullptr;       // [ncell+1]: items of cell c
   double* partial = nullptr;         // per item: its pairs' mass
@@ -256,6 +257,8 @@ struct PairBufs {
 
 // Pair list of the grid against the current octree, and its work items.
 int pairs_build(map_ctx* ctx, const PreparedGrid* g, cudaStream_t s, const PairBufs& out = PairBufs());
+// Sorts the last call's lists (and f_ai) by particle index within each cell.
+int pairs_sort_lists(map_ctx* ctx, cudaStream_t s);
 int check_particles(map_ctx* ctx, const map_particles* p, bool need_m, bool need_h, cudaStream_t s);
 int integrals_run(map_ctx* ctx, const PreparedGrid* g, const map_particles* p, map_outputs* out, cudaStream_t s);
 SnapDesc make_desc(map_ctx* ctx, const PreparedGrid* g, const map_particles* p, const map_outputs* out,

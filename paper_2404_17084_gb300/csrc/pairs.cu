@@ -336,11 +336,15 @@ __global__ void item_fill(int64_t ncell, const int64_t* __restrict__ off, const 
   }
 }
 
-// Sort each cell's pair list (<= 1024 entries) in shared memory, one warp
-// per cell, bitonic; longer lists are left to the library segmented sort.
+// Sort each cell's pair list (<= 1024 entries) by particle index in shared
+// memory, one warp per cell, bitonic, carrying f_ai: the keys are (index,
+// position in the list) in 64 bits, and f_ai is gathered by position from a
+// copy.  Longer lists are left to the library segmented sort.
 __global__ void __launch_bounds__(128) sort_small_segments(int64_t ncell, const int64_t* __restrict__ off,
-                                                           const int32_t* __restrict__ in, int32_t* out) {
-  __shared__ int32_t buf[4][1024];
+                                                           const int32_t* __restrict__ idx_in,
+                                                           const double* __restrict__ frac_in, int32_t* idx,
+                                                           double* frac) {
+  __shared__ unsigned long long buf[4][1024];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int64_t c = blockIdx.x * 4LL + warp;
   if (c >= ncell) return;
@@ -349,22 +353,27 @@ __global__ void __launch_bounds__(128) sort_small_segments(int64_t ncell, const 
   if (L > 1024 || L == 0) return;
   int P = 1;
   while (P < L) P <<= 1;
-  int32_t* v = buf[warp];
-  for (int i = lane; i < P; i += 32) v[i] = i < L ? in[b + i] : 0x7fffffff;
+  unsigned long long* v = buf[warp];
+  for (int i = lane; i < P; i += 32)
+    v[i] = i < L ? ((unsigned long long)(uint32_t)idx_in[b + i] << 32) | (unsigned)i : ~0ULL;
   __syncwarp();
   for (int k = 2; k <= P; k <<= 1)
     for (int j = k >> 1; j > 0; j >>= 1) {
       for (int i = lane; i < P; i += 32) {
         const int ixj = i ^ j;
         if (ixj > i) {
-          const int32_t a0 = v[i], a1 = v[ixj];
+          const unsigned long long a0 = v[i], a1 = v[ixj];
           const bool up = (i & k) == 0;
           if ((a0 > a1) == up) { v[i] = a1; v[ixj] = a0; }
         }
       }
       __syncwarp();
     }
-  for (int i = lane; i < L; i += 32) out[b + i] = v[i];
+  for (int i = lane; i < L; i += 32) {
+    const unsigned long long key = v[i];
+    idx[b + i] = (int32_t)(key >> 32);
+    if (frac) frac[b + i] = frac_in[b + (int)(key & 0xffffffffu)];
+  }
 }
 
 __global__ void mark_large(int64_t ncell, const int64_t* __restrict__ off, int64_t* beg, int64_t* end,
@@ -438,42 +447,23 @@ int pairs_build(map_ctx* ctx, const PreparedGrid* g, cudaStream_t s, const PairB
   CUDA_TRY(cudaMemcpyAsync(ctx->h_scratch, off + nc, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
   CUDA_TRY(cudaStreamSynchronize(s));
   const int64_t np = ctx->h_scratch[0];
-  int32_t *raw, *sorted;
-  MAP_TRY(ensure_t(ctx, ctx->ws_pairs[2], np + 1, &raw));
-  MAP_TRY(ensure_t(ctx, out.idx ? *out.idx : ctx->ws_pairs[3], np + 1, &sorted));
+  // the list in the walk's order (deterministic); map_get_pairs and
+  // map_copy_pairs sort each cell's entries by particle index when read
+  int32_t* list;
+  MAP_TRY(ensure_t(ctx, out.idx ? *out.idx : ctx->ws_pairs[3], np + 1, &list));
   // rows that fit go straight to the list; the other cells are walked again
   int32_t* ovf;
   MAP_TRY(ensure_t(ctx, ctx->ws_pairs[9], nc, &ovf));
   unsigned long long* d_novf = ctx->d_counters + 6;
   CUDA_TRY(cudaMemsetAsync(d_novf, 0, sizeof(unsigned long long), s));
-  place_rows<<<nblk(nc * 32, tpb), tpb, 0, s>>>(nc, count, off, rows, raw, ovf, d_novf); ++ctx->launches;
+  place_rows<<<nblk(nc * 32, tpb), tpb, 0, s>>>(nc, count, off, rows, list, ovf, d_novf); ++ctx->launches;
   CUDA_TRY(cudaGetLastError());
   if (per_warp)
-    pair_walk_warp<true><<<(unsigned)((nc + 3) / 4), tpb, 0, s>>>(nc, ovf, PT, PG, nullptr, off, raw, d_novf);
+    pair_walk_warp<true><<<(unsigned)((nc + 3) / 4), tpb, 0, s>>>(nc, ovf, PT, PG, nullptr, off, list, d_novf);
   else
-    pair_traverse<true><<<nblk(nc, tpb), tpb, 0, s>>>(nc, ovf, PT, PG, nullptr, off, raw, d_novf);
+    pair_traverse<true><<<nblk(nc, tpb), tpb, 0, s>>>(nc, ovf, PT, PG, nullptr, off, list, d_novf);
   ++ctx->launches;
   CUDA_TRY(cudaGetLastError());
-  if (np > 0) {
-    sort_small_segments<<<nblk(nc, 4), 128, 0, s>>>(nc, off, raw, sorted); ++ctx->launches;
-    CUDA_TRY(cudaGetLastError());
-    int64_t *lb, *le;
-    MAP_TRY(ensure_t(ctx, ctx->ws_misc[1], nc + 1, &lb));
-    MAP_TRY(ensure_t(ctx, ctx->ws_misc[2], nc + 1, &le));
-    unsigned long long* d_nl = ctx->d_counters + 5;
-    CUDA_TRY(cudaMemsetAsync(d_nl, 0, sizeof(unsigned long long), s));
-    mark_large<<<nblk(nc, 256), 256, 0, s>>>(nc, off, lb, le, d_nl); ++ctx->launches;
-    CUDA_TRY(cudaGetLastError());
-    CUDA_TRY(cudaMemcpyAsync(ctx->h_scratch, d_nl, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
-    CUDA_TRY(cudaStreamSynchronize(s));
-    const int64_t nlarge = ctx->h_scratch[0];
-    if (nlarge > 0) {
-      tb = 0;
-      CUDA_TRY(cub::DeviceSegmentedSort::SortKeys(nullptr, tb, raw, sorted, np, nlarge, lb, le, s));
-      MAP_TRY(ctx_ensure(ctx, ctx->cub_tmp, tb));
-      CUDA_TRY(cub::DeviceSegmentedSort::SortKeys(ctx->cub_tmp.p, tb, raw, sorted, np, nlarge, lb, le, s));
-    }
-  }
   // work items: K blocks of 32 pairs at most, K chosen so that the launch has
   // at least 16 items per resident warp (4 warps x 6 CTAs per SM)
   const int64_t blocks = np / 32 + nc;
@@ -500,11 +490,59 @@ int pairs_build(map_ctx* ctx, const PreparedGrid* g, cudaStream_t s, const PairB
   CUDA_TRY(cudaGetLastError());
   ctx->n_pairs = np;
   ctx->pair_off = off;
-  ctx->pair_idx = sorted;
+  ctx->pair_idx = list;
+  ctx->pairs_sorted = false;
   ctx->items = items;
   ctx->item_off = ioff;
   ctx->partial = part;
   ctx->n_items = nitems;
   ctx->last_ncell = nc;
+  return MAP_OK;
+}
+
+// Sorts the last mapping call's lists by particle index within each cell,
+// f_ai alongside, in place (through copies), on stream s.
+int pairs_sort_lists(map_ctx* ctx, cudaStream_t s) {
+  if (ctx->pairs_sorted || !ctx->pair_off || !ctx->pair_idx) return MAP_OK;
+  const int64_t nc = ctx->last_ncell, np = ctx->n_pairs;
+  if (np > 0) {
+    int32_t* idx = const_cast<int32_t*>(ctx->pair_idx);
+    double* frac = ctx->pair_frac;
+    int32_t* idx_in;
+    double* frac_in = nullptr;
+    MAP_TRY(ensure_t(ctx, ctx->ws_pairs[2], np, &idx_in));
+    CUDA_TRY(cudaMemcpyAsync(idx_in, idx, np * sizeof(int32_t), cudaMemcpyDeviceToDevice, s));
+    if (frac) {
+      MAP_TRY(ensure_t(ctx, ctx->ws_pairs[13], np, &frac_in));
+      CUDA_TRY(cudaMemcpyAsync(frac_in, frac, np * sizeof(double), cudaMemcpyDeviceToDevice, s));
+    }
+    sort_small_segments<<<nblk(nc, 4), 128, 0, s>>>(nc, ctx->pair_off, idx_in, frac_in, idx, frac); ++ctx->launches;
+    CUDA_TRY(cudaGetLastError());
+    int64_t *lb, *le;
+    MAP_TRY(ensure_t(ctx, ctx->ws_misc[1], nc + 1, &lb));
+    MAP_TRY(ensure_t(ctx, ctx->ws_misc[2], nc + 1, &le));
+    unsigned long long* d_nl = ctx->d_counters + 5;
+    CUDA_TRY(cudaMemsetAsync(d_nl, 0, sizeof(unsigned long long), s));
+    mark_large<<<nblk(nc, 256), 256, 0, s>>>(nc, ctx->pair_off, lb, le, d_nl); ++ctx->launches;
+    CUDA_TRY(cudaGetLastError());
+    CUDA_TRY(cudaMemcpyAsync(ctx->h_scratch, d_nl, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+    CUDA_TRY(cudaStreamSynchronize(s));
+    const int64_t nlarge = ctx->h_scratch[0];
+    if (nlarge > 0) {
+      size_t tb = 0;
+      if (frac) {
+        CUDA_TRY(cub::DeviceSegmentedSort::SortPairs(nullptr, tb, idx_in, idx, frac_in, frac, np, nlarge, lb, le, s));
+        MAP_TRY(ctx_ensure(ctx, ctx->cub_tmp, tb));
+        CUDA_TRY(cub::DeviceSegmentedSort::SortPairs(ctx->cub_tmp.p, tb, idx_in, idx, frac_in, frac, np, nlarge, lb,
+                                                     le, s));
+      } else {
+        CUDA_TRY(cub::DeviceSegmentedSort::SortKeys(nullptr, tb, idx_in, idx, np, nlarge, lb, le, s));
+        MAP_TRY(ctx_ensure(ctx, ctx->cub_tmp, tb));
+        CUDA_TRY(cub::DeviceSegmentedSort::SortKeys(ctx->cub_tmp.p, tb, idx_in, idx, np, nlarge, lb, le, s));
+      }
+      CUDA_TRY(cudaStreamSynchronize(s));  // the lists are complete for any stream
+    }
+  }
+  ctx->pairs_sorted = true;
   return MAP_OK;
 }

@@ -214,8 +214,27 @@ def test_few_large_cells():
         out = gpu_map(g, p, h, prec)
         assert np.array_equal(out["off"], ref["off"])
         assert np.array_equal(out["idx"], ref["idx"])
+        assert np.abs(out["frac"] - ref["frac"]).max() < (1e-11 if prec == 0 else 5e-6)
         assert rel_err(out["mass"], ref["mass"]).max() < TOL[prec][0]
         assert abs(out["total"] - ref["mass"].sum()) < TOL[prec][1] * ref["mass"].sum()
+
+
+def test_lists_longer_than_the_shared_memory_sort():
+    """8 cells for 4096 particles: lists of more than 1024 pairs, which the
+    library segmented sort orders (with f_ai alongside) when they are read;
+    lists bit-equal, per-pair integrals and masses within the gates."""
+    lat = synth.lattice_particles(2, jitter=0.2, seed=11)
+    g = synth.voronoi(lat.pos())
+    p = synth.uniform_particles(4096, synth.BASE_SEED + 11)
+    h, _ = oracle_h(p)
+    ref = oracle.map_cells(g, p.x, p.y, p.z, p.m, h)
+    assert np.diff(ref["off"]).max() > 1024
+    for prec in (0, 1):
+        out = gpu_map(g, p, h, prec)
+        assert np.array_equal(out["off"], ref["off"])
+        assert np.array_equal(out["idx"], ref["idx"])
+        assert np.abs(out["frac"] - ref["frac"]).max() < (1e-11 if prec == 0 else 5e-6)
+        assert rel_err(out["mass"], ref["mass"]).max() < TOL[prec][0]
 
 
 def test_grid_upload_from_pinned_host_and_reuse(uniform4096):
