@@ -11,13 +11,17 @@
 // sorted particle arrays, so adjacent accepted leaves merge into one range,
 // and a node whose box lies wholly within R of the query box is taken as one
 // range without descending (the same candidates its leaves would give).  The
-// ranges are expanded into a list of positions that every Newton step of every
-// particle of the leaf sums over with all 32 lanes.  When an iterate outgrows
-// the list (2h > R), or the list is far larger than needed (R > 8h), it is
-// gathered again with R = 2.5 h.  A list longer than the buffer is expanded
-// and summed chunk by chunk; ranges beyond their own buffer come from a
-// resumable walk.  The Newton and bisection rules are those of the
-// per-particle definition; only the order of the sums differs.
+// ranges are expanded into a list of positions that the particles of the leaf
+// sum over with all 32 lanes.  A particle's first pass over that list also
+// keeps, in a list of its own, the candidates within min(2.5 h, R) of it;
+// its later steps sum over that shorter list while it covers the support
+// (2h <= 0.999 of its radius).  When an iterate outgrows the leaf's list
+// (2h > R), or the list is far larger than needed (R > 8h), it is gathered
+// again with R = 2.5 h; the next particle keeps whatever list covers it.  A
+// list longer than the buffer is expanded and summed chunk by chunk; ranges
+// beyond their own buffer come from a resumable walk.  The Newton and
+// bisection rules are those of the per-particle definition; only the order
+// of the sums differs.
 //
 // Mixed build: Newton sums and the Newton step in FP32 (on hi/lo-split
 // coordinates), stop at |dh| < 1e-6 h; bisection sums in FP64.  FP64 build: every sum in FP64 behind
@@ -32,6 +36,7 @@ constexpr int HS_CAP = 1024;    // candidate positions held per warp (a multiple
 // Depth-first stack: the tree has at most 22 levels and a popped node pushes at
 // most its 8 children, so at most 8 + 7 * 21 = 155 entries are live.
 constexpr int HS_STK = 160;
+constexpr int HS_PCAP = 512;   // one particle's own candidates (within 2.5 h of it)
 constexpr unsigned FULL = 0xffffffffu;
 
 struct HsTree {
@@ -45,6 +50,7 @@ struct HsTree {
 struct HsWarp {
   int2 rng[HS_RNG];
   int32_t cand[HS_CAP];
+  int32_t pcand[HS_PCAP];  // the current particle's candidates within pR of it
   int32_t stk[HS_STK];
 };
 
@@ -56,6 +62,9 @@ struct HsBuf {
   bool rng_done;    // the walk finished: the ranges cover every candidate
   int64_t total;    // positions in the ranges held
   bool expanded;    // cand holds all of them
+  int64_t pk;       // the particle whose own list pcand holds (-1: none)
+  double pR;        // its radius
+  int pn;           // its length
 };
 
 __device__ __forceinline__ double w_m4(double q) {
@@ -172,72 +181,80 @@ __device__ int walk_next(const HsTree& T, HsWarp& W, HsWalk& it, const float* q,
   return nr;
 }
 
-// Lane partial sums of w(q) and 3 w + q w'(q) over cand[0, cnt) for the
+// Lane partial sums of w(q) and 3 w + q w'(q) over list[0, cnt) for the
 // particle at sorted position k.  A lane takes positions lane, lane + 32, ...
 // in that order; two of them per pass, with the loads of both issued before
-// either term is added (the order of the additions is unchanged).
+// either term is added (the order of the additions is unchanged).  With keep
+// set, the candidates with q^2 < keep_q2 are also appended, in list order, to
+// keep[*nkeep ...] (*nkeep = -1 when they do not fit in HS_PCAP).
 template <bool F32>
-__device__ __forceinline__ void warp_accum(const HsTree& T, const HsWarp& W, int cnt, int64_t k, double h,
-                                           float& s32, float& d32, double& s64, double& d64) {
+__device__ __forceinline__ void warp_accum(const HsTree& T, const int32_t* list, int cnt, int64_t k, double h,
+                                           float& s32, float& d32, double& s64, double& d64, int32_t* keep,
+                                           float keep_q2, int* nkeep) {
   const int lane = threadIdx.x & 31;
+  const unsigned lt = (1u << lane) - 1u;
   const float* P0 = T.split + 6 * k;
   const float hx = P0[0], lx = P0[1], hy = P0[2], ly = P0[3], hz = P0[4], lz = P0[5];
   const float inv_hf = 1.0f / (float)h;
-  if (F32) {
-    auto term = [&](float2 a, float2 b, float2 c) {
-      const float dx = ((a.x - hx) + (a.y - lx)) * inv_hf;
-      const float dy = ((b.x - hy) + (b.y - ly)) * inv_hf;
-      const float dz = ((c.x - hz) + (c.y - lz)) * inv_hf;
-      const float q2 = dx * dx + dy * dy + dz * dz;
-      if (q2 >= 4.f) return;
+  double x = 0.0, y = 0.0, z = 0.0, R2 = 0.0, inv_h = 0.0;
+  if (!F32) {
+    x = T.xs[k]; y = T.ys[k]; z = T.zs[k];
+    R2 = 4.0 * h * h;
+    inv_h = 1.0 / h;
+  }
+  // q^2 of one candidate (FP32, as the screen), its terms added when inside
+  auto term = [&](int64_t c, float2 a, float2 b, float2 cc) -> float {
+    const float dx = ((a.x - hx) + (a.y - lx)) * inv_hf;
+    const float dy = ((b.x - hy) + (b.y - ly)) * inv_hf;
+    const float dz = ((cc.x - hz) + (cc.y - lz)) * inv_hf;
+    const float q2 = dx * dx + dy * dy + dz * dz;
+    if (F32) {
+      if (q2 >= 4.f) return q2;
       const float q = sqrtf(q2);
       float w, dwq;
       if (q < 1.f) { w = 1.f - 1.5f * q2 + 0.75f * q2 * q; dwq = -3.f * q2 + 2.25f * q2 * q; }
       else { const float t = 2.f - q; w = 0.25f * t * t * t; dwq = -0.75f * t * t * q; }
       s32 += w;
       d32 += 3.f * w + dwq;
-    };
-    int j = lane;
-    for (; j + 32 < cnt; j += 64) {
-      const float2* P = reinterpret_cast<const float2*>(T.split + 6 * (int64_t)W.cand[j]);
-      const float2* Q = reinterpret_cast<const float2*>(T.split + 6 * (int64_t)W.cand[j + 32]);
-      const float2 a = P[0], b = P[1], c = P[2], a1 = Q[0], b1 = Q[1], c1 = Q[2];
-      term(a, b, c);
-      term(a1, b1, c1);
-    }
-    if (j < cnt) {
-      const float2* P = reinterpret_cast<const float2*>(T.split + 6 * (int64_t)W.cand[j]);
-      term(P[0], P[1], P[2]);
-    }
-  } else {
-    const double x = T.xs[k], y = T.ys[k], z = T.zs[k];
-    const double R2 = 4.0 * h * h, inv_h = 1.0 / h;
-    auto term = [&](int64_t c, float2 a, float2 b, float2 cc) {
-      const float dx = ((a.x - hx) + (a.y - lx)) * inv_hf;
-      const float dy = ((b.x - hy) + (b.y - ly)) * inv_hf;
-      const float dz = ((cc.x - hz) + (cc.y - lz)) * inv_hf;
-      if (dx * dx + dy * dy + dz * dz > 4.00004f) return;  // FP32 screen, 1e-5 relative margin
+    } else {
+      if (q2 > 4.00004f) return q2;  // FP32 screen, 1e-5 relative margin
       const double ex = T.xs[c] - x, ey = T.ys[c] - y, ez = T.zs[c] - z;
       const double r2 = ex * ex + ey * ey + ez * ez;
-      if (r2 >= R2) return;
+      if (r2 >= R2) return q2;
       const double q = sqrt(r2) * inv_h;
       const double w = w_m4(q);
       s64 += w;
       d64 += 3.0 * w + q * dw_m4(q);
-    };
-    int j = lane;
-    for (; j + 32 < cnt; j += 64) {
-      const int64_t c0 = W.cand[j], c1 = W.cand[j + 32];
-      const float2* P = reinterpret_cast<const float2*>(T.split + 6 * c0);
-      const float2* Q = reinterpret_cast<const float2*>(T.split + 6 * c1);
-      const float2 a = P[0], b = P[1], c = P[2], a1 = Q[0], b1 = Q[1], cc1 = Q[2];
-      term(c0, a, b, c);
-      term(c1, a1, b1, cc1);
     }
-    if (j < cnt) {
-      const int64_t c0 = W.cand[j];
-      const float2* P = reinterpret_cast<const float2*>(T.split + 6 * c0);
-      term(c0, P[0], P[1], P[2]);
+    return q2;
+  };
+  auto append = [&](bool pred, int32_t v) {
+    const unsigned m = __ballot_sync(FULL, pred);
+    if (*nkeep < 0) return;
+    if (*nkeep + __popc(m) > HS_PCAP) { *nkeep = -1; return; }
+    if (pred) keep[*nkeep + __popc(m & lt)] = v;
+    *nkeep += __popc(m);
+  };
+  for (int j0 = 0; j0 < cnt; j0 += 64) {
+    const int j = j0 + lane, j1 = j + 32;
+    const bool v0 = j < cnt, v1 = j1 < cnt;
+    int32_t c0 = 0, c1 = 0;
+    float2 a = make_float2(0.f, 0.f), b = a, c = a, a1 = a, b1 = a, cc1 = a;
+    if (v0) {
+      c0 = list[j];
+      const float2* P = reinterpret_cast<const float2*>(T.split + 6 * (int64_t)c0);
+      a = P[0]; b = P[1]; c = P[2];
+    }
+    if (v1) {
+      c1 = list[j1];
+      const float2* Q = reinterpret_cast<const float2*>(T.split + 6 * (int64_t)c1);
+      a1 = Q[0]; b1 = Q[1]; cc1 = Q[2];
+    }
+    const float q0 = v0 ? term(c0, a, b, c) : 1e30f;
+    const float q1 = v1 ? term(c1, a1, b1, cc1) : 1e30f;
+    if (keep) {
+      append(v0 && q0 < keep_q2, c0);
+      append(v1 && q1 < keep_q2, c1);
     }
   }
 }
@@ -290,17 +307,40 @@ __device__ __forceinline__ void regather(const HsTree& T, HsWarp& W, HsBuf& B, d
 // n(h) and dn/dh for the particle at sorted position k (warp-uniform result).
 template <bool F32>
 __device__ void warp_density(const HsTree& T, HsWarp& W, HsBuf& B, int64_t k, double h, double& n, double& dn) {
-  if (2.0 * h > B.R || B.R > 8.0 * h) regather(T, W, B, 2.5 * h);
   float s32 = 0.f, d32 = 0.f;
   double s64 = 0.0, d64 = 0.0;
-  if (B.expanded) {
-    warp_accum<F32>(T, W, (int)B.total, k, h, s32, d32, s64, d64);
+  int none = 0;
+  if (B.pk == k && 2.0 * h <= 0.999 * B.pR && B.pR <= 8.0 * h) {
+    // the particle's own list covers its support at this h
+    warp_accum<F32>(T, W.pcand, B.pn, k, h, s32, d32, s64, d64, nullptr, 0.f, &none);
+  } else {
+    if (2.0 * h > B.R || B.R > 8.0 * h) regather(T, W, B, 2.5 * h);
+  }
+  if (B.pk == k && 2.0 * h <= 0.999 * B.pR && B.pR <= 8.0 * h) {
+    // done above
+  } else if (B.expanded) {
+    // the leaf's list; the first pass for a particle also keeps its own
+    // candidates within pR = min(2.5 h, R) of it for the next steps (the
+    // leaf's list holds every candidate within R of the leaf's box, so of
+    // the particle)
+    if (B.pk != k) {
+      const double pR = fmin(2.5 * h, B.R);
+      const float kq = (float)(pR / h);
+      int nk = 0;
+      warp_accum<F32>(T, W.cand, (int)B.total, k, h, s32, d32, s64, d64, W.pcand, kq * kq * 1.00001f, &nk);
+      __syncwarp();
+      B.pk = k;
+      B.pR = nk >= 0 ? pR : 0.0;  // 0: nothing kept (it did not fit)
+      B.pn = nk >= 0 ? nk : 0;
+    } else {
+      warp_accum<F32>(T, W.cand, (int)B.total, k, h, s32, d32, s64, d64, nullptr, 0.f, &none);
+    }
   } else if (B.rng_done) {
     // the ranges are complete but longer than the position buffer
     int r = 0, off = 0;
     while (r < B.nr) {
       const int c = expand(W, B.nr, r, off);
-      warp_accum<F32>(T, W, c, k, h, s32, d32, s64, d64);
+      warp_accum<F32>(T, W.cand, c, k, h, s32, d32, s64, d64, nullptr, 0.f, &none);
     }
   } else {
     // more ranges than their buffer: one resumable walk, range chunk by chunk
@@ -312,7 +352,7 @@ __device__ void warp_density(const HsTree& T, HsWarp& W, HsBuf& B, int64_t k, do
       int r = 0, off = 0;
       while (r < nr) {
         const int c = expand(W, nr, r, off);
-        warp_accum<F32>(T, W, c, k, h, s32, d32, s64, d64);
+        warp_accum<F32>(T, W.cand, c, k, h, s32, d32, s64, d64, nullptr, 0.f, &none);
       }
       if (walk_done(it)) break;
       nr = 0;
@@ -366,11 +406,15 @@ __global__ void __launch_bounds__(HS_WARPS * 32)
     B.total = 0;
     B.rng_done = false;
     B.expanded = false;
+    B.pk = -1;
+    B.pR = 0.0;
+    B.pn = 0;
     const double R0 = 2.5 * gmax;
-    double Rleaf = R0;
     for (int64_t k = a0; k < a1; ++k) {
-      // each particle starts from the leaf's list (regathered after a bisection grew it)
-      if (B.R != Rleaf) regather(T, W, B, Rleaf);
+      // the leaf's list for its first particle; later particles keep the
+      // list they find while it covers their support (warp_density
+      // regathers when 2h > R or R > 8h)
+      if (k == a0) regather(T, W, B, R0);
       const double g0 = h0s[k];
       const double lo = g0 / 16.0, hi = g0 * 16.0;
       double h = g0;
@@ -395,7 +439,6 @@ __global__ void __launch_bounds__(HS_WARPS * 32)
         if (fabs(hn - h) < tol * hn) { h = hn; ok = true; break; }
         h = hn;
       }
-      if (B.R > Rleaf && B.R <= 2.0 * R0) Rleaf = B.R;  // Newton grew the list: keep it for the leaf
       int r = 0;
       if (!ok) {
         auto g = [&](double hh) {
