@@ -153,11 +153,11 @@ OPS = {
 
 # DRAM traffic of the mixed pair-integral kernel per pair:
 # dram__bytes_read.sum + dram__bytes_write.sum of one ncu capture of the 2^16
-# clumpy case (400 MB for 7,813,809 pairs, profiles/pair_integrals_mixed_clumpy_65536.md),
+# clumpy case (397 MB for 7,813,809 pairs, profiles/pair_integrals_mixed_clumpy_65536.md),
 # scaled to a launch by its pair count (the kernel streams the same per-pair
 # data at any size).  It belongs to the kernel as captured: set it to None
 # when the kernel changes.
-INTEGRAL_DRAM_BYTES_PER_PAIR = 51.1
+INTEGRAL_DRAM_BYTES_PER_PAIR = 50.9
 
 
 def counted_work(L, torch, precision, device, grids, dev, parts):
