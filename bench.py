@@ -393,8 +393,7 @@ def run_batch(args):
     totals = torch.empty(len(snaps), dtype=torch.float64, device=dev)
 
     def step():
-        for hp in hparts:
-            L.solve_h(ctx, hp)
+        L.solve_h_batch(ctx, hparts)
         L.map_batch(ctx, parts, handles, mass, totals=totals)
 
     def barrier():

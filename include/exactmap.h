@@ -211,8 +211,10 @@ int map_get_timing(map_ctx* ctx, float* ms);
  * one persistent launch).  Snapshot j is the particle set parts[j] (m, h
  * given) on the resident grid grids[j], with outputs outs[j], exactly as in
  * map_particles_to_cells; every snapshot's result equals what that call
- * gives.  Octree and pair list are built snapshot by snapshot (synchronising
- * the stream); the pair integrals of all snapshots then run in ONE launch of
+ * gives.  Octrees and pair lists are built by the context's workers (worker
+ * contexts with their own streams and host threads, several snapshots at
+ * once, largest first; the workspace they hold is not counted against the
+ * HBM budget); the pair integrals of all snapshots then run in ONE launch of
  * the persistent kernel, whose device work queue hands out the cells of every
  * snapshot, largest pair count first.  That launch, with its descriptor
  * upload and the per-snapshot sums, is captured in a CUDA graph and replayed
@@ -314,6 +316,15 @@ void map_server_destroy(map_server* srv);
  * Writes p->h; route (optional, n int32) receives 0 Newton, 1 bisection,
  * 2 estimate.  Errors: MAP_EINVAL, MAP_ENOMEM, MAP_ECUDA. */
 int solve_h(map_ctx* ctx, map_particles* p, int32_t* route, void* stream);
+
+/* solve_h for nsnap independent particle sets (Eq. 7-9 for each; the
+ * configuration of many uneven instances): parts[j].h receives exactly what
+ * solve_h on parts[j] alone gives; routes (NULL, or nsnap pointers each NULL
+ * or n int32) as in solve_h.  The sets are solved by the context's workers,
+ * several at once, each on its own stream, ordered after and before
+ * `stream`; the call returns when all are done.  Errors: MAP_EINVAL,
+ * MAP_ENOMEM, MAP_ECUDA (the first one met). */
+int solve_h_batch(map_ctx* ctx, int nsnap, map_particles* parts, int32_t* const* routes, void* stream);
 
 
 /* solve_h for callers that cannot allocate device memory (a process that has

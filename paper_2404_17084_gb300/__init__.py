@@ -83,6 +83,7 @@ _lib.map_get_stats.argtypes = [_P, ctypes.POINTER(map_stats)]
 _lib.map_get_work.argtypes = [_P, ctypes.POINTER(_I64), ctypes.POINTER(_I64)]
 _lib.map_get_timing.argtypes = [_P, ctypes.POINTER(ctypes.c_float)]
 _lib.solve_h.argtypes = [_P, ctypes.POINTER(map_particles), _P, _P]
+_lib.solve_h_batch.argtypes = [_P, ctypes.c_int, ctypes.POINTER(map_particles), ctypes.POINTER(_P), _P]
 _lib.build_pseudo_particles.argtypes = [_P, ctypes.POINTER(map_particles), ctypes.POINTER(ctypes.c_double),
                                         ctypes.c_int, ctypes.POINTER(map_particles), _P, _P,
                                         ctypes.POINTER(_I64), _P]
@@ -120,7 +121,7 @@ _lib.map_get_autotune.argtypes = [_P, ctypes.POINTER(ctypes.c_int), ctypes.POINT
                                   ctypes.POINTER(ctypes.c_int)]
 for _name in ("map_init", "map_grid_upload", "map_grid_release", "map_grid_volumes", "map_particles_to_cells",
               "map_get_pairs", "map_copy_pairs", "map_get_stats", "map_get_work", "map_get_timing", "solve_h",
-              "build_pseudo_particles", "map_batch", "map_get_autotune"):
+              "build_pseudo_particles", "map_batch", "map_get_autotune", "solve_h_batch"):
     getattr(_lib, _name).restype = ctypes.c_int
 
 
@@ -356,6 +357,17 @@ def map_get_timing(ctx):
 
 def solve_h(ctx, p: map_particles, route=None, stream=None) -> None:
     _check(_lib.solve_h(ctx, ctypes.byref(p), _ptr(route), _stream(stream)), "solve_h")
+
+
+def solve_h_batch(ctx, parts, routes=None, stream=None) -> None:
+    """solve_h for a list of particle sets (map_particles) at once; routes:
+    None or a list of int32 CUDA tensors / None."""
+    n = len(parts)
+    P = (map_particles * n)(*parts)
+    R = None
+    if routes is not None:
+        R = (_P * n)(*[_ptr(r) if r is not None else None for r in routes])
+    _check(_lib.solve_h_batch(ctx, n, P, R, _stream(stream)), "solve_h_batch")
 
 
 def build_pseudo_particles(ctx, full: map_particles, src, out: map_particles, kind=None, ident=None, stream=None):

@@ -147,6 +147,7 @@ void map_destroy(map_ctx* ctx) {
     for (auto& b : *v)
       if (b.p) cudaFree(b.p);
   if (ctx->bexec) cudaGraphExecDestroy(ctx->bexec);
+  destroy_workers(ctx);
   for (auto& e : ctx->bev) if (e) cudaEventDestroy(e);
   if (ctx->bstream) cudaStreamDestroy(ctx->bstream);
   delete ctx;

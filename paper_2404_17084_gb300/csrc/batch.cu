@@ -1,10 +1,14 @@
 // Batched mapping: many independent snapshots (particle set + resident grid)
 // in one persistent pair-integral launch.
 //
-// Each snapshot's octree and pair list are built in turn (these steps size
-// their buffers from device counts, so they synchronise the stream).  The
-// pair lists are written to per-snapshot buffers of the context, reused by
-// later batches of the same shape.  The pair
+// Each snapshot's octree and pair list are built by one of the context's
+// workers: BATCH_WORKERS worker contexts, each with its own workspace,
+// stream and host thread, take the snapshots largest first (these steps size
+// their buffers from device counts and so synchronise their stream; running
+// several at once keeps the GPU busy between those points).  The pair lists
+// are written to per-snapshot buffers of the context, reused by later
+// batches of the same shape.  solve_h_batch solves the snapshots' smoothing
+// lengths on the same workers.  The pair
 // integrals of every snapshot then run in ONE launch of the persistent
 // kernel: its device work queue hands out the cells of all snapshots, the
 // snapshots laid out largest pair count first (longest-processing-time
@@ -21,8 +25,10 @@
 // the context.  Each shape is deterministic; two shapes are separate
 // compilations of the same source and may round FP32 differently.
 #include <algorithm>
+#include <atomic>
 #include <cstring>
 #include <numeric>
+#include <thread>
 
 #include "internal.cuh"
 
@@ -36,6 +42,29 @@ __global__ void sum_totals(int n, const double* __restrict__ v, double* out) {
   }
 }
 
+constexpr int BATCH_WORKERS = 4;
+
+int ensure_workers(map_ctx* ctx) {
+  if (!ctx->wev) CUDA_TRY(cudaEventCreateWithFlags(&ctx->wev, cudaEventDisableTiming));
+  while ((int)ctx->workers.size() < BATCH_WORKERS) {
+    map_config c = ctx->cfg;
+    c.autotune = 0;
+    c.count_work = 0;
+    c.hbm_budget = 0;  // the workers' workspace is not counted against the budget
+    BatchWorker w;
+    MAP_TRY(map_init(&w.ctx, &c));
+    if (cudaStreamCreateWithFlags(&w.stream, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&w.done, cudaEventDisableTiming) != cudaSuccess) {
+      cudaGetLastError();
+      if (w.stream) cudaStreamDestroy(w.stream);
+      map_destroy(w.ctx);
+      return MAP_ECUDA;
+    }
+    ctx->workers.push_back(w);
+  }
+  return MAP_OK;
+}
+
 int ensure_stream(map_ctx* ctx) {
   if (!ctx->bstream) CUDA_TRY(cudaStreamCreateWithFlags(&ctx->bstream, cudaStreamNonBlocking));
   for (auto& e : ctx->bev)
@@ -44,6 +73,54 @@ int ensure_stream(map_ctx* ctx) {
 }
 
 }  // namespace
+
+void destroy_workers(map_ctx* ctx) {
+  for (BatchWorker& w : ctx->workers) {
+    if (w.stream) cudaStreamSynchronize(w.stream);
+    if (w.done) cudaEventDestroy(w.done);
+    if (w.stream) cudaStreamDestroy(w.stream);
+    map_destroy(w.ctx);
+  }
+  ctx->workers.clear();
+  if (ctx->wev) cudaEventDestroy(ctx->wev);
+  ctx->wev = nullptr;
+}
+
+int run_on_workers(map_ctx* ctx, int n, const int* order, cudaStream_t s,
+                   const std::function<int(BatchWorker&, int)>& fn) {
+  MAP_TRY(ensure_workers(ctx));
+  CUDA_TRY(cudaEventRecord(ctx->wev, s));
+  std::vector<int64_t> l0(ctx->workers.size());
+  for (size_t w = 0; w < ctx->workers.size(); ++w) {
+    CUDA_TRY(cudaStreamWaitEvent(ctx->workers[w].stream, ctx->wev, 0));
+    l0[w] = ctx->workers[w].ctx->launches;
+  }
+  std::atomic<int> next{0}, err{MAP_OK};
+  std::vector<std::thread> th;
+  for (size_t w = 0; w < ctx->workers.size(); ++w)
+    th.emplace_back([&, w]() {
+      BatchWorker& W = ctx->workers[w];
+      if (cudaSetDevice(ctx->device) != cudaSuccess) { int e = MAP_OK; err.compare_exchange_strong(e, MAP_ECUDA); }
+      for (;;) {
+        if (err.load() != MAP_OK) break;
+        const int i = next.fetch_add(1);
+        if (i >= n) break;
+        const int r = fn(W, order[i]);
+        if (r != MAP_OK) {
+          int e = MAP_OK;
+          err.compare_exchange_strong(e, r);
+          break;
+        }
+      }
+      cudaEventRecord(W.done, W.stream);
+    });
+  for (auto& t : th) t.join();
+  for (size_t w = 0; w < ctx->workers.size(); ++w) {
+    CUDA_TRY(cudaStreamWaitEvent(s, ctx->workers[w].done, 0));
+    ctx->launches += ctx->workers[w].ctx->launches - l0[w];
+  }
+  return err.load();
+}
 
 // Times each launch shape of the integral kernel on this batch (descriptors
 // already on the device) and records the fastest.
@@ -73,7 +150,34 @@ int integrals_autotune(map_ctx* ctx, const BatchArgs& B, cudaStream_t s) {
   return MAP_OK;
 }
 
+// The host-side part of check_particles (pointers and count), for a batch
+// before its workers start.
+static bool check_sizes(const map_particles* p) {
+  return p && p->n > 0 && p->n < (int64_t)INT32_MAX && p->x && p->y && p->z;
+}
+
 extern "C" {
+
+int solve_h_batch(map_ctx* ctx, int nsnap, map_particles* parts, int32_t* const* routes, void* stream) {
+  if (!ctx || nsnap < 1 || !parts) return MAP_EINVAL;
+  for (int j = 0; j < nsnap; ++j)
+    if (!check_sizes(&parts[j]) || !parts[j].h) return MAP_EINVAL;
+  CUDA_TRY(cudaSetDevice(ctx->device));
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  std::vector<int> big(nsnap);
+  std::iota(big.begin(), big.end(), 0);
+  std::stable_sort(big.begin(), big.end(), [&](int a, int b) { return parts[a].n > parts[b].n; });
+  phase_begin(ctx, 3, s);
+  const int rc = run_on_workers(ctx, nsnap, big.data(), s, [&](BatchWorker& W, int j) -> int {
+    map_particles* p = &parts[j];
+    MAP_TRY(check_particles(W.ctx, p, false, false, W.stream));
+    return h_solve_run(W.ctx, p->x, p->y, p->z, p->n, p->h, routes ? routes[j] : nullptr, nullptr, W.stream);
+  });
+  phase_end(ctx, 3, s);
+  ctx->last_stream = s;
+  return rc;
+}
+
 
 int map_batch(map_ctx* ctx, int nsnap, const map_particles* parts, const int* grids, const map_outputs* outs,
               double* totals, void* stream) {
@@ -92,16 +196,26 @@ int map_batch(map_ctx* ctx, int nsnap, const map_particles* parts, const int* gr
     ctx->batch_ioff.resize(nsnap);
     ctx->batch_part.resize(nsnap);
   }
-  // 1. octree and pair list per snapshot, kept in the batch slots
+  // 1. octree and pair list per snapshot, kept in the batch slots, built on
+  // the workers (largest snapshots first)
   std::vector<SnapDesc> hd(nsnap);
   std::vector<int64_t> np(nsnap);
   int64_t n_pairs = 0, total = 0;
+  for (int j = 0; j < nsnap; ++j)
+    if (!check_sizes(&parts[j])) return MAP_EINVAL;
+  std::vector<int> big(nsnap);
+  std::iota(big.begin(), big.end(), 0);
+  std::stable_sort(big.begin(), big.end(), [&](int a, int b) { return parts[a].n > parts[b].n; });
+  size_t slot_bytes0 = 0;
+  for (auto* v : {&ctx->batch_off, &ctx->batch_idx, &ctx->batch_itm, &ctx->batch_ioff, &ctx->batch_part})
+    for (int j = 0; j < nsnap; ++j) slot_bytes0 += (*v)[j].cap;
   phase_begin(ctx, 1, s);
-  for (int j = 0; j < nsnap; ++j) {
+  int rc = run_on_workers(ctx, nsnap, big.data(), s, [&](BatchWorker& W, int j) -> int {
+    map_ctx* wc = W.ctx;
     const map_particles* p = &parts[j];
-    MAP_TRY(check_particles(ctx, p, true, true, s));
+    MAP_TRY(check_particles(wc, p, true, true, W.stream));
     const PreparedGrid* g = ctx->grids[grids[j]];
-    MAP_TRY(tree_build(ctx, p->x, p->y, p->z, p->m, p->h, p->n, s));
+    MAP_TRY(tree_build(wc, p->x, p->y, p->z, p->m, p->h, p->n, W.stream));
     // the list goes straight to the snapshot's slot (reused by later batches)
     PairBufs pb;
     pb.off = &ctx->batch_off[j];
@@ -109,11 +223,20 @@ int map_batch(map_ctx* ctx, int nsnap, const map_particles* parts, const int* gr
     pb.items = &ctx->batch_itm[j];
     pb.ioff = &ctx->batch_ioff[j];
     pb.part = &ctx->batch_part[j];
-    MAP_TRY(pairs_build(ctx, g, s, pb));
-    hd[j] = make_desc(ctx, g, p, &outs[j], ctx->pair_off, ctx->pair_idx, nullptr, j);
-    np[j] = ctx->n_pairs;
+    MAP_TRY(pairs_build(wc, g, W.stream, pb));
+    hd[j] = make_desc(wc, g, p, &outs[j], wc->pair_off, wc->pair_idx, nullptr, j);
+    np[j] = wc->n_pairs;
+    return MAP_OK;
+  });
+  // the slots belong to this context: count their growth here
+  size_t slot_bytes1 = 0;
+  for (auto* v : {&ctx->batch_off, &ctx->batch_idx, &ctx->batch_itm, &ctx->batch_ioff, &ctx->batch_part})
+    for (int j = 0; j < nsnap; ++j) slot_bytes1 += (*v)[j].cap;
+  ctx->bytes_in_use += slot_bytes1 - slot_bytes0;
+  if (rc != MAP_OK) return rc;
+  for (int j = 0; j < nsnap; ++j) {
     n_pairs += np[j];
-    total += g->ncell;
+    total += ctx->grids[grids[j]]->ncell;
   }
   phase_end(ctx, 1, s);
   ctx->pair_off = nullptr;  // no single pair list describes a batch

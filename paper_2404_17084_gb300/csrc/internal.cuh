@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <functional>
 #include <vector>
 
 #include "../../include/exactmap.h"
@@ -125,6 +126,15 @@ struct PairItem {
   int32_t cnt;
 };
 
+// A worker of a context: its own context (octree, pair-list and h-solve
+// workspace), stream and completion event, for the per-snapshot preparation
+// of batches.
+struct BatchWorker {
+  map_ctx* ctx = nullptr;
+  cudaStream_t stream = nullptr;
+  cudaEvent_t done = nullptr;
+};
+
 struct map_ctx {
   map_config cfg;
   int device = 0;
@@ -175,6 +185,8 @@ struct map_ctx {
   cudaGraphExec_t bexec = nullptr;
   std::vector<unsigned char> bsig;
   int64_t bexec_launches = 0;  // kernels per replay of bexec
+  std::vector<BatchWorker> workers;  // created by the first batch call that uses them
+  cudaEvent_t wev = nullptr;         // the caller's stream, before the workers start
 };
 
 inline void phase_begin(map_ctx* ctx, int k, cudaStream_t s) { if (ctx->ev[2 * k]) cudaEventRecord(ctx->ev[2 * k], s); }
@@ -268,6 +280,12 @@ int integrals_upload(map_ctx* ctx, const SnapDesc* h_desc, const int64_t* h_ibas
 int integrals_enqueue(map_ctx* ctx, const BatchArgs& B, int variant, cudaStream_t s);
 int integrals_sum(map_ctx* ctx, const SnapDesc* d_desc, int nsnap, double* totals, cudaStream_t s);
 int integrals_autotune(map_ctx* ctx, const BatchArgs& B, cudaStream_t s);
+// Runs fn(worker, j) for j = order[0..n) on the context's workers, each on
+// its own stream and host thread, after the work queued on s; s then waits
+// for all of them.  Returns the first error.  Work is handed out in `order`.
+int run_on_workers(map_ctx* ctx, int n, const int* order, cudaStream_t s,
+                   const std::function<int(BatchWorker&, int)>& fn);
+void destroy_workers(map_ctx* ctx);
 int h_solve_run(map_ctx* ctx, const double* x, const double* y, const double* z, int64_t n, double* h,
                 int32_t* route, const double* h0_override, cudaStream_t s);
 int pseudo_run(map_ctx* ctx, const map_particles* full, const double* src, int nsrc, map_particles* out,

@@ -86,3 +86,27 @@ def test_batch_fp64_vs_oracle(snapshots):
         cells = sample_cells(g.ncell, 60, j)
         ref = oracle.map_cells(g, p.x, p.y, p.z, p.m, h, cells=cells)
         assert rel_err(masses[j][cells], ref["mass"]).max() < 1e-9
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_solve_h_batch_equals_single(snapshots, precision):
+    """solve_h_batch (the sets solved by the context's workers, several at
+    once) gives every set the h and routes of solve_h on it alone, bit for
+    bit."""
+    L = lib()
+    ctx = L.map_init(L.map_config_default(precision=precision))
+    try:
+        sets = [dev_particles(p) for _, p, _, _ in snapshots]
+        routes = [torch.empty(p.n, dtype=torch.int32, device="cuda") for _, p, _, _ in snapshots]
+        L.solve_h_batch(ctx, [L.make_particles(x, y, z, None, h) for x, y, z, _, h in sets], routes)
+        torch.cuda.synchronize()
+        got = [(t[4].cpu().numpy().copy(), r.cpu().numpy().copy()) for t, r in zip(sets, routes)]
+        for j, (x, y, z, _, _) in enumerate(sets):
+            h1 = torch.empty_like(x)
+            r1 = torch.empty_like(routes[j])
+            L.solve_h(ctx, L.make_particles(x, y, z, None, h1), r1)
+            torch.cuda.synchronize()
+            assert np.array_equal(got[j][0], h1.cpu().numpy()), j
+            assert np.array_equal(got[j][1], r1.cpu().numpy()), j
+    finally:
+        L.map_destroy(ctx)
