@@ -42,7 +42,7 @@ __global__ void sum_totals(int n, const double* __restrict__ v, double* out) {
   }
 }
 
-constexpr int BATCH_WORKERS = 4;
+constexpr int BATCH_WORKERS = 8;
 
 int ensure_workers(map_ctx* ctx) {
   if (!ctx->wev) CUDA_TRY(cudaEventCreateWithFlags(&ctx->wev, cudaEventDisableTiming));
