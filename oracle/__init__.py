@@ -11,6 +11,7 @@ Routes (see the C file's header for the full statement):
     with each pyramid integral I(r0, R0, phi) evaluated by adaptive
     Gauss-Kronrod quadrature of its 1-D reduction;
   * cell mass and density: Eq. (1)-(3), long double sums;
+  * inverse mapping: Eq. (4), a plain numpy sum over the pair list;
   * smoothing lengths: Eq. (7)-(9), Newton -> bisection -> estimate;
   * octree, adaptive walk: Section III-A/B, Eq. (5).
 """
@@ -167,6 +168,21 @@ def map_cells(grid, x, y, z, m, h, cells=None, off=None, idx=None, want_frac=Tru
     lib.or_map_cells(*[_ptr(a) for a in g], _ptr(cells), len(cells), _ptr(x), _ptr(y), _ptr(z), _ptr(m), _ptr(h),
                      _ptr(off), _ptr(idx), _ptr(frac), _ptr(mass), _ptr(vol), _ptr(rho), _nthreads(nthreads))
     return dict(cells=cells, off=off, idx=idx, frac=frac, mass=mass, vol=vol, rho=rho)
+
+
+def inverse_map(off, idx, frac, cell_value, n):
+    """Eq. (4): out[a] = sum over the pairs (i, a) of cell_value[i] * f_ai.
+
+    off, idx, frac: a cell-major pair list (off[k]..off[k+1] are the pairs of
+    the k-th listed cell, whose value is cell_value[k]); n particles.  Each
+    product is rounded once; np.add.at adds them into each particle's slot
+    one at a time in list order, from +0."""
+    off = np.asarray(off, np.int64)
+    cell = np.repeat(np.arange(len(off) - 1), np.diff(off))
+    terms = np.asarray(cell_value, np.float64)[cell] * np.asarray(frac, np.float64)
+    out = np.zeros(n)
+    np.add.at(out, np.asarray(idx, np.int64), terms)
+    return out
 
 
 # ----------------------------------------------------------------- smoothing lengths

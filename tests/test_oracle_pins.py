@@ -346,3 +346,90 @@ def test_octree_invariants_and_walk_partition():
     acc, opened = t.walk(src, 0.0)
     assert np.all(t.size[acc] == 0.0)
     assert sum(int(t.count[i]) for i in opened) + sum(int(t.count[i]) for i in acc) == p.n
+
+
+# ----------------------------------------------------------------- inverse mapping (Eq. 4)
+
+def test_inverse_map_octants_by_symmetry():
+    """Eight octant cells (a 2x2x2 lattice of sites).  The kernel is
+    spherically symmetric, so a particle where k cell boundaries meet puts the
+    same share of its support into each cell it touches, and the share the
+    cube's walls cut off is fixed by symmetry too: at the cube's centre 1/8 in
+    every cell, on an edge between two cells 1/2 each, on a wall 1/2 of the
+    support inside the cube, at a corner 1/8.  Eq. 4 must then return those
+    weighted means of the cell values."""
+    sites = synth.lattice_particles(2)
+    g = synth.voronoi(sites.pos(), nthreads=1)
+    v = np.array([0.9, 0.1, 0.35, 0.6, 0.05, 0.8, 0.45, 0.2])  # cell k = 4 ix + 2 iy + iz
+    pos = np.array([[0.5, 0.5, 0.5],    # all eight cells, 1/8 each
+                    [0.5, 0.5, 0.2],    # the four cells with iz = 0, 1/4 each
+                    [0.5, 0.2, 0.2],    # cells (0,0,0) and (1,0,0), 1/2 each
+                    [0.2, 0.2, 0.2],    # cell (0,0,0) alone
+                    [0.0, 0.0, 0.0],    # cube corner: 1/8 of the support, in cell (0,0,0)
+                    [0.0, 0.5, 0.5],    # wall x = 0 at the cells' common edge: 1/8 in each ix = 0 cell
+                    [0.5, 0.5, 1.0]])   # wall z = 1: 1/8 in each iz = 1 cell
+    want = np.array([v.mean(), v[[0, 2, 4, 6]].mean(), (v[0] + v[4]) / 2, v[0], v[0] / 8,
+                     v[[0, 1, 2, 3]].sum() / 8, v[[1, 3, 5, 7]].sum() / 8])
+    h = np.full(len(pos), 0.1)
+    res = oracle.map_cells(g, pos[:, 0], pos[:, 1], pos[:, 2], np.ones(len(pos)), h, nthreads=1)
+    got = oracle.inverse_map(res["off"], res["idx"], res["frac"], v, len(pos))
+    assert np.max(np.abs(got - want)) < 1e-12, got - want
+
+
+def test_inverse_map_constant_and_linear_fields():
+    """Cubic lattice, particles at the sites: a constant cell value comes back
+    unchanged on every particle whose support lies inside the cube (the
+    weights sum to 1, Eq. 1-3 mass conservation); a linear field x_i of the
+    sites comes back as the particle's own x (the lattice is symmetric about
+    every site, so the weights' first moment is the particle position)."""
+    n = 8
+    p = synth.lattice_particles(n)
+    g = synth.voronoi(p.pos(), nthreads=1)
+    h = np.full(p.n, 1.2 / n)
+    res = oracle.map_cells(g, p.x, p.y, p.z, p.m, h)
+    interior = np.all((p.pos() >= 2 * h[:, None]) & (p.pos() <= 1 - 2 * h[:, None]), axis=1)
+    assert interior.sum() >= 8
+    const = oracle.inverse_map(res["off"], res["idx"], res["frac"], np.full(g.ncell, 0.37), p.n)
+    assert np.max(np.abs(const[interior] - 0.37)) < 1e-12
+    assert np.all(const <= 0.37 + 1e-12)  # wall particles lose weight outside the cube
+    lin = oracle.inverse_map(res["off"], res["idx"], res["frac"], g.site[:, 0], p.n)
+    assert np.max(np.abs(lin[interior] - p.x[interior])) < 1e-12
+
+
+def test_inverse_map_conserves_the_weighted_total():
+    """sum_a m_a f_ion,a = sum_i f_ion,i M_i (the ionised mass is the same on
+    the particles and on the grid), with M_i the oracle's cell masses from
+    its own long double sums; a random field on a random Voronoi grid."""
+    p = synth.uniform_particles(400, 11)
+    g = synth.voronoi(p.pos(), nthreads=1)
+    rng = np.random.default_rng(3)
+    m = rng.uniform(0.5, 1.5, p.n) / p.n
+    h = rng.uniform(0.06, 0.14, p.n)
+    res = oracle.map_cells(g, p.x, p.y, p.z, m, h)
+    f_ion = rng.random(g.ncell)
+    got = oracle.inverse_map(res["off"], res["idx"], res["frac"], f_ion, p.n)
+    assert abs(np.dot(m, got) - np.dot(f_ion, res["mass"])) < 1e-13
+    # every term is non-negative, so no particle exceeds the largest value
+    assert np.all(got >= 0) and np.all(got <= f_ion.max() * (1 + 1e-12))
+
+
+def test_inverse_map_brute_force_tiny():
+    """Four particles, 27 cells: the sum written out as a double loop over
+    particles and cells with f_ai taken one pair at a time from the oracle's
+    single-pair integral, against the pair-list sum (tolerance: the order of
+    the additions)."""
+    p = synth.uniform_particles(27, 21)
+    g = synth.voronoi(p.pos(), nthreads=1)
+    pos = np.array([[0.3, 0.4, 0.5], [0.05, 0.9, 0.5], [0.7, 0.2, 0.8], [0.5, 0.5, 0.5]])
+    h = np.array([0.2, 0.15, 0.1, 0.3])
+    v = np.random.default_rng(5).random(g.ncell)
+    res = oracle.map_cells(g, pos[:, 0], pos[:, 1], pos[:, 2], np.ones(4), h, nthreads=1)
+    got = oracle.inverse_map(res["off"], res["idx"], res["frac"], v, 4)
+    for a in range(4):
+        acc = 0.0
+        for i in range(g.ncell):
+            r = oracle.map_cells(g, pos[a:a + 1, 0], pos[a:a + 1, 1], pos[a:a + 1, 2], [1.0], h[a:a + 1],
+                                 cells=[i], off=np.array([0, 1], np.int64), idx=np.array([0], np.int32),
+                                 nthreads=1)
+            acc += v[i] * r["frac"][0]
+        assert abs(got[a] - acc) < 1e-14 * max(1.0, abs(acc)), (a, got[a], acc)
