@@ -268,6 +268,7 @@ def run_ours(args):
     n_pairs = st.n_pairs
     mass_mixed = mass.cpu().numpy()
     h_mixed = h.cpu().numpy()
+    inverse = inverse_run(L, torch, ctx, g, args.n, n_pairs, mass, m, dev)
     terms, work = counted_work(L, torch, L.MAP_MIXED, local, g, dev, L.make_particles(x, y, z, m, h))
     # ---- e2e through the public API with host buffers
     e2e = None if args.skip_e2e else e2e_run(L, torch, ctx, p, g, dev, args, barrier, world)
@@ -335,6 +336,7 @@ def run_ours(args):
                      "shapes": ["4 warps/CTA, 5 CTAs/SM", "4 warps/CTA, 4 CTAs/SM", "4 warps/CTA, 6 CTAs/SM"]},
         "stats": {"edge_terms": int(terms), "total_mass": st.total_mass, **{k: int(v) for k, v in work.items()},
                   "counted_by": "one untimed call of a count_work context on the same particles and h"},
+        "inverse_mapping": inverse,
         "secondary": {"edge_integrals_per_s": terms * world / (ms * 1e-3),
                       "note": "edge integrals K'_e with a nonzero term per second of the step; each stands for "
                               "the two vertex pyramids (wedges) that share the edge's foot"},
@@ -791,6 +793,42 @@ def run_pseudo(args):
     }
     L.map_destroy(ctx)
     emit(line, rank)
+
+
+def inverse_run(L, torch, ctx, g, n, n_pairs, mass, m, dev, reps=20):
+    """Eq. 4 on the last step's mapping: random per-cell values carried back to
+    the particles.  The first call also builds the particle-major copy of the
+    pair list; later calls only sum.  Algorithmic bytes of a sum: per pair its
+    cell index and f_ai (12 B), per particle two offsets and the result
+    (24 B), per cell its value (8 B); FP64 work: one product and one sum per
+    pair."""
+    rng = np.random.default_rng(12)
+    vals = [torch.as_tensor(rng.random(g.ncell), dtype=torch.float64, device=dev) for _ in range(2)]
+    out = torch.empty(n, dtype=torch.float64, device=dev)
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+    torch.cuda.synchronize()
+    ev[0].record()
+    L.map_cells_to_particles(ctx, vals[0], out)
+    ev[1].record()
+    for k in range(reps):
+        L.map_cells_to_particles(ctx, vals[(k + 1) & 1], out)
+    ev[2].record()
+    torch.cuda.synchronize()
+    first_ms = ev[0].elapsed_time(ev[1])
+    apply_ms = ev[1].elapsed_time(ev[2]) / reps
+    # reps is even: out holds vals[0] carried back
+    lhs = float(torch.dot(m, out))
+    rhs = float(torch.dot(vals[0], mass))
+    nbytes = 12 * n_pairs + 24 * n + 8 * g.ncell
+    peak = load_peaks().get("hbm_gbs")
+    gbs = nbytes / (apply_ms * 1e-3) / 1e9
+    return {"first_call_ms": first_ms, "apply_ms": apply_ms, "index_build_ms": first_ms - apply_ms,
+            "pairs_per_s": n_pairs / (apply_ms * 1e-3), "bytes_per_apply": int(nbytes), "achieved_GBps": gbs,
+            "frac_of_hbm": (gbs / peak) if peak else None,
+            "fp64_Gops": 2 * n_pairs / (apply_ms * 1e-3) / 1e9,
+            "mass_identity_rel": abs(lhs - rhs) / abs(rhs),
+            "note": "sum_a m_a out_a vs sum_i v_i M_i on the same mapping; apply = mean of %d calls, inputs "
+                    "(index %d MB) larger than L2" % (reps, (12 * n_pairs) >> 20)}
 
 
 def e2e_run(L, torch, ctx, p, g, dev, args, barrier, world):

@@ -185,6 +185,35 @@ int map_get_pairs(map_ctx* ctx, const int64_t** pair_off, const int32_t** pair_i
 int map_copy_pairs(map_ctx* ctx, int64_t* pair_off, int32_t* pair_idx, double* pair_frac, int64_t capacity,
                    void* stream);
 
+/* ------------------------------------------------------------ the inverse mapping (Section II-B, Eq. 4) */
+
+/* Carry a per-cell quantity back to the particles of the last
+ * map_particles_to_cells call with that call's pair integrals:
+ *     particle_value[a] = sum_i cell_value[i] f_ai
+ * over the cells i whose pair list holds a (Eq. 4; the quantity there is the
+ * ionic fraction the radiative transfer step leaves in each cell).  With the
+ * same weights as M_i = sum_a m_a f_ai, the mass-weighted totals agree:
+ * sum_a m_a particle_value[a] = sum_i cell_value[i] M_i (up to rounding and
+ * to the particles' own mass outside the grid).
+ *
+ * cell_value: device, ncell doubles of that call's grid; particle_value:
+ * device, n doubles, written; n must be that call's particle count.  Each
+ * particle's terms are products rounded once, added in ascending cell order
+ * without FMA contraction starting from +0: equal bit for bit to that plain
+ * sequential FP64 sum.  A particle in no pair list gets 0.
+ *
+ * The first call after a mapping builds a particle-major copy of its pair
+ * list (cell and f_ai of every pair, 12 bytes per pair, plus 8 bytes per
+ * particle; radix-sort workspace on top while it is built), kept by the
+ * context until the next mapping call; later calls with other cell values
+ * reuse it.  Asynchronous on stream, which the caller orders after the
+ * mapping call (the same stream, or an event); on another stream than the
+ * mapping call's, the first call waits for the copy to be built.
+ * Errors: MAP_EINVAL (NULL pointer; no single mapping call with per-pair
+ * integrals in this context: map_batch and the server keep none; n is not
+ * that call's particle count; 2^32 or more pairs), MAP_ENOMEM, MAP_ECUDA. */
+int map_cells_to_particles(map_ctx* ctx, const double* cell_value, double* particle_value, int64_t n, void* stream);
+
 /* Statistics of the last mapping call; synchronises its stream. */
 int map_get_stats(map_ctx* ctx, map_stats* stats);
 

@@ -79,6 +79,7 @@ _lib.map_grid_volumes.argtypes = [_P, ctypes.c_int, _P, _P]
 _lib.map_particles_to_cells.argtypes = [_P, ctypes.POINTER(map_particles), ctypes.c_int, ctypes.POINTER(map_outputs), _P]
 _lib.map_get_pairs.argtypes = [_P, ctypes.POINTER(_P), ctypes.POINTER(_P), ctypes.POINTER(_P), ctypes.POINTER(_I64)]
 _lib.map_copy_pairs.argtypes = [_P, _P, _P, _P, _I64, _P]
+_lib.map_cells_to_particles.argtypes = [_P, _P, _P, _I64, _P]
 _lib.map_get_stats.argtypes = [_P, ctypes.POINTER(map_stats)]
 _lib.map_get_work.argtypes = [_P, ctypes.POINTER(_I64), ctypes.POINTER(_I64)]
 _lib.map_get_timing.argtypes = [_P, ctypes.POINTER(ctypes.c_float)]
@@ -120,8 +121,9 @@ _lib.map_batch.argtypes = [_P, ctypes.c_int, ctypes.POINTER(map_particles), ctyp
 _lib.map_get_autotune.argtypes = [_P, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_float),
                                   ctypes.POINTER(ctypes.c_int)]
 for _name in ("map_init", "map_grid_upload", "map_grid_release", "map_grid_volumes", "map_particles_to_cells",
-              "map_get_pairs", "map_copy_pairs", "map_get_stats", "map_get_work", "map_get_timing", "solve_h",
-              "build_pseudo_particles", "map_batch", "map_get_autotune", "solve_h_batch"):
+              "map_get_pairs", "map_copy_pairs", "map_cells_to_particles", "map_get_stats", "map_get_work",
+              "map_get_timing", "solve_h", "build_pseudo_particles", "map_batch", "map_get_autotune",
+              "solve_h_batch"):
     getattr(_lib, _name).restype = ctypes.c_int
 
 
@@ -331,6 +333,18 @@ def map_copy_pairs(ctx, ncell: int, device=None, stream=None):
     frac = torch.empty(max(n, 1), dtype=torch.float64, device=dev)
     _check(_lib.map_copy_pairs(ctx, _ptr(off), _ptr(idx), _ptr(frac), max(n, 1), _stream(stream)), "map_copy_pairs")
     return off, idx[:n], frac[:n]
+
+
+def map_cells_to_particles(ctx, cell_value, particle_value, stream=None):
+    """Inverse mapping (Eq. 4): particle_value[a] = sum_i cell_value[i] f_ai
+    over the pairs of the last map_particles_to_cells call (float64 CUDA
+    tensors: ncell values in, one per particle out)."""
+    for t in (cell_value, particle_value):
+        if t.dtype != torch.float64:
+            raise ValueError("expected float64 tensors")
+    _check(_lib.map_cells_to_particles(ctx, _ptr(cell_value), _ptr(particle_value), particle_value.numel(),
+                                       _stream(stream)), "map_cells_to_particles")
+    return particle_value
 
 
 def map_get_stats(ctx) -> map_stats:

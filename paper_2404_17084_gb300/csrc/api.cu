@@ -136,6 +136,7 @@ void map_destroy(map_ctx* ctx) {
   for (auto& b : ctx->ws_tree) if (b.p) cudaFree(b.p);
   for (auto& b : ctx->ws_pairs) if (b.p) cudaFree(b.p);
   for (auto& b : ctx->ws_misc) if (b.p) cudaFree(b.p);
+  for (auto& b : ctx->ws_inv) if (b.p) cudaFree(b.p);
   for (auto& b : ctx->ws_grid) if (b.p) cudaFree(b.p);
   if (ctx->cub_tmp.p) cudaFree(ctx->cub_tmp.p);
   if (ctx->d_counters) cudaFree(ctx->d_counters);
@@ -211,6 +212,7 @@ int map_particles_to_cells(map_ctx* ctx, const map_particles* p, int handle, map
   MAP_TRY(pairs_build(ctx, g, s));
   phase_end(ctx, 1, s);
   MAP_TRY(integrals_run(ctx, g, p, out, s));
+  ctx->last_npart = p->n;
   ctx->last_stream = s;
   return MAP_OK;
 }

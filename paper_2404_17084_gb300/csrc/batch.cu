@@ -242,6 +242,7 @@ int map_batch(map_ctx* ctx, int nsnap, const map_particles* parts, const int* gr
   ctx->pair_off = nullptr;  // no single pair list describes a batch
   ctx->pair_idx = nullptr;
   ctx->pair_frac = nullptr;
+  ctx->inv_ready = false;
   ctx->items = nullptr;
   ctx->item_off = nullptr;
   ctx->partial = nullptr;

@@ -818,6 +818,7 @@ int integrals_run(map_ctx* ctx, const PreparedGrid* g, const map_particles* p, m
   double* frac;
   MAP_TRY(ensure_t(ctx, ctx->ws_misc[0], ctx->n_pairs + 1, &frac));
   ctx->pair_frac = frac;
+  ctx->inv_ready = false;
   SnapDesc* d_desc;
   int64_t* d_base;
   MAP_TRY(ensure_t(ctx, ctx->ws_misc[3], 1, &d_desc));

@@ -147,6 +147,7 @@ struct map_ctx {
   DevBuf ws_pairs[14];
   DevBuf ws_misc[8];
   DevBuf ws_grid[3];                   // grid preparation: face -> cell, per-face volume term and radius^2
+  DevBuf ws_inv[6];                    // particle-major copy of the pair list (inverse mapping, Eq. 4)
   DevBuf cub_tmp;
   DevTree tree;
   // results of the last mapping call
@@ -156,6 +157,14 @@ struct map_ctx {
   int32_t* pair_idx = nullptr;        // in the walk's order until pairs_sort_lists
   double* pair_frac = nullptr;
   bool pairs_sorted = false;          // lists sorted by particle index within each cell
+  int64_t last_npart = 0;             // particles of the last single mapping call
+  // particle-major copy of the last call's pairs (cell and f_ai per entry,
+  // ascending cell order within a particle), built by the first inverse
+  // mapping after the call
+  bool inv_ready = false;
+  const int64_t* inv_off = nullptr;   // [last_npart+1]
+  const int32_t* inv_cell = nullptr;
+  const double* inv_frac = nullptr;
   struct PairItem* items = nullptr;  // work items of the pair-integral kernel
   int64_t* item_off = nullptr;       // [ncell+1]: items of cell c
   double* partial = nullptr;         // per item: its pairs' mass

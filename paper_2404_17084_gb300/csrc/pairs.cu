@@ -492,6 +492,7 @@ int pairs_build(map_ctx* ctx, const PreparedGrid* g, cudaStream_t s, const PairB
   ctx->pair_off = off;
   ctx->pair_idx = list;
   ctx->pairs_sorted = false;
+  ctx->inv_ready = false;
   ctx->items = items;
   ctx->item_off = ioff;
   ctx->partial = part;

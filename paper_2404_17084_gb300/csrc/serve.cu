@@ -83,6 +83,7 @@ void trim(map_ctx* ctx) {
   for (auto& b : ctx->ws_tree) drop(b);
   for (auto& b : ctx->ws_pairs) drop(b);
   for (auto& b : ctx->ws_misc) drop(b);
+  for (auto& b : ctx->ws_inv) drop(b);
   for (auto& b : ctx->ws_grid) drop(b);
   for (auto* v : {&ctx->batch_off, &ctx->batch_idx, &ctx->batch_itm, &ctx->batch_ioff, &ctx->batch_part})
     for (auto& b : *v) drop(b);
@@ -91,6 +92,7 @@ void trim(map_ctx* ctx) {
   ctx->pair_off = nullptr;
   ctx->pair_idx = nullptr;
   ctx->pair_frac = nullptr;
+  ctx->inv_ready = false;
   ctx->items = nullptr;
   ctx->item_off = nullptr;
   ctx->partial = nullptr;
