@@ -159,6 +159,11 @@ OPS = {
 # data at any size).  It belongs to the kernel as captured: set it to None
 # when the kernel changes.
 INTEGRAL_DRAM_BYTES_PER_PAIR = 50.9
+# DRAM bytes per pair of one inverse-mapping sum (inv_apply): 451.2 MB read +
+# written for 32,168,427 pairs in ncu on the 2^18 clumpy snapshot
+# (profiles/inv_apply_clumpy_262144.md), scaled by pair count like the
+# figure above; None once the kernel changes.
+INVERSE_DRAM_BYTES_PER_PAIR = 14.03
 
 
 def counted_work(L, torch, precision, device, grids, dev, parts):
@@ -713,6 +718,130 @@ def run_uniform(args):
     emit(line, rank)
 
 
+def run_inverse(args):
+    """Inverse mapping (Eq. 4) on the clumpy-cloud snapshot: the mapping runs
+    once (untimed), then a step is one call carrying random per-cell values
+    (an ionic-fraction field) back to every particle with the mapping's pair
+    integrals.  The first warm-up call builds the particle-major copy of the
+    pair list.  e2e: cell values from pinned host memory in, particle values
+    out, every step."""
+    import torch
+    import paper_2404_17084_gb300 as L
+    import oracle
+
+    rank, world, local = dist_env()
+    dist_init(world)
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    p, g = make_snapshot(rank, args.n)
+    t = lambda a: torch.as_tensor(np.ascontiguousarray(a), dtype=torch.float64, device=dev)
+    x, y, z, m = t(p.x), t(p.y), t(p.z), t(p.m)
+    h = torch.empty_like(x)
+    mass = torch.empty(g.ncell, dtype=torch.float64, device=dev)
+    ctx = L.map_init(L.map_config_default(precision=L.MAP_MIXED, device=local))
+    handle = L.map_grid_upload(ctx, L.grid_to_device(g, dev))
+    L.solve_h(ctx, L.make_particles(x, y, z, None, h))
+    L.map_particles_to_cells(ctx, L.make_particles(x, y, z, m, h), handle, mass)
+    n_pairs = L.map_get_stats(ctx).n_pairs
+    rng = np.random.default_rng(rank_seed(12, rank))
+    cv_host = [torch.from_numpy(rng.random(g.ncell)).pin_memory() for _ in range(2)]
+    cv = [c.to(dev) for c in cv_host]
+    out = torch.empty(p.n, dtype=torch.float64, device=dev)
+    k = [0]
+
+    def step():
+        L.map_cells_to_particles(ctx, cv[k[0] & 1], out)
+        k[0] += 1
+
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    step()  # builds the particle-major copy of the pair list
+    torch.cuda.synchronize()
+    first_ms = (time.perf_counter() - t0) * 1e3
+    sampler = ClockSampler(local)
+    for _ in range(max(args.warmup, 3)):
+        step()
+    torch.cuda.synchronize()
+    _, l0 = L.map_get_work(ctx)
+    if world > 1:
+        torch.distributed.barrier()
+    sampler.start()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(args.steps):
+        step()
+    e1.record()
+    torch.cuda.synchronize()
+    clocks = sampler.stop()
+    _, l1 = L.map_get_work(ctx)
+    ms = max_over_ranks(e0.elapsed_time(e1) / args.steps, world, dev)
+    launches = l1 - l0
+    # the mass-weighted totals of a call: sum_a m_a out_a = sum_i v_i M_i
+    L.map_cells_to_particles(ctx, cv[0], out)
+    ident = abs(float(torch.dot(m, out)) - float(torch.dot(cv[0], mass))) / float(torch.dot(cv[0], mass))
+    # e2e: host cell values in, host particle values out
+    out_host = torch.empty(p.n, dtype=torch.float64).pin_memory()
+    e2e_steps = max(args.steps, 5)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for j in range(e2e_steps):
+        cv[0].copy_(cv_host[j & 1], non_blocking=True)
+        L.map_cells_to_particles(ctx, cv[0], out)
+        out_host.copy_(out, non_blocking=True)
+        torch.cuda.synchronize()
+    e2e_ms = (time.perf_counter() - t0) * 1e3 / e2e_steps
+    L.map_destroy(ctx)
+    nbytes = 12 * n_pairs + 24 * p.n + 8 * g.ncell
+    peak = load_peaks().get("hbm_gbs")
+    gbs = nbytes / (ms * 1e-3) / 1e9
+    line = {
+        "metric": "pair terms/s of the inverse mapping (Eq. 4)",
+        "value": n_pairs * world / (ms * 1e-3), "unit": "pair terms/s", "n_gpus": world, "steps": args.steps,
+        "warmup": max(args.warmup, 3), "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD.replace("mixed FP32/FP64", "inverse mapping of random per-cell values "
+                                                "with the mixed build's pair integrals"),
+                   "n_particles": p.n, "n_cells": g.ncell, "n_pairs": int(n_pairs),
+                   "l2": "inputs larger than L2 (particle-major pair list %d MB)" % ((12 * n_pairs) >> 20),
+                   "step": "one map_cells_to_particles call (the particle-major copy built before timing)"},
+        "first_call_ms": first_ms,
+        "roofline": {"bound": "hbm", "kernel": "inv_apply", "achieved": gbs, "peak": peak, "unit": "GB/s",
+                     "frac": (gbs / peak) if peak else None,
+                     "traffic": INVERSE_DRAM_BYTES_PER_PAIR * n_pairs if INVERSE_DRAM_BYTES_PER_PAIR else None,
+                     "algorithmic_bytes": int(nbytes),
+                     "note": "per pair cell index + f_ai (12 B), per particle two offsets and the result (24 B), "
+                             "per cell its value (8 B); peak = measured copy bandwidth"},
+        "mass_identity_rel": ident,
+        "e2e": {"value": n_pairs * world / (e2e_ms * 1e-3), "unit": "pair terms/s",
+                "h2d_bytes_per_step": 8 * g.ncell, "d2h_bytes_per_step": 8 * p.n, "ms_per_step": e2e_ms,
+                "steps": e2e_steps},
+        "gpu_launches": int(launches), "clocks": clocks,
+    }
+    if rank == 0 and not args.no_cpu_baseline:
+        # the oracle's sum on a pair list of the same shape (cell-major, the
+        # same pairs per cell on average), bounded to about args.cpu_seconds
+        npc = max(1, int(round(n_pairs / g.ncell)))
+        ncell_s = max(1, min(g.ncell, int(2e6 // npc)))
+        ns = ncell_s * npc
+        off = np.arange(ncell_s + 1, dtype=np.int64) * npc
+        idx = rng.integers(0, p.n, ns).astype(np.int32)
+        fr = rng.random(ns)
+        vals = rng.random(ncell_s)
+        reps, t0 = 0, time.perf_counter()
+        while time.perf_counter() - t0 < min(args.cpu_seconds, 10.0) or reps == 0:
+            oracle.inverse_map(off, idx, fr, vals, p.n)
+            reps += 1
+        cpu_s = time.perf_counter() - t0
+        line["cpu_baseline"] = {"value": reps * ns / cpu_s, "unit": "pair terms/s", "cores": 1, "kind": "oracle",
+                                "sample": f"{ns} pairs ({ncell_s} cells x {npc}, random particles) x {reps} calls "
+                                          f"of the numpy sum, {cpu_s:.1f} s"}
+    if world > 1:
+        torch.distributed.barrier()
+    emit(line, rank)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
 def run_pseudo(args):
     """Pseudo-particle path: 2^22 particles from the log-normal field, h from
     the GPU solve, the source at the densest particle; the octree walk turns
@@ -973,10 +1102,12 @@ def main():
     ap.add_argument("--dump", action="store_true", help="save per-cell results to <outdir>/cells.npz")
     ap.add_argument("--outdir", default=os.path.join(ROOT, "bench_out"),
                     help="folder for the clock samples and --dump output")
-    ap.add_argument("--workload", default="clumpy", choices=["clumpy", "batch", "serve", "uniform", "pseudo"],
+    ap.add_argument("--workload", default="clumpy",
+                    choices=["clumpy", "batch", "serve", "uniform", "pseudo", "inverse"],
                     help="clumpy: one 2^20 snapshot (default); batch: uneven snapshots in one launch; "
                          "serve: Poisson stream of requests through the serving loop; uniform: 4096 uniform "
-                         "particles, FP64; pseudo: 2^22 particles reduced to pseudo-particles")
+                         "particles, FP64; pseudo: 2^22 particles reduced to pseudo-particles; inverse: "
+                         "per-cell values carried back to the 2^20 snapshot's particles (Eq. 4)")
     ap.add_argument("--pool", type=int, default=32, help="distinct requests of the serve workload")
     ap.add_argument("--requests", type=int, default=160, help="requests submitted in the serve workload")
     ap.add_argument("--rate", type=float, default=0.0, help="serve arrival rate (req/s); 0 = 80%% of capacity")
@@ -994,6 +1125,8 @@ def main():
         run_uniform(args)
     elif args.workload == "pseudo":
         run_pseudo(args)
+    elif args.workload == "inverse":
+        run_inverse(args)
     else:
         run_ours(args)
 

@@ -198,9 +198,10 @@ int map_copy_pairs(map_ctx* ctx, int64_t* pair_off, int32_t* pair_idx, double* p
  *
  * cell_value: device, ncell doubles of that call's grid; particle_value:
  * device, n doubles, written; n must be that call's particle count.  Each
- * particle's terms are products rounded once, added in ascending cell order
- * without FMA contraction starting from +0: equal bit for bit to that plain
- * sequential FP64 sum.  A particle in no pair list gets 0.
+ * particle's terms are fused into its running sum one at a time in ascending
+ * cell order, from +0, with one rounding per term (acc <- RN(acc + v_i f_ai),
+ * an FMA): equal bit for bit to that sequential sum.  A particle in no pair
+ * list gets 0.
  *
  * The first call after a mapping builds a particle-major copy of its pair
  * list (cell and f_ai of every pair, 12 bytes per pair, plus 8 bytes per

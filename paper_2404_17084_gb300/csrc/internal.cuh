@@ -147,7 +147,7 @@ struct map_ctx {
   DevBuf ws_pairs[14];
   DevBuf ws_misc[8];
   DevBuf ws_grid[3];                   // grid preparation: face -> cell, per-face volume term and radius^2
-  DevBuf ws_inv[6];                    // particle-major copy of the pair list (inverse mapping, Eq. 4)
+  DevBuf ws_inv[11];                   // particle-major copy of the pair list (inverse mapping, Eq. 4)
   DevBuf cub_tmp;
   DevTree tree;
   // results of the last mapping call
@@ -165,6 +165,8 @@ struct map_ctx {
   const int64_t* inv_off = nullptr;   // [last_npart+1]
   const int32_t* inv_cell = nullptr;
   const double* inv_frac = nullptr;
+  const int32_t* inv_order = nullptr; // particles by decreasing entry count
+  const int64_t* inv_nlong = nullptr; // device: particles summed by a whole warp
   struct PairItem* items = nullptr;  // work items of the pair-integral kernel
   int64_t* item_off = nullptr;       // [ncell+1]: items of cell c
   double* partial = nullptr;         // per item: its pairs' mass
