@@ -235,24 +235,51 @@ class Tree:
                                               self.leaf, self.first_child, self.nchild, self.pbegin, self.order)])
         self.nnodes = int(n)
 
-    def walk(self, src, theta):
-        """Adaptive walk, Eq. (5): a node is opened when r_node = 0 or
-        s_node^2 > theta^2 r_node^2; an opened leaf yields its particles.
-        Depth-first, children in octant order.  Returns (accepted node ids,
-        opened leaf ids)."""
-        sx, sy, sz = (float(v) for v in src)
+    def walk(self, src, theta, r_part=0.0, r_leaf=0.0, regions=None):
+        """Adaptive walk (Section III-B).  A node is opened when, for some source
+        (src: one point or k x 3):
+          * Eq. (5): r_node = 0 or s_node^2 > theta^2 r_node^2;
+          * its bounding sphere (centre of mass, radius s_node) reaches within
+            r_part of the source: r_node < r_part + s_node;
+          * it is not a leaf and its bounding sphere reaches within r_leaf:
+            r_node < r_leaf + s_node (in the annulus at least leaves);
+        or when, for some recorded region (cx, cy, cz, R, s_min) of an earlier
+        step, its centre of mass lies within R of the region's centre and
+        s_node > s_min.  Distances are compared squared, r^2 < (r_x + s)^2,
+        each product and sum rounded once.  An opened leaf yields its
+        particles.  Depth-first, children in octant order.  Returns (accepted
+        node ids, opened leaf ids)."""
+        srcs = np.asarray(src, np.float64).reshape(-1, 3)
+        regs = np.zeros((0, 5)) if regions is None else np.asarray(regions, np.float64).reshape(-1, 5)
         acc, opened = [], []
         stack = [0]
         while stack:
             nid = stack.pop()
-            dx = self.com[nid, 0] - sx
-            dy = self.com[nid, 1] - sy
-            dz = self.com[nid, 2] - sz
-            r2 = (dx * dx + dy * dy) + dz * dz
-            s = self.size[nid]
-            if not (r2 == 0.0 or s * s > theta * theta * r2):
+            s = float(self.size[nid])
+            leaf = bool(self.leaf[nid])
+            op = False
+            for sx, sy, sz in srcs:
+                dx = float(self.com[nid, 0]) - sx
+                dy = float(self.com[nid, 1]) - sy
+                dz = float(self.com[nid, 2]) - sz
+                r2 = (dx * dx + dy * dy) + dz * dz
+                tp = r_part + s
+                tl = r_leaf + s
+                if r2 == 0.0 or s * s > theta * theta * r2:
+                    op = True
+                elif r_part > 0.0 and r2 < tp * tp:
+                    op = True
+                elif not leaf and r_leaf > 0.0 and r2 < tl * tl:
+                    op = True
+            for cx, cy, cz, rad, smin in regs:
+                dx = float(self.com[nid, 0]) - cx
+                dy = float(self.com[nid, 1]) - cy
+                dz = float(self.com[nid, 2]) - cz
+                if (dx * dx + dy * dy) + dz * dz < rad * rad and s > smin:
+                    op = True
+            if not op:
                 acc.append(nid)
-            elif self.leaf[nid]:
+            elif leaf:
                 opened.append(nid)
             else:
                 fc, nc = int(self.first_child[nid]), int(self.nchild[nid])

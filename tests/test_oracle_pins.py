@@ -348,6 +348,71 @@ def test_octree_invariants_and_walk_partition():
     assert sum(int(t.count[i]) for i in opened) + sum(int(t.count[i]) for i in acc) == p.n
 
 
+def _walk_output(t, acc, opened):
+    """Particle sets of the accepted nodes and the extracted particles."""
+    parts = np.concatenate([t.particles_of(i) for i in opened]) if len(opened) else np.zeros(0, np.int64)
+    return parts
+
+
+def test_walk_controls_geometry():
+    """Section III-B's thresholds, checked on the particles themselves (not on
+    the walk's own bounding-sphere test): every particle within r_part of a
+    source comes out as an individual particle; no pseudo-particle coarser
+    than a leaf holds a particle within r_leaf of a source; with several
+    sources each source's neighbourhood is resolved; the output still
+    partitions the particles and conserves mass."""
+    p = synth.lognormal_particles(6000, 13, ngrid=32)
+    t = oracle.Tree(p.x, p.y, p.z, p.m, 16)
+    pos = p.pos()
+    srcs = np.array([pos[17], pos[4001]])
+    for r_part, r_leaf in ((0.05, 0.05), (0.05, 0.15), (0.0, 0.2), (0.1, 0.3)):
+        acc, opened = t.walk(srcs, 0.5, r_part=r_part, r_leaf=r_leaf)
+        parts = _walk_output(t, acc, opened)
+        covered = np.concatenate([t.particles_of(i) for i in np.concatenate([acc, opened])])
+        assert len(covered) == p.n and len(np.unique(covered)) == p.n
+        assert abs(t.mass[acc].sum() + p.m[parts].sum() - p.m.sum()) < 1e-12
+        d = np.min(np.linalg.norm(pos[:, None, :] - srcs[None, :, :], axis=2), axis=1)
+        assert np.all(np.isin(np.nonzero(d < r_part)[0], parts))
+        for i in acc:
+            if not t.leaf[i]:
+                assert d[t.particles_of(i)].min() >= r_leaf, (r_part, r_leaf, i)
+        # more resolution near the sources than the plain walk gives
+        acc0, opened0 = t.walk(srcs, 0.5)
+        assert len(acc) + len(parts) >= len(acc0) + len(_walk_output(t, acc0, opened0))
+    # r_part covering the cube: every particle alone; r_leaf covering it with
+    # a theta that opens nothing by itself: exactly the leaves
+    acc, opened = t.walk(srcs[0], 0.5, r_part=2.0)
+    assert len(acc) == 0 and len(_walk_output(t, acc, opened)) == p.n
+    acc, opened = t.walk(srcs[0], 1e9, r_leaf=2.0)
+    assert len(opened) == 0 and np.array_equal(np.sort(acc), np.nonzero(t.leaf)[0])
+
+
+def test_walk_region_memory():
+    """A region recorded in an earlier step (centre, radius, smallest size
+    reached there): every pseudo-particle whose centre of mass lies inside it
+    is no larger than that size, unless it is a single particle or a leaf
+    that cannot be opened further than its particles; outside, the walk is the
+    plain one."""
+    p = synth.lognormal_particles(6000, 13, ngrid=32)
+    t = oracle.Tree(p.x, p.y, p.z, p.m, 16)
+    src = p.pos()[17]
+    acc0, opened0 = t.walk(src, 0.5)
+    # the region: a large accepted node of the plain walk, refined to a size
+    # a quarter of its own
+    big = acc0[np.argmax(t.size[acc0])]
+    region = np.array([[*t.com[big], t.size[big], 0.25 * t.size[big]]])
+    acc, opened = t.walk(src, 0.5, regions=region)
+    inside = np.linalg.norm(t.com[acc] - t.com[big], axis=1) < t.size[big]
+    assert inside.sum() > 1
+    assert np.all(t.size[acc][inside] <= 0.25 * t.size[big])
+    assert big not in set(acc.tolist())
+    # nodes away from the region are untouched
+    far0 = {int(i) for i in acc0 if np.linalg.norm(t.com[i] - t.com[big]) > 3 * t.size[big]}
+    assert far0 <= set(acc.tolist())
+    covered = np.concatenate([t.particles_of(i) for i in np.concatenate([acc, opened])])
+    assert len(covered) == p.n and len(np.unique(covered)) == p.n
+
+
 # ----------------------------------------------------------------- inverse mapping (Eq. 4)
 
 def test_inverse_map_octants_by_symmetry():
