@@ -909,6 +909,18 @@ def run_pseudo(args):
     mp, mf = mass_p.cpu().numpy(), mass_f.cpu().numpy()
     rel = np.abs(mp - mf) / np.maximum(mf, 1e-12 * mf.max())
     step_ms = build_ms + map_ms
+    # the walk controls of Section III-B around the same source: particles
+    # within r_part, at least leaves out to r_leaf
+    kind = torch.empty(cap, dtype=torch.int32, device=dev)
+    controls = {}
+    for r_part, r_leaf in ((0.02, 0.05), (0.05, 0.1)):
+        def build_c():
+            npseudo[0] = L.build_pseudo_particles(ctx, full, src, outp, kind=kind, r_part=r_part, r_leaf=r_leaf)
+        ms_c = _step_timer(torch, build_c, args.steps, max(args.warmup, 3))
+        kc = npseudo[0]
+        controls[f"r_part={r_part},r_leaf={r_leaf}"] = {
+            "build_ms": ms_c, "n_pseudo": kc, "particles": int((kind[:kc] == 1).sum().item()),
+            "mass_rel": float(abs(om[:kc].sum().item() - m.sum().item()) / m.sum().item())}
     line = {
         "metric": "particle-cell pair integrals/sec at 1 GB300 (mixed vs FP64 form) + p50/p99 latency",
         "value": st_p.n_pairs / (step_ms * 1e-3), "unit": "pair integrals/s", "n_gpus": 1,
@@ -927,7 +939,8 @@ def run_pseudo(args):
                    "vs_full_resolution_per_cell_rel": {"p50": float(np.percentile(rel, 50)),
                                                         "p90": float(np.percentile(rel, 90)),
                                                         "p99": float(np.percentile(rel, 99))},
-                   "mass_pseudo_vs_full": float(abs(om[:k].sum().item() - m.sum().item()) / m.sum().item())},
+                   "mass_pseudo_vs_full": float(abs(om[:k].sum().item() - m.sum().item()) / m.sum().item()),
+                   "walk_controls": controls},
         "e2e": None, "gpu_launches": None,
     }
     L.map_destroy(ctx)

@@ -399,6 +399,33 @@ int solve_h_noalloc(const double* x, const double* y, const double* z, int64_t n
 int build_pseudo_particles(map_ctx* ctx, const map_particles* full, const double* src, int nsrc,
                            map_particles* out, int32_t* kind, int64_t* ident, int64_t* n_pseudo, void* stream);
 
+/* Walk controls (Section III-B).  Besides Eq. (5), a node is opened when,
+ * for some source, its bounding sphere (centre of mass, radius s_node)
+ * reaches within r_part of it (r_node < r_part + s_node: around the sources
+ * every leaf yields its particles), or when it is not a leaf and its
+ * bounding sphere reaches within r_leaf (r_node < r_leaf + s_node: in the
+ * annulus out to r_leaf the walk reaches at least the leaves).  It is also
+ * opened when its centre of mass lies within the radius of a region recorded
+ * in an earlier step and it is larger than the smallest size reached there
+ * (|com - c| < R and s_node > s_min: the region memory of Section III-B,
+ * whose recording needs the radiative transfer results and is the caller's).
+ * Distances are compared squared, each product and sum rounded once, so the
+ * walk is reproducible bit for bit.  0 turns r_part / r_leaf off. */
+typedef struct {
+  const double* src;     /* host, 3 doubles per source */
+  int nsrc;              /* >= 1 */
+  double r_part;         /* >= 0 */
+  double r_leaf;         /* >= 0 */
+  const double* regions; /* host, 5 doubles per region: centre x, y, z, radius R, smallest size s_min; may be NULL */
+  int nregion;           /* >= 0 */
+} map_walk;
+
+/* build_pseudo_particles with the walk controls above (theta from the
+ * context's configuration); the same outputs, ordering and errors, plus
+ * MAP_EINVAL for a negative or non-finite control or region value. */
+int build_pseudo_particles_walk(map_ctx* ctx, const map_particles* full, const map_walk* walk, map_particles* out,
+                                int32_t* kind, int64_t* ident, int64_t* n_pseudo, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

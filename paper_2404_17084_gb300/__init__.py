@@ -88,6 +88,15 @@ _lib.solve_h_batch.argtypes = [_P, ctypes.c_int, ctypes.POINTER(map_particles), 
 _lib.build_pseudo_particles.argtypes = [_P, ctypes.POINTER(map_particles), ctypes.POINTER(ctypes.c_double),
                                         ctypes.c_int, ctypes.POINTER(map_particles), _P, _P,
                                         ctypes.POINTER(_I64), _P]
+class map_walk(ctypes.Structure):
+    _fields_ = [("src", _P), ("nsrc", ctypes.c_int), ("r_part", ctypes.c_double), ("r_leaf", ctypes.c_double),
+                ("regions", _P), ("nregion", ctypes.c_int)]
+
+
+_lib.build_pseudo_particles_walk.argtypes = [_P, ctypes.POINTER(map_particles), ctypes.POINTER(map_walk),
+                                             ctypes.POINTER(map_particles), _P, _P, ctypes.POINTER(_I64), _P]
+
+
 class map_server_config(ctypes.Structure):
     _fields_ = [("device", ctypes.c_int), ("precision", ctypes.c_int), ("slots", ctypes.c_int),
                 ("hbm_budget", ctypes.c_size_t), ("hfact", ctypes.c_double)]
@@ -122,8 +131,8 @@ _lib.map_get_autotune.argtypes = [_P, ctypes.POINTER(ctypes.c_int), ctypes.POINT
                                   ctypes.POINTER(ctypes.c_int)]
 for _name in ("map_init", "map_grid_upload", "map_grid_release", "map_grid_volumes", "map_particles_to_cells",
               "map_get_pairs", "map_copy_pairs", "map_cells_to_particles", "map_get_stats", "map_get_work",
-              "map_get_timing", "solve_h", "build_pseudo_particles", "map_batch", "map_get_autotune",
-              "solve_h_batch"):
+              "map_get_timing", "solve_h", "build_pseudo_particles", "build_pseudo_particles_walk", "map_batch",
+              "map_get_autotune", "solve_h_batch"):
     getattr(_lib, _name).restype = ctypes.c_int
 
 
@@ -384,14 +393,25 @@ def solve_h_batch(ctx, parts, routes=None, stream=None) -> None:
     _check(_lib.solve_h_batch(ctx, n, P, R, _stream(stream)), "solve_h_batch")
 
 
-def build_pseudo_particles(ctx, full: map_particles, src, out: map_particles, kind=None, ident=None, stream=None):
+def build_pseudo_particles(ctx, full: map_particles, src, out: map_particles, kind=None, ident=None, stream=None,
+                           r_part=0.0, r_leaf=0.0, regions=None):
     """Returns the number of pseudo-particles written (raises MapError with
-    code MAP_ECAPACITY, attribute .required, if out is too small)."""
-    srcs = [float(v) for v in src]
+    code MAP_ECAPACITY, attribute .required, if out is too small).  src: one
+    or more source positions (flat or k x 3); r_part, r_leaf, regions (k x 5:
+    centre, radius, smallest size): the walk controls of Section III-B."""
+    srcs = [float(v) for v in np.asarray(src, dtype=np.float64).ravel()]
     arr = (ctypes.c_double * len(srcs))(*srcs)
     n = ctypes.c_int64(0)
-    code = _lib.build_pseudo_particles(ctx, ctypes.byref(full), arr, len(srcs) // 3, ctypes.byref(out), _ptr(kind),
-                                       _ptr(ident), ctypes.byref(n), _stream(stream))
+    if r_part == 0.0 and r_leaf == 0.0 and regions is None:
+        code = _lib.build_pseudo_particles(ctx, ctypes.byref(full), arr, len(srcs) // 3, ctypes.byref(out),
+                                           _ptr(kind), _ptr(ident), ctypes.byref(n), _stream(stream))
+    else:
+        regs = [] if regions is None else [float(v) for v in np.asarray(regions, dtype=np.float64).ravel()]
+        rarr = (ctypes.c_double * max(len(regs), 1))(*regs)
+        walk = map_walk(ctypes.cast(arr, _P), len(srcs) // 3, float(r_part), float(r_leaf),
+                        ctypes.cast(rarr, _P) if regs else None, len(regs) // 5)
+        code = _lib.build_pseudo_particles_walk(ctx, ctypes.byref(full), ctypes.byref(walk), ctypes.byref(out),
+                                                _ptr(kind), _ptr(ident), ctypes.byref(n), _stream(stream))
     if code != MAP_OK:
         err = MapError(code, "build_pseudo_particles")
         err.required = n.value

@@ -300,17 +300,29 @@ int solve_h(map_ctx* ctx, map_particles* p, int32_t* route, void* stream) {
   return MAP_OK;
 }
 
-int build_pseudo_particles(map_ctx* ctx, const map_particles* full, const double* src, int nsrc, map_particles* out,
-                           int32_t* kind, int64_t* ident, int64_t* n_pseudo, void* stream) {
-  if (!ctx || !full || !src || nsrc < 1 || !out || !n_pseudo || !full->m || !full->h) return MAP_EINVAL;
+int build_pseudo_particles_walk(map_ctx* ctx, const map_particles* full, const map_walk* walk, map_particles* out,
+                                int32_t* kind, int64_t* ident, int64_t* n_pseudo, void* stream) {
+  if (!ctx || !full || !walk || !walk->src || walk->nsrc < 1 || !out || !n_pseudo || !full->m || !full->h)
+    return MAP_EINVAL;
+  if (walk->nregion < 0 || (walk->nregion > 0 && !walk->regions)) return MAP_EINVAL;
+  if (!(std::isfinite(walk->r_part) && walk->r_part >= 0.0 && std::isfinite(walk->r_leaf) && walk->r_leaf >= 0.0))
+    return MAP_EINVAL;
+  for (int k = 0; k < 3 * walk->nsrc; ++k)
+    if (!std::isfinite(walk->src[k])) return MAP_EINVAL;
+  for (int k = 0; k < 5 * walk->nregion; ++k)
+    if (!std::isfinite(walk->regions[k]) || (k % 5 >= 3 && walk->regions[k] < 0.0)) return MAP_EINVAL;
   CUDA_TRY(cudaSetDevice(ctx->device));
   cudaStream_t s = S(stream);
   MAP_TRY(check_particles(ctx, full, true, true, s));
-  for (int k = 0; k < 3 * nsrc; ++k)
-    if (!std::isfinite(src[k])) return MAP_EINVAL;
-  int r = pseudo_run(ctx, full, src, nsrc, out, kind, ident, n_pseudo, s);
+  int r = pseudo_run(ctx, full, walk, out, kind, ident, n_pseudo, s);
   ctx->last_stream = s;
   return r;
+}
+
+int build_pseudo_particles(map_ctx* ctx, const map_particles* full, const double* src, int nsrc, map_particles* out,
+                           int32_t* kind, int64_t* ident, int64_t* n_pseudo, void* stream) {
+  const map_walk walk{src, nsrc, 0.0, 0.0, nullptr, 0};
+  return build_pseudo_particles_walk(ctx, full, &walk, out, kind, ident, n_pseudo, stream);
 }
 
 }  // extern "C"

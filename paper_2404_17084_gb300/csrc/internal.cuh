@@ -299,8 +299,8 @@ int run_on_workers(map_ctx* ctx, int n, const int* order, cudaStream_t s,
 void destroy_workers(map_ctx* ctx);
 int h_solve_run(map_ctx* ctx, const double* x, const double* y, const double* z, int64_t n, double* h,
                 int32_t* route, const double* h0_override, cudaStream_t s);
-int pseudo_run(map_ctx* ctx, const map_particles* full, const double* src, int nsrc, map_particles* out,
-               int32_t* kind, int64_t* ident, int64_t* n_pseudo, cudaStream_t s);
+int pseudo_run(map_ctx* ctx, const map_particles* full, const map_walk* walk, map_particles* out, int32_t* kind,
+               int64_t* ident, int64_t* n_pseudo, cudaStream_t s);
 
 // blocks of t threads covering n items
 inline unsigned nblk(int64_t n, int t) { return (unsigned)((n + t - 1) / t); }

@@ -1,7 +1,9 @@
 // Pseudo-particles (Section III-A/B) and their smoothing lengths (Section III-C/D).
 //
 // Walk (Eq. 5): a node is opened when r_node = 0 or s_node^2 > theta^2 r_node^2,
-// r_node being the distance from its centre of mass to the nearest source.  A
+// r_node being the distance from its centre of mass to the nearest source, or
+// when one of the walk controls of Section III-B asks for it (r_part, r_leaf,
+// regions of an earlier step; see the opening rule below).  A
 // node is reached when all its ancestors are opened; reached nodes that are
 // not opened become pseudo-particles (centre of mass, node mass); reached
 // leaves that are opened yield their particles, which keep their h.  Because
@@ -26,16 +28,41 @@ namespace {
 
 constexpr int64_t KIND_PARTICLE = (int64_t)1 << 62;
 
+// Opening rule of the walk (Eq. 5 and the controls of Section III-B), every
+// distance compared squared with each product and sum rounded once.
+struct WalkRule {
+  const double* src;  // 3 per source
+  int nsrc;
+  double theta, r_part, r_leaf;
+  const double* reg;  // 5 per region: centre, radius, smallest size
+  int nreg;
+};
+
+__device__ __forceinline__ double sq3(double dx, double dy, double dz) {
+  return __dadd_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)), __dmul_rn(dz, dz));
+}
+
 __global__ void open_flags(int64_t nn, const double* __restrict__ com, const unsigned long long* __restrict__ size_bits,
-                           const double* __restrict__ src, int nsrc, double theta, int8_t* open) {
+                           const int32_t* __restrict__ nchild, WalkRule R, int8_t* open) {
   int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (i >= nn) return;
   const double s = bitsd(size_bits[i]);
+  const bool leaf = nchild[i] == 0;
+  const double s2 = __dmul_rn(s, s), th2 = __dmul_rn(R.theta, R.theta);
+  const double tp = __dadd_rn(R.r_part, s), tl = __dadd_rn(R.r_leaf, s);
+  const double tp2 = __dmul_rn(tp, tp), tl2 = __dmul_rn(tl, tl);
+  const double cx = com[3 * i], cy = com[3 * i + 1], cz = com[3 * i + 2];
   bool op = false;
-  for (int k = 0; k < nsrc; ++k) {
-    const double dx = com[3 * i] - src[3 * k], dy = com[3 * i + 1] - src[3 * k + 1], dz = com[3 * i + 2] - src[3 * k + 2];
-    const double r2 = (dx * dx + dy * dy) + dz * dz;
-    if (r2 == 0.0 || s * s > theta * theta * r2) op = true;
+  for (int k = 0; k < R.nsrc; ++k) {
+    const double r2 = sq3(__dsub_rn(cx, R.src[3 * k]), __dsub_rn(cy, R.src[3 * k + 1]), __dsub_rn(cz, R.src[3 * k + 2]));
+    if (r2 == 0.0 || s2 > __dmul_rn(th2, r2)) op = true;
+    else if (R.r_part > 0.0 && r2 < tp2) op = true;
+    else if (!leaf && R.r_leaf > 0.0 && r2 < tl2) op = true;
+  }
+  for (int k = 0; k < R.nreg; ++k) {
+    const double* g = R.reg + 5 * k;
+    const double d2 = sq3(__dsub_rn(cx, g[0]), __dsub_rn(cy, g[1]), __dsub_rn(cz, g[2]));
+    if (d2 < __dmul_rn(g[3], g[3]) && s > g[4]) op = true;
   }
   open[i] = op ? 1 : 0;
 }
@@ -251,8 +278,9 @@ __global__ void min_member_level(int64_t nm, const int32_t* __restrict__ members
 
 }  // namespace
 
-int pseudo_run(map_ctx* ctx, const map_particles* full, const double* src, int nsrc, map_particles* out,
-               int32_t* kind, int64_t* ident, int64_t* n_pseudo, cudaStream_t s) {
+int pseudo_run(map_ctx* ctx, const map_particles* full, const map_walk* walk, map_particles* out, int32_t* kind,
+               int64_t* ident, int64_t* n_pseudo, cudaStream_t s) {
+  const int nsrc = walk->nsrc, nreg = walk->nregion;
   const int64_t n = full->n;
   MAP_TRY(tree_build(ctx, full->x, full->y, full->z, full->m, full->h, n, s, true));
   DevTree& T = ctx->tree;
@@ -262,7 +290,7 @@ int pseudo_run(map_ctx* ctx, const map_particles* full, const double* src, int n
   int8_t *open, *status;
   int64_t *head, *slot, *mpos;
   int32_t *is_head, *node_of_slot, *mflag, *members;
-  MAP_TRY(ensure_t(ctx, ctx->ws_misc[1], 3 * nsrc, &d_src));
+  MAP_TRY(ensure_t(ctx, ctx->ws_misc[1], 3 * nsrc + 5 * nreg, &d_src));
   MAP_TRY(ensure_t(ctx, ctx->ws_misc[2], 2 * nn, &open));
   status = open + nn;
   MAP_TRY(ensure_t(ctx, ctx->ws_misc[3], 2 * (n + 1), &head));
@@ -272,8 +300,11 @@ int pseudo_run(map_ctx* ctx, const map_particles* full, const double* src, int n
   MAP_TRY(ensure_t(ctx, ctx->ws_misc[5], 2 * (nn + 1), &mflag));
   members = mflag + (nn + 1);
   MAP_TRY(ensure_t(ctx, ctx->ws_misc[6], nn + 1, &mpos));
-  CUDA_TRY(cudaMemcpyAsync(d_src, src, 3 * nsrc * sizeof(double), cudaMemcpyHostToDevice, s));
-  open_flags<<<nblk(nn, tpb), tpb, 0, s>>>(nn, T.com, T.size_bits, d_src, nsrc, ctx->cfg.theta, open); ++ctx->launches;
+  CUDA_TRY(cudaMemcpyAsync(d_src, walk->src, 3 * nsrc * sizeof(double), cudaMemcpyHostToDevice, s));
+  if (nreg > 0)
+    CUDA_TRY(cudaMemcpyAsync(d_src + 3 * nsrc, walk->regions, 5 * nreg * sizeof(double), cudaMemcpyHostToDevice, s));
+  const WalkRule rule{d_src, nsrc, ctx->cfg.theta, walk->r_part, walk->r_leaf, d_src + 3 * nsrc, nreg};
+  open_flags<<<nblk(nn, tpb), tpb, 0, s>>>(nn, T.com, T.size_bits, T.nchild, rule, open); ++ctx->launches;
   walk_status<<<nblk(nn, tpb), tpb, 0, s>>>(nn, T.parent, open, T.nchild, status); ++ctx->launches;
   CUDA_TRY(cudaMemsetAsync(is_head, 0, (n + 1) * sizeof(int32_t), s));
   mark_heads<<<nblk(nn, tpb), tpb, 0, s>>>(nn, status, T.begin, T.end, head, is_head); ++ctx->launches;

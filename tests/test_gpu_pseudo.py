@@ -11,7 +11,7 @@ from gpu_helpers import lib, oracle_h, gpu_map, rel_err
 pytestmark = pytest.mark.gpu
 
 
-def gpu_pseudo(p, h, src, theta=0.5, ngb_max=10000):
+def gpu_pseudo(p, h, src, theta=0.5, ngb_max=10000, **walk):
     L = lib()
     ctx = L.map_init(L.map_config_default(precision=0, theta=theta, ngb_bruteforce_max=ngb_max))
     try:
@@ -22,7 +22,7 @@ def gpu_pseudo(p, h, src, theta=0.5, ngb_max=10000):
         kind = torch.empty(cap, dtype=torch.int32, device="cuda")
         ident = torch.empty(cap, dtype=torch.int64, device="cuda")
         n = L.build_pseudo_particles(ctx, L.make_particles(x, y, z, m, hh), src, L.make_particles(ox, oy, oz, om, oh),
-                                     kind, ident)
+                                     kind, ident, **walk)
         torch.cuda.synchronize()
         out = {k: v[:n].cpu().numpy() for k, v in dict(x=ox, y=oy, z=oz, m=om, h=oh, kind=kind, ident=ident).items()}
         return out
@@ -30,9 +30,9 @@ def gpu_pseudo(p, h, src, theta=0.5, ngb_max=10000):
         L.map_destroy(ctx)
 
 
-def oracle_pseudo(p, h, src, theta=0.5, hfact=oracle.HFACT):
+def oracle_pseudo(p, h, src, theta=0.5, hfact=oracle.HFACT, **walk):
     t = oracle.Tree(p.x, p.y, p.z, p.m)
-    acc, opened = t.walk(src, theta)
+    acc, opened = t.walk(src, theta, **walk)
     members = np.sort(np.concatenate([acc, opened]))
     # h of accepted nodes over the member set (brute force), Eq. (7)-(9)
     first = np.array([t.particles_of(i)[0] for i in acc], np.int64)
@@ -52,11 +52,28 @@ def cloud():
     return p, h, src
 
 
-@pytest.mark.parametrize("ngb_max", [10000, 50])
-def test_pseudo_particles_match_oracle(cloud, ngb_max):
-    p, h, src = cloud
-    out = gpu_pseudo(p, h, src, ngb_max=ngb_max)
-    t, acc, opened, h_acc = oracle_pseudo(p, h, src)
+def walk_cases(p, h, src):
+    """Plain walk; r_part and r_leaf annuli around two sources; a region
+    recorded around a large node of the plain walk."""
+    t = oracle.Tree(p.x, p.y, p.z, p.m)
+    acc0, _ = t.walk(src, 0.5)
+    big = acc0[np.argmax(t.size[acc0])]
+    second = p.pos()[int(np.argsort(h)[len(h) // 2])]
+    return [dict(src=src), dict(src=np.stack([src, second]), r_part=0.03, r_leaf=0.08),
+            dict(src=src, r_leaf=0.1, regions=np.array([[*t.com[big], t.size[big], 0.3 * t.size[big]]]))]
+
+
+@pytest.mark.parametrize("ngb_max,case", [(10000, 0), (50, 0), (10000, 1), (50, 1), (10000, 2)])
+def test_pseudo_particles_match_oracle(cloud, ngb_max, case):
+    p, h, src0 = cloud
+    walk = walk_cases(p, h, src0)[case]
+    src = walk.pop("src")
+    out = gpu_pseudo(p, h, src, ngb_max=ngb_max, **walk)
+    t, acc, opened, h_acc = oracle_pseudo(p, h, src, **walk)
+    if case:
+        t0 = oracle.Tree(p.x, p.y, p.z, p.m)
+        acc0, op0 = t0.walk(src0, 0.5)
+        assert len(out["m"]) > len(acc0) + int(t0.count[op0].sum())  # the controls resolve more
     # the set of pseudo-particles: node labels and extracted particle indices
     gpu_nodes = np.sort(out["ident"][out["kind"] == 0])
     gpu_parts = np.sort(out["ident"][out["kind"] == 1])
