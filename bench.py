@@ -909,6 +909,7 @@ def run_pseudo(args):
     mp, mf = mass_p.cpu().numpy(), mass_f.cpu().numpy()
     rel = np.abs(mp - mf) / np.maximum(mf, 1e-12 * mf.max())
     step_ms = build_ms + map_ms
+    mass_plain = float(abs(om[:k].sum().item() - m.sum().item()) / m.sum().item())
     # the walk controls of Section III-B around the same source: particles
     # within r_part, at least leaves out to r_leaf
     kind = torch.empty(cap, dtype=torch.int32, device=dev)
@@ -939,7 +940,7 @@ def run_pseudo(args):
                    "vs_full_resolution_per_cell_rel": {"p50": float(np.percentile(rel, 50)),
                                                         "p90": float(np.percentile(rel, 90)),
                                                         "p99": float(np.percentile(rel, 99))},
-                   "mass_pseudo_vs_full": float(abs(om[:k].sum().item() - m.sum().item()) / m.sum().item()),
+                   "mass_pseudo_vs_full": mass_plain,
                    "walk_controls": controls},
         "e2e": None, "gpu_launches": None,
     }
