@@ -170,30 +170,51 @@ __device__ __forceinline__ void acc_member(const double* com, int32_t b, double 
   ds += 3.0 * w + q * dw_m4(q);
 }
 
-__device__ void set_density(const NodeSet& S, double x, double y, double z, double rcut, double h, double& n,
+// n(h) and dn/dh at (x, y, z) over the candidates, summed by the 32 lanes of
+// a warp (strided over the members or the level-k_mid nodes) and combined by
+// a butterfly reduction, so that every lane holds the same sums.
+__device__ void set_density(const NodeSet& S, int lane, double x, double y, double z, double rcut, double h, double& n,
                             double& dn) {
   const double R2 = 4.0 * h * h, inv_h = 1.0 / h, norm = 1.0 / (MAP_PI * h * h * h);
   double s = 0.0, ds = 0.0;
   if (!S.use_kmid) {
-    for (int64_t j = 0; j < S.nm; ++j) acc_member(S.com, S.members[j], x, y, z, R2, inv_h, s, ds);
+    for (int64_t j = lane; j < S.nm; j += 32) acc_member(S.com, S.members[j], x, y, z, R2, inv_h, s, ds);
   } else {
+    // the lanes test 32 level-k_mid nodes at a time, then share out the
+    // members of each flagged one
     const double rc2 = rcut * rcut;
-    for (int64_t m = S.mid_begin; m < S.mid_end; ++m) {
-      const double dx = S.com[3 * m] - x, dy = S.com[3 * m + 1] - y, dz = S.com[3 * m + 2] - z;
-      if (dx * dx + dy * dy + dz * dz >= rc2) continue;  // k_mid node not flagged
-      const int64_t k = m - S.mid_begin;
-      for (int64_t j = S.mid_off[k]; j < S.mid_off[k + 1]; ++j) acc_member(S.com, S.mid_sorted[j], x, y, z, R2, inv_h, s, ds);
+    for (int64_t m0 = S.mid_begin; m0 < S.mid_end; m0 += 32) {
+      const int64_t m = m0 + lane;
+      bool flag = false;
+      if (m < S.mid_end) {
+        const double dx = S.com[3 * m] - x, dy = S.com[3 * m + 1] - y, dz = S.com[3 * m + 2] - z;
+        flag = dx * dx + dy * dy + dz * dz < rc2;
+      }
+      for (unsigned bal = __ballot_sync(0xffffffffu, flag); bal; bal &= bal - 1) {
+        const int64_t k = m0 + (__ffs(bal) - 1) - S.mid_begin;
+        for (int64_t j = S.mid_off[k] + lane; j < S.mid_off[k + 1]; j += 32)
+          acc_member(S.com, S.mid_sorted[j], x, y, z, R2, inv_h, s, ds);
+      }
     }
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    s += __shfl_xor_sync(0xffffffffu, s, o);
+    ds += __shfl_xor_sync(0xffffffffu, ds, o);
   }
   n = s * norm;
   dn = -ds * norm * inv_h;
 }
 
+// One warp per output slot holding an accepted node: Newton-Raphson on
+// h = hfact n(h)^(-1/3) from Eq. (9)'s guess, bisection on [h0/16, 16 h0]
+// when it fails, the guess itself when that has no sign change (Section
+// III-C).  The lanes hold identical sums, so the iteration is warp-uniform.
 __global__ void pseudo_h(int64_t nout, const int32_t* __restrict__ node_of_slot, NodeSet S,
                          const unsigned long long* __restrict__ size_bits, const int32_t* __restrict__ parent,
                          const int32_t* __restrict__ level, const int64_t* __restrict__ nb, const double* __restrict__ hs,
                          int kmid, double hfact, double* oh) {
-  int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const int lane = threadIdx.x & 31;
+  const int64_t j = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   if (j >= nout) return;
   const int32_t nd = node_of_slot[j];
   if (nd < 0) return;  // extracted particle keeps its h
@@ -217,7 +238,7 @@ __global__ void pseudo_h(int64_t nout, const int32_t* __restrict__ node_of_slot,
   bool ok = false;
   for (int it = 0; it < 30; ++it) {
     double nn, dn;
-    set_density(S, x, y, z, rcut, h, nn, dn);
+    set_density(S, lane, x, y, z, rcut, h, nn, dn);
     const double f = h - hfact * pow(nn, -1.0 / 3.0);
     const double fp = 1.0 + hfact / 3.0 * pow(nn, -4.0 / 3.0) * dn;
     const double hn = h - f / fp;
@@ -227,9 +248,9 @@ __global__ void pseudo_h(int64_t nout, const int32_t* __restrict__ node_of_slot,
   }
   if (!ok) {
     double nn, dn;
-    set_density(S, x, y, z, rcut, lo, nn, dn);
+    set_density(S, lane, x, y, z, rcut, lo, nn, dn);
     const double flo = lo - hfact * pow(nn, -1.0 / 3.0);
-    set_density(S, x, y, z, rcut, hi, nn, dn);
+    set_density(S, lane, x, y, z, rcut, hi, nn, dn);
     const double fhi = hi - hfact * pow(nn, -1.0 / 3.0);
     if (!(flo < 0.0 && fhi > 0.0)) {
       h = g0;
@@ -237,14 +258,14 @@ __global__ void pseudo_h(int64_t nout, const int32_t* __restrict__ node_of_slot,
       double a0 = lo, b0 = hi;
       for (int it = 0; it < 200; ++it) {
         const double mid = 0.5 * (a0 + b0);
-        set_density(S, x, y, z, rcut, mid, nn, dn);
+        set_density(S, lane, x, y, z, rcut, mid, nn, dn);
         if (mid - hfact * pow(nn, -1.0 / 3.0) < 0.0) a0 = mid; else b0 = mid;
         if (b0 - a0 < 1e-12 * mid) break;
       }
       h = 0.5 * (a0 + b0);
     }
   }
-  oh[j] = h;
+  if (lane == 0) oh[j] = h;
 }
 
 __global__ void member_anc(int64_t nm, const int32_t* __restrict__ members, const int32_t* __restrict__ parent,
@@ -373,7 +394,7 @@ int pseudo_run(map_ctx* ctx, const map_particles* full, const map_walk* walk, ma
     S.mid_off = moff;
     S.mid_sorted = vout;
   }
-  pseudo_h<<<nblk(nout, 128), 128, 0, s>>>(nout, node_of_slot, S, T.size_bits, T.parent, T.level, T.begin, T.hs,
+  pseudo_h<<<nblk(nout * 32, 128), 128, 0, s>>>(nout, node_of_slot, S, T.size_bits, T.parent, T.level, T.begin, T.hs,
                                            kmid, ctx->cfg.hfact, out->h); ++ctx->launches;
   CUDA_TRY(cudaGetLastError());
   return MAP_OK;
