@@ -12,6 +12,8 @@ Routes (see the C file's header for the full statement):
     Gauss-Kronrod quadrature of its 1-D reduction;
   * cell mass and density: Eq. (1)-(3), long double sums;
   * inverse mapping: Eq. (4), a plain numpy sum over the pair list;
+  * table variant: pyramid integrals interpolated trilinearly in a table of I
+    (set_table), the paper's production route;
   * smoothing lengths: Eq. (7)-(9), Newton -> bisection -> estimate;
   * octree, adaptive walk: Section III-A/B, Eq. (5).
 """
@@ -60,6 +62,10 @@ def _load():
         lib.or_W.argtypes = [_D, _D]
         lib.or_wedge.restype = _D
         lib.or_wedge.argtypes = [_D, _D, _D]
+        lib.or_wedge_table.argtypes = [_D, _D, _D]
+        lib.or_wedge_table.restype = _D
+        lib.or_table_set.argtypes = [_INT]
+        lib.or_table_set.restype = None
         grid8 = [_P] * 8
         lib.or_pair_count.argtypes = grid8 + [_P, _I64, _P, _P, _P, _P, _I64, _P, _INT]
         lib.or_pair_fill.argtypes = grid8 + [_P, _I64, _P, _P, _P, _P, _I64, _P, _P, _INT]
@@ -100,6 +106,18 @@ def F(u: float) -> float:
 
 def H(u: float) -> float:
     return _load().or_H(u)
+
+
+def set_table(n: int) -> None:
+    """Table variant (Section II-B's production route): n nodes per axis of
+    I over r0 in [0, 2], rho = R0 / sqrt(4 - r0^2) in [0, 1], phi in
+    [0, pi/2], interpolated trilinearly by wedge_table and by map_cells while
+    it is set; n = 0 drops it (exact pyramid integrals again)."""
+    _load().or_table_set(int(n))
+
+
+def wedge_table(r0: float, R0: float, phi: float) -> float:
+    return _load().or_wedge_table(r0, R0, phi)
 
 
 def wedge(r0: float, R0: float, phi: float) -> float:

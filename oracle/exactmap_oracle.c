@@ -23,6 +23,9 @@
  *    integral by adaptive Gauss-Kronrod quadrature, split at the radii 1 and
  *    2 where the kernel changes polynomial piece.  It does NOT use the
  *    closed form the CUDA path uses.
+ *  - Table variant (the paper's production route, Section II-B): with a
+ *    table set (or_table_set), each pyramid integral inside the table's box
+ *    is interpolated trilinearly between pre-computed values of I.
  *  - Kernel: the standard 3-D M4 cubic spline with support 2h,
  *    W = w(q)/(pi h^3), w = 1 - 1.5q^2 + 0.75q^3 (q<1), 0.25(2-q)^3 (q<2).
  *    (The paper names the M4 kernel in Section III-C but prints no formula.)
@@ -161,6 +164,66 @@ double or_wedge(double r0, double R0, double phi) {
   return tot;
 }
 
+/* ------------------------------------- table variant (Section II-B, production) */
+
+/* The paper's production route: I(r0, R0, phi) pre-computed on a grid and
+ * interpolated.  Here: n nodes per axis over r0 in [0, 2], rho = R0 /
+ * sqrt(4 - r0^2) in [0, 1] (R0 beyond the support's reach of the edge line
+ * needs no table) and phi in [0, pi/2], filled with or_wedge, and trilinear
+ * interpolation between the eight surrounding nodes.  Outside that box
+ * (r0 >= 2 or rho >= 1) or with no table set, the exact or_wedge is used. */
+static int tab_n = 0;
+static double* tab = NULL;
+
+void or_table_set(int n) {
+  free(tab);
+  tab = NULL;
+  tab_n = 0;
+  if (n < 2) return;
+  tab = (double*)malloc(sizeof(double) * (size_t)n * n * n);
+#pragma omp parallel for schedule(dynamic, 1)
+  for (int i = 0; i < n; ++i) {
+    double r0 = 2.0 * i / (n - 1);
+    double span = sqrt(fmax(4.0 - r0 * r0, 0.0));
+    for (int j = 0; j < n; ++j) {
+      double R0 = span * j / (n - 1);
+      for (int k = 0; k < n; ++k) {
+        double phi = 0.5 * OR_PI * k / (n - 1);
+        /* or_wedge takes phi < pi/2: the last node is the limit, approached
+           within 1e-12 */
+        if (k == n - 1) phi = 0.5 * OR_PI - 1e-12;
+        tab[((size_t)i * n + j) * n + k] = or_wedge(r0, R0, phi);
+      }
+    }
+  }
+  tab_n = n;
+}
+
+double or_wedge_table(double r0, double R0, double phi) {
+  if (!tab || r0 >= 2.0) return or_wedge(r0, R0, phi);
+  double span = sqrt(4.0 - r0 * r0);
+  double rho = R0 / span;
+  if (rho >= 1.0) return or_wedge(r0, R0, phi);
+  int n = tab_n;
+  double u[3] = {r0 / 2.0 * (n - 1), rho * (n - 1), phi / (0.5 * OR_PI) * (n - 1)};
+  int i0[3];
+  double t[3];
+  for (int d = 0; d < 3; ++d) {
+    double x = u[d] < 0.0 ? 0.0 : u[d];
+    int k = (int)floor(x);
+    if (k > n - 2) k = n - 2;
+    i0[d] = k;
+    t[d] = x - k;
+  }
+  double v = 0.0;
+  for (int c = 0; c < 8; ++c) {
+    int a = c & 1, b = (c >> 1) & 1, e = (c >> 2) & 1;
+    double wgt = (a ? t[0] : 1.0 - t[0]) * (b ? t[1] : 1.0 - t[1]) * (e ? t[2] : 1.0 - t[2]);
+    v += wgt * tab[((size_t)(i0[0] + a) * n + (i0[1] + b)) * n + (i0[2] + e)];
+  }
+  return v;
+}
+
 /* ---------------------------------------------------------------- cells */
 
 typedef struct {
@@ -211,7 +274,7 @@ double or_pair_fraction(const or_grid* g, int64_t c, double x, double y, double 
       double ta = (ex * (ax - px) + ey * (ay - py) + ez * (az - pz)) / h;
       double tb = (ex * (bx - px) + ey * (by - py) + ez * (bz - pz)) / h;
       double phia = atan(fabs(ta) / R0), phib = atan(fabs(tb) / R0);
-      double Ia = or_wedge(r0, R0, phia), Ib = or_wedge(r0, R0, phib);
+      double Ia = or_wedge_table(r0, R0, phia), Ib = or_wedge_table(r0, R0, phib);
       double contrib;
       if (ta < 0.0 && tb > 0.0) contrib = Ia + Ib;      /* foot between the vertices */
       else if (ta >= 0.0) contrib = Ib - Ia;            /* foot before a: b is far */
