@@ -38,6 +38,8 @@ extern "C" {
 /* ------------------------------------------------------------ configuration */
 #define MAP_FP64 0  /* every wedge integral in FP64 (closed form) */
 #define MAP_MIXED 1 /* wedge integrals in FP32, FP64 accumulation */
+#define MAP_TABLE 2 /* pyramid integrals interpolated in a pre-computed table (the paper's production route,
+                       Section II-B); FP32 geometry, FP64 per-pair sums; see table_n */
 
 typedef struct {
   int precision;                     /* MAP_FP64 or MAP_MIXED */
@@ -56,6 +58,11 @@ typedef struct {
                                         of one launch shape that keeps the tally in registers (slower, and
                                         its FP32 rounding may differ within the mixed build's tolerance);
                                         0: those counts read 0; default 0 */
+  int table_n;                       /* MAP_TABLE: nodes per axis of the table of I(r0, R0, phi) over r0 in
+                                        [0, 2], R0 / sqrt(4 - r0^2) in [0, 1], phi in [0, pi/2] (n^3 FP32
+                                        texels, trilinear interpolation by the texture unit, whose weights
+                                        carry 8 fractional bits), built by map_init in FP64 from the closed
+                                        form; 2..512, default 64 */
 } map_config;
 
 /* Fill *cfg with the defaults listed above. */
@@ -118,7 +125,8 @@ typedef struct map_ctx map_ctx;
 /* ------------------------------------------------------------ lifetime */
 
 /* Create a context on cfg->device (NULL cfg = defaults).  Allocates a small
- * pinned host block and selects the device; no device workspace yet. */
+ * pinned host block and selects the device; no device workspace yet, except
+ * the table of a MAP_TABLE context (built here, synchronously). */
 int map_init(map_ctx** ctx, const map_config* cfg);
 
 /* Free all device and host memory of the context (grids included). */

@@ -30,6 +30,7 @@ MAP_EHANDLE = -6
 MAP_ECAPACITY = -7
 MAP_FP64 = 0
 MAP_MIXED = 1
+MAP_TABLE = 2
 
 if not os.path.exists(LIB_PATH):
     raise ImportError(f"libexactmap.so not built ({LIB_PATH}); run paper_2404_17084_gb300/build.py")
@@ -44,7 +45,7 @@ class map_config(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int), ("device", ctypes.c_int), ("hbm_budget", ctypes.c_size_t),
                 ("theta", ctypes.c_double), ("hfact", ctypes.c_double), ("leaf_size", ctypes.c_int),
                 ("ngb_bruteforce_max", ctypes.c_int), ("autotune", ctypes.c_int),
-                ("queue_timeout_ns", ctypes.c_ulonglong), ("count_work", ctypes.c_int)]
+                ("queue_timeout_ns", ctypes.c_ulonglong), ("count_work", ctypes.c_int), ("table_n", ctypes.c_int)]
 
 
 class map_particles(ctypes.Structure):

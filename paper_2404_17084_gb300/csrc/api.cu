@@ -75,6 +75,7 @@ void map_config_default(map_config* cfg) {
   cfg->autotune = 0;
   cfg->queue_timeout_ns = 2000000000ULL;
   cfg->count_work = 0;
+  cfg->table_n = 64;
 }
 
 const char* map_strerror(int code) {
@@ -97,7 +98,14 @@ int map_init(map_ctx** out, const map_config* cfg) {
   map_ctx* ctx = new (std::nothrow) map_ctx();
   if (!ctx) return MAP_ENOMEM;
   if (cfg) ctx->cfg = *cfg; else map_config_default(&ctx->cfg);
-  if (ctx->cfg.precision != MAP_FP64 && ctx->cfg.precision != MAP_MIXED) { delete ctx; return MAP_EINVAL; }
+  if (ctx->cfg.precision != MAP_FP64 && ctx->cfg.precision != MAP_MIXED && ctx->cfg.precision != MAP_TABLE) {
+    delete ctx;
+    return MAP_EINVAL;
+  }
+  if (ctx->cfg.precision == MAP_TABLE && (ctx->cfg.table_n < 2 || ctx->cfg.table_n > 512)) {
+    delete ctx;
+    return MAP_EINVAL;
+  }
   if (ctx->cfg.leaf_size < 1 || !(ctx->cfg.hfact > 0) || !(ctx->cfg.theta >= 0)) { delete ctx; return MAP_EINVAL; }
   int ndev = 0;
   if (cudaGetDeviceCount(&ndev) != cudaSuccess || ctx->cfg.device < 0 || ctx->cfg.device >= ndev) {
@@ -119,6 +127,10 @@ int map_init(map_ctx** out, const map_config* cfg) {
   cudaMemset(ctx->d_counters, 0, 16 * sizeof(unsigned long long));
   for (auto& e : ctx->ev)
     if (cudaEventCreate(&e) != cudaSuccess) { cudaGetLastError(); map_destroy(ctx); return MAP_ECUDA; }
+  if (ctx->cfg.precision == MAP_TABLE) {
+    const int r = table_ensure(ctx, nullptr);
+    if (r != MAP_OK) { cudaGetLastError(); map_destroy(ctx); return r; }
+  }
   *out = ctx;
   return MAP_OK;
 }
@@ -137,6 +149,7 @@ void map_destroy(map_ctx* ctx) {
   for (auto& b : ctx->ws_pairs) if (b.p) cudaFree(b.p);
   for (auto& b : ctx->ws_misc) if (b.p) cudaFree(b.p);
   for (auto& b : ctx->ws_inv) if (b.p) cudaFree(b.p);
+  table_free(ctx);
   for (auto& b : ctx->ws_grid) if (b.p) cudaFree(b.p);
   if (ctx->cub_tmp.p) cudaFree(ctx->cub_tmp.p);
   if (ctx->d_counters) cudaFree(ctx->d_counters);

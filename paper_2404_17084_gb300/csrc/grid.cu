@@ -228,7 +228,7 @@ int grid_prepare(map_ctx* ctx, const map_grid* in, PreparedGrid* g, cudaStream_t
   // (its rare FP64 faces rebuild their edge records from the vertices), FP64
   // edges for the FP64 build
   MAP_TRY(ctx_alloc_grid(ctx, g, (void**)&g->face32, nf * sizeof(float4)));
-  if (ctx->cfg.precision == MAP_MIXED) {
+  if (ctx->cfg.precision != MAP_FP64) {
     MAP_TRY(ctx_alloc_grid(ctx, g, (void**)&g->fsph32, nf * sizeof(float4)));
     MAP_TRY(ctx_alloc_grid(ctx, g, (void**)&g->edge32, nl * EDGE_STRIDE * sizeof(float)));
   } else {

@@ -526,7 +526,7 @@ int h_solve_run(map_ctx* ctx, const double* x, const double* y, const double* z,
   const HsTree V{T.xs, T.ys, T.zs, T.split, T.begin, T.end, T.first_child, T.nchild, T.owner, T.idx, T.box32};
   const int64_t warps = (n + 31) / 32;
   const unsigned blocks = (unsigned)((warps + HS_WARPS - 1) / HS_WARPS);
-  if (ctx->cfg.precision == MAP_MIXED)
+  if (ctx->cfg.precision != MAP_FP64)
     h_solve_leaves<true><<<blocks, HS_WARPS * 32, 0, s>>>(n, V, h0s, ctx->cfg.hfact, 1e-6, h, route);
   else
     h_solve_leaves<false><<<blocks, HS_WARPS * 32, 0, s>>>(n, V, h0s, ctx->cfg.hfact, 1e-10, h, route);

@@ -755,7 +755,9 @@ int integrals_enqueue(map_ctx* ctx, const BatchArgs& B, int variant, cudaStream_
   CUDA_TRY(cudaMemsetAsync(ctx->d_counters, 0, 4 * sizeof(unsigned long long), s));
   CUDA_TRY(cudaMemsetAsync(ctx->d_counters + 8, 0, 8 * sizeof(unsigned long long), s));
   const bool count = ctx->cfg.count_work != 0;
-  if (ctx->cfg.precision == MAP_MIXED && count) {
+  if (ctx->cfg.precision == MAP_TABLE) {
+    MAP_TRY(launch_table(ctx, B, s));
+  } else if (ctx->cfg.precision == MAP_MIXED && count) {
     MAP_TRY((launch_mixed<4, 5, true>(ctx, B, s)));
   } else if (ctx->cfg.precision == MAP_MIXED) {
     switch (variant) {
@@ -796,7 +798,7 @@ SnapDesc make_desc(map_ctx* ctx, const PreparedGrid* g, const map_particles* p, 
   d.frac = frac;
   d.cell_mass = out->cell_mass;
   d.cell_rho = out->cell_rho;
-  const bool mixed = ctx->cfg.precision == MAP_MIXED;
+  const bool mixed = ctx->cfg.precision != MAP_FP64;  // the table variant reads the FP32 records too
   d.face = mixed ? (const void*)g->face32 : (const void*)g->face64;
   d.edge = mixed ? (const void*)g->edge32 : (const void*)g->edge64;
   d.face64 = g->face64;
@@ -830,7 +832,7 @@ int integrals_run(map_ctx* ctx, const PreparedGrid* g, const map_particles* p, m
   if (ctx->cfg.autotune && ctx->cfg.precision == MAP_MIXED && !ctx->tune_done[MAP_MIXED])
     MAP_TRY(integrals_autotune(ctx, B, s));
   phase_begin(ctx, 2, s);
-  MAP_TRY(integrals_enqueue(ctx, B, ctx->tuned[ctx->cfg.precision], s));
+  MAP_TRY(integrals_enqueue(ctx, B, ctx->tuned[ctx->cfg.precision == MAP_MIXED ? MAP_MIXED : MAP_FP64], s));
   phase_end(ctx, 2, s);
   if (out->cell_vol) CUDA_TRY(cudaMemcpyAsync(out->cell_vol, g->vol, g->ncell * sizeof(double), cudaMemcpyDeviceToDevice, s));
   MAP_TRY(integrals_sum(ctx, d_desc, 1, ctx->d_total, s));

@@ -198,6 +198,9 @@ struct map_ctx {
   int64_t bexec_launches = 0;  // kernels per replay of bexec
   std::vector<BatchWorker> workers;  // created by the first batch call that uses them
   cudaEvent_t wev = nullptr;         // the caller's stream, before the workers start
+  // MAP_TABLE: the table of the pyramid integral (n^3 FP32 texels)
+  cudaArray_t tab_arr = nullptr;
+  cudaTextureObject_t tab_tex = 0;
 };
 
 inline void phase_begin(map_ctx* ctx, int k, cudaStream_t s) { if (ctx->ev[2 * k]) cudaEventRecord(ctx->ev[2 * k], s); }
@@ -291,6 +294,11 @@ int integrals_upload(map_ctx* ctx, const SnapDesc* h_desc, const int64_t* h_ibas
 int integrals_enqueue(map_ctx* ctx, const BatchArgs& B, int variant, cudaStream_t s);
 int integrals_sum(map_ctx* ctx, const SnapDesc* d_desc, int nsnap, double* totals, cudaStream_t s);
 int integrals_autotune(map_ctx* ctx, const BatchArgs& B, cudaStream_t s);
+// MAP_TABLE: build the table (synchronises the stream), free it, and launch
+// the table variant of the pair-integral kernel
+int table_ensure(map_ctx* ctx, cudaStream_t s);
+void table_free(map_ctx* ctx);
+int launch_table(map_ctx* ctx, const BatchArgs& B, cudaStream_t s);
 // Runs fn(worker, j) for j = order[0..n) on the context's workers, each on
 // its own stream and host thread, after the work queued on s; s then waits
 // for all of them.  Returns the first error.  Work is handed out in `order`.

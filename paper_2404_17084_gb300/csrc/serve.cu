@@ -63,7 +63,7 @@ size_t request_bytes(const map_request& r, int precision) {
   const double parts = 48.0 * r.n + 200.0 * r.n + 160.0 * 16.0 * r.n;
   // per loop entry: the staged index and the edge records the precision keeps
   // (12 floats for the mixed build, 12 doubles for FP64)
-  const double loop = precision == MAP_MIXED ? 64.0 : 112.0;
+  const double loop = precision != MAP_FP64 ? 64.0 : 112.0;
   const double grid = 96.0 * r.ncell + 146.0 * r.nface + loop * r.nloop + 48.0 * r.nvert;
   const double outs = 24.0 * r.ncell;
   return (size_t)(1.25 * (parts + grid + outs)) + (64u << 20);
