@@ -20,6 +20,7 @@ Routes (see the C file's header for the full statement):
 from __future__ import annotations
 
 import ctypes
+import math
 import os
 import subprocess
 
@@ -324,3 +325,209 @@ def particle_h_guess(tree: "Tree", hfact=HFACT):
     leaf = tree.leaf_of_particles()
     side = np.ldexp(1.0, -tree.level[leaf].astype(np.int64))
     return hfact * side / np.cbrt(tree.count[leaf].astype(np.float64))
+
+
+# ----------------------------------------------------------------- grid construction (Section II-A)
+
+class VoronoiGrid:
+    """Clipped Voronoi grid in the CSR layout the mapping reads (cell ->
+    faces -> vertex loops CCW from outside; planes (n, d) with unit outward n;
+    face_nb = neighbour site, or -1-w for cube wall w in the order x<=1,
+    x>=0, y<=1, y>=0, z<=1, z>=0)."""
+
+    def __init__(self, cells, site):
+        cfo, fvo, fv, nb, pl, vs = [0], [0], [], [], [], []
+        for verts, faces, planes, nbs in cells:
+            base = sum(len(v) for v in vs)
+            vs.append(verts)
+            for loop, plane, b in zip(faces, planes, nbs):
+                fv.extend(base + k for k in loop)
+                fvo.append(len(fv))
+                pl.append(plane)
+                nb.append(b)
+            cfo.append(len(fvo) - 1)
+        v = np.concatenate(vs) if vs else np.zeros((0, 3))
+        self.cell_face_off = np.array(cfo, np.int64)
+        self.face_vert_off = np.array(fvo, np.int64)
+        self.face_vert = np.array(fv, np.int32)
+        self.face_nb = np.array(nb, np.int32)
+        self.face_plane = np.array(pl, np.float64).reshape(-1, 4)
+        self.vx, self.vy, self.vz = (np.ascontiguousarray(v[:, k]) for k in range(3))
+        self.site = np.ascontiguousarray(site, np.float64).reshape(-1, 3)
+
+    @property
+    def ncell(self):
+        return len(self.cell_face_off) - 1
+
+    @property
+    def nface(self):
+        return len(self.face_vert_off) - 1
+
+
+def _clip_cell(verts, faces, planes, nbs, n, d, nb):
+    """Keep the part of a convex polyhedron with n.x <= d (vertices relative to
+    the site).  Each face loop is clipped in turn (a vertex within a relative
+    1e-13 of the plane counts as on it); the new face collects the vertices on
+    the plane, ordered by angle around their mean."""
+    scale = math.sqrt(max(float(np.max(np.sum(verts * verts, axis=1))), 1e-300))
+    tol = 1e-13 * scale
+    s = verts @ n - d
+    if s.max() <= tol:
+        return verts, faces, planes, nbs
+    cls = np.where(s < -tol, -1, np.where(s > tol, 1, 0))
+    new_v = [verts[i] for i in range(len(verts)) if cls[i] <= 0]
+    remap = {}
+    for i in range(len(verts)):
+        if cls[i] <= 0:
+            remap[i] = len(remap)
+    on = {remap[i] for i in range(len(verts)) if cls[i] == 0}
+    cut = {}
+
+    def cut_vertex(a, b):
+        key = (min(a, b), max(a, b))
+        if key not in cut:
+            t = s[a] / (s[a] - s[b])
+            new_v.append(verts[a] + (verts[b] - verts[a]) * t)
+            cut[key] = len(new_v) - 1
+            on.add(cut[key])
+        return cut[key]
+
+    nf, npl, nnb = [], [], []
+    for loop, plane, b in zip(faces, planes, nbs):
+        out = []
+        for k in range(len(loop)):
+            a, c = loop[k], loop[(k + 1) % len(loop)]
+            if cls[a] <= 0:
+                out.append(remap[a])
+            if cls[a] * cls[c] < 0:
+                out.append(cut_vertex(a, c))
+        o2 = []
+        for q in out:
+            if not o2 or o2[-1] != q:
+                o2.append(q)
+        while len(o2) > 1 and o2[0] == o2[-1]:
+            o2.pop()
+        if len(o2) >= 3:
+            nf.append(o2)
+            npl.append(plane)
+            nnb.append(b)
+    new_v = np.array(new_v)
+    if len(on) >= 3:
+        ids = sorted(on)
+        c = new_v[ids].mean(axis=0)
+        a = np.array([1.0, 0, 0]) if abs(n[0]) < 0.6 else np.array([0, 1.0, 0])
+        u1 = np.cross(n, a)
+        u1 /= np.linalg.norm(u1)
+        u2 = np.cross(n, u1)
+        ang = [math.atan2(float((new_v[i] - c) @ u2), float((new_v[i] - c) @ u1)) for i in ids]
+        nf.append([i for _, i in sorted(zip(ang, ids))])
+        npl.append((n, d))
+        nnb.append(nb)
+    used = sorted({q for loop in nf for q in loop})
+    ren = {q: k for k, q in enumerate(used)}
+    return new_v[used], [[ren[q] for q in loop] for loop in nf], npl, nnb
+
+
+def voronoi_cells(sites):
+    """The Voronoi cell of every site, clipped to the unit cube (Section II-A):
+    the cube cut by the bisector plane of every other site, nearest first, a
+    site at distance D being skipped once D/2 is at least the cell's largest
+    vertex radius (its plane cannot reach the cell).  Vertices within a
+    relative 1e-11 of each other are welded and faces left with fewer than
+    three vertices dropped.  Plain numpy, for small site counts."""
+    sites = np.asarray(sites, np.float64).reshape(-1, 3)
+    cells = []
+    for i, s in enumerate(sites):
+        lo, hi = -s, 1.0 - s
+        verts = np.array([[hi[0] if k & 1 else lo[0], hi[1] if k & 2 else lo[1], hi[2] if k & 4 else lo[2]]
+                          for k in range(8)])
+        faces = [[1, 3, 7, 5], [0, 4, 6, 2], [2, 6, 7, 3], [0, 1, 5, 4], [4, 5, 7, 6], [0, 2, 3, 1]]
+        axes = [np.array(v, float) for v in ((1, 0, 0), (-1, 0, 0), (0, 1, 0), (0, -1, 0), (0, 0, 1), (0, 0, -1))]
+        planes = [(axes[w], float(hi[w // 2] if w % 2 == 0 else -lo[w // 2])) for w in range(6)]
+        nbs = [-1 - w for w in range(6)]
+        d2 = np.sum((sites - s) ** 2, axis=1)
+        for j in np.argsort(d2, kind="stable"):
+            if j == i or d2[j] <= 0.0:
+                continue
+            if d2[j] >= 4.0 * float(np.max(np.sum(verts * verts, axis=1))):
+                break
+            dd = sites[j] - s
+            ln = math.sqrt(d2[j])
+            verts, faces, planes, nbs = _clip_cell(verts, faces, planes, nbs, dd / ln, 0.5 * ln, int(j))
+        # weld and drop degenerate faces
+        scale = math.sqrt(max(float(np.max(np.sum(verts * verts, axis=1))), 1e-300))
+        rep = list(range(len(verts)))
+        for a in range(len(verts)):
+            for b in range(a):
+                if rep[b] == b and np.sum((verts[a] - verts[b]) ** 2) < (1e-11 * scale) ** 2:
+                    rep[a] = b
+                    break
+        keep = []
+        for loop, plane, b in zip(faces, planes, nbs):
+            o = []
+            for q in loop:
+                if not o or o[-1] != rep[q]:
+                    o.append(rep[q])
+            while len(o) > 1 and o[0] == o[-1]:
+                o.pop()
+            if len(o) >= 3:
+                keep.append((o, plane, b))
+        used = sorted({q for o, _, _ in keep for q in o})
+        ren = {q: k for k, q in enumerate(used)}
+        out_faces, out_planes, out_nb = [], [], []
+        for o, (nv, _), b in keep:
+            out_faces.append([ren[q] for q in o])
+            if b < 0:
+                w = -1 - b
+                dabs = 1.0 if w % 2 == 0 else 0.0
+            else:
+                dabs = float(nv @ (0.5 * (s + sites[b])))
+            out_planes.append([nv[0], nv[1], nv[2], dabs])
+            out_nb.append(b)
+        cells.append((verts[used] + s, out_faces, out_planes, out_nb))
+    return VoronoiGrid(cells, sites)
+
+
+def cell_centroids(grid):
+    """Centroid of every cell: the volume-weighted mean of the tetrahedra
+    (site, fan triangle of a face)."""
+    out = np.empty((grid.ncell, 3))
+    v = np.stack([grid.vx, grid.vy, grid.vz], 1)
+    for c in range(grid.ncell):
+        s = grid.site[c]
+        tv, tc = 0.0, np.zeros(3)
+        for f in range(grid.cell_face_off[c], grid.cell_face_off[c + 1]):
+            loop = grid.face_vert[grid.face_vert_off[f]:grid.face_vert_off[f + 1]]
+            a = v[loop[0]]
+            for k in range(1, len(loop) - 1):
+                b, e = v[loop[k]], v[loop[k + 1]]
+                vol = float(np.dot(a - s, np.cross(b - s, e - s))) / 6.0
+                tv += vol
+                tc += vol * (s + a + b + e) / 4.0
+        out[c] = tc / tv
+    return out
+
+
+def merge_sites(sites, tol):
+    """Indices of the sites kept when tightly packed cells are merged
+    (Section II-A footnote): a site within tol of any earlier site is
+    dropped."""
+    sites = np.asarray(sites, np.float64).reshape(-1, 3)
+    keep = []
+    for i in range(len(sites)):
+        d2 = np.sum((sites[:i] - sites[i]) ** 2, axis=1)
+        if not np.any(d2 < tol * tol):
+            keep.append(i)
+    return np.array(keep, np.int64)
+
+
+def build_grid(sites, lloyd=5, merge_tol=0.0):
+    """Grid construction of Section II-A: merge tightly packed sites, then
+    `lloyd` Lloyd iterations (each site moved to its cell's centroid), then
+    the Voronoi cells of the final sites.  Returns (grid, kept indices)."""
+    sites = np.asarray(sites, np.float64).reshape(-1, 3)
+    keep = merge_sites(sites, merge_tol) if merge_tol > 0 else np.arange(len(sites))
+    s = sites[keep]
+    for _ in range(lloyd):
+        s = cell_centroids(voronoi_cells(s))
+    return voronoi_cells(s), keep

@@ -552,3 +552,70 @@ def test_table_mapping_mass_conservation():
     finally:
         oracle.set_table(0)
     assert dev[1] < 0.006 and dev[0] > dev[1] > dev[2], dev
+
+
+# ----------------------------------------------------------------- grid construction (Section II-A)
+
+def test_voronoi_oracle_against_definition_and_qhull():
+    """The oracle's clipped Voronoi cells: volumes tile the cube; every vertex
+    of a cell is no farther from its site than from any other site (the
+    defining property) and lies on at least three of the cell's face planes;
+    cells untouched by the walls have exactly Qhull's Voronoi vertices
+    (scipy.spatial.Voronoi); a cubic lattice gives cubes."""
+    spatial = pytest.importorskip("scipy.spatial")
+    p = synth.uniform_particles(150, 23)
+    sites = p.pos()
+    g = oracle.voronoi_cells(sites)
+    vol, _ = oracle.cell_geometry(g)
+    assert abs(vol.sum() - 1.0) < 1e-13 and np.all(vol > 0)
+    v = np.stack([g.vx, g.vy, g.vz], 1)
+    qh = spatial.Voronoi(sites)
+    n_checked = 0
+    for c in range(g.ncell):
+        fb, fe = g.cell_face_off[c], g.cell_face_off[c + 1]
+        ids = np.unique(g.face_vert[g.face_vert_off[fb]:g.face_vert_off[fe]])
+        cv = v[ids]
+        d_own = np.linalg.norm(cv - sites[c], axis=1)
+        d_all = np.linalg.norm(cv[:, None, :] - sites[None, :, :], axis=2).min(axis=1)
+        assert np.all(d_own <= d_all + 1e-12)
+        pl = g.face_plane[fb:fe]
+        on = np.abs(cv @ pl[:, :3].T - pl[:, 3]) < 1e-12
+        assert np.all(on.sum(axis=1) >= 3)
+        region = qh.regions[qh.point_region[c]]
+        if -1 in region or np.any(g.face_nb[fb:fe] < 0):
+            continue
+        qv = qh.vertices[region]
+        if len(qv) != len(cv):
+            continue  # a degenerate vertex listed twice by one side
+        dmin = np.linalg.norm(qv[:, None, :] - cv[None, :, :], axis=2).min(axis=1)
+        assert dmin.max() < 1e-10
+        n_checked += 1
+    assert n_checked >= 10
+    lat = oracle.voronoi_cells(synth.lattice_particles(3).pos())
+    lv, _ = oracle.cell_geometry(lat)
+    assert np.max(np.abs(lv * 27 - 1)) < 1e-13 and np.all(np.diff(lat.cell_face_off) == 6)
+
+
+def test_centroids_lloyd_and_merge():
+    """Cell centroids: the volume-weighted mean of the centroids is the cube's
+    centre (0.5, 0.5, 0.5) exactly; a lattice is a fixed point of the Lloyd
+    step (centroids = sites).  Lloyd iterations keep the cells tiling the
+    cube and make the cell volumes more even.  Merging drops exactly the
+    sites within tol of an earlier site."""
+    p = synth.uniform_particles(120, 31)
+    g = oracle.voronoi_cells(p.pos())
+    vol, _ = oracle.cell_geometry(g)
+    cen = oracle.cell_centroids(g)
+    assert np.max(np.abs((vol[:, None] * cen).sum(0) - 0.5)) < 1e-13
+    lat = synth.lattice_particles(3)
+    assert np.max(np.abs(oracle.cell_centroids(oracle.voronoi_cells(lat.pos())) - lat.pos())) < 1e-13
+    g2, keep = oracle.build_grid(p.pos(), lloyd=3)
+    v2, _ = oracle.cell_geometry(g2)
+    assert len(keep) == p.n and abs(v2.sum() - 1) < 1e-13
+    assert np.std(v2) < 0.7 * np.std(vol)
+    sites = np.concatenate([p.pos(), p.pos()[:10] + 1e-9, p.pos()[5:8] + 0.3e-9])
+    kept = oracle.merge_sites(sites, 1e-8)
+    assert np.array_equal(kept, np.arange(p.n))
+    d = np.linalg.norm(sites[:, None, :] - sites[None, :, :], axis=2)
+    for i in range(len(sites)):
+        assert (i in set(kept.tolist())) == (not np.any(d[i, :i] < 1e-8))
