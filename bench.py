@@ -22,6 +22,7 @@ collective on the data path); time = max over ranks.
 from __future__ import annotations
 
 import argparse
+import ctypes
 import json
 import platform
 import os
@@ -874,6 +875,118 @@ def run_inverse(args):
         torch.distributed.destroy_process_group()
 
 
+def run_tessellate(args):
+    """Grid construction on the device (Section II-A) for the clumpy-cloud
+    snapshot's 2^20 particle positions: merge sites closer than 1e-6 of the
+    mean spacing, 5 Lloyd iterations, then the clipped Voronoi cells, left
+    resident for the mapping.  A step is one map_grid_build (and the release
+    of its grid).  e2e: the sites from pinned host memory in, the grid's
+    arrays back to pinned host memory."""
+    import torch
+    import paper_2404_17084_gb300 as L
+    import oracle
+    import synth
+
+    rank, world, local = dist_env()
+    dist_init(world)
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    p = synth.lognormal_particles(args.n, rank_seed(synth.BASE_SEED + 2, rank), sigma=SIGMA)
+    n = p.n
+    tol = 1e-6 * (1.0 / n) ** (1.0 / 3.0)
+    hx, hy, hz = (torch.from_numpy(np.ascontiguousarray(a)).pin_memory() for a in (p.x, p.y, p.z))
+    x, y, z = hx.to(dev), hy.to(dev), hz.to(dev)
+    ctx = L.map_init(L.map_config_default(precision=L.MAP_MIXED, device=local))
+    info = {}
+
+    def step():
+        hd, nk = L.map_grid_build(ctx, x, y, z, 5, tol)
+        info["ncell"] = nk
+        info["sizes"] = L.map_grid_sizes(ctx, hd)
+        L.map_grid_release(ctx, hd)
+
+    sampler = ClockSampler(local)
+    for _ in range(max(args.warmup, 3)):
+        step()
+    torch.cuda.synchronize()
+    _, l0 = L.map_get_work(ctx)
+    if world > 1:
+        torch.distributed.barrier()
+    sampler.start()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(args.steps):
+        step()
+    e1.record()
+    torch.cuda.synchronize()
+    clocks = sampler.stop()
+    _, l1 = L.map_get_work(ctx)
+    ms = max_over_ranks(e0.elapsed_time(e1) / args.steps, world, dev)
+
+    def final_only():
+        hd, _ = L.map_grid_build(ctx, x, y, z, 0, tol)
+        L.map_grid_release(ctx, hd)
+
+    one_ms = _step_timer(torch, final_only, 3, 1)
+    # e2e: host sites in, host grid out
+    nc, nf, nl, nv = info["sizes"]
+    host = {k: torch.empty(sz, dtype=dt).pin_memory() for k, sz, dt in (
+        ("cfo", nc + 1, torch.int64), ("fvo", nf + 1, torch.int64), ("fv", nl, torch.int32),
+        ("fpl", 4 * nf, torch.float64), ("vx", nv, torch.float64), ("vy", nv, torch.float64),
+        ("vz", nv, torch.float64), ("site", 3 * nc, torch.float64))}
+    e2e_steps = max(args.steps, 3)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        x.copy_(hx, non_blocking=True); y.copy_(hy, non_blocking=True); z.copy_(hz, non_blocking=True)
+        hd, _ = L.map_grid_build(ctx, x, y, z, 5, tol)
+        L._check(L._lib.map_grid_copy(ctx, hd, *[ctypes.c_void_p(host[k].data_ptr()) for k in
+                                                  ("cfo", "fvo", "fv", "fpl", "vx", "vy", "vz", "site")],
+                                      L._stream(None)), "map_grid_copy")
+        torch.cuda.synchronize()
+        L.map_grid_release(ctx, hd)
+    e2e_ms = (time.perf_counter() - t0) * 1e3 / e2e_steps
+    d2h = sum(t.numel() * t.element_size() for t in host.values())
+    L.map_destroy(ctx)
+    line = {
+        "metric": "Voronoi cells/s of the grid construction (merge + 5 Lloyd iterations + clipped cells)",
+        "value": n * world / (ms * 1e-3), "unit": "sites/s", "n_gpus": world, "steps": args.steps,
+        "warmup": max(args.warmup, 3), "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": f"grid construction for the clumpy cloud: 2^{int(np.log2(n))} particle positions "
+                               "(log-normal field, sigma_ln_rho = 1.5) as sites, merge within 1e-6 of the mean "
+                               "spacing, 5 Lloyd iterations, cells clipped to the unit cube",
+                   "n_sites": n, "n_cells": int(info["ncell"]), "n_faces": int(nf), "n_loop_entries": int(nl),
+                   "step": "one map_grid_build (6 tessellations, 5 centroid passes, CSR packing, grid "
+                           "preparation) + release"},
+        "final_tessellation_ms": one_ms,
+        "e2e": {"value": n * world / (e2e_ms * 1e-3), "unit": "sites/s", "h2d_bytes_per_step": 24 * n,
+                "d2h_bytes_per_step": int(d2h), "ms_per_step": e2e_ms, "steps": e2e_steps},
+        "gpu_launches": int((l1 - l0) // max(args.steps, 1) * args.steps), "clocks": clocks,
+    }
+    if rank == 0 and not args.no_cpu_baseline:
+        # the oracle's brute-force cells on a sample of the sites (no Lloyd)
+        pos = p.pos()
+        rng = np.random.default_rng(5)
+        t0, k = time.perf_counter(), 0
+        sample = rng.choice(n, 400, replace=False)
+        while time.perf_counter() - t0 < min(args.cpu_seconds, 10.0) and k < len(sample):
+            oracle.voronoi_cells_of(pos, [int(sample[k])])
+            k += 1
+        cpu_s = time.perf_counter() - t0
+        line["cpu_baseline"] = {"value": k / cpu_s, "unit": "sites/s", "cores": 1, "kind": "oracle",
+                                "sample": f"{k} random cells of the {n} sites (no Lloyd step), {cpu_s:.1f} s"}
+        t0 = time.perf_counter()
+        synth.voronoi(pos)
+        line["host_generator_s"] = {"seconds": time.perf_counter() - t0, "threads": os.cpu_count(),
+                                    "note": "the package's host C++ tessellation of the same sites (no Lloyd)"}
+    if world > 1:
+        torch.distributed.barrier()
+    emit(line, rank)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
 def run_pseudo(args):
     """Pseudo-particle path: 2^22 particles from the log-normal field, h from
     the GPU solve, the source at the densest particle; the octree walk turns
@@ -1149,11 +1262,12 @@ def main():
     ap.add_argument("--outdir", default=os.path.join(ROOT, "bench_out"),
                     help="folder for the clock samples and --dump output")
     ap.add_argument("--workload", default="clumpy",
-                    choices=["clumpy", "batch", "serve", "uniform", "pseudo", "inverse"],
+                    choices=["clumpy", "batch", "serve", "uniform", "pseudo", "inverse", "tessellate"],
                     help="clumpy: one 2^20 snapshot (default); batch: uneven snapshots in one launch; "
                          "serve: Poisson stream of requests through the serving loop; uniform: 4096 uniform "
                          "particles, FP64; pseudo: 2^22 particles reduced to pseudo-particles; inverse: "
-                         "per-cell values carried back to the 2^20 snapshot's particles (Eq. 4)")
+                         "per-cell values carried back to the 2^20 snapshot's particles (Eq. 4); tessellate: "
+                         "the grid built on the device from the 2^20 snapshot's positions")
     ap.add_argument("--pool", type=int, default=32, help="distinct requests of the serve workload")
     ap.add_argument("--requests", type=int, default=160, help="requests submitted in the serve workload")
     ap.add_argument("--rate", type=float, default=0.0, help="serve arrival rate (req/s); 0 = 80%% of capacity")
@@ -1173,6 +1287,8 @@ def main():
         run_pseudo(args)
     elif args.workload == "inverse":
         run_inverse(args)
+    elif args.workload == "tessellate":
+        run_tessellate(args)
     else:
         run_ours(args)
 

@@ -155,6 +155,33 @@ int map_grid_release(map_ctx* ctx, int handle);
 /* Copy the volumes V_i of a resident grid into vol (device, ncell doubles). */
 int map_grid_volumes(map_ctx* ctx, int handle, double* vol, void* stream);
 
+/* Build a resident grid on the device from point sites (Section II-A): drop
+ * every site that lies within merge_tol of a site of lower index (the merging
+ * of tightly packed cells; 0 keeps all), move the sites `lloyd` times to
+ * their cells' centroids (Lloyd iterations; the paper applies 5), then
+ * tessellate: each cell is the unit cube cut by the bisector planes of its
+ * neighbours, vertices within a relative 1e-11 welded.  The grid's sites are
+ * the final (moved) sites; its cells keep their own vertices (none shared).
+ *
+ * x, y, z: device, n doubles in [0, 1].  kept (optional, device, capacity n
+ * int64): the indices of the sites that survived the merge, in order;
+ * *n_kept (optional): their number = the grid's cell count.  *handle: as
+ * map_grid_upload.  Synchronises the stream.  Workspace: about 4 KB per site
+ * while it runs (cells are built in fixed slots of 96 vertices, 48 faces and
+ * 320 loop entries).
+ * Errors: MAP_EINVAL (n < 1, a site outside the cube or not finite, lloyd <
+ * 0, merge_tol < 0), MAP_ECAPACITY (a cell outgrew its slot), MAP_ENOMEM,
+ * MAP_ECUDA. */
+int map_grid_build(map_ctx* ctx, const double* x, const double* y, const double* z, int64_t n, int lloyd,
+                   double merge_tol, int* handle, int64_t* kept, int64_t* n_kept, void* stream);
+
+/* Sizes of a resident grid (any pointer may be NULL), and a copy of its
+ * arrays in the layout of map_grid (device or page-locked host buffers of
+ * those sizes; a NULL destination is skipped; asynchronous on stream). */
+int map_grid_sizes(map_ctx* ctx, int handle, int64_t* ncell, int64_t* nface, int64_t* nloop, int64_t* nvert);
+int map_grid_copy(map_ctx* ctx, int handle, int64_t* cell_face_off, int64_t* face_vert_off, int32_t* face_vert,
+                  double* face_plane, double* vx, double* vy, double* vz, double* site, void* stream);
+
 /* ------------------------------------------------------------ the mapping (Section II-B, Eq. 1-3) */
 
 /* For every cell i of the resident grid: build the list of particles a whose

@@ -428,64 +428,72 @@ def _clip_cell(verts, faces, planes, nbs, n, d, nb):
     return new_v[used], [[ren[q] for q in loop] for loop in nf], npl, nnb
 
 
-def voronoi_cells(sites):
-    """The Voronoi cell of every site, clipped to the unit cube (Section II-A):
-    the cube cut by the bisector plane of every other site, nearest first, a
-    site at distance D being skipped once D/2 is at least the cell's largest
-    vertex radius (its plane cannot reach the cell).  Vertices within a
-    relative 1e-11 of each other are welded and faces left with fewer than
-    three vertices dropped.  Plain numpy, for small site counts."""
-    sites = np.asarray(sites, np.float64).reshape(-1, 3)
-    cells = []
-    for i, s in enumerate(sites):
-        lo, hi = -s, 1.0 - s
-        verts = np.array([[hi[0] if k & 1 else lo[0], hi[1] if k & 2 else lo[1], hi[2] if k & 4 else lo[2]]
-                          for k in range(8)])
-        faces = [[1, 3, 7, 5], [0, 4, 6, 2], [2, 6, 7, 3], [0, 1, 5, 4], [4, 5, 7, 6], [0, 2, 3, 1]]
-        axes = [np.array(v, float) for v in ((1, 0, 0), (-1, 0, 0), (0, 1, 0), (0, -1, 0), (0, 0, 1), (0, 0, -1))]
-        planes = [(axes[w], float(hi[w // 2] if w % 2 == 0 else -lo[w // 2])) for w in range(6)]
-        nbs = [-1 - w for w in range(6)]
-        d2 = np.sum((sites - s) ** 2, axis=1)
-        for j in np.argsort(d2, kind="stable"):
-            if j == i or d2[j] <= 0.0:
-                continue
-            if d2[j] >= 4.0 * float(np.max(np.sum(verts * verts, axis=1))):
+def _voronoi_cell(sites, i):
+    """The cell of site i: the cube cut by the bisector plane of every other
+    site, nearest first, a site at distance D being skipped once D/2 is at
+    least the cell's largest vertex radius (its plane cannot reach the cell).
+    Vertices within a relative 1e-11 of each other are welded and faces left
+    with fewer than three vertices dropped.  Returns (vertices, loops,
+    planes, neighbours) with absolute vertices."""
+    s = sites[i]
+    lo, hi = -s, 1.0 - s
+    verts = np.array([[hi[0] if k & 1 else lo[0], hi[1] if k & 2 else lo[1], hi[2] if k & 4 else lo[2]]
+                      for k in range(8)])
+    faces = [[1, 3, 7, 5], [0, 4, 6, 2], [2, 6, 7, 3], [0, 1, 5, 4], [4, 5, 7, 6], [0, 2, 3, 1]]
+    axes = [np.array(v, float) for v in ((1, 0, 0), (-1, 0, 0), (0, 1, 0), (0, -1, 0), (0, 0, 1), (0, 0, -1))]
+    planes = [(axes[w], float(hi[w // 2] if w % 2 == 0 else -lo[w // 2])) for w in range(6)]
+    nbs = [-1 - w for w in range(6)]
+    d2 = np.sum((sites - s) ** 2, axis=1)
+    for j in np.argsort(d2, kind="stable"):
+        if j == i or d2[j] <= 0.0:
+            continue
+        if d2[j] >= 4.0 * float(np.max(np.sum(verts * verts, axis=1))):
+            break
+        dd = sites[j] - s
+        ln = math.sqrt(d2[j])
+        verts, faces, planes, nbs = _clip_cell(verts, faces, planes, nbs, dd / ln, 0.5 * ln, int(j))
+    scale = math.sqrt(max(float(np.max(np.sum(verts * verts, axis=1))), 1e-300))
+    rep = list(range(len(verts)))
+    for a in range(len(verts)):
+        for b in range(a):
+            if rep[b] == b and np.sum((verts[a] - verts[b]) ** 2) < (1e-11 * scale) ** 2:
+                rep[a] = b
                 break
-            dd = sites[j] - s
-            ln = math.sqrt(d2[j])
-            verts, faces, planes, nbs = _clip_cell(verts, faces, planes, nbs, dd / ln, 0.5 * ln, int(j))
-        # weld and drop degenerate faces
-        scale = math.sqrt(max(float(np.max(np.sum(verts * verts, axis=1))), 1e-300))
-        rep = list(range(len(verts)))
-        for a in range(len(verts)):
-            for b in range(a):
-                if rep[b] == b and np.sum((verts[a] - verts[b]) ** 2) < (1e-11 * scale) ** 2:
-                    rep[a] = b
-                    break
-        keep = []
-        for loop, plane, b in zip(faces, planes, nbs):
-            o = []
-            for q in loop:
-                if not o or o[-1] != rep[q]:
-                    o.append(rep[q])
-            while len(o) > 1 and o[0] == o[-1]:
-                o.pop()
-            if len(o) >= 3:
-                keep.append((o, plane, b))
-        used = sorted({q for o, _, _ in keep for q in o})
-        ren = {q: k for k, q in enumerate(used)}
-        out_faces, out_planes, out_nb = [], [], []
-        for o, (nv, _), b in keep:
-            out_faces.append([ren[q] for q in o])
-            if b < 0:
-                w = -1 - b
-                dabs = 1.0 if w % 2 == 0 else 0.0
-            else:
-                dabs = float(nv @ (0.5 * (s + sites[b])))
-            out_planes.append([nv[0], nv[1], nv[2], dabs])
-            out_nb.append(b)
-        cells.append((verts[used] + s, out_faces, out_planes, out_nb))
-    return VoronoiGrid(cells, sites)
+    keep = []
+    for loop, plane, b in zip(faces, planes, nbs):
+        o = []
+        for q in loop:
+            if not o or o[-1] != rep[q]:
+                o.append(rep[q])
+        while len(o) > 1 and o[0] == o[-1]:
+            o.pop()
+        if len(o) >= 3:
+            keep.append((o, plane, b))
+    used = sorted({q for o, _, _ in keep for q in o})
+    ren = {q: k for k, q in enumerate(used)}
+    out_faces, out_planes, out_nb = [], [], []
+    for o, (nv, _), b in keep:
+        out_faces.append([ren[q] for q in o])
+        if b < 0:
+            dabs = 1.0 if (-1 - b) % 2 == 0 else 0.0
+        else:
+            dabs = float(nv @ (0.5 * (s + sites[b])))
+        out_planes.append([nv[0], nv[1], nv[2], dabs])
+        out_nb.append(b)
+    return verts[used] + s, out_faces, out_planes, out_nb
+
+
+def voronoi_cells_of(sites, which):
+    """The cells of the listed sites only (each against all sites)."""
+    sites = np.asarray(sites, np.float64).reshape(-1, 3)
+    return [_voronoi_cell(sites, int(i)) for i in which]
+
+
+def voronoi_cells(sites):
+    """The Voronoi cell of every site, clipped to the unit cube (Section
+    II-A), as a VoronoiGrid.  Plain numpy, for small site counts."""
+    sites = np.asarray(sites, np.float64).reshape(-1, 3)
+    return VoronoiGrid([_voronoi_cell(sites, i) for i in range(len(sites))], sites)
 
 
 def cell_centroids(grid):

@@ -77,6 +77,10 @@ _lib.map_strerror.restype = ctypes.c_char_p
 _lib.map_grid_upload.argtypes = [_P, ctypes.POINTER(map_grid), ctypes.POINTER(ctypes.c_int), _P]
 _lib.map_grid_release.argtypes = [_P, ctypes.c_int]
 _lib.map_grid_volumes.argtypes = [_P, ctypes.c_int, _P, _P]
+_lib.map_grid_build.argtypes = [_P, _P, _P, _P, _I64, ctypes.c_int, ctypes.c_double, ctypes.POINTER(ctypes.c_int),
+                                _P, ctypes.POINTER(_I64), _P]
+_lib.map_grid_sizes.argtypes = [_P, ctypes.c_int] + [ctypes.POINTER(_I64)] * 4
+_lib.map_grid_copy.argtypes = [_P, ctypes.c_int] + [_P] * 8 + [_P]
 _lib.map_particles_to_cells.argtypes = [_P, ctypes.POINTER(map_particles), ctypes.c_int, ctypes.POINTER(map_outputs), _P]
 _lib.map_get_pairs.argtypes = [_P, ctypes.POINTER(_P), ctypes.POINTER(_P), ctypes.POINTER(_P), ctypes.POINTER(_I64)]
 _lib.map_copy_pairs.argtypes = [_P, _P, _P, _P, _I64, _P]
@@ -130,7 +134,8 @@ _lib.map_batch.argtypes = [_P, ctypes.c_int, ctypes.POINTER(map_particles), ctyp
                            ctypes.POINTER(map_outputs), _P, _P]
 _lib.map_get_autotune.argtypes = [_P, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_float),
                                   ctypes.POINTER(ctypes.c_int)]
-for _name in ("map_init", "map_grid_upload", "map_grid_release", "map_grid_volumes", "map_particles_to_cells",
+for _name in ("map_init", "map_grid_upload", "map_grid_release", "map_grid_volumes", "map_grid_build",
+              "map_grid_sizes", "map_grid_copy", "map_particles_to_cells",
               "map_get_pairs", "map_copy_pairs", "map_cells_to_particles", "map_get_stats", "map_get_work",
               "map_get_timing", "solve_h", "build_pseudo_particles", "build_pseudo_particles_walk", "map_batch",
               "map_get_autotune", "solve_h_batch"):
@@ -355,6 +360,43 @@ def map_cells_to_particles(ctx, cell_value, particle_value, stream=None):
     _check(_lib.map_cells_to_particles(ctx, _ptr(cell_value), _ptr(particle_value), particle_value.numel(),
                                        _stream(stream)), "map_cells_to_particles")
     return particle_value
+
+
+def map_grid_build(ctx, x, y, z, lloyd: int = 5, merge_tol: float = 0.0, kept=None, stream=None):
+    """Grid construction on the device (Section II-A): merge, Lloyd
+    iterations, Voronoi cells.  x, y, z: float64 CUDA tensors of the sites;
+    kept: optional int64 CUDA tensor (capacity n) for the surviving site
+    indices.  Returns (grid handle, number of cells)."""
+    h = ctypes.c_int(-1)
+    nk = _I64(0)
+    _check(_lib.map_grid_build(ctx, _ptr(x), _ptr(y), _ptr(z), x.numel(), int(lloyd), float(merge_tol),
+                               ctypes.byref(h), _ptr(kept), ctypes.byref(nk), _stream(stream)), "map_grid_build")
+    return h.value, nk.value
+
+
+def map_grid_sizes(ctx, handle: int):
+    v = [_I64(0) for _ in range(4)]
+    _check(_lib.map_grid_sizes(ctx, handle, *[ctypes.byref(a) for a in v]), "map_grid_sizes")
+    return tuple(a.value for a in v)
+
+
+def map_grid_copy(ctx, handle: int, device=None, stream=None) -> dict:
+    """A resident grid's arrays as new CUDA tensors (the layout of map_grid)."""
+    nc, nf, nl, nv = map_grid_sizes(ctx, handle)
+    dev = device or torch.device("cuda", torch.cuda.current_device())
+    e = lambda n, dt: torch.empty(max(n, 1), dtype=dt, device=dev)
+    out = dict(cell_face_off=e(nc + 1, torch.int64), face_vert_off=e(nf + 1, torch.int64),
+               face_vert=e(nl, torch.int32), face_plane=e(4 * nf, torch.float64), vx=e(nv, torch.float64),
+               vy=e(nv, torch.float64), vz=e(nv, torch.float64), site=e(3 * nc, torch.float64))
+    _check(_lib.map_grid_copy(ctx, handle, *[_ptr(out[k]) for k in ("cell_face_off", "face_vert_off", "face_vert",
+                                                                     "face_plane", "vx", "vy", "vz", "site")],
+                              _stream(stream)), "map_grid_copy")
+    out["face_vert"] = out["face_vert"][:nl]
+    out["face_plane"] = out["face_plane"][:4 * nf].view(nf, 4) if nf else out["face_plane"][:0].view(0, 4)
+    for k in ("vx", "vy", "vz"):
+        out[k] = out[k][:nv]
+    out["site"] = out["site"][:3 * nc].view(nc, 3)
+    return out
 
 
 def map_get_stats(ctx) -> map_stats:

@@ -149,6 +149,7 @@ void map_destroy(map_ctx* ctx) {
   for (auto& b : ctx->ws_pairs) if (b.p) cudaFree(b.p);
   for (auto& b : ctx->ws_misc) if (b.p) cudaFree(b.p);
   for (auto& b : ctx->ws_inv) if (b.p) cudaFree(b.p);
+  for (auto& b : ctx->ws_vor) if (b.p) cudaFree(b.p);
   table_free(ctx);
   for (auto& b : ctx->ws_grid) if (b.p) cudaFree(b.p);
   if (ctx->cub_tmp.p) cudaFree(ctx->cub_tmp.p);
@@ -188,6 +189,39 @@ int map_grid_upload(map_ctx* ctx, const map_grid* grid, int* handle, void* strea
     if (!ctx->grids[i]) { ctx->grids[i] = g; *handle = (int)i; return MAP_OK; }
   ctx->grids.push_back(g);
   *handle = (int)ctx->grids.size() - 1;
+  return MAP_OK;
+}
+
+int map_grid_sizes(map_ctx* ctx, int handle, int64_t* ncell, int64_t* nface, int64_t* nloop, int64_t* nvert) {
+  if (!ctx) return MAP_EINVAL;
+  if (handle < 0 || handle >= (int)ctx->grids.size() || !ctx->grids[handle]) return MAP_EHANDLE;
+  const PreparedGrid* g = ctx->grids[handle];
+  if (ncell) *ncell = g->ncell;
+  if (nface) *nface = g->nface;
+  if (nloop) *nloop = g->nloop;
+  if (nvert) *nvert = g->nvert;
+  return MAP_OK;
+}
+
+int map_grid_copy(map_ctx* ctx, int handle, int64_t* cell_face_off, int64_t* face_vert_off, int32_t* face_vert,
+                  double* face_plane, double* vx, double* vy, double* vz, double* site, void* stream) {
+  if (!ctx) return MAP_EINVAL;
+  if (handle < 0 || handle >= (int)ctx->grids.size() || !ctx->grids[handle]) return MAP_EHANDLE;
+  const PreparedGrid* g = ctx->grids[handle];
+  CUDA_TRY(cudaSetDevice(ctx->device));
+  cudaStream_t s = S(stream);
+  auto cp = [&](void* dst, const void* src, size_t bytes) -> int {
+    if (dst && bytes) CUDA_TRY(cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDefault, s));
+    return MAP_OK;
+  };
+  MAP_TRY(cp(cell_face_off, g->cell_face_off, (g->ncell + 1) * sizeof(int64_t)));
+  MAP_TRY(cp(face_vert_off, g->face_vert_off, (g->nface + 1) * sizeof(int64_t)));
+  MAP_TRY(cp(face_vert, g->face_vert, g->nloop * sizeof(int32_t)));
+  MAP_TRY(cp(face_plane, g->face_plane, g->nface * 4 * sizeof(double)));
+  MAP_TRY(cp(vx, g->vx, g->nvert * sizeof(double)));
+  MAP_TRY(cp(vy, g->vy, g->nvert * sizeof(double)));
+  MAP_TRY(cp(vz, g->vz, g->nvert * sizeof(double)));
+  MAP_TRY(cp(site, g->site, g->ncell * 3 * sizeof(double)));
   return MAP_OK;
 }
 

@@ -84,6 +84,7 @@ void trim(map_ctx* ctx) {
   for (auto& b : ctx->ws_pairs) drop(b);
   for (auto& b : ctx->ws_misc) drop(b);
   for (auto& b : ctx->ws_inv) drop(b);
+  for (auto& b : ctx->ws_vor) drop(b);
   for (auto& b : ctx->ws_grid) drop(b);
   for (auto* v : {&ctx->batch_off, &ctx->batch_idx, &ctx->batch_itm, &ctx->batch_ioff, &ctx->batch_part})
     for (auto& b : *v) drop(b);
