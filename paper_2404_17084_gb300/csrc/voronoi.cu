@@ -28,9 +28,10 @@
 
 namespace {
 
-constexpr int VOR_MAXV = 96;
-constexpr int VOR_MAXF = 48;
-constexpr int VOR_MAXL = 320;
+constexpr int VOR_MAXV = 128;
+constexpr int VOR_MAXF = 64;
+constexpr int VOR_MAXL = 448;
+constexpr int VOR_NEAR = 32;  // nearest sites of the surrounding 27 buckets, cut first and in order
 
 struct Poly {
   int nv, nf, nl;
@@ -327,7 +328,45 @@ __global__ void __launch_bounds__(64) vor_cells(int64_t n, const double* __restr
   const double bw = 1.0 / G;
   const int bx = bucket_coord(sx, G), by = bucket_coord(sy, G), bz = bucket_coord(sz, G);
   bool bad = false;
-  for (int r = 0; r <= G && !bad; ++r) {
+  // first the VOR_NEAR nearest sites of the 27 surrounding buckets, nearest
+  // first (they shape the cell; later cuts are then mostly skipped)
+  double kd2[VOR_NEAR];
+  int kj[VOR_NEAR];
+  int kn = 0;
+  for (int dz = -1; dz <= 1; ++dz)
+    for (int dy = -1; dy <= 1; ++dy)
+      for (int dx = -1; dx <= 1; ++dx) {
+        const int cx = bx + dx, cy = by + dy, cz = bz + dz;
+        if (cx < 0 || cy < 0 || cz < 0 || cx >= G || cy >= G || cz >= G) continue;
+        const int64_t b = ((int64_t)cz * G + cy) * G + cx;
+        for (int64_t q = B.off[b]; q < B.off[b + 1]; ++q) {
+          const int32_t j = B.sites[q];
+          if (j == i) continue;
+          const double ex = x[j] - sx, ey = y[j] - sy, ez = z[j] - sz;
+          const double d2 = ex * ex + ey * ey + ez * ez;
+          if (d2 <= 0.0 || (kn == VOR_NEAR && d2 >= kd2[VOR_NEAR - 1])) continue;
+          int k = kn < VOR_NEAR ? kn++ : VOR_NEAR - 1;
+          for (; k > 0 && (kd2[k - 1] > d2 || (kd2[k - 1] == d2 && kj[k - 1] > j)); --k) {
+            kd2[k] = kd2[k - 1];
+            kj[k] = kj[k - 1];
+          }
+          kd2[k] = d2;
+          kj[k] = j;
+        }
+      }
+  for (int k = 0; k < kn && !bad; ++k) {
+    if (kd2[k] >= 4.0 * P->rmax2) break;
+    const int j = kj[k];
+    const double ex = x[j] - sx, ey = y[j] - sy, ez = z[j] - sz;
+    const double len = sqrt(kd2[k]);
+    const int rc = poly_clip(*P, *Q, ex / len, ey / len, ez / len, 0.5 * len, j);
+    if (rc < 0) bad = true;
+    else if (rc > 0) { Poly* t = P; P = Q; Q = t; }
+  }
+  // then every other site, ring by ring (the 27 buckets again only when the
+  // nearest list was full: sites closer than its last entry are done)
+  const double done2 = kn == VOR_NEAR ? kd2[VOR_NEAR - 1] : 1e300;
+  for (int r = kn == VOR_NEAR ? 0 : 2; r <= G && !bad; ++r) {
     // every site outside rings 0..r-1 is at least (r-1) bucket widths away
     const double reach = (r - 1) * bw;
     if (r >= 2 && reach * reach >= 4.0 * P->rmax2) break;
@@ -343,7 +382,7 @@ __global__ void __launch_bounds__(64) vor_cells(int64_t n, const double* __restr
             if (j == i) continue;
             const double ex = x[j] - sx, ey = y[j] - sy, ez = z[j] - sz;
             const double d2 = ex * ex + ey * ey + ez * ez;
-            if (d2 <= 0.0 || d2 >= 4.0 * P->rmax2) continue;
+            if (d2 <= 0.0 || d2 >= 4.0 * P->rmax2 || (r <= 1 && d2 < done2)) continue;
             const double len = sqrt(d2);
             const int rc = poly_clip(*P, *Q, ex / len, ey / len, ez / len, 0.5 * len, j);
             if (rc < 0) { bad = true; break; }
