@@ -28,9 +28,9 @@
 
 namespace {
 
-constexpr int VOR_MAXV = 128;
-constexpr int VOR_MAXF = 64;
-constexpr int VOR_MAXL = 448;
+constexpr int VOR_MAXV = 96;
+constexpr int VOR_MAXF = 48;
+constexpr int VOR_MAXL = 320;
 constexpr int VOR_NEAR = 32;  // nearest sites of the surrounding 27 buckets, cut first and in order
 
 struct Poly {
@@ -247,7 +247,7 @@ struct Buckets {
   const int32_t* sites;  // site indices grouped by bucket
 };
 
-__device__ __forceinline__ int bucket_coord(double v, int G) {
+__host__ __device__ __forceinline__ int bucket_coord(double v, int G) {
   int b = (int)floor(v * G);
   return b < 0 ? 0 : (b >= G ? G - 1 : b);
 }
@@ -313,12 +313,11 @@ struct SlotArrays {
   int* nb;              // VOR_MAXF per cell
 };
 
-// One thread per site: its cell, written to its slot.
-__global__ void __launch_bounds__(64) vor_cells(int64_t n, const double* __restrict__ x, const double* __restrict__ y,
-                                                const double* __restrict__ z, Buckets B, SlotArrays S,
-                                                unsigned long long* overflow) {
-  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (i >= n) return;
+// The cell of site i, written to its slot (one thread; also callable on the
+// host).  Returns false when the cell outgrew the slot.
+__host__ __device__ __forceinline__ void build_cell(int64_t i, const double* __restrict__ x,
+                                                    const double* __restrict__ y, const double* __restrict__ z,
+                                                    const Buckets& B, const SlotArrays& S, int* overflow_local) {
   Poly A, C;
   Poly* P = &A;
   Poly* Q = &C;
@@ -373,7 +372,8 @@ __global__ void __launch_bounds__(64) vor_cells(int64_t n, const double* __restr
     for (int dz = -r; dz <= r && !bad; ++dz)
       for (int dy = -r; dy <= r && !bad; ++dy)
         for (int dx = -r; dx <= r && !bad; ++dx) {
-          if (max(abs(dx), max(abs(dy), abs(dz))) != r) continue;
+          const int ax = dx < 0 ? -dx : dx, ay = dy < 0 ? -dy : dy, az = dz < 0 ? -dz : dz;
+          if ((ax > ay ? (ax > az ? ax : az) : (ay > az ? ay : az)) != r) continue;
           const int cx = bx + dx, cy = by + dy, cz = bz + dz;
           if (cx < 0 || cy < 0 || cz < 0 || cx >= G || cy >= G || cz >= G) continue;
           const int64_t b = ((int64_t)cz * G + cy) * G + cx;
@@ -404,9 +404,20 @@ __global__ void __launch_bounds__(64) vor_cells(int64_t n, const double* __restr
       S.nb[(size_t)i * VOR_MAXF + f] = P->nb[f];
     }
   } else {
-    atomicAdd(overflow, 1ULL);
+    ++*overflow_local;
   }
   S.info[i] = info;
+}
+
+// One thread per site: its cell, written to its slot.
+__global__ void __launch_bounds__(64) vor_cells(int64_t n, const double* __restrict__ x, const double* __restrict__ y,
+                                                const double* __restrict__ z, Buckets B, SlotArrays S,
+                                                unsigned long long* overflow) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  int over = 0;
+  build_cell(i, x, y, z, B, S, &over);
+  if (over) atomicAdd(overflow, 1ULL);
 }
 
 // centroid of each cell (site + volume-weighted mean of the fan tetrahedra)
