@@ -409,12 +409,15 @@ __host__ __device__ __forceinline__ void build_cell(int64_t i, const double* __r
   S.info[i] = info;
 }
 
-// One thread per site: its cell, written to its slot.
+// One thread per site, the sites taken in bucket order so that the threads
+// of a warp build neighbouring cells (the same candidate buckets, similar
+// work): its cell, written to its slot.
 __global__ void __launch_bounds__(64) vor_cells(int64_t n, const double* __restrict__ x, const double* __restrict__ y,
                                                 const double* __restrict__ z, Buckets B, SlotArrays S,
                                                 unsigned long long* overflow) {
-  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (i >= n) return;
+  const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (t >= n) return;
+  const int64_t i = B.sites[t];
   int over = 0;
   build_cell(i, x, y, z, B, S, &over);
   if (over) atomicAdd(overflow, 1ULL);
