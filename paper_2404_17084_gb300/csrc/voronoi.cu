@@ -412,7 +412,7 @@ __host__ __device__ __forceinline__ void build_cell(int64_t i, const double* __r
 // One thread per site, the sites taken in bucket order so that the threads
 // of a warp build neighbouring cells (the same candidate buckets, similar
 // work): its cell, written to its slot.
-__global__ void __launch_bounds__(64) vor_cells(int64_t n, const double* __restrict__ x, const double* __restrict__ y,
+__global__ void __launch_bounds__(64, 16) vor_cells(int64_t n, const double* __restrict__ x, const double* __restrict__ y,
                                                 const double* __restrict__ z, Buckets B, SlotArrays S,
                                                 unsigned long long* overflow) {
   const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
