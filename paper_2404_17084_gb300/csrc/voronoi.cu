@@ -553,13 +553,15 @@ int vor_tessellate(map_ctx* ctx, const double* x, const double* y, const double*
   MAP_TRY(ensure_t(ctx, ctx->ws_vor[10], (size_t)n * VOR_MAXF, &S.nb));
   unsigned long long* d_over = ctx->d_counters + 7;
   CUDA_TRY(cudaMemsetAsync(d_over, 0, sizeof(unsigned long long), s));
-  // the cell builder keeps two polyhedra per thread in local memory: make
-  // sure the per-thread stack holds its frame
+  // the cell builder keeps two polyhedra per thread in local memory (a frame
+  // of about 14 KB): make sure the per-thread stack holds it, whatever the
+  // function attributes report
   cudaFuncAttributes fa{};
   CUDA_TRY(cudaFuncGetAttributes(&fa, vor_cells));
   size_t stack = 0;
   CUDA_TRY(cudaDeviceGetLimit(&stack, cudaLimitStackSize));
-  if (stack < fa.localSizeBytes + 1024) CUDA_TRY(cudaDeviceSetLimit(cudaLimitStackSize, fa.localSizeBytes + 1024));
+  const size_t need = (fa.localSizeBytes > 16384 ? fa.localSizeBytes : 16384) + 1024;
+  if (stack < need) CUDA_TRY(cudaDeviceSetLimit(cudaLimitStackSize, need));
   vor_cells<<<nblk(n, 64), 64, 0, s>>>(n, x, y, z, B, S, d_over); ++ctx->launches;
   CUDA_TRY(cudaGetLastError());
   CUDA_TRY(cudaMemcpyAsync(ctx->h_scratch, d_over, sizeof(unsigned long long), cudaMemcpyDeviceToHost, s));
