@@ -40,8 +40,7 @@ struct Poly {
   short fs[VOR_MAXF];          // first loop entry of each face
   unsigned char fl[VOR_MAXF];  // loop length
   int nb[VOR_MAXF];            // neighbour site, or -1-w for wall w
-  double rmax2;                // largest squared vertex radius
-  double lo[3], hi[3];         // bounding box of the vertices
+  double rmax2;
 };
 
 // a cell as written to its slot (site-relative vertices)
@@ -64,19 +63,12 @@ __host__ __device__ __forceinline__ void poly_box(Poly& P, double sx, double sy,
   double r = 0.0;
   for (int i = 0; i < 8; ++i) r = fmax(r, P.vx[i] * P.vx[i] + P.vy[i] * P.vy[i] + P.vz[i] * P.vz[i]);
   P.rmax2 = r;
-  for (int k = 0; k < 3; ++k) { P.lo[k] = lo[k]; P.hi[k] = hi[k]; }
 }
 
 // Cut P by n.x <= d into Q.  Returns 0 when nothing changed (Q untouched), 1
 // when Q holds the cut cell, -1 on overflow.
 __host__ __device__ __forceinline__ int poly_clip(const Poly& P, Poly& Q, double nx, double ny, double nz, double d, int nbid) {
   const double tol = 1e-13 * sqrt(P.rmax2);
-  // the bounding box's support in direction n bounds n.v over the vertices:
-  // a plane beyond it (with half the tolerance to spare for rounding) cuts
-  // nothing, decided without visiting the vertices
-  const double sup = fmax(nx * P.lo[0], nx * P.hi[0]) + fmax(ny * P.lo[1], ny * P.hi[1]) +
-                     fmax(nz * P.lo[2], nz * P.hi[2]);
-  if (sup - d < 0.5 * tol) return 0;
   signed char cls[VOR_MAXV];
   double s[VOR_MAXV];
   double smax = -1e300;
@@ -194,17 +186,12 @@ __host__ __device__ __forceinline__ int poly_clip(const Poly& P, Poly& Q, double
     Q.loop[k] = (unsigned char)used[id];
   }
   double r = 0.0;
-  double blo[3] = {1e300, 1e300, 1e300}, bhi[3] = {-1e300, -1e300, -1e300};
   for (int i = 0; i < nv; ++i) {
     Q.vx[i] = tx[i]; Q.vy[i] = ty[i]; Q.vz[i] = tz[i];
     r = fmax(r, tx[i] * tx[i] + ty[i] * ty[i] + tz[i] * tz[i]);
-    blo[0] = fmin(blo[0], tx[i]); bhi[0] = fmax(bhi[0], tx[i]);
-    blo[1] = fmin(blo[1], ty[i]); bhi[1] = fmax(bhi[1], ty[i]);
-    blo[2] = fmin(blo[2], tz[i]); bhi[2] = fmax(bhi[2], tz[i]);
   }
   Q.nv = nv;
   Q.rmax2 = r;
-  for (int k = 0; k < 3; ++k) { Q.lo[k] = blo[k]; Q.hi[k] = bhi[k]; }
   return 1;
 }
 
@@ -251,7 +238,6 @@ __host__ __device__ __forceinline__ void poly_compact(Poly& P, Poly& Q) {
   }
   Q.nv = nv;
   Q.rmax2 = P.rmax2;
-  for (int k = 0; k < 3; ++k) { Q.lo[k] = P.lo[k]; Q.hi[k] = P.hi[k]; }
   P = Q;
 }
 
