@@ -98,6 +98,8 @@ class map_walk(ctypes.Structure):
                 ("regions", _P), ("nregion", ctypes.c_int)]
 
 
+_lib.solve_h_noalloc.argtypes = [_P, _P, _P, _I64, ctypes.c_double, _P, _P, _P]
+_lib.solve_h_noalloc.restype = ctypes.c_int
 _lib.build_pseudo_particles_walk.argtypes = [_P, ctypes.POINTER(map_particles), ctypes.POINTER(map_walk),
                                              ctypes.POINTER(map_particles), _P, _P, ctypes.POINTER(_I64), _P]
 
@@ -436,6 +438,34 @@ def solve_h_batch(ctx, parts, routes=None, stream=None) -> None:
     _check(_lib.solve_h_batch(ctx, n, P, R, _stream(stream)), "solve_h_batch")
 
 
+def solve_h_noalloc(x, y, z, h, route=None, hfact: float = 1.2, stream=None) -> None:
+    """solve_h without a context or device allocations (at most 32768
+    particles; see the header): x, y, z, h float64 CUDA tensors, route an
+    optional int32 CUDA tensor."""
+    _check(_lib.solve_h_noalloc(_ptr(x), _ptr(y), _ptr(z), x.numel(), float(hfact), _ptr(h), _ptr(route),
+                                _stream(stream)), "solve_h_noalloc")
+
+
+def build_pseudo_particles_walk(ctx, full: map_particles, src, out: map_particles, kind=None, ident=None,
+                                r_part=0.0, r_leaf=0.0, regions=None, stream=None):
+    """build_pseudo_particles through the walk-controls entry point (Section
+    III-B: r_part, r_leaf, regions of an earlier step, several sources)."""
+    srcs = [float(v) for v in np.asarray(src, dtype=np.float64).ravel()]
+    arr = (ctypes.c_double * len(srcs))(*srcs)
+    regs = [] if regions is None else [float(v) for v in np.asarray(regions, dtype=np.float64).ravel()]
+    rarr = (ctypes.c_double * max(len(regs), 1))(*regs)
+    walk = map_walk(ctypes.cast(arr, _P), len(srcs) // 3, float(r_part), float(r_leaf),
+                    ctypes.cast(rarr, _P) if regs else None, len(regs) // 5)
+    n = ctypes.c_int64(0)
+    code = _lib.build_pseudo_particles_walk(ctx, ctypes.byref(full), ctypes.byref(walk), ctypes.byref(out),
+                                            _ptr(kind), _ptr(ident), ctypes.byref(n), _stream(stream))
+    if code != MAP_OK:
+        err = MapError(code, "build_pseudo_particles_walk")
+        err.required = n.value
+        raise err
+    return n.value
+
+
 def build_pseudo_particles(ctx, full: map_particles, src, out: map_particles, kind=None, ident=None, stream=None,
                            r_part=0.0, r_leaf=0.0, regions=None):
     """Returns the number of pseudo-particles written (raises MapError with
@@ -449,12 +479,7 @@ def build_pseudo_particles(ctx, full: map_particles, src, out: map_particles, ki
         code = _lib.build_pseudo_particles(ctx, ctypes.byref(full), arr, len(srcs) // 3, ctypes.byref(out),
                                            _ptr(kind), _ptr(ident), ctypes.byref(n), _stream(stream))
     else:
-        regs = [] if regions is None else [float(v) for v in np.asarray(regions, dtype=np.float64).ravel()]
-        rarr = (ctypes.c_double * max(len(regs), 1))(*regs)
-        walk = map_walk(ctypes.cast(arr, _P), len(srcs) // 3, float(r_part), float(r_leaf),
-                        ctypes.cast(rarr, _P) if regs else None, len(regs) // 5)
-        code = _lib.build_pseudo_particles_walk(ctx, ctypes.byref(full), ctypes.byref(walk), ctypes.byref(out),
-                                                _ptr(kind), _ptr(ident), ctypes.byref(n), _stream(stream))
+        return build_pseudo_particles_walk(ctx, full, src, out, kind, ident, r_part, r_leaf, regions, stream)
     if code != MAP_OK:
         err = MapError(code, "build_pseudo_particles")
         err.required = n.value

@@ -44,3 +44,11 @@ def test_strerror_and_defaults_without_gpu():
     lib.map_strerror.restype = ctypes.c_char_p
     assert lib.map_strerror(0) == b"ok"
     assert b"memory" in lib.map_strerror(-2)
+
+
+def test_binding_wraps_every_declared_symbol():
+    """The Python binding has a function of the same name for every entry
+    point the header declares (argument marshalling only)."""
+    import paper_2404_17084_gb300 as L
+    missing = sorted(n for n in declared_functions() if not callable(getattr(L, n, None)))
+    assert not missing, missing
