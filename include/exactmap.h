@@ -166,9 +166,11 @@ int map_grid_volumes(map_ctx* ctx, int handle, double* vol, void* stream);
  * x, y, z: device, n doubles in [0, 1].  kept (optional, device, capacity n
  * int64): the indices of the sites that survived the merge, in order;
  * *n_kept (optional): their number = the grid's cell count.  *handle: as
- * map_grid_upload.  Synchronises the stream.  Workspace: about 4 KB per site
- * while it runs (cells are built in fixed slots of 96 vertices, 48 faces and
- * 320 loop entries).
+ * map_grid_upload.  Synchronises the stream.  Workspace: about 3 KB per site
+ * (cells are built in fixed slots of 96 vertices, 48 faces and 320 loop
+ * entries), kept by the context for later builds until map_destroy; the
+ * first call also raises the per-thread stack to at least 17 KB for the
+ * context's device.
  * Errors: MAP_EINVAL (n < 1, a site outside the cube or not finite, lloyd <
  * 0, merge_tol < 0), MAP_ECAPACITY (a cell outgrew its slot), MAP_ENOMEM,
  * MAP_ECUDA. */
