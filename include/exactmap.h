@@ -241,10 +241,11 @@ int map_copy_pairs(map_ctx* ctx, int64_t* pair_off, int32_t* pair_idx, double* p
  * list gets 0.
  *
  * The first call after a mapping builds a particle-major copy of its pair
- * list (cell and f_ai of every pair, 12 bytes per pair, plus 8 bytes per
- * particle; radix-sort workspace on top while it is built), kept by the
- * context until the next mapping call; later calls with other cell values
- * reuse it.  Asynchronous on stream, which the caller orders after the
+ * list (cell and f_ai of every pair, 12 bytes per pair, plus 12 bytes per
+ * particle), kept by the context until the next mapping call; later calls
+ * with other cell values reuse it.  The build's sort workspace (about 20
+ * bytes per pair) also stays with the context, for the next mapping's build,
+ * until map_destroy.  Asynchronous on stream, which the caller orders after the
  * mapping call (the same stream, or an event); on another stream than the
  * mapping call's, the first call waits for the copy to be built.
  * Errors: MAP_EINVAL (NULL pointer; no single mapping call with per-pair
