@@ -464,6 +464,19 @@ typedef struct {
 int build_pseudo_particles_walk(map_ctx* ctx, const map_particles* full, const map_walk* walk, map_particles* out,
                                 int32_t* kind, int64_t* ident, int64_t* n_pseudo, void* stream);
 
+/* ------------------------------------------------------------ measurement */
+
+/* Measured issue rates of device `device`, in lane operations per second
+ * (one FMA = one operation): FP32 FMA, the special-function unit
+ * (reciprocal square root) and FP64 FMA, each from a grid of 16 blocks of
+ * 256 threads per SM running eight independent dependency chains per thread,
+ * timed with CUDA events after a warm-up launch (a few milliseconds each).
+ * They are the denominators of the pair-integral kernel's roofline (its
+ * operation model counts FP32 and special-function operations).  The paper
+ * has no counterpart.  Synchronises the device.
+ * Errors: MAP_EINVAL (NULL output), MAP_ECUDA. */
+int map_device_peaks(int device, double* ffma, double* mufu, double* dfma);
+
 #ifdef __cplusplus
 }
 #endif

@@ -98,6 +98,8 @@ class map_walk(ctypes.Structure):
                 ("regions", _P), ("nregion", ctypes.c_int)]
 
 
+_lib.map_device_peaks.argtypes = [ctypes.c_int] + [ctypes.POINTER(ctypes.c_double)] * 3
+_lib.map_device_peaks.restype = ctypes.c_int
 _lib.solve_h_noalloc.argtypes = [_P, _P, _P, _I64, ctypes.c_double, _P, _P, _P]
 _lib.solve_h_noalloc.restype = ctypes.c_int
 _lib.build_pseudo_particles_walk.argtypes = [_P, ctypes.POINTER(map_particles), ctypes.POINTER(map_walk),
@@ -436,6 +438,14 @@ def solve_h_batch(ctx, parts, routes=None, stream=None) -> None:
     if routes is not None:
         R = (_P * n)(*[_ptr(r) if r is not None else None for r in routes])
     _check(_lib.solve_h_batch(ctx, n, P, R, _stream(stream)), "solve_h_batch")
+
+
+def map_device_peaks(device: int = 0) -> dict:
+    """Measured issue rates (lane operations per second) of the FP32 FMA, the
+    special-function (reciprocal square root) and the FP64 FMA pipes."""
+    v = [ctypes.c_double(0.0) for _ in range(3)]
+    _check(_lib.map_device_peaks(int(device), *[ctypes.byref(a) for a in v]), "map_device_peaks")
+    return {"ffma": v[0].value, "mufu": v[1].value, "dfma": v[2].value}
 
 
 def solve_h_noalloc(x, y, z, h, route=None, hfact: float = 1.2, stream=None) -> None:

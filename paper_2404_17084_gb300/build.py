@@ -17,7 +17,7 @@ CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libexactmap.so")
 SOURCES = ["api.cu", "grid.cu", "tree.cu", "pairs.cu", "integrate.cu", "pseudo.cu", "noalloc.cu",
-           "hsolve.cu", "batch.cu", "serve.cu", "inverse.cu", "table.cu", "voronoi.cu"]
+           "hsolve.cu", "batch.cu", "serve.cu", "inverse.cu", "table.cu", "voronoi.cu", "peaks.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr",
          "-I" + os.path.join(ROOT, "include")]
