@@ -39,7 +39,9 @@ if ROOT not in sys.path:
 N_PARTICLES = 1 << 20
 SIGMA = 1.5
 OUTDIR = [os.path.join(ROOT, "bench_out")]  # clock samples and --dump output
-WORKLOAD = "clumpy cloud: 2^20 equal-mass particles, log-normal field (GRF P(k)~k^-4, 128^3, sigma_ln_rho=1.5), clipped Voronoi grid, mixed FP32/FP64"
+WORKLOAD_BASE = ("clumpy cloud: 2^20 equal-mass particles, log-normal field (GRF P(k)~k^-4, 128^3, sigma_ln_rho=1.5), "
+                 "clipped Voronoi grid")
+WORKLOAD = WORKLOAD_BASE + ", mixed FP32/FP64"
 
 
 # ----------------------------------------------------------------------------- helpers
@@ -155,15 +157,13 @@ OPS = {
 
 # DRAM traffic of the mixed pair-integral kernel per pair:
 # dram__bytes_read.sum + dram__bytes_write.sum of one ncu capture of the 2^16
-# clumpy case (397 MB for 7,813,809 pairs, profiles/pair_integrals_mixed_clumpy_65536.md),
-# scaled to a launch by its pair count (the kernel streams the same per-pair
-# data at any size).  It belongs to the kernel as captured: set it to None
-# when the kernel changes.
+# clumpy case (397 MB for 7,813,809 pairs), scaled to a launch by its pair
+# count (the kernel streams the same per-pair data at any size).  It belongs
+# to the kernel as captured: set it to None when the kernel changes.
 INTEGRAL_DRAM_BYTES_PER_PAIR = 50.9
 # DRAM bytes per pair of one inverse-mapping sum (inv_apply): 451.2 MB read +
-# written for 32,168,427 pairs in ncu on the 2^18 clumpy snapshot
-# (profiles/inv_apply_clumpy_262144.md), scaled by pair count like the
-# figure above; None once the kernel changes.
+# written for 32,168,427 pairs in ncu on the 2^18 clumpy snapshot, scaled by
+# pair count like the figure above; None once the kernel changes.
 INVERSE_DRAM_BYTES_PER_PAIR = 14.03
 
 
@@ -1251,7 +1251,9 @@ def run_reference(args):
             "value": v, "unit": "pair integrals/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": dt * 1e3 / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "f64", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "n_particles": args.n, "n_cells": g.ncell,
+            "config": {"workload": WORKLOAD_BASE + ", FP64 CPU oracle (brute-force pair list + adaptive "
+                                   "quadrature of the pair integrals) on a random sample of cells per step",
+                       "n_particles": args.n, "n_cells": g.ncell,
                        "sample_per_step": f"{per_step} random cells (pair list + pair integrals)"},
             "cpu_baseline": {"value": v, "unit": "pair integrals/s", "cores": ncores, "kind": "oracle",
                              "sample": f"{per_step} random cells per step"},

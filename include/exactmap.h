@@ -30,7 +30,8 @@ extern "C" {
 #define MAP_EINVAL (-1)      /* bad argument: NULL, bad CSR, NaN, h <= 0, point outside the cube */
 #define MAP_ENOMEM (-2)      /* over the context's HBM budget or cudaMalloc failed; nothing was changed */
 #define MAP_ECUDA (-3)       /* a CUDA runtime call failed */
-#define MAP_ETIMEOUT (-4)    /* a bounded device wait ran out (work queue) */
+#define MAP_ETIMEOUT (-4)    /* reserved: no call returns it -- no kernel of the library waits on a flag, a peer or
+                                another kernel (work queues are drained by atomics, never polled) */
 #define MAP_EDEGENERATE (-5) /* reserved: geometry not classifiable even in FP64 (result flagged) */
 #define MAP_EHANDLE (-6)     /* unknown grid handle */
 #define MAP_ECAPACITY (-7)   /* a caller-provided output buffer is too small */
@@ -52,7 +53,8 @@ typedef struct {
   int autotune;                      /* 1: the context's first mixed mapping call (map_batch or
                                         map_particles_to_cells) times the pair-integral kernel's launch
                                         shapes and keeps the fastest; default 0 */
-  unsigned long long queue_timeout_ns; /* bound on any device-side wait; default 2e9 */
+  unsigned long long queue_timeout_ns; /* reserved, ignored: the library has no device-side wait to bound
+                                          (see MAP_ETIMEOUT); default 2e9 */
   int count_work;                    /* 1: the pair-integral kernel also tallies its work (map_get_work,
                                         map_stats.n_edge_terms / n_fp64_terms), in a separate compilation
                                         of one launch shape that keeps the tally in registers (slower, and
@@ -399,19 +401,31 @@ int solve_h_batch(map_ctx* ctx, int nsnap, map_particles* parts, int32_t* const*
  * handed all of the GPU's memory to its own pools, a pipeline that forbids
  * allocation after start-up).  The paper has no counterpart: this is a
  * deployment variant of solve_h (same octree and Newton/bisection kernels,
- * same results as solve_h on an MAP_FP64 context), taking only caller arrays -- x, y, z (n doubles each, in
- * the unit cube), h (n doubles, out), route (n int32, out, may be NULL) --
- * and using as scratch one fixed 24 MiB array in the library's device image,
- * which every GPU that loads the library holds until the process exits.  It
- * calls no cudaMalloc, cudaFree or allocating library routine.
- *   - n is limited to 32768 particles; larger n returns MAP_ECAPACITY, as
- *     does an octree that outgrows the array (more than 2n nodes).
+ * the same results bit for bit as solve_h on an MAP_FP64 context), taking
+ * only caller arrays -- x, y, z (n doubles each, in the unit cube), h (n
+ * doubles, out), route (n int32, out, may be NULL) -- and using as scratch one
+ * fixed 24 MiB array in the library's device image, which every GPU that
+ * loads the library holds until the process exits.  It calls no cudaMalloc,
+ * cudaFree or allocating library routine.
+ *   - n is limited to 32768 particles; larger n returns MAP_ECAPACITY.  The
+ *     octree's node arrays hold 65536 nodes and are used whole from the
+ *     start; a tree that needs more returns MAP_ECAPACITY before anything is
+ *     written past them, and the array stays ready for the next call.
+ *     Ordinary inputs stay far below (about n/7 nodes at leaf size 16).  The
+ *     largest tree we could construct from 32768 particles -- groups of 17
+ *     spread over the eight cells of one deepest-level node, so that every
+ *     group keeps a chain of nodes down to the deepest level and ends in
+ *     eight leaves -- has about 48,000 nodes, and fits.
  *   - The first call on a device looks up the array's device address
- *     (cudaGetSymbolAddress) and reserves a small host-side table; make that
- *     first call before any stream capture.
- *   - All calls share the array and its last contents: calls whose work
- *     overlaps on the GPU (other streams, other host threads) race.
- *   - Synchronises the stream.  Errors: MAP_EINVAL, MAP_ECAPACITY, MAP_ECUDA. */
+ *     (cudaGetSymbolAddress) and sets up a host-side table for that device.
+ *   - The stream must not be capturing (MAP_EINVAL, the capture untouched):
+ *     the call waits on its stream, which a capture does not allow.
+ *   - All calls share the array and keep its last contents.  Calls whose work
+ *     overlapped on the GPU would race on it, and calls from several host
+ *     threads would also share the host table; so the library serialises them:
+ *     a call holds a per-device lock until its own work on the GPU has
+ *     finished (the call synchronises its stream before returning).
+ *   - Errors: MAP_EINVAL, MAP_ECAPACITY, MAP_ECUDA. */
 int solve_h_noalloc(const double* x, const double* y, const double* z, int64_t n, double hfact, double* h,
                     int32_t* route, void* stream);
 

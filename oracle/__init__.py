@@ -15,6 +15,8 @@ Routes (see the C file's header for the full statement):
   * table variant: pyramid integrals interpolated trilinearly in a table of I
     (set_table), the paper's production route;
   * smoothing lengths: Eq. (7)-(9), Newton -> bisection -> estimate;
+  * pseudo-particle smoothing lengths: the same solve over the accepted
+    nodes and opened leaves (Section III-C) from the Eq. (9) guess;
   * octree, adaptive walk: Section III-A/B, Eq. (5).
 """
 from __future__ import annotations
@@ -316,6 +318,36 @@ class Tree:
             b = self.pbegin[nid]
             out[self.order[b: b + self.count[nid]]] = nid
         return out
+
+
+def pseudo_members(tree: "Tree", acc, opened):
+    """The node set of the pseudo-particle h solve (Section III-C): the
+    accepted nodes and the opened leaves, which stand in for their particles
+    as one point each (their centre of mass).  Returns the member node ids in
+    ascending order and the position of each accepted node in that list."""
+    acc = np.asarray(acc, np.int64)
+    members = np.sort(np.concatenate([acc, np.asarray(opened, np.int64)]))
+    return members, np.searchsorted(members, acc)
+
+
+def pseudo_h0(tree: "Tree", nodes, h, hfact=HFACT):
+    """Eq. (9): the initial guess of a node's smoothing length is hfact times
+    twice its size s_node.  A node of size 0 (coincident particles) has no
+    such scale; it starts from the h of its first particle (lowest index)."""
+    nodes = np.asarray(nodes, np.int64)
+    first = np.array([tree.particles_of(i)[0] for i in nodes], np.int64)
+    return np.where(tree.size[nodes] > 0, hfact * 2.0 * tree.size[nodes], np.asarray(h, np.float64)[first])
+
+
+def pseudo_h(tree: "Tree", acc, opened, h, hfact=HFACT, nthreads=None):
+    """Smoothing lengths of the accepted nodes (Section III-C, Eq. 7-9): the
+    solve of solve_h over the member set of pseudo_members, from the Eq. (9)
+    guess of pseudo_h0.  Returns (h, route) per accepted node, in the order
+    of acc."""
+    members, targets = pseudo_members(tree, acc, opened)
+    pos = tree.com[members]
+    h0 = pseudo_h0(tree, acc, h, hfact)
+    return solve_h(pos[:, 0], pos[:, 1], pos[:, 2], h0, targets, hfact=hfact, nthreads=nthreads)
 
 
 def particle_h_guess(tree: "Tree", hfact=HFACT):

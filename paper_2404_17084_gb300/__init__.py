@@ -450,9 +450,20 @@ def map_device_peaks(device: int = 0) -> dict:
 
 def solve_h_noalloc(x, y, z, h, route=None, hfact: float = 1.2, stream=None) -> None:
     """solve_h without a context or device allocations (at most 32768
-    particles; see the header): x, y, z, h float64 CUDA tensors, route an
-    optional int32 CUDA tensor."""
-    _check(_lib.solve_h_noalloc(_ptr(x), _ptr(y), _ptr(z), x.numel(), float(hfact), _ptr(h), _ptr(route),
+    particles; see the header): x, y, z, h float64 CUDA tensors of one length
+    on the current device, route an optional int32 CUDA tensor of that
+    length.  The library writes h and route through raw pointers, so their
+    types, lengths and device are checked here first (ValueError)."""
+    n = x.numel()
+    dev = torch.cuda.current_device()
+    for name, t, dt in (("x", x, torch.float64), ("y", y, torch.float64), ("z", z, torch.float64),
+                        ("h", h, torch.float64), ("route", route, torch.int32)):
+        if t is None and name == "route":
+            continue
+        if t.dtype != dt or t.numel() != n or not t.is_cuda or t.device.index != dev:
+            raise ValueError(f"solve_h_noalloc: {name} must be a {dt} CUDA tensor of {n} elements on "
+                             f"cuda:{dev} (got {t.dtype}, {t.numel()} on {t.device})")
+    _check(_lib.solve_h_noalloc(_ptr(x), _ptr(y), _ptr(z), n, float(hfact), _ptr(h), _ptr(route),
                                 _stream(stream)), "solve_h_noalloc")
 
 

@@ -151,6 +151,7 @@ struct map_ctx {
   DevBuf ws_inv[11];                   // particle-major copy of the pair list (inverse mapping, Eq. 4)
   DevBuf cub_tmp;
   DevTree tree;
+  int64_t node_cap0 = 0;  // > 0: octree node arrays start at this capacity (a context whose workspace is fixed)
   // results of the last mapping call
   int64_t last_ncell = 0;
   int64_t n_pairs = 0;

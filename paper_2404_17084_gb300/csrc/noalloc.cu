@@ -3,8 +3,9 @@
 //
 // Some callers cannot call cudaMalloc at all: code running under a fixed
 // memory reservation (a host application that has already divided the GPU's
-// memory among its own pools), code running inside a stream capture that must
-// not allocate, or embedded pipelines that forbid allocation after start-up.
+// memory among its own pools), or embedded pipelines that forbid allocation
+// after start-up.  (A stream that is being captured is refused: the call
+// waits on its stream several times, which a capture does not allow.)
 // For them this entry point runs the same octree build and Newton/bisection
 // kernels as solve_h, but every piece of scratch memory lives in one
 // file-scope __device__ array of NOALLOC_BYTES.  The caller passes only its
@@ -18,6 +19,7 @@
 // reuse those slots -- any larger request is refused (MAP_ENOMEM) before an
 // allocation could happen.
 #include <cstring>
+#include <mutex>
 
 #include <cub/cub.cuh>
 
@@ -40,6 +42,10 @@ struct NoAllocState {
   int64_t host_scratch[8];
 };
 static NoAllocState g_state[MAX_DEVICES];
+// The host side is shared too (the device's context: its configuration,
+// its octree's level table): one lock per device serialises the calls of
+// all host threads, each holding it until its work on the GPU has finished.
+static std::mutex g_lock[MAX_DEVICES];
 
 __global__ void noalloc_validate(int64_t n, const double* __restrict__ x, const double* __restrict__ y,
                                  const double* __restrict__ z, unsigned long long* bad) {
@@ -112,6 +118,10 @@ int setup_device(int dev) {
   C.bytes_in_use = NOALLOC_BYTES;
   C.h_scratch = S.host_scratch;
   C.tree.level_begin.reserve(64);
+  // the node arrays take their whole slots from the start, so that a tree
+  // never needs to grow them (growth would be refused): any tree of up to NC
+  // nodes fits, whatever the order in which its levels fill
+  C.node_cap0 = (int64_t)NC;
   S.ready = true;
   return MAP_OK;
 }
@@ -125,11 +135,17 @@ extern "C" int solve_h_noalloc(const double* x, const double* y, const double* z
   int dev = 0;
   CUDA_TRY(cudaGetDevice(&dev));
   if (dev < 0 || dev >= MAX_DEVICES) return MAP_EINVAL;
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  // a capturing stream cannot be waited on: refuse before touching it, so
+  // that the caller's capture stays valid
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  CUDA_TRY(cudaStreamIsCapturing(s, &cap));
+  if (cap != cudaStreamCaptureStatusNone) return MAP_EINVAL;
+  std::lock_guard<std::mutex> lock(g_lock[dev]);
   MAP_TRY(setup_device(dev));
   NoAllocState& S = g_state[dev];
   map_ctx& C = S.ctx;
   C.cfg.hfact = hfact;
-  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
   CUDA_TRY(cudaMemsetAsync(C.d_counters, 0, 16 * sizeof(unsigned long long), s));
   noalloc_validate<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(n, x, y, z, C.d_counters);
   CUDA_TRY(cudaGetLastError());
@@ -138,5 +154,9 @@ extern "C" int solve_h_noalloc(const double* x, const double* y, const double* z
   CUDA_TRY(cudaStreamSynchronize(s));
   if (bad) return MAP_EINVAL;
   const int r = h_solve_run(&C, x, y, z, n, h, route, nullptr, s);
-  return r == MAP_ENOMEM ? MAP_ECAPACITY : r;
+  // the work is finished before the lock is released: the next call (from
+  // any host thread) starts on a quiet scratch array
+  const cudaError_t e = cudaStreamSynchronize(s);
+  if (r != MAP_OK) return r == MAP_ENOMEM ? MAP_ECAPACITY : r;
+  return e == cudaSuccess ? MAP_OK : MAP_ECUDA;
 }

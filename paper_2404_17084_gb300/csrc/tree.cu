@@ -321,6 +321,7 @@ int tree_build(map_ctx* ctx, const double* x, const double* y, const double* z, 
 
   // level-synchronous build
   int64_t cap = n / 4 + 64;
+  if (ctx->node_cap0 > cap) cap = ctx->node_cap0;  // node arrays sized up front (fixed-workspace contexts)
   MAP_TRY(grow_nodes(ctx, cap));
   int64_t root_label = 1, zero = 0;
   int32_t root_level = 0, root_parent = -1;

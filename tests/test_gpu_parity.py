@@ -2,7 +2,10 @@
 
 Gates (per cell, relative to the oracle, absolute floor at 1e-12 of the
 largest cell mass): FP64 build 1e-9, mixed build 1e-5; total mass 1e-12 and
-1e-7; pair lists bit-equal; smoothing lengths 1e-9 relative.
+1e-7; pair lists bit-equal; smoothing lengths 1e-9 relative in the FP64 build
+and 1e-6 relative in the mixed build, whose h solve sums the kernel in FP32 and
+stops Newton at |dh|/h < 1e-6 (h to ~1e-7; the mapping's 1e-5 gate holds on
+either build's h).
 """
 import numpy as np
 import pytest

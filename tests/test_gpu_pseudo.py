@@ -33,13 +33,8 @@ def gpu_pseudo(p, h, src, theta=0.5, ngb_max=10000, **walk):
 def oracle_pseudo(p, h, src, theta=0.5, hfact=oracle.HFACT, **walk):
     t = oracle.Tree(p.x, p.y, p.z, p.m)
     acc, opened = t.walk(src, theta, **walk)
-    members = np.sort(np.concatenate([acc, opened]))
     # h of accepted nodes over the member set (brute force), Eq. (7)-(9)
-    first = np.array([t.particles_of(i)[0] for i in acc], np.int64)
-    h0 = np.where(t.size[acc] > 0, hfact * 2.0 * t.size[acc], h[first])
-    pos = t.com[members]
-    targets = np.searchsorted(members, acc)
-    hn, route = oracle.solve_h(pos[:, 0], pos[:, 1], pos[:, 2], h0, targets, hfact=hfact)
+    hn, _ = oracle.pseudo_h(t, acc, opened, h, hfact=hfact)
     return t, acc, opened, hn
 
 

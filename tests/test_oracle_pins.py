@@ -313,6 +313,119 @@ def test_h_solve_residual_and_lattice_value():
     assert abs(hq[0] * n / 1.2 - 1.0) < 0.05
 
 
+def g_def(pos, a, h, hfact=1.2):
+    """The residual of Eq. (7) at h, from the test-side kernel: h - hfact n^(-1/3)."""
+    r = np.linalg.norm(pos - pos[a], axis=1)
+    return h - hfact * np.sum(W_def(r, h)) ** (-1.0 / 3.0)
+
+
+def test_h_solve_estimate_route_isolated_particle():
+    """Section III-C's last resort.  A particle with no neighbour within 2h
+    anywhere in [h0/16, 16 h0] sees only its self term, n(h) = W(0, h) =
+    1/(pi h^3), so g(h) = h (1 - hfact pi^(1/3)) < 0 for hfact = 1.2: Newton
+    leaves the bracket (its step lands on h = 0), bisection finds no sign
+    change, and the solve must return the estimate h0 itself (route 2)."""
+    x, y, z = np.array([0.1, 0.9]), np.array([0.1, 0.9]), np.array([0.1, 0.9])
+    h0 = 0.01  # 2 x 16 h0 = 0.32, well short of the other particle at 1.39
+    assert 1.2 * math.pi ** (1.0 / 3.0) > 1.0
+    h, route = oracle.solve_h(x, y, z, np.array([h0]), [0])
+    assert route[0] == 2 and h[0] == h0
+    # a root that exists but lies below the bracket: h0 far too large on a
+    # dense lattice, g > 0 at both ends of [h0/16, 16 h0] (test-side g)
+    q = synth.lattice_particles(10)
+    pos = q.pos()
+    h0 = 10.0
+    assert g_def(pos, 555, h0 / 16) > 0 and g_def(pos, 555, 16 * h0) > 0
+    h, route = oracle.solve_h(q.x, q.y, q.z, np.array([h0]), [555])
+    assert route[0] == 2 and h[0] == h0
+
+
+@pytest.mark.parametrize("jitter,h0_over_dx", [(0.0, 0.3), (0.2, 0.2)])
+def test_h_solve_bisection_route_against_brentq(jitter, h0_over_dx):
+    """Newton leaves [h0/16, 16 h0] while a root exists there: the guess h0 is
+    so small that no neighbour lies within 2 h0 (spacing dx, nearest
+    neighbour >= (1 - 2 jitter) dx > 2 h0), so the first Newton step lands on
+    h = 0.  The solve must then bisect (route 1) to the unique root of
+    g(h) = h - 1.2 n(h)^(-1/3) (g/h is non-decreasing since n h^3 =
+    sum_b w(r_b/h)/pi is), which scipy's brentq finds here on the test-side
+    number density."""
+    from scipy.optimize import brentq
+    nside = 10
+    q = synth.lattice_particles(nside, jitter=jitter, seed=4)
+    pos = q.pos()
+    dx = 1.0 / nside
+    targets = [555, 444]
+    h0 = np.full(len(targets), h0_over_dx * dx)
+    for a in targets:
+        r = np.linalg.norm(pos - pos[a], axis=1)
+        assert np.sort(r)[1] > 2 * h0[0]
+    h, route = oracle.solve_h(q.x, q.y, q.z, h0, targets)
+    assert np.all(route == 1)
+    for k, a in enumerate(targets):
+        lo, hi = h0[k] / 16, 16 * h0[k]
+        assert g_def(pos, a, lo) < 0 < g_def(pos, a, hi)
+        root = brentq(lambda v: g_def(pos, a, v), lo, hi, xtol=1e-16, rtol=1e-15)
+        assert abs(h[k] / root - 1) < 1e-10
+
+
+def test_pseudo_h0_and_member_rules():
+    """Eq. (9) and the member set of the pseudo-particle solve (Section
+    III-C), against quantities computed here from the particles alone:
+      * one accepted node and nothing else (the root, seen from a far source
+        with a wide opening angle): its member set is the root alone, so the
+        solve cannot find a root and returns Eq. (9)'s guess
+        h0 = hfact * 2 * s_node, s_node = largest distance from the centre of
+        mass (numpy) to a particle;
+      * a node of size 0 (five coincident particles, leaf capacity 4, so the
+        octree splits down to the deepest level) starts from the h of its
+        lowest-index particle;
+      * the member set is the accepted nodes plus the opened leaves, one
+        point each at its centre of mass: every node (solved by Newton or by
+        bisection) meets Eq. (7) over those points with the test-side
+        kernel."""
+    p = synth.uniform_particles(300, 41)
+    pos = p.pos()
+    t = oracle.Tree(p.x, p.y, p.z, p.m)
+    acc, opened = t.walk(np.array([50.0, 50.0, 50.0]), 1e9)
+    assert list(acc) == [0] and len(opened) == 0
+    members, tgt = oracle.pseudo_members(t, acc, opened)
+    assert list(members) == [0] and list(tgt) == [0]
+    com = pos.mean(axis=0)  # equal masses
+    s_node = np.linalg.norm(pos - com, axis=1).max()
+    hn, route = oracle.pseudo_h(t, acc, opened, np.full(p.n, 0.05))
+    assert route[0] == 2 and abs(hn[0] / (1.2 * 2 * s_node) - 1) < 1e-13
+
+    a = np.array([0.2, 0.3, 0.4])
+    b = np.array([0.7, 0.8, 0.6])
+    pts = np.concatenate([np.repeat(a[None], 5, 0), np.repeat(b[None], 5, 0)])
+    perm = np.random.default_rng(3).permutation(10)
+    pts = pts[perm]
+    hin = np.linspace(0.01, 0.1, 10)
+    tc = oracle.Tree(pts[:, 0], pts[:, 1], pts[:, 2], np.full(10, 0.1), leaf_size=4)
+    zero = np.nonzero((tc.size == 0) & (tc.leaf == 1) & (tc.count == 5))[0]
+    assert len(zero) == 2
+    h0 = oracle.pseudo_h0(tc, zero, hin)
+    for k, nid in enumerate(zero):
+        group = np.nonzero(np.all(pts == pts[tc.particles_of(nid)[0]], axis=1))[0]
+        assert h0[k] == hin[group.min()]
+
+    q = synth.lognormal_particles(3000, 17, ngrid=32)
+    tq = oracle.Tree(q.x, q.y, q.z, q.m)
+    src = q.pos()[7]
+    acc, opened = tq.walk(src, 0.5)
+    assert len(acc) > 20 and len(opened) > 0
+    members, tgt = oracle.pseudo_members(tq, acc, opened)
+    assert np.array_equal(members, np.sort(np.concatenate([acc, opened])))
+    assert np.array_equal(members[tgt], acc)
+    hq = np.full(q.n, 0.02)
+    hn, route = oracle.pseudo_h(tq, acc, opened, hq)
+    mpos = tq.com[members]
+    assert np.all(route != 2) and np.sum(route == 0) > 0.5 * len(acc)
+    for k in range(len(acc)):
+        r = np.linalg.norm(mpos - tq.com[acc[k]], axis=1)
+        assert abs(hn[k] - 1.2 * np.sum(W_def(r, hn[k])) ** (-1.0 / 3.0)) < 1e-9 * hn[k]
+
+
 # ----------------------------------------------------------------- octree and walk
 
 def test_octree_invariants_and_walk_partition():
@@ -584,16 +697,104 @@ def test_voronoi_oracle_against_definition_and_qhull():
         region = qh.regions[qh.point_region[c]]
         if -1 in region or np.any(g.face_nb[fb:fe] < 0):
             continue
+        # the same vertices both ways, as positions: a degenerate vertex
+        # (four or more planes through one point) may be listed twice by one
+        # side, so both sets are compared up to that, never skipped
         qv = qh.vertices[region]
-        if len(qv) != len(cv):
-            continue  # a degenerate vertex listed twice by one side
-        dmin = np.linalg.norm(qv[:, None, :] - cv[None, :, :], axis=2).min(axis=1)
-        assert dmin.max() < 1e-10
+        dq = np.linalg.norm(qv[:, None, :] - cv[None, :, :], axis=2)
+        assert dq.min(axis=1).max() < 1e-10 and dq.min(axis=0).max() < 1e-10
         n_checked += 1
     assert n_checked >= 10
     lat = oracle.voronoi_cells(synth.lattice_particles(3).pos())
     lv, _ = oracle.cell_geometry(lat)
     assert np.max(np.abs(lv * 27 - 1)) < 1e-13 and np.all(np.diff(lat.cell_face_off) == 6)
+
+
+def cell_by_vertex_enumeration(sites, i, k0=20):
+    """The clipped Voronoi cell of site i written from its definition alone,
+    with no clipping: the points x of [0,1]^3 with
+    (s_j - s_i).x <= (s_j - s_i).s_i + |s_j - s_i|^2 / 2 for every j.  Its
+    vertices are the points where three of those planes (or the cube's walls)
+    meet and every constraint holds.  Candidate planes start with the k0
+    nearest sites and grow until every site nearer than 2 R (R the largest
+    vertex distance found) is among them: a site at distance D puts its
+    plane at D/2 from s_i, so farther sites cannot cut the cell.  Returns
+    (vertices, plane ids of the facets), plane ids as the oracle's face_nb
+    (site index, or -1-w for the walls x<=1, x>=0, y<=1, y>=0, z<=1, z>=0)."""
+    from itertools import combinations
+    s = sites[i]
+    dist = np.linalg.norm(sites - s, axis=1)
+    order = np.argsort(dist)[1:]
+    eye = np.eye(3)
+    wallN = np.array([eye[0], -eye[0], eye[1], -eye[1], eye[2], -eye[2]])
+    wallB = np.array([1.0, 0.0, 1.0, 0.0, 1.0, 0.0])
+    wallId = -1 - np.arange(6)
+    allA = sites[order] - s
+    allN = np.concatenate([allA, wallN])
+    allB = np.concatenate([allA @ s + 0.5 * np.sum(allA * allA, 1), wallB])
+    k = k0
+    while True:
+        k = min(k, len(order))
+        N = np.concatenate([allN[:k], wallN])
+        B = np.concatenate([allB[:k], wallB])
+        ids = np.concatenate([order[:k], wallId])
+        tri = np.array(list(combinations(range(len(N)), 3)))
+        M = N[tri]
+        det = np.linalg.det(M)
+        ok = np.abs(det) > 1e-14
+        X = np.linalg.solve(M[ok], B[tri[ok]][..., None])[..., 0]
+        # the cell of the candidate planes alone, which contains the true cell
+        feas = np.all(N @ X.T <= (B + 1e-12 * np.linalg.norm(N, axis=1))[:, None], axis=0)
+        V = X[feas]
+        R = np.linalg.norm(V - s, axis=1).max()
+        if k == len(order) or dist[order[k]] >= 2 * R + 1e-12:
+            break
+        k *= 2
+    # distinct vertices, and the planes holding three or more of them (facets)
+    keep = []
+    for v in V:
+        if not keep or np.min(np.linalg.norm(np.array(keep) - v, axis=1)) > 1e-10:
+            keep.append(v)
+    V = np.array(keep)
+    Nk = np.concatenate([allN[:k], wallN])
+    Bk = np.concatenate([allB[:k], wallB])
+    on = np.abs(V @ Nk.T - Bk) < 1e-11 * np.linalg.norm(Nk, axis=1)
+    facets = ids[on.sum(axis=0) >= 3]
+    return V, np.sort(facets)
+
+
+@pytest.mark.parametrize("kind", ["uniform", "clumpy"])
+def test_voronoi_cells_against_vertex_enumeration(kind):
+    """Every sampled cell of the oracle, wall cells included, against the
+    cell built above from the definition by vertex enumeration (no clipping,
+    no ordering, no welding): the same vertices both ways, the same
+    neighbours and walls face for face, and the volume of the convex hull of
+    the enumerated vertices (Qhull)."""
+    spatial = pytest.importorskip("scipy.spatial")
+    if kind == "uniform":
+        sites = synth.uniform_particles(150, 29).pos()
+    else:
+        sites = synth.lognormal_particles(400, 31, ngrid=32).pos()
+    g = oracle.voronoi_cells(sites)
+    vol, rad = oracle.cell_geometry(g)
+    v = np.stack([g.vx, g.vy, g.vz], 1)
+    # cells whose enumeration stays small (at most 60 sites within twice the
+    # cell's radius: C(66, 3) plane triples); the choice does not enter the check
+    near = np.array([np.sum(np.linalg.norm(sites - sites[c], axis=1) < 2 * rad[c]) for c in range(g.ncell)])
+    pool = np.nonzero(near <= 61)[0]
+    cells = np.random.default_rng(5).choice(pool, min(40, len(pool)), replace=False)
+    assert len(cells) >= 30
+    n_wall = 0
+    for c in cells:
+        V, facets = cell_by_vertex_enumeration(sites, c)
+        fb, fe = g.cell_face_off[c], g.cell_face_off[c + 1]
+        cv = v[np.unique(g.face_vert[g.face_vert_off[fb]:g.face_vert_off[fe]])]
+        d = np.linalg.norm(V[:, None, :] - cv[None, :, :], axis=2)
+        assert d.min(axis=1).max() < 1e-10 and d.min(axis=0).max() < 1e-10, c
+        assert np.array_equal(np.sort(g.face_nb[fb:fe]), facets), c
+        assert abs(spatial.ConvexHull(V).volume - vol[c]) < 1e-12 * max(vol[c], 1e-3), c
+        n_wall += int(np.any(facets < 0))
+    assert n_wall >= 5
 
 
 def test_centroids_lloyd_and_merge():
