@@ -204,6 +204,29 @@ def algorithmic_ops(work: dict, terms: int, mixed: bool):
     return f, m
 
 
+def oracle_errors(g, p, h, mass_gpu, ncells, seed):
+    """Per-cell error of a GPU result against the FP64 oracle, run on the same
+    particles and the GPU's own h, on a seeded random sample of cells (the
+    floor of the relative error is 1e-12 of the largest reference mass)."""
+    import oracle
+    rng = np.random.default_rng(seed)
+    cells = np.sort(rng.choice(g.ncell, min(ncells, g.ncell), replace=False)).astype(np.int64)
+    r = oracle.map_cells(g, p.x, p.y, p.z, p.m, h, cells=cells, nthreads=os.cpu_count() or 1)
+    ref = r["mass"]
+    scale = np.maximum(np.abs(ref), 1e-12 * np.abs(ref).max())
+    e = np.abs(np.asarray(mass_gpu)[cells] - ref) / scale
+    return {"cells": int(len(cells)), "max_rel": float(e.max()), "p99_rel": float(np.percentile(e, 99))}
+
+
+def merge_errors(errs):
+    """One error summary for several sampled snapshots."""
+    errs = [e for e in errs if e]
+    return {"cells": int(sum(e["cells"] for e in errs)), "max_rel": float(max(e["max_rel"] for e in errs)),
+            "p99_rel": float(max(e["p99_rel"] for e in errs)), "snapshots": len(errs),
+            "note": "per-cell mass against the FP64 oracle run on the same particles and the GPU's h; p99 is the "
+                    "largest per-snapshot p99"}
+
+
 def load_peaks():
     try:
         return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
@@ -279,6 +302,9 @@ def run_ours(args):
     # ---- e2e through the public API with host buffers
     e2e = None if args.skip_e2e else e2e_run(L, torch, ctx, p, g, dev, args, barrier, world)
     L.map_destroy(ctx)
+    # ---- the metric's latency half: a short serving pass at 50% and 90% of capacity
+    import synth
+    serving = None if args.skip_serve else serving_latency(L, local, rank_seed(synth.BASE_SEED + 5, rank) + 77)
 
     # ---- FP64 build (one timed step: GB300's FP64 rate makes it ~70x slower)
     fp64 = None
@@ -372,6 +398,11 @@ def run_ours(args):
                      "measured_peaks_Tops": (None if meas is None else
                                              {k: round(v / 1e12, 3) for k, v in meas.items()})},
         "e2e": e2e,
+        "latency_ms": (None if serving is None else
+                       {**serving["loads"]["0.9"]["latency_ms"], "at": "90% of the serving capacity",
+                        "p50_at_50pct": serving["loads"]["0.5"]["latency_ms"]["p50"],
+                        "p99_at_50pct": serving["loads"]["0.5"]["latency_ms"]["p99"]}),
+        "serving": serving,
         "gpu_launches": int(launches),
         "clocks": clocks,
         "autotune": {"chosen": tune_chosen, "ms_per_shape": tune_ms,
@@ -481,6 +512,10 @@ def run_batch(args):
     torch.cuda.synchronize()
     single_s = time.perf_counter() - s0
     same = all(np.array_equal(a, b.cpu().numpy()) for a, b in zip(batch_mass, single_mass))
+    # error against the FP64 oracle: 8 snapshots spread over the sizes, 25 cells each
+    pick = np.linspace(0, len(snaps) - 1, 8).astype(int)
+    batch_err = merge_errors([oracle_errors(snaps[j][1], snaps[j][0], keep[j][4].cpu().numpy(), batch_mass[j], 25,
+                                            100 + int(j)) for j in pick])
     # the batch's grids take most of the GPU's memory (edge records of 1.1e7
     # cells): release them before the counting context uploads its own copy
     L.map_destroy(ctx)
@@ -517,6 +552,7 @@ def run_batch(args):
                                           "4 warps/CTA, 6 CTAs/SM"]},
                   "one_call_per_snapshot_mapping_s": single_s, "batched_equals_single": bool(same),
                   "host_input_generation_s": gen_s},
+        "accuracy_vs_oracle": batch_err,
         "roofline": {"bound": "alu", "kernel": "pair_integrals_mixed (batched launch)",
                      "achieved": achieved / 1e12, "peak": peak_ops / 1e12, "unit": "Tops/s (FP32 issue slots)",
                      "frac": achieved / peak_ops,
@@ -537,64 +573,57 @@ def run_batch(args):
         torch.distributed.destroy_process_group()
 
 
-SERVE_WORKLOAD = ("serving loop: Poisson stream of {n} mapping requests ({pool} distinct), particle counts "
-                  "log-normal in log2 (median 2^15, sigma 1.5) clipped to [2^12, 2^21], random uniform / log-normal "
-                  "clumpy fields, host inputs and outputs, {slots} slots admitted by HBM, mixed FP32/FP64")
+SERVE_WORKLOAD = ("serving loop: Poisson stream of {n} mapping requests ({pool} distinct, each on its own grid kept "
+                  "resident by id), particle counts log-normal in log2 (median 2^15, sigma 1.5) clipped to [2^12, "
+                  "2^{hi}], random uniform / log-normal clumpy fields, host inputs and outputs, {slots} slots "
+                  "admitted by HBM, mixed FP32/FP64")
 
 
-def serve_specs(k: int, seed: int):
+def serve_specs(k: int, seed: int, log2_hi: float = 21.0):
     rng = np.random.default_rng(seed)
-    l2 = np.clip(rng.normal(15.0, 1.5, k), 12.0, 21.0)
+    l2 = np.clip(rng.normal(15.0, 1.5, k), 12.0, log2_hi)
     kinds = rng.choice(["uniform", "clumpy"], size=k)
     sig = rng.uniform(1.0, 2.0, k)
     seeds = rng.integers(1, 2**31, k)
     return [(int(2.0 ** l2[j]), str(kinds[j]), float(sig[j]), int(seeds[j])) for j in range(k)]
 
 
-def run_serve(args):
-    """Serving workload: requests (host arrays) arrive as a Poisson stream and
-    go through the library's serving loop (continuous batching over slots,
-    admission by HBM); throughput and p50/p99 latency are measured on the
-    host clock from submission to results in host memory."""
-    import threading
-    import torch
-    import paper_2404_17084_gb300 as L
-    import synth
+class ServeSession:
+    """A server over a pool of distinct requests (host arrays), each request
+    on its own grid id so that its grid stays resident after its first use;
+    Poisson streams of requests drawn from the pool, timed on the host clock
+    from submission to results in host memory."""
 
-    rank, world, local = dist_env()
-    torch.cuda.set_device(local)
-    t0 = time.perf_counter()
-    pool = []
-    for spec in serve_specs(args.pool, rank_seed(synth.BASE_SEED + 5, rank)):
-        p = synth.batch_particles(spec)
-        pool.append((p, synth.voronoi(p.pos())))
-    gen_s = time.perf_counter() - t0
-    srv = L.map_server_create(L.map_server_config_default(device=local, precision=L.MAP_MIXED, slots=args.slots))
-    outs = [np.empty(g.ncell) for _, g in pool]
+    def __init__(self, L, local, pool, slots):
+        self.L, self.pool = L, pool
+        self.srv = L.map_server_create(L.map_server_config_default(device=local, precision=L.MAP_MIXED, slots=slots))
+        self.outs = [np.empty(g.ncell) for _, g in pool]
+        self.hs = [np.empty(p.n) for p, _ in pool]
 
-    def burst(idx):
-        ts = [L.map_server_submit(srv, pool[j][0].x, pool[j][0].y, pool[j][0].z, pool[j][0].m, pool[j][1],
-                                  outs[j]) for j in idx]
-        return [L.map_server_wait(srv, t) for t in ts]
+    def submit(self, j, out, h=None):
+        p, g = self.pool[j]
+        return self.L.map_server_submit(self.srv, p.x, p.y, p.z, p.m, g, out, h=h, grid_id=j)
 
-    # warm-up, then capacity: the whole pool back to back (all queued at
-    # once), the better of two passes
-    for _ in range(max(1, args.warmup // 3)):
-        burst(range(len(pool)))
-    cap_s = float("inf")
-    for _ in range(2):
-        c0 = time.perf_counter()
-        burst(range(len(pool)))
-        cap_s = min(cap_s, time.perf_counter() - c0)
-    capacity = len(pool) / cap_s
+    def burst(self, idx, first=False):
+        ts = [self.submit(j, self.outs[j], self.hs[j] if first else None) for j in idx]
+        return [self.L.map_server_wait(self.srv, t) for t in ts]
 
-    def stream(rate, seed, sampler=None):
-        """One Poisson stream of args.requests requests at `rate` per second."""
+    def capacity(self):
+        """Requests per second with the whole pool queued at once, the better of two passes."""
+        best = float("inf")
+        for _ in range(2):
+            c0 = time.perf_counter()
+            self.burst(range(len(self.pool)))
+            best = min(best, time.perf_counter() - c0)
+        return len(self.pool) / best
+
+    def stream(self, rate, nreq, seed, sampler=None):
+        import threading
         rng = np.random.default_rng(seed)
-        order = rng.integers(0, len(pool), args.requests)
-        gaps = rng.exponential(1.0 / rate, args.requests)
-        tickets = [None] * args.requests
-        out_bufs = [np.empty(pool[j][1].ncell) for j in order]
+        order = rng.integers(0, len(self.pool), nreq)
+        gaps = rng.exponential(1.0 / rate, nreq)
+        tickets = [None] * nreq
+        bufs = [np.empty(self.pool[j][1].ncell) for j in order]
 
         def submitter():
             t_next = time.perf_counter()
@@ -603,41 +632,105 @@ def run_serve(args):
                 d = t_next - time.perf_counter()
                 if d > 0:
                     time.sleep(d)
-                p, g = pool[j]
-                tickets[i] = L.map_server_submit(srv, p.x, p.y, p.z, p.m, g, out_bufs[i])
+                tickets[i] = self.submit(int(j), bufs[i])
 
         if sampler:
             sampler.start()
         w0 = time.perf_counter()
         th = threading.Thread(target=submitter)
         th.start()
-        results = []
-        for i in range(args.requests):
+        res = []
+        for i in range(nreq):
             while tickets[i] is None:
                 time.sleep(0.0005)
-            results.append(L.map_server_wait(srv, tickets[i]))
+            res.append(self.L.map_server_wait(self.srv, tickets[i]))
         wall = time.perf_counter() - w0
         th.join()
         clocks = sampler.stop() if sampler else None
-        return order, out_bufs, results, wall, clocks
+        lat = np.array([r.latency_ms for r in res])
+        que = np.array([r.queue_ms for r in res])
+        return {"order": order, "results": res, "wall": wall, "clocks": clocks,
+                "summary": {"arrival_rate_per_s": rate, "requests_per_s": nreq / wall,
+                            "pairs_per_s": sum(r.n_pairs for r in res) / wall,
+                            "latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99)),
+                                           "max": float(lat.max())},
+                            "queue_ms": {"p50": float(np.percentile(que, 50)), "p99": float(np.percentile(que, 99))},
+                            "all_ok": all(r.status == 0 for r in res),
+                            "results_equal_to_first_pass": all(np.array_equal(bufs[i], self.outs[order[i]])
+                                                               for i in range(nreq))}}
 
-    # the headline stream at 80% of capacity, then the latency at 50% and 90%
-    rate = args.rate if args.rate > 0 else 0.8 * capacity
-    order, out_bufs, results, wall, clocks = stream(rate, synth.BASE_SEED + 6, ClockSampler(local))
-    sweep = {}
-    for load in (0.5, 0.9):
-        o2, b2, r2, w2, _ = stream(load * capacity, synth.BASE_SEED + 6 + int(load * 10))
-        l2 = np.array([r.latency_ms for r in r2])
-        sweep[str(load)] = {"arrival_rate_per_s": load * capacity, "requests_per_s": args.requests / w2,
-                            "latency_ms": {"p50": float(np.percentile(l2, 50)), "p99": float(np.percentile(l2, 99))},
-                            "all_ok": all(r.status == 0 for r in r2),
-                            "results_equal_to_first_pass": all(np.array_equal(b2[i], outs[o2[i]])
-                                                               for i in range(args.requests))}
-    L.map_server_destroy(srv)
-    ok = all(r.status == 0 for r in results)
-    same = all(np.array_equal(out_bufs[i], outs[order[i]]) for i in range(args.requests))
-    lat = np.array([r.latency_ms for r in results])
-    que = np.array([r.queue_ms for r in results])
+    def errors(self, k, seed):
+        """Error of served results against the FP64 oracle (the served h): k pool entries, 40 cells each."""
+        pick = np.argsort([p.n for p, _ in self.pool])[np.linspace(0, len(self.pool) - 1, k).astype(int)]
+        return merge_errors([oracle_errors(self.pool[j][1], self.pool[j][0], self.hs[j], self.outs[j], 40,
+                                           seed + int(j)) for j in pick])
+
+    def close(self):
+        grid = self.L.map_server_grid_stats(self.srv)
+        self.L.map_server_destroy(self.srv)
+        return {"uploads": grid[0], "hits": grid[1], "resident": grid[2], "resident_bytes": grid[3]}
+
+
+def serve_pool(k, seed, log2_hi=21.0):
+    import synth
+    pool = []
+    for spec in serve_specs(k, seed, log2_hi):
+        p = synth.batch_particles(spec)
+        pool.append((p, synth.voronoi(p.pos())))
+    return pool
+
+
+def serving_latency(L, local, seed, pool_size=16, nreq=64, slots=4):
+    """The metric's latency half for the default line: a short serving pass
+    (a pool of distinct requests of 2^12 to 2^18 particles on resident grids)
+    at 50% and 90% of the measured capacity."""
+    t0 = time.perf_counter()
+    pool = serve_pool(pool_size, seed, 18.0)
+    gen_s = time.perf_counter() - t0
+    S = ServeSession(L, local, pool, slots)
+    try:
+        S.burst(range(len(pool)), first=True)  # uploads every grid once: resident from here on
+        cap = S.capacity()
+        loads = {}
+        for load in (0.5, 0.9):
+            loads[str(load)] = S.stream(load * cap, nreq, seed + int(load * 10))["summary"]
+        err = S.errors(3, 300)
+    finally:
+        grid = S.close()
+    return {"workload": SERVE_WORKLOAD.format(n=nreq, pool=pool_size, slots=slots, hi=18), "capacity_per_s": cap,
+            "loads": loads, "accuracy_vs_oracle": err, "grids": grid, "host_input_generation_s": gen_s,
+            "n_particles_p50": int(np.median([p.n for p, _ in pool]))}
+
+
+def run_serve(args):
+    """Serving workload: requests (host arrays) arrive as a Poisson stream and
+    go through the library's serving loop (continuous batching over slots,
+    admission by HBM, grids resident by id); throughput and p50/p99 latency
+    are measured on the host clock from submission to results in host memory."""
+    import torch
+    import paper_2404_17084_gb300 as L
+    import synth
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    t0 = time.perf_counter()
+    pool = serve_pool(args.pool, rank_seed(synth.BASE_SEED + 5, rank))
+    gen_s = time.perf_counter() - t0
+    S = ServeSession(L, local, pool, args.slots)
+    try:
+        for _ in range(max(1, args.warmup // 3)):
+            S.burst(range(len(pool)), first=True)
+        capacity = S.capacity()
+        # the headline stream at 80% of capacity, then the latency at 50% and 90%
+        rate = args.rate if args.rate > 0 else 0.8 * capacity
+        main = S.stream(rate, args.requests, synth.BASE_SEED + 6, ClockSampler(local))
+        sweep = {str(load): S.stream(load * capacity, args.requests, synth.BASE_SEED + 6 + int(load * 10))["summary"]
+                 for load in (0.5, 0.9)}
+        err = S.errors(4, 400)
+    finally:
+        grid = S.close()
+    summ = main["summary"]
+    order, results, wall = main["order"], main["results"], main["wall"]
     pairs = int(sum(r.n_pairs for r in results))
     line = {
         "metric": "particle-cell pair integrals/sec at 1 GB300 (mixed vs FP64 form) + p50/p99 latency",
@@ -652,21 +745,20 @@ def run_serve(args):
         "vs_baseline": None,
         "dtype": "f32+f64",
         "data": "synthetic",
-        "config": {"workload": SERVE_WORKLOAD.format(n=args.requests, pool=len(pool), slots=args.slots),
+        "config": {"workload": SERVE_WORKLOAD.format(n=args.requests, pool=len(pool), slots=args.slots, hi=21),
                    "arrival_rate_per_s": rate, "capacity_per_s": capacity,
-                   "step": "one request: copy-in, grid upload, solve_h, pair list, pair integrals, copy-out"},
-        "serving": {"requests_per_s": args.requests / wall, "latency_ms": {"p50": float(np.percentile(lat, 50)),
-                    "p99": float(np.percentile(lat, 99)), "max": float(lat.max())},
-                    "queue_ms": {"p50": float(np.percentile(que, 50)), "p99": float(np.percentile(que, 99))},
-                    "all_ok": bool(ok), "results_equal_to_first_pass": bool(same),
-                    "n_particles_p50": int(np.median([pool[j][0].n for j in order])),
-                    "host_input_generation_s": gen_s,
-                    "load_sweep": sweep},
+                   "step": "one request: copy-in, solve_h, octree, pair list, pair integrals, copy-out (its grid "
+                           "uploaded by its first request only)"},
+        "latency_ms": summ["latency_ms"],
+        "serving": {**summ, "n_particles_p50": int(np.median([pool[j][0].n for j in order])),
+                    "host_input_generation_s": gen_s, "load_sweep": sweep, "grids": grid},
+        "accuracy_vs_oracle": err,
         "e2e": {"value": pairs / wall, "unit": "pair integrals/s",
-                "h2d_bytes_per_step": int(np.mean([pool[j][0].n * 32 + pool[j][1].nbytes() for j in order])),
-                "d2h_bytes_per_step": int(np.mean([pool[j][1].ncell * 8 for j in order]))},
+                "h2d_bytes_per_step": int(np.mean([pool[j][0].n * 32 for j in order])),
+                "d2h_bytes_per_step": int(np.mean([pool[j][1].ncell * 8 for j in order])),
+                "note": "grids resident by id: after a grid's first request, a request copies in its particles only"},
         "gpu_launches": None,
-        "clocks": clocks,
+        "clocks": main["clocks"],
     }
     emit(line, rank)
 
@@ -1056,6 +1148,8 @@ def run_pseudo(args):
     st_f = L.map_get_stats(ctx)
     full_phases = L.map_get_timing(ctx)
     mp, mf = mass_p.cpu().numpy(), mass_f.cpu().numpy()
+    pq = synth.Particles(ox[:k].cpu().numpy(), oy[:k].cpu().numpy(), oz[:k].cpu().numpy(), om[:k].cpu().numpy())
+    pseudo_err = oracle_errors(g, pq, oh[:k].cpu().numpy(), mp, 300, 21)
     rel = np.abs(mp - mf) / np.maximum(mf, 1e-12 * mf.max())
     step_ms = build_ms + map_ms
     mass_plain = float(abs(om[:k].sum().item() - m.sum().item()) / m.sum().item())
@@ -1091,6 +1185,7 @@ def run_pseudo(args):
                                                         "p99": float(np.percentile(rel, 99))},
                    "mass_pseudo_vs_full": mass_plain,
                    "walk_controls": controls},
+        "accuracy_vs_oracle": pseudo_err,
         "e2e": None, "gpu_launches": None,
     }
     L.map_destroy(ctx)
@@ -1171,19 +1266,12 @@ def e2e_run(L, torch, ctx, p, g, dev, args, barrier, world):
             "d2h_bytes_per_step": int(d2h), "ms_per_step": sec * 1e3, "steps": steps}
 
 
-def oracle_sample(p, g, h, target_s: float, seed: int = 7):
-    """Time the oracle on a random sample of cells sized for ~target_s seconds."""
+def oracle_sample(p, g, h, ncells: int, seed: int = 7):
+    """Time the oracle on a seeded random sample of ncells cells."""
     import oracle
     rng = np.random.default_rng(seed)
-    order = rng.permutation(g.ncell)
+    cells = np.sort(rng.permutation(g.ncell)[:min(ncells, g.ncell)])
     ncores = os.cpu_count() or 1
-    # calibration on a few cells
-    k = 8
-    t0 = time.perf_counter()
-    r = oracle.map_cells(g, p.x, p.y, p.z, p.m, h, cells=np.sort(order[:k]), nthreads=ncores)
-    dt = time.perf_counter() - t0
-    k2 = int(min(g.ncell, max(k, k * target_s / max(dt, 1e-3))))
-    cells = np.sort(order[:k2])
     t0 = time.perf_counter()
     r = oracle.map_cells(g, p.x, p.y, p.z, p.m, h, cells=cells, nthreads=ncores)
     dt = time.perf_counter() - t0
@@ -1194,7 +1282,8 @@ def cpu_baseline(p, g, h, mass_mixed, h_fp64, mass_fp64, args):
     """Oracle timing on a bounded sample of cells, and the per-cell error of
     each GPU build against the oracle run on that build's own h."""
     import oracle
-    cells, r, dt, ncores = oracle_sample(p, g, h, args.cpu_seconds)
+    # a seeded random 1% of the cells, at least 2000
+    cells, r, dt, ncores = oracle_sample(p, g, h, max(2000, g.ncell // 100))
     npairs = len(r["idx"])
 
     def err(mass_gpu, ref):
@@ -1205,9 +1294,13 @@ def cpu_baseline(p, g, h, mass_mixed, h_fp64, mass_fp64, args):
     acc = {"cells": int(len(cells)), "mixed_max_rel": float(err_mixed.max()),
            "mixed_p99_rel": float(np.percentile(err_mixed, 99))}
     if mass_fp64 is not None:
-        r64 = oracle.map_cells(g, p.x, p.y, p.z, p.m, h_fp64, cells=cells, nthreads=ncores)
-        err_fp64 = err(mass_fp64, r64["mass"])
-        acc.update(fp64_max_rel=float(err_fp64.max()), fp64_p99_rel=float(np.percentile(err_fp64, 99)))
+        # the FP64 build on the first 2000 of those cells (its own h)
+        c64 = cells[:2000]
+        r64 = oracle.map_cells(g, p.x, p.y, p.z, p.m, h_fp64, cells=c64, nthreads=ncores)
+        scale = np.maximum(np.abs(r64["mass"]), 1e-12 * np.abs(r64["mass"]).max())
+        err_fp64 = np.abs(mass_fp64[c64] - r64["mass"]) / scale
+        acc.update(fp64_cells=int(len(c64)), fp64_max_rel=float(err_fp64.max()),
+                   fp64_p99_rel=float(np.percentile(err_fp64, 99)))
     acc["note"] = "per-cell mass vs the FP64 oracle on the same cells, each build with its own GPU-solved h"
     # the same oracle on one core, on a sixteenth of the sample
     c1 = cells[:max(4, len(cells) // 16)]
@@ -1215,8 +1308,9 @@ def cpu_baseline(p, g, h, mass_mixed, h_fp64, mass_fp64, args):
     r1 = oracle.map_cells(g, p.x, p.y, p.z, p.m, h, cells=c1, nthreads=1)
     dt1 = time.perf_counter() - t1
     base = {"value": npairs / dt, "unit": "pair integrals/s", "cores": ncores, "kind": "oracle",
-            "sample": f"{len(cells)} random cells of the same snapshot ({npairs} pairs; pair list by brute force "
-                      f"over all {p.n} particles + adaptive-quadrature pair integrals), {dt:.1f} s",
+            "sample": f"{len(cells)} random cells (max(2000, 1% of the cells)) of the same snapshot ({npairs} pairs; "
+                      f"pair list by brute force over all {p.n} particles + adaptive-quadrature pair integrals), "
+                      f"{dt:.1f} s",
             "value_1core": len(r1["idx"]) / dt1,
             "sample_1core": f"the first {len(c1)} of those cells ({len(r1['idx'])} pairs) on one core, {dt1:.1f} s",
             "cpu": platform.processor() or platform.machine()}
@@ -1273,6 +1367,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--skip-fp64", action="store_true")
     ap.add_argument("--skip-e2e", action="store_true")
+    ap.add_argument("--skip-serve", action="store_true", help="no serving pass (latency) in the default line")
     ap.add_argument("--dump", action="store_true", help="save per-cell results to <outdir>/cells.npz")
     ap.add_argument("--outdir", default=os.path.join(ROOT, "bench_out"),
                     help="folder for the clock samples and --dump output")

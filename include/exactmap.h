@@ -11,6 +11,12 @@
  *  - Calls are asynchronous on the given CUDA stream (NULL = legacy default
  *    stream) unless documented as synchronising; statistics are read back with
  *    map_get_stats(), which synchronises that stream.
+ *  - The calls of one context run in stream order, one after the other: a call
+ *    on another stream than the context's previous call first makes its
+ *    stream wait for the previous call's stream (an event; the host does not
+ *    wait).  Workspace is allocated and freed in the stream-ordered
+ *    allocator's pool on the calling stream, so no call waits for the whole
+ *    device (map_destroy waits for the context's own streams).
  *  - A context is not thread-safe: use one context per host thread.
  *  - Lengths are in the unit cube [0,1]^3; masses are arbitrary positive
  *    numbers; the kernel is the M4 cubic spline with support 2h.
@@ -117,7 +123,8 @@ typedef struct {
 typedef struct {
   int64_t n_pairs;      /* listed particle-cell pairs (one pair integral each) */
   int64_t n_edge_terms; /* edge integrals evaluated (two vertex pyramids each); count_work only */
-  int64_t n_fp64_terms; /* edge integrals evaluated in FP64 in the mixed build; count_work only */
+  int64_t n_fp64_terms; /* edge integrals evaluated in FP64 in the mixed build (faces whose plane passes within
+                           1e-4 h of the particle) */
   double total_mass;    /* sum_i M_i */
   int status;           /* device-side status word (MAP_OK or a MAP_E* code) */
 } map_stats;
@@ -145,13 +152,18 @@ const char* map_strerror(int code);
  * what the context's precision reads: FP32 face planes, face bounding
  * spheres and edge records for MAP_MIXED, FP64 edge records for MAP_FP64.  The grid stays
  * resident until map_grid_release / map_destroy.  Synchronises the stream.
- * Errors: MAP_EINVAL (empty or inconsistent sizes), MAP_ENOMEM. */
+ * Errors: MAP_EINVAL (empty or inconsistent sizes, a corrupted CSR: an
+ * offset array that is not increasing, a loop of fewer than 3 entries, a
+ * cell of fewer than 4 faces, a vertex index out of range, or last offsets
+ * that disagree with nface / nloop -- checked on the device before any
+ * kernel indexes with them), MAP_ENOMEM. */
 int map_grid_upload(map_ctx* ctx, const map_grid* grid, int* handle, void* stream);
 
 /* Release a resident grid.  Its device buffers stay with the context and
  * serve later uploads of the same or a smaller grid (no cudaMalloc then);
  * they are freed by map_destroy, or when an upload or the HBM budget needs
- * the room.  Waits for the device.  MAP_EHANDLE if unknown. */
+ * the room.  Returns at once: later calls of the context that reuse or free
+ * those buffers are ordered after its earlier work.  MAP_EHANDLE if unknown. */
 int map_grid_release(map_ctx* ctx, int handle);
 
 /* Copy the volumes V_i of a resident grid into vol (device, ncell doubles). */
@@ -247,9 +259,8 @@ int map_copy_pairs(map_ctx* ctx, int64_t* pair_off, int32_t* pair_idx, double* p
  * particle), kept by the context until the next mapping call; later calls
  * with other cell values reuse it.  The build's sort workspace (about 20
  * bytes per pair) also stays with the context, for the next mapping's build,
- * until map_destroy.  Asynchronous on stream, which the caller orders after the
- * mapping call (the same stream, or an event); on another stream than the
- * mapping call's, the first call waits for the copy to be built.
+ * until map_destroy.  Asynchronous on stream (ordered after the mapping
+ * call like every call of the context).
  * Errors: MAP_EINVAL (NULL pointer; no single mapping call with per-pair
  * integrals in this context: map_batch and the server keep none; n is not
  * that call's particle count; 2^32 or more pairs), MAP_ENOMEM, MAP_ECUDA. */
@@ -306,14 +317,21 @@ int map_get_autotune(map_ctx* ctx, int* chosen, float* ms, int* nvariants);
 
 /* A request loop with continuous batching (the paper has no counterpart: it
  * maps one snapshot at a time).  Requests carry host arrays; the server runs
- * up to `slots` of them at once, each on its own context and CUDA stream, so
+ * up to `slots` of them at once, each on its own context (its octree and
+ * pair-list workspace stays allocated between requests) and CUDA stream, so
  * their work overlaps on the device.  Queued requests are admitted in arrival
  * order as soon as a slot is idle and the request's device-memory estimate
- * fits hbm_budget next to what running requests and idle slots' cached
- * workspace hold (idle caches are released to make room).  A request runs:
- * copy-in, grid upload, solve_h, map_particles_to_cells, copy-out.  Its
- * result depends on its own inputs only, so it is bit-identical alone and in
- * any mix.  Threads: submit, wait and stats may be called from any thread. */
+ * fits hbm_budget next to what running requests, idle slots' cached
+ * workspace and the resident grids hold (idle caches, then the least
+ * recently used resident grids that no running request maps onto, are
+ * released to make room).  Grids are kept resident by id: a request whose
+ * grid_id is >= 0 uploads its grid only when no resident grid has that id,
+ * and maps onto the resident copy otherwise.  A request runs: copy-in of its
+ * particles (and of its grid when not resident) through its slot's pinned
+ * staging buffers, solve_h, map_particles_to_cells, copy-out.  No step waits
+ * for the whole device: allocations are stream-ordered on the slot's stream.
+ * Its result depends on its own inputs only, so it is bit-identical alone and
+ * in any mix.  Threads: submit, wait and stats may be called from any thread. */
 typedef struct map_server map_server;
 
 typedef struct {
@@ -327,7 +345,11 @@ typedef struct {
 /* One mapping request.  All pointers are HOST memory owned by the caller and
  * must stay valid until map_server_wait returns for the request.  The grid
  * arrays follow map_grid; cell_mass (ncell) is required, cell_rho (ncell) and
- * h (n, the solved smoothing lengths) are optional outputs. */
+ * h (n, the solved smoothing lengths) are optional outputs.  grid_id >= 0:
+ * the grid is kept resident under that id after the request (the caller
+ * guarantees that every request with the same id carries the same grid; a
+ * request that finds its id resident does not read its grid arrays); < 0:
+ * the grid is uploaded for this request alone. */
 typedef struct {
   int64_t n;
   const double *x, *y, *z, *m;
@@ -339,6 +361,7 @@ typedef struct {
   double* cell_mass;
   double* cell_rho;
   double* h;
+  int64_t grid_id;
 } map_request;
 
 typedef struct {
@@ -369,8 +392,13 @@ int map_server_wait(map_server* srv, int64_t ticket, map_request_result* res);
  * holds or has reserved. */
 int map_server_stats(map_server* srv, int64_t* completed, int* running, int64_t* queued, size_t* held_bytes);
 
+/* Resident grids: uploads so far (requests that found no resident grid for
+ * their id), hits (requests that mapped onto a resident grid), grids
+ * resident now and their device bytes.  Any pointer may be NULL. */
+int map_server_grid_stats(map_server* srv, int64_t* uploads, int64_t* hits, int64_t* resident, size_t* bytes);
+
 /* Fail the queued requests, wait for the running ones, stop the workers and
- * free everything. */
+ * free everything (resident grids included). */
 void map_server_destroy(map_server* srv);
 
 /* ------------------------------------------------------------ smoothing lengths (Section III-C, Eq. 7-9) */

@@ -115,7 +115,7 @@ class map_request(ctypes.Structure):
     _fields_ = [("n", _I64), ("x", _P), ("y", _P), ("z", _P), ("m", _P), ("ncell", _I64), ("nface", _I64),
                 ("nloop", _I64), ("nvert", _I64), ("cell_face_off", _P), ("face_vert_off", _P),
                 ("face_vert", _P), ("face_plane", _P), ("vx", _P), ("vy", _P), ("vz", _P), ("site", _P),
-                ("cell_mass", _P), ("cell_rho", _P), ("h", _P)]
+                ("cell_mass", _P), ("cell_rho", _P), ("h", _P), ("grid_id", _I64)]
 
 
 class map_request_result(ctypes.Structure):
@@ -130,9 +130,11 @@ _lib.map_server_submit.argtypes = [_P, ctypes.POINTER(map_request), ctypes.POINT
 _lib.map_server_wait.argtypes = [_P, _I64, ctypes.POINTER(map_request_result)]
 _lib.map_server_stats.argtypes = [_P, ctypes.POINTER(_I64), ctypes.POINTER(ctypes.c_int), ctypes.POINTER(_I64),
                                   ctypes.POINTER(ctypes.c_size_t)]
+_lib.map_server_grid_stats.argtypes = [_P, ctypes.POINTER(_I64), ctypes.POINTER(_I64), ctypes.POINTER(_I64),
+                                       ctypes.POINTER(ctypes.c_size_t)]
 _lib.map_server_destroy.argtypes = [_P]
 _lib.map_server_destroy.restype = None
-for _name in ("map_server_create", "map_server_submit", "map_server_wait", "map_server_stats"):
+for _name in ("map_server_create", "map_server_submit", "map_server_wait", "map_server_stats", "map_server_grid_stats"):
     getattr(_lib, _name).restype = ctypes.c_int
 _lib.map_batch.argtypes = [_P, ctypes.c_int, ctypes.POINTER(map_particles), ctypes.POINTER(ctypes.c_int),
                            ctypes.POINTER(map_outputs), _P, _P]
@@ -281,10 +283,11 @@ def _host(a, dtype):
     return a, ctypes.c_void_p(a.ctypes.data)
 
 
-def map_server_submit(srv, x, y, z, m, grid, cell_mass, cell_rho=None, h=None) -> int:
+def map_server_submit(srv, x, y, z, m, grid, cell_mass, cell_rho=None, h=None, grid_id: int = -1) -> int:
     """Queue one request of host (numpy) arrays: particles x, y, z, m and a
     grid (synth.Grid or dict of its CSR arrays); cell_mass (ncell float64,
-    written on completion) and optional cell_rho, h.  Returns the ticket."""
+    written on completion) and optional cell_rho, h; grid_id >= 0 keeps the
+    grid resident under that id for later requests.  Returns the ticket."""
     G = grid if isinstance(grid, dict) else {k: getattr(grid, k) for k in (
         "cell_face_off", "face_vert_off", "face_vert", "face_plane", "vx", "vy", "vz", "site")}
     keep = []
@@ -303,7 +306,7 @@ def map_server_submit(srv, x, y, z, m, grid, cell_mass, cell_rho=None, h=None) -
                       ptr(G["vy"], np.float64), ptr(G["vz"], np.float64), ptr(G["site"], np.float64),
                       ctypes.c_void_p(cell_mass.ctypes.data),
                       ctypes.c_void_p(cell_rho.ctypes.data) if cell_rho is not None else None,
-                      ctypes.c_void_p(h.ctypes.data) if h is not None else None)
+                      ctypes.c_void_p(h.ctypes.data) if h is not None else None, int(grid_id))
     keep += [cell_mass, cell_rho, h]
     t = _I64()
     _check(_lib.map_server_submit(srv, ctypes.byref(req), ctypes.byref(t)), "map_server_submit")
@@ -316,6 +319,15 @@ def map_server_wait(srv, ticket: int) -> map_request_result:
     _check(_lib.map_server_wait(srv, ticket, ctypes.byref(res)), "map_server_wait")
     _server_keep.pop((srv.value, ticket), None)
     return res
+
+
+def map_server_grid_stats(srv):
+    """(uploads, hits, resident grids, resident bytes)."""
+    u, hh, r = _I64(), _I64(), _I64()
+    b = ctypes.c_size_t()
+    _check(_lib.map_server_grid_stats(srv, ctypes.byref(u), ctypes.byref(hh), ctypes.byref(r), ctypes.byref(b)),
+           "map_server_grid_stats")
+    return u.value, hh.value, r.value, b.value
 
 
 def map_server_stats(srv):

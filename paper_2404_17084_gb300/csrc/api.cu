@@ -37,26 +37,60 @@ int check_particles(map_ctx* ctx, const map_particles* p, bool need_m, bool need
   return ctx->h_scratch[0] ? MAP_EINVAL : MAP_OK;
 }
 
+int ctx_enter(map_ctx* ctx, cudaStream_t s) {
+  CUDA_TRY(cudaSetDevice(ctx->device));
+  if (!ctx->ord_ev) CUDA_TRY(cudaEventCreateWithFlags(&ctx->ord_ev, cudaEventDisableTiming));
+  if (ctx->has_last && ctx->last_stream != s) CUDA_TRY(cudaStreamWaitEvent(s, ctx->ord_ev, 0));
+  ctx->cur_stream = s;
+  ctx->last_stream = s;
+  ctx->has_last = true;
+  return MAP_OK;
+}
+
+int dev_alloc(map_ctx* ctx, void** p, size_t bytes) {
+  *p = nullptr;
+  if (cudaMallocAsync(p, bytes > 0 ? bytes : 16, ctx->cur_stream) != cudaSuccess) {
+    cudaGetLastError();
+    *p = nullptr;
+    return MAP_ENOMEM;
+  }
+  return MAP_OK;
+}
+
+void dev_free(map_ctx* ctx, void* p) {
+  if (p) cudaFreeAsync(p, ctx->cur_stream);
+}
+
 int ctx_ensure(map_ctx* ctx, DevBuf& b, size_t bytes) {
   if (b.cap >= bytes) return MAP_OK;
   size_t nb = bytes + bytes / 4 + 4096;
   size_t after = ctx->bytes_in_use - b.cap + nb;
   if (ctx->cfg.hbm_budget && after > ctx->cfg.hbm_budget) return MAP_ENOMEM;
   if (b.p) {
-    // the stream-ordered contents are dead; wait for users before freeing
-    cudaDeviceSynchronize();
-    cudaFree(b.p);
+    // the contents are dead; earlier users of the buffer are ordered before
+    // this call's stream (ctx_enter), so the free waits for them in stream order
+    dev_free(ctx, b.p);
     ctx->bytes_in_use -= b.cap;
     b.p = nullptr;
     b.cap = 0;
   }
-  if (cudaMalloc(&b.p, nb) != cudaSuccess) {
-    cudaGetLastError();
-    b.p = nullptr;
-    return MAP_ENOMEM;
-  }
+  MAP_TRY(dev_alloc(ctx, &b.p, nb));
   b.cap = nb;
   ctx->bytes_in_use += nb;
+  return MAP_OK;
+}
+
+// The mapping of Eq. (1)-(3) on a prepared grid (the context already entered on s).
+int map_run(map_ctx* ctx, const map_particles* p, PreparedGrid* g, map_outputs* out, cudaStream_t s) {
+  MAP_TRY(check_particles(ctx, p, true, true, s));
+  phase_begin(ctx, 0, s);
+  MAP_TRY(tree_build(ctx, p->x, p->y, p->z, p->m, p->h, p->n, s));
+  phase_end(ctx, 0, s);
+  phase_begin(ctx, 1, s);
+  MAP_TRY(pairs_build(ctx, g, s));
+  phase_end(ctx, 1, s);
+  MAP_TRY(integrals_run(ctx, g, p, out, s));
+  ctx->last_npart = p->n;
   return MAP_OK;
 }
 
@@ -138,31 +172,38 @@ int map_init(map_ctx** out, const map_config* cfg) {
 void map_destroy(map_ctx* ctx) {
   if (!ctx) return;
   cudaSetDevice(ctx->device);
-  cudaDeviceSynchronize();
+  // wait for the context's own work only (other contexts keep running): its
+  // workers, its batch stream and the end of its last call -- an event, as
+  // the caller's stream may no longer exist; then return the workspace
+  destroy_workers(ctx);
+  if (ctx->bstream) cudaStreamSynchronize(ctx->bstream);
+  if (ctx->ord_ev) cudaEventSynchronize(ctx->ord_ev);
+  ctx->cur_stream = nullptr;
   for (PreparedGrid* g : ctx->grids)
     if (g) {
-      for (const DevBuf& b : g->allocs) cudaFree(b.p);
+      for (const DevBuf& b : g->allocs) dev_free(ctx, b.p);
       delete g;
     }
-  for (const DevBuf& b : ctx->grid_pool) cudaFree(b.p);
-  for (auto& b : ctx->ws_tree) if (b.p) cudaFree(b.p);
-  for (auto& b : ctx->ws_pairs) if (b.p) cudaFree(b.p);
-  for (auto& b : ctx->ws_misc) if (b.p) cudaFree(b.p);
-  for (auto& b : ctx->ws_inv) if (b.p) cudaFree(b.p);
-  for (auto& b : ctx->ws_vor) if (b.p) cudaFree(b.p);
+  for (const DevBuf& b : ctx->grid_pool) dev_free(ctx, b.p);
+  for (auto& b : ctx->ws_tree) dev_free(ctx, b.p);
+  for (auto& b : ctx->ws_pairs) dev_free(ctx, b.p);
+  for (auto& b : ctx->ws_misc) dev_free(ctx, b.p);
+  for (auto& b : ctx->ws_inv) dev_free(ctx, b.p);
+  for (auto& b : ctx->ws_vor) dev_free(ctx, b.p);
   table_free(ctx);
-  for (auto& b : ctx->ws_grid) if (b.p) cudaFree(b.p);
-  if (ctx->cub_tmp.p) cudaFree(ctx->cub_tmp.p);
+  for (auto& b : ctx->ws_grid) dev_free(ctx, b.p);
+  dev_free(ctx, ctx->cub_tmp.p);
+  dev_free(ctx, ctx->ws_near.p);
+  for (auto* v : {&ctx->batch_off, &ctx->batch_idx, &ctx->batch_itm, &ctx->batch_ioff, &ctx->batch_part})
+    for (auto& b : *v) dev_free(ctx, b.p);
+  cudaStreamSynchronize(ctx->cur_stream);
   if (ctx->d_counters) cudaFree(ctx->d_counters);
   if (ctx->d_total) cudaFree(ctx->d_total);
   if (ctx->h_stats) cudaFreeHost(ctx->h_stats);
   if (ctx->h_scratch) cudaFreeHost(ctx->h_scratch);
   for (auto& e : ctx->ev) if (e) cudaEventDestroy(e);
-  for (auto* v : {&ctx->batch_off, &ctx->batch_idx, &ctx->batch_itm, &ctx->batch_ioff, &ctx->batch_part})
-    for (auto& b : *v)
-      if (b.p) cudaFree(b.p);
+  if (ctx->ord_ev) cudaEventDestroy(ctx->ord_ev);
   if (ctx->bexec) cudaGraphExecDestroy(ctx->bexec);
-  destroy_workers(ctx);
   for (auto& e : ctx->bev) if (e) cudaEventDestroy(e);
   if (ctx->bstream) cudaStreamDestroy(ctx->bstream);
   delete ctx;
@@ -175,7 +216,7 @@ int map_grid_upload(map_ctx* ctx, const map_grid* grid, int* handle, void* strea
   if (grid->nvert >= (int64_t)INT32_MAX || !grid->cell_face_off || !grid->face_vert_off || !grid->face_vert ||
       !grid->face_plane || !grid->vx || !grid->vy || !grid->vz || !grid->site)
     return MAP_EINVAL;
-  CUDA_TRY(cudaSetDevice(ctx->device));
+  MAP_ENTER(ctx, S(stream));
   PreparedGrid* g = new (std::nothrow) PreparedGrid();
   if (!g) return MAP_ENOMEM;
   int r = grid_prepare(ctx, grid, g, S(stream));
@@ -208,8 +249,8 @@ int map_grid_copy(map_ctx* ctx, int handle, int64_t* cell_face_off, int64_t* fac
   if (!ctx) return MAP_EINVAL;
   if (handle < 0 || handle >= (int)ctx->grids.size() || !ctx->grids[handle]) return MAP_EHANDLE;
   const PreparedGrid* g = ctx->grids[handle];
-  CUDA_TRY(cudaSetDevice(ctx->device));
   cudaStream_t s = S(stream);
+  MAP_ENTER(ctx, s);
   auto cp = [&](void* dst, const void* src, size_t bytes) -> int {
     if (dst && bytes) CUDA_TRY(cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDefault, s));
     return MAP_OK;
@@ -228,8 +269,8 @@ int map_grid_copy(map_ctx* ctx, int handle, int64_t* cell_face_off, int64_t* fac
 int map_grid_release(map_ctx* ctx, int handle) {
   if (!ctx) return MAP_EINVAL;
   if (handle < 0 || handle >= (int)ctx->grids.size() || !ctx->grids[handle]) return MAP_EHANDLE;
-  cudaSetDevice(ctx->device);
-  cudaDeviceSynchronize();
+  // no wait: the buffers go to the context's pool, and the calls that reuse
+  // or free them are ordered after this context's earlier work (ctx_enter)
   PreparedGrid* g = ctx->grids[handle];
   grid_recycle(ctx, g);  // kept for the next upload; freed by map_destroy or when room runs out
   delete g;
@@ -241,6 +282,7 @@ int map_grid_volumes(map_ctx* ctx, int handle, double* vol, void* stream) {
   if (!ctx || !vol) return MAP_EINVAL;
   if (handle < 0 || handle >= (int)ctx->grids.size() || !ctx->grids[handle]) return MAP_EHANDLE;
   const PreparedGrid* g = ctx->grids[handle];
+  MAP_ENTER(ctx, S(stream));
   CUDA_TRY(cudaMemcpyAsync(vol, g->vol, g->ncell * sizeof(double), cudaMemcpyDeviceToDevice, S(stream)));
   return MAP_OK;
 }
@@ -248,20 +290,9 @@ int map_grid_volumes(map_ctx* ctx, int handle, double* vol, void* stream) {
 int map_particles_to_cells(map_ctx* ctx, const map_particles* p, int handle, map_outputs* out, void* stream) {
   if (!ctx || !p || !out || !out->cell_mass) return MAP_EINVAL;
   if (handle < 0 || handle >= (int)ctx->grids.size() || !ctx->grids[handle]) return MAP_EHANDLE;
-  CUDA_TRY(cudaSetDevice(ctx->device));
   cudaStream_t s = S(stream);
-  MAP_TRY(check_particles(ctx, p, true, true, s));
-  const PreparedGrid* g = ctx->grids[handle];
-  phase_begin(ctx, 0, s);
-  MAP_TRY(tree_build(ctx, p->x, p->y, p->z, p->m, p->h, p->n, s));
-  phase_end(ctx, 0, s);
-  phase_begin(ctx, 1, s);
-  MAP_TRY(pairs_build(ctx, g, s));
-  phase_end(ctx, 1, s);
-  MAP_TRY(integrals_run(ctx, g, p, out, s));
-  ctx->last_npart = p->n;
-  ctx->last_stream = s;
-  return MAP_OK;
+  MAP_ENTER(ctx, s);
+  return map_run(ctx, p, ctx->grids[handle], out, s);
 }
 
 int map_get_pairs(map_ctx* ctx, const int64_t** pair_off, const int32_t** pair_idx, const double** pair_frac,
@@ -269,6 +300,7 @@ int map_get_pairs(map_ctx* ctx, const int64_t** pair_off, const int32_t** pair_i
   if (!ctx) return MAP_EINVAL;
   if (pair_off || pair_idx || pair_frac) {
     CUDA_TRY(cudaSetDevice(ctx->device));
+    ctx->cur_stream = ctx->last_stream;
     MAP_TRY(pairs_sort_lists(ctx, ctx->last_stream));
   }
   if (pair_off) *pair_off = ctx->pair_off;
@@ -287,8 +319,10 @@ int map_copy_pairs(map_ctx* ctx, int64_t* pair_off, int32_t* pair_idx, double* p
   cudaStream_t s = S(stream);
   if (!ctx->pairs_sorted) {
     // sort on the mapping call's stream, then order this copy after it
+    ctx->cur_stream = ctx->last_stream;
     MAP_TRY(pairs_sort_lists(ctx, ctx->last_stream));
   }
+  MAP_ENTER(ctx, s);
   CUDA_TRY(cudaMemcpyAsync(pair_off, ctx->pair_off, (ctx->last_ncell + 1) * sizeof(int64_t), cudaMemcpyDeviceToDevice, s));
   if (ctx->n_pairs > 0) {
     CUDA_TRY(cudaMemcpyAsync(pair_idx, ctx->pair_idx, ctx->n_pairs * sizeof(int32_t), cudaMemcpyDeviceToDevice, s));
@@ -337,13 +371,12 @@ int map_get_work(map_ctx* ctx, int64_t* counts, int64_t* launches) {
 
 int solve_h(map_ctx* ctx, map_particles* p, int32_t* route, void* stream) {
   if (!ctx || !p || !p->h) return MAP_EINVAL;
-  CUDA_TRY(cudaSetDevice(ctx->device));
   cudaStream_t s = S(stream);
+  MAP_ENTER(ctx, s);
   MAP_TRY(check_particles(ctx, p, false, false, s));
   phase_begin(ctx, 3, s);
   MAP_TRY(h_solve_run(ctx, p->x, p->y, p->z, p->n, p->h, route, nullptr, s));
   phase_end(ctx, 3, s);
-  ctx->last_stream = s;
   return MAP_OK;
 }
 
@@ -358,12 +391,10 @@ int build_pseudo_particles_walk(map_ctx* ctx, const map_particles* full, const m
     if (!std::isfinite(walk->src[k])) return MAP_EINVAL;
   for (int k = 0; k < 5 * walk->nregion; ++k)
     if (!std::isfinite(walk->regions[k]) || (k % 5 >= 3 && walk->regions[k] < 0.0)) return MAP_EINVAL;
-  CUDA_TRY(cudaSetDevice(ctx->device));
   cudaStream_t s = S(stream);
+  MAP_ENTER(ctx, s);
   MAP_TRY(check_particles(ctx, full, true, true, s));
-  int r = pseudo_run(ctx, full, walk, out, kind, ident, n_pseudo, s);
-  ctx->last_stream = s;
-  return r;
+  return pseudo_run(ctx, full, walk, out, kind, ident, n_pseudo, s);
 }
 
 int build_pseudo_particles(map_ctx* ctx, const map_particles* full, const double* src, int nsrc, map_particles* out,

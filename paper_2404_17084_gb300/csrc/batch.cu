@@ -77,9 +77,9 @@ int ensure_stream(map_ctx* ctx) {
 void destroy_workers(map_ctx* ctx) {
   for (BatchWorker& w : ctx->workers) {
     if (w.stream) cudaStreamSynchronize(w.stream);
+    map_destroy(w.ctx);  // before its stream goes
     if (w.done) cudaEventDestroy(w.done);
     if (w.stream) cudaStreamDestroy(w.stream);
-    map_destroy(w.ctx);
   }
   ctx->workers.clear();
   if (ctx->wev) cudaEventDestroy(ctx->wev);
@@ -162,19 +162,19 @@ int solve_h_batch(map_ctx* ctx, int nsnap, map_particles* parts, int32_t* const*
   if (!ctx || nsnap < 1 || !parts) return MAP_EINVAL;
   for (int j = 0; j < nsnap; ++j)
     if (!check_sizes(&parts[j]) || !parts[j].h) return MAP_EINVAL;
-  CUDA_TRY(cudaSetDevice(ctx->device));
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  MAP_ENTER(ctx, s);
   std::vector<int> big(nsnap);
   std::iota(big.begin(), big.end(), 0);
   std::stable_sort(big.begin(), big.end(), [&](int a, int b) { return parts[a].n > parts[b].n; });
   phase_begin(ctx, 3, s);
   const int rc = run_on_workers(ctx, nsnap, big.data(), s, [&](BatchWorker& W, int j) -> int {
     map_particles* p = &parts[j];
+    MAP_ENTER(W.ctx, W.stream);
     MAP_TRY(check_particles(W.ctx, p, false, false, W.stream));
     return h_solve_run(W.ctx, p->x, p->y, p->z, p->n, p->h, routes ? routes[j] : nullptr, nullptr, W.stream);
   });
   phase_end(ctx, 3, s);
-  ctx->last_stream = s;
   return rc;
 }
 
@@ -186,8 +186,8 @@ int map_batch(map_ctx* ctx, int nsnap, const map_particles* parts, const int* gr
     if (grids[j] < 0 || grids[j] >= (int)ctx->grids.size() || !ctx->grids[grids[j]]) return MAP_EHANDLE;
     if (!outs[j].cell_mass) return MAP_EINVAL;
   }
-  CUDA_TRY(cudaSetDevice(ctx->device));
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  MAP_ENTER(ctx, s);
   MAP_TRY(ensure_stream(ctx));
   if ((int)ctx->batch_off.size() < nsnap) {
     ctx->batch_off.resize(nsnap);
@@ -213,6 +213,7 @@ int map_batch(map_ctx* ctx, int nsnap, const map_particles* parts, const int* gr
   int rc = run_on_workers(ctx, nsnap, big.data(), s, [&](BatchWorker& W, int j) -> int {
     map_ctx* wc = W.ctx;
     const map_particles* p = &parts[j];
+    MAP_ENTER(wc, W.stream);
     MAP_TRY(check_particles(wc, p, true, true, W.stream));
     const PreparedGrid* g = ctx->grids[grids[j]];
     MAP_TRY(tree_build(wc, p->x, p->y, p->z, p->m, p->h, p->n, W.stream));
@@ -267,9 +268,11 @@ int map_batch(map_ctx* ctx, int nsnap, const map_particles* parts, const int* gr
   MAP_TRY(ensure_t(ctx, ctx->ws_misc[5], nsnap, &d_desc));
   MAP_TRY(ensure_t(ctx, ctx->ws_misc[6], 2 * (nsnap + 1), &d_base));
   MAP_TRY(ensure_t(ctx, ctx->ws_misc[7], nsnap, &d_tot));
+  int64_t* near;
+  MAP_TRY(ensure_t(ctx, ctx->ws_near, ibase[nsnap] + 1, &near));
   int64_t* d_ibase = d_base;
   int64_t* d_cbase = d_base + nsnap + 1;
-  const BatchArgs B{d_desc, d_ibase, d_cbase, nsnap, ibase[nsnap], total, ctx->d_counters};
+  const BatchArgs B{d_desc, d_ibase, d_cbase, nsnap, ibase[nsnap], total, ctx->d_counters, near};
 
   // 3. the integral launch of the whole batch: ordered after the caller's
   // stream, on the context's own stream (graphs cannot be captured on the
@@ -284,7 +287,7 @@ int map_batch(map_ctx* ctx, int nsnap, const map_particles* parts, const int* gr
   }
   const int variant = ctx->tuned[prec];
   // graph signature: descriptor bytes, queue layout, launch shape, targets
-  std::vector<unsigned char> sig(sizeof(SnapDesc) * nsnap + 2 * sizeof(int64_t) * (nsnap + 1) + 4 * sizeof(void*));
+  std::vector<unsigned char> sig(sizeof(SnapDesc) * nsnap + 2 * sizeof(int64_t) * (nsnap + 1) + 5 * sizeof(void*));
   {
     unsigned char* q = sig.data();
     std::memcpy(q, qd.data(), sizeof(SnapDesc) * nsnap);
@@ -293,7 +296,7 @@ int map_batch(map_ctx* ctx, int nsnap, const map_particles* parts, const int* gr
     q += sizeof(int64_t) * (nsnap + 1);
     std::memcpy(q, base.data(), sizeof(int64_t) * (nsnap + 1));
     q += sizeof(int64_t) * (nsnap + 1);
-    const void* extra[4] = {d_desc, d_base, d_tot, reinterpret_cast<const void*>((intptr_t)(variant * 2 + prec))};
+    const void* extra[5] = {d_desc, d_base, d_tot, near, reinterpret_cast<const void*>((intptr_t)(variant * 2 + prec))};
     std::memcpy(q, extra, sizeof(extra));
   }
   if (!ctx->bexec || sig != ctx->bsig) {
@@ -340,7 +343,6 @@ int map_batch(map_ctx* ctx, int nsnap, const map_particles* parts, const int* gr
     }
   CUDA_TRY(cudaEventRecord(ctx->bev[1], ctx->bstream));
   CUDA_TRY(cudaStreamWaitEvent(s, ctx->bev[1], 0));
-  ctx->last_stream = s;
   return MAP_OK;
 }
 

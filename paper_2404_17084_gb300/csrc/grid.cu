@@ -171,7 +171,7 @@ void grid_recycle(map_ctx* ctx, PreparedGrid* g) {
 
 void grid_pool_drop(map_ctx* ctx) {
   for (const DevBuf& b : ctx->grid_pool) {
-    cudaFree(b.p);
+    dev_free(ctx, b.p);
     ctx->bytes_in_use -= b.cap;
   }
   ctx->grid_pool.clear();
@@ -197,14 +197,10 @@ int ctx_alloc_grid(map_ctx* ctx, PreparedGrid* g, void** p, size_t bytes) {
   }
   if (ctx->cfg.hbm_budget && ctx->bytes_in_use + bytes > ctx->cfg.hbm_budget) grid_pool_drop(ctx);
   if (ctx->cfg.hbm_budget && ctx->bytes_in_use + bytes > ctx->cfg.hbm_budget) return MAP_ENOMEM;
-  if (cudaMalloc(p, bytes) != cudaSuccess) {
-    cudaGetLastError();
+  if (dev_alloc(ctx, p, bytes) != MAP_OK) {
     if (ctx->grid_pool.empty()) return MAP_ENOMEM;
     grid_pool_drop(ctx);
-    if (cudaMalloc(p, bytes) != cudaSuccess) {
-      cudaGetLastError();
-      return MAP_ENOMEM;
-    }
+    MAP_TRY(dev_alloc(ctx, p, bytes));
   }
   ctx->bytes_in_use += bytes;
   g->bytes += bytes;

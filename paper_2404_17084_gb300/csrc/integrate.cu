@@ -201,6 +201,21 @@ __device__ __noinline__ double face_fp64(const SnapDesc& A, int64_t f, int64_t k
   return acc;
 }
 
+// Mixed build: the particle in the cell's site-relative frame, in units of
+// h, and its signed distance to a face plane (> 0 on the inner side).  Every
+// rounding is explicit, so that the integral kernel and the near-plane
+// fix-up, two compilations, take the same decisions bit for bit.
+__device__ __forceinline__ void pair_frame(const SnapDesc& A, int32_t a, double sx, double sy, double sz, float& yx,
+                                           float& yy, float& yz, float& hinv) {
+  hinv = __frcp_rn((float)A.h[a]);
+  yx = __fmul_rn((float)(A.x[a] - sx), hinv);
+  yy = __fmul_rn((float)(A.y[a] - sy), hinv);
+  yz = __fmul_rn((float)(A.z[a] - sz), hinv);
+}
+__device__ __forceinline__ float face_r0s(const float4& F, float yx, float yy, float yz, float hinv) {
+  return __fsub_rn(__fmul_rn(F.w, hinv), __fmaf_rn(F.x, yx, __fmaf_rn(F.y, yy, __fmul_rn(F.z, yz))));
+}
+
 // COUNT: also tally the work (face tests, edge records, pieces) for the
 // operation count; a separate compilation, as the tally holds registers.
 template <typename T, bool MIXED, int NW, int MINB, bool COUNT>
@@ -515,7 +530,6 @@ __global__ void __launch_bounds__(NW * 32, MINB) pair_integrals_mixed(BatchArgs 
   const SnapDesc& A = S.d;
   wedge::WorkCount wc;
   unsigned n_in = 0, n_mid = 0, n_split = 0, n_out = 0;
-  int n64 = 0;
   int cur = -1;
   for (int r = 0; r < 32; ++r) S.col[r][lane] = 0.f;
   __syncwarp();
@@ -549,6 +563,7 @@ __global__ void __launch_bounds__(NW * 32, MINB) pair_integrals_mixed(BatchArgs 
     const float* __restrict__ ecell = reinterpret_cast<const float*>(A.edge) + l0 * EDGE_STRIDE;
     const double sx = A.site[3 * c], sy = A.site[3 * c + 1], sz = A.site[3 * c + 2];
     double macc = 0.0;
+    bool item_near = false;
     const int64_t pb = item.lo, pe = item.lo + item.cnt;
     for (int64_t p0 = pb; p0 < pe; p0 += 32) {
       const int64_t p = p0 + lane;
@@ -557,32 +572,28 @@ __global__ void __launch_bounds__(NW * 32, MINB) pair_integrals_mixed(BatchArgs 
       int32_t a = 0;
       if (active) {
         a = A.pair_idx[p];
-        hinv = 1.0f / (float)A.h[a];
-        yx = (float)(A.x[a] - sx) * hinv;
-        yy = (float)(A.y[a] - sy) * hinv;
-        yz = (float)(A.z[a] - sz) * hinv;
+        pair_frame(A, a, sx, sy, sz, yx, yy, yz, hinv);
       }
       M.py[lane] = make_float4(yx, yy, yz, hinv);
-      bool inside = true;
-      double dacc = 0.0;
+      bool inside = true;   // on the inner side of every face decided here
+      bool nearp = false;   // a face plane within TAU h: its side and edges are left to the fix-up
       int cntc = 0, cnt0 = 0, cnt1 = 0;  // stack heights (warp-uniform)
       __syncwarp();
       int kb = 0;
       for (int fi = 0; fi < nf; ++fi) {
         const float4 F = face[f0 + fi];
         const int ke = (int)(A.fvo[f0 + fi + 1] - l0);
-        const float r0s = F.w * hinv - (F.x * yx + F.y * yy + F.z * yz);
-        bool fin = r0s >= 0.f;
+        const float r0s = face_r0s(F, yx, yy, yz, hinv);
+        const bool fin = r0s >= 0.f;
         const float r0 = fabsf(r0s);
         bool inrange = active && r0 < 2.f;
         if (COUNT && active) wc.faces++;
         if (inrange && r0 < TAU) {
-          int c64 = 0;
-          dacc += face_fp64(A, f0 + fi, kb, ke, l0, a, sx, sy, sz, fin, c64);
-          if (COUNT) n64 += c64;
-          inrange = false;  // its edges are done
+          nearp = true;
+          inrange = false;
+        } else {
+          inside = inside && fin;
         }
-        inside = inside && fin;
         if (inrange) {
           // the face's bounding sphere wholly beyond the support: nothing to add
           const float4 Q = fsph[f0 + fi];
@@ -617,14 +628,20 @@ __global__ void __launch_bounds__(NW * 32, MINB) pair_integrals_mixed(BatchArgs 
       float comp;
       const float rs = take_row(S.col, lane, comp);
       if (active) {
-        const double f = (inside ? 1.0 : 0.0) + dacc + ((double)rs - (double)comp);
+        // a pair with a near-plane face gets its inside term from the fix-up
+        const double f = ((inside && !nearp) ? 1.0 : 0.0) + ((double)rs - (double)comp);
         if (A.frac) A.frac[p] = f;
         macc += A.m[a] * f;
       }
+      item_near = item_near || __any_sync(FULL, nearp);
       __syncwarp();
     }
     for (int o = 16; o > 0; o >>= 1) macc += __shfl_down_sync(FULL, macc, o);
-    if (lane == 0) A.partial[it] = macc;
+    if (lane == 0) {
+      A.partial[it] = macc;
+      // the item's near-plane faces: evaluated in FP64 by pair_near_fix
+      if (item_near) B.near[atomicAdd(&B.counters[14], 1ULL)] = g;
+    }
     __syncwarp();
   }
   if (!COUNT) return;
@@ -633,12 +650,11 @@ __global__ void __launch_bounds__(NW * 32, MINB) pair_integrals_mixed(BatchArgs 
     return v;
   };
   const unsigned long long terms = wsum((unsigned long long)wc.terms), faces = wsum((unsigned long long)wc.faces);
-  const unsigned long long edges = wsum((unsigned long long)wc.edges), fp64 = wsum((unsigned long long)n64);
+  const unsigned long long edges = wsum((unsigned long long)wc.edges);
   const unsigned long long split = wsum((unsigned long long)n_split);
   const unsigned long long outs = wsum((unsigned long long)n_out);
   if (lane == 0) {
     atomicAdd(&B.counters[1], terms);
-    atomicAdd(&B.counters[2], fp64);
     atomicAdd(&B.counters[8], faces);
     atomicAdd(&B.counters[9], edges);
     atomicAdd(&B.counters[10], 2ull * n_in);
@@ -646,6 +662,74 @@ __global__ void __launch_bounds__(NW * 32, MINB) pair_integrals_mixed(BatchArgs 
     atomicAdd(&B.counters[12], outs);
     atomicAdd(&B.counters[13], split);
   }
+}
+
+// Near-plane faces of the mixed build: a face whose plane passes within TAU h
+// of the particle is left out by pair_integrals_mixed (FP32 rounding could
+// give its plane inconsistent sides), which lists the items holding such
+// pairs.  One warp per listed item: each lane takes a pair, repeats the
+// kernel's face tests with the same rounding, evaluates every near-plane face
+// in FP64 (its side from the FP64 distance, its edges by the FP64 closed
+// form), and sets the pair's inside term -- which the kernel leaves out for
+// such pairs -- from the sides of all its faces.  The pair's f_ai and the
+// item's mass partial are corrected in a fixed order, so the result is
+// bit-reproducible.  Kept out of the integral kernel, whose registers the
+// FP64 path would otherwise inflate (a call, or its inlined body, at every
+// face of every pair).
+__global__ void __launch_bounds__(128) pair_near_fix(BatchArgs B) {
+  const int lane = threadIdx.x & 31;
+  const int64_t nlist = (int64_t)B.counters[14];
+  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  int n64 = 0;
+  for (int64_t q = (((int64_t)blockIdx.x * blockDim.x) + threadIdx.x) >> 5; q < nlist; q += nwarps) {
+    const int64_t g = B.near[q];
+    int jl = 0, jh = B.nsnap - 1;
+    while (jl < jh) {
+      const int jm = (jl + jh + 1) >> 1;
+      if (B.item_base[jm] <= g) jl = jm; else jh = jm - 1;
+    }
+    const SnapDesc& A = B.snaps[jl];
+    const int64_t it = g - B.item_base[jl];
+    const PairItem item = A.items[it];
+    const int64_t c = item.cell;
+    const float4* __restrict__ face = reinterpret_cast<const float4*>(A.face);
+    const int64_t f0 = A.cfo[c];
+    const int nf = (int)(A.cfo[c + 1] - f0);
+    const int64_t l0 = A.fvo[f0];
+    const double sx = A.site[3 * c], sy = A.site[3 * c + 1], sz = A.site[3 * c + 2];
+    double dsum = 0.0;
+    for (int64_t p0 = item.lo; p0 < item.lo + item.cnt; p0 += 32) {
+      const int64_t p = p0 + lane;
+      if (p >= item.lo + item.cnt) break;
+      const int32_t a = A.pair_idx[p];
+      float yx, yy, yz, hinv;
+      pair_frame(A, a, sx, sy, sz, yx, yy, yz, hinv);
+      bool inside = true, nearp = false;
+      double dacc = 0.0;
+      int kb = 0;
+      for (int fi = 0; fi < nf; ++fi) {
+        const int ke = (int)(A.fvo[f0 + fi + 1] - l0);
+        const float r0s = face_r0s(face[f0 + fi], yx, yy, yz, hinv);
+        bool fin = r0s >= 0.f;
+        const float r0 = fabsf(r0s);
+        if (r0 < 2.f && r0 < TAU) {
+          dacc += face_fp64(A, f0 + fi, kb, ke, l0, a, sx, sy, sz, fin, n64);
+          nearp = true;
+        }
+        inside = inside && fin;
+        kb = ke;
+      }
+      if (nearp) {
+        const double d = (inside ? 1.0 : 0.0) + dacc;
+        if (A.frac) A.frac[p] += d;
+        dsum += A.m[a] * d;
+      }
+    }
+    for (int o = 16; o > 0; o >>= 1) dsum += __shfl_down_sync(FULL, dsum, o);
+    if (lane == 0) A.partial[it] += dsum;
+  }
+  for (int o = 16; o > 0; o >>= 1) n64 += __shfl_down_sync(FULL, n64, o);
+  if (lane == 0 && n64) atomicAdd(&B.counters[2], (unsigned long long)n64);
 }
 
 template <int NW, int MINB, bool COUNT = false>
@@ -753,6 +837,7 @@ int integrals_upload(map_ctx* ctx, const SnapDesc* h_desc, const int64_t* h_ibas
 
 int integrals_enqueue(map_ctx* ctx, const BatchArgs& B, int variant, cudaStream_t s) {
   CUDA_TRY(cudaMemsetAsync(ctx->d_counters, 0, 4 * sizeof(unsigned long long), s));
+  CUDA_TRY(cudaMemsetAsync(ctx->d_counters + 14, 0, sizeof(unsigned long long), s));
   CUDA_TRY(cudaMemsetAsync(ctx->d_counters + 8, 0, 8 * sizeof(unsigned long long), s));
   const bool count = ctx->cfg.count_work != 0;
   if (ctx->cfg.precision == MAP_TABLE) {
@@ -769,6 +854,10 @@ int integrals_enqueue(map_ctx* ctx, const BatchArgs& B, int variant, cudaStream_
     MAP_TRY((launch<double, false, 4, 4, true>(ctx, B, s)));
   } else {
     MAP_TRY((launch<double, false, 4, 4>(ctx, B, s)));
+  }
+  if (ctx->cfg.precision == MAP_MIXED && B.total > 0) {
+    pair_near_fix<<<(unsigned)ctx->sm_count * 4, 128, 0, s>>>(B); ++ctx->launches;
+    CUDA_TRY(cudaGetLastError());
   }
   if (B.total_cells > 0) {
     cell_sums<<<nblk(B.total_cells, 256), 256, 0, s>>>(B.snaps, B.cell_base, B.nsnap, B.total_cells);
@@ -825,10 +914,12 @@ int integrals_run(map_ctx* ctx, const PreparedGrid* g, const map_particles* p, m
   int64_t* d_base;
   MAP_TRY(ensure_t(ctx, ctx->ws_misc[3], 1, &d_desc));
   MAP_TRY(ensure_t(ctx, ctx->ws_misc[4], 4, &d_base));
+  int64_t* near;
+  MAP_TRY(ensure_t(ctx, ctx->ws_near, ctx->n_items + 1, &near));
   const SnapDesc h = make_desc(ctx, g, p, out, ctx->pair_off, ctx->pair_idx, frac, 0);
   const int64_t ibase[2] = {0, ctx->n_items}, cbase[2] = {0, g->ncell};
   MAP_TRY(integrals_upload(ctx, &h, ibase, cbase, 1, d_desc, d_base, d_base + 2, s));
-  BatchArgs B{d_desc, d_base, d_base + 2, 1, ctx->n_items, g->ncell, ctx->d_counters};
+  BatchArgs B{d_desc, d_base, d_base + 2, 1, ctx->n_items, g->ncell, ctx->d_counters, near};
   if (ctx->cfg.autotune && ctx->cfg.precision == MAP_MIXED && !ctx->tune_done[MAP_MIXED])
     MAP_TRY(integrals_autotune(ctx, B, s));
   phase_begin(ctx, 2, s);

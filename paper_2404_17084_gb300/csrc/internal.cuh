@@ -150,6 +150,7 @@ struct map_ctx {
   DevBuf ws_vor[22];                   // grid construction: buckets, cell slots, CSR arrays
   DevBuf ws_inv[11];                   // particle-major copy of the pair list (inverse mapping, Eq. 4)
   DevBuf cub_tmp;
+  DevBuf ws_near;                      // items with a near-plane face (mixed build's FP64 fix-up)
   DevTree tree;
   int64_t node_cap0 = 0;  // > 0: octree node arrays start at this capacity (a context whose workspace is fixed)
   // results of the last mapping call
@@ -174,12 +175,16 @@ struct map_ctx {
   double* partial = nullptr;         // per item: its pairs' mass
   int64_t n_items = 0;
   // device counters: [0] status, [1] edge terms, [2] fp64 terms, [3] work queue,
-  // [4..5] scratch, [8] face tests, [9] edge records read, [10] inner-piece
-  // antiderivative evaluations, [11] middle-piece Gauss-Legendre intervals
+  // [4..7] scratch, [8] face tests, [9] edge records read, [10] inner-piece
+  // antiderivative evaluations, [11] middle-piece Gauss-Legendre intervals,
+  // [14] items with a near-plane face (mixed build)
   unsigned long long* d_counters = nullptr;
   double* d_total = nullptr;
   map_stats* h_stats = nullptr;  // pinned
-  cudaStream_t last_stream = nullptr;
+  cudaStream_t last_stream = nullptr;  // stream of the context's last call
+  bool has_last = false;               // a call has run (ord_ev marks its end)
+  cudaStream_t cur_stream = nullptr;   // stream of the call in progress: workspace is allocated and freed on it
+  cudaEvent_t ord_ev = nullptr;        // the end of the context's last call, on its stream
   int64_t* h_scratch = nullptr;  // pinned scratch for small readbacks
   int64_t launches = 0;          // kernels this context has launched (own kernels only)
   int64_t last_work[6] = {0, 0, 0, 0, 0, 0};  // work tally of the last mapping call (see map_get_work)
@@ -211,6 +216,29 @@ inline void phase_end(map_ctx* ctx, int k, cudaStream_t s) {
 }
 
 // ---------------------------------------------------------------- allocation
+// Every call of a context starts with MAP_ENTER on its stream: the stream is
+// ordered after the end of the context's previous call (an event, no host
+// wait) and becomes the context's last stream, so that the context's buffers
+// can be freed and allocated in stream order on it.
+// Workspace then comes from the stream-ordered allocator (dev_alloc /
+// dev_free on the current call's stream): growing or releasing a buffer never
+// waits for the device.
+int ctx_enter(map_ctx* ctx, cudaStream_t s);
+// Marks the end of a call on its stream (at every return of the entry
+// point): the next call of the context, on any stream, waits for this point.
+// An event outlives the caller's stream, which may be destroyed in between.
+struct CallScope {
+  map_ctx* ctx;
+  cudaStream_t s;
+  ~CallScope() {
+    if (ctx->ord_ev) cudaEventRecord(ctx->ord_ev, s);
+  }
+};
+#define MAP_ENTER(ctx, s)          \
+  MAP_TRY(ctx_enter((ctx), (s)));  \
+  CallScope call_scope_{(ctx), (s)}
+int dev_alloc(map_ctx* ctx, void** p, size_t bytes);
+void dev_free(map_ctx* ctx, void* p);
 int ctx_ensure(map_ctx* ctx, DevBuf& b, size_t bytes);
 int ctx_alloc_grid(map_ctx* ctx, PreparedGrid* g, void** p, size_t bytes);
 
@@ -260,7 +288,8 @@ struct BatchArgs {
   int nsnap;
   int64_t total;        // items
   int64_t total_cells;
-  unsigned long long* counters;  // [1] edge terms, [2] FP64 terms, [3] queue, [8..13] work tally
+  unsigned long long* counters;  // [1] edge terms, [2] FP64 terms, [3] queue, [8..13] work tally, [14] near-plane items
+  int64_t* near;                 // mixed build: queue positions of items with a near-plane face (capacity: total)
 };
 
 constexpr int N_VARIANTS = 3;  // launch shapes of the mixed pair-integral kernel (register caps 102, 128, 85)
@@ -288,6 +317,8 @@ int pairs_build(map_ctx* ctx, const PreparedGrid* g, cudaStream_t s, const PairB
 // Sorts the last call's lists (and f_ai) by particle index within each cell.
 int pairs_sort_lists(map_ctx* ctx, cudaStream_t s);
 int check_particles(map_ctx* ctx, const map_particles* p, bool need_m, bool need_h, cudaStream_t s);
+// map_particles_to_cells on a prepared grid (after ctx_enter on s)
+int map_run(map_ctx* ctx, const map_particles* p, PreparedGrid* g, map_outputs* out, cudaStream_t s);
 int integrals_run(map_ctx* ctx, const PreparedGrid* g, const map_particles* p, map_outputs* out, cudaStream_t s);
 SnapDesc make_desc(map_ctx* ctx, const PreparedGrid* g, const map_particles* p, const map_outputs* out,
                    const int64_t* pair_off, const int32_t* pair_idx, double* frac, int orig);

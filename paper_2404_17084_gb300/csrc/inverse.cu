@@ -260,9 +260,8 @@ int build_index(map_ctx* ctx, cudaStream_t s) {
   ctx->inv_order = order;
   ctx->inv_nlong = nlong;
   ctx->inv_ready = true;
-  // the copy reads the pair list, which a later map_get_pairs sorts in place
-  // on the mapping call's stream
-  if (s != ctx->last_stream) CUDA_TRY(cudaStreamSynchronize(s));
+  // the copy reads the pair list, which a later map_get_pairs sorts in place:
+  // that sort runs on this call's stream or one ordered after it (ctx_enter)
   return MAP_OK;
 }
 
@@ -274,8 +273,8 @@ extern "C" int map_cells_to_particles(map_ctx* ctx, const double* cell_value, do
   if (!ctx->pair_off || !ctx->pair_frac || n != ctx->last_npart) return MAP_EINVAL;
   if (ctx->n_pairs >= (int64_t(1) << 32) || ctx->last_ncell >= (int64_t(1) << 31)) return MAP_EINVAL;
   if (n == 0) return MAP_OK;
-  CUDA_TRY(cudaSetDevice(ctx->device));
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  MAP_ENTER(ctx, s);
   if (!ctx->inv_ready) MAP_TRY(build_index(ctx, s));
   const int64_t groups = (n + 31) / 32;
   const int64_t per_block = INV_THREADS / 32;

@@ -281,11 +281,11 @@ static int grow_nodes(map_ctx* ctx, int64_t need) {
     size_t nb = bytes + bytes / 2 + 4096;
     if (ctx->cfg.hbm_budget && ctx->bytes_in_use + nb > ctx->cfg.hbm_budget) return MAP_ENOMEM;
     void* np = nullptr;
-    if (cudaMalloc(&np, nb) != cudaSuccess) { cudaGetLastError(); return MAP_ENOMEM; }
+    MAP_TRY(dev_alloc(ctx, &np, nb));
     ctx->bytes_in_use += nb;
     if (b.p) {
-      CUDA_TRY(cudaMemcpy(np, b.p, b.cap, cudaMemcpyDeviceToDevice));
-      cudaFree(b.p);
+      CUDA_TRY(cudaMemcpyAsync(np, b.p, b.cap, cudaMemcpyDeviceToDevice, ctx->cur_stream));
+      dev_free(ctx, b.p);
       ctx->bytes_in_use -= b.cap;
     }
     b.p = np;

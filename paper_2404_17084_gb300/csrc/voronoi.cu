@@ -586,8 +586,8 @@ extern "C" int map_grid_build(map_ctx* ctx, const double* x, const double* y, co
                               double merge_tol, int* handle, int64_t* kept, int64_t* n_kept, void* stream) {
   if (!ctx || !x || !y || !z || n < 1 || n >= (int64_t(1) << 31) || lloyd < 0 || !handle) return MAP_EINVAL;
   if (!(merge_tol >= 0.0) || !std::isfinite(merge_tol)) return MAP_EINVAL;
-  CUDA_TRY(cudaSetDevice(ctx->device));
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  MAP_ENTER(ctx, s);
   map_particles chk{n, x, y, z, nullptr, nullptr};
   MAP_TRY(check_particles(ctx, &chk, false, false, s));  // finite, inside the cube
   // the sites, merged, in one of two ping-pong buffers (x block, y block, z block)

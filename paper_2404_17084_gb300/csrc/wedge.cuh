@@ -53,10 +53,11 @@
 // taking N R0/(R0^2+s^2) by 6-point Gauss-Legendre.  N vanishes at the poles
 // s = +-i R0 and tends to zero with (2-U)^5 at the support, so the integrand
 // keeps its relative accuracy where the kernel is small; its only
-// singularities are the branch points s = +-i c.  An interval that straddles
-// the foot s = 0 is split there, so that each part starts or ends level with
-// the branch points: unsplit, an interval of length 2 sqrt 3 at c = 1 loses
-// 1e-4 relative; split, the rule's truncation stays below ~5e-8 absolute.
+// singularities are the branch points s = +-i c.  An interval longer than c
+// that straddles the foot s = 0 is split there, so that each part starts or
+// ends level with the branch points: unsplit, an interval of length 2 sqrt 3
+// at c = 1 loses 1e-4 relative; split, the rule's truncation stays below
+// ~8e-8 absolute, and an interval no longer than c stays below ~6e-9 unsplit.
 #pragma once
 
 #include <cuda_runtime.h>
@@ -254,7 +255,9 @@ __device__ __forceinline__ float mid_gl<float>(float r0, float R0, float c2, flo
     const f2 pm = mul2(t5, add2(sp(1.f), U));
     const f2 num = fma2(sp(r0), pm, mul2(sp(-pr0), U));
     const f2 den = mul2(U, add2(sp(R02), s2));
-    const f2 q = f2{den.x > 0.f ? __fdividef(num.x, den.x) : 0.f, den.y > 0.f ? __fdividef(num.y, den.y) : 0.f};
+    // den = 0 only with R0 = 0 (and a node at the foot), where the panel's
+    // factor R0 makes the piece 0: a floor instead of a branch keeps q finite
+    const f2 q = f2{__fdividef(num.x, fmaxf(den.x, 1e-30f)), __fdividef(num.y, fmaxf(den.y, 1e-30f))};
     acc = fma2(sp(gw[k]), q, acc);
   }
   return R0 * half * (acc.x + acc.y);
@@ -273,8 +276,9 @@ __device__ __forceinline__ T piece_inner(T r0, T R0, T lo, T hi) {
   return (g1 - g0) * T(INV_4PI);
 }
 
-// Mixed build: a middle interval never straddles the foot s = 0 (the split
-// puts a breakpoint there), so every call is one Gauss-Legendre panel; kappa
+// Mixed build: a middle interval straddles the foot s = 0 only when it is no
+// longer than c (a longer one is split there), so every call is one
+// Gauss-Legendre panel; kappa
 // dPhi is evaluated unconditionally (kappa = 0 for r0 >= 1), keeping the
 // lanes of a warp on one path.
 template <typename T, bool MIXED>
@@ -303,9 +307,9 @@ __device__ __forceinline__ T piece_outer(T r0, T R0, T lo, T hi) {
 //   middle:             [x0, min(x1, -s1)] and [max(x0, s1), x1],
 //   inner:              [max(x0, -s1), min(x1, s1)],
 // with x0 = max(aa, -s2), x1 = min(ab, s2), each kept when non-empty.  For
-// c^2 >= 1 (s1 = 0) the middle pieces are the middle interval split at the
-// foot s = 0, so that each starts or ends level with the branch points of the
-// middle-piece integrand (FP32 only: in FP64 the interval stays whole).
+// c^2 >= 1 (s1 = 0) a middle interval longer than c is split at the foot
+// s = 0, so that each part starts or ends level with the branch points of
+// the middle-piece integrand (FP32 only: in FP64 the interval stays whole).
 // Every lane runs the same instructions.  The
 // breakpoints use the fast square root in FP32: E is smooth across u = 1 and
 // u = 2, so moving a breakpoint by an ulp changes K' only at third order.
@@ -355,9 +359,16 @@ __device__ __forceinline__ EdgeSplit<T> split_edge_flat(T r0, T R0, T aa, T ab, 
   P.pos = pos;
   P.x0 = aa > -P.s2 ? aa : -P.s2;
   P.x1 = ab < P.s2 ? ab : P.s2;
-  // the foot split serves the FP32 quadrature only; the FP64 closed form
-  // takes the middle interval whole
-  P.whole = sizeof(T) == 8 && !(c2 < T(1));
+  // the foot split serves the FP32 quadrature only, and only for a long
+  // interval: with the branch points at s = +-ic, a 6-node panel over
+  // [x0, x1] of length at most c keeps its truncation below ~6e-9 wherever
+  // the interval lies (the Bernstein ellipse of the centred, worst case has
+  // rho >= 2 + sqrt 5), under the split pieces' own ~8e-8; the FP64 closed
+  // form takes the middle interval whole
+  {
+    const T len = P.x1 - P.x0;
+    P.whole = !(c2 < T(1)) && (sizeof(T) == 8 || len * len <= c2);
+  }
   const T s1 = P.s1, s2 = P.s2, x0 = P.x0, x1 = P.x1;
   const bool v0 = (x1 < s1 ? x1 : s1) > (x0 > -s1 ? x0 : -s1);
   const bool v1 = ((P.whole || x1 < -s1) ? x1 : -s1) > x0;
