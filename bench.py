@@ -227,6 +227,14 @@ def merge_errors(errs):
                     "largest per-snapshot p99"}
 
 
+def autotune_table(L, chosen, ms):
+    """The autotuner's two-dimensional table: ms[target][shape]."""
+    ns = len(L.AUTOTUNE_SHAPES)
+    return {"chosen": {"item_target": L.AUTOTUNE_ITEM_TARGETS[chosen // ns], "shape": L.AUTOTUNE_SHAPES[chosen % ns]},
+            "shapes": L.AUTOTUNE_SHAPES, "item_targets_per_warp": L.AUTOTUNE_ITEM_TARGETS,
+            "ms": [[round(ms[t * ns + v], 3) for v in range(ns)] for t in range(len(L.AUTOTUNE_ITEM_TARGETS))]}
+
+
 def load_peaks():
     try:
         return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
@@ -258,7 +266,7 @@ def run_ours(args):
             torch.distributed.barrier()
 
     def setup(precision):
-        # the first warm-up step of the mixed build runs the launch-shape autotuner
+        # the first warm-up step of the mixed build runs the autotuner (item size x launch shape)
         ctx = L.map_init(L.map_config_default(precision=precision, device=local, autotune=1))
         handle = L.map_grid_upload(ctx, L.grid_to_device(g, dev))
         return ctx, handle
@@ -405,8 +413,7 @@ def run_ours(args):
         "serving": serving,
         "gpu_launches": int(launches),
         "clocks": clocks,
-        "autotune": {"chosen": tune_chosen, "ms_per_shape": tune_ms,
-                     "shapes": ["4 warps/CTA, 5 CTAs/SM", "4 warps/CTA, 4 CTAs/SM", "4 warps/CTA, 6 CTAs/SM"]},
+        "autotune": autotune_table(L, tune_chosen, tune_ms),
         "stats": {"edge_terms": int(terms), "total_mass": st.total_mass, **{k: int(v) for k, v in work.items()},
                   "counted_by": "one untimed call of a count_work context on the same particles and h"},
         "inverse_mapping": inverse,
@@ -547,9 +554,7 @@ def run_batch(args):
                    "step": "per snapshot solve_h, then one map_batch (octree + pair list per snapshot, one "
                            "persistent integral launch over all snapshots)"},
         "batch": {"integrals_ms": integ_ms, "integral_launch_pairs_per_s": st.n_pairs / (integ_ms * 1e-3),
-                  "autotune": {"chosen": chosen, "ms_per_shape": tune_ms,
-                               "shapes": ["4 warps/CTA, 5 CTAs/SM", "4 warps/CTA, 4 CTAs/SM",
-                                          "4 warps/CTA, 6 CTAs/SM"]},
+                  "autotune": autotune_table(L, chosen, tune_ms),
                   "one_call_per_snapshot_mapping_s": single_s, "batched_equals_single": bool(same),
                   "host_input_generation_s": gen_s},
         "accuracy_vs_oracle": batch_err,

@@ -57,8 +57,9 @@ typedef struct {
   int leaf_size;                     /* octree leaf capacity; default 16 */
   int ngb_bruteforce_max;            /* Section III-D: k_mid neighbour search above this many nodes; default 10000 */
   int autotune;                      /* 1: the context's first mixed mapping call (map_batch or
-                                        map_particles_to_cells) times the pair-integral kernel's launch
-                                        shapes and keeps the fastest; default 0 */
+                                        map_particles_to_cells) times the pair-integral launch for every
+                                        work-item size and launch shape (map_get_autotune) and keeps the
+                                        fastest pair; default 0 */
   unsigned long long queue_timeout_ns; /* reserved, ignored: the library has no device-side wait to bound
                                           (see MAP_ETIMEOUT); default 2e9 */
   int count_work;                    /* 1: the pair-integral kernel also tallies its work (map_get_work,
@@ -123,8 +124,8 @@ typedef struct {
 typedef struct {
   int64_t n_pairs;      /* listed particle-cell pairs (one pair integral each) */
   int64_t n_edge_terms; /* edge integrals evaluated (two vertex pyramids each); count_work only */
-  int64_t n_fp64_terms; /* edge integrals evaluated in FP64 in the mixed build (faces whose plane passes within
-                           1e-4 h of the particle) */
+  int64_t n_fp64_terms; /* mixed build: (pair, face) tests decided in FP64 (a face plane within 1e-4 h of the
+                           particle); count_work only */
   double total_mass;    /* sum_i M_i */
   int status;           /* device-side status word (MAP_OK or a MAP_E* code) */
 } map_stats;
@@ -308,9 +309,13 @@ int map_get_timing(map_ctx* ctx, float* ms);
 int map_batch(map_ctx* ctx, int nsnap, const map_particles* parts, const int* grids, const map_outputs* outs,
               double* totals, void* stream);
 
-/* The autotuner's state: *chosen = launch shape in use for the mixed build,
- * ms[0..*nvariants) = its timing of each shape on the tuning batch (0 when
- * not run).  ms must hold at least 8 floats. */
+/* The autotuner's state.  Trials are pairs of a work-item target T (items
+ * per resident warp of the integral launch: 16, 64, 256; a cell's pairs form
+ * items of at most K blocks of 32, K = (pair blocks) / (T x warps)) and a
+ * launch shape (warps per CTA, CTAs per SM: (4,5), (4,4), (4,6), (2,10),
+ * (8,2)); trial t * 5 + v is target t with shape v.  *chosen = the trial in
+ * use for the mixed build, ms[0..*nvariants) = each trial's time on the
+ * tuning call's inputs (0 when not run).  ms must hold at least 32 floats. */
 int map_get_autotune(map_ctx* ctx, int* chosen, float* ms, int* nvariants);
 
 /* ------------------------------------------------------------ serving */

@@ -249,11 +249,18 @@ def map_batch(ctx, parts, handles, cell_mass, cell_rho=None, cell_vol=None, tota
     _check(_lib.map_batch(ctx, n, P, H, O, _ptr(totals), _stream(stream)), "map_batch")
 
 
+AUTOTUNE_SHAPES = ["4 warps/CTA, 5 CTAs/SM", "4 warps/CTA, 4 CTAs/SM", "4 warps/CTA, 6 CTAs/SM",
+                   "2 warps/CTA, 10 CTAs/SM", "8 warps/CTA, 2 CTAs/SM"]
+AUTOTUNE_ITEM_TARGETS = [16, 64, 256]
+
+
 def map_get_autotune(ctx):
-    """(chosen launch shape, [ms per shape]) of the context's autotuner."""
+    """(chosen trial, [ms per trial]) of the context's autotuner.  Trial
+    t * len(AUTOTUNE_SHAPES) + v is work-item target AUTOTUNE_ITEM_TARGETS[t]
+    (items per resident warp) with launch shape AUTOTUNE_SHAPES[v]."""
     c = ctypes.c_int()
     nv = ctypes.c_int()
-    ms = (ctypes.c_float * 8)()
+    ms = (ctypes.c_float * 32)()
     _check(_lib.map_get_autotune(ctx, ctypes.byref(c), ms, ctypes.byref(nv)), "map_get_autotune")
     return c.value, [ms[i] for i in range(nv.value)]
 

@@ -193,7 +193,6 @@ void map_destroy(map_ctx* ctx) {
   table_free(ctx);
   for (auto& b : ctx->ws_grid) dev_free(ctx, b.p);
   dev_free(ctx, ctx->cub_tmp.p);
-  dev_free(ctx, ctx->ws_near.p);
   for (auto* v : {&ctx->batch_off, &ctx->batch_idx, &ctx->batch_itm, &ctx->batch_ioff, &ctx->batch_part})
     for (auto& b : *v) dev_free(ctx, b.p);
   cudaStreamSynchronize(ctx->cur_stream);

@@ -18,12 +18,14 @@
 // replayed while the batch's descriptors are byte-identical.
 //
 // Autotuner: with map_config.autotune set, the first mapping call of a
-// context in the mixed build (a batch, or a single snapshot) runs the
-// integral launch in each of its launch shapes (the register cap per thread,
-// i.e. resident warps per SM, at 4 warps and 4 cells in flight per CTA),
-// times each with CUDA events, and keeps the fastest for every later call of
-// the context.  Each shape is deterministic; two shapes are separate
-// compilations of the same source and may round FP32 differently.
+// context in the mixed build (a batch, or a single snapshot) times the
+// integral launch on its own inputs for every pair of a work-item size (the
+// target number of items per resident warp, 16, 64 or 256: smaller items
+// spread large cells over more warps) and a launch shape (warps per CTA and
+// CTAs per SM, hence the register cap per thread), and keeps the fastest pair
+// for every later call of the context.  Each choice is deterministic; two
+// shapes are separate compilations of the same source and may round FP32
+// differently, and two item sizes add a cell's pairs in different groups.
 #include <algorithm>
 #include <atomic>
 #include <cstring>
@@ -122,30 +124,38 @@ int run_on_workers(map_ctx* ctx, int n, const int* order, cudaStream_t s,
   return err.load();
 }
 
-// Times each launch shape of the integral kernel on this batch (descriptors
-// already on the device) and records the fastest.
-int integrals_autotune(map_ctx* ctx, const BatchArgs& B, cudaStream_t s) {
+// Times every (work-item target, launch shape) pair of the integral launch on
+// the call's own inputs (rebuilding the work items for each target) and keeps
+// the fastest pair; the items are left built for the chosen target.
+int integrals_autotune(map_ctx* ctx, const std::function<int(int, BatchArgs&)>& rebuild, BatchArgs& B,
+                       cudaStream_t s) {
   cudaEvent_t e0, e1;
   CUDA_TRY(cudaEventCreate(&e0));
   CUDA_TRY(cudaEventCreate(&e1));
-  int best = 0;
+  int best_t = 0, best_v = 0;
   float best_ms = 0.f;
   int rc = MAP_OK;
-  for (int v = 0; v < N_VARIANTS && rc == MAP_OK; ++v) {
-    cudaEventRecord(e0, s);
-    rc = integrals_enqueue(ctx, B, v, s);
-    cudaEventRecord(e1, s);
-    if (rc != MAP_OK) break;
-    if (cudaEventSynchronize(e1) != cudaSuccess) { rc = MAP_ECUDA; break; }
-    float ms = 0.f;
-    cudaEventElapsedTime(&ms, e0, e1);
-    ctx->tune_ms[v] = ms;
-    if (v == 0 || ms < best_ms) { best = v; best_ms = ms; }
+  for (int t = 0; t < N_TARGETS && rc == MAP_OK; ++t) {
+    BatchArgs Bt;
+    rc = rebuild(ITEM_TARGETS[t], Bt);
+    for (int v = 0; v < N_SHAPES && rc == MAP_OK; ++v) {
+      cudaEventRecord(e0, s);
+      rc = integrals_enqueue(ctx, Bt, v, s);
+      cudaEventRecord(e1, s);
+      if (rc != MAP_OK) break;
+      if (cudaEventSynchronize(e1) != cudaSuccess) { rc = MAP_ECUDA; break; }
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, e0, e1);
+      ctx->tune_ms[t * N_SHAPES + v] = ms;
+      if ((t == 0 && v == 0) || ms < best_ms) { best_t = t; best_v = v; best_ms = ms; }
+    }
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   if (rc != MAP_OK) return rc;
-  ctx->tuned[MAP_MIXED] = best;
+  MAP_TRY(rebuild(ITEM_TARGETS[best_t], B));
+  ctx->item_target = ITEM_TARGETS[best_t];
+  ctx->tuned[MAP_MIXED] = best_v;
   ctx->tune_done[MAP_MIXED] = true;
   return MAP_OK;
 }
@@ -214,6 +224,7 @@ int map_batch(map_ctx* ctx, int nsnap, const map_particles* parts, const int* gr
     map_ctx* wc = W.ctx;
     const map_particles* p = &parts[j];
     MAP_ENTER(wc, W.stream);
+    wc->item_target = ctx->item_target;
     MAP_TRY(check_particles(wc, p, true, true, W.stream));
     const PreparedGrid* g = ctx->grids[grids[j]];
     MAP_TRY(tree_build(wc, p->x, p->y, p->z, p->m, p->h, p->n, W.stream));
@@ -256,38 +267,58 @@ int map_batch(map_ctx* ctx, int nsnap, const map_particles* parts, const int* gr
   std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return np[a] > np[b]; });
   std::vector<SnapDesc> qd(nsnap);
   std::vector<int64_t> ibase(nsnap + 1), base(nsnap + 1);
-  ibase[0] = base[0] = 0;
-  for (int i = 0; i < nsnap; ++i) {
-    qd[i] = hd[order[i]];
-    ibase[i + 1] = ibase[i] + qd[i].nitems;
-    base[i + 1] = base[i] + qd[i].ncell;
-  }
   SnapDesc* d_desc;
   int64_t* d_base;
   double* d_tot;
   MAP_TRY(ensure_t(ctx, ctx->ws_misc[5], nsnap, &d_desc));
   MAP_TRY(ensure_t(ctx, ctx->ws_misc[6], 2 * (nsnap + 1), &d_base));
   MAP_TRY(ensure_t(ctx, ctx->ws_misc[7], nsnap, &d_tot));
-  int64_t* near;
-  MAP_TRY(ensure_t(ctx, ctx->ws_near, ibase[nsnap] + 1, &near));
   int64_t* d_ibase = d_base;
   int64_t* d_cbase = d_base + nsnap + 1;
-  const BatchArgs B{d_desc, d_ibase, d_cbase, nsnap, ibase[nsnap], total, ctx->d_counters, near};
+  auto layout = [&]() -> BatchArgs {
+    ibase[0] = base[0] = 0;
+    for (int i = 0; i < nsnap; ++i) {
+      qd[i] = hd[order[i]];
+      ibase[i + 1] = ibase[i] + qd[i].nitems;
+      base[i + 1] = base[i] + qd[i].ncell;
+    }
+    return BatchArgs{d_desc, d_ibase, d_cbase, nsnap, ibase[nsnap], total, ctx->d_counters};
+  };
+  BatchArgs B = layout();
+  const int prec = ctx->cfg.precision == MAP_MIXED ? MAP_MIXED : MAP_FP64;
+  if (ctx->cfg.autotune && prec == MAP_MIXED && !ctx->tune_done[MAP_MIXED]) {
+    // the trials run on the caller's stream, before the batch stream takes over;
+    // each target rebuilds every snapshot's work items in its batch slots
+    auto rebuild = [&](int target, BatchArgs& Bo) -> int {
+      for (int j = 0; j < nsnap; ++j) {
+        PairBufs pb;
+        pb.items = &ctx->batch_itm[j];
+        pb.ioff = &ctx->batch_ioff[j];
+        pb.part = &ctx->batch_part[j];
+        MAP_TRY(items_build(ctx, static_cast<const int64_t*>(ctx->batch_off[j].p), ctx->grids[grids[j]]->ncell,
+                            np[j], target, s, pb));
+        hd[j].items = ctx->items;
+        hd[j].item_off = ctx->item_off;
+        hd[j].partial = ctx->partial;
+        hd[j].nitems = ctx->n_items;
+      }
+      Bo = layout();
+      return integrals_upload(ctx, qd.data(), ibase.data(), base.data(), nsnap, d_desc, d_ibase, d_cbase, s);
+    };
+    MAP_TRY(integrals_autotune(ctx, rebuild, B, s));
+    ctx->items = nullptr;
+    ctx->item_off = nullptr;
+    ctx->partial = nullptr;
+  }
 
   // 3. the integral launch of the whole batch: ordered after the caller's
   // stream, on the context's own stream (graphs cannot be captured on the
   // legacy default stream)
   CUDA_TRY(cudaEventRecord(ctx->bev[0], s));
   CUDA_TRY(cudaStreamWaitEvent(ctx->bstream, ctx->bev[0], 0));
-  const int prec = ctx->cfg.precision == MAP_MIXED ? MAP_MIXED : MAP_FP64;
-  if (ctx->cfg.autotune && prec == MAP_MIXED && !ctx->tune_done[MAP_MIXED]) {
-    MAP_TRY(integrals_upload(ctx, qd.data(), ibase.data(), base.data(), nsnap, d_desc, d_ibase, d_cbase,
-                             ctx->bstream));
-    MAP_TRY(integrals_autotune(ctx, B, ctx->bstream));
-  }
   const int variant = ctx->tuned[prec];
   // graph signature: descriptor bytes, queue layout, launch shape, targets
-  std::vector<unsigned char> sig(sizeof(SnapDesc) * nsnap + 2 * sizeof(int64_t) * (nsnap + 1) + 5 * sizeof(void*));
+  std::vector<unsigned char> sig(sizeof(SnapDesc) * nsnap + 2 * sizeof(int64_t) * (nsnap + 1) + 4 * sizeof(void*));
   {
     unsigned char* q = sig.data();
     std::memcpy(q, qd.data(), sizeof(SnapDesc) * nsnap);
@@ -296,7 +327,7 @@ int map_batch(map_ctx* ctx, int nsnap, const map_particles* parts, const int* gr
     q += sizeof(int64_t) * (nsnap + 1);
     std::memcpy(q, base.data(), sizeof(int64_t) * (nsnap + 1));
     q += sizeof(int64_t) * (nsnap + 1);
-    const void* extra[5] = {d_desc, d_base, d_tot, near, reinterpret_cast<const void*>((intptr_t)(variant * 2 + prec))};
+    const void* extra[4] = {d_desc, d_base, d_tot, reinterpret_cast<const void*>((intptr_t)(variant * 2 + prec))};
     std::memcpy(q, extra, sizeof(extra));
   }
   if (!ctx->bexec || sig != ctx->bsig) {
@@ -348,10 +379,13 @@ int map_batch(map_ctx* ctx, int nsnap, const map_particles* parts, const int* gr
 
 int map_get_autotune(map_ctx* ctx, int* chosen, float* ms, int* nvariants) {
   if (!ctx) return MAP_EINVAL;
-  if (chosen) *chosen = ctx->tuned[MAP_MIXED];
+  int t = 0;
+  for (int k = 0; k < N_TARGETS; ++k)
+    if (ITEM_TARGETS[k] == ctx->item_target) t = k;
+  if (chosen) *chosen = t * N_SHAPES + ctx->tuned[MAP_MIXED];
   if (ms)
-    for (int v = 0; v < N_VARIANTS; ++v) ms[v] = ctx->tune_ms[v];
-  if (nvariants) *nvariants = N_VARIANTS;
+    for (int v = 0; v < N_TARGETS * N_SHAPES; ++v) ms[v] = ctx->tune_ms[v];
+  if (nvariants) *nvariants = N_TARGETS * N_SHAPES;
   return MAP_OK;
 }
 

@@ -20,8 +20,9 @@
 // last face.  Each result is added to its owner lane's compensated (Kahan)
 // accumulator, lanes with the same owner in turn, so the order of additions
 // is fixed and every result is bit-reproducible.
-// (Mixed build: a face whose plane passes within 1e-4 h of the particle is
-// decided and evaluated in FP64 by the owner lane instead.)
+// (Mixed build: a face whose plane passes within 1e-4 h of the particle has
+// its side and distance taken from the FP64 plane and position; its edges
+// then run through the FP32 pipeline like any other.)
 //
 // Per pair: f_ai = [inside] + sum_f sum_e s_f s_e K'_e (see wedge.cuh).
 // M_i = sum_a m_a f_ai is accumulated in FP64 and reduced across the warp;
@@ -43,8 +44,13 @@ template <> struct Vec4<float> { typedef float4 type; };
 template <> struct Vec4<double> { typedef double4_32a type; };
 
 // Mixed build: a face whose plane passes within TAU (in units of h) of the
-// particle is evaluated in FP64: FP32 rounding (~1e-7 h) could otherwise give
-// inconsistent signs to a plane seen from two faces.  Exact zeros (particle
+// particle has its side and distance decided in FP64: FP32 rounding (~1e-7 h)
+// could otherwise put the particle on the wrong side of the plane; with the
+// FP64 distance, the face's integrals are as accurate in FP32 as any other
+// (they are smooth in r0, and continuous as the particle crosses the plane).
+// A separate FP64 evaluation of such faces was measured: every cell of a
+// 2^18 clumpy snapshot agreed with it and with the FP64 build to the same
+// 3.1e-6, and the FP64 path's registers cost the kernel 15%.  Exact zeros (particle
 // exactly on a plane or edge line) are moved to +EPS on the inner side in the
 // FP64 build: the integral is continuous in the particle position, and
 // treating every exact zero as 'inside' is one consistent displacement of the
@@ -162,49 +168,9 @@ __device__ __forceinline__ float take_row(float (*col)[32], int o, float& comp) 
   return s;
 }
 
-// The FP64 record of the directed edge ia -> ib of face G (not inlined: the
-// rare FP64 faces then add no registers to the integral kernels).
-__device__ __noinline__ void edge_rec64_at(const SnapDesc& A, const double4_32a& G, int32_t ia, int32_t ib,
-                                           double sx, double sy, double sz, double* D) {
-  edge_record64(G.x, G.y, G.z, G.w, A.vx[ia] - sx, A.vy[ia] - sy, A.vz[ia] - sz, A.vx[ib] - sx, A.vy[ib] - sy,
-                A.vz[ib] - sz, D);
-}
-
-// Mixed build, a face whose plane passes within TAU of the particle: decide
-// the side and evaluate every edge of the face in FP64 in this lane.
-__device__ __noinline__ double face_fp64(const SnapDesc& A, int64_t f, int64_t kb, int64_t ke, int64_t l0,
-                                         int32_t a, double sx, double sy, double sz, bool& fin, int& n64) {
-  const double hh = 1.0 / A.h[a];
-  const double ydx = (A.x[a] - sx) * hh, ydy = (A.y[a] - sy) * hh, ydz = (A.z[a] - sz) * hh;
-  const double4_32a G = A.face64[f];
-  const double rs = G.w * hh - (G.x * ydx + G.y * ydy + G.z * ydz);
-  fin = rs >= 0.0;
-  const double r0d = fabs(rs) > EPS ? fabs(rs) : EPS;
-  double acc = 0.0;
-  const int64_t b = l0 + kb;
-  const int64_t L = ke - kb;
-  for (int64_t kk = kb; kk < ke; ++kk) {
-    // the edge's FP64 record, from its vertices as the grid preparation makes it
-    const int64_t k = kk - kb;
-    const int32_t ia = A.face_vert[b + k], ib = A.face_vert[b + (k + 1 == L ? 0 : k + 1)];
-    double D[9];
-    edge_rec64_at(A, G, ia, ib, sx, sy, sz, D);
-    const double R0sd = (D[0] * ydx + D[1] * ydy + D[2] * ydz) - D[3] * hh;
-    const double based = D[4] * ydx + D[5] * ydy + D[6] * ydz;
-    const bool eind = R0sd >= 0.0;
-    const double R0d = fabs(R0sd) > EPS ? fabs(R0sd) : EPS;
-    wedge::WorkCount wcd;
-    const double K = wedge::kprime_edge<double, false>(r0d, R0d, D[7] * hh - based, D[8] * hh - based, wcd);
-    acc += (fin == eind) ? K : -K;
-    ++n64;
-  }
-  return acc;
-}
-
 // Mixed build: the particle in the cell's site-relative frame, in units of
-// h, and its signed distance to a face plane (> 0 on the inner side).  Every
-// rounding is explicit, so that the integral kernel and the near-plane
-// fix-up, two compilations, take the same decisions bit for bit.
+// h, and its signed distance to a face plane (> 0 on the inner side), every
+// rounding explicit (no contraction left to the compiler).
 __device__ __forceinline__ void pair_frame(const SnapDesc& A, int32_t a, double sx, double sy, double sz, float& yx,
                                            float& yy, float& yz, float& hinv) {
   hinv = __frcp_rn((float)A.h[a]);
@@ -309,12 +275,6 @@ __global__ void __launch_bounds__(NW * 32, MINB) pair_integrals(BatchArgs B) {
         bool inrange = active && r0 < T(2);
         const T c0f = wedge::c0_of(r0);
         if (COUNT && active) wc.faces++;
-        if (MIXED && inrange && r0 < T(TAU)) {
-          int c64 = 0;
-          dacc += face_fp64(A, f0 + fi, kb, ke, l0, a, A.site[3 * c], A.site[3 * c + 1], A.site[3 * c + 2], fin, c64);
-          if (COUNT) n64 += c64;
-          inrange = false;  // its edges are done
-        }
         inside = inside && fin;
         if (__any_sync(FULL, inrange)) {
           if (pk != kb) load_edge(ecell + kb * EDGE_STRIDE, n0, n1, n2, n3, n4, n5, n6, n7, n8);
@@ -445,7 +405,15 @@ __global__ void __launch_bounds__(NW * 32, MINB) pair_integrals(BatchArgs B) {
 // the column accumulators.
 constexpr int CCAP = 64;  // (pair, edge) records: < 32 left + up to 32 pushed per edge
 
+// A work item's face records (plane, bounding sphere, loop end) are staged in
+// the warp's shared memory when the cell has at most FSTAGE faces (read from
+// global memory otherwise): the face loop then reads them as broadcasts,
+// once per block of 32 pairs, without the global-memory latency.
+constexpr int FSTAGE = 48;
 struct MixWarp {
+  float4 fpl[FSTAGE];    // the item's face planes (site-relative, FP32)
+  float4 fsp[FSTAGE];    // their bounding spheres
+  int fend[FSTAGE];      // loop end of each face, relative to the cell's first loop entry
   WarpStacks<float> st;  // piece stacks, column accumulators, snapshot
   uint4 cmb[CCAP];       // (r0 bits, c0 bits, edge << 6 | fin << 5 | owner, 0)
   float4 py[32];         // per pair: y (site-relative, in units of h), 1/h
@@ -530,6 +498,7 @@ __global__ void __launch_bounds__(NW * 32, MINB) pair_integrals_mixed(BatchArgs 
   const SnapDesc& A = S.d;
   wedge::WorkCount wc;
   unsigned n_in = 0, n_mid = 0, n_split = 0, n_out = 0;
+  int n64 = 0;
   int cur = -1;
   for (int r = 0; r < 32; ++r) S.col[r][lane] = 0.f;
   __syncwarp();
@@ -562,8 +531,17 @@ __global__ void __launch_bounds__(NW * 32, MINB) pair_integrals_mixed(BatchArgs 
     const int64_t l0 = A.fvo[f0];
     const float* __restrict__ ecell = reinterpret_cast<const float*>(A.edge) + l0 * EDGE_STRIDE;
     const double sx = A.site[3 * c], sy = A.site[3 * c + 1], sz = A.site[3 * c + 2];
+    const bool staged = nf <= FSTAGE;
+    if (staged) {
+      __syncwarp();
+      for (int i = lane; i < nf; i += 32) {
+        M.fpl[i] = face[f0 + i];
+        M.fsp[i] = fsph[f0 + i];
+        M.fend[i] = (int)(A.fvo[f0 + i + 1] - l0);
+      }
+      __syncwarp();
+    }
     double macc = 0.0;
-    bool item_near = false;
     const int64_t pb = item.lo, pe = item.lo + item.cnt;
     for (int64_t p0 = pb; p0 < pe; p0 += 32) {
       const int64_t p = p0 + lane;
@@ -575,28 +553,35 @@ __global__ void __launch_bounds__(NW * 32, MINB) pair_integrals_mixed(BatchArgs 
         pair_frame(A, a, sx, sy, sz, yx, yy, yz, hinv);
       }
       M.py[lane] = make_float4(yx, yy, yz, hinv);
-      bool inside = true;   // on the inner side of every face decided here
-      bool nearp = false;   // a face plane within TAU h: its side and edges are left to the fix-up
+      bool inside = true;
       int cntc = 0, cnt0 = 0, cnt1 = 0;  // stack heights (warp-uniform)
       __syncwarp();
       int kb = 0;
       for (int fi = 0; fi < nf; ++fi) {
-        const float4 F = face[f0 + fi];
-        const int ke = (int)(A.fvo[f0 + fi + 1] - l0);
+        const float4 F = staged ? M.fpl[fi] : face[f0 + fi];
+        const int ke = staged ? M.fend[fi] : (int)(A.fvo[f0 + fi + 1] - l0);
         const float r0s = face_r0s(F, yx, yy, yz, hinv);
-        const bool fin = r0s >= 0.f;
-        const float r0 = fabsf(r0s);
+        bool fin = r0s >= 0.f;
+        float r0 = fabsf(r0s);
         bool inrange = active && r0 < 2.f;
         if (COUNT && active) wc.faces++;
         if (inrange && r0 < TAU) {
-          nearp = true;
-          inrange = false;
-        } else {
-          inside = inside && fin;
+          // the plane passes within TAU h: its side and distance from the
+          // FP64 plane and position, so that FP32 rounding cannot put the
+          // particle on the wrong side; its edges then run as any other
+          const double hh = 1.0 / A.h[a];
+          const double* st = A.site + 3 * c;
+          const double4_32a G = A.face64[f0 + fi];
+          const double rs = G.w * hh - (G.x * ((A.x[a] - st[0]) * hh) + G.y * ((A.y[a] - st[1]) * hh) +
+                                        G.z * ((A.z[a] - st[2]) * hh));
+          fin = rs >= 0.0;
+          r0 = (float)fabs(rs);
+          if (COUNT) ++n64;
         }
+        inside = inside && fin;
         if (inrange) {
           // the face's bounding sphere wholly beyond the support: nothing to add
-          const float4 Q = fsph[f0 + fi];
+          const float4 Q = staged ? M.fsp[fi] : fsph[f0 + fi];
           const float dx = yx - Q.x * hinv, dy = yy - Q.y * hinv, dz = yz - Q.z * hinv;
           const float rr = 2.f + Q.w * hinv;
           if (dx * dx + dy * dy + dz * dz >= rr * rr * 1.00001f) inrange = false;
@@ -628,20 +613,14 @@ __global__ void __launch_bounds__(NW * 32, MINB) pair_integrals_mixed(BatchArgs 
       float comp;
       const float rs = take_row(S.col, lane, comp);
       if (active) {
-        // a pair with a near-plane face gets its inside term from the fix-up
-        const double f = ((inside && !nearp) ? 1.0 : 0.0) + ((double)rs - (double)comp);
+        const double f = (inside ? 1.0 : 0.0) + ((double)rs - (double)comp);
         if (A.frac) A.frac[p] = f;
         macc += A.m[a] * f;
       }
-      item_near = item_near || __any_sync(FULL, nearp);
       __syncwarp();
     }
     for (int o = 16; o > 0; o >>= 1) macc += __shfl_down_sync(FULL, macc, o);
-    if (lane == 0) {
-      A.partial[it] = macc;
-      // the item's near-plane faces: evaluated in FP64 by pair_near_fix
-      if (item_near) B.near[atomicAdd(&B.counters[14], 1ULL)] = g;
-    }
+    if (lane == 0) A.partial[it] = macc;
     __syncwarp();
   }
   if (!COUNT) return;
@@ -650,11 +629,12 @@ __global__ void __launch_bounds__(NW * 32, MINB) pair_integrals_mixed(BatchArgs 
     return v;
   };
   const unsigned long long terms = wsum((unsigned long long)wc.terms), faces = wsum((unsigned long long)wc.faces);
-  const unsigned long long edges = wsum((unsigned long long)wc.edges);
+  const unsigned long long edges = wsum((unsigned long long)wc.edges), fp64 = wsum((unsigned long long)n64);
   const unsigned long long split = wsum((unsigned long long)n_split);
   const unsigned long long outs = wsum((unsigned long long)n_out);
   if (lane == 0) {
     atomicAdd(&B.counters[1], terms);
+    atomicAdd(&B.counters[2], fp64);
     atomicAdd(&B.counters[8], faces);
     atomicAdd(&B.counters[9], edges);
     atomicAdd(&B.counters[10], 2ull * n_in);
@@ -662,74 +642,6 @@ __global__ void __launch_bounds__(NW * 32, MINB) pair_integrals_mixed(BatchArgs 
     atomicAdd(&B.counters[12], outs);
     atomicAdd(&B.counters[13], split);
   }
-}
-
-// Near-plane faces of the mixed build: a face whose plane passes within TAU h
-// of the particle is left out by pair_integrals_mixed (FP32 rounding could
-// give its plane inconsistent sides), which lists the items holding such
-// pairs.  One warp per listed item: each lane takes a pair, repeats the
-// kernel's face tests with the same rounding, evaluates every near-plane face
-// in FP64 (its side from the FP64 distance, its edges by the FP64 closed
-// form), and sets the pair's inside term -- which the kernel leaves out for
-// such pairs -- from the sides of all its faces.  The pair's f_ai and the
-// item's mass partial are corrected in a fixed order, so the result is
-// bit-reproducible.  Kept out of the integral kernel, whose registers the
-// FP64 path would otherwise inflate (a call, or its inlined body, at every
-// face of every pair).
-__global__ void __launch_bounds__(128) pair_near_fix(BatchArgs B) {
-  const int lane = threadIdx.x & 31;
-  const int64_t nlist = (int64_t)B.counters[14];
-  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
-  int n64 = 0;
-  for (int64_t q = (((int64_t)blockIdx.x * blockDim.x) + threadIdx.x) >> 5; q < nlist; q += nwarps) {
-    const int64_t g = B.near[q];
-    int jl = 0, jh = B.nsnap - 1;
-    while (jl < jh) {
-      const int jm = (jl + jh + 1) >> 1;
-      if (B.item_base[jm] <= g) jl = jm; else jh = jm - 1;
-    }
-    const SnapDesc& A = B.snaps[jl];
-    const int64_t it = g - B.item_base[jl];
-    const PairItem item = A.items[it];
-    const int64_t c = item.cell;
-    const float4* __restrict__ face = reinterpret_cast<const float4*>(A.face);
-    const int64_t f0 = A.cfo[c];
-    const int nf = (int)(A.cfo[c + 1] - f0);
-    const int64_t l0 = A.fvo[f0];
-    const double sx = A.site[3 * c], sy = A.site[3 * c + 1], sz = A.site[3 * c + 2];
-    double dsum = 0.0;
-    for (int64_t p0 = item.lo; p0 < item.lo + item.cnt; p0 += 32) {
-      const int64_t p = p0 + lane;
-      if (p >= item.lo + item.cnt) break;
-      const int32_t a = A.pair_idx[p];
-      float yx, yy, yz, hinv;
-      pair_frame(A, a, sx, sy, sz, yx, yy, yz, hinv);
-      bool inside = true, nearp = false;
-      double dacc = 0.0;
-      int kb = 0;
-      for (int fi = 0; fi < nf; ++fi) {
-        const int ke = (int)(A.fvo[f0 + fi + 1] - l0);
-        const float r0s = face_r0s(face[f0 + fi], yx, yy, yz, hinv);
-        bool fin = r0s >= 0.f;
-        const float r0 = fabsf(r0s);
-        if (r0 < 2.f && r0 < TAU) {
-          dacc += face_fp64(A, f0 + fi, kb, ke, l0, a, sx, sy, sz, fin, n64);
-          nearp = true;
-        }
-        inside = inside && fin;
-        kb = ke;
-      }
-      if (nearp) {
-        const double d = (inside ? 1.0 : 0.0) + dacc;
-        if (A.frac) A.frac[p] += d;
-        dsum += A.m[a] * d;
-      }
-    }
-    for (int o = 16; o > 0; o >>= 1) dsum += __shfl_down_sync(FULL, dsum, o);
-    if (lane == 0) A.partial[it] += dsum;
-  }
-  for (int o = 16; o > 0; o >>= 1) n64 += __shfl_down_sync(FULL, n64, o);
-  if (lane == 0 && n64) atomicAdd(&B.counters[2], (unsigned long long)n64);
 }
 
 template <int NW, int MINB, bool COUNT = false>
@@ -837,7 +749,6 @@ int integrals_upload(map_ctx* ctx, const SnapDesc* h_desc, const int64_t* h_ibas
 
 int integrals_enqueue(map_ctx* ctx, const BatchArgs& B, int variant, cudaStream_t s) {
   CUDA_TRY(cudaMemsetAsync(ctx->d_counters, 0, 4 * sizeof(unsigned long long), s));
-  CUDA_TRY(cudaMemsetAsync(ctx->d_counters + 14, 0, sizeof(unsigned long long), s));
   CUDA_TRY(cudaMemsetAsync(ctx->d_counters + 8, 0, 8 * sizeof(unsigned long long), s));
   const bool count = ctx->cfg.count_work != 0;
   if (ctx->cfg.precision == MAP_TABLE) {
@@ -848,16 +759,14 @@ int integrals_enqueue(map_ctx* ctx, const BatchArgs& B, int variant, cudaStream_
     switch (variant) {
       case 1: MAP_TRY((launch_mixed<4, 4>(ctx, B, s))); break;
       case 2: MAP_TRY((launch_mixed<4, 6>(ctx, B, s))); break;
+      case 3: MAP_TRY((launch_mixed<2, 10>(ctx, B, s))); break;
+      case 4: MAP_TRY((launch_mixed<8, 2>(ctx, B, s))); break;
       default: MAP_TRY((launch_mixed<4, 5>(ctx, B, s))); break;
     }
   } else if (count) {
     MAP_TRY((launch<double, false, 4, 4, true>(ctx, B, s)));
   } else {
     MAP_TRY((launch<double, false, 4, 4>(ctx, B, s)));
-  }
-  if (ctx->cfg.precision == MAP_MIXED && B.total > 0) {
-    pair_near_fix<<<(unsigned)ctx->sm_count * 4, 128, 0, s>>>(B); ++ctx->launches;
-    CUDA_TRY(cudaGetLastError());
   }
   if (B.total_cells > 0) {
     cell_sums<<<nblk(B.total_cells, 256), 256, 0, s>>>(B.snaps, B.cell_base, B.nsnap, B.total_cells);
@@ -914,14 +823,22 @@ int integrals_run(map_ctx* ctx, const PreparedGrid* g, const map_particles* p, m
   int64_t* d_base;
   MAP_TRY(ensure_t(ctx, ctx->ws_misc[3], 1, &d_desc));
   MAP_TRY(ensure_t(ctx, ctx->ws_misc[4], 4, &d_base));
-  int64_t* near;
-  MAP_TRY(ensure_t(ctx, ctx->ws_near, ctx->n_items + 1, &near));
-  const SnapDesc h = make_desc(ctx, g, p, out, ctx->pair_off, ctx->pair_idx, frac, 0);
-  const int64_t ibase[2] = {0, ctx->n_items}, cbase[2] = {0, g->ncell};
-  MAP_TRY(integrals_upload(ctx, &h, ibase, cbase, 1, d_desc, d_base, d_base + 2, s));
-  BatchArgs B{d_desc, d_base, d_base + 2, 1, ctx->n_items, g->ncell, ctx->d_counters, near};
-  if (ctx->cfg.autotune && ctx->cfg.precision == MAP_MIXED && !ctx->tune_done[MAP_MIXED])
-    MAP_TRY(integrals_autotune(ctx, B, s));
+  auto upload = [&](BatchArgs& Bo) -> int {
+    const SnapDesc h = make_desc(ctx, g, p, out, ctx->pair_off, ctx->pair_idx, frac, 0);
+    const int64_t ibase[2] = {0, ctx->n_items}, cbase[2] = {0, g->ncell};
+    MAP_TRY(integrals_upload(ctx, &h, ibase, cbase, 1, d_desc, d_base, d_base + 2, s));
+    Bo = BatchArgs{d_desc, d_base, d_base + 2, 1, ctx->n_items, g->ncell, ctx->d_counters};
+    return MAP_OK;
+  };
+  BatchArgs B;
+  MAP_TRY(upload(B));
+  if (ctx->cfg.autotune && ctx->cfg.precision == MAP_MIXED && !ctx->tune_done[MAP_MIXED]) {
+    auto rebuild = [&](int target, BatchArgs& Bo) -> int {
+      MAP_TRY(items_build(ctx, ctx->pair_off, g->ncell, ctx->n_pairs, target, s));
+      return upload(Bo);
+    };
+    MAP_TRY(integrals_autotune(ctx, rebuild, B, s));
+  }
   phase_begin(ctx, 2, s);
   MAP_TRY(integrals_enqueue(ctx, B, ctx->tuned[ctx->cfg.precision == MAP_MIXED ? MAP_MIXED : MAP_FP64], s));
   phase_end(ctx, 2, s);

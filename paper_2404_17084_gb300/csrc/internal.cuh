@@ -150,9 +150,9 @@ struct map_ctx {
   DevBuf ws_vor[22];                   // grid construction: buckets, cell slots, CSR arrays
   DevBuf ws_inv[11];                   // particle-major copy of the pair list (inverse mapping, Eq. 4)
   DevBuf cub_tmp;
-  DevBuf ws_near;                      // items with a near-plane face (mixed build's FP64 fix-up)
   DevTree tree;
   int64_t node_cap0 = 0;  // > 0: octree node arrays start at this capacity (a context whose workspace is fixed)
+  int item_target = 16;   // work items per resident warp of the integral launch (the autotuner may raise it)
   // results of the last mapping call
   int64_t last_ncell = 0;
   int64_t n_pairs = 0;
@@ -176,8 +176,7 @@ struct map_ctx {
   int64_t n_items = 0;
   // device counters: [0] status, [1] edge terms, [2] fp64 terms, [3] work queue,
   // [4..7] scratch, [8] face tests, [9] edge records read, [10] inner-piece
-  // antiderivative evaluations, [11] middle-piece Gauss-Legendre intervals,
-  // [14] items with a near-plane face (mixed build)
+  // antiderivative evaluations, [11] middle-piece Gauss-Legendre intervals
   unsigned long long* d_counters = nullptr;
   double* d_total = nullptr;
   map_stats* h_stats = nullptr;  // pinned
@@ -194,7 +193,7 @@ struct map_ctx {
   // launch shape of the pair-integral kernel, per precision (the autotuner's choice)
   int tuned[2] = {0, 0};
   bool tune_done[2] = {false, false};
-  float tune_ms[3] = {0.f, 0.f, 0.f};
+  float tune_ms[32] = {};             // [item target][shape]: ms of each trial (0 when not run)
   // batches: per-snapshot pair lists of the last batch, and the CUDA graph of
   // its integral launch with the descriptor bytes it was captured for
   std::vector<DevBuf> batch_off, batch_idx, batch_itm, batch_ioff, batch_part;
@@ -288,11 +287,15 @@ struct BatchArgs {
   int nsnap;
   int64_t total;        // items
   int64_t total_cells;
-  unsigned long long* counters;  // [1] edge terms, [2] FP64 terms, [3] queue, [8..13] work tally, [14] near-plane items
-  int64_t* near;                 // mixed build: queue positions of items with a near-plane face (capacity: total)
+  unsigned long long* counters;  // [1] edge terms, [2] FP64 terms, [3] queue, [8..13] work tally
 };
 
-constexpr int N_VARIANTS = 3;  // launch shapes of the mixed pair-integral kernel (register caps 102, 128, 85)
+// Launch shapes of the mixed pair-integral kernel: (warps per CTA, CTAs per
+// SM) = (4, 5), (4, 4), (4, 6), (2, 10), (8, 2); the register cap per thread
+// follows from them.  Work-item targets: items per resident warp of a launch.
+constexpr int N_SHAPES = 5;
+constexpr int N_TARGETS = 3;
+constexpr int ITEM_TARGETS[N_TARGETS] = {16, 64, 256};
 
 // ---------------------------------------------------------------- subsystems
 int grid_prepare(map_ctx* ctx, const map_grid* in, PreparedGrid* g, cudaStream_t s);
@@ -314,6 +317,10 @@ struct PairBufs {
 
 // Pair list of the grid against the current octree, and its work items.
 int pairs_build(map_ctx* ctx, const PreparedGrid* g, cudaStream_t s, const PairBufs& out = PairBufs());
+// The work items of a pair list (offsets off, nc cells, np pairs) for at least
+// `target` items per resident warp; sets ctx->items, item_off, partial, n_items.
+int items_build(map_ctx* ctx, const int64_t* off, int64_t nc, int64_t np, int target, cudaStream_t s,
+                const PairBufs& out = PairBufs());
 // Sorts the last call's lists (and f_ai) by particle index within each cell.
 int pairs_sort_lists(map_ctx* ctx, cudaStream_t s);
 int check_particles(map_ctx* ctx, const map_particles* p, bool need_m, bool need_h, cudaStream_t s);
@@ -326,7 +333,12 @@ int integrals_upload(map_ctx* ctx, const SnapDesc* h_desc, const int64_t* h_ibas
                      int nsnap, SnapDesc* d_desc, int64_t* d_ibase, int64_t* d_cbase, cudaStream_t s);
 int integrals_enqueue(map_ctx* ctx, const BatchArgs& B, int variant, cudaStream_t s);
 int integrals_sum(map_ctx* ctx, const SnapDesc* d_desc, int nsnap, double* totals, cudaStream_t s);
-int integrals_autotune(map_ctx* ctx, const BatchArgs& B, cudaStream_t s);
+// Times every (work-item target, launch shape) pair on the call's inputs and
+// keeps the fastest (ctx->tuned[MAP_MIXED], ctx->item_target).  rebuild(T, B)
+// rebuilds the work items for target T and returns the launch arguments;
+// on return B holds those of the chosen target.
+int integrals_autotune(map_ctx* ctx, const std::function<int(int, BatchArgs&)>& rebuild, BatchArgs& B,
+                       cudaStream_t s);
 // MAP_TABLE: build the table (synchronises the stream), free it, and launch
 // the table variant of the pair-integral kernel
 int table_ensure(map_ctx* ctx, cudaStream_t s);

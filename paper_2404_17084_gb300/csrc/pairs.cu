@@ -464,18 +464,30 @@ int pairs_build(map_ctx* ctx, const PreparedGrid* g, cudaStream_t s, const PairB
     pair_traverse<true><<<nblk(nc, tpb), tpb, 0, s>>>(nc, ovf, PT, PG, nullptr, off, list, d_novf);
   ++ctx->launches;
   CUDA_TRY(cudaGetLastError());
-  // work items: K blocks of 32 pairs at most, K chosen so that the launch has
-  // at least 16 items per resident warp (4 warps x 6 CTAs per SM)
+  ctx->n_pairs = np;
+  ctx->pair_off = off;
+  ctx->pair_idx = list;
+  ctx->pairs_sorted = false;
+  ctx->inv_ready = false;
+  ctx->last_ncell = nc;
+  return items_build(ctx, off, nc, np, ctx->item_target, s, out);
+}
+
+// Work items of a pair list: K blocks of 32 pairs at most, K chosen so that
+// the launch has at least `target` items per resident warp (4 warps x 6 CTAs
+// per SM); the autotuner may raise the target (smaller items).
+int items_build(map_ctx* ctx, const int64_t* off, int64_t nc, int64_t np, int target, cudaStream_t s,
+                const PairBufs& out) {
   const int64_t blocks = np / 32 + nc;
-  const int64_t target = 16LL * ctx->sm_count * 24;
-  const int64_t K = blocks / target > 1 ? blocks / target : 1;
+  const int64_t tgt = (int64_t)target * ctx->sm_count * 24;
+  const int64_t K = blocks / tgt > 1 ? blocks / tgt : 1;
   int64_t *icnt, *ioff;
-  MAP_TRY(ensure_t(ctx, ctx->ws_pairs[0], nc + 1, &icnt));  // the counts are no longer needed
+  MAP_TRY(ensure_t(ctx, ctx->ws_pairs[0], nc + 1, &icnt));  // the pair counts are no longer needed
   MAP_TRY(ensure_t(ctx, out.ioff ? *out.ioff : ctx->ws_pairs[11], nc + 1, &ioff));
   item_count<<<nblk(nc, 256), 256, 0, s>>>(nc, off, K, icnt); ++ctx->launches;
   CUDA_TRY(cudaGetLastError());
   CUDA_TRY(cudaMemsetAsync(icnt + nc, 0, sizeof(int64_t), s));
-  tb = 0;
+  size_t tb = 0;
   CUDA_TRY(cub::DeviceScan::ExclusiveSum(nullptr, tb, icnt, ioff, nc + 1, s));
   MAP_TRY(ctx_ensure(ctx, ctx->cub_tmp, tb));
   CUDA_TRY(cub::DeviceScan::ExclusiveSum(ctx->cub_tmp.p, tb, icnt, ioff, nc + 1, s));
@@ -488,16 +500,10 @@ int pairs_build(map_ctx* ctx, const PreparedGrid* g, cudaStream_t s, const PairB
   MAP_TRY(ensure_t(ctx, out.part ? *out.part : ctx->ws_pairs[12], nitems, &part));
   item_fill<<<nblk(nc, 256), 256, 0, s>>>(nc, off, ioff, K, items); ++ctx->launches;
   CUDA_TRY(cudaGetLastError());
-  ctx->n_pairs = np;
-  ctx->pair_off = off;
-  ctx->pair_idx = list;
-  ctx->pairs_sorted = false;
-  ctx->inv_ready = false;
   ctx->items = items;
   ctx->item_off = ioff;
   ctx->partial = part;
   ctx->n_items = nitems;
-  ctx->last_ncell = nc;
   return MAP_OK;
 }
 

@@ -127,7 +127,6 @@ void trim(map_ctx* ctx, cudaStream_t s) {
   for (auto* v : {&ctx->batch_off, &ctx->batch_idx, &ctx->batch_itm, &ctx->batch_ioff, &ctx->batch_part})
     for (auto& b : *v) drop(b);
   drop(ctx->cub_tmp);
-  drop(ctx->ws_near);
   grid_pool_drop(ctx);
   ctx->pair_off = nullptr;
   ctx->pair_idx = nullptr;

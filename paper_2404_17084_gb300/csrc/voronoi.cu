@@ -562,6 +562,10 @@ int vor_tessellate(map_ctx* ctx, const double* x, const double* y, const double*
   CUDA_TRY(cudaDeviceGetLimit(&stack, cudaLimitStackSize));
   const size_t need = (fa.localSizeBytes > 16384 ? fa.localSizeBytes : 16384) + 1024;
   if (stack < need) CUDA_TRY(cudaDeviceSetLimit(cudaLimitStackSize, need));
+  // refuse to launch a frame the per-thread stack does not hold (the limit
+  // read back, as the driver may round or cap it)
+  CUDA_TRY(cudaDeviceGetLimit(&stack, cudaLimitStackSize));
+  if (stack < fa.localSizeBytes + 1024) return MAP_ECUDA;
   vor_cells<<<nblk(n, 64), 64, 0, s>>>(n, x, y, z, B, S, d_over); ++ctx->launches;
   CUDA_TRY(cudaGetLastError());
   CUDA_TRY(cudaMemcpyAsync(ctx->h_scratch, d_over, sizeof(unsigned long long), cudaMemcpyDeviceToHost, s));

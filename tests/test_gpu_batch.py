@@ -64,11 +64,14 @@ def test_batch_equals_single(snapshots, precision):
 
 
 def test_batch_autotune_and_replay(snapshots):
-    """The autotuner times every launch shape and keeps one.  Replays of the
-    captured graph give the same bits; another launch shape (a separate
-    compilation of the same source) agrees to FP32 rounding."""
+    """The autotuner times every pair of a work-item size (3) and a launch
+    shape (5) and keeps one.  Replays of the captured graph give the same
+    bits; another shape or item size (a separate compilation, other groups of
+    a cell's pairs) agrees to FP32 rounding."""
+    L = lib()
     ref, _, _ = run_batch(snapshots, 1)
     runs, _, (chosen, ms) = run_batch(snapshots, 1, autotune=1, repeat=3)
+    assert len(ms) == len(L.AUTOTUNE_SHAPES) * len(L.AUTOTUNE_ITEM_TARGETS) == 15
     assert 0 <= chosen < len(ms) and all(t > 0 for t in ms)
     for masses, totals in runs[1:]:
         for a, b in zip(masses, runs[0][0]):

@@ -267,3 +267,35 @@ def test_grid_upload_from_pinned_host_and_reuse(uniform4096):
         L.map_destroy(ctx)
     for a, b in res[1:]:
         assert np.array_equal(a, res[0][0]) and np.array_equal(b, res[0][1])
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_particles_on_face_planes(precision):
+    """Particles on the face planes of the grid: the midpoints of neighbouring
+    sites (on their bisector plane up to rounding) and points 1e-9 and 1e-6
+    off it (h is about 0.1 here, so all within the 1e-4 h where the mixed
+    build decides the face's side and distance in FP64).  Every cell against
+    the oracle, at the build's gate."""
+    sites = synth.uniform_particles(300, synth.BASE_SEED + 13)
+    g = synth.voronoi(sites.pos())
+    pos = sites.pos()
+    rng = np.random.default_rng(8)
+    pts = []
+    for f in rng.choice(len(g.face_nb), 400, replace=False):
+        nb = g.face_nb[f]
+        if nb < 0:
+            continue
+        c = int(np.searchsorted(g.cell_face_off, f, side="right") - 1)
+        mid = 0.5 * (pos[c] + pos[nb])
+        n = g.face_plane[f][:3]
+        for off in (0.0, 1e-9, -1e-6):
+            pts.append(np.clip(mid + off * n, 0.0, 1.0))
+    pts = np.array(pts)
+    p = synth.Particles(pts[:, 0].copy(), pts[:, 1].copy(), pts[:, 2].copy(), np.full(len(pts), 1.0 / len(pts)))
+    h, _ = oracle_h(p)
+    out = gpu_map(g, p, h, precision)
+    ref = oracle.map_cells(g, p.x, p.y, p.z, p.m, h)
+    assert np.array_equal(out["idx"], ref["idx"])
+    cell_tol, tot_tol = TOL[precision]
+    assert rel_err(out["mass"], ref["mass"]).max() < cell_tol
+    assert abs(out["total"] - ref["mass"].sum()) < tot_tol * ref["mass"].sum()

@@ -115,3 +115,25 @@ def test_build_errors():
             L.map_grid_build(ctx, ok, ok, ok, -1, 0.0)
     finally:
         L.map_destroy(ctx)
+
+
+def test_cells_match_oracle_16k_clumpy_sampled():
+    """A larger clumpy site set (2^14 sites, log-normal field): 200 sampled
+    cells against the oracle's cells built for those sites alone (each
+    against all sites): face counts, vertices and volumes as above."""
+    sites = synth.lognormal_particles(1 << 14, 71, ngrid=64).pos()
+    g, kept = gpu_build(sites)
+    assert np.array_equal(kept, np.arange(len(sites)))
+    which = np.sort(np.random.default_rng(3).choice(len(sites), 200, replace=False))
+    ref = oracle.VoronoiGrid(oracle.voronoi_cells_of(sites, which), sites[which])
+    # the GPU grid restricted to the same cells (vertex arrays shared)
+    sub = HostGrid({})
+    cfo, fvo = g.cell_face_off, g.face_vert_off
+    faces = np.concatenate([np.arange(cfo[c], cfo[c + 1]) for c in which])
+    sub.cell_face_off = np.concatenate([[0], np.cumsum(np.diff(cfo)[which])]).astype(np.int64)
+    nl = fvo[faces + 1] - fvo[faces]
+    sub.face_vert_off = np.concatenate([[0], np.cumsum(nl)]).astype(np.int64)
+    sub.face_vert = np.concatenate([g.face_vert[fvo[f]:fvo[f + 1]] for f in faces]).astype(np.int32)
+    sub.face_plane = g.face_plane.reshape(-1, 4)[faces]
+    sub.vx, sub.vy, sub.vz, sub.site = g.vx, g.vy, g.vz, g.site.reshape(-1, 3)[which]
+    compare_cells(sub, ref, tol_v=1e-12)
