@@ -134,7 +134,9 @@ __device__ __forceinline__ void drain(WarpStacks<T>& S, int& cnt0, int& cnt1, in
       else if constexpr (WarpStacks<T>::NK == 3) v = -P.x * wedge::dphi(P.z, P.w, P.y);  // P.x = c0 (the push)
     }
     if constexpr (WarpStacks<T>::COL) {
-      if (on) S.col[o][lane] += v;  // this lane's column: no other lane touches it
+      // FP32 pieces are stacked unfolded, their sign s_f s_e in the owner's bit 7
+      v = __int_as_float(__float_as_int(v) ^ ((o & 0x80) << 24));
+      if (on) S.col[o & 31][lane] += v;  // this lane's column: no other lane touches it
       __syncwarp();
     } else {
       // lanes holding pieces of the same owner add in turn, in lane order
@@ -415,7 +417,7 @@ struct MixWarp {
   float4 fsp[FSTAGE];    // their bounding spheres
   int fend[FSTAGE];      // loop end of each face, relative to the cell's first loop entry
   WarpStacks<float> st;  // piece stacks, column accumulators, snapshot
-  uint4 cmb[CCAP];       // (r0 bits, c0 bits, edge << 6 | fin << 5 | owner, 0)
+  uint4 cmb[CCAP];       // (r0 bits, c0 bits, edge record offset in floats, fin << 5 | owner)
   float4 py[32];         // per pair: y (site-relative, in units of h), 1/h
 };
 
@@ -431,12 +433,12 @@ __device__ __forceinline__ void edge_round(MixWarp& M, const float* __restrict__
   uint4 C = make_uint4(0u, 0u, 0u, 0u);
   if (on) C = M.cmb[base + lane];
   __syncwarp();  // the records are taken: new ones may overwrite them
-  const int o = (int)(C.z & 31u);
-  const bool fin = (C.z >> 5) & 1u;
+  const int o = (int)(C.w & 31u);
+  const bool fin = C.w & 32u;
   const float r0 = __uint_as_float(C.x), c0f = __uint_as_float(C.y);
   const float4 Y = M.py[o];
   float e0 = 0.f, e1 = 0.f, e2 = 0.f, e3 = 0.f, e4 = 0.f, e5 = 0.f, e6 = 0.f, e7 = 0.f, e8 = 0.f;
-  if (on) load_edge(ecell + (size_t)(C.z >> 6) * EDGE_STRIDE, e0, e1, e2, e3, e4, e5, e6, e7, e8);
+  if (on) load_edge(ecell + C.z, e0, e1, e2, e3, e4, e5, e6, e7, e8);
   // R0 = m.y - delta/h and the foot's along-edge position e.y, side by side
   // in two-lane arithmetic, then the vertices' positions from the foot
   using wedge::f2;
@@ -454,29 +456,33 @@ __device__ __forceinline__ void edge_round(MixWarp& M, const float* __restrict__
     n_split += P.split;
     n_out += ((P.v >> 3) & 1u) + ((P.v >> 4) & 1u);
   }
-  int t0, t1;
-  const int o0 = cnt0 + warp_excl2(nin, &t0);
+  // inner pieces (0 or 1 per record): one ballot; middle pieces: two
+  const unsigned bin = __ballot_sync(FULL, nin);
+  const int t0 = __popc(bin);
+  const int o0 = cnt0 + __popc(bin & ((1u << lane) - 1u));
+  int t1;
   const int o1 = cnt1 + warp_excl2(nmid, &t1);
-  const unsigned char ow = (unsigned char)o;
+  // pieces go unfolded; their sign s_f s_e rides in the owner's bit 7
+  const unsigned char ow = (unsigned char)(o | (P.pos ? 0 : 0x80));
   float lo, hi;
-  if (P.v & 1u) { P.get(0, lo, hi); S.e[0][o0] = float4{r0, R0, lo, hi}; S.own[0][o0] = ow; }
-  if (P.v & 2u) { P.get(1, lo, hi); S.e[1][o1] = float4{r0, R0, lo, hi}; S.own[1][o1] = ow; }
+  if (P.v & 1u) { P.get_raw(0, lo, hi); S.e[0][o0] = float4{r0, R0, lo, hi}; S.own[0][o0] = ow; }
+  if (P.v & 2u) { P.get_raw(1, lo, hi); S.e[1][o1] = float4{r0, R0, lo, hi}; S.own[1][o1] = ow; }
   if (P.v & 4u) {
     const int q = o1 + ((P.v >> 1) & 1u);
-    P.get(2, lo, hi); S.e[1][q] = float4{r0, R0, lo, hi}; S.own[1][q] = ow;
+    P.get_raw(2, lo, hi); S.e[1][q] = float4{r0, R0, lo, hi}; S.own[1][q] = ow;
   }
   // beyond the support: -c0 (dPhi_left + dPhi_right) as the argument of the
   // product of the two intervals' numbers (R0^2 + lo hi) + i (hi - lo) R0
   {
     float l3, h3, l4, h4;
-    P.get(3, l3, h3);
-    P.get(4, l4, h4);
+    P.get_raw(3, l3, h3);
+    P.get_raw(4, l4, h4);
     const bool v3 = P.v & 8u, v4 = P.v & 16u;
     const float R02 = R0 * R0;
     const float ar = v3 ? R02 + l3 * h3 : 1.f, ai = v3 ? (h3 - l3) * R0 : 0.f;
     const float br = v4 ? R02 + l4 * h4 : 1.f, bi = v4 ? (h4 - l4) * R0 : 0.f;
     const f2 z = wedge::fma2(f2{-ai, ai}, f2{bi, br}, wedge::mul2(wedge::sp(ar), f2{br, bi}));
-    if (on) S.col[o][lane] += -c0f * wedge::xatan2(z.y, z.x);
+    if (on) S.col[o][lane] += (P.pos ? -c0f : c0f) * wedge::xatan2(z.y, z.x);
   }
   cnt0 += t0;
   cnt1 += t1;
@@ -592,7 +598,8 @@ __global__ void __launch_bounds__(NW * 32, MINB) pair_integrals_mixed(BatchArgs 
           const float c0f = wedge::c0_of(r0);
           const unsigned tag = (unsigned)lane | (fin ? 32u : 0u);
           for (int k = kb; k < ke; ++k) {
-            if (inrange) M.cmb[cntc + rank] = make_uint4(__float_as_uint(r0), __float_as_uint(c0f), tag | ((unsigned)k << 6), 0u);
+            if (inrange)
+              M.cmb[cntc + rank] = make_uint4(__float_as_uint(r0), __float_as_uint(c0f), (unsigned)k * EDGE_STRIDE, tag);
             cntc += nn;
             if (cntc >= 32) {
               cntc -= 32;

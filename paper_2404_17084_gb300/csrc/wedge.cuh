@@ -129,10 +129,13 @@ __device__ __forceinline__ T pmid(T u) {
   return t2 * t2 * t * (T(1) + u);
 }
 
-// kappa = r0 E_mid(r0) - r0 E(r0): zero for r0 >= 1
+// kappa = r0 E_mid(r0) - r0 E(r0): zero for r0 >= 1 (so only the inner
+// branch of r0 E(r0) is needed)
 template <typename T>
 __device__ __forceinline__ T kappa_of(T r0) {
-  return r0 < T(1) ? pmid(r0) * T(INV_120PI) - c0_of(r0) : T(0);
+  const T r2 = r0 * r0, r3 = r2 * r0;
+  const T a = (T(1) - T(1.4) * r0 + (T(2) / T(3)) * r3 - T(0.3) * r3 * r2 + T(0.1) * r3 * r3) * T(INV_4PI);
+  return r0 < T(1) ? pmid(r0) * T(INV_120PI) - a : T(0);
 }
 
 // Phi(hi) - Phi(lo), Phi = atan2(s, R0), in one atan2 (exact for any order of lo, hi)
@@ -334,6 +337,16 @@ struct EdgeSplit {
     }
     lo = pos ? l : h;
     hi = pos ? h : l;
+  }
+  // bounds of piece i, unfolded (lo <= hi for a non-empty piece)
+  __device__ __forceinline__ void get_raw(int i, T& l, T& h) const {
+    switch (i) {
+      case 0: l = x0 > -s1 ? x0 : -s1; h = x1 < s1 ? x1 : s1; break;
+      case 1: l = x0; h = (whole || x1 < -s1) ? x1 : -s1; break;
+      case 2: l = x0 > s1 ? x0 : s1; h = x1; break;
+      case 3: l = aa; h = far ? ab : (ab < -s2 ? ab : -s2); break;
+      default: l = aa > s2 ? aa : s2; h = ab; break;
+    }
   }
 };
 
