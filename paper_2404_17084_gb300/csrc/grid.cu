@@ -101,9 +101,10 @@ __global__ void prep_faces(int64_t nface, const int32_t* __restrict__ fcell, con
       }
       rec[9] = rec[10] = rec[11] = 0.f;
       float4* Ef = reinterpret_cast<float4*>(edge32 + (b + k) * EDGE_STRIDE);
-      Ef[0] = make_float4(rec[0], rec[1], rec[2], rec[3]);
-      Ef[1] = make_float4(rec[4], rec[5], rec[6], rec[7]);
-      Ef[2] = make_float4(rec[8], rec[9], rec[10], rec[11]);
+      // interleaved: (m.x, t.x, m.y, t.y), (m.z, t.z, a_A, a_B), (delta, 0, 0, 0)
+      Ef[0] = make_float4(rec[0], rec[4], rec[1], rec[5]);
+      Ef[1] = make_float4(rec[2], rec[6], rec[7], rec[8]);
+      Ef[2] = make_float4(rec[3], rec[9], rec[10], rec[11]);
       if (fsph32) {
         const float dx = ax32 - mx, dy = ay32 - my, dz = az32 - mz;
         sr2 = fmaxf(sr2, dx * dx + dy * dy + dz * dz);

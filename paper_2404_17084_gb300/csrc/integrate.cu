@@ -33,6 +33,7 @@
 // the edges: only a lane whose face can reach its support queues the face's
 // edges, as (pair, edge) records that the warp then splits 32 at a time.
 #include <cub/cub.cuh>
+#include <type_traits>
 
 #include "internal.cuh"
 #include "wedge.cuh"
@@ -69,12 +70,16 @@ __device__ __forceinline__ int warp_excl2(int v, int* tot) {
   return __popc(b0 & lt) + 2 * __popc(b1 & lt);
 }
 
-// One edge record (EDGE_STRIDE words, 16-byte aligned) in vector loads.
+// One edge record (EDGE_STRIDE words, 16-byte aligned) in vector loads:
+// e0..e2 the in-plane edge normal m, e3 its offset delta, e4..e6 the edge
+// direction t, e7, e8 the vertices' positions along t.  The FP32 record is
+// interleaved, (m.x, t.x, m.y, t.y), (m.z, t.z, a_A, a_B), (delta), so that
+// the pairs the two-lane arithmetic takes sit in adjacent registers.
 __device__ __forceinline__ void load_edge(const float* E, float& e0, float& e1, float& e2, float& e3, float& e4,
                                           float& e5, float& e6, float& e7, float& e8) {
   const float4 a = reinterpret_cast<const float4*>(E)[0], b = reinterpret_cast<const float4*>(E)[1];
   const float4 c = reinterpret_cast<const float4*>(E)[2];
-  e0 = a.x; e1 = a.y; e2 = a.z; e3 = a.w; e4 = b.x; e5 = b.y; e6 = b.z; e7 = b.w; e8 = c.x;
+  e0 = a.x; e4 = a.y; e1 = a.z; e5 = a.w; e2 = b.x; e6 = b.y; e7 = b.z; e8 = b.w; e3 = c.x;
 }
 __device__ __forceinline__ void load_edge(const double* E, double& e0, double& e1, double& e2, double& e3,
                                           double& e4, double& e5, double& e6, double& e7, double& e8) {
@@ -126,19 +131,26 @@ __device__ __forceinline__ void drain(WarpStacks<T>& S, int& cnt0, int& cnt1, in
     const bool on = lane < n;
     T v = T(0);
     int o = 32 + lane;  // a key no owner has, for idle lanes
-    if (on) {
-      const typename Vec4<T>::type P = S.e[K][base + lane];
-      o = S.own[K][base + lane];
-      if (K == 1) v = wedge::piece_mid<T, MIXED>(P.x, P.y, P.z, P.w);
-      else if (K == 0) v = wedge::piece_inner<T>(P.x, P.y, P.z, P.w);
-      else if constexpr (WarpStacks<T>::NK == 3) v = -P.x * wedge::dphi(P.z, P.w, P.y);  // P.x = c0 (the push)
-    }
     if constexpr (WarpStacks<T>::COL) {
+      // every lane evaluates (an idle lane a copy of the first piece) and
+      // adds its value or 0: no divergent region
+      const int idx = base + (on ? lane : 0);
+      const typename Vec4<T>::type P = S.e[K][idx];
+      o = S.own[K][idx];
+      if (K == 1) v = wedge::piece_mid<T, MIXED>(P.x, P.y, P.z, P.w);
+      else v = wedge::piece_inner<T>(P.x, P.y, P.z, P.w);
       // FP32 pieces are stacked unfolded, their sign s_f s_e in the owner's bit 7
       v = __int_as_float(__float_as_int(v) ^ ((o & 0x80) << 24));
-      if (on) S.col[o & 31][lane] += v;  // this lane's column: no other lane touches it
+      S.col[o & 31][lane] += on ? v : 0.f;  // this lane's column: no other lane touches it
       __syncwarp();
     } else {
+      if (on) {
+        const typename Vec4<T>::type P = S.e[K][base + lane];
+        o = S.own[K][base + lane];
+        if (K == 1) v = wedge::piece_mid<T, MIXED>(P.x, P.y, P.z, P.w);
+        else if (K == 0) v = wedge::piece_inner<T>(P.x, P.y, P.z, P.w);
+        else if constexpr (WarpStacks<T>::NK == 3) v = -P.x * wedge::dphi(P.z, P.w, P.y);  // P.x = c0 (the push)
+      }
       // lanes holding pieces of the same owner add in turn, in lane order
       const unsigned grp = __match_any_sync(FULL, o);
       const int rank = __popc(grp & ((1u << lane) - 1u));
@@ -418,7 +430,7 @@ struct MixWarp {
   int fend[FSTAGE];      // loop end of each face, relative to the cell's first loop entry
   WarpStacks<float> st;  // piece stacks, column accumulators, snapshot
   uint4 cmb[CCAP];       // (r0 bits, c0 bits, edge record offset in floats, fin << 5 | owner)
-  float4 py[32];         // per pair: y (site-relative, in units of h), 1/h
+  float4 py[2][32];      // per pair: (y.x, y.x, y.y, y.y), (y.z, y.z, 1/h, 1/h), y site-relative in units of h
 };
 
 // Splits the n (<= 32) records on top of the record stack, one per lane.
@@ -430,59 +442,74 @@ __device__ __forceinline__ void edge_round(MixWarp& M, const float* __restrict__
   const int lane = threadIdx.x & 31;
   __syncwarp();
   const bool on = lane < n;
-  uint4 C = make_uint4(0u, 0u, 0u, 0u);
-  if (on) C = M.cmb[base + lane];
+  const uint4 C = M.cmb[base + (on ? lane : 0)];  // an idle lane takes a copy of the first record
   __syncwarp();  // the records are taken: new ones may overwrite them
   const int o = (int)(C.w & 31u);
   const bool fin = C.w & 32u;
   const float r0 = __uint_as_float(C.x), c0f = __uint_as_float(C.y);
-  const float4 Y = M.py[o];
-  float e0 = 0.f, e1 = 0.f, e2 = 0.f, e3 = 0.f, e4 = 0.f, e5 = 0.f, e6 = 0.f, e7 = 0.f, e8 = 0.f;
-  if (on) load_edge(ecell + C.z, e0, e1, e2, e3, e4, e5, e6, e7, e8);
+  const float4 Y0 = M.py[0][o], Y1 = M.py[1][o];
+  float e0, e1, e2, e3, e4, e5, e6, e7, e8;
+  load_edge(ecell + C.z, e0, e1, e2, e3, e4, e5, e6, e7, e8);
   // R0 = m.y - delta/h and the foot's along-edge position e.y, side by side
   // in two-lane arithmetic, then the vertices' positions from the foot
   using wedge::f2;
-  const f2 g = wedge::fma2(f2{e2, e6}, wedge::sp(Y.z),
-                           wedge::fma2(f2{e1, e5}, wedge::sp(Y.y), wedge::mul2(f2{e0, e4}, wedge::sp(Y.x))));
-  const float R0s = fmaf(-e3, Y.w, g.x);
+  const f2 g = wedge::fma2(f2{e2, e6}, f2{Y1.x, Y1.y},
+                           wedge::fma2(f2{e1, e5}, f2{Y0.z, Y0.w}, wedge::mul2(f2{e0, e4}, f2{Y0.x, Y0.y})));
+  const float R0s = fmaf(-e3, Y1.z, g.x);
   const bool ein = R0s >= 0.f;
   const float R0 = fabsf(R0s);
-  const f2 ab = wedge::fma2(f2{e7, e8}, wedge::sp(Y.w), wedge::sp(-g.y));
-  const wedge::EdgeSplit<float> P = wedge::split_edge_flat<float>(r0, R0, ab.x, ab.y, fin == ein, on);
-  const int nin = P.v & 1u, nmid = ((P.v >> 1) & 1u) + ((P.v >> 2) & 1u);
+  const f2 ab = wedge::fma2(f2{e7, e8}, f2{Y1.z, Y1.w}, wedge::sp(-g.y));
+  // the edge's pieces as wedge::split_edge_flat cuts them, written with
+  // min/max instructions for the clamps and one predicate per piece (the
+  // same bounds: no value is NaN, and a +-0 bound gives the same integrals)
+  const float aa = ab.x, bb = ab.y;
+  const float c2 = fmaf(r0, r0, R0 * R0);
+  const bool far = c2 >= 4.f, lt1 = c2 < 1.f;
+  float s1, s2;
+  {
+    const f2 xs = f2{4.f - c2, 1.f - c2};
+    const f2 r = f2{rsqrtf(xs.x), rsqrtf(xs.y)};
+    const f2 y = wedge::mul2(xs, r);
+    const f2 q = wedge::fma2(wedge::mul2(wedge::sp(0.5f), r), wedge::fma2(f2{-y.x, -y.y}, y, xs), y);
+    s2 = far ? 0.f : q.x;
+    s1 = lt1 ? q.y : 0.f;
+  }
+  const float x0 = fmaxf(aa, -s2), x1 = fminf(bb, s2);
+  const float len = x1 - x0;
+  const bool whole = !lt1 && len * len <= c2;
+  const float l0 = fmaxf(x0, -s1), h0 = fminf(x1, s1);
+  const float h1 = whole ? x1 : fminf(x1, -s1);
+  const float l2 = fmaxf(x0, s1);
+  const float h3 = far ? bb : fminf(bb, -s2);
+  const float l4 = fmaxf(aa, s2);
+  const bool v0 = on && h0 > l0, v1 = on && h1 > x0, v2 = on && !whole && x1 > l2;
+  const bool v3 = h3 > aa, v4 = !far && bb > l4;
+  const bool pos = fin == ein;
   if (COUNT && on) {
     wc.edges++;
-    if (P.v) wc.terms++;
-    n_split += P.split;
-    n_out += ((P.v >> 3) & 1u) + ((P.v >> 4) & 1u);
+    if (v0 || v1 || v2 || v3 || v4) wc.terms++;
+    n_split += v1 && v2 && !lt1;
+    n_out += (unsigned)v3 + (unsigned)v4;
   }
   // inner pieces (0 or 1 per record): one ballot; middle pieces: two
-  const unsigned bin = __ballot_sync(FULL, nin);
-  const int t0 = __popc(bin);
-  const int o0 = cnt0 + __popc(bin & ((1u << lane) - 1u));
-  int t1;
-  const int o1 = cnt1 + warp_excl2(nmid, &t1);
+  const unsigned lt = (1u << lane) - 1u;
+  const unsigned bin = __ballot_sync(FULL, v0), bm1 = __ballot_sync(FULL, v1), bm2 = __ballot_sync(FULL, v2);
+  const int t0 = __popc(bin), t1 = __popc(bm1) + __popc(bm2);
+  const int o0 = cnt0 + __popc(bin & lt);
+  const int o1 = cnt1 + __popc(bm1 & lt) + __popc(bm2 & lt);
   // pieces go unfolded; their sign s_f s_e rides in the owner's bit 7
-  const unsigned char ow = (unsigned char)(o | (P.pos ? 0 : 0x80));
-  float lo, hi;
-  if (P.v & 1u) { P.get_raw(0, lo, hi); S.e[0][o0] = float4{r0, R0, lo, hi}; S.own[0][o0] = ow; }
-  if (P.v & 2u) { P.get_raw(1, lo, hi); S.e[1][o1] = float4{r0, R0, lo, hi}; S.own[1][o1] = ow; }
-  if (P.v & 4u) {
-    const int q = o1 + ((P.v >> 1) & 1u);
-    P.get_raw(2, lo, hi); S.e[1][q] = float4{r0, R0, lo, hi}; S.own[1][q] = ow;
-  }
+  const unsigned char ow = (unsigned char)(o | (pos ? 0 : 0x80));
+  if (v0) { S.e[0][o0] = float4{r0, R0, l0, h0}; S.own[0][o0] = ow; }
+  if (v1) { S.e[1][o1] = float4{r0, R0, x0, h1}; S.own[1][o1] = ow; }
+  if (v2) { const int q = o1 + (int)v1; S.e[1][q] = float4{r0, R0, l2, x1}; S.own[1][q] = ow; }
   // beyond the support: -c0 (dPhi_left + dPhi_right) as the argument of the
   // product of the two intervals' numbers (R0^2 + lo hi) + i (hi - lo) R0
   {
-    float l3, h3, l4, h4;
-    P.get_raw(3, l3, h3);
-    P.get_raw(4, l4, h4);
-    const bool v3 = P.v & 8u, v4 = P.v & 16u;
     const float R02 = R0 * R0;
-    const float ar = v3 ? R02 + l3 * h3 : 1.f, ai = v3 ? (h3 - l3) * R0 : 0.f;
-    const float br = v4 ? R02 + l4 * h4 : 1.f, bi = v4 ? (h4 - l4) * R0 : 0.f;
+    const float ar = v3 ? fmaf(aa, h3, R02) : 1.f, ai = v3 ? (h3 - aa) * R0 : 0.f;
+    const float br = v4 ? fmaf(l4, bb, R02) : 1.f, bi = v4 ? (bb - l4) * R0 : 0.f;
     const f2 z = wedge::fma2(f2{-ai, ai}, f2{bi, br}, wedge::mul2(wedge::sp(ar), f2{br, bi}));
-    if (on) S.col[o][lane] += (P.pos ? -c0f : c0f) * wedge::xatan2(z.y, z.x);
+    S.col[o][lane] += on ? (pos ? -c0f : c0f) * wedge::xatan2(z.y, z.x) : 0.f;
   }
   cnt0 += t0;
   cnt1 += t1;
@@ -548,84 +575,91 @@ __global__ void __launch_bounds__(NW * 32, MINB) pair_integrals_mixed(BatchArgs 
       __syncwarp();
     }
     double macc = 0.0;
-    const int64_t pb = item.lo, pe = item.lo + item.cnt;
-    for (int64_t p0 = pb; p0 < pe; p0 += 32) {
-      const int64_t p = p0 + lane;
-      const bool active = p < pe;
-      float yx = 0.f, yy = 0.f, yz = 0.f, hinv = 0.f;
-      int32_t a = 0;
-      if (active) {
-        a = A.pair_idx[p];
-        pair_frame(A, a, sx, sy, sz, yx, yy, yz, hinv);
-      }
-      M.py[lane] = make_float4(yx, yy, yz, hinv);
-      bool inside = true;
-      int cntc = 0, cnt0 = 0, cnt1 = 0;  // stack heights (warp-uniform)
-      __syncwarp();
-      int kb = 0;
-      for (int fi = 0; fi < nf; ++fi) {
-        const float4 F = staged ? M.fpl[fi] : face[f0 + fi];
-        const int ke = staged ? M.fend[fi] : (int)(A.fvo[f0 + fi + 1] - l0);
-        const float r0s = face_r0s(F, yx, yy, yz, hinv);
-        bool fin = r0s >= 0.f;
-        float r0 = fabsf(r0s);
-        bool inrange = active && r0 < 2.f;
-        if (COUNT && active) wc.faces++;
-        if (inrange && r0 < TAU) {
-          // the plane passes within TAU h: its side and distance from the
-          // FP64 plane and position, so that FP32 rounding cannot put the
-          // particle on the wrong side; its edges then run as any other
-          const double hh = 1.0 / A.h[a];
-          const double* st = A.site + 3 * c;
-          const double4_32a G = A.face64[f0 + fi];
-          const double rs = G.w * hh - (G.x * ((A.x[a] - st[0]) * hh) + G.y * ((A.y[a] - st[1]) * hh) +
-                                        G.z * ((A.z[a] - st[2]) * hh));
-          fin = rs >= 0.0;
-          r0 = (float)fabs(rs);
-          if (COUNT) ++n64;
+    // the block loop compiled twice: shared-memory face records (STAGED)
+    // or global ones, so that each reads its own memory space
+    auto blocks = [&](auto stag) {
+      constexpr bool STAGED = decltype(stag)::value;
+      const int64_t pb = item.lo, pe = item.lo + item.cnt;
+      for (int64_t p0 = pb; p0 < pe; p0 += 32) {
+        const int64_t p = p0 + lane;
+        const bool active = p < pe;
+        float yx = 0.f, yy = 0.f, yz = 0.f, hinv = 0.f;
+        int32_t a = 0;
+        if (active) {
+          a = A.pair_idx[p];
+          pair_frame(A, a, sx, sy, sz, yx, yy, yz, hinv);
         }
-        inside = inside && fin;
-        if (inrange) {
-          // the face's bounding sphere wholly beyond the support: nothing to add
-          const float4 Q = staged ? M.fsp[fi] : fsph[f0 + fi];
-          const float dx = yx - Q.x * hinv, dy = yy - Q.y * hinv, dz = yz - Q.z * hinv;
-          const float rr = 2.f + Q.w * hinv;
-          if (dx * dx + dy * dy + dz * dz >= rr * rr * 1.00001f) inrange = false;
-        }
-        const unsigned mn = __ballot_sync(FULL, inrange);
-        if (mn) {
-          const int nn = __popc(mn), rank = __popc(mn & lt);
-          const float c0f = wedge::c0_of(r0);
-          const unsigned tag = (unsigned)lane | (fin ? 32u : 0u);
-          for (int k = kb; k < ke; ++k) {
-            if (inrange)
-              M.cmb[cntc + rank] = make_uint4(__float_as_uint(r0), __float_as_uint(c0f), (unsigned)k * EDGE_STRIDE, tag);
-            cntc += nn;
-            if (cntc >= 32) {
-              cntc -= 32;
-              edge_round<COUNT>(M, ecell, cntc, 32, cnt0, cnt1, n_in, n_mid, wc, n_split, n_out);
+        M.py[0][lane] = make_float4(yx, yx, yy, yy);
+        M.py[1][lane] = make_float4(yz, yz, hinv, hinv);
+        bool inside = true;
+        int cntc = 0, cnt0 = 0, cnt1 = 0;  // stack heights (warp-uniform)
+        __syncwarp();
+        int kb = 0;
+        for (int fi = 0; fi < nf; ++fi) {
+          const float4 F = STAGED ? M.fpl[fi] : face[f0 + fi];
+          const int ke = STAGED ? M.fend[fi] : (int)(A.fvo[f0 + fi + 1] - l0);
+          const float r0s = face_r0s(F, yx, yy, yz, hinv);
+          bool fin = r0s >= 0.f;
+          float r0 = fabsf(r0s);
+          bool inrange = active && r0 < 2.f;
+          if (COUNT && active) wc.faces++;
+          if (inrange && r0 < TAU) {
+            // the plane passes within TAU h: its side and distance from the
+            // FP64 plane and position, so that FP32 rounding cannot put the
+            // particle on the wrong side; its edges then run as any other
+            const double hh = 1.0 / A.h[a];
+            const double* st = A.site + 3 * c;
+            const double4_32a G = A.face64[f0 + fi];
+            const double rs = G.w * hh - (G.x * ((A.x[a] - st[0]) * hh) + G.y * ((A.y[a] - st[1]) * hh) +
+                                          G.z * ((A.z[a] - st[2]) * hh));
+            fin = rs >= 0.0;
+            r0 = (float)fabs(rs);
+            if (COUNT) ++n64;
+          }
+          inside = inside && fin;
+          if (inrange) {
+            // the face's bounding sphere wholly beyond the support: nothing to add
+            const float4 Q = STAGED ? M.fsp[fi] : fsph[f0 + fi];
+            const float dx = yx - Q.x * hinv, dy = yy - Q.y * hinv, dz = yz - Q.z * hinv;
+            const float rr = 2.f + Q.w * hinv;
+            if (dx * dx + dy * dy + dz * dz >= rr * rr * 1.00001f) inrange = false;
+          }
+          const unsigned mn = __ballot_sync(FULL, inrange);
+          if (mn) {
+            const int nn = __popc(mn), rank = __popc(mn & lt);
+            const float c0f = wedge::c0_of(r0);
+            const unsigned tag = (unsigned)lane | (fin ? 32u : 0u);
+            for (int k = kb; k < ke; ++k) {
+              if (inrange)
+                M.cmb[cntc + rank] = make_uint4(__float_as_uint(r0), __float_as_uint(c0f), (unsigned)k * EDGE_STRIDE, tag);
+              cntc += nn;
+              if (cntc >= 32) {
+                cntc -= 32;
+                edge_round<COUNT>(M, ecell, cntc, 32, cnt0, cnt1, n_in, n_mid, wc, n_split, n_out);
+              }
             }
           }
+          kb = ke;
         }
-        kb = ke;
+        // what is left: fewer than 32 records, then fewer than 32 pieces of each kind
+        if (cntc) edge_round<COUNT>(M, ecell, 0, cntc, cnt0, cnt1, n_in, n_mid, wc, n_split, n_out);
+        if (cnt0 || cnt1) {
+          int cnt2 = 0;
+          unsigned n_st = 0;
+          drain<float, true>(S, cnt0, cnt1, cnt2, true, n_in, n_mid, n_st);
+        }
+        __syncwarp();
+        float comp;
+        const float rs = take_row(S.col, lane, comp);
+        if (active) {
+          const double f = (inside ? 1.0 : 0.0) + ((double)rs - (double)comp);
+          if (A.frac) A.frac[p] = f;
+          macc += A.m[a] * f;
+        }
+        __syncwarp();
       }
-      // what is left: fewer than 32 records, then fewer than 32 pieces of each kind
-      if (cntc) edge_round<COUNT>(M, ecell, 0, cntc, cnt0, cnt1, n_in, n_mid, wc, n_split, n_out);
-      if (cnt0 || cnt1) {
-        int cnt2 = 0;
-        unsigned n_st = 0;
-        drain<float, true>(S, cnt0, cnt1, cnt2, true, n_in, n_mid, n_st);
-      }
-      __syncwarp();
-      float comp;
-      const float rs = take_row(S.col, lane, comp);
-      if (active) {
-        const double f = (inside ? 1.0 : 0.0) + ((double)rs - (double)comp);
-        if (A.frac) A.frac[p] = f;
-        macc += A.m[a] * f;
-      }
-      __syncwarp();
-    }
+    };
+    if (staged) blocks(std::true_type{}); else blocks(std::false_type{});
     for (int o = 16; o > 0; o >>= 1) macc += __shfl_down_sync(FULL, macc, o);
     if (lane == 0) A.partial[it] = macc;
     __syncwarp();

@@ -39,7 +39,7 @@ struct PreparedGrid {
   float4* face32 = nullptr;          // same, FP32
   float4* fsph32 = nullptr;          // per face: bounding-sphere centre (site-relative) and radius, FP32
   double* edge64 = nullptr;          // EDGE_STRIDE doubles per loop entry (site-relative); FP64 contexts
-  float* edge32 = nullptr;           // EDGE_STRIDE floats per loop entry; mixed contexts
+  float* edge32 = nullptr;           // EDGE_STRIDE floats per loop entry, interleaved (m.x, t.x, m.y, t.y), (m.z, t.z, a_A, a_B), (delta); mixed contexts
   double* site = nullptr;            // [3*ncell]
   double* vol = nullptr;             // [ncell]
   double* rad = nullptr;             // [ncell] largest vertex distance from the site

@@ -138,9 +138,9 @@ __global__ void __launch_bounds__(NW * 32, MINB) pair_integrals_table(BatchArgs 
           for (int k = kb; k < ke; ++k) {
             const float4 E0 = ecell[3 * k], E1 = ecell[3 * k + 1], E2 = ecell[3 * k + 2];
             if (!inrange) continue;
-            const float R0s = (E0.x * yx + E0.y * yy + E0.z * yz) - E0.w * hinv;
-            const float base = E1.x * yx + E1.y * yy + E1.z * yz;
-            const float lo = E1.w * hinv - base, hi = E2.x * hinv - base;
+            const float R0s = (E0.x * yx + E0.z * yy + E1.x * yz) - E2.x * hinv;
+            const float base = E0.y * yx + E0.w * yy + E1.y * yz;
+            const float lo = E1.z * hinv - base, hi = E1.w * hinv - base;
             const float kp = kprime_table(tab, tn1, r0, fabsf(R0s), lo, hi, inv_span, c0);
             const float y = ((R0s >= 0.f) == fin ? kp : -kp) - cmp;
             const float t = acc + y;

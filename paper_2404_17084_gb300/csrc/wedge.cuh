@@ -80,12 +80,14 @@ struct WorkCount {
 // iteratively reweighted least squares on Chebyshev nodes (relative error
 // 1.2e-8 in exact arithmetic, ~2 ulp evaluated in FP32), then
 // atan2 = (pi/2 - atan) when |y| > |x|, (pi - .) when x is negative (sign
-// bit, so that atan2(+-0, -0) = +-pi), sign of y.  The quotient uses the
-// hardware reciprocal (2 ulp).
+// bit, so that atan2(+-0, -0) = +-pi), sign of y; the two corrections are
+// fused multiply-adds with sign factors +-1 (one rounding each, as a
+// subtraction).  The quotient uses the hardware reciprocal (2 ulp).
 __device__ __forceinline__ float atan2_fast(float y, float x) {
   const float ax = fabsf(x), ay = fabsf(y);
-  const float mx = fmaxf(ax, ay), mn = fminf(ax, ay);
-  const float t = mx > 0.f ? __fdividef(mn, mx) : 0.f;
+  // (the floor FLT_MIN only keeps 0/0 out: t = 0 when x = y = 0)
+  const float mx = fmaxf(fmaxf(ax, ay), 1.17549435e-38f), mn = fminf(ax, ay);
+  const float t = __fdividef(mn, mx);
   const float u = t * t;
   float p = 0.0028498810715973377f;
   p = fmaf(p, u, -0.0160685945302248f);
@@ -96,9 +98,12 @@ __device__ __forceinline__ float atan2_fast(float y, float x) {
   p = fmaf(p, u, 0.1999261975288391f);
   p = fmaf(p, u, -0.3333307206630707f);
   p = fmaf(p, u, 1.0f);
+  // the octant and half-plane corrections as sign multiplies:
+  // r <- pi/2 - r when |y| > |x| (s1 = -1), r <- pi - r when x is negative
+  const float s1 = copysignf(1.f, ax - ay), s2 = copysignf(1.f, x);
   float r = t * p;
-  r = ay > ax ? 1.57079632679489662f - r : r;
-  r = __float_as_int(x) < 0 ? 3.14159265358979324f - r : r;
+  r = fmaf(r, s1, fmaf(-0.785398163397448310f, s1, 0.785398163397448310f));
+  r = fmaf(r, s2, fmaf(-1.57079632679489662f, s2, 1.57079632679489662f));
   return copysignf(r, y);
 }
 
