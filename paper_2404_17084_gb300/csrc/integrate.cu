@@ -77,8 +77,8 @@ __device__ __forceinline__ int warp_excl2(int v, int* tot) {
 // the pairs the two-lane arithmetic takes sit in adjacent registers.
 __device__ __forceinline__ void load_edge(const float* E, float& e0, float& e1, float& e2, float& e3, float& e4,
                                           float& e5, float& e6, float& e7, float& e8) {
-  const float4 a = reinterpret_cast<const float4*>(E)[0], b = reinterpret_cast<const float4*>(E)[1];
-  const float4 c = reinterpret_cast<const float4*>(E)[2];
+  const float4 a = __ldg(reinterpret_cast<const float4*>(E)), b = __ldg(reinterpret_cast<const float4*>(E) + 1);
+  const float4 c = __ldg(reinterpret_cast<const float4*>(E) + 2);
   e0 = a.x; e4 = a.y; e1 = a.z; e5 = a.w; e2 = b.x; e6 = b.y; e7 = b.z; e8 = b.w; e3 = c.x;
 }
 __device__ __forceinline__ void load_edge(const double* E, double& e0, double& e1, double& e2, double& e3,
@@ -187,10 +187,10 @@ __device__ __forceinline__ float take_row(float (*col)[32], int o, float& comp) 
 // rounding explicit (no contraction left to the compiler).
 __device__ __forceinline__ void pair_frame(const SnapDesc& A, int32_t a, double sx, double sy, double sz, float& yx,
                                            float& yy, float& yz, float& hinv) {
-  hinv = __frcp_rn((float)A.h[a]);
-  yx = __fmul_rn((float)(A.x[a] - sx), hinv);
-  yy = __fmul_rn((float)(A.y[a] - sy), hinv);
-  yz = __fmul_rn((float)(A.z[a] - sz), hinv);
+  hinv = __frcp_rn((float)__ldg(A.h + a));
+  yx = __fmul_rn((float)(__ldg(A.x + a) - sx), hinv);
+  yy = __fmul_rn((float)(__ldg(A.y + a) - sy), hinv);
+  yz = __fmul_rn((float)(__ldg(A.z + a) - sz), hinv);
 }
 __device__ __forceinline__ float face_r0s(const float4& F, float yx, float yy, float yz, float hinv) {
   return __fsub_rn(__fmul_rn(F.w, hinv), __fmaf_rn(F.x, yx, __fmaf_rn(F.y, yy, __fmul_rn(F.z, yz))));
@@ -467,10 +467,12 @@ __device__ __forceinline__ void edge_round(MixWarp& M, const float* __restrict__
   const bool far = c2 >= 4.f, lt1 = c2 < 1.f;
   float s1, s2;
   {
+    // the breakpoints sqrt(4 - c^2), sqrt(1 - c^2): reciprocal square root
+    // and one Newton step y (3/2 - r y/2), both in two-lane arithmetic
     const f2 xs = f2{4.f - c2, 1.f - c2};
     const f2 r = f2{rsqrtf(xs.x), rsqrtf(xs.y)};
     const f2 y = wedge::mul2(xs, r);
-    const f2 q = wedge::fma2(wedge::mul2(wedge::sp(0.5f), r), wedge::fma2(f2{-y.x, -y.y}, y, xs), y);
+    const f2 q = wedge::mul2(y, wedge::fma2(wedge::mul2(wedge::sp(-0.5f), r), y, wedge::sp(1.5f)));
     s2 = far ? 0.f : q.x;
     s1 = lt1 ? q.y : 0.f;
   }
@@ -586,7 +588,7 @@ __global__ void __launch_bounds__(NW * 32, MINB) pair_integrals_mixed(BatchArgs 
         float yx = 0.f, yy = 0.f, yz = 0.f, hinv = 0.f;
         int32_t a = 0;
         if (active) {
-          a = A.pair_idx[p];
+          a = __ldg(A.pair_idx + p);
           pair_frame(A, a, sx, sy, sz, yx, yy, yz, hinv);
         }
         M.py[0][lane] = make_float4(yx, yx, yy, yy);

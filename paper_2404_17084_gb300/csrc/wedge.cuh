@@ -157,11 +157,12 @@ __device__ __forceinline__ T omega(T r0, T R0, T s, T U) {
 }
 
 // 4 pi G'_in (WANT_IN) and 120 pi G''_mid (WANT_MID) at s.
-template <typename T, bool WANT_IN, bool WANT_MID>
+// (WITH_L = false: the terms in L left out, for a caller that adds them itself)
+template <typename T, bool WANT_IN, bool WANT_MID, bool WITH_L = true>
 __device__ __forceinline__ void antider(T r0, T R0, T c2, T c, T s, T& gin, T& gmid) {
   const T U = xsqrt(c2 + s * s);
   const T Om = omega(r0, R0, s, U);
-  const T L = xasinh(s / c);
+  const T L = WITH_L ? xasinh(s / c) : T(0);
   const T r02 = r0 * r0;
   const T R0s = R0 * s;
   const T P2 = R0s;
@@ -236,7 +237,10 @@ __device__ __forceinline__ f2 add2(f2 a, f2 b) {
 __device__ __forceinline__ f2 sp(float v) { return f2{v, v}; }
 
 // The FP32 rule with the nodes +x_k and -x_k of each pair in one two-lane
-// operation: the same arithmetic per node as the scalar form above.
+// operation.  Per node it differs from the scalar form above in two places:
+// the Newton step is taken as y (3/2 - r y/2) (no negated operand; ~1.5 ulp
+// instead of ~1), and den carries + 1e-30 in its last FMA instead of a
+// floor (the same guard, see below).
 template <>
 __device__ __forceinline__ float mid_gl<float>(float r0, float R0, float c2, float lo, float hi) {
   const float gx[3] = {0.2386191860831969086305017f, 0.6612093864662645136613996f, 0.9324695142031520278123016f};
@@ -251,21 +255,21 @@ __device__ __forceinline__ float mid_gl<float>(float r0, float R0, float c2, flo
     const f2 s = add2(sp(ctr), f2{hg, -hg});
     const f2 s2 = mul2(s, s);
     const f2 u2 = add2(sp(c2), s2);
-    // square root from the reciprocal square root and one Newton step
+    // square root from the reciprocal square root
     const f2 r = f2{rsqrtf(u2.x), rsqrtf(u2.y)};
     const f2 y = mul2(u2, r);
-    const f2 e = fma2(f2{-y.x, -y.y}, y, u2);
-    const f2 U = fma2(mul2(sp(0.5f), r), e, y);
+    // one Newton step, y + r (u2 - y^2)/2 = y (3/2 - r y/2)
+    const f2 U = mul2(y, fma2(mul2(sp(-0.5f), r), y, sp(1.5f)));
     // p(U) = (2 - U)^5 (1 + U)
-    const f2 t = add2(sp(2.f), f2{-U.x, -U.y});
+    const f2 t = fma2(U, sp(-1.f), sp(2.f));
     const f2 t2 = mul2(t, t);
     const f2 t5 = mul2(mul2(t2, t2), t);
     const f2 pm = mul2(t5, add2(sp(1.f), U));
     const f2 num = fma2(sp(r0), pm, mul2(sp(-pr0), U));
-    const f2 den = mul2(U, add2(sp(R02), s2));
     // den = 0 only with R0 = 0 (and a node at the foot), where the panel's
-    // factor R0 makes the piece 0: a floor instead of a branch keeps q finite
-    const f2 q = f2{__fdividef(num.x, fmaxf(den.x, 1e-30f)), __fdividef(num.y, fmaxf(den.y, 1e-30f))};
+    // factor R0 makes the piece 0: 1e-30 added keeps q finite
+    const f2 den = fma2(U, add2(sp(R02), s2), sp(1e-30f));
+    const f2 q = f2{__fdividef(num.x, den.x), __fdividef(num.y, den.y)};
     acc = fma2(sp(gw[k]), q, acc);
   }
   return R0 * half * (acc.x + acc.y);
@@ -282,6 +286,27 @@ __device__ __forceinline__ T piece_inner(T r0, T R0, T lo, T hi) {
   antider<T, true, false>(r0, R0, c2, c, hi, g1, d);
   antider<T, true, false>(r0, R0, c2, c, lo, g0, d);
   return (g1 - g0) * T(INV_4PI);
+}
+
+// FP32: the L terms of both ends in one logarithm,
+//     L(hi) - L(lo) = ln(E(hi) / E(lo)),  E(x) = x + sqrt(c^2 + x^2),
+// with E(x) = c^2 / (sqrt(c^2 + x^2) - x) for x < 0 (no cancellation), and
+// L's coefficient in 4 pi G'_in, r0/10 (3/8 c^4 + r0^2 (c^2/2 + r0^2)) R0,
+// applied once.  The hardware logarithm's absolute error (~2e-7) times that
+// coefficient (< 0.2 for an inner piece, c^2 < 1) stays below 3e-9 per piece.
+template <>
+__device__ __forceinline__ float piece_inner<float>(float r0, float R0, float lo, float hi) {
+  const float c2 = r0 * r0 + R0 * R0;
+  float g1, g0, d;
+  antider<float, true, false, false>(r0, R0, c2, 0.f, hi, g1, d);
+  antider<float, true, false, false>(r0, R0, c2, 0.f, lo, g0, d);
+  const float U1 = xsqrt(c2 + hi * hi), U0 = xsqrt(c2 + lo * lo);
+  const float E1 = hi >= 0.f ? hi + U1 : __fdividef(c2, U1 - hi);
+  const float E0 = lo >= 0.f ? lo + U0 : __fdividef(c2, U0 - lo);
+  const float dL = __logf(__fdividef(E1, E0));
+  const float r02 = r0 * r0;
+  const float kL = 0.1f * r0 * R0 * (0.375f * c2 * c2 + r02 * (0.5f * c2 + r02));
+  return (g1 - g0 + kL * dL) * float(INV_4PI);
 }
 
 // Mixed build: a middle interval straddles the foot s = 0 only when it is no
