@@ -157,9 +157,8 @@ OPS = {
 
 # DRAM traffic of the mixed pair-integral kernel per pair:
 # dram__bytes_read.sum + dram__bytes_write.sum of one ncu capture of the 2^16
-# clumpy case (385 MB for 7,813,809 pairs; profiles/pair_integrals_mixed_clumpy_65536.md),
-# scaled to a launch by its pair count (the kernel streams the same per-pair
-# data at any size).  It belongs to the kernel as captured: set it to None
+# clumpy case (385 MB for 7,813,809 pairs), scaled to a launch by its pair
+# count (the kernel streams the same per-pair data at any size).  It belongs to the kernel as captured: set it to None
 # when the kernel changes.
 INTEGRAL_DRAM_BYTES_PER_PAIR = 49.3
 # DRAM bytes per pair of one inverse-mapping sum (inv_apply): 451.2 MB read +
