@@ -204,6 +204,28 @@ def algorithmic_ops(work: dict, terms: int, mixed: bool):
     return f, m
 
 
+def alu_roofline(L, local, f32, mufu, launch_ms, sm_count, f_clk):
+    """The integral kernel's roofline: its time bound is the slower of its
+    FP32 ops at the measured FP32 FMA issue rate and its MUFU ops at the
+    measured MUFU rate (map_device_peaks, this run); frac = bound / launch
+    time, achieved = frac x the FP32 rate.  Falls back to the nominal rates,
+    said so."""
+    nominal_ops = sm_count * 128 * f_clk * 1e6       # FP32 lane-ops per second
+    try:
+        meas = L.map_device_peaks(local)
+        peak_ops, peak_mufu = meas["ffma"], meas["mufu"]
+        source = ("measured: FP32 FMA and MUFU issue microbenchmarks (map_device_peaks), "
+                  f"nominal {nominal_ops / 1e12:.2f} = {sm_count} SMs x 128 lanes x {f_clk:.0f} MHz")
+    except Exception as exc:  # the nominal rates, said so
+        meas = None
+        peak_ops, peak_mufu = nominal_ops, nominal_ops / 8.0
+        source = f"nominal (microbenchmark failed: {exc}): {sm_count} SMs x 128 FP32 lanes x {f_clk:.0f} MHz"
+    bound_s = max(f32 / peak_ops, mufu / peak_mufu)
+    frac = bound_s / (launch_ms * 1e-3)
+    return {"achieved": frac * peak_ops / 1e12, "peak": peak_ops / 1e12, "frac": frac, "peak_source": source,
+            "measured_peaks_Tops": (None if meas is None else {k: round(v / 1e12, 3) for k, v in meas.items()})}
+
+
 def oracle_errors(g, p, h, mass_gpu, ncells, seed):
     """Per-cell error of a GPU result against the FP64 oracle, run on the same
     particles and the GPU's own h, on a seeded random sample of cells (the
@@ -363,21 +385,7 @@ def run_ours(args):
     peaks = load_peaks()
     sm_count = torch.cuda.get_device_properties(dev).multi_processor_count
     f_clk = (clocks or {}).get("sm_max_mhz") or peaks.get("sm_max_mhz", 2070.0)
-    nominal_ops = sm_count * 128 * f_clk * 1e6       # FP32 lane-ops per second
-    # measured issue rates of the FP32 FMA and special-function pipes; the
-    # kernel's bound is the slower of its two op counts at those rates
-    try:
-        meas = L.map_device_peaks(local)
-        peak_ops, peak_mufu = meas["ffma"], meas["mufu"]
-        peak_source = ("measured: FP32 FMA and MUFU issue microbenchmarks (map_device_peaks), "
-                       f"nominal {nominal_ops / 1e12:.2f} = {sm_count} SMs x 128 lanes x {f_clk:.0f} MHz")
-    except Exception as exc:  # the nominal rates, said so
-        meas = None
-        peak_ops, peak_mufu = nominal_ops, nominal_ops / 8.0
-        peak_source = f"nominal (microbenchmark failed: {exc}): {sm_count} SMs x 128 FP32 lanes x {f_clk:.0f} MHz"
-    bound_s = max(f32 / peak_ops, mufu / peak_mufu)  # seconds at the peaks
-    frac = bound_s / (integ_ms * 1e-3)
-    achieved = frac * peak_ops
+    roof = alu_roofline(L, local, f32, mufu, integ_ms, sm_count, f_clk)
     line = {
         "metric": "particle-cell pair integrals/sec at 1 GB300 (mixed vs FP64 form) + p50/p99 latency",
         "value": n_pairs * world / (ms * 1e-3),
@@ -397,14 +405,12 @@ def run_ours(args):
         "phases_ms": {k: round(v, 3) for k, v in phases.items()},
         "fp64": fp64,
         "table_variant": table,
-        "roofline": {"bound": "alu", "kernel": "pair_integrals_mixed", "achieved": achieved / 1e12,
-                     "peak": peak_ops / 1e12, "unit": "Tops/s (FP32 issue slots)", "frac": frac,
+        "roofline": {"bound": "alu", "kernel": "pair_integrals_mixed", "achieved": roof["achieved"],
+                     "peak": roof["peak"], "unit": "Tops/s (FP32 issue slots)", "frac": roof["frac"],
                      "traffic": (None if INTEGRAL_DRAM_BYTES_PER_PAIR is None
                                  else INTEGRAL_DRAM_BYTES_PER_PAIR * n_pairs),
                      "ops_fp32": int(f32), "ops_mufu": int(mufu), "launch_ms": integ_ms,
-                     "peak_source": peak_source,
-                     "measured_peaks_Tops": (None if meas is None else
-                                             {k: round(v / 1e12, 3) for k, v in meas.items()})},
+                     "peak_source": roof["peak_source"], "measured_peaks_Tops": roof["measured_peaks_Tops"]},
         "e2e": e2e,
         "latency_ms": (None if serving is None else
                        {**serving["loads"]["0.9"]["latency_ms"], "at": "90% of the serving capacity",
@@ -532,8 +538,7 @@ def run_batch(args):
     f32, mufu = algorithmic_ops(work, terms, True)
     sm_count = torch.cuda.get_device_properties(dev).multi_processor_count
     f_clk = (clocks or {}).get("sm_max_mhz") or 2070.0
-    peak_ops = sm_count * 128 * f_clk * 1e6
-    achieved = max(f32, 8.0 * mufu) / (integ_ms * 1e-3)
+    roof = alu_roofline(L, local, f32, mufu, integ_ms, sm_count, f_clk)
     n_part = int(sum(p.n for p, _ in snaps))
     line = {
         "metric": "particle-cell pair integrals/sec at 1 GB300 (mixed vs FP64 form) + p50/p99 latency",
@@ -559,11 +564,12 @@ def run_batch(args):
                   "host_input_generation_s": gen_s},
         "accuracy_vs_oracle": batch_err,
         "roofline": {"bound": "alu", "kernel": "pair_integrals_mixed (batched launch)",
-                     "achieved": achieved / 1e12, "peak": peak_ops / 1e12, "unit": "Tops/s (FP32 issue slots)",
-                     "frac": achieved / peak_ops,
+                     "achieved": roof["achieved"], "peak": roof["peak"], "unit": "Tops/s (FP32 issue slots)",
+                     "frac": roof["frac"],
                      "traffic": (None if INTEGRAL_DRAM_BYTES_PER_PAIR is None
                                  else INTEGRAL_DRAM_BYTES_PER_PAIR * int(st.n_pairs)),
-                     "launch_ms": integ_ms},
+                     "ops_fp32": int(f32), "ops_mufu": int(mufu), "launch_ms": integ_ms,
+                     "peak_source": roof["peak_source"], "measured_peaks_Tops": roof["measured_peaks_Tops"]},
         "e2e": None,
         "gpu_launches": int((l1 - l0) // max(args.steps, 1) * args.steps),
         "clocks": clocks,

@@ -144,11 +144,11 @@ struct map_ctx {
   std::vector<DevBuf> grid_pool;       // buffers of released grids, reused by later uploads
   // workspace
   DevBuf ws_tree[32];
-  DevBuf ws_pairs[14];
+  DevBuf ws_pairs[15];
   DevBuf ws_misc[8];
   DevBuf ws_grid[3];                   // grid preparation: face -> cell, per-face volume term and radius^2
   DevBuf ws_vor[22];                   // grid construction: buckets, cell slots, CSR arrays
-  DevBuf ws_inv[11];                   // particle-major copy of the pair list (inverse mapping, Eq. 4)
+  DevBuf ws_inv[13];                   // particle-major copy of the pair list (inverse mapping, Eq. 4)
   DevBuf cub_tmp;
   DevTree tree;
   int64_t node_cap0 = 0;  // > 0: octree node arrays start at this capacity (a context whose workspace is fixed)
@@ -166,8 +166,9 @@ struct map_ctx {
   // mapping after the call
   bool inv_ready = false;
   const int64_t* inv_off = nullptr;   // [last_npart+1]
-  const int32_t* inv_cell = nullptr;
+  const int32_t* inv_cell = nullptr;  // per entry: the Morton rank of its cell's site
   const double* inv_frac = nullptr;
+  const int32_t* inv_morton = nullptr; // [last_ncell]: cells in Morton order of their sites
   const int32_t* inv_order = nullptr; // particles by decreasing entry count
   const int64_t* inv_nlong = nullptr; // device: particles summed by a whole warp
   struct PairItem* items = nullptr;  // work items of the pair-integral kernel

@@ -14,6 +14,14 @@
 // one at a time in ascending cell order (acc <- RN(acc + v_i f_ai), one
 // rounding per term), so the result equals that sequential FP64 sum bit for
 // bit.
+//
+// Locality of the cell-value gather: the copy stores, per entry, the Morton
+// rank of its cell's site (the order the pair walk visits cells in) instead
+// of the cell index, and every call first permutes the caller's cell values
+// into that order (one coalesced write per cell).  A particle's cells lie
+// within its support, so their ranks are close and the gathers of one
+// particle's entries share 32-byte sectors; the terms, their values and
+// their order are unchanged.
 #include <cub/cub.cuh>
 
 #include "internal.cuh"
@@ -33,15 +41,28 @@ __global__ void inv_pack(int64_t nc, const int64_t* __restrict__ off, unsigned l
   }
 }
 
-// sorted entry k: its cell and f_ai
+// rank[morton[k]] = k: the Morton rank of every cell
+__global__ void inv_rank(int64_t nc, const int32_t* __restrict__ morton, int32_t* __restrict__ rank) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < nc; k += stride) rank[morton[k]] = (int32_t)k;
+}
+
+// sorted entry k: the Morton rank of its cell, and f_ai
 __global__ void inv_gather(int64_t np, const unsigned long long* __restrict__ val, const double* __restrict__ frac,
-                           int32_t* __restrict__ cell, double* __restrict__ f) {
+                           const int32_t* __restrict__ rank, int32_t* __restrict__ cell, double* __restrict__ f) {
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < np; k += stride) {
     const unsigned long long v = val[k];
-    cell[k] = (int32_t)(v >> 32);
+    cell[k] = rank[v >> 32];
     f[k] = frac[v & 0xffffffffull];
   }
+}
+
+// the caller's cell values in Morton order: out[k] = v[morton[k]]
+__global__ void inv_permute(int64_t nc, const int32_t* __restrict__ morton, const double* __restrict__ v,
+                            double* __restrict__ out) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < nc; k += stride) out[k] = __ldg(v + morton[k]);
 }
 
 // ioff[a] = number of entries whose particle index is below a (a = 0..n)
@@ -228,7 +249,16 @@ int build_index(map_ctx* ctx, cudaStream_t s) {
     CUDA_TRY(cub::DeviceRadixSort::SortPairs(nullptr, tb, ctx->pair_idx, key_s, val, val_s, np, 0, nb, s));
     MAP_TRY(ctx_ensure(ctx, ctx->cub_tmp, tb));
     CUDA_TRY(cub::DeviceRadixSort::SortPairs(ctx->cub_tmp.p, tb, ctx->pair_idx, key_s, val, val_s, np, 0, nb, s));
-    inv_gather<<<g, 256, 0, s>>>(np, val_s, ctx->pair_frac, cell, f); ++ctx->launches;
+    // the pair walk's Morton order of the cells, sorted by pairs_build with
+    // the list this copy is made from (a buffer no other step writes)
+    if (ctx->ws_pairs[14].cap < (size_t)nc * sizeof(int32_t)) return MAP_EINVAL;
+    const int32_t* morton = static_cast<const int32_t*>(ctx->ws_pairs[14].p);
+    int32_t* rank;
+    MAP_TRY(ensure_t(ctx, ctx->ws_inv[11], nc, &rank));
+    inv_rank<<<g, 256, 0, s>>>(nc, morton, rank); ++ctx->launches;
+    CUDA_TRY(cudaGetLastError());
+    ctx->inv_morton = morton;
+    inv_gather<<<g, 256, 0, s>>>(np, val_s, ctx->pair_frac, rank, cell, f); ++ctx->launches;
     CUDA_TRY(cudaGetLastError());
     inv_bounds<<<g, 256, 0, s>>>(np, n, key_s, ioff); ++ctx->launches;
     CUDA_TRY(cudaGetLastError());
@@ -283,8 +313,17 @@ extern "C" int map_cells_to_particles(map_ctx* ctx, const double* cell_value, do
   CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, inv_apply, INV_THREADS, 0));
   const int64_t cap = (int64_t)ctx->sm_count * (per_sm > 0 ? per_sm : 1);
   if (blocks > cap) blocks = cap;
+  const double* cv = cell_value;
+  if (ctx->inv_cell) {
+    const int64_t nc = ctx->last_ncell;
+    double* cv_m;
+    MAP_TRY(ensure_t(ctx, ctx->ws_inv[12], nc, &cv_m));
+    inv_permute<<<(unsigned)ctx->sm_count * 8, 256, 0, s>>>(nc, ctx->inv_morton, cell_value, cv_m); ++ctx->launches;
+    CUDA_TRY(cudaGetLastError());
+    cv = cv_m;
+  }
   inv_apply<<<(unsigned)blocks, INV_THREADS, 0, s>>>(n, ctx->inv_nlong, ctx->inv_order, ctx->inv_off, ctx->inv_cell,
-                                                      ctx->inv_frac, cell_value, particle_value);
+                                                      ctx->inv_frac, cv, particle_value);
   ++ctx->launches;
   CUDA_TRY(cudaGetLastError());
   return MAP_OK;

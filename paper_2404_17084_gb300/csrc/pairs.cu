@@ -415,7 +415,7 @@ int pairs_build(map_ctx* ctx, const PreparedGrid* g, cudaStream_t s, const PairB
   MAP_TRY(ensure_t(ctx, ctx->ws_pairs[4], nc, &k_in));
   MAP_TRY(ensure_t(ctx, ctx->ws_pairs[5], nc, &k_out));
   MAP_TRY(ensure_t(ctx, ctx->ws_pairs[6], nc, &o_in));
-  MAP_TRY(ensure_t(ctx, ctx->ws_pairs[7], nc, &order));
+  MAP_TRY(ensure_t(ctx, ctx->ws_pairs[14], nc, &order));  // kept for the inverse mapping's gather order
   site_keys<<<nblk(nc, 256), 256, 0, s>>>(nc, g->site, k_in, o_in); ++ctx->launches;
   CUDA_TRY(cudaGetLastError());
   size_t tb = 0;
