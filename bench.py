@@ -158,13 +158,12 @@ OPS = {
 # DRAM traffic of the mixed pair-integral kernel per pair:
 # dram__bytes_read.sum + dram__bytes_write.sum of one ncu capture of the 2^16
 # clumpy case (385 MB for 7,813,809 pairs), scaled to a launch by its pair
-# count (the kernel streams the same per-pair data at any size).  It belongs to the kernel as captured: set it to None
-# when the kernel changes.
+# count (the kernel streams the same per-pair data at any size).  It belongs
+# to the kernel as captured: set it to None when the kernel changes.
 INTEGRAL_DRAM_BYTES_PER_PAIR = 49.3
-# DRAM bytes per pair of one inverse-mapping sum (inv_apply): 451.2 MB read +
-# written for 32,168,427 pairs in ncu on the 2^18 clumpy snapshot, scaled by
-# pair count like the figure above; None once the kernel changes.
-INVERSE_DRAM_BYTES_PER_PAIR = 14.03
+# DRAM bytes per pair of one inverse-mapping sum (inv_apply): None -- the
+# kernel now gathers in Morton order, and no capture of it has been taken.
+INVERSE_DRAM_BYTES_PER_PAIR = None
 
 
 def counted_work(L, torch, precision, device, grids, dev, parts):
