@@ -500,6 +500,7 @@ def run_batch(args):
     sampler.start()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     integ = []
+    g0 = L.map_batch_graph_stats(ctx)
     e0.record()
     for _ in range(args.steps):
         step()
@@ -511,6 +512,12 @@ def run_batch(args):
     st = L.map_get_stats(ctx)
     work, l1 = L.map_get_work(ctx)
     chosen, tune_ms = L.map_get_autotune(ctx)
+    g1 = L.map_batch_graph_stats(ctx)
+    phases = L.map_get_timing(ctx)
+    graph = {"captures": g1[0] - g0[0], "replays": g1[1] - g0[1], "fallbacks": g1[2] - g0[2],
+             "note": "map_batch calls of the timed steps that replayed the whole captured step (validation, "
+                     "octrees, pair lists, work items, integral launch, sums) as one graph launch",
+             "phases_ms_last_step": {k: round(v, 3) for k, v in phases.items()}}
     integ_ms = float(np.mean(integ))
     batch_mass = [mm.cpu().numpy() for mm in mass]
     # the same snapshots one call at a time (mapping only, h as solved above)
@@ -560,6 +567,7 @@ def run_batch(args):
         "batch": {"integrals_ms": integ_ms, "integral_launch_pairs_per_s": st.n_pairs / (integ_ms * 1e-3),
                   "autotune": autotune_table(L, chosen, tune_ms),
                   "one_call_per_snapshot_mapping_s": single_s, "batched_equals_single": bool(same),
+                  "graph": graph,
                   "host_input_generation_s": gen_s},
         "accuracy_vs_oracle": batch_err,
         "roofline": {"bound": "alu", "kernel": "pair_integrals_mixed (batched launch)",

@@ -300,7 +300,25 @@ int map_get_timing(map_ctx* ctx, float* ms);
  * the persistent kernel, whose device work queue hands out the cells of every
  * snapshot, largest pair count first.  That launch, with its descriptor
  * upload and the per-snapshot sums, is captured in a CUDA graph and replayed
- * while the batch's pointers and sizes are unchanged.  totals (optional,
+ * while the batch's pointers and sizes are unchanged.
+ *
+ * The whole step as one graph: after a call that ran eagerly (a context's
+ * first call, or one whose inputs moved), the context captures the entire
+ * step -- per snapshot the particle validation, the octree, the pair list
+ * and the work items (built without host reads, on the workers' streams,
+ * into buffers a quarter larger than that call's lists), then the integral
+ * launch and the sums.  A later call with the same particle buffers (x, y,
+ * z, m, h and n), grids, outputs and launch choices replays it: one graph
+ * launch, then one read of three device words (the pair and item totals and
+ * a flag), so such a call returns once its results are complete.  Values in
+ * the buffers may change between calls (new positions, h, masses): the
+ * replay computes from them.  A replay whose lists outgrow their buffers
+ * skips its integral launch and the call runs eagerly instead (and captures
+ * anew); invalid particles give MAP_EINVAL.  Releasing a grid drops the
+ * graph.  Counting contexts (count_work) never capture.  Results of a replay
+ * equal those of the eager step on the same inputs bit for bit.
+ *
+ * totals (optional,
  * device, nsnap doubles) receives sum_i M_i per snapshot.  Per-pair fractions
  * are not kept (map_get_pairs / map_copy_pairs then report no list);
  * map_get_stats covers the whole batch.  The batch runs on a stream of the
@@ -317,6 +335,11 @@ int map_batch(map_ctx* ctx, int nsnap, const map_particles* parts, const int* gr
  * use for the mixed build, ms[0..*nvariants) = each trial's time on the
  * tuning call's inputs (0 when not run).  ms must hold at least 32 floats. */
 int map_get_autotune(map_ctx* ctx, int* chosen, float* ms, int* nvariants);
+
+/* How map_batch's whole-step graph has been used by this context: captures,
+ * replays, and replays that fell back to the eager step (lists outgrew their
+ * buffers).  Any pointer may be NULL.  Errors: MAP_EINVAL (ctx NULL). */
+int map_batch_graph_stats(map_ctx* ctx, int64_t* captures, int64_t* replays, int64_t* fallbacks);
 
 /* ------------------------------------------------------------ serving */
 

@@ -140,11 +140,13 @@ _lib.map_batch.argtypes = [_P, ctypes.c_int, ctypes.POINTER(map_particles), ctyp
                            ctypes.POINTER(map_outputs), _P, _P]
 _lib.map_get_autotune.argtypes = [_P, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_float),
                                   ctypes.POINTER(ctypes.c_int)]
+_lib.map_batch_graph_stats.argtypes = [_P, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64),
+                                       ctypes.POINTER(ctypes.c_int64)]
 for _name in ("map_init", "map_grid_upload", "map_grid_release", "map_grid_volumes", "map_grid_build",
               "map_grid_sizes", "map_grid_copy", "map_particles_to_cells",
               "map_get_pairs", "map_copy_pairs", "map_cells_to_particles", "map_get_stats", "map_get_work",
               "map_get_timing", "solve_h", "build_pseudo_particles", "build_pseudo_particles_walk", "map_batch",
-              "map_get_autotune", "solve_h_batch"):
+              "map_get_autotune", "solve_h_batch", "map_batch_graph_stats"):
     getattr(_lib, _name).restype = ctypes.c_int
 
 
@@ -263,6 +265,13 @@ def map_get_autotune(ctx):
     ms = (ctypes.c_float * 32)()
     _check(_lib.map_get_autotune(ctx, ctypes.byref(c), ms, ctypes.byref(nv)), "map_get_autotune")
     return c.value, [ms[i] for i in range(nv.value)]
+
+
+def map_batch_graph_stats(ctx):
+    """(captures, replays, fallbacks) of map_batch's whole-step graph."""
+    v = [ctypes.c_int64() for _ in range(3)]
+    _check(_lib.map_batch_graph_stats(ctx, *[ctypes.byref(x) for x in v]), "map_batch_graph_stats")
+    return tuple(x.value for x in v)
 
 
 # ---------------------------------------------------------------- serving

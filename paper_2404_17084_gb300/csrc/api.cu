@@ -22,6 +22,15 @@ inline cudaStream_t S(void* s) { return reinterpret_cast<cudaStream_t>(s); }
 
 }  // namespace
 
+int validate_enqueue(map_ctx* ctx, const map_particles* p, bool need_m, bool need_h, unsigned long long* status,
+                     cudaStream_t s) {
+  const int tpb = 256;
+  validate_particles<<<(unsigned)((p->n + tpb - 1) / tpb), tpb, 0, s>>>(p->n, p->x, p->y, p->z, need_m ? p->m : nullptr,
+                                                                        need_h ? p->h : nullptr, status); ++ctx->launches;
+  CUDA_TRY(cudaGetLastError());
+  return MAP_OK;
+}
+
 int check_particles(map_ctx* ctx, const map_particles* p, bool need_m, bool need_h, cudaStream_t s) {
   if (!p || p->n <= 0 || !p->x || !p->y || !p->z) return MAP_EINVAL;
   if (need_m && !p->m) return MAP_EINVAL;
@@ -175,6 +184,10 @@ void map_destroy(map_ctx* ctx) {
   // wait for the context's own work only (other contexts keep running): its
   // workers, its batch stream and the end of its last call -- an event, as
   // the caller's stream may no longer exist; then return the workspace
+  if (ctx->bstream) {
+    cudaStreamSynchronize(ctx->bstream);
+    batch_graph_drop(ctx);
+  }
   destroy_workers(ctx);
   if (ctx->bstream) cudaStreamSynchronize(ctx->bstream);
   if (ctx->ord_ev) cudaEventSynchronize(ctx->ord_ev);
@@ -271,6 +284,7 @@ int map_grid_release(map_ctx* ctx, int handle) {
   // no wait: the buffers go to the context's pool, and the calls that reuse
   // or free them are ordered after this context's earlier work (ctx_enter)
   PreparedGrid* g = ctx->grids[handle];
+  if (ctx->bgraph.exec) batch_graph_drop(ctx);  // its graph may read this grid
   grid_recycle(ctx, g);  // kept for the next upload; freed by map_destroy or when room runs out
   delete g;
   ctx->grids[handle] = nullptr;

@@ -217,11 +217,12 @@ __global__ void __launch_bounds__(NW * 32, MINB) pair_integrals(BatchArgs B) {
     __syncwarp();
   }
 
+  const int64_t total = queue_total(B);
   for (;;) {
     int64_t g = 0;
     if (lane == 0) g = (int64_t)atomicAdd(&B.counters[3], 1ULL);
     g = __shfl_sync(FULL, g, 0);
-    if (g >= B.total) break;
+    if (g >= total) break;
     // the snapshot owning queue position g: last j with item_base[j] <= g
     int jl = 0, jh = B.nsnap - 1;
     while (jl < jh) {
@@ -538,11 +539,12 @@ __global__ void __launch_bounds__(NW * 32, MINB) pair_integrals_mixed(BatchArgs 
   for (int r = 0; r < 32; ++r) S.col[r][lane] = 0.f;
   __syncwarp();
 
+  const int64_t total = queue_total(B);
   for (;;) {
     int64_t g = 0;
     if (lane == 0) g = (int64_t)atomicAdd(&B.counters[3], 1ULL);
     g = __shfl_sync(FULL, g, 0);
-    if (g >= B.total) break;
+    if (g >= total) break;
     int jl = 0, jh = B.nsnap - 1;
     while (jl < jh) {
       const int jm = (jl + jh + 1) >> 1;
@@ -738,9 +740,9 @@ __global__ void put_i64(I64Chunk c, int64_t* dst) {
 // M_i = sum of cell i's item partials, in item order; rho_i = M_i / V_i.
 // One thread per cell over the cells of all snapshots.
 __global__ void cell_sums(const SnapDesc* __restrict__ d, const int64_t* __restrict__ cell_base, int nsnap,
-                          int64_t total_cells) {
+                          int64_t total_cells, const int64_t* bad) {
   const int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (g >= total_cells) return;
+  if (g >= total_cells || (bad && *bad)) return;
   int jl = 0, jh = nsnap - 1;
   while (jl < jh) {
     const int jm = (jl + jh + 1) >> 1;
@@ -812,7 +814,7 @@ int integrals_enqueue(map_ctx* ctx, const BatchArgs& B, int variant, cudaStream_
     MAP_TRY((launch<double, false, 4, 4>(ctx, B, s)));
   }
   if (B.total_cells > 0) {
-    cell_sums<<<nblk(B.total_cells, 256), 256, 0, s>>>(B.snaps, B.cell_base, B.nsnap, B.total_cells);
+    cell_sums<<<nblk(B.total_cells, 256), 256, 0, s>>>(B.snaps, B.cell_base, B.nsnap, B.total_cells, B.bad);
     ++ctx->launches;
     CUDA_TRY(cudaGetLastError());
   }

@@ -203,6 +203,19 @@ struct map_ctx {
   cudaGraphExec_t bexec = nullptr;
   std::vector<unsigned char> bsig;
   int64_t bexec_launches = 0;  // kernels per replay of bexec
+  // map_batch's whole step as one CUDA graph: the snapshots' validation,
+  // octrees, pair lists and work items on the workers' streams, then the one
+  // integral launch and the sums.  Captured after an eager call, replayed
+  // while a call names the same buffers, grids and outputs (sig) and every
+  // workspace it baked in is still the same allocation (bufs).
+  struct BatchGraph {
+    cudaGraphExec_t exec = nullptr;
+    std::vector<unsigned char> sig;
+    std::vector<const void*> bufs;
+    int64_t launches = 0;                 // kernels per replay
+    DevBuf desc, base, tot, caps, flags;  // its own descriptors, queue bases, totals, capacities, flags
+    int64_t captures = 0, replays = 0, fallbacks = 0;
+  } bgraph;
   std::vector<BatchWorker> workers;  // created by the first batch call that uses them
   cudaEvent_t wev = nullptr;         // the caller's stream, before the workers start
   // MAP_TABLE: the table of the pyramid integral (n^3 FP32 texels)
@@ -286,10 +299,19 @@ struct BatchArgs {
   const int64_t* item_base;
   const int64_t* cell_base;
   int nsnap;
-  int64_t total;        // items
+  int64_t total;        // items (with total_dev: an upper bound, for the launch shape)
   int64_t total_cells;
   unsigned long long* counters;  // [1] edge terms, [2] FP64 terms, [3] queue, [8..13] work tally
+  const int64_t* total_dev = nullptr;  // graph replays: the item count, written on the device
+  const int64_t* bad = nullptr;        // graph replays: nonzero = skip the launch (invalid input, overflow)
 };
+
+// The queue length a launch of the pair-integral kernels serves: the host's
+// count, or (graph replays) the device's, 0 when the replay is to be skipped.
+__device__ __forceinline__ int64_t queue_total(const BatchArgs& B) {
+  if (!B.total_dev) return B.total;
+  return (B.bad && *B.bad) ? 0 : *B.total_dev;
+}
 
 // Launch shapes of the mixed pair-integral kernel: (warps per CTA, CTAs per
 // SM) = (4, 5), (4, 4), (4, 6), (2, 10), (8, 2); the register cap per thread
@@ -306,6 +328,13 @@ void grid_recycle(map_ctx* ctx, PreparedGrid* g);
 void grid_pool_drop(map_ctx* ctx);
 int tree_build(map_ctx* ctx, const double* x, const double* y, const double* z, const double* m,
                const double* h, int64_t n, cudaStream_t s, bool want_size = false);
+// The same tree from launches of fixed shape and no host reads (capturable in
+// a CUDA graph): node arrays sized for the largest possible tree of n
+// particles, tree_nodes_max(n, leaf).  Same nodes, same order, same sums as
+// tree_build.
+int64_t tree_nodes_max(int64_t n, int leaf_size);
+int tree_build_graph(map_ctx* ctx, const double* x, const double* y, const double* z, const double* m,
+                     const double* h, int64_t n, cudaStream_t s);
 // Output buffers of a pair-list build; nullptr members mean the context's
 // workspace.
 struct PairBufs {
@@ -322,9 +351,20 @@ int pairs_build(map_ctx* ctx, const PreparedGrid* g, cudaStream_t s, const PairB
 // `target` items per resident warp; sets ctx->items, item_off, partial, n_items.
 int items_build(map_ctx* ctx, const int64_t* off, int64_t nc, int64_t np, int target, cudaStream_t s,
                 const PairBufs& out = PairBufs());
+// pairs_build with no host reads (capturable): the list and the items go to
+// out, which must hold cap_pairs pairs and cap_items items; when a build needs
+// more, nothing is written beyond them and the counts (off[nc], ioff[nc])
+// say so.  Sets the context's list pointers like pairs_build; n_pairs and
+// n_items are left unknown (-1).
+int pairs_build_graph(map_ctx* ctx, const PreparedGrid* g, cudaStream_t s, const PairBufs& out, int64_t cap_pairs,
+                      int64_t cap_items);
 // Sorts the last call's lists (and f_ai) by particle index within each cell.
 int pairs_sort_lists(map_ctx* ctx, cudaStream_t s);
 int check_particles(map_ctx* ctx, const map_particles* p, bool need_m, bool need_h, cudaStream_t s);
+// The validation kernel of check_particles alone: ORs 1 into *status (device)
+// when a particle is invalid; no host read.
+int validate_enqueue(map_ctx* ctx, const map_particles* p, bool need_m, bool need_h, unsigned long long* status,
+                     cudaStream_t s);
 // map_particles_to_cells on a prepared grid (after ctx_enter on s)
 int map_run(map_ctx* ctx, const map_particles* p, PreparedGrid* g, map_outputs* out, cudaStream_t s);
 int integrals_run(map_ctx* ctx, const PreparedGrid* g, const map_particles* p, map_outputs* out, cudaStream_t s);
@@ -351,6 +391,9 @@ int launch_table(map_ctx* ctx, const BatchArgs& B, cudaStream_t s);
 int run_on_workers(map_ctx* ctx, int n, const int* order, cudaStream_t s,
                    const std::function<int(BatchWorker&, int)>& fn);
 void destroy_workers(map_ctx* ctx);
+// Drops the batch graph (its inputs changed place: a grid released, a
+// workspace reallocated) and frees its buffers.
+void batch_graph_drop(map_ctx* ctx);
 int h_solve_run(map_ctx* ctx, const double* x, const double* y, const double* z, int64_t n, double* h,
                 int32_t* route, const double* h0_override, cudaStream_t s);
 int pseudo_run(map_ctx* ctx, const map_particles* full, const map_walk* walk, map_particles* out, int32_t* kind,

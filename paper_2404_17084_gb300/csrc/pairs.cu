@@ -108,8 +108,10 @@ struct WalkCells {  // per warp: the 32 lanes' cells, one entry per lane
 template <bool FILL>
 __global__ void __launch_bounds__(128) pair_traverse(int64_t ncell, const int32_t* __restrict__ order, PairTree T,
                                                      PairGrid G, int64_t* count, const int64_t* __restrict__ off,
-                                                     int32_t* out, const unsigned long long* n_dev) {
+                                                     int32_t* out, const unsigned long long* n_dev,
+                                                     int64_t cap = INT64_MAX) {
   __shared__ int32_t s_stack[4][200];
+  if (FILL && off[ncell] > cap) return;  // the list does not fit its buffer: nothing is written
   __shared__ WalkCells s_cells[4];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const unsigned lt = (1u << lane) - 1u;
@@ -205,8 +207,10 @@ constexpr int WALK_CAND = 512;  // candidate positions gathered before they are 
 template <bool FILL>
 __global__ void __launch_bounds__(128) pair_walk_warp(int64_t ncell, const int32_t* __restrict__ cells, PairTree T,
                                                       PairGrid G, int64_t* count, const int64_t* __restrict__ off,
-                                                      int32_t* out, const unsigned long long* n_dev) {
+                                                      int32_t* out, const unsigned long long* n_dev,
+                                                      int64_t cap = INT64_MAX) {
   __shared__ int32_t s_stk[4][WALK_STK];
+  if (FILL && off[ncell] > cap) return;  // the list does not fit its buffer: nothing is written
   __shared__ int32_t s_cand[4][WALK_CAND];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int64_t t = blockIdx.x * 4 + warp;
@@ -301,10 +305,11 @@ __global__ void __launch_bounds__(128) pair_walk_warp(int64_t ncell, const int32
 // for the filling pass.
 __global__ void __launch_bounds__(128) place_rows(int64_t ncell, const int64_t* __restrict__ count,
                                                   const int64_t* __restrict__ off, const int32_t* __restrict__ rows,
-                                                  int32_t* out, int32_t* ovf, unsigned long long* n_ovf) {
+                                                  int32_t* out, int32_t* ovf, unsigned long long* n_ovf,
+                                                  int64_t cap = INT64_MAX) {
   const int64_t c = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
-  if (c >= ncell) return;
+  if (c >= ncell || off[ncell] > cap) return;
   const int64_t n = count[c];
   if (n > PAIR_ROW) {
     if (lane == 0) ovf[atomicAdd(n_ovf, 1ULL)] = (int32_t)c;
@@ -316,17 +321,24 @@ __global__ void __launch_bounds__(128) place_rows(int64_t ncell, const int64_t* 
 }
 
 // Work items: cell c's n pairs in max(1, ceil(ceil(n/32)/K)) items of at
-// most K blocks of 32 pairs.
-__global__ void item_count(int64_t ncell, const int64_t* __restrict__ off, int64_t K, int64_t* cnt) {
+// most K blocks of 32 pairs, K = max(1, (np/32 + ncell) / tgt) from the
+// list's pair count np = off[ncell] (read on the device).
+__device__ __forceinline__ int64_t item_blocks(int64_t ncell, const int64_t* __restrict__ off, int64_t tgt) {
+  const int64_t blocks = off[ncell] / 32 + ncell;
+  return blocks / tgt > 1 ? blocks / tgt : 1;
+}
+__global__ void item_count(int64_t ncell, const int64_t* __restrict__ off, int64_t tgt, int64_t* cnt) {
   const int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (c >= ncell) return;
+  const int64_t K = item_blocks(ncell, off, tgt);
   const int64_t blocks = (off[c + 1] - off[c] + 31) / 32;
   cnt[c] = blocks > K ? (blocks + K - 1) / K : 1;
 }
 __global__ void item_fill(int64_t ncell, const int64_t* __restrict__ off, const int64_t* __restrict__ ioff,
-                          int64_t K, PairItem* items) {
+                          int64_t tgt, PairItem* items, int64_t cap = INT64_MAX) {
   const int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (c >= ncell) return;
+  if (c >= ncell || ioff[ncell] > cap) return;
+  const int64_t K = item_blocks(ncell, off, tgt);
   const int64_t b = off[c], n = off[c + 1] - b, span = 32 * K;
   int64_t lo = 0;
   for (int64_t i = ioff[c]; i < ioff[c + 1]; ++i) {
@@ -478,13 +490,12 @@ int pairs_build(map_ctx* ctx, const PreparedGrid* g, cudaStream_t s, const PairB
 // per SM); the autotuner may raise the target (smaller items).
 int items_build(map_ctx* ctx, const int64_t* off, int64_t nc, int64_t np, int target, cudaStream_t s,
                 const PairBufs& out) {
-  const int64_t blocks = np / 32 + nc;
+  (void)np;
   const int64_t tgt = (int64_t)target * ctx->sm_count * 24;
-  const int64_t K = blocks / tgt > 1 ? blocks / tgt : 1;
   int64_t *icnt, *ioff;
   MAP_TRY(ensure_t(ctx, ctx->ws_pairs[0], nc + 1, &icnt));  // the pair counts are no longer needed
   MAP_TRY(ensure_t(ctx, out.ioff ? *out.ioff : ctx->ws_pairs[11], nc + 1, &ioff));
-  item_count<<<nblk(nc, 256), 256, 0, s>>>(nc, off, K, icnt); ++ctx->launches;
+  item_count<<<nblk(nc, 256), 256, 0, s>>>(nc, off, tgt, icnt); ++ctx->launches;
   CUDA_TRY(cudaGetLastError());
   CUDA_TRY(cudaMemsetAsync(icnt + nc, 0, sizeof(int64_t), s));
   size_t tb = 0;
@@ -498,12 +509,99 @@ int items_build(map_ctx* ctx, const int64_t* off, int64_t nc, int64_t np, int ta
   double* part;
   MAP_TRY(ensure_t(ctx, out.items ? *out.items : ctx->ws_pairs[10], nitems, &items));
   MAP_TRY(ensure_t(ctx, out.part ? *out.part : ctx->ws_pairs[12], nitems, &part));
-  item_fill<<<nblk(nc, 256), 256, 0, s>>>(nc, off, ioff, K, items); ++ctx->launches;
+  item_fill<<<nblk(nc, 256), 256, 0, s>>>(nc, off, ioff, tgt, items); ++ctx->launches;
   CUDA_TRY(cudaGetLastError());
   ctx->items = items;
   ctx->item_off = ioff;
   ctx->partial = part;
   ctx->n_items = nitems;
+  return MAP_OK;
+}
+
+// pairs_build with no host reads: the list's and the items' sizes stay on
+// the device; the buffers hold cap_pairs and cap_items, and a build that
+// needs more writes nothing beyond them (its off[nc] or ioff[nc] says so).
+int pairs_build_graph(map_ctx* ctx, const PreparedGrid* g, cudaStream_t s, const PairBufs& out, int64_t cap_pairs,
+                      int64_t cap_items) {
+  if (!out.off || !out.idx || !out.items || !out.ioff || !out.part) return MAP_EINVAL;
+  DevTree& T = ctx->tree;
+  const int64_t nc = g->ncell;
+  const int tpb = 128;
+  uint64_t *k_in, *k_out;
+  int32_t *o_in, *order;
+  MAP_TRY(ensure_t(ctx, ctx->ws_pairs[4], nc, &k_in));
+  MAP_TRY(ensure_t(ctx, ctx->ws_pairs[5], nc, &k_out));
+  MAP_TRY(ensure_t(ctx, ctx->ws_pairs[6], nc, &o_in));
+  MAP_TRY(ensure_t(ctx, ctx->ws_pairs[14], nc, &order));
+  site_keys<<<nblk(nc, 256), 256, 0, s>>>(nc, g->site, k_in, o_in); ++ctx->launches;
+  CUDA_TRY(cudaGetLastError());
+  size_t tb = 0;
+  CUDA_TRY(cub::DeviceRadixSort::SortPairs(nullptr, tb, k_in, k_out, o_in, order, nc, 0, 30, s));
+  MAP_TRY(ctx_ensure(ctx, ctx->cub_tmp, tb));
+  CUDA_TRY(cub::DeviceRadixSort::SortPairs(ctx->cub_tmp.p, tb, k_in, k_out, o_in, order, nc, 0, 30, s));
+  PairTree PT{T.xs, T.ys, T.zs, T.hs, T.split, T.idx, T.begin, T.end, T.first_child, T.nchild, T.bbox_bits,
+              T.hmax_bits, T.box32};
+  PairGrid PG{g->cell_face_off, g->face_plane, g->face32, g->site, g->rad};
+  int64_t *count, *off;
+  MAP_TRY(ensure_t(ctx, ctx->ws_pairs[0], nc + 1, &count));
+  MAP_TRY(ensure_t(ctx, *out.off, nc + 1, &off));
+  int32_t* rows;
+  MAP_TRY(ensure_t(ctx, ctx->ws_pairs[8], (size_t)nc * PAIR_ROW, &rows));
+  CUDA_TRY(cudaMemsetAsync(count + nc, 0, sizeof(int64_t), s));
+  const bool per_warp = T.n > 16 * nc;
+  if (per_warp)
+    pair_walk_warp<false><<<(unsigned)((nc + 3) / 4), tpb, 0, s>>>(nc, nullptr, PT, PG, count, nullptr, rows, nullptr);
+  else
+    pair_traverse<false><<<nblk(nc, tpb), tpb, 0, s>>>(nc, order, PT, PG, count, nullptr, rows, nullptr);
+  ++ctx->launches;
+  CUDA_TRY(cudaGetLastError());
+  tb = 0;
+  CUDA_TRY(cub::DeviceScan::ExclusiveSum(nullptr, tb, count, off, nc + 1, s));
+  MAP_TRY(ctx_ensure(ctx, ctx->cub_tmp, tb));
+  CUDA_TRY(cub::DeviceScan::ExclusiveSum(ctx->cub_tmp.p, tb, count, off, nc + 1, s));
+  int32_t* list;
+  MAP_TRY(ensure_t(ctx, *out.idx, cap_pairs + 1, &list));
+  int32_t* ovf;
+  MAP_TRY(ensure_t(ctx, ctx->ws_pairs[9], nc, &ovf));
+  unsigned long long* d_novf = ctx->d_counters + 6;
+  CUDA_TRY(cudaMemsetAsync(d_novf, 0, sizeof(unsigned long long), s));
+  place_rows<<<nblk(nc * 32, tpb), tpb, 0, s>>>(nc, count, off, rows, list, ovf, d_novf, cap_pairs); ++ctx->launches;
+  CUDA_TRY(cudaGetLastError());
+  if (per_warp)
+    pair_walk_warp<true><<<(unsigned)((nc + 3) / 4), tpb, 0, s>>>(nc, ovf, PT, PG, nullptr, off, list, d_novf,
+                                                                  cap_pairs);
+  else
+    pair_traverse<true><<<nblk(nc, tpb), tpb, 0, s>>>(nc, ovf, PT, PG, nullptr, off, list, d_novf, cap_pairs);
+  ++ctx->launches;
+  CUDA_TRY(cudaGetLastError());
+  // the work items (the item size from the device-side pair count)
+  const int64_t tgt = (int64_t)ctx->item_target * ctx->sm_count * 24;
+  int64_t *icnt, *ioff;
+  MAP_TRY(ensure_t(ctx, ctx->ws_pairs[0], nc + 1, &icnt));
+  MAP_TRY(ensure_t(ctx, *out.ioff, nc + 1, &ioff));
+  item_count<<<nblk(nc, 256), 256, 0, s>>>(nc, off, tgt, icnt); ++ctx->launches;
+  CUDA_TRY(cudaGetLastError());
+  CUDA_TRY(cudaMemsetAsync(icnt + nc, 0, sizeof(int64_t), s));
+  tb = 0;
+  CUDA_TRY(cub::DeviceScan::ExclusiveSum(nullptr, tb, icnt, ioff, nc + 1, s));
+  MAP_TRY(ctx_ensure(ctx, ctx->cub_tmp, tb));
+  CUDA_TRY(cub::DeviceScan::ExclusiveSum(ctx->cub_tmp.p, tb, icnt, ioff, nc + 1, s));
+  PairItem* items;
+  double* part;
+  MAP_TRY(ensure_t(ctx, *out.items, cap_items, &items));
+  MAP_TRY(ensure_t(ctx, *out.part, cap_items, &part));
+  item_fill<<<nblk(nc, 256), 256, 0, s>>>(nc, off, ioff, tgt, items, cap_items); ++ctx->launches;
+  CUDA_TRY(cudaGetLastError());
+  ctx->n_pairs = -1;
+  ctx->pair_off = off;
+  ctx->pair_idx = list;
+  ctx->pairs_sorted = false;
+  ctx->inv_ready = false;
+  ctx->last_ncell = nc;
+  ctx->items = items;
+  ctx->item_off = ioff;
+  ctx->partial = part;
+  ctx->n_items = -1;
   return MAP_OK;
 }
 

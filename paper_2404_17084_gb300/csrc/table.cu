@@ -71,11 +71,12 @@ __global__ void __launch_bounds__(NW * 32, MINB) pair_integrals_table(BatchArgs 
   const int lane = threadIdx.x & 31;
   SnapDesc& A = descs[threadIdx.x >> 5];
   int cur = -1;
+  const int64_t total = queue_total(B);
   for (;;) {
     int64_t g = 0;
     if (lane == 0) g = (int64_t)atomicAdd(&B.counters[3], 1ULL);
     g = __shfl_sync(FULLM, g, 0);
-    if (g >= B.total) break;
+    if (g >= total) break;
     int jl = 0, jh = B.nsnap - 1;
     while (jl < jh) {
       const int jm = (jl + jh + 1) >> 1;

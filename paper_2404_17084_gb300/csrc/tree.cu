@@ -136,14 +136,13 @@ __global__ void split_write(int64_t lb, int64_t le, int64_t next_begin, const ui
 // internal nodes sum their children in octant order (mass, mass-weighted
 // position); bounding box and largest h are the union / maximum over the
 // particles (leaves) or the children (internal nodes), exact in any order.
-__global__ void node_sums(int64_t lb, int64_t le, const int64_t* __restrict__ nb, const int64_t* __restrict__ ne,
-                          const int64_t* __restrict__ fc, const int32_t* __restrict__ nch,
-                          const double* __restrict__ xs, const double* __restrict__ ys,
-                          const double* __restrict__ zs, const double* __restrict__ ms,
-                          const double* __restrict__ hs, double* mass, double* msum /* 3 per node: sum m x */,
-                          unsigned long long* hmax_bits, unsigned long long* bbox, int32_t* owner) {
-  int64_t i = lb + blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (i >= le) return;
+__device__ __forceinline__ void node_sum_one(int64_t i, const int64_t* __restrict__ nb,
+                                             const int64_t* __restrict__ ne, const int64_t* __restrict__ fc,
+                                             const int32_t* __restrict__ nch, const double* __restrict__ xs,
+                                             const double* __restrict__ ys, const double* __restrict__ zs,
+                                             const double* __restrict__ ms, const double* __restrict__ hs,
+                                             double* mass, double* msum, unsigned long long* hmax_bits,
+                                             unsigned long long* bbox, int32_t* owner) {
   double M = 0, Sx = 0, Sy = 0, Sz = 0, hm = 0;
   double lo0 = 1e300, lo1 = 1e300, lo2 = 1e300, hi0 = 0, hi1 = 0, hi2 = 0;
   if (nch[i] == 0) {
@@ -176,6 +175,17 @@ __global__ void node_sums(int64_t lb, int64_t le, const int64_t* __restrict__ nb
   hmax_bits[i] = dbits(hm);
   bbox[6 * i] = dbits(lo0); bbox[6 * i + 1] = dbits(lo1); bbox[6 * i + 2] = dbits(lo2);
   bbox[6 * i + 3] = dbits(hi0); bbox[6 * i + 4] = dbits(hi1); bbox[6 * i + 5] = dbits(hi2);
+}
+
+__global__ void node_sums(int64_t lb, int64_t le, const int64_t* __restrict__ nb, const int64_t* __restrict__ ne,
+                          const int64_t* __restrict__ fc, const int32_t* __restrict__ nch,
+                          const double* __restrict__ xs, const double* __restrict__ ys,
+                          const double* __restrict__ zs, const double* __restrict__ ms,
+                          const double* __restrict__ hs, double* mass, double* msum /* 3 per node: sum m x */,
+                          unsigned long long* hmax_bits, unsigned long long* bbox, int32_t* owner) {
+  int64_t i = lb + blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= le) return;
+  node_sum_one(i, nb, ne, fc, nch, xs, ys, zs, ms, hs, mass, msum, hmax_bits, bbox, owner);
 }
 
 __global__ void node_com(int64_t nn, const double* __restrict__ mass, const double* __restrict__ msum, double* com,
@@ -256,6 +266,138 @@ __global__ void collect_big(int64_t nn, const int64_t* __restrict__ nb, const in
   int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (i >= nn) return;
   if (ne[i] - nb[i] > BIG_NODE) big[atomicAdd(nbig, 1ULL)] = (int32_t)i;
+}
+
+// ---------------------------------------------------------------- build with no host reads
+// The level-synchronous build numbers the nodes level by level, each level in
+// key order.  The same numbering follows from the sorted keys alone: with
+// pfx_L(k) = k >> 3 (21 - L) the level-L prefix, the node (L, P) exists iff
+// L = 0 or its parent prefix at level L - 1 holds more than leaf_size
+// particles (then every ancestor holds more too, so all of them split), and
+// it is flagged at the sorted position of its first particle.  The flags of
+// all levels, laid out level-major ([L n + i], 22 n entries and a terminal
+// 0), are scanned: the scan is the node number, scan[L n] the first node of
+// level L, scan[22 n] the node count.
+
+__device__ __forceinline__ uint64_t pfx(uint64_t key, int L) { return key >> (3 * (MORTON_BITS - L)); }
+
+// first sorted position in [0, hi] whose level-L prefix equals P
+__device__ __forceinline__ int64_t prefix_begin(const uint64_t* keys, int64_t hi, int L, uint64_t P) {
+  int64_t lo = 0;
+  while (lo < hi) {
+    const int64_t mid = (lo + hi) >> 1;
+    if (pfx(keys[mid], L) < P) lo = mid + 1; else hi = mid;
+  }
+  return lo;
+}
+
+// one past the last sorted position in [lo, n) whose level-L prefix equals P
+__device__ __forceinline__ int64_t prefix_end(const uint64_t* keys, int64_t lo, int64_t n, int L, uint64_t P) {
+  int64_t hi = n;
+  while (lo < hi) {
+    const int64_t mid = (lo + hi) >> 1;
+    if (pfx(keys[mid], L) <= P) lo = mid + 1; else hi = mid;
+  }
+  return lo;
+}
+
+// The levels at which sorted position i starts a node: d = the shallowest
+// level where its prefix differs from position i - 1's (22: none); from d on
+// it starts a node while the enclosing node one level up splits.  Calls
+// visit(L, lo) for each, lo being the first position of the parent node.
+template <typename F>
+__device__ __forceinline__ void node_starts(const uint64_t* __restrict__ keys, int64_t n, int64_t i, int leaf,
+                                            F visit) {
+  const uint64_t k = keys[i];
+  int d = 0;
+  if (i > 0) {
+    const uint64_t x = keys[i - 1] ^ k;
+    d = x == 0 ? MORTON_BITS + 1 : MORTON_BITS - (63 - __clzll((long long)x)) / 3;
+  }
+  if (d > MORTON_BITS) return;
+  // the parent of the level-d node starts before i (unless d = 0)
+  const int64_t lo_d = d == 0 ? 0 : prefix_begin(keys, i, d - 1, pfx(k, d - 1));
+  for (int L = d; L <= MORTON_BITS; ++L) {
+    if (L > 0) {
+      const int64_t lo = L - 1 >= d ? i : lo_d;  // first position of the parent
+      if (!(lo + leaf < n && pfx(keys[lo + leaf], L - 1) == pfx(k, L - 1))) return;  // parent is a leaf
+    }
+    visit(L, L == 0 ? (int64_t)-1 : (L - 1 >= d ? i : lo_d));
+  }
+}
+
+__global__ void tree_flags(int64_t n, const uint64_t* __restrict__ keys, int leaf, int32_t* __restrict__ flags) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+    for (int L = 0; L <= MORTON_BITS; ++L) flags[L * n + i] = 0;
+    node_starts(keys, n, i, leaf, [&](int L, int64_t) { flags[L * n + i] = 1; });
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) flags[(int64_t)(MORTON_BITS + 1) * n] = 0;
+}
+
+// the node records from the scanned flags (id = scan[L n + i])
+__global__ void tree_fill(int64_t n, const uint64_t* __restrict__ keys, int leaf, const int32_t* __restrict__ scan,
+                          int64_t* nb, int64_t* ne, int32_t* lev, int64_t* label, int64_t* first_child,
+                          int32_t* nchild, int32_t* parent) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+    const uint64_t k = keys[i];
+    node_starts(keys, n, i, leaf, [&](int L, int64_t lo_parent) {
+      const int64_t id = scan[L * n + i];
+      const int64_t e = prefix_end(keys, i, n, L, pfx(k, L));
+      nb[id] = i;
+      ne[id] = e;
+      lev[id] = L;
+      label[id] = (int64_t)((1ULL << (3 * L)) | pfx(k, L));
+      parent[id] = L == 0 ? -1 : scan[(L - 1) * n + lo_parent];
+      if (e - i > leaf && L < MORTON_BITS) {
+        const int64_t f = scan[(L + 1) * n + i];
+        first_child[id] = f;
+        nchild[id] = (int32_t)(scan[(L + 1) * n + e] - f);
+      } else {
+        first_child[id] = -1;
+        nchild[id] = 0;
+      }
+    });
+  }
+}
+
+// bottom-up sums of one level whose node range is read on the device
+__global__ void node_sums_level(int L, int64_t n, const int32_t* __restrict__ scan, const int64_t* __restrict__ nb,
+                                const int64_t* __restrict__ ne, const int64_t* __restrict__ fc,
+                                const int32_t* __restrict__ nch, const double* __restrict__ xs,
+                                const double* __restrict__ ys, const double* __restrict__ zs,
+                                const double* __restrict__ ms, const double* __restrict__ hs, double* mass,
+                                double* msum, unsigned long long* hmax_bits, unsigned long long* bbox,
+                                int32_t* owner) {
+  const int64_t lb = scan[L * n], le = scan[(L + 1) * n];
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t i = lb + (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < le; i += stride)
+    node_sum_one(i, nb, ne, fc, nch, xs, ys, zs, ms, hs, mass, msum, hmax_bits, bbox, owner);
+}
+
+__global__ void node_com_box(int64_t n, const int32_t* __restrict__ scan, const double* __restrict__ mass,
+                             const double* __restrict__ msum, double* com, unsigned long long* size_bits,
+                             const unsigned long long* __restrict__ bbox, const unsigned long long* __restrict__ hmax,
+                             const int64_t* __restrict__ fc, const int32_t* __restrict__ nch, float* box32) {
+  const int64_t nn = scan[(int64_t)(MORTON_BITS + 1) * n];
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nn; i += stride) {
+    const double M = mass[i];
+    com[3 * i] = msum[3 * i] / M;
+    com[3 * i + 1] = msum[3 * i + 1] / M;
+    com[3 * i + 2] = msum[3 * i + 2] / M;
+    size_bits[i] = 0ULL;
+    for (int k = 0; k < 3; ++k) {
+      box32[8 * i + k] = __double2float_rd(bitsd(bbox[6 * i + k]));
+      box32[8 * i + 3 + k] = __double2float_ru(bitsd(bbox[6 * i + 3 + k]));
+    }
+    box32[8 * i + 6] = __double2float_ru(bitsd(hmax[i]));
+    const int nc = nch[i];
+    const int64_t f = fc[i];
+    const unsigned link = nc == 0 ? 0u : (f < (1LL << 28) ? ((unsigned)f << 4) | (unsigned)nc : NODE_LINK_FAR);
+    box32[8 * i + 7] = __uint_as_float(link);
+  }
 }
 
 
@@ -400,5 +542,79 @@ int tree_build(map_ctx* ctx, const double* x, const double* y, const double* z, 
   node_box32<<<nblk(T.nnodes, tpb), tpb, 0, s>>>(T.nnodes, T.bbox_bits, T.hmax_bits, T.first_child, T.nchild,
                                                  box32); ++ctx->launches;
   CUDA_TRY(cudaGetLastError());
+  return MAP_OK;
+}
+
+// ---------------------------------------------------------------- tree build with no host reads
+
+int64_t tree_nodes_max(int64_t n, int leaf_size) {
+  // internal nodes of one level hold disjoint sets of more than leaf_size
+  // particles, so each level has at most n / (leaf_size + 1) of them (21
+  // levels split); every leaf holds at least one particle; plus the root
+  const int64_t per_level = n / ((int64_t)(leaf_size > 0 ? leaf_size : 0) + 1);
+  return n + (int64_t)MORTON_BITS * per_level + 64;
+}
+
+int tree_build_graph(map_ctx* ctx, const double* x, const double* y, const double* z, const double* m,
+                     const double* h, int64_t n, cudaStream_t s) {
+  DevTree& T = ctx->tree;
+  T.n = n;
+  const int tpb = 256;
+  const int leaf = ctx->cfg.leaf_size;
+  uint64_t* keys_in;
+  int32_t* idx_in;
+  MAP_TRY(ensure_t(ctx, ctx->ws_tree[0], n, &keys_in));
+  MAP_TRY(ensure_t(ctx, ctx->ws_tree[1], n, &idx_in));
+  MAP_TRY(ensure_t(ctx, ctx->ws_tree[2], n, &T.keys));
+  MAP_TRY(ensure_t(ctx, ctx->ws_tree[3], n, &T.idx));
+  MAP_TRY(ensure_t(ctx, ctx->ws_tree[4], 5 * n, &T.xs));
+  T.ys = T.xs + n; T.zs = T.xs + 2 * n; T.ms = T.xs + 3 * n; T.hs = T.xs + 4 * n;
+  MAP_TRY(ensure_t(ctx, ctx->ws_tree[5], n, &T.owner));
+  MAP_TRY(ensure_t(ctx, ctx->ws_tree[23], 6 * n, &T.split));
+  morton_keys<<<nblk(n, tpb), tpb, 0, s>>>(n, x, y, z, keys_in, idx_in); ++ctx->launches;
+  CUDA_TRY(cudaGetLastError());
+  size_t tmp_bytes = 0;
+  CUDA_TRY(cub::DeviceRadixSort::SortPairs(nullptr, tmp_bytes, keys_in, T.keys, idx_in, T.idx, n, 0, 63, s));
+  MAP_TRY(ctx_ensure(ctx, ctx->cub_tmp, tmp_bytes));
+  CUDA_TRY(cub::DeviceRadixSort::SortPairs(ctx->cub_tmp.p, tmp_bytes, keys_in, T.keys, idx_in, T.idx, n, 0, 63, s));
+  gather_sorted<<<nblk(n, tpb), tpb, 0, s>>>(n, T.idx, x, y, z, m, h, T.xs, T.ys, T.zs, T.ms, T.hs, T.split); ++ctx->launches;
+  CUDA_TRY(cudaGetLastError());
+
+  // node flags of every level, their scan, the node records
+  const int64_t nflag = (int64_t)(MORTON_BITS + 1) * n + 1;
+  if (nflag >= (int64_t)INT32_MAX) return MAP_ECAPACITY;
+  int32_t *flags, *scan;
+  MAP_TRY(ensure_t(ctx, ctx->ws_tree[25], nflag, &flags));
+  MAP_TRY(ensure_t(ctx, ctx->ws_tree[26], nflag, &scan));
+  const int64_t cap = tree_nodes_max(n, leaf);
+  MAP_TRY(grow_nodes(ctx, cap));
+  const unsigned g = (unsigned)(ctx->sm_count * 8);
+  tree_flags<<<g, tpb, 0, s>>>(n, T.keys, leaf, flags); ++ctx->launches;
+  CUDA_TRY(cudaGetLastError());
+  size_t sb = 0;
+  CUDA_TRY(cub::DeviceScan::ExclusiveSum(nullptr, sb, flags, scan, (int)nflag, s));
+  MAP_TRY(ctx_ensure(ctx, ctx->cub_tmp, sb));
+  CUDA_TRY(cub::DeviceScan::ExclusiveSum(ctx->cub_tmp.p, sb, flags, scan, (int)nflag, s));
+  tree_fill<<<g, tpb, 0, s>>>(n, T.keys, leaf, scan, T.begin, T.end, T.level, T.label, T.first_child, T.nchild,
+                             T.parent); ++ctx->launches;
+  CUDA_TRY(cudaGetLastError());
+  // bottom-up sums, deepest level first (empty levels launch and return)
+  double* msum;
+  MAP_TRY(ensure_t(ctx, ctx->ws_tree[20], 3 * cap, &msum));
+  for (int L = MORTON_BITS; L >= 0; --L) {
+    node_sums_level<<<g, tpb, 0, s>>>(L, n, scan, T.begin, T.end, T.first_child, T.nchild, T.xs, T.ys, T.zs, T.ms,
+                                      T.hs, T.mass, msum, T.hmax_bits, T.bbox_bits, T.owner); ++ctx->launches;
+    CUDA_TRY(cudaGetLastError());
+  }
+  float* box32;
+  MAP_TRY(ensure_t(ctx, ctx->ws_tree[24], 8 * cap, &box32));
+  T.box32 = box32;
+  node_com_box<<<g, tpb, 0, s>>>(n, scan, T.mass, msum, T.com, T.size_bits, T.bbox_bits, T.hmax_bits, T.first_child,
+                                 T.nchild, box32); ++ctx->launches;
+  CUDA_TRY(cudaGetLastError());
+  // host-side sizes are unknown without a read: an upper bound, no levels
+  T.nnodes = cap;
+  T.nlevels = MORTON_BITS + 1;
+  T.level_begin.clear();
   return MAP_OK;
 }

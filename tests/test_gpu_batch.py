@@ -113,3 +113,73 @@ def test_solve_h_batch_equals_single(snapshots, precision):
             assert np.array_equal(got[j][1], r1.cpu().numpy()), j
     finally:
         L.map_destroy(ctx)
+
+
+def test_batch_whole_step_graph(snapshots):
+    """After an eager call the whole step (validation, octrees, pair lists,
+    work items, the integral launch, the sums) is captured once; calls on the
+    same buffers replay it, computing from the buffers' current values: new
+    positions give the single-snapshot results on those positions bit for
+    bit; lists that outgrow their buffers (h raised) fall back to the eager
+    step and capture anew; an invalid particle is refused."""
+    L = lib()
+    ctx = L.map_init(L.map_config_default(precision=1))
+    try:
+        handles, parts, keep, mass = [], [], [], []
+        for _, p, g, h in snapshots:
+            handles.append(L.map_grid_upload(ctx, L.grid_to_device(g)))
+            t = dev_particles(p, h)
+            keep.append(t)
+            parts.append(L.make_particles(*t))
+            mass.append(torch.full((g.ncell,), -1.0, dtype=torch.float64, device="cuda"))
+        totals = torch.zeros(len(snapshots), dtype=torch.float64, device="cuda")
+
+        def call():
+            L.map_batch(ctx, parts, handles, mass, totals=totals)
+            torch.cuda.synchronize()
+            return [m.cpu().numpy().copy() for m in mass], totals.cpu().numpy().copy()
+
+        first, t1 = call()
+        assert L.map_batch_graph_stats(ctx) == (1, 0, 0)
+        for m in mass:
+            m.fill_(-1.0)
+        again, t2 = call()
+        assert L.map_batch_graph_stats(ctx) == (1, 1, 0)
+        for a, b in zip(first, again):
+            assert np.array_equal(a, b)
+        assert np.array_equal(t1, t2)
+        assert L.map_get_stats(ctx).n_pairs == sum(gpu_map(g, p, h, 1)["n_pairs"] for _, p, g, h in snapshots)
+
+        # new positions in the same buffers: moved by up to 1e-3, kept in the cube
+        rng = np.random.default_rng(5)
+        moved = []
+        for (_, p, g, h), t in zip(snapshots, keep):
+            q = synth.Particles(*(np.clip(c + rng.uniform(-1e-3, 1e-3, p.n), 0.0, 1.0) for c in (p.x, p.y, p.z)), p.m)
+            for dst, src in zip(t[:3], (q.x, q.y, q.z)):
+                dst.copy_(torch.as_tensor(src, device="cuda"))
+            moved.append(q)
+        got, _ = call()
+        assert L.map_batch_graph_stats(ctx) == (1, 2, 0)
+        for j, (_, p, g, h) in enumerate(snapshots):
+            assert np.array_equal(got[j], gpu_map(g, moved[j], h, 1)["mass"]), j
+
+        # h raised 1.6x: about 4x the pairs, beyond the captured buffers
+        for t in keep:
+            t[4].mul_(1.6)
+        grown, _ = call()
+        assert L.map_batch_graph_stats(ctx) == (2, 2, 1)
+        for j, (_, p, g, h) in enumerate(snapshots):
+            assert np.array_equal(grown[j], gpu_map(g, moved[j], 1.6 * h, 1)["mass"]), j
+
+        # an invalid particle: refused by the replay, the graph kept
+        keep[0][4][0] = float("nan")
+        with pytest.raises(L.MapError) as e:
+            call()
+        assert e.value.code == L.MAP_EINVAL
+        keep[0][4][0] = float(1.6 * snapshots[0][3][0])
+        again2, _ = call()
+        assert L.map_batch_graph_stats(ctx) == (2, 3, 1)  # the refused call counts as no replay
+        for a, b in zip(grown, again2):
+            assert np.array_equal(a, b)
+    finally:
+        L.map_destroy(ctx)
