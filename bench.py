@@ -501,6 +501,7 @@ def run_batch(args):
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     integ = []
     g0 = L.map_batch_graph_stats(ctx)
+    h0 = L.solve_h_batch_graph_stats(ctx)
     e0.record()
     for _ in range(args.steps):
         step()
@@ -513,10 +514,13 @@ def run_batch(args):
     work, l1 = L.map_get_work(ctx)
     chosen, tune_ms = L.map_get_autotune(ctx)
     g1 = L.map_batch_graph_stats(ctx)
+    h1 = L.solve_h_batch_graph_stats(ctx)
     phases = L.map_get_timing(ctx)
     graph = {"captures": g1[0] - g0[0], "replays": g1[1] - g0[1], "fallbacks": g1[2] - g0[2],
-             "note": "map_batch calls of the timed steps that replayed the whole captured step (validation, "
-                     "octrees, pair lists, work items, integral launch, sums) as one graph launch",
+             "solve_h_batch": {"captures": h1[0] - h0[0], "replays": h1[1] - h0[1]},
+             "note": "calls of the timed steps that replayed their whole captured step as one graph launch: "
+                     "map_batch (validation, octrees, pair lists, work items, integral launch, sums) and "
+                     "solve_h_batch (validation, octrees, h solve)",
              "phases_ms_last_step": {k: round(v, 3) for k, v in phases.items()}}
     integ_ms = float(np.mean(integ))
     batch_mass = [mm.cpu().numpy() for mm in mass]

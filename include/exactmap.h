@@ -448,9 +448,19 @@ int solve_h(map_ctx* ctx, map_particles* p, int32_t* route, void* stream);
  * solve_h on parts[j] alone gives; routes (NULL, or nsnap pointers each NULL
  * or n int32) as in solve_h.  The sets are solved by the context's workers,
  * several at once, each on its own stream, ordered after and before
- * `stream`; the call returns when all are done.  Errors: MAP_EINVAL,
- * MAP_ENOMEM, MAP_ECUDA (the first one met). */
+ * `stream`; the call returns when all are done.  As map_batch, the call
+ * captures its whole step after running it (validation, octree built
+ * without host reads, h solve, per set on its worker's stream) and a later
+ * call naming the same buffers (x, y, z, h, routes) and sizes replays it as
+ * one graph launch with one read of a flag word, computing from the
+ * buffers' current values (the same h, bit for bit).  Counting contexts
+ * never capture.  Errors: MAP_EINVAL, MAP_ENOMEM, MAP_ECUDA (the first one
+ * met). */
 int solve_h_batch(map_ctx* ctx, int nsnap, map_particles* parts, int32_t* const* routes, void* stream);
+
+/* Captures and replays of solve_h_batch's graph.  Either pointer may be NULL.
+ * Errors: MAP_EINVAL (ctx NULL). */
+int solve_h_batch_graph_stats(map_ctx* ctx, int64_t* captures, int64_t* replays);
 
 
 /* solve_h for callers that cannot allocate device memory (a process that has

@@ -142,11 +142,12 @@ _lib.map_get_autotune.argtypes = [_P, ctypes.POINTER(ctypes.c_int), ctypes.POINT
                                   ctypes.POINTER(ctypes.c_int)]
 _lib.map_batch_graph_stats.argtypes = [_P, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64),
                                        ctypes.POINTER(ctypes.c_int64)]
+_lib.solve_h_batch_graph_stats.argtypes = [_P, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64)]
 for _name in ("map_init", "map_grid_upload", "map_grid_release", "map_grid_volumes", "map_grid_build",
               "map_grid_sizes", "map_grid_copy", "map_particles_to_cells",
               "map_get_pairs", "map_copy_pairs", "map_cells_to_particles", "map_get_stats", "map_get_work",
               "map_get_timing", "solve_h", "build_pseudo_particles", "build_pseudo_particles_walk", "map_batch",
-              "map_get_autotune", "solve_h_batch", "map_batch_graph_stats"):
+              "map_get_autotune", "solve_h_batch", "map_batch_graph_stats", "solve_h_batch_graph_stats"):
     getattr(_lib, _name).restype = ctypes.c_int
 
 
@@ -271,6 +272,13 @@ def map_batch_graph_stats(ctx):
     """(captures, replays, fallbacks) of map_batch's whole-step graph."""
     v = [ctypes.c_int64() for _ in range(3)]
     _check(_lib.map_batch_graph_stats(ctx, *[ctypes.byref(x) for x in v]), "map_batch_graph_stats")
+    return tuple(x.value for x in v)
+
+
+def solve_h_batch_graph_stats(ctx):
+    """(captures, replays) of solve_h_batch's whole-step graph."""
+    v = [ctypes.c_int64() for _ in range(2)]
+    _check(_lib.solve_h_batch_graph_stats(ctx, *[ctypes.byref(x) for x in v]), "solve_h_batch_graph_stats")
     return tuple(x.value for x in v)
 
 

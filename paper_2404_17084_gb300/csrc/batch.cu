@@ -205,8 +205,7 @@ int integrals_autotune(map_ctx* ctx, const std::function<int(int, BatchArgs&)>& 
 
 static int64_t* gtot(map_ctx* ctx) { return static_cast<int64_t*>(ctx->bgraph.tot.p); }
 
-void batch_graph_drop(map_ctx* ctx) {
-  auto& G = ctx->bgraph;
+static void graph_drop(map_ctx* ctx, map_ctx::BatchGraph& G) {
   if (G.exec) {
     if (ctx->bstream) cudaStreamSynchronize(ctx->bstream);  // a replay may still run
     cudaGraphExecDestroy(G.exec);
@@ -223,6 +222,11 @@ void batch_graph_drop(map_ctx* ctx) {
   }
   G.sig.clear();
   G.bufs.clear();
+}
+
+void batch_graph_drop(map_ctx* ctx) {
+  graph_drop(ctx, ctx->bgraph);
+  graph_drop(ctx, ctx->hgraph);
 }
 
 namespace {
@@ -250,7 +254,7 @@ std::vector<unsigned char> graph_sig(map_ctx* ctx, int nsnap, const map_particle
 }
 
 // every workspace allocation the graph reads or writes
-std::vector<const void*> graph_bufs(map_ctx* ctx, int nsnap) {
+std::vector<const void*> graph_bufs(map_ctx* ctx, int nsnap, const map_ctx::BatchGraph& G) {
   std::vector<const void*> v;
   for (BatchWorker& W : ctx->workers) {
     map_ctx* c = W.ctx;
@@ -262,8 +266,7 @@ std::vector<const void*> graph_bufs(map_ctx* ctx, int nsnap) {
   }
   for (auto* vec : {&ctx->batch_off, &ctx->batch_idx, &ctx->batch_itm, &ctx->batch_ioff, &ctx->batch_part})
     for (int j = 0; j < nsnap; ++j) v.push_back((*vec)[j].p);
-  auto& G = ctx->bgraph;
-  for (DevBuf* b : {&G.desc, &G.base, &G.tot, &G.caps, &G.flags}) v.push_back(b->p);
+  for (const DevBuf* b : {&G.desc, &G.base, &G.tot, &G.caps, &G.flags}) v.push_back(b->p);
   v.push_back(ctx->d_counters);
   v.push_back(ctx->d_total);
   return v;
@@ -358,7 +361,7 @@ constexpr int GRAPH_FALLBACK = -1000;  // internal: the replay's lists outgrew t
 int batch_graph_build(map_ctx* ctx, int nsnap, const map_particles* parts, const int* grids,
                       const map_outputs* outs, const std::vector<int64_t>& np, const std::vector<int>& order,
                       cudaStream_t s) {
-  batch_graph_drop(ctx);
+  graph_drop(ctx, ctx->bgraph);
   auto& G = ctx->bgraph;
   MAP_TRY(ensure_workers(ctx));
   std::vector<int64_t> caps(2 * nsnap);
@@ -387,7 +390,7 @@ int batch_graph_build(map_ctx* ctx, int nsnap, const map_particles* parts, const
   CUDA_TRY(cudaStreamSynchronize(ctx->bstream));
   if (ctx->h_scratch[2] != 0) return MAP_ECAPACITY;
   // 2. the same, captured
-  const std::vector<const void*> bufs0 = graph_bufs(ctx, nsnap);
+  const std::vector<const void*> bufs0 = graph_bufs(ctx, nsnap, ctx->bgraph);
   const int64_t l0 = ctx->launches;
   std::vector<int64_t> wl0;
   for (BatchWorker& W : ctx->workers) wl0.push_back(W.ctx->launches);
@@ -401,7 +404,7 @@ int batch_graph_build(map_ctx* ctx, int nsnap, const map_particles* parts, const
     ctx->workers[w].ctx->launches = wl0[w];
   }
   ctx->launches = l0;
-  if (rc != MAP_OK || ce != cudaSuccess || graph_bufs(ctx, nsnap) != bufs0) {
+  if (rc != MAP_OK || ce != cudaSuccess || graph_bufs(ctx, nsnap, ctx->bgraph) != bufs0) {
     if (graph) cudaGraphDestroy(graph);
     cudaGetLastError();
     return rc != MAP_OK ? rc : MAP_ECUDA;
@@ -463,6 +466,134 @@ int batch_graph_replay(map_ctx* ctx, int nsnap, const int* grids, const map_outp
 
 }  // namespace
 
+// ---------------------------------------------------------------- solve_h_batch as one graph
+// The same scheme for solve_h_batch: per set (on the worker run_on_workers
+// gives it) the validation and the h solve over an octree built without host
+// reads; one flag word read back.  Replayed while the call names the same
+// buffers (positions, h, routes) and sizes.
+
+namespace {
+
+__global__ void any_flag(int n, const unsigned long long* __restrict__ f, int64_t* out) {
+  if (blockIdx.x != 0 || threadIdx.x != 0) return;
+  int64_t b = 0;
+  for (int i = 0; i < n; ++i) b |= f[i] ? 1 : 0;
+  out[0] = b;
+}
+
+std::vector<unsigned char> hgraph_sig(map_ctx* ctx, int nsnap, const map_particles* parts, int32_t* const* routes) {
+  std::vector<unsigned char> v;
+  auto put = [&](const void* p, size_t n) {
+    const unsigned char* c = static_cast<const unsigned char*>(p);
+    v.insert(v.end(), c, c + n);
+  };
+  const double hf = ctx->cfg.hfact;
+  const int64_t head[3] = {nsnap, ctx->cfg.precision, ctx->cfg.leaf_size};
+  put(head, sizeof(head));
+  put(&hf, sizeof(hf));
+  for (int j = 0; j < nsnap; ++j) {
+    const void* ptr[5] = {parts[j].x, parts[j].y, parts[j].z, parts[j].h, routes ? routes[j] : nullptr};
+    put(ptr, sizeof(ptr));
+    put(&parts[j].n, sizeof(parts[j].n));
+  }
+  return v;
+}
+
+int hgraph_enqueue(map_ctx* ctx, int nsnap, map_particles* parts, int32_t* const* routes, bool capturing) {
+  auto& G = ctx->hgraph;
+  cudaStream_t bs = ctx->bstream;
+  const int W = (int)ctx->workers.size();
+  std::vector<int> big(nsnap);
+  std::iota(big.begin(), big.end(), 0);
+  std::stable_sort(big.begin(), big.end(), [&](int a, int b) { return parts[a].n > parts[b].n; });
+  unsigned long long* flags = static_cast<unsigned long long*>(G.flags.p);
+  gphase(ctx, 3, false, bs, capturing);
+  CUDA_TRY(cudaEventRecord(ctx->wev, bs));
+  for (BatchWorker& Wk : ctx->workers) CUDA_TRY(cudaStreamWaitEvent(Wk.stream, ctx->wev, 0));
+  for (int r = 0; r < nsnap; ++r) {
+    const int j = big[r];
+    BatchWorker& Wk = ctx->workers[r % W];
+    map_ctx* wc = Wk.ctx;
+    wc->cur_stream = Wk.stream;
+    map_particles* p = &parts[j];
+    CUDA_TRY(cudaMemsetAsync(flags + j, 0, sizeof(unsigned long long), Wk.stream));
+    MAP_TRY(validate_enqueue(wc, p, false, false, flags + j, Wk.stream));
+    MAP_TRY(h_solve_run(wc, p->x, p->y, p->z, p->n, p->h, routes ? routes[j] : nullptr, nullptr, Wk.stream, true));
+  }
+  for (BatchWorker& Wk : ctx->workers) {
+    CUDA_TRY(cudaEventRecord(Wk.done, Wk.stream));
+    CUDA_TRY(cudaStreamWaitEvent(bs, Wk.done, 0));
+  }
+  any_flag<<<1, 1, 0, bs>>>(nsnap, flags, static_cast<int64_t*>(G.tot.p)); ++ctx->launches;
+  CUDA_TRY(cudaGetLastError());
+  gphase(ctx, 3, true, bs, capturing);
+  return MAP_OK;
+}
+
+int hgraph_build(map_ctx* ctx, int nsnap, map_particles* parts, int32_t* const* routes, cudaStream_t s) {
+  auto& G = ctx->hgraph;
+  graph_drop(ctx, G);
+  MAP_TRY(ensure_workers(ctx));
+  unsigned long long* f;
+  int64_t* t;
+  MAP_TRY(ensure_t(ctx, G.flags, nsnap, &f));
+  MAP_TRY(ensure_t(ctx, G.tot, 4, &t));
+  CUDA_TRY(cudaEventRecord(ctx->bev[0], s));
+  CUDA_TRY(cudaStreamWaitEvent(ctx->bstream, ctx->bev[0], 0));
+  MAP_TRY(hgraph_enqueue(ctx, nsnap, parts, routes, false));  // sizes every workspace
+  CUDA_TRY(cudaMemcpyAsync(ctx->h_scratch, t, sizeof(int64_t), cudaMemcpyDeviceToHost, ctx->bstream));
+  CUDA_TRY(cudaStreamSynchronize(ctx->bstream));
+  if (ctx->h_scratch[0] != 0) return MAP_EINVAL;
+  const std::vector<const void*> bufs0 = graph_bufs(ctx, 0, G);
+  const int64_t l0 = ctx->launches;
+  std::vector<int64_t> wl0;
+  for (BatchWorker& W : ctx->workers) wl0.push_back(W.ctx->launches);
+  CUDA_TRY(cudaStreamBeginCapture(ctx->bstream, cudaStreamCaptureModeThreadLocal));
+  const int rc = hgraph_enqueue(ctx, nsnap, parts, routes, true);
+  cudaGraph_t graph = nullptr;
+  const cudaError_t ce = cudaStreamEndCapture(ctx->bstream, &graph);
+  int64_t launched = ctx->launches - l0;
+  for (size_t w = 0; w < ctx->workers.size(); ++w) {
+    launched += ctx->workers[w].ctx->launches - wl0[w];
+    ctx->workers[w].ctx->launches = wl0[w];
+  }
+  ctx->launches = l0;
+  if (rc != MAP_OK || ce != cudaSuccess || graph_bufs(ctx, 0, G) != bufs0) {
+    if (graph) cudaGraphDestroy(graph);
+    cudaGetLastError();
+    return rc != MAP_OK ? rc : MAP_ECUDA;
+  }
+  const cudaError_t ie = cudaGraphInstantiate(&G.exec, graph, 0);
+  cudaGraphDestroy(graph);
+  if (ie != cudaSuccess) {
+    G.exec = nullptr;
+    cudaGetLastError();
+    return MAP_ECUDA;
+  }
+  G.sig = hgraph_sig(ctx, nsnap, parts, routes);
+  G.bufs = bufs0;
+  G.launches = launched;
+  ++G.captures;
+  return MAP_OK;
+}
+
+int hgraph_replay(map_ctx* ctx, cudaStream_t s) {
+  auto& G = ctx->hgraph;
+  CUDA_TRY(cudaEventRecord(ctx->bev[0], s));
+  CUDA_TRY(cudaStreamWaitEvent(ctx->bstream, ctx->bev[0], 0));
+  CUDA_TRY(cudaGraphLaunch(G.exec, ctx->bstream));
+  ctx->launches += G.launches;
+  CUDA_TRY(cudaMemcpyAsync(ctx->h_scratch, G.tot.p, sizeof(int64_t), cudaMemcpyDeviceToHost, ctx->bstream));
+  CUDA_TRY(cudaStreamSynchronize(ctx->bstream));
+  if (ctx->h_scratch[0] != 0) return MAP_EINVAL;
+  ++G.replays;
+  CUDA_TRY(cudaEventRecord(ctx->bev[1], ctx->bstream));
+  CUDA_TRY(cudaStreamWaitEvent(s, ctx->bev[1], 0));
+  return MAP_OK;
+}
+
+}  // namespace
+
 // The host-side part of check_particles (pointers and count), for a batch
 // before its workers start.
 static bool check_sizes(const map_particles* p) {
@@ -477,6 +608,14 @@ int solve_h_batch(map_ctx* ctx, int nsnap, map_particles* parts, int32_t* const*
     if (!check_sizes(&parts[j]) || !parts[j].h) return MAP_EINVAL;
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
   MAP_ENTER(ctx, s);
+  MAP_TRY(ensure_stream(ctx));
+  const bool graphable = ctx->cfg.count_work == 0;
+  if (ctx->hgraph.exec) {
+    if (graphable && ctx->hgraph.sig == hgraph_sig(ctx, nsnap, parts, routes) &&
+        ctx->hgraph.bufs == graph_bufs(ctx, 0, ctx->hgraph))
+      return hgraph_replay(ctx, s);
+    graph_drop(ctx, ctx->hgraph);
+  }
   std::vector<int> big(nsnap);
   std::iota(big.begin(), big.end(), 0);
   std::stable_sort(big.begin(), big.end(), [&](int a, int b) { return parts[a].n > parts[b].n; });
@@ -488,7 +627,13 @@ int solve_h_batch(map_ctx* ctx, int nsnap, map_particles* parts, int32_t* const*
     return h_solve_run(W.ctx, p->x, p->y, p->z, p->n, p->h, routes ? routes[j] : nullptr, nullptr, W.stream);
   });
   phase_end(ctx, 3, s);
-  return rc;
+  if (rc != MAP_OK) return rc;
+  // capture the step for the calls that repeat this one (optional)
+  if (graphable && hgraph_build(ctx, nsnap, parts, routes, s) != MAP_OK) {
+    graph_drop(ctx, ctx->hgraph);
+    cudaGetLastError();
+  }
+  return MAP_OK;
 }
 
 
@@ -508,11 +653,11 @@ int map_batch(map_ctx* ctx, int nsnap, const map_particles* parts, const int* gr
   const bool graphable = ctx->cfg.count_work == 0;
   if (ctx->bgraph.exec) {
     if (graphable && (int)ctx->batch_off.size() >= nsnap && ctx->bgraph.sig == graph_sig(ctx, nsnap, parts, grids, outs) &&
-        ctx->bgraph.bufs == graph_bufs(ctx, nsnap)) {
+        ctx->bgraph.bufs == graph_bufs(ctx, nsnap, ctx->bgraph)) {
       const int rc = batch_graph_replay(ctx, nsnap, grids, outs, totals, s);
       if (rc != GRAPH_FALLBACK) return rc;
     }
-    batch_graph_drop(ctx);
+    graph_drop(ctx, ctx->bgraph);
   }
   if ((int)ctx->batch_off.size() < nsnap) {
     ctx->batch_off.resize(nsnap);
@@ -692,7 +837,7 @@ int map_batch(map_ctx* ctx, int nsnap, const map_particles* parts, const int* gr
   // capture the step for the calls that repeat this one (optional: on any
   // failure there is no graph, and this call's results stand)
   if (graphable && batch_graph_build(ctx, nsnap, parts, grids, outs, np, order, s) != MAP_OK) {
-    batch_graph_drop(ctx);
+    graph_drop(ctx, ctx->bgraph);
     cudaGetLastError();
   }
   return MAP_OK;
@@ -703,6 +848,13 @@ int map_batch_graph_stats(map_ctx* ctx, int64_t* captures, int64_t* replays, int
   if (captures) *captures = ctx->bgraph.captures;
   if (replays) *replays = ctx->bgraph.replays;
   if (fallbacks) *fallbacks = ctx->bgraph.fallbacks;
+  return MAP_OK;
+}
+
+int solve_h_batch_graph_stats(map_ctx* ctx, int64_t* captures, int64_t* replays) {
+  if (!ctx) return MAP_EINVAL;
+  if (captures) *captures = ctx->hgraph.captures;
+  if (replays) *replays = ctx->hgraph.replays;
   return MAP_OK;
 }
 

@@ -511,8 +511,9 @@ __global__ void gather_h0(int64_t n, const int32_t* __restrict__ idx, const doub
 }  // namespace
 
 int h_solve_run(map_ctx* ctx, const double* x, const double* y, const double* z, int64_t n, double* h, int32_t* route,
-                const double* h0_override, cudaStream_t s) {
-  MAP_TRY(tree_build(ctx, x, y, z, nullptr, nullptr, n, s));
+                const double* h0_override, cudaStream_t s, bool graph) {
+  if (graph) MAP_TRY(tree_build_graph(ctx, x, y, z, nullptr, nullptr, n, s));
+  else MAP_TRY(tree_build(ctx, x, y, z, nullptr, nullptr, n, s));
   DevTree& T = ctx->tree;
   double* h0s;
   MAP_TRY(ensure_t(ctx, ctx->ws_tree[22], n, &h0s));

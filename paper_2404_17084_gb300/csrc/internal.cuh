@@ -215,7 +215,7 @@ struct map_ctx {
     int64_t launches = 0;                 // kernels per replay
     DevBuf desc, base, tot, caps, flags;  // its own descriptors, queue bases, totals, capacities, flags
     int64_t captures = 0, replays = 0, fallbacks = 0;
-  } bgraph;
+  } bgraph, hgraph;  // map_batch's step; solve_h_batch's step (its flags in tot)
   std::vector<BatchWorker> workers;  // created by the first batch call that uses them
   cudaEvent_t wev = nullptr;         // the caller's stream, before the workers start
   // MAP_TABLE: the table of the pyramid integral (n^3 FP32 texels)
@@ -394,8 +394,10 @@ void destroy_workers(map_ctx* ctx);
 // Drops the batch graph (its inputs changed place: a grid released, a
 // workspace reallocated) and frees its buffers.
 void batch_graph_drop(map_ctx* ctx);
+// (graph: the octree from tree_build_graph, so that the call reads nothing
+// back and can be captured; the same tree, the same h)
 int h_solve_run(map_ctx* ctx, const double* x, const double* y, const double* z, int64_t n, double* h,
-                int32_t* route, const double* h0_override, cudaStream_t s);
+                int32_t* route, const double* h0_override, cudaStream_t s, bool graph = false);
 int pseudo_run(map_ctx* ctx, const map_particles* full, const map_walk* walk, map_particles* out, int32_t* kind,
                int64_t* ident, int64_t* n_pseudo, cudaStream_t s);
 

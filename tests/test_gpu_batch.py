@@ -183,3 +183,43 @@ def test_batch_whole_step_graph(snapshots):
             assert np.array_equal(a, b)
     finally:
         L.map_destroy(ctx)
+
+
+def test_solve_h_batch_graph_replay(snapshots):
+    """solve_h_batch captures its step after the first call; a call on the
+    same buffers with moved positions replays it and gives solve_h's h and
+    routes on the moved sets, bit for bit; an out-of-cube position is
+    refused by the replay."""
+    L = lib()
+    ctx = L.map_init(L.map_config_default(precision=1))
+    try:
+        sets = [dev_particles(p) for _, p, _, _ in snapshots]
+        routes = [torch.empty(p.n, dtype=torch.int32, device="cuda") for _, p, _, _ in snapshots]
+        hp = [L.make_particles(x, y, z, None, h) for x, y, z, _, h in sets]
+        L.solve_h_batch(ctx, hp, routes)
+        assert L.solve_h_batch_graph_stats(ctx) == (1, 0)
+        rng = np.random.default_rng(7)
+        for (x, y, z, _, _), (_, p, _, _) in zip(sets, snapshots):
+            for t in (x, y, z):
+                t.copy_(torch.clamp(t + torch.as_tensor(rng.uniform(-1e-3, 1e-3, p.n), device="cuda"), 0.0, 1.0))
+        L.solve_h_batch(ctx, hp, routes)
+        torch.cuda.synchronize()
+        assert L.solve_h_batch_graph_stats(ctx) == (1, 1)
+        got = [(t[4].cpu().numpy().copy(), r.cpu().numpy().copy()) for t, r in zip(sets, routes)]
+        ref_ctx = L.map_init(L.map_config_default(precision=1))
+        try:
+            for j, (x, y, z, _, _) in enumerate(sets):
+                h1 = torch.empty_like(x)
+                r1 = torch.empty_like(routes[j])
+                L.solve_h(ref_ctx, L.make_particles(x, y, z, None, h1), r1)
+                torch.cuda.synchronize()
+                assert np.array_equal(got[j][0], h1.cpu().numpy()), j
+                assert np.array_equal(got[j][1], r1.cpu().numpy()), j
+        finally:
+            L.map_destroy(ref_ctx)
+        sets[1][0][3] = 1.5
+        with pytest.raises(L.MapError) as e:
+            L.solve_h_batch(ctx, hp, routes)
+        assert e.value.code == L.MAP_EINVAL
+    finally:
+        L.map_destroy(ctx)
