@@ -161,9 +161,11 @@ OPS = {
 # count (the kernel streams the same per-pair data at any size).  It belongs
 # to the kernel as captured: set it to None when the kernel changes.
 INTEGRAL_DRAM_BYTES_PER_PAIR = 49.3
-# DRAM bytes per pair of one inverse-mapping sum (inv_apply): None -- the
-# kernel now gathers in Morton order, and no capture of it has been taken.
-INVERSE_DRAM_BYTES_PER_PAIR = None
+# DRAM bytes per pair of one inverse-mapping sum (inv_apply, Morton-ordered
+# gather): 449.6 MB read + written for 32,168,427 pairs in ncu on the 2^18
+# clumpy snapshot, scaled by pair count like the figure above; None once the
+# kernel changes.
+INVERSE_DRAM_BYTES_PER_PAIR = 13.97
 
 
 def counted_work(L, torch, precision, device, grids, dev, parts):
