@@ -435,8 +435,9 @@ void map_server_destroy(map_server* srv);
  * (self term included) for every particle: Newton-Raphson (at most 30
  * iterations, converged at |dh|/h < 1e-10), else bisection on
  * [h0/16, 16 h0] (|dh|/h < 1e-12), else the estimate h0.  A MAP_MIXED
- * context sums the kernel in FP32 (on FP32 hi/lo splits of the coordinates)
- * and stops Newton at |dh|/h < 1e-6, which gives h to ~1e-7 relative.  The
+ * context sums the kernel in FP32 (on FP32 hi/lo splits of the coordinates),
+ * in the bisection too, and stops Newton at |dh|/h < 1e-6, which gives h to
+ * ~1e-7 relative.  The
  * initial guess
  * h0 is hfact * (side of the particle's octree leaf cube) / (leaf count)^(1/3).
  * Writes p->h; route (optional, n int32) receives 0 Newton, 1 bisection,

@@ -23,8 +23,8 @@
 // bisection rules are those of the per-particle definition; only the order
 // of the sums differs.
 //
-// Mixed build: Newton sums and the Newton step in FP32 (on hi/lo-split
-// coordinates), stop at |dh| < 1e-6 h; bisection sums in FP64.  FP64 build: every sum in FP64 behind
+// Mixed build: Newton and bisection sums and the Newton step in FP32 (on
+// hi/lo-split coordinates), stop at |dh| < 1e-6 h.  FP64 build: every sum in FP64 behind
 // an FP32 distance screen with a 1e-5 relative margin, stop at 1e-10.
 #include "internal.cuh"
 
@@ -441,9 +441,12 @@ __global__ void __launch_bounds__(HS_WARPS * 32)
       }
       int r = 0;
       if (!ok) {
+        // (the mixed build bisects on its FP32 sums too: the root moves by
+        // ~1e-7 relative, inside the build's 1e-6, and GB300's FP64 rate
+        // is 1/64 of its FP32 rate)
         auto g = [&](double hh) {
           double nn, dn;
-          warp_density<false>(T, W, B, k, hh, nn, dn);
+          warp_density<MIXED>(T, W, B, k, hh, nn, dn);
           return hh - hfact * rcbrt(nn);
         };
         // Bisection on [lo, hi] needs g(lo) < 0 < g(hi).  g(h)/h is
