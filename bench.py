@@ -1254,7 +1254,9 @@ def inverse_run(L, torch, ctx, g, n, n_pairs, mass, m, dev, reps=20):
 def e2e_run(L, torch, ctx, p, g, dev, args, barrier, world):
     """Same metric through the public API: pinned host inputs copied in (the
     particles by torch, the grid by map_grid_upload itself), the grid
-    prepared, solve_h + mapping, cell masses read back."""
+    prepared, solve_h + mapping, cell masses read back.  The h solve needs
+    only the particles, so it runs on a second context and stream while the
+    grid is copied in and prepared (calls of one context run in order)."""
     pin = lambda a, dt: torch.as_tensor(np.ascontiguousarray(a), dtype=dt).pin_memory()
     hp = [pin(a, torch.float64) for a in (p.x, p.y, p.z, p.m)]
     hg = dict(cell_face_off=pin(g.cell_face_off, torch.int64), face_vert_off=pin(g.face_vert_off, torch.int64),
@@ -1265,11 +1267,18 @@ def e2e_run(L, torch, ctx, p, g, dev, args, barrier, world):
     h2d = sum(t.numel() * t.element_size() for t in hp) + sum(t.numel() * t.element_size() for t in hg.values())
     d2h = out_host.numel() * out_host.element_size()
 
+    ctx_h = L.map_init(L.map_config_default(precision=L.MAP_MIXED, device=dev.index or 0))
+    side = torch.cuda.Stream(device=dev)
+
     def one():
+        main = torch.cuda.current_stream(dev)
         dp = [t.to(dev, non_blocking=True) for t in hp]
-        handle = L.map_grid_upload(ctx, hg)
         hh = torch.empty_like(dp[0])
-        L.solve_h(ctx, L.make_particles(dp[0], dp[1], dp[2], None, hh))
+        side.wait_stream(main)
+        with torch.cuda.stream(side):
+            L.solve_h(ctx_h, L.make_particles(dp[0], dp[1], dp[2], None, hh), stream=side)
+        handle = L.map_grid_upload(ctx, hg)
+        main.wait_stream(side)
         mass = torch.empty(g.ncell, dtype=torch.float64, device=dev)
         L.map_particles_to_cells(ctx, L.make_particles(dp[0], dp[1], dp[2], dp[3], hh), handle, mass)
         out_host.copy_(mass, non_blocking=True)
@@ -1277,17 +1286,21 @@ def e2e_run(L, torch, ctx, p, g, dev, args, barrier, world):
         L.map_grid_release(ctx, handle)
         return L.map_get_stats(ctx).n_pairs
 
-    steps = max(1, args.steps // 2)
-    one()
-    barrier()
-    t0 = time.perf_counter()
-    npairs = 0
-    for _ in range(steps):
-        npairs = one()
-    barrier()
-    sec = (time.perf_counter() - t0) / steps
+    try:
+        steps = max(1, args.steps // 2)
+        one()
+        barrier()
+        t0 = time.perf_counter()
+        npairs = 0
+        for _ in range(steps):
+            npairs = one()
+        barrier()
+        sec = (time.perf_counter() - t0) / steps
+    finally:
+        L.map_destroy(ctx_h)
     return {"value": npairs * world / sec, "unit": "pair integrals/s", "h2d_bytes_per_step": int(h2d),
-            "d2h_bytes_per_step": int(d2h), "ms_per_step": sec * 1e3, "steps": steps}
+            "d2h_bytes_per_step": int(d2h), "ms_per_step": sec * 1e3, "steps": steps,
+            "note": "solve_h on a second context and stream, beside the grid upload"}
 
 
 def oracle_sample(p, g, h, ncells: int, seed: int = 7):
