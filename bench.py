@@ -361,6 +361,22 @@ def run_ours(args):
                      mass_mixed_h64=mass_mixed_h64, h_mixed=h_mixed, h_fp64=h_fp64)
         fp64 = {"value": st64.n_pairs * world / (ms64 * 1e-3), "ms_per_step": ms64, "steps": 1, "warmup": 0,
                 "integrals_ms": integ64, "phases_ms": {k: round(v, 3) for k, v in phases64.items()}}
+        # the FP64 kernel against the measured FP64 FMA rate: the op model of
+        # the FP64 form (closed-form middle pieces), every op on the FP64 pipe
+        # (its divides, square roots and arctangents are FP64 sequences; the
+        # model counts each as one MUFU op, so this bound is a lower one)
+        try:
+            h64 = torch.from_numpy(h_fp64).to(dev)  # kept alive through the call
+            terms64, work64 = counted_work(L, torch, L.MAP_FP64, local, g, dev, L.make_particles(x, y, z, m, h64))
+            f64_ops, f64_mufu = algorithmic_ops(work64, terms64, False)
+            dfma = L.map_device_peaks(local)["dfma"]
+            frac64 = (f64_ops + f64_mufu) / dfma / (integ64 * 1e-3)
+            fp64["roofline"] = {"bound": "fp64", "kernel": "pair_integrals<double>", "achieved": frac64 * dfma / 1e12,
+                                "peak": dfma / 1e12, "unit": "Tops/s (FP64 FMA issue)", "frac": frac64,
+                                "ops": int(f64_ops + f64_mufu), "launch_ms": integ64,
+                                "peak_source": "measured: FP64 FMA microbenchmark (map_device_peaks)"}
+        except Exception as exc:  # reported, not fatal
+            fp64["roofline"] = {"error": str(exc)}
         # the table variant (the paper's production route): its own timed
         # steps, then one mapping on the FP64 build's h for its error alone
         ctxt, handlet = setup(L.MAP_TABLE)

@@ -137,3 +137,28 @@ def test_cells_match_oracle_16k_clumpy_sampled():
     sub.face_plane = g.face_plane.reshape(-1, 4)[faces]
     sub.vx, sub.vy, sub.vz, sub.site = g.vx, g.vy, g.vz, g.site.reshape(-1, 3)[which]
     compare_cells(sub, ref, tol_v=1e-12)
+
+
+def test_full_size_build_sampled_cells():
+    """The bench's tessellation at full size: the 2^20 clumpy snapshot's
+    positions, sites merged below 1e-6 of the mean spacing, 5 Lloyd
+    iterations, the final cells.  32 sampled cells of the GPU grid against
+    the oracle's cells of the same final sites (each built against all of
+    them): face counts, vertices and volumes as above."""
+    n = 1 << 20
+    pos = synth.lognormal_particles(n, synth.BASE_SEED + 2, sigma=1.5).pos()
+    g, kept = gpu_build(pos, lloyd=5, merge_tol=1e-6 * n ** (-1.0 / 3.0))
+    sites = g.site.reshape(-1, 3)
+    assert len(sites) == len(kept) > 0.99 * n
+    which = np.sort(np.random.default_rng(13).choice(len(sites), 32, replace=False))
+    ref = oracle.VoronoiGrid(oracle.voronoi_cells_of(sites, which), sites[which])
+    sub = HostGrid({})
+    cfo, fvo = g.cell_face_off, g.face_vert_off
+    faces = np.concatenate([np.arange(cfo[c], cfo[c + 1]) for c in which])
+    sub.cell_face_off = np.concatenate([[0], np.cumsum(np.diff(cfo)[which])]).astype(np.int64)
+    nl = fvo[faces + 1] - fvo[faces]
+    sub.face_vert_off = np.concatenate([[0], np.cumsum(nl)]).astype(np.int64)
+    sub.face_vert = np.concatenate([g.face_vert[fvo[f]:fvo[f + 1]] for f in faces]).astype(np.int32)
+    sub.face_plane = g.face_plane.reshape(-1, 4)[faces]
+    sub.vx, sub.vy, sub.vz, sub.site = g.vx, g.vy, g.vz, sites[which]
+    compare_cells(sub, ref, tol_v=1e-12)
