@@ -30,7 +30,8 @@
 
 namespace {
 
-constexpr int HS_WARPS = 4;     // warps per block
+constexpr int HS_WARPS = 2;     // warps per block: small blocks free their SM slots as soon as their
+                                // warps end, and a warp's leaves take very different times
 constexpr int HS_RNG = 384;     // particle ranges held per warp
 constexpr int HS_CAP = 1024;    // candidate positions held per warp (a multiple of 32)
 // Depth-first stack: the tree has at most 22 levels and a popped node pushes at

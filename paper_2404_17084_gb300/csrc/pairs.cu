@@ -98,6 +98,7 @@ __device__ __forceinline__ bool pair_rule(const PairGrid& G, const PairTree& T, 
 // off[c] (the cells of `order` whose count exceeded the row; their number is
 // read from *n_dev).
 constexpr int PAIR_ROW = 256;
+constexpr int PT_WARPS = 4;  // warps per block of the traversal (1 and 2 measured: no faster)
 
 struct WalkCells {  // per warp: the 32 lanes' cells, one entry per lane
   float hx[32], lx[32], hy[32], ly[32], hz[32], lz[32], R[32];
@@ -106,13 +107,13 @@ struct WalkCells {  // per warp: the 32 lanes' cells, one entry per lane
 };
 
 template <bool FILL>
-__global__ void __launch_bounds__(128) pair_traverse(int64_t ncell, const int32_t* __restrict__ order, PairTree T,
-                                                     PairGrid G, int64_t* count, const int64_t* __restrict__ off,
-                                                     int32_t* out, const unsigned long long* n_dev,
-                                                     int64_t cap = INT64_MAX) {
-  __shared__ int32_t s_stack[4][200];
+__global__ void __launch_bounds__(PT_WARPS * 32)
+    pair_traverse(int64_t ncell, const int32_t* __restrict__ order, PairTree T, PairGrid G, int64_t* count,
+                  const int64_t* __restrict__ off, int32_t* out, const unsigned long long* n_dev,
+                  int64_t cap = INT64_MAX) {
+  __shared__ int32_t s_stack[PT_WARPS][200];
   if (FILL && off[ncell] > cap) return;  // the list does not fit its buffer: nothing is written
-  __shared__ WalkCells s_cells[4];
+  __shared__ WalkCells s_cells[PT_WARPS];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const unsigned lt = (1u << lane) - 1u;
   const int64_t t = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x);
@@ -449,7 +450,7 @@ int pairs_build(map_ctx* ctx, const PreparedGrid* g, cudaStream_t s, const PairB
   if (per_warp)
     pair_walk_warp<false><<<(unsigned)((nc + 3) / 4), tpb, 0, s>>>(nc, nullptr, PT, PG, count, nullptr, rows, nullptr);
   else
-    pair_traverse<false><<<nblk(nc, tpb), tpb, 0, s>>>(nc, order, PT, PG, count, nullptr, rows, nullptr);
+    pair_traverse<false><<<nblk(nc, PT_WARPS * 32), PT_WARPS * 32, 0, s>>>(nc, order, PT, PG, count, nullptr, rows, nullptr);
   ++ctx->launches;
   CUDA_TRY(cudaGetLastError());
   tb = 0;
@@ -473,7 +474,7 @@ int pairs_build(map_ctx* ctx, const PreparedGrid* g, cudaStream_t s, const PairB
   if (per_warp)
     pair_walk_warp<true><<<(unsigned)((nc + 3) / 4), tpb, 0, s>>>(nc, ovf, PT, PG, nullptr, off, list, d_novf);
   else
-    pair_traverse<true><<<nblk(nc, tpb), tpb, 0, s>>>(nc, ovf, PT, PG, nullptr, off, list, d_novf);
+    pair_traverse<true><<<nblk(nc, PT_WARPS * 32), PT_WARPS * 32, 0, s>>>(nc, ovf, PT, PG, nullptr, off, list, d_novf);
   ++ctx->launches;
   CUDA_TRY(cudaGetLastError());
   ctx->n_pairs = np;
@@ -552,7 +553,7 @@ int pairs_build_graph(map_ctx* ctx, const PreparedGrid* g, cudaStream_t s, const
   if (per_warp)
     pair_walk_warp<false><<<(unsigned)((nc + 3) / 4), tpb, 0, s>>>(nc, nullptr, PT, PG, count, nullptr, rows, nullptr);
   else
-    pair_traverse<false><<<nblk(nc, tpb), tpb, 0, s>>>(nc, order, PT, PG, count, nullptr, rows, nullptr);
+    pair_traverse<false><<<nblk(nc, PT_WARPS * 32), PT_WARPS * 32, 0, s>>>(nc, order, PT, PG, count, nullptr, rows, nullptr);
   ++ctx->launches;
   CUDA_TRY(cudaGetLastError());
   tb = 0;
@@ -571,7 +572,7 @@ int pairs_build_graph(map_ctx* ctx, const PreparedGrid* g, cudaStream_t s, const
     pair_walk_warp<true><<<(unsigned)((nc + 3) / 4), tpb, 0, s>>>(nc, ovf, PT, PG, nullptr, off, list, d_novf,
                                                                   cap_pairs);
   else
-    pair_traverse<true><<<nblk(nc, tpb), tpb, 0, s>>>(nc, ovf, PT, PG, nullptr, off, list, d_novf, cap_pairs);
+    pair_traverse<true><<<nblk(nc, PT_WARPS * 32), PT_WARPS * 32, 0, s>>>(nc, ovf, PT, PG, nullptr, off, list, d_novf, cap_pairs);
   ++ctx->launches;
   CUDA_TRY(cudaGetLastError());
   // the work items (the item size from the device-side pair count)
