@@ -99,6 +99,11 @@ __device__ __forceinline__ bool pair_rule(const PairGrid& G, const PairTree& T, 
 // read from *n_dev).
 constexpr int PAIR_ROW = 256;
 constexpr int PT_WARPS = 4;  // warps per block of the traversal (1 and 2 measured: no faster)
+// CTAs per SM the traversal is compiled for: 12 caps it at 40 registers (a
+// few spilled) for 48 resident warps; the walk waits on its node and
+// candidate loads, so the extra warps pay (2^20: 15.2 ms at 64 registers,
+// 14.0 at 48, 13.6 at 40, 16.1 at 32)
+constexpr int PT_MINB = 12;
 
 struct WalkCells {  // per warp: the 32 lanes' cells, one entry per lane
   float hx[32], lx[32], hy[32], ly[32], hz[32], lz[32], R[32];
@@ -107,7 +112,7 @@ struct WalkCells {  // per warp: the 32 lanes' cells, one entry per lane
 };
 
 template <bool FILL>
-__global__ void __launch_bounds__(PT_WARPS * 32)
+__global__ void __launch_bounds__(PT_WARPS * 32, PT_MINB)
     pair_traverse(int64_t ncell, const int32_t* __restrict__ order, PairTree T, PairGrid G, int64_t* count,
                   const int64_t* __restrict__ off, int32_t* out, const unsigned long long* n_dev,
                   int64_t cap = INT64_MAX) {
