@@ -115,7 +115,8 @@ def test_solve_h_batch_equals_single(snapshots, precision):
         L.map_destroy(ctx)
 
 
-def test_batch_whole_step_graph(snapshots):
+@pytest.mark.parametrize("precision", [1, 0])
+def test_batch_whole_step_graph(snapshots, precision):
     """After an eager call the whole step (validation, octrees, pair lists,
     work items, the integral launch, the sums) is captured once; calls on the
     same buffers replay it, computing from the buffers' current values: new
@@ -123,7 +124,7 @@ def test_batch_whole_step_graph(snapshots):
     bit; lists that outgrow their buffers (h raised) fall back to the eager
     step and capture anew; an invalid particle is refused."""
     L = lib()
-    ctx = L.map_init(L.map_config_default(precision=1))
+    ctx = L.map_init(L.map_config_default(precision=precision))
     try:
         handles, parts, keep, mass = [], [], [], []
         for _, p, g, h in snapshots:
@@ -148,7 +149,7 @@ def test_batch_whole_step_graph(snapshots):
         for a, b in zip(first, again):
             assert np.array_equal(a, b)
         assert np.array_equal(t1, t2)
-        assert L.map_get_stats(ctx).n_pairs == sum(gpu_map(g, p, h, 1)["n_pairs"] for _, p, g, h in snapshots)
+        assert L.map_get_stats(ctx).n_pairs == sum(gpu_map(g, p, h, precision)["n_pairs"] for _, p, g, h in snapshots)
 
         # new positions in the same buffers: moved by up to 1e-3, kept in the cube
         rng = np.random.default_rng(5)
@@ -161,7 +162,7 @@ def test_batch_whole_step_graph(snapshots):
         got, _ = call()
         assert L.map_batch_graph_stats(ctx) == (1, 2, 0)
         for j, (_, p, g, h) in enumerate(snapshots):
-            assert np.array_equal(got[j], gpu_map(g, moved[j], h, 1)["mass"]), j
+            assert np.array_equal(got[j], gpu_map(g, moved[j], h, precision)["mass"]), j
 
         # h raised 1.6x: about 4x the pairs, beyond the captured buffers
         for t in keep:
@@ -169,7 +170,7 @@ def test_batch_whole_step_graph(snapshots):
         grown, _ = call()
         assert L.map_batch_graph_stats(ctx) == (2, 2, 1)
         for j, (_, p, g, h) in enumerate(snapshots):
-            assert np.array_equal(grown[j], gpu_map(g, moved[j], 1.6 * h, 1)["mass"]), j
+            assert np.array_equal(grown[j], gpu_map(g, moved[j], 1.6 * h, precision)["mass"]), j
 
         # an invalid particle: refused by the replay, the graph kept
         keep[0][4][0] = float("nan")
