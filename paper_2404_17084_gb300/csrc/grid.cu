@@ -222,8 +222,8 @@ int grid_prepare(map_ctx* ctx, const map_grid* in, PreparedGrid* g, cudaStream_t
   MAP_TRY(ctx_alloc_grid(ctx, g, (void**)&g->face64, nf * sizeof(double4_32a)));
   // FP32 faces for the pair rule's screen; then the records a context's
   // integral kernel reads: face spheres and FP32 edges for the mixed build
-  // (its rare FP64 faces rebuild their edge records from the vertices), FP64
-  // edges for the FP64 build
+  // (a face whose plane passes within 1e-4 h of a particle takes its side
+  // from face64), FP64 edges for the FP64 build
   MAP_TRY(ctx_alloc_grid(ctx, g, (void**)&g->face32, nf * sizeof(float4)));
   if (ctx->cfg.precision != MAP_FP64) {
     MAP_TRY(ctx_alloc_grid(ctx, g, (void**)&g->fsph32, nf * sizeof(float4)));
@@ -280,7 +280,8 @@ int grid_prepare(map_ctx* ctx, const map_grid* in, PreparedGrid* g, cudaStream_t
   std::memcpy(hi, hs, sizeof(hi));
   g->max_faces = hi[0];
   g->max_loops = hi[1];
-  // the mixed integral kernel packs a cell-relative loop index in 26 bits
+  // the mixed integral kernel keeps a cell-relative edge-record offset in 32
+  // bits (loop index x EDGE_STRIDE); 2^26 loop entries per cell bounds it
   if (g->max_loops >= (1 << 26)) return MAP_EINVAL;
   unsigned long long st;
   std::memcpy(&st, &hi[4], sizeof(st));
