@@ -23,9 +23,13 @@
 // bisection rules are those of the per-particle definition; only the order
 // of the sums differs.
 //
-// Mixed build: Newton and bisection sums and the Newton step in FP32 (on
-// hi/lo-split coordinates), stop at |dh| < 1e-6 h.  FP64 build: every sum in FP64 behind
-// an FP32 distance screen with a 1e-5 relative margin, stop at 1e-10.
+// Mixed build: Newton and bisection sums in FP32 (on hi/lo-split
+// coordinates); the Newton iterate, its step and the list-coverage tests in
+// FP32 too (hfact as an FP32 hi/lo pair), the converged step applied in FP64;
+// stop at |dh| < 1e-6 h.  FP64 build: every sum in FP64 behind an FP32
+// distance screen with a 1e-5 relative margin, stop at 1e-10.
+#include <type_traits>
+
 #include "internal.cuh"
 
 namespace {
@@ -55,16 +59,18 @@ struct HsWarp {
   int32_t stk[HS_STK];
 };
 
-// Candidate list held by one warp (values uniform across its lanes).
+// Candidate list held by one warp (values uniform across its lanes); S is
+// the build's type for h (FP32 in the mixed build, FP64 in the FP64 build).
+template <typename S>
 struct HsBuf {
   float q[6];       // query box: the leaf's outward-rounded FP32 box
-  double R;         // gather radius
+  S R;              // gather radius
   int nr;           // ranges held
   bool rng_done;    // the walk finished: the ranges cover every candidate
   int64_t total;    // positions in the ranges held
   bool expanded;    // cand holds all of them
   int64_t pk;       // the particle whose own list pcand holds (-1: none)
-  double pR;        // its radius
+  S pR;             // its radius
   int pn;           // its length
 };
 
@@ -108,9 +114,13 @@ struct HsWalk {
   unsigned m;     // pending range children (leaves, or nodes taken whole)
 };
 
-__device__ __forceinline__ void walk_begin(const HsTree& T, HsWarp& W, HsWalk& it, double R, int& nr) {
+__device__ __forceinline__ float walk_margin(double R) { return (float)(R + 1e-6) * 1.000001f; }
+__device__ __forceinline__ float walk_margin(float R) { return (R + 1e-6f) * 1.000001f; }
+
+template <typename S>
+__device__ __forceinline__ void walk_begin(const HsTree& T, HsWarp& W, HsWalk& it, S R, int& nr) {
   __syncwarp();
-  it.Rm = (float)(R + 1e-6) * 1.000001f;
+  it.Rm = walk_margin(R);
   it.Rin = (float)R;
   it.m = 0u;
   it.c0 = 0;
@@ -188,8 +198,8 @@ __device__ int walk_next(const HsTree& T, HsWarp& W, HsWalk& it, const float* q,
 // either term is added (the order of the additions is unchanged).  With keep
 // set, the candidates with q^2 < keep_q2 are also appended, in list order, to
 // keep[*nkeep ...] (*nkeep = -1 when they do not fit in HS_PCAP).
-template <bool F32>
-__device__ __forceinline__ void warp_accum(const HsTree& T, const int32_t* list, int cnt, int64_t k, double h,
+template <bool F32, typename S>
+__device__ __forceinline__ void warp_accum(const HsTree& T, const int32_t* list, int cnt, int64_t k, S h,
                                            float& s32, float& d32, double& s64, double& d64, int32_t* keep,
                                            float keep_q2, int* nkeep) {
   const int lane = threadIdx.x & 31;
@@ -200,8 +210,8 @@ __device__ __forceinline__ void warp_accum(const HsTree& T, const int32_t* list,
   double x = 0.0, y = 0.0, z = 0.0, R2 = 0.0, inv_h = 0.0;
   if (!F32) {
     x = T.xs[k]; y = T.ys[k]; z = T.zs[k];
-    R2 = 4.0 * h * h;
-    inv_h = 1.0 / h;
+    R2 = 4.0 * (double)h * (double)h;
+    inv_h = 1.0 / (double)h;
   }
   // q^2 of one candidate (FP32, as the screen), its terms added when inside
   auto term = [&](int64_t c, float2 a, float2 b, float2 cc) -> float {
@@ -260,6 +270,9 @@ __device__ __forceinline__ void warp_accum(const HsTree& T, const int32_t* list,
   }
 }
 
+__device__ __forceinline__ float rcbrt_s(float v) { return rcbrtf(v); }
+__device__ __forceinline__ double rcbrt_s(double v) { return rcbrt(v); }
+
 template <typename V>
 __device__ __forceinline__ V warp_total(V v) {
   for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(FULL, v, o);
@@ -286,7 +299,8 @@ __device__ int expand(HsWarp& W, int nr, int& r, int& off) {
 }
 
 // Gathers the candidate ranges for radius R, and their positions when they fit.
-__device__ __forceinline__ void regather(const HsTree& T, HsWarp& W, HsBuf& B, double R) {
+template <typename S>
+__device__ __forceinline__ void regather(const HsTree& T, HsWarp& W, HsBuf<S>& B, S R) {
   const int lane = threadIdx.x & 31;
   HsWalk it;
   B.R = R;
@@ -305,19 +319,21 @@ __device__ __forceinline__ void regather(const HsTree& T, HsWarp& W, HsBuf& B, d
   }
 }
 
-// n(h) and dn/dh for the particle at sorted position k (warp-uniform result).
-template <bool F32>
-__device__ void warp_density(const HsTree& T, HsWarp& W, HsBuf& B, int64_t k, double h, double& n, double& dn) {
+// n(h) and dn/dh for the particle at sorted position k (warp-uniform result),
+// in the build's type S for h (every test on h and the radii in S).
+template <bool F32, typename S>
+__device__ void warp_density(const HsTree& T, HsWarp& W, HsBuf<S>& B, int64_t k, S h, S& n, S& dn) {
   float s32 = 0.f, d32 = 0.f;
   double s64 = 0.0, d64 = 0.0;
   int none = 0;
-  if (B.pk == k && 2.0 * h <= 0.999 * B.pR && B.pR <= 8.0 * h) {
+  const bool own = B.pk == k && S(2) * h <= S(0.999) * B.pR && B.pR <= S(8) * h;
+  if (own) {
     // the particle's own list covers its support at this h
     warp_accum<F32>(T, W.pcand, B.pn, k, h, s32, d32, s64, d64, nullptr, 0.f, &none);
   } else {
-    if (2.0 * h > B.R || B.R > 8.0 * h) regather(T, W, B, 2.5 * h);
+    if (S(2) * h > B.R || B.R > S(8) * h) regather(T, W, B, S(2.5) * h);
   }
-  if (B.pk == k && 2.0 * h <= 0.999 * B.pR && B.pR <= 8.0 * h) {
+  if (own) {
     // done above
   } else if (B.expanded) {
     // the leaf's list; the first pass for a particle also keeps its own
@@ -325,13 +341,13 @@ __device__ void warp_density(const HsTree& T, HsWarp& W, HsBuf& B, int64_t k, do
     // leaf's list holds every candidate within R of the leaf's box, so of
     // the particle)
     if (B.pk != k) {
-      const double pR = fmin(2.5 * h, B.R);
+      const S pR = S(2.5) * h < B.R ? S(2.5) * h : B.R;
       const float kq = (float)(pR / h);
       int nk = 0;
       warp_accum<F32>(T, W.cand, (int)B.total, k, h, s32, d32, s64, d64, W.pcand, kq * kq * 1.00001f, &nk);
       __syncwarp();
       B.pk = k;
-      B.pR = nk >= 0 ? pR : 0.0;  // 0: nothing kept (it did not fit)
+      B.pR = nk >= 0 ? pR : S(0);  // 0: nothing kept (it did not fit)
       B.pn = nk >= 0 ? nk : 0;
     } else {
       warp_accum<F32>(T, W.cand, (int)B.total, k, h, s32, d32, s64, d64, nullptr, 0.f, &none);
@@ -359,13 +375,13 @@ __device__ void warp_density(const HsTree& T, HsWarp& W, HsBuf& B, int64_t k, do
       nr = 0;
     }
     B.nr = 0;
-    B.R = -1.0;  // the buffer no longer holds the first ranges: regather next time
+    B.R = S(-1);  // the buffer no longer holds the first ranges: regather next time
   }
   if (F32) {
     const float ih = 1.0f / (float)h;
     const float norm = ih * ih * ih * (float)(1.0 / MAP_PI);
-    n = (double)(warp_total(s32) * norm);
-    dn = (double)(-warp_total(d32) * norm * ih);
+    n = (S)(warp_total(s32) * norm);
+    dn = (S)(-warp_total(d32) * norm * ih);
   } else {
     const double ih = 1.0 / h;
     const double norm = ih * ih * ih * (1.0 / MAP_PI);
@@ -378,6 +394,11 @@ template <bool MIXED>
 __global__ void __launch_bounds__(HS_WARPS * 32)
     h_solve_leaves(int64_t n, HsTree T, const double* __restrict__ h0s, double hfact, double tol, double* hout,
                    int32_t* route) {
+  // the build's type for h: the mixed build iterates in FP32 (its sums are
+  // FP32, and GB300's FP64 rate is 1/64 of its FP32 rate)
+  using S = typename std::conditional<MIXED, float, double>::type;
+  const S hf_s = (S)hfact, hf3_s = (S)(hfact / 3.0), tol_s = (S)tol;
+  const S hf_lo = (S)(hfact - (double)hf_s);
   __shared__ HsWarp sw[HS_WARPS];
   HsWarp& W = sw[threadIdx.x >> 5];
   const int lane = threadIdx.x & 31;
@@ -399,56 +420,58 @@ __global__ void __launch_bounds__(HS_WARPS * 32)
     double gmax = 0.0;
     for (int64_t k = a0 + lane; k < a1; k += 32) gmax = fmax(gmax, h0s[k]);
     for (int o = 16; o > 0; o >>= 1) gmax = fmax(gmax, __shfl_xor_sync(FULL, gmax, o));
-    HsBuf B;
+    HsBuf<S> B;
 #pragma unroll
     for (int i = 0; i < 6; ++i) B.q[i] = T.box32[8 * (int64_t)L + i];
-    B.R = -1.0;
+    B.R = S(-1);
     B.nr = 0;
     B.total = 0;
     B.rng_done = false;
     B.expanded = false;
     B.pk = -1;
-    B.pR = 0.0;
+    B.pR = S(0);
     B.pn = 0;
-    const double R0 = 2.5 * gmax;
+    const S R0 = S(2.5) * (S)gmax;
     for (int64_t k = a0; k < a1; ++k) {
       // the leaf's list for its first particle; later particles keep the
       // list they find while it covers their support (warp_density
       // regathers when 2h > R or R > 8h)
       if (k == a0) regather(T, W, B, R0);
-      const double g0 = h0s[k];
-      const double lo = g0 / 16.0, hi = g0 * 16.0;
-      double h = g0;
+      // Newton in S: g = h - hfact t, g' = 1 + hfact/3 t^4 dn/dh with t = n^(-1/3)
+      S hs = (S)h0s[k];
+      const S lo_s = hs / S(16), hi_s = hs * S(16);
+      double h = 0.0;
       bool ok = false;
       for (int it = 0; it < 30; ++it) {
-        double nn, dn;
-        warp_density<MIXED>(T, W, B, k, h, nn, dn);
-        // g = h - hfact t, g' = 1 + hfact/3 t^4 dn/dh with t = n^(-1/3)
-        double hn;
-        if (MIXED) {
-          const float t = rcbrtf((float)nn);
-          const double f = h - hfact * (double)t;
-          const float fp = 1.0f + (float)(hfact / 3.0) * (t * t) * (t * t) * (float)dn;
-          hn = h - (double)((float)f / fp);
-        } else {
-          const double t = rcbrt(nn);
-          const double f = h - hfact * t;
-          const double fp = 1.0 + hfact / 3.0 * (t * t) * (t * t) * dn;
-          hn = h - f / fp;
+        S nn, dn;
+        warp_density<MIXED>(T, W, B, k, hs, nn, dn);
+        const S t = rcbrt_s(nn);
+        S f = hs - hf_s * t;
+        if (MIXED) f -= hf_lo * t;  // hfact as an FP32 pair
+        const S fp = S(1) + hf3_s * (t * t) * (t * t) * dn;
+        const S d = f / fp;
+        const S hn = hs - d;
+        if (!(hn >= lo_s && hn <= hi_s)) break;
+        if ((hn > hs ? hn - hs : hs - hn) < tol_s * hn) {
+          // the mixed build applies its converged step in FP64 (the result
+          // keeps FP64's spacing, not FP32's)
+          h = MIXED ? (double)hs - (double)d : (double)hn;
+          ok = true;
+          break;
         }
-        if (!(hn >= lo && hn <= hi)) break;
-        if (fabs(hn - h) < tol * hn) { h = hn; ok = true; break; }
-        h = hn;
+        hs = hn;
       }
       int r = 0;
       if (!ok) {
+        const double g0 = h0s[k];
+        const double lo = g0 / 16.0, hi = g0 * 16.0;
         // (the mixed build bisects on its FP32 sums too: the root moves by
         // ~1e-7 relative, inside the build's 1e-6, and GB300's FP64 rate
         // is 1/64 of its FP32 rate)
         auto g = [&](double hh) {
-          double nn, dn;
-          warp_density<MIXED>(T, W, B, k, hh, nn, dn);
-          return hh - hfact * rcbrt(nn);
+          S nn, dn;
+          warp_density<MIXED>(T, W, B, k, (S)hh, nn, dn);
+          return hh - hfact * rcbrt((double)nn);
         };
         // Bisection on [lo, hi] needs g(lo) < 0 < g(hi).  g(h)/h is
         // nondecreasing in h (w is nonincreasing in q, so sum_b w(r_ab/h)
