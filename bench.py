@@ -250,11 +250,14 @@ def merge_errors(errs):
                     "largest per-snapshot p99"}
 
 
-def autotune_table(L, chosen, ms):
-    """The autotuner's two-dimensional table: ms[target][shape]."""
-    ns = len(L.AUTOTUNE_SHAPES)
-    return {"chosen": {"item_target": L.AUTOTUNE_ITEM_TARGETS[chosen // ns], "shape": L.AUTOTUNE_SHAPES[chosen % ns]},
-            "shapes": L.AUTOTUNE_SHAPES, "item_targets_per_warp": L.AUTOTUNE_ITEM_TARGETS,
+def autotune_table(L, chosen, ms, shapes):
+    """The autotuner's two-dimensional table: ms[target][shape]; the shapes
+    as launched (warps per CTA, CTAs per SM, registers), read from the
+    library."""
+    ns = len(shapes)
+    label = [f"{s['warps_per_cta']} warps/CTA, {s['ctas_per_sm']} CTAs/SM, {s['registers']} registers" for s in shapes]
+    return {"chosen": {"item_target": L.AUTOTUNE_ITEM_TARGETS[chosen // ns], "shape": label[chosen % ns]},
+            "shapes": label, "item_targets_per_warp": L.AUTOTUNE_ITEM_TARGETS,
             "ms": [[round(ms[t * ns + v], 3) for v in range(ns)] for t in range(len(L.AUTOTUNE_ITEM_TARGETS))]}
 
 
@@ -325,6 +328,7 @@ def run_ours(args):
     sampler = ClockSampler(local)
     ms, st, work, launches, integ_ms, phases, clocks = timed(ctx, handle, args.steps, args.warmup, sampler)
     tune_chosen, tune_ms = L.map_get_autotune(ctx)
+    tune_shapes = L.map_autotune_shapes(ctx)
     n_pairs = st.n_pairs
     mass_mixed = mass.cpu().numpy()
     h_mixed = h.cpu().numpy()
@@ -436,7 +440,7 @@ def run_ours(args):
         "serving": serving,
         "gpu_launches": int(launches),
         "clocks": clocks,
-        "autotune": autotune_table(L, tune_chosen, tune_ms),
+        "autotune": autotune_table(L, tune_chosen, tune_ms, tune_shapes),
         "stats": {"edge_terms": int(terms), "total_mass": st.total_mass, **{k: int(v) for k, v in work.items()},
                   "counted_by": "one untimed call of a count_work context on the same particles and h"},
         "inverse_mapping": inverse,
@@ -531,6 +535,7 @@ def run_batch(args):
     st = L.map_get_stats(ctx)
     work, l1 = L.map_get_work(ctx)
     chosen, tune_ms = L.map_get_autotune(ctx)
+    tune_shapes = L.map_autotune_shapes(ctx)
     g1 = L.map_batch_graph_stats(ctx)
     h1 = L.solve_h_batch_graph_stats(ctx)
     phases = L.map_get_timing(ctx)
@@ -587,7 +592,7 @@ def run_batch(args):
                    "step": "per snapshot solve_h, then one map_batch (octree + pair list per snapshot, one "
                            "persistent integral launch over all snapshots)"},
         "batch": {"integrals_ms": integ_ms, "integral_launch_pairs_per_s": st.n_pairs / (integ_ms * 1e-3),
-                  "autotune": autotune_table(L, chosen, tune_ms),
+                  "autotune": autotune_table(L, chosen, tune_ms, tune_shapes),
                   "one_call_per_snapshot_mapping_s": single_s, "batched_equals_single": bool(same),
                   "graph": graph,
                   "host_input_generation_s": gen_s},

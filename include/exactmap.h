@@ -330,11 +330,20 @@ int map_batch(map_ctx* ctx, int nsnap, const map_particles* parts, const int* gr
 /* The autotuner's state.  Trials are pairs of a work-item target T (items
  * per resident warp of the integral launch: 16, 64, 256; a cell's pairs form
  * items of at most K blocks of 32, K = (pair blocks) / (T x warps)) and a
- * launch shape (warps per CTA, CTAs per SM: (4,5), (4,4), (4,6), (2,10),
- * (8,2)); trial t * 5 + v is target t with shape v.  *chosen = the trial in
- * use for the mixed build, ms[0..*nvariants) = each trial's time on the
- * tuning call's inputs (0 when not run).  ms must hold at least 32 floats. */
+ * launch shape of the mixed kernel (warps per CTA, CTAs per SM: (4,5),
+ * (4,4), (2,9), (8,2); see map_autotune_shapes); trial t * 4 + v is target t
+ * with shape v.  *chosen = the trial in use for the mixed build,
+ * ms[0..*nvariants) = each trial's time on the tuning call's inputs (0 when
+ * not run).  ms must hold at least 32 floats. */
 int map_get_autotune(map_ctx* ctx, int* chosen, float* ms, int* nvariants);
+
+/* The autotuner's launch shapes as launched on the context's device: per
+ * shape v < *nshapes, warps_per_cta[v], ctas_per_sm[v] (the CTAs per SM the
+ * persistent launch uses: the shape's own count, lowered to what the device
+ * keeps resident at once) and registers[v] per thread (registers may be
+ * NULL).  The arrays must hold at least 8 ints.  Errors: MAP_EINVAL (NULL
+ * ctx or array), MAP_ECUDA. */
+int map_autotune_shapes(map_ctx* ctx, int* warps_per_cta, int* ctas_per_sm, int* registers, int* nshapes);
 
 /* How map_batch's whole-step graph has been used by this context: captures,
  * replays, and replays that fell back to the eager step (lists outgrew their

@@ -140,6 +140,8 @@ _lib.map_batch.argtypes = [_P, ctypes.c_int, ctypes.POINTER(map_particles), ctyp
                            ctypes.POINTER(map_outputs), _P, _P]
 _lib.map_get_autotune.argtypes = [_P, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_float),
                                   ctypes.POINTER(ctypes.c_int)]
+_lib.map_autotune_shapes.argtypes = [_P, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
+                                     ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)]
 _lib.map_batch_graph_stats.argtypes = [_P, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64),
                                        ctypes.POINTER(ctypes.c_int64)]
 _lib.solve_h_batch_graph_stats.argtypes = [_P, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64)]
@@ -147,7 +149,8 @@ for _name in ("map_init", "map_grid_upload", "map_grid_release", "map_grid_volum
               "map_grid_sizes", "map_grid_copy", "map_particles_to_cells",
               "map_get_pairs", "map_copy_pairs", "map_cells_to_particles", "map_get_stats", "map_get_work",
               "map_get_timing", "solve_h", "build_pseudo_particles", "build_pseudo_particles_walk", "map_batch",
-              "map_get_autotune", "solve_h_batch", "map_batch_graph_stats", "solve_h_batch_graph_stats"):
+              "map_get_autotune", "map_autotune_shapes", "solve_h_batch", "map_batch_graph_stats",
+              "solve_h_batch_graph_stats"):
     getattr(_lib, _name).restype = ctypes.c_int
 
 
@@ -252,9 +255,18 @@ def map_batch(ctx, parts, handles, cell_mass, cell_rho=None, cell_vol=None, tota
     _check(_lib.map_batch(ctx, n, P, H, O, _ptr(totals), _stream(stream)), "map_batch")
 
 
-AUTOTUNE_SHAPES = ["4 warps/CTA, 5 CTAs/SM", "4 warps/CTA, 4 CTAs/SM", "4 warps/CTA, 6 CTAs/SM",
-                   "2 warps/CTA, 10 CTAs/SM", "8 warps/CTA, 2 CTAs/SM"]
+AUTOTUNE_SHAPES = ["4 warps/CTA, 5 CTAs/SM", "4 warps/CTA, 4 CTAs/SM", "2 warps/CTA, 9 CTAs/SM",
+                   "8 warps/CTA, 2 CTAs/SM"]
 AUTOTUNE_ITEM_TARGETS = [16, 64, 256]
+
+
+def map_autotune_shapes(ctx):
+    """The autotuner's launch shapes as launched on the context's device:
+    one dict per shape (warps_per_cta, ctas_per_sm, registers)."""
+    w, c, r = (ctypes.c_int * 8)(), (ctypes.c_int * 8)(), (ctypes.c_int * 8)()
+    n = ctypes.c_int()
+    _check(_lib.map_autotune_shapes(ctx, w, c, r, ctypes.byref(n)), "map_autotune_shapes")
+    return [{"warps_per_cta": w[i], "ctas_per_sm": c[i], "registers": r[i]} for i in range(n.value)]
 
 
 def map_get_autotune(ctx):

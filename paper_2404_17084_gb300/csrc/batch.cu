@@ -870,4 +870,15 @@ int map_get_autotune(map_ctx* ctx, int* chosen, float* ms, int* nvariants) {
   return MAP_OK;
 }
 
+int map_autotune_shapes(map_ctx* ctx, int* warps_per_cta, int* ctas_per_sm, int* registers, int* nshapes) {
+  if (!ctx || !warps_per_cta || !ctas_per_sm) return MAP_EINVAL;
+  for (int v = 0; v < N_SHAPES; ++v) {
+    int r = 0;
+    MAP_TRY(integrals_shape(ctx, v, &warps_per_cta[v], &ctas_per_sm[v], &r));
+    if (registers) registers[v] = r;
+  }
+  if (nshapes) *nshapes = N_SHAPES;
+  return MAP_OK;
+}
+
 }  // extern "C"

@@ -689,12 +689,27 @@ __global__ void __launch_bounds__(NW * 32, MINB) pair_integrals_mixed(BatchArgs 
   }
 }
 
+// CTAs per SM of a launch of shape (NW, MINB): as many as are resident at
+// once, at most MINB (a persistent launch beyond residency would only queue).
+template <int NW, int MINB, bool COUNT = false>
+int mixed_per_sm(int* per_sm, int* regs) {
+  auto kern = pair_integrals_mixed<NW, MINB, COUNT>;
+  CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, kern, NW * 32, 0));
+  if (*per_sm > MINB) *per_sm = MINB;
+  if (*per_sm < 1) *per_sm = 1;
+  if (regs) {
+    cudaFuncAttributes a;
+    CUDA_TRY(cudaFuncGetAttributes(&a, kern));
+    *regs = a.numRegs;
+  }
+  return MAP_OK;
+}
+
 template <int NW, int MINB, bool COUNT = false>
 int launch_mixed(map_ctx* ctx, const BatchArgs& B, cudaStream_t s) {
   auto kern = pair_integrals_mixed<NW, MINB, COUNT>;
   int per_sm = 0;
-  CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, NW * 32, 0));
-  if (per_sm < 1) per_sm = 1;
+  MAP_TRY((mixed_per_sm<NW, MINB, COUNT>(&per_sm, nullptr)));
   int64_t blocks = (int64_t)per_sm * ctx->sm_count;
   const int64_t need = (B.total + NW - 1) / NW;
   if (blocks > need) blocks = need > 0 ? need : 1;
@@ -803,9 +818,8 @@ int integrals_enqueue(map_ctx* ctx, const BatchArgs& B, int variant, cudaStream_
   } else if (ctx->cfg.precision == MAP_MIXED) {
     switch (variant) {
       case 1: MAP_TRY((launch_mixed<4, 4>(ctx, B, s))); break;
-      case 2: MAP_TRY((launch_mixed<4, 6>(ctx, B, s))); break;
-      case 3: MAP_TRY((launch_mixed<2, 10>(ctx, B, s))); break;
-      case 4: MAP_TRY((launch_mixed<8, 2>(ctx, B, s))); break;
+      case 2: MAP_TRY((launch_mixed<2, 9>(ctx, B, s))); break;
+      case 3: MAP_TRY((launch_mixed<8, 2>(ctx, B, s))); break;
       default: MAP_TRY((launch_mixed<4, 5>(ctx, B, s))); break;
     }
   } else if (count) {
@@ -819,6 +833,17 @@ int integrals_enqueue(map_ctx* ctx, const BatchArgs& B, int variant, cudaStream_
     CUDA_TRY(cudaGetLastError());
   }
   return MAP_OK;
+}
+
+int integrals_shape(map_ctx* ctx, int v, int* warps, int* ctas, int* regs) {
+  CUDA_TRY(cudaSetDevice(ctx->device));
+  switch (v) {
+    case 0: *warps = 4; return mixed_per_sm<4, 5>(ctas, regs);
+    case 1: *warps = 4; return mixed_per_sm<4, 4>(ctas, regs);
+    case 2: *warps = 2; return mixed_per_sm<2, 9>(ctas, regs);
+    case 3: *warps = 8; return mixed_per_sm<8, 2>(ctas, regs);
+    default: return MAP_EINVAL;
+  }
 }
 
 int integrals_sum(map_ctx* ctx, const SnapDesc* d_desc, int nsnap, double* totals, cudaStream_t s) {

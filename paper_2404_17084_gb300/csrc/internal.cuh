@@ -314,9 +314,12 @@ __device__ __forceinline__ int64_t queue_total(const BatchArgs& B) {
 }
 
 // Launch shapes of the mixed pair-integral kernel: (warps per CTA, CTAs per
-// SM) = (4, 5), (4, 4), (4, 6), (2, 10), (8, 2); the register cap per thread
-// follows from them.  Work-item targets: items per resident warp of a launch.
-constexpr int N_SHAPES = 5;
+// SM) = (4, 5), (4, 4), (2, 9), (8, 2).  Each is compiled for its CTAs per SM
+// (the register cap per thread follows) and launched with at most that many
+// per SM; all four fit an SM's registers and shared memory at once, so the
+// launched shape is the resident one (integrals_shape reports it).
+// Work-item targets: items per resident warp of a launch.
+constexpr int N_SHAPES = 4;
 constexpr int N_TARGETS = 3;
 constexpr int ITEM_TARGETS[N_TARGETS] = {16, 64, 256};
 
@@ -373,6 +376,9 @@ SnapDesc make_desc(map_ctx* ctx, const PreparedGrid* g, const map_particles* p, 
 int integrals_upload(map_ctx* ctx, const SnapDesc* h_desc, const int64_t* h_ibase, const int64_t* h_cbase,
                      int nsnap, SnapDesc* d_desc, int64_t* d_ibase, int64_t* d_cbase, cudaStream_t s);
 int integrals_enqueue(map_ctx* ctx, const BatchArgs& B, int variant, cudaStream_t s);
+// Launch geometry of shape v of the mixed kernel on the context's device:
+// warps per CTA, CTAs per SM launched, registers per thread.
+int integrals_shape(map_ctx* ctx, int v, int* warps, int* ctas, int* regs);
 int integrals_sum(map_ctx* ctx, const SnapDesc* d_desc, int nsnap, double* totals, cudaStream_t s);
 // Times every (work-item target, launch shape) pair on the call's inputs and
 // keeps the fastest (ctx->tuned[MAP_MIXED], ctx->item_target).  rebuild(T, B)

@@ -65,13 +65,21 @@ def test_batch_equals_single(snapshots, precision):
 
 def test_batch_autotune_and_replay(snapshots):
     """The autotuner times every pair of a work-item size (3) and a launch
-    shape (5) and keeps one.  Replays of the captured graph give the same
+    shape (4) and keeps one; each shape launches as many CTAs per SM as it
+    names, all resident at once.  Replays of the captured graph give the same
     bits; another shape or item size (a separate compilation, other groups of
     a cell's pairs) agrees to FP32 rounding."""
     L = lib()
     ref, _, _ = run_batch(snapshots, 1)
     runs, _, (chosen, ms) = run_batch(snapshots, 1, autotune=1, repeat=3)
-    assert len(ms) == len(L.AUTOTUNE_SHAPES) * len(L.AUTOTUNE_ITEM_TARGETS) == 15
+    assert len(ms) == len(L.AUTOTUNE_SHAPES) * len(L.AUTOTUNE_ITEM_TARGETS) == 12
+    ctx = L.map_init(L.map_config_default())
+    try:
+        shapes = L.map_autotune_shapes(ctx)
+    finally:
+        L.map_destroy(ctx)
+    assert [(s["warps_per_cta"], s["ctas_per_sm"]) for s in shapes] == [(4, 5), (4, 4), (2, 9), (8, 2)]
+    assert all(0 < s["registers"] <= 65536 // (32 * s["warps_per_cta"] * s["ctas_per_sm"]) for s in shapes)
     assert 0 <= chosen < len(ms) and all(t > 0 for t in ms)
     for masses, totals in runs[1:]:
         for a, b in zip(masses, runs[0][0]):
