@@ -1277,7 +1277,9 @@ def e2e_run(L, torch, ctx, p, g, dev, args, barrier, world):
     particles by torch, the grid by map_grid_upload itself), the grid
     prepared, solve_h + mapping, cell masses read back.  The h solve needs
     only the particles, so it runs on a second context and stream while the
-    grid is copied in and prepared (calls of one context run in order)."""
+    grid is copied in and prepared (calls of one context run in order).  Both
+    streams are created ones: work on the legacy default stream would wait
+    for the side stream's h solve instead of running beside it."""
     pin = lambda a, dt: torch.as_tensor(np.ascontiguousarray(a), dtype=dt).pin_memory()
     hp = [pin(a, torch.float64) for a in (p.x, p.y, p.z, p.m)]
     hg = dict(cell_face_off=pin(g.cell_face_off, torch.int64), face_vert_off=pin(g.face_vert_off, torch.int64),
@@ -1289,20 +1291,22 @@ def e2e_run(L, torch, ctx, p, g, dev, args, barrier, world):
     d2h = out_host.numel() * out_host.element_size()
 
     ctx_h = L.map_init(L.map_config_default(precision=L.MAP_MIXED, device=dev.index or 0))
+    main = torch.cuda.Stream(device=dev)
     side = torch.cuda.Stream(device=dev)
 
     def one():
-        main = torch.cuda.current_stream(dev)
-        dp = [t.to(dev, non_blocking=True) for t in hp]
-        hh = torch.empty_like(dp[0])
-        side.wait_stream(main)
-        with torch.cuda.stream(side):
-            L.solve_h(ctx_h, L.make_particles(dp[0], dp[1], dp[2], None, hh), stream=side)
-        handle = L.map_grid_upload(ctx, hg)
-        main.wait_stream(side)
-        mass = torch.empty(g.ncell, dtype=torch.float64, device=dev)
-        L.map_particles_to_cells(ctx, L.make_particles(dp[0], dp[1], dp[2], dp[3], hh), handle, mass)
-        out_host.copy_(mass, non_blocking=True)
+        with torch.cuda.stream(main):
+            dp = [t.to(dev, non_blocking=True) for t in hp]
+            hh = torch.empty_like(dp[0])
+            side.wait_stream(main)
+            with torch.cuda.stream(side):
+                L.solve_h(ctx_h, L.make_particles(dp[0], dp[1], dp[2], None, hh), stream=side)
+            handle = L.map_grid_upload(ctx, hg, stream=main)
+            main.wait_stream(side)
+            mass = torch.empty(g.ncell, dtype=torch.float64, device=dev)
+            L.map_particles_to_cells(ctx, L.make_particles(dp[0], dp[1], dp[2], dp[3], hh), handle, mass,
+                                     stream=main)
+            out_host.copy_(mass, non_blocking=True)
         torch.cuda.synchronize()
         L.map_grid_release(ctx, handle)
         return L.map_get_stats(ctx).n_pairs

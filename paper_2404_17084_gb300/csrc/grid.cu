@@ -18,13 +18,24 @@ __global__ void face_cells(int64_t ncell, const int64_t* __restrict__ cfo, int32
   for (int64_t f = cfo[c]; f < cfo[c + 1]; ++f) fcell[f] = (int32_t)c;
 }
 
+// FP32 copies of the vertex coordinates, for the face spheres' centres.
+__global__ void vert32(int64_t nv, const double* __restrict__ vx, const double* __restrict__ vy,
+                       const double* __restrict__ vz, float4* v32) {
+  const int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (k < nv) v32[k] = make_float4((float)vx[k], (float)vy[k], (float)vz[k], 0.f);
+}
+
 // One thread per face: site-relative planes, the face's bounding sphere and
 // edge records, its term dr * area / 3 of the cell volume (divergence
-// theorem) and the largest squared vertex distance from the site.
+// theorem) and the largest squared vertex distance from the site.  The
+// FP64 pipe runs at 1/64 of the FP32 rate, so FP64 work is kept to the
+// site-relative differences, one component of the area sum and the exact
+// squares of the few vertices that can be the farthest.
 __global__ void prep_faces(int64_t nface, const int32_t* __restrict__ fcell, const int64_t* __restrict__ fvo,
                            const int32_t* __restrict__ fv, const double4_32a* __restrict__ plane,
                            const double* __restrict__ vx, const double* __restrict__ vy,
-                           const double* __restrict__ vz, const double* __restrict__ site, double4_32a* face64,
+                           const double* __restrict__ vz, const float4* __restrict__ v32,
+                           const double* __restrict__ site, double4_32a* face64,
                            float4* face32, float4* fsph32, double* edge64, float* edge32, double* volf, double* r2f,
                            unsigned long long* status) {
   const int64_t f = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
@@ -41,35 +52,55 @@ __global__ void prep_faces(int64_t nface, const int32_t* __restrict__ fcell, con
   // site-relative vertices: differences in FP64, FP32 copies for the mixed
   // build's records (their rounding, ~1e-7 of the cell size, is that of
   // rounding an FP64 record)
-  float mx = 0.f, my = 0.f, mz = 0.f;  // FP32 vertex mean (face sphere centre)
+  // face sphere centre: the vertex mean from the FP32 copies (any centre
+  // serves: the radius below is measured from it to the accurate
+  // site-relative vertices)
+  float mx = 0.f, my = 0.f, mz = 0.f;
   if (fsph32) {
+    const float sx32 = (float)sx, sy32 = (float)sy, sz32 = (float)sz;
     for (int64_t k = 0; k < L; ++k) {
-      const int32_t ia = fv[b + k];
-      mx += (float)(vx[ia] - sx); my += (float)(vy[ia] - sy); mz += (float)(vz[ia] - sz);
+      const float4 V = v32[fv[b + k]];
+      mx += V.x - sx32; my += V.y - sy32; mz += V.z - sz32;
     }
     const float il = 1.0f / (float)L;
     mx *= il; my *= il; mz *= il;
   }
-  float sr2 = 0.f;  // FP32 squared sphere radius
+  // The loop's cross-product sum is 2 area n (a planar loop, unit n): its
+  // component on the normal's largest axis, over that normal component,
+  // gives the area.
+  const double anx = fabs(P.x), any = fabs(P.y), anz = fabs(P.z);
+  const int axis = anx >= any && anx >= anz ? 0 : (any >= anz ? 1 : 2);
+  const double n_axis = axis == 0 ? P.x : (axis == 1 ? P.y : P.z);
+  float sr2 = 0.f;   // FP32 squared sphere radius
+  float r2s = 0.f;   // largest FP32 squared vertex distance so far
   double R2 = 0.0;
-  double ax = 0, ay = 0, az = 0;
+  double acc = 0.0;
   const int32_t i0 = fv[b];
   const double X0 = vx[i0] - sx, Y0 = vy[i0] - sy, Z0 = vz[i0] - sz;
   double Ax = X0, Ay = Y0, Az = Z0;
+  float ax32 = (float)Ax, ay32 = (float)Ay, az32 = (float)Az;
+  const float x032 = ax32, y032 = ay32, z032 = az32;
   for (int64_t k = 0; k < L; ++k) {
     double Bx = X0, By = Y0, Bz = Z0;
+    float bx32 = x032, by32 = y032, bz32 = z032;
     if (k + 1 < L) {
       const int32_t ib = fv[b + k + 1];
       Bx = vx[ib] - sx; By = vy[ib] - sy; Bz = vz[ib] - sz;
+      bx32 = (float)Bx; by32 = (float)By; bz32 = (float)Bz;
     }
     // cell radius: fixed evaluation order, no FMA contraction; one
-    // correctly rounded square root of the cell's largest square at the end
-    const double r2 = __dadd_rn(__dadd_rn(__dmul_rn(Ax, Ax), __dmul_rn(Ay, Ay)), __dmul_rn(Az, Az));
-    R2 = r2 > R2 ? r2 : R2;
-    // area vector (site-relative loop)
-    ax += Ay * Bz - Az * By;
-    ay += Az * Bx - Ax * Bz;
-    az += Ax * By - Ay * Bx;
+    // correctly rounded square root of the cell's largest square at the end.
+    // Only a vertex whose FP32 square (within 5e-7 of its FP64 one) comes
+    // within 1e-5 of the largest so far can be the farthest; the others
+    // skip the FP64 square.
+    const float q = ax32 * ax32 + ay32 * ay32 + az32 * az32;
+    if (q >= r2s * (1.f - 1e-5f)) {
+      r2s = fmaxf(r2s, q);
+      const double r2 = __dadd_rn(__dadd_rn(__dmul_rn(Ax, Ax), __dmul_rn(Ay, Ay)), __dmul_rn(Az, Az));
+      R2 = r2 > R2 ? r2 : R2;
+    }
+    // area: one component of the site-relative loop's cross-product sum
+    acc += axis == 0 ? Ay * Bz - Az * By : (axis == 1 ? Az * Bx - Ax * Bz : Ax * By - Ay * Bx);
     // a zero-length edge gets R0s = m.y - delta*hinv = +huge: it never
     // makes p 'outside' and its r0^2 + R0^2 is beyond the support
     if (edge64) {
@@ -80,8 +111,6 @@ __global__ void prep_faces(int64_t nface, const int32_t* __restrict__ fcell, con
       for (int j = 9; j < EDGE_STRIDE; ++j) E[j] = 0;
     }
     if (edge32) {
-      const float ax32 = (float)Ax, ay32 = (float)Ay, az32 = (float)Az;
-      const float bx32 = (float)Bx, by32 = (float)By, bz32 = (float)Bz;
       float rec[12];
       float ex = bx32 - ax32, ey = by32 - ay32, ez = bz32 - az32;
       const float len = sqrtf(ex * ex + ey * ey + ez * ez);
@@ -111,11 +140,12 @@ __global__ void prep_faces(int64_t nface, const int32_t* __restrict__ fcell, con
       }
     }
     Ax = Bx; Ay = By; Az = Bz;
+    ax32 = bx32; ay32 = by32; az32 = bz32;
   }
   // bounding sphere: centre at the vertex mean, radius the largest vertex
   // distance, rounded up (FP32 rounding is far inside the margin)
   if (fsph32) fsph32[f] = make_float4(mx, my, mz, sqrtf(sr2) * (1.0f + 1e-5f) + 1e-12f);
-  const double area = 0.5 * (ax * P.x + ay * P.y + az * P.z);
+  const double area = 0.5 * acc / n_axis;
   volf[f] = dr * area / 3.0;
   r2f[f] = R2;
 }
@@ -264,11 +294,17 @@ int grid_prepare(map_ctx* ctx, const map_grid* in, PreparedGrid* g, cudaStream_t
   MAP_TRY(ensure_t(ctx, ctx->ws_grid[0], nf, &fcell));
   MAP_TRY(ensure_t(ctx, ctx->ws_grid[1], nf, &volf));
   MAP_TRY(ensure_t(ctx, ctx->ws_grid[2], nf, &r2f));
+  float4* v32 = nullptr;
+  if (g->fsph32) {
+    MAP_TRY(ensure_t(ctx, ctx->ws_grid[3], nv, &v32));
+    vert32<<<nblk(nv, tpb), tpb, 0, s>>>(nv, g->vx, g->vy, g->vz, v32); ++ctx->launches;
+    CUDA_TRY(cudaGetLastError());
+  }
   face_cells<<<(unsigned)blocks, tpb, 0, s>>>(nc, g->cell_face_off, fcell); ++ctx->launches;
   CUDA_TRY(cudaGetLastError());
   prep_faces<<<nblk(nf, tpb), tpb, 0, s>>>(nf, fcell, g->face_vert_off, g->face_vert, g->face_plane, g->vx, g->vy,
-                                           g->vz, g->site, g->face64, g->face32, g->fsph32, g->edge64, g->edge32,
-                                           volf, r2f, d_status); ++ctx->launches;
+                                           g->vz, v32, g->site, g->face64, g->face32, g->fsph32, g->edge64,
+                                           g->edge32, volf, r2f, d_status); ++ctx->launches;
   CUDA_TRY(cudaGetLastError());
   prep_cells<<<(unsigned)blocks, tpb, 0, s>>>(nc, g->cell_face_off, g->face_vert_off, volf, r2f, g->vol, g->rad,
                                               d_small, d_small + 1); ++ctx->launches;

@@ -146,7 +146,8 @@ struct map_ctx {
   DevBuf ws_tree[32];
   DevBuf ws_pairs[15];
   DevBuf ws_misc[8];
-  DevBuf ws_grid[3];                   // grid preparation: face -> cell, per-face volume term and radius^2
+  DevBuf ws_grid[4];                   // grid preparation: face -> cell, per-face volume term and radius^2,
+                                       // FP32 vertex copies
   DevBuf ws_vor[22];                   // grid construction: buckets, cell slots, CSR arrays
   DevBuf ws_inv[13];                   // particle-major copy of the pair list (inverse mapping, Eq. 4)
   DevBuf cub_tmp;
