@@ -150,21 +150,25 @@ __global__ void prep_faces(int64_t nface, const int32_t* __restrict__ fcell, con
   r2f[f] = R2;
 }
 
-// One thread per cell: volume (the faces' terms in face order), radius R_i
-// and the largest face and loop counts.
+// One thread per cell: volume (the faces' terms in face order), radius R_i,
+// the inscribed radius (the smallest distance from the site to a face
+// plane, rounded down to FP32) and the largest face and loop counts.
 __global__ void prep_cells(int64_t ncell, const int64_t* __restrict__ cfo, const int64_t* __restrict__ fvo,
-                           const double* __restrict__ volf, const double* __restrict__ r2f, double* vol, double* rad,
-                           int* maxf, int* maxl) {
+                           const double* __restrict__ volf, const double* __restrict__ r2f,
+                           const double4_32a* __restrict__ face64, double* vol, double* rad, float* rin, int* maxf,
+                           int* maxl) {
   const int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (c >= ncell) return;
   const int64_t f0 = cfo[c], f1 = cfo[c + 1];
-  double V = 0.0, R2 = 0.0;
+  double V = 0.0, R2 = 0.0, dmin = 1e300;
   for (int64_t f = f0; f < f1; ++f) {
     V += volf[f];
     R2 = r2f[f] > R2 ? r2f[f] : R2;
+    dmin = face64[f].w < dmin ? face64[f].w : dmin;
   }
   vol[c] = V;
   rad[c] = __dsqrt_rn(R2);
+  rin[c] = __double2float_rd(dmin);
   atomicMax(maxf, (int)(f1 - f0));
   atomicMax(maxl, (int)(fvo[f1] - fvo[f0]));
 }
@@ -264,6 +268,7 @@ int grid_prepare(map_ctx* ctx, const map_grid* in, PreparedGrid* g, cudaStream_t
   MAP_TRY(ctx_alloc_grid(ctx, g, (void**)&g->site, nc * 3 * sizeof(double)));
   MAP_TRY(ctx_alloc_grid(ctx, g, (void**)&g->vol, nc * sizeof(double)));
   MAP_TRY(ctx_alloc_grid(ctx, g, (void**)&g->rad, nc * sizeof(double)));
+  MAP_TRY(ctx_alloc_grid(ctx, g, (void**)&g->rin, nc * sizeof(float)));
   MAP_TRY(ctx_alloc_grid(ctx, g, (void**)&g->vx, nv * sizeof(double)));
   MAP_TRY(ctx_alloc_grid(ctx, g, (void**)&g->vy, nv * sizeof(double)));
   MAP_TRY(ctx_alloc_grid(ctx, g, (void**)&g->vz, nv * sizeof(double)));
@@ -306,7 +311,8 @@ int grid_prepare(map_ctx* ctx, const map_grid* in, PreparedGrid* g, cudaStream_t
                                            g->vz, v32, g->site, g->face64, g->face32, g->fsph32, g->edge64,
                                            g->edge32, volf, r2f, d_status); ++ctx->launches;
   CUDA_TRY(cudaGetLastError());
-  prep_cells<<<(unsigned)blocks, tpb, 0, s>>>(nc, g->cell_face_off, g->face_vert_off, volf, r2f, g->vol, g->rad,
+  prep_cells<<<(unsigned)blocks, tpb, 0, s>>>(nc, g->cell_face_off, g->face_vert_off, volf, r2f, g->face64, g->vol,
+                                              g->rad, g->rin,
                                               d_small, d_small + 1); ++ctx->launches;
   CUDA_TRY(cudaGetLastError());
   int64_t hs[4] = {0, 0, 0, 0};

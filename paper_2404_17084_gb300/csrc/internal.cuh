@@ -43,6 +43,7 @@ struct PreparedGrid {
   double* site = nullptr;            // [3*ncell]
   double* vol = nullptr;             // [ncell]
   double* rad = nullptr;             // [ncell] largest vertex distance from the site
+  float* rin = nullptr;              // [ncell] smallest site-to-face-plane distance, rounded down
   double* vx = nullptr;              // vertices (for the pair rule bounding tests)
   double* vy = nullptr;
   double* vz = nullptr;

@@ -29,6 +29,7 @@ struct PairGrid {
   const float4* face32;      // site-relative planes (n, d - n.s) in FP32 (screening)
   const double* site;
   const double* rad;
+  const float* rin;  // inscribed radius: smallest site-to-face-plane distance, rounded down
 };
 
 // The exact rule, FP64, fixed order, no FMA contraction.
@@ -52,7 +53,7 @@ __device__ __forceinline__ bool exact_face(const double4_32a P, double x, double
 // below 1e-6 of the magnitudes involved, and the margin is 1e-5.  No FP64
 // operation runs unless a value falls inside the margin.
 struct SiteSplit {
-  float hx, lx, hy, ly, hz, lz, R;
+  float hx, lx, hy, ly, hz, lz, R, rin;
 };
 
 __device__ __forceinline__ bool pair_rule(const PairGrid& G, const PairTree& T, int64_t c, const SiteSplit& S,
@@ -70,10 +71,12 @@ __device__ __forceinline__ bool pair_rule(const PairGrid& G, const PairTree& T, 
       !exact_dist(G.site[3 * c], G.site[3 * c + 1], G.site[3 * c + 2], G.rad[c], T.xs[k], T.ys[k], T.zs[k], T.hs[k]))
     return false;
   const float thr = 2.f * hf;
-  // every face test passes when the particle lies within 2h of the site: the
-  // site is inside each face plane, so n.r - d < |r - s| for every face (the
+  // every face test passes when the particle lies within 2h + r_in of the
+  // site: each face plane is at least r_in from the site, so
+  // n.r - d = n.(r - s) - (d - n.s) <= |r - s| - r_in < 2h for every face (the
   // 1e-4 relative margin covers the FP32 rounding many times over)
-  if (d2 < thr * thr * 0.9999f) return true;
+  const float tin = thr + S.rin;
+  if (d2 < tin * tin * 0.9999f) return true;
   const float l1 = fabsf(fx) + fabsf(fy) + fabsf(fz);
   for (int64_t f = G.cfo[c]; f < G.cfo[c + 1]; ++f) {
     const float4 F = G.face32[f];
@@ -106,7 +109,7 @@ constexpr int PT_WARPS = 4;  // warps per block of the traversal (1 and 2 measur
 constexpr int PT_MINB = 12;
 
 struct WalkCells {  // per warp: the 32 lanes' cells, one entry per lane
-  float hx[32], lx[32], hy[32], ly[32], hz[32], lz[32], R[32];
+  float hx[32], lx[32], hy[32], ly[32], hz[32], lz[32], R[32], rin[32];
   int64_t c[32], w[32], cnt[32];
   int32_t need[32];  // the lanes that reach the current leaf, in lane order
 };
@@ -133,6 +136,7 @@ __global__ void __launch_bounds__(PT_WARPS * 32, PT_MINB)
   W.hy[lane] = fsy; W.ly[lane] = (float)(sy - (double)fsy);
   W.hz[lane] = fsz; W.lz[lane] = (float)(sz - (double)fsz);
   W.R[lane] = fR;
+  W.rin[lane] = valid ? G.rin[c] : 0.f;
   W.c[lane] = c;
   W.w[lane] = valid ? (FILL ? off[c] : c * PAIR_ROW) : 0;
   W.cnt[lane] = 0;
@@ -176,6 +180,7 @@ __global__ void __launch_bounds__(PT_WARPS * 32, PT_MINB)
             SS.hy = W.hy[l]; SS.ly = W.ly[l];
             SS.hz = W.hz[l]; SS.lz = W.lz[l];
             SS.R = W.R[l];
+            SS.rin = W.rin[l];
             hit = pair_rule(G, T, W.c[l], SS, k0 + j);
           }
           if (__any_sync(0xffffffffu, hit)) {
@@ -229,6 +234,7 @@ __global__ void __launch_bounds__(128) pair_walk_warp(int64_t ncell, const int32
   SS.hy = fsy; SS.ly = (float)(sy - (double)fsy);
   SS.hz = fsz; SS.lz = (float)(sz - (double)fsz);
   SS.R = fR;
+  SS.rin = G.rin[c];
   int32_t* stk = s_stk[warp];
   int32_t* cand = s_cand[warp];
   int64_t w = FILL ? off[c] : c * PAIR_ROW;
@@ -443,7 +449,7 @@ int pairs_build(map_ctx* ctx, const PreparedGrid* g, cudaStream_t s, const PairB
 
   PairTree PT{T.xs, T.ys, T.zs, T.hs, T.split, T.idx, T.begin, T.end, T.first_child, T.nchild, T.bbox_bits,
               T.hmax_bits, T.box32};
-  PairGrid PG{g->cell_face_off, g->face_plane, g->face32, g->site, g->rad};
+  PairGrid PG{g->cell_face_off, g->face_plane, g->face32, g->site, g->rad, g->rin};
   int64_t *count, *off;
   MAP_TRY(ensure_t(ctx, ctx->ws_pairs[0], nc + 1, &count));
   MAP_TRY(ensure_t(ctx, out.off ? *out.off : ctx->ws_pairs[1], nc + 1, &off));
@@ -547,7 +553,7 @@ int pairs_build_graph(map_ctx* ctx, const PreparedGrid* g, cudaStream_t s, const
   CUDA_TRY(cub::DeviceRadixSort::SortPairs(ctx->cub_tmp.p, tb, k_in, k_out, o_in, order, nc, 0, 30, s));
   PairTree PT{T.xs, T.ys, T.zs, T.hs, T.split, T.idx, T.begin, T.end, T.first_child, T.nchild, T.bbox_bits,
               T.hmax_bits, T.box32};
-  PairGrid PG{g->cell_face_off, g->face_plane, g->face32, g->site, g->rad};
+  PairGrid PG{g->cell_face_off, g->face_plane, g->face32, g->site, g->rad, g->rin};
   int64_t *count, *off;
   MAP_TRY(ensure_t(ctx, ctx->ws_pairs[0], nc + 1, &count));
   MAP_TRY(ensure_t(ctx, *out.off, nc + 1, &off));
