@@ -1317,14 +1317,18 @@ def e2e_run(L, torch, ctx, p, g, dev, args, barrier, world):
         barrier()
         t0 = time.perf_counter()
         npairs = 0
+        step_ms = []
         for _ in range(steps):
+            ts = time.perf_counter()
             npairs = one()
+            step_ms.append((time.perf_counter() - ts) * 1e3)
         barrier()
         sec = (time.perf_counter() - t0) / steps
     finally:
         L.map_destroy(ctx_h)
     return {"value": npairs * world / sec, "unit": "pair integrals/s", "h2d_bytes_per_step": int(h2d),
             "d2h_bytes_per_step": int(d2h), "ms_per_step": sec * 1e3, "steps": steps,
+            "ms_each_step": [round(v, 2) for v in step_ms],
             "note": "solve_h on a second context and stream, beside the grid upload"}
 
 

@@ -100,6 +100,7 @@ struct DevTree {
   double* zs = nullptr;
   double* ms = nullptr;
   double* hs = nullptr;
+  float* hs32 = nullptr;             // h in sorted order, FP32 (trees built with h; the pair walk)
   int32_t* owner = nullptr;           // sorted position -> leaf node
   float* split = nullptr;             // 6 floats per sorted position: FP32 hi/lo of x, y, z
   // node arrays

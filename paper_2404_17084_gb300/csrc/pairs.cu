@@ -14,6 +14,7 @@ namespace {
 
 struct PairTree {
   const double *xs, *ys, *zs, *hs;
+  const float* hs32;   // h in FP32 (the screen)
   const float* split;  // 6 per sorted position: FP32 hi/lo of x, y, z
   const int32_t* idx;
   const int64_t *nb, *ne, *fc;
@@ -62,7 +63,7 @@ __device__ __forceinline__ bool pair_rule(const PairGrid& G, const PairTree& T, 
   const float fx = (P[0] - S.hx) + (P[1] - S.lx);
   const float fy = (P[2] - S.hy) + (P[3] - S.ly);
   const float fz = (P[4] - S.hz) + (P[5] - S.lz);
-  const float hf = (float)T.hs[k];
+  const float hf = T.hs32[k];
   const float reach = fmaf(2.f, hf, S.R);
   const float reach2 = reach * reach;
   const float d2 = fx * fx + fy * fy + fz * fz;
@@ -447,7 +448,7 @@ int pairs_build(map_ctx* ctx, const PreparedGrid* g, cudaStream_t s, const PairB
   MAP_TRY(ctx_ensure(ctx, ctx->cub_tmp, tb));
   CUDA_TRY(cub::DeviceRadixSort::SortPairs(ctx->cub_tmp.p, tb, k_in, k_out, o_in, order, nc, 0, 30, s));
 
-  PairTree PT{T.xs, T.ys, T.zs, T.hs, T.split, T.idx, T.begin, T.end, T.first_child, T.nchild, T.bbox_bits,
+  PairTree PT{T.xs, T.ys, T.zs, T.hs, T.hs32, T.split, T.idx, T.begin, T.end, T.first_child, T.nchild, T.bbox_bits,
               T.hmax_bits, T.box32};
   PairGrid PG{g->cell_face_off, g->face_plane, g->face32, g->site, g->rad, g->rin};
   int64_t *count, *off;
@@ -551,7 +552,7 @@ int pairs_build_graph(map_ctx* ctx, const PreparedGrid* g, cudaStream_t s, const
   CUDA_TRY(cub::DeviceRadixSort::SortPairs(nullptr, tb, k_in, k_out, o_in, order, nc, 0, 30, s));
   MAP_TRY(ctx_ensure(ctx, ctx->cub_tmp, tb));
   CUDA_TRY(cub::DeviceRadixSort::SortPairs(ctx->cub_tmp.p, tb, k_in, k_out, o_in, order, nc, 0, 30, s));
-  PairTree PT{T.xs, T.ys, T.zs, T.hs, T.split, T.idx, T.begin, T.end, T.first_child, T.nchild, T.bbox_bits,
+  PairTree PT{T.xs, T.ys, T.zs, T.hs, T.hs32, T.split, T.idx, T.begin, T.end, T.first_child, T.nchild, T.bbox_bits,
               T.hmax_bits, T.box32};
   PairGrid PG{g->cell_face_off, g->face_plane, g->face32, g->site, g->rad, g->rin};
   int64_t *count, *off;

@@ -54,7 +54,7 @@ __global__ void morton_keys(int64_t n, const double* __restrict__ x, const doubl
 __global__ void gather_sorted(int64_t n, const int32_t* __restrict__ idx, const double* __restrict__ x,
                               const double* __restrict__ y, const double* __restrict__ z,
                               const double* __restrict__ m, const double* __restrict__ h, double* xs, double* ys,
-                              double* zs, double* ms, double* hs, float* split) {
+                              double* zs, double* ms, double* hs, float* split, float* hs32) {
   int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (i >= n) return;
   int32_t a = idx[i];
@@ -64,6 +64,7 @@ __global__ void gather_sorted(int64_t n, const int32_t* __restrict__ idx, const 
   zs[i] = pz;
   ms[i] = m ? m[a] : 1.0;
   hs[i] = h ? h[a] : 0.0;
+  if (hs32) hs32[i] = (float)h[a];  // set only for trees built with h
   // FP32 hi/lo split of the coordinates: x = hi + lo to ~2^-48, so that the
   // difference of two nearby points, (hi_j - hi_i) + (lo_j - lo_i), keeps
   // ~24 bits relative to the separation
@@ -452,13 +453,16 @@ int tree_build(map_ctx* ctx, const double* x, const double* y, const double* z, 
   T.ys = T.xs + n; T.zs = T.xs + 2 * n; T.ms = T.xs + 3 * n; T.hs = T.xs + 4 * n;
   MAP_TRY(ensure_t(ctx, ctx->ws_tree[5], n, &T.owner));
   MAP_TRY(ensure_t(ctx, ctx->ws_tree[23], 6 * n, &T.split));
+  T.hs32 = nullptr;
+  if (h) MAP_TRY(ensure_t(ctx, ctx->ws_tree[27], n, &T.hs32));
   morton_keys<<<nblk(n, tpb), tpb, 0, s>>>(n, x, y, z, keys_in, idx_in); ++ctx->launches;
   CUDA_TRY(cudaGetLastError());
   size_t tmp_bytes = 0;
   CUDA_TRY(cub::DeviceRadixSort::SortPairs(nullptr, tmp_bytes, keys_in, T.keys, idx_in, T.idx, n, 0, 63, s));
   MAP_TRY(ctx_ensure(ctx, ctx->cub_tmp, tmp_bytes));
   CUDA_TRY(cub::DeviceRadixSort::SortPairs(ctx->cub_tmp.p, tmp_bytes, keys_in, T.keys, idx_in, T.idx, n, 0, 63, s));
-  gather_sorted<<<nblk(n, tpb), tpb, 0, s>>>(n, T.idx, x, y, z, m, h, T.xs, T.ys, T.zs, T.ms, T.hs, T.split); ++ctx->launches;
+  gather_sorted<<<nblk(n, tpb), tpb, 0, s>>>(n, T.idx, x, y, z, m, h, T.xs, T.ys, T.zs, T.ms, T.hs, T.split,
+                                             T.hs32); ++ctx->launches;
   CUDA_TRY(cudaGetLastError());
 
   // level-synchronous build
@@ -571,13 +575,16 @@ int tree_build_graph(map_ctx* ctx, const double* x, const double* y, const doubl
   T.ys = T.xs + n; T.zs = T.xs + 2 * n; T.ms = T.xs + 3 * n; T.hs = T.xs + 4 * n;
   MAP_TRY(ensure_t(ctx, ctx->ws_tree[5], n, &T.owner));
   MAP_TRY(ensure_t(ctx, ctx->ws_tree[23], 6 * n, &T.split));
+  T.hs32 = nullptr;
+  if (h) MAP_TRY(ensure_t(ctx, ctx->ws_tree[27], n, &T.hs32));
   morton_keys<<<nblk(n, tpb), tpb, 0, s>>>(n, x, y, z, keys_in, idx_in); ++ctx->launches;
   CUDA_TRY(cudaGetLastError());
   size_t tmp_bytes = 0;
   CUDA_TRY(cub::DeviceRadixSort::SortPairs(nullptr, tmp_bytes, keys_in, T.keys, idx_in, T.idx, n, 0, 63, s));
   MAP_TRY(ctx_ensure(ctx, ctx->cub_tmp, tmp_bytes));
   CUDA_TRY(cub::DeviceRadixSort::SortPairs(ctx->cub_tmp.p, tmp_bytes, keys_in, T.keys, idx_in, T.idx, n, 0, 63, s));
-  gather_sorted<<<nblk(n, tpb), tpb, 0, s>>>(n, T.idx, x, y, z, m, h, T.xs, T.ys, T.zs, T.ms, T.hs, T.split); ++ctx->launches;
+  gather_sorted<<<nblk(n, tpb), tpb, 0, s>>>(n, T.idx, x, y, z, m, h, T.xs, T.ys, T.zs, T.ms, T.hs, T.split,
+                                             T.hs32); ++ctx->launches;
   CUDA_TRY(cudaGetLastError());
 
   // node flags of every level, their scan, the node records
