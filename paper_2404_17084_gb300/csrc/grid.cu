@@ -28,7 +28,7 @@ __global__ void vert32(int64_t nv, const double* __restrict__ vx, const double* 
 // One thread per face: site-relative planes, the face's bounding sphere and
 // edge records, its term dr * area / 3 of the cell volume (divergence
 // theorem) and the largest squared vertex distance from the site.  The
-// FP64 pipe runs at 1/64 of the FP32 rate, so FP64 work is kept to the
+// FP64 pipe runs at about 1/74 of the FP32 rate, so FP64 work is kept to the
 // site-relative differences, one component of the area sum and the exact
 // squares of the few vertices that can be the farthest.
 __global__ void prep_faces(int64_t nface, const int32_t* __restrict__ fcell, const int64_t* __restrict__ fvo,

@@ -395,7 +395,7 @@ __global__ void __launch_bounds__(HS_WARPS * 32)
     h_solve_leaves(int64_t n, HsTree T, const double* __restrict__ h0s, double hfact, double tol, double* hout,
                    int32_t* route) {
   // the build's type for h: the mixed build iterates in FP32 (its sums are
-  // FP32, and GB300's FP64 rate is 1/64 of its FP32 rate)
+  // FP32, and GB300's FP64 rate is about 1/74 of its FP32 rate)
   using S = typename std::conditional<MIXED, float, double>::type;
   const S hf_s = (S)hfact, hf3_s = (S)(hfact / 3.0), tol_s = (S)tol;
   const S hf_lo = (S)(hfact - (double)hf_s);
@@ -467,7 +467,7 @@ __global__ void __launch_bounds__(HS_WARPS * 32)
         const double lo = g0 / 16.0, hi = g0 * 16.0;
         // (the mixed build bisects on its FP32 sums too: the root moves by
         // ~1e-7 relative, inside the build's 1e-6, and GB300's FP64 rate
-        // is 1/64 of its FP32 rate)
+        // is about 1/74 of its FP32 rate)
         auto g = [&](double hh) {
           S nn, dn;
           warp_density<MIXED>(T, W, B, k, (S)hh, nn, dn);
